@@ -1,0 +1,558 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than its own formulas: conservation
+laws, derivative identities checked by finite differences, closed-form two-body orbits,
+the convergence order of the integrator and the paper's printed few-body results.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2011_14984_gb300 import ics
+from conftest import load_solar_system
+
+
+# ----------------------------------------------------------------------------------------
+# helpers written independently of the oracle
+# ----------------------------------------------------------------------------------------
+
+def kepler_state(a, e, M, GM):
+    """Relative position/velocity of a Kepler orbit (pericentre on +x), textbook Newton
+    iteration on Kepler's equation E - e sin E = M."""
+    E = M if e < 0.8 else math.pi
+    for _ in range(100):
+        E -= (E - e * math.sin(E) - M) / (1 - e * math.cos(E))
+    r = a * (1 - e * math.cos(E))
+    n = math.sqrt(GM / a ** 3)
+    b = a * math.sqrt(1 - e * e)
+    Ed = n / (1 - e * math.cos(E))
+    return (np.array([a * (math.cos(E) - e), b * math.sin(E), 0.0]),
+            np.array([-a * math.sin(E) * Ed, b * math.cos(E) * Ed, 0.0]), r)
+
+
+def binary(m1, m2, a, e, M=0.0, G=1.0):
+    mt = m1 + m2
+    rx, rv, _ = kepler_state(a, e, M, G * mt)
+    m = np.array([m1, m2])
+    x = np.stack([(m2 / mt) * rx, -(m1 / mt) * rx])
+    v = np.stack([(m2 / mt) * rv, -(m1 / mt) * rv])
+    return m, x, v
+
+
+def rel_err(a, b):
+    return np.linalg.norm(a - b, axis=-1) / np.maximum(np.linalg.norm(b, axis=-1), 1e-300)
+
+
+ALL = lambda n: np.arange(n, dtype=np.int32)  # noqa: E731
+
+
+# ----------------------------------------------------------------------------------------
+# Newtonian acceleration (Eq. acc-newton)
+# ----------------------------------------------------------------------------------------
+
+def test_acc_total_force_vanishes_unequal_masses():
+    """sum_i m_i a_i = 0 (pairwise antisymmetry, Newton's third law)."""
+    n = 300
+    m, x, _ = ics.plummer(n, 3, masses=ics.kroupa_masses(n, 3))
+    a = oracle.acc(m, x, ALL(n), ALL(n))
+    F = (m[:, None] * a).sum(0)
+    scale = (m[:, None] * np.abs(a)).sum()
+    assert np.all(np.abs(F) < 1e-14 * scale)
+
+
+def test_acc_is_minus_gradient_of_pair_potential():
+    """a_i = -(1/m_i) dU/dx_i with U = -G sum_{i<j} m_i m_j / r_ij (central differences of
+    the potential energy, i.e. of a different function than the force sum)."""
+    n = 12
+    rng = np.random.default_rng(5)
+    m = rng.random(n) + 0.1
+    x = rng.standard_normal((n, 3))
+    v = np.zeros((n, 3))
+    G = 0.7
+    a = oracle.acc(m, x, ALL(n), ALL(n), G=G)
+    h = 1e-5
+    fd = np.zeros_like(a)
+    for i in range(n):
+        for c in range(3):
+            xp = x.copy(); xp[i, c] += h
+            xm = x.copy(); xm[i, c] -= h
+            Up = oracle.energy(m, xp, v, G=G)["U"]
+            Um = oracle.energy(m, xm, v, G=G)["U"]
+            fd[i, c] = -(Up - Um) / (2 * h) / m[i]
+    assert np.max(rel_err(a, fd)) < 1e-7
+
+
+def test_acc_softened_is_minus_gradient_of_softened_potential():
+    n = 8
+    rng = np.random.default_rng(6)
+    m = rng.random(n) + 0.1
+    x = 0.05 * rng.standard_normal((n, 3))
+    v = np.zeros((n, 3))
+    eps2 = 0.03 ** 2
+    a = oracle.acc(m, x, ALL(n), ALL(n), eps2=eps2)
+    h = 1e-6
+    fd = np.zeros_like(a)
+    for i in range(n):
+        for c in range(3):
+            xp = x.copy(); xp[i, c] += h
+            xm = x.copy(); xm[i, c] -= h
+            fd[i, c] = -(oracle.energy(m, xp, v, eps2=eps2)["U"]
+                         - oracle.energy(m, xm, v, eps2=eps2)["U"]) / (2 * h) / m[i]
+    assert np.max(rel_err(a, fd)) < 1e-6
+
+
+def test_acc_far_field_of_plummer_sphere_is_monopole():
+    """A test particle far outside a centred cluster feels -G M x / r^3 up to O((r_s/r)^2)."""
+    n = 2048
+    m, x, _ = ics.plummer(n, 4, max_mass_fraction=0.9)
+    R = 200.0
+    probe = np.array([[R / math.sqrt(3)] * 3])
+    xs = np.concatenate([x, probe])
+    ms = np.concatenate([m, [1e-12]])
+    a = oracle.acc(ms, xs, np.array([n]), ALL(n))[0]
+    expect = -m.sum() * probe[0] / R ** 3
+    assert np.linalg.norm(a - expect) / np.linalg.norm(expect) < 1e-4
+
+
+def test_acc_circular_binary_centripetal():
+    """Each body of a circular binary needs a = v^2 / r toward the centre of mass."""
+    m, x, v = binary(0.3, 0.7, 2.0, 0.0, G=1.3)
+    a = oracle.acc(m, x, ALL(2), ALL(2), G=1.3)
+    for i in range(2):
+        r = np.linalg.norm(x[i])
+        want = -(v[i] @ v[i]) / r * x[i] / r
+        assert np.linalg.norm(a[i] - want) < 1e-13 * np.linalg.norm(want)
+
+
+def test_acc_brute_force_high_precision():
+    """Index bookkeeping and accumulation against a 40-digit evaluation at N = 7."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    n = 7
+    rng = np.random.default_rng(8)
+    m = rng.random(n) + 0.05
+    x = rng.standard_normal((n, 3))
+    A = np.array([4, 0, 6], dtype=np.int32)
+    B = np.array([1, 4, 2, 6, 5], dtype=np.int32)
+    a = oracle.acc(m, x, A, B)
+    for k, i in enumerate(A):
+        s = [mpmath.mpf(0)] * 3
+        for j in B:
+            if j == i:
+                continue
+            d = [mpmath.mpf(x[j, c]) - mpmath.mpf(x[i, c]) for c in range(3)]
+            r = mpmath.sqrt(sum(t * t for t in d))
+            for c in range(3):
+                s[c] += mpmath.mpf(m[j]) * d[c] / r ** 3
+        ref = np.array([float(t) for t in s])
+        assert np.linalg.norm(a[k] - ref) <= 1e-14 * np.linalg.norm(ref)
+
+
+def test_acc_coincident_particles_rejected():
+    m = np.ones(3)
+    x = np.array([[0.0, 0, 0], [1.0, 0, 0], [1.0, 0, 0]])
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.acc(m, x, ALL(3), ALL(3))
+    assert e.value.code == oracle.ECOINCIDENT
+    # softening makes the same configuration regular
+    oracle.acc(m, x, ALL(3), ALL(3), eps2=1e-4)
+
+
+# ----------------------------------------------------------------------------------------
+# gradient acceleration (Eq. acc-gradient-g, Eq. acc-gradient, Eqs. force-gradient-inter)
+# ----------------------------------------------------------------------------------------
+
+def _g_from(m, x, A, B, G=1.0, eps2=0.0):
+    """g via accel_gradient with eps chosen so that a~ - a = g."""
+    a, at = oracle.accel_gradient(m, x, A, B, eps_grad=math.sqrt(48.0), G=G, eps2=eps2)
+    return a, at - a
+
+
+@pytest.mark.parametrize("eps2", [0.0, 0.02 ** 2])
+def test_gradient_is_derivative_of_acc_along_acc(eps2):
+    """d/dh a_i(x + h a) at h = 0 equals G sum_j m_j T(x_ji) a_ji = g_i / 2 when every
+    particle k is displaced by h a_k; checked with Richardson-extrapolated differences."""
+    n = 48
+    m, x, _ = ics.plummer(n, 12, masses=ics.kroupa_masses(n, 12))
+    A = ALL(n)
+    a, g = _g_from(m, x, A, A, eps2=eps2)
+    g_direct = oracle.grad(m, x, A, a, A, a, eps2=eps2)
+    np.testing.assert_allclose(g, g_direct, rtol=1e-9, atol=1e-12 * np.abs(g_direct).max())
+    d = np.linalg.norm(x[:, None] - x[None], axis=-1) + np.eye(n)
+    h = 1e-4 * d.min() / np.abs(a).max()
+
+    def D(hh):
+        return (oracle.acc(m, x + hh * a, A, A, eps2=eps2)
+                - oracle.acc(m, x - hh * a, A, A, eps2=eps2)) / hh
+    fd = (4 * D(h / 2) - D(h)) / 3
+    assert np.max(rel_err(g, fd)) < 1e-6
+
+
+def test_gradient_two_body_closed_form():
+    """Two bodies: g_1 = 4 G (m_1 + m_2) a_1 / r^3, so a~ = (1 + eps^2 G M / (12 r^3)) a."""
+    G = 1.7
+    m, x, _ = binary(0.25, 1.5, 0.8, 0.3, M=1.1, G=G)
+    eps = 0.05
+    a, at = oracle.accel_gradient(m, x, ALL(2), ALL(2), eps, G=G)
+    r = np.linalg.norm(x[0] - x[1])
+    factor = 1 + eps ** 2 * G * m.sum() / (12 * r ** 3)
+    np.testing.assert_allclose(at, factor * a, rtol=1e-14)
+
+
+def test_gradient_total_vanishes():
+    """sum_i m_i g_i = 0: the summand m_i m_j T(x_ji) a_ji is antisymmetric in i, j."""
+    n = 200
+    m, x, _ = ics.plummer(n, 13, masses=ics.kroupa_masses(n, 13))
+    a, g = _g_from(m, x, ALL(n), ALL(n))
+    tot = (m[:, None] * g).sum(0)
+    assert np.all(np.abs(tot) < 1e-12 * (m[:, None] * np.abs(g)).sum())
+
+
+def _V(m, x, S, F=None):
+    """Gradient potential V = -sum_k m_k |a_k|^2 (Eq. potential-gradient); with F given, the
+    inter-level V_S + V_F of Eq. gs-gf built from the S-F accelerations only."""
+    if F is None:
+        a = oracle.acc(m, x, S, S)
+        return -np.sum(m[S] * np.sum(a * a, axis=1))
+    aS = oracle.acc(m, x, S, F)
+    aF = oracle.acc(m, x, F, S)
+    return -np.sum(m[S] * np.sum(aS * aS, axis=1)) - np.sum(m[F] * np.sum(aF * aF, axis=1))
+
+
+@pytest.mark.parametrize("cross", [False, True])
+def test_gradient_is_minus_gradient_of_gradient_potential(cross):
+    """g_i = -(1/m_i) dV/dx_i by central differences of V (Eqs. potential-gradient, gs-gf)."""
+    n = 7
+    rng = np.random.default_rng(21)
+    m = rng.random(n) + 0.2
+    x = rng.standard_normal((n, 3))
+    if cross:
+        S = np.array([0, 3, 5], dtype=np.int32)
+        F = np.array([1, 2, 4, 6], dtype=np.int32)
+        _, gS = _g_from(m, x, S, F)
+        _, gF = _g_from(m, x, F, S)
+        g = np.zeros((n, 3)); g[S] = gS; g[F] = gF
+        V = lambda xx: _V(m, xx, S, F)  # noqa: E731
+    else:
+        A = ALL(n)
+        _, g = _g_from(m, x, A, A)
+        V = lambda xx: _V(m, xx, A)  # noqa: E731
+    h = 1e-5
+    fd = np.zeros((n, 3))
+    for i in range(n):
+        for c in range(3):
+            xp = x.copy(); xp[i, c] += h
+            xm = x.copy(); xm[i, c] -= h
+            fd[i, c] = -(V(xp) - V(xm)) / (2 * h) / m[i]
+    assert np.max(rel_err(g, fd)) < 1e-6
+
+
+def test_accel_gradient_rejects_partial_overlap():
+    m, x, _ = ics.plummer(10, 1)
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.accel_gradient(m, x, np.array([0, 1, 2]), np.array([2, 3]), 0.1)
+    assert e.value.code == oracle.EINVAL
+
+
+# ----------------------------------------------------------------------------------------
+# time-steps (Eqs. dt-freefall, dt-flyby, their derivatives, Eq. time-step-factor)
+# ----------------------------------------------------------------------------------------
+
+def test_symmetrisation_factor_properties():
+    """s(0) = 1; s(d) + s(-d) = 2 (antisymmetric about (0, tau)); s solves the harmonic-mean
+    definition 2 / s = 1 + 1 / (1 + s d) with tau(t + tau_sym) expanded to first order;
+    harmonic never exceeds arithmetic; s in (0, 2)."""
+    assert oracle.sym_harmonic(0.0) == 1.0
+    for d in np.concatenate([np.linspace(-50, 50, 401), [1e-12, -1e-9, 1e6, -1e6]]):
+        s = oracle.sym_harmonic(d)
+        assert 0.0 < s < 2.0
+        assert abs(s + oracle.sym_harmonic(-d) - 2.0) < 1e-14
+        # harmonic mean condition s (2 + s d) = 2 (1 + s d), residual scaled by its terms
+        res = s * (2 + s * d) - 2 * (1 + s * d)
+        assert abs(res) < 1e-14 * (s * (2 + abs(s * d)) + 2 * (1 + abs(s * d)))
+        if d < 2:
+            sa = oracle.sym_arithmetic(d)
+            # arithmetic definition: s = (1 + (1 + s d)) / 2
+            assert abs(sa - 0.5 * (1 + (1 + sa * d))) < 1e-12 * max(1.0, abs(sa))
+            assert s <= sa * (1 + 1e-15)
+
+
+def test_circular_binary_timestep_is_eta_period_over_two_pi():
+    """Eq. eta-two-pi: both criteria give tau = eta P / (2 pi) for a circular binary."""
+    for (m1, m2, a, G, eta) in [(0.5, 0.5, 1.0, 1.0, 0.2), (10.0, 10.0, 10.0, 39.47, 0.01),
+                                (1.0, 1e-3, 5.2, 2.959122e-4, 0.05)]:
+        m, x, v = binary(m1, m2, a, 0.0, G=G)
+        P = 2 * math.pi * math.sqrt(a ** 3 / (G * (m1 + m2)))
+        tau = oracle.timesteps(m, x, v, ALL(2), G=G, eta=eta)
+        np.testing.assert_allclose(tau, eta * P / (2 * math.pi), rtol=1e-13)
+        t = oracle.pair_timescales(x[0], v[0], m1, x[1], v[1], m2, G=G)
+        np.testing.assert_allclose([t[0], t[2]], [P / (2 * math.pi)] * 2, rtol=1e-13)
+
+
+def test_pericentre_timestep_closed_form():
+    """At pericentre r.v = 0 so s = 1, and v_p^2 = G M (1 + e) / r_p makes the fly-by time
+    the shorter one: tau = eta (r_p^3 / (G M (1 + e)))^(1/2)."""
+    m1, m2, a, e, G, eta = 0.6, 0.4, 1.5, 0.9, 1.0, 0.1
+    m, x, v = binary(m1, m2, a, e, G=G)
+    rp = a * (1 - e)
+    tau = oracle.timesteps(m, x, v, ALL(2), G=G, eta=eta)
+    np.testing.assert_allclose(tau, eta * math.sqrt(rp ** 3 / (G * (m1 + m2) * (1 + e))),
+                               rtol=1e-12)
+
+
+def test_freefall_derivative_matches_finite_difference():
+    """dt_ff/dt along straight-line motion (no acceleration needed for t_ff)."""
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        xi, xj, vi, vj = rng.standard_normal((4, 3))
+        mi, mj = rng.random(2) + 0.1
+        h = 1e-5
+        tp = oracle.pair_timescales(xi + h * vi, vi, mi, xj + h * vj, vj, mj)[0]
+        tm = oracle.pair_timescales(xi - h * vi, vi, mi, xj - h * vj, vj, mj)[0]
+        t = oracle.pair_timescales(xi, vi, mi, xj, vj, mj)
+        assert abs(t[1] - (tp - tm) / (2 * h)) < 1e-7 * max(1.0, abs(t[1]))
+
+
+@pytest.mark.parametrize("e", [0.0, 0.3, 0.9])
+def test_flyby_derivative_exact_on_isolated_binary(e):
+    """The two-body form of dt_fb/dt is exact for an isolated binary: compare with the
+    derivative of r(t)/|v(t)| along the closed-form Kepler orbit."""
+    G, m1, m2, a = 1.0, 0.7, 0.3, 1.0
+    GM = G * (m1 + m2)
+    n = math.sqrt(GM / a ** 3)
+    for M in [0.3, 1.1, 2.0, 4.0, 5.5]:
+        rx, rv, _ = kepler_state(a, e, M, GM)
+        t = oracle.pair_timescales(rx, rv, m1, np.zeros(3), np.zeros(3), m2, G=G)
+        h = 1e-5
+
+        def tfb(MM):
+            px, pv, _ = kepler_state(a, e, MM, GM)
+            return np.linalg.norm(px) / np.linalg.norm(pv)
+        fd = (tfb(M + n * h) - tfb(M - n * h)) / (2 * h)
+        assert abs(t[3] - fd) < 1e-6 * max(1.0, abs(fd))
+        # the free-fall derivative along the same orbit
+        def tff(MM):
+            px, _, _ = kepler_state(a, e, MM, GM)
+            return math.sqrt(np.linalg.norm(px) ** 3 / GM)
+        fd_ff = (tff(M + n * h) - tff(M - n * h)) / (2 * h)
+        assert abs(t[1] - fd_ff) < 1e-6 * max(1.0, abs(fd_ff))
+
+
+def test_timesteps_min_over_set_and_degenerate_cases():
+    """tau_i is the minimum over the other members of the set only (Sec. 4.3: 'the same
+    level'), a single particle has tau = +inf, and zero relative velocity leaves only the
+    free-fall criterion."""
+    m = np.array([1.0, 1.0, 1.0])
+    x = np.array([[0.0, 0, 0], [1.0, 0, 0], [10.0, 0, 0]])
+    v = np.zeros((3, 3))
+    eta = 0.3
+    tau = oracle.timesteps(m, x, v, ALL(3), eta=eta)
+    tff01 = math.sqrt(1.0 / 2.0)
+    tff12 = math.sqrt(9.0 ** 3 / 2.0)
+    np.testing.assert_allclose(tau, eta * np.array([tff01, tff01, tff12]), rtol=1e-14)
+    tau_sub = oracle.timesteps(m, x, v, np.array([0, 2], dtype=np.int32), eta=eta)
+    np.testing.assert_allclose(tau_sub, eta * math.sqrt(10.0 ** 3 / 2.0), rtol=1e-14)
+    assert np.isinf(oracle.timesteps(m, x, v, np.array([1], dtype=np.int32))[0])
+
+
+def test_timestep_brute_force_high_precision():
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    n = 6
+    rng = np.random.default_rng(31)
+    m = rng.random(n) + 0.1
+    x = rng.standard_normal((n, 3))
+    v = rng.standard_normal((n, 3))
+    G, eta = 1.3, 0.17
+    P = np.array([5, 1, 3, 0], dtype=np.int32)
+    tau = oracle.timesteps(m, x, v, P, G=G, eta=eta)
+    mp = mpmath.mpf
+
+    def s(d):
+        return (d + mpmath.sqrt(1 + d * d) - 1) / d if d != 0 else mp(1)
+    for k, i in enumerate(P):
+        best = mpmath.inf
+        for j in P:
+            if j == i:
+                continue
+            r = [mp(x[i, c]) - mp(x[j, c]) for c in range(3)]
+            u = [mp(v[i, c]) - mp(v[j, c]) for c in range(3)]
+            r2 = sum(t * t for t in r); v2 = sum(t * t for t in u)
+            rv = sum(r[c] * u[c] for c in range(3))
+            rr = mpmath.sqrt(r2)
+            gm = mp(G) * (mp(m[i]) + mp(m[j]))
+            tff = mpmath.sqrt(rr ** 3 / gm)
+            tfb = rr / mpmath.sqrt(v2)
+            dff = mp(eta) * mp(1.5) * rv / r2 * tff
+            dfb = mp(eta) * rv / r2 * (1 + gm / (v2 * rr)) * tfb
+            best = min(best, s(dff) * eta * tff, s(dfb) * eta * tfb)
+        assert abs(tau[k] - float(best)) <= 1e-13 * float(best)
+
+
+# ----------------------------------------------------------------------------------------
+# partition (Sec. 3.1)
+# ----------------------------------------------------------------------------------------
+
+def test_partition_stable_and_tie_goes_slow():
+    P = np.array([7, 3, 9, 1, 4, 8], dtype=np.int32)
+    tau = np.array([0.5, 0.25, 0.25, 1.0, 0.1, 0.2499999])
+    S, F = oracle.partition(P, tau, 0.25)
+    assert S.tolist() == [7, 3, 9, 1]
+    assert F.tolist() == [4, 8]
+    S, F = oracle.partition(P, tau, 2.0)
+    assert S.size == 0 and F.tolist() == P.tolist()
+    S, F = oracle.partition(P[:0], tau[:0], 1.0)
+    assert S.size == 0 and F.size == 0
+
+
+# ----------------------------------------------------------------------------------------
+# FSI and HHS-FSI (Algorithms fsi and hhs-fsi)
+# ----------------------------------------------------------------------------------------
+
+def _fsi_orbit_error(e, n_steps):
+    G, m1, m2, a = 1.0, 0.5, 0.5, 1.0
+    m, x, v = binary(m1, m2, a, e, G=G)
+    P = 2 * math.pi * math.sqrt(a ** 3 / (G * (m1 + m2)))
+    dt = P / n_steps
+    S = ALL(2)
+    for _ in range(n_steps):
+        x, v = oracle.fsi(m, x, v, S, dt, G=G)
+    rx, _, _ = kepler_state(a, e, 2 * math.pi, G * (m1 + m2))
+    return np.linalg.norm((x[0] - x[1]) - rx) / a, m, x, v
+
+
+@pytest.mark.parametrize("e", [0.0, 0.5])
+def test_fsi_is_fourth_order_on_kepler_orbit(e):
+    """Halving dt cuts the position error after one period about 16x (Eq. fsi is a fourth-
+    order method; without the gradient term it would be second order)."""
+    errs = [_fsi_orbit_error(e, n)[0] for n in (100, 200, 400)]
+    orders = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert all(3.7 < p < 4.3 for p in orders), (errs, orders)
+
+
+def test_fsi_conserves_momentum_exactly_for_equal_masses_and_L_to_roundoff():
+    """Paper, Sec. 6.1.1: Delta P = 0 exactly for the equal-mass binaries and
+    |Delta L / L| below 1e-12."""
+    m, x, v = binary(10.0, 10.0, 10.0, 0.9, G=1.0)
+    e0 = oracle.energy(m, x, v)
+    S = ALL(2)
+    for _ in range(2000):
+        x, v = oracle.fsi(m, x, v, S, 0.05)
+    e1 = oracle.energy(m, x, v)
+    assert np.all(e1["P"] == e0["P"])
+    assert np.linalg.norm(e1["L"] - e0["L"]) / np.linalg.norm(e0["L"]) < 1e-12
+
+
+def test_fsi_time_reversible():
+    """A symmetric composition: k steps forward then k steps with -dt return the start."""
+    m, x0, v0 = ics.plummer(16, 9)
+    x, v = x0, v0
+    S = ALL(16)
+    for _ in range(20):
+        x, v = oracle.fsi(m, x, v, S, 1e-3)
+    for _ in range(20):
+        x, v = oracle.fsi(m, x, v, S, -1e-3)
+    assert np.max(np.abs(x - x0)) < 1e-12 and np.max(np.abs(v - v0)) < 1e-11
+
+
+def test_hhs_fsi_with_all_particles_slow_is_two_half_fsi_steps():
+    """If every tau_i >= tau_pivot then S = P, F is empty and hhs_fsi(P, tau) reduces to
+    fsi(P, tau/2) twice (the inter-level kicks vanish) -- identical bits."""
+    m, x, v = ics.plummer(32, 10)
+    P = ALL(32)
+    tau = oracle.timesteps(m, x, v, P)
+    piv = 0.5 * tau.min()
+    xh, vh = oracle.hhs_fsi(m, x, v, P, piv)
+    xf, vf = oracle.fsi(m, x, v, P, piv / 2)
+    xf, vf = oracle.fsi(m, xf, vf, P, piv / 2)
+    assert np.array_equal(xh, xf) and np.array_equal(vh, vf)
+
+
+def test_hhs_fsi_depth_limit():
+    m, x, v = binary(0.5, 0.5, 1e-3, 0.0)
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.hhs_fsi(m, x, v, ALL(2), 1.0, eta=0.2, max_depth=3)
+    assert e.value.code == oracle.EDEPTH
+
+
+def _kepler_adaptive_dE(eta, e, n_periods):
+    """max |dE/E| over top-level steps of P/8 (the error oscillates along the orbit)."""
+    G = 1.0
+    m, x, v = binary(0.5, 0.5, 1.0, e, G=G)
+    E0 = oracle.energy(m, x, v)["E"]
+    P = 2 * math.pi
+    # top-level pivot above the largest step so that the pair always sits on a deeper level
+    dt = P / 8
+    worst = 0.0
+    for _ in range(8 * n_periods):
+        x, v = oracle.steps(m, x, v, dt, 1, G=G, eta=eta)
+        worst = max(worst, abs((oracle.energy(m, x, v)["E"] - E0) / E0))
+    return worst
+
+
+@pytest.mark.parametrize("e", [0.1, 0.5])
+def test_kepler_energy_error_scales_as_eta_to_the_fourth(e):
+    """Paper Sec. 6.1.1: |dE/E| ~ eta^4 for binaries with adaptive (hierarchical) steps.
+    (An exactly circular orbit keeps its energy to round-off at these steps, so the
+    eccentric orbits carry the check.)"""
+    etas = (0.128, 0.064, 0.032)
+    errs = [_kepler_adaptive_dE(eta, e, 2) for eta in etas]
+    orders = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert all(3.5 < p < 4.5 for p in orders), (errs, orders)
+
+
+def _solar(eta, years, fsi_only=False):
+    names, m, x, v, G = load_solar_system()
+    e0 = oracle.energy(m, x, v, G=G)
+    dt = 4096.0  # days: above every particle step, so all bodies sit on deeper levels
+    n = int(round(years * 365.25 / dt))
+    oracle.reset_counters()
+    x1, v1 = oracle.steps(m, x, v, dt, n, G=G, eta=eta)
+    c = oracle.counters()
+    e1 = oracle.energy(m, x1, v1, G=G)
+    return abs((e1["E"] - e0["E"]) / e0["E"]), e0, e1, c
+
+
+@pytest.mark.slow
+def test_solar_system_hhs_fsi_fourth_order_and_conservation():
+    """Paper Sec. 6.1.2 and its Fig. solarsystem: HHS-FSI on the Sun and four giants is of
+    fourth order (|dE/E| ~ eta^4) with the planets on several hierarchy levels, and at
+    eta = 0.004 |dE/E| ~ 1e-13, |dL/L| ~ 1e-14, |dP| < 1e-15 (here over 1000 yr)."""
+    errs = []
+    for eta in (0.1, 0.05, 0.025):
+        dE, _, _, c = _solar(eta, 200)
+        errs.append(dE)
+        assert c["max_depth"] >= 3  # bodies spread over several levels
+    orders = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert all(3.3 < p < 4.7 for p in orders), (errs, orders)
+    dE, e0, e1, _ = _solar(0.004, 1000)
+    assert dE < 1e-12
+    assert np.linalg.norm(e1["L"] - e0["L"]) / np.linalg.norm(e0["L"]) < 1e-13
+    assert np.linalg.norm(e1["P"] - e0["P"]) < 1e-15
+
+
+# ----------------------------------------------------------------------------------------
+# energy, momentum, angular momentum
+# ----------------------------------------------------------------------------------------
+
+def test_energy_and_angular_momentum_of_kepler_binary():
+    """E = -G m1 m2 / (2a) and |L| = mu (G M a (1 - e^2))^(1/2) for any orbital phase."""
+    G, m1, m2, a, e = 2.0, 0.3, 0.9, 1.7, 0.6
+    for M in (0.0, 1.0, 3.0):
+        m, x, v = binary(m1, m2, a, e, M=M, G=G)
+        en = oracle.energy(m, x, v, G=G)
+        assert abs(en["E"] - (-G * m1 * m2 / (2 * a))) < 1e-14
+        mu = m1 * m2 / (m1 + m2)
+        assert abs(np.linalg.norm(en["L"]) - mu * math.sqrt(G * (m1 + m2) * a * (1 - e * e))) < 1e-14
+        assert np.max(np.abs(en["P"])) < 1e-15
+
+
+def test_plummer_henon_units_virial():
+    """The generator's Plummer sphere in Henon units: E ~ -1/4 and 2T/|U| ~ 1."""
+    m, x, v = ics.plummer(4096, 2)
+    en = oracle.energy(m, x, v)
+    assert abs(en["E"] + 0.25) < 0.02
+    assert abs(2 * en["T"] / abs(en["U"]) - 1) < 0.06

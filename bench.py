@@ -1,0 +1,410 @@
+#!/usr/bin/env python3
+"""Benchmark of the HHS-FSI hot path: acc + gradient interactions per second.
+
+Workload (default): Plummer sphere N = 65536, equal masses, Henon units (G = M = 1),
+seed 2, eta = 0.2, top-level pivot step 2^-7, mixed precision (FP32 pair bodies on
+float-float separations, FP64 state and sums).
+
+One timed step = one top-level HHS-FSI step (Algorithm hhs-fsi on all particles: time-step
+pass, partition, inter-level acc / gradient passes and kicks, FSI steps of the slow sets,
+recursion into the fast sets).  The energy / momentum / angular momentum reduction (the
+on-the-fly analysis) runs once at the end of the timed region, as the paper samples it on a
+cadence rather than every step.  `value` = acc + gradient pair interactions evaluated in the
+timed region / device time; L2 is flushed (256 MiB write) before every timed step.
+
+Extra keys: full_pass (one acc + gradient pass over all N), fp64 (the same workload in FP64
+mode: full pass and 16 hierarchical steps), energy (|dE/E| after 16 steps from the initial
+state in both precisions), roofline (dominant pair kernel vs the CUDA-core peak),
+cpu_baseline (the FP64 oracle on the host cores), e2e (through the C-ABI with host buffers).
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FLOPS_PER_PAIR = {"acc": 20.0, "grad": 38.0, "tstep": 45.0}
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate
+METRIC = "acc+gradient interactions/s"
+UNIT = "interactions/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=16)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="frost", choices=["frost", "reference"])
+    p.add_argument("--workload", default="plummer_64k")
+    p.add_argument("--dt", type=float, default=2.0 ** -7)
+    p.add_argument("--eta", type=float, default=0.2)
+    p.add_argument("--fp64-steps", type=int, default=16)
+    p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ---------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"frost_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle on a bounded sample of the workload
+# ---------------------------------------------------------------------------------------
+def oracle_sample(workload, n_sample, seed=0):
+    from paper_2011_14984_gb300 import ics
+    m, x, v = ics.workload(workload)
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(m.size, n_sample, replace=False)).astype(np.int32)
+    return m, x, v, idx
+
+
+def time_oracle_pass(m, x, idx, eps_grad):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.accel_gradient(m, x, idx, idx, eps_grad)
+    dt = time.perf_counter() - t0
+    n = idx.size
+    return 2.0 * n * (n - 1), dt  # acc + gradient interactions of the pass
+
+
+def cpu_baseline(workload, seconds, n_sample=16384):
+    import oracle
+    m, x, v, idx = oracle_sample(workload, n_sample)
+    pairs = 0.0
+    elapsed = 0.0
+    reps = 0
+    while elapsed < seconds or reps == 0:
+        p, dt = time_oracle_pass(m, x, idx, 2.0 ** -7)
+        pairs += p
+        elapsed += dt
+        reps += 1
+    return {"value": pairs / elapsed, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{reps} FP64 acc+gradient passes (same-set, a~ with eps=2^-7) over a random "
+                      f"{n_sample}-particle subset of {workload}, {elapsed:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    n_sample = 8192
+    m, x, v, idx = oracle_sample(args.workload, n_sample)
+    for _ in range(max(args.warmup, 0)):
+        time_oracle_pass(m, x, idx, args.dt)
+    pairs = 0.0
+    elapsed = 0.0
+    for _ in range(args.steps):
+        p, dt = time_oracle_pass(m, x, idx, args.dt)
+        pairs += p
+        elapsed += dt
+    value = pairs / elapsed
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * elapsed / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "sample": f"{n_sample}-particle subset",
+                       "step": "one FP64 acc+gradient pass over the subset"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": f"{args.steps} FP64 acc+gradient passes over a random "
+                                       f"{n_sample}-particle subset of {args.workload}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+# the CUDA path
+# ---------------------------------------------------------------------------------------
+def run_frost(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2011_14984_gb300 import build as fbuild
+    from paper_2011_14984_gb300 import frost as fr
+    from paper_2011_14984_gb300 import ics
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    fbuild.build()
+    fr.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    m, x, v = ics.workload(args.workload)
+    n = m.size
+    E0_ref = None
+
+    def new(prec):
+        return fr.Frost(m, x, v, G=1.0, eta=args.eta, precision=prec, stream=stream.cuda_stream)
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    # ---- timed hierarchical steps (mixed) ----
+    f = new("mixed")
+    e_init = f.energy()
+    for _ in range(args.warmup):
+        f.step(args.dt, 1)
+    torch.cuda.synchronize()
+    f.reset_stats()
+    f.set_timing(True)
+    launches0 = f.stats()["kernel_launches"]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    ms_total = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        a, b = ev(), ev()
+        a.record(stream)
+        f.step(args.dt, 1)
+        b.record(stream)
+        b.synchronize()
+        ms_total += a.elapsed_time(b)
+    a, b = ev(), ev()
+    a.record(stream)
+    e_end = f.energy()
+    b.record(stream)
+    b.synchronize()
+    ms_energy = a.elapsed_time(b)
+    ms_total += ms_energy
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    st = f.stats()
+    f.set_timing(False)
+    interactions = float(st["acc_pairs"] + st["grad_pairs"])
+    launches = st["kernel_launches"] - launches0 + 3  # + the energy pass kernels
+    ms_max = ms_total
+    if world > 1:
+        t = torch.tensor([ms_total, interactions], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        ms_max = float(tmax[0])
+        interactions = float(t[1])
+    value = interactions / (ms_max * 1e-3)
+
+    # roofline of the dominant pair kernel (largest share of kernel time)
+    kinds = ["acc", "grad", "tstep"]
+    kms = st["timed_ms"]
+    dom = int(np.argmax(kms))
+    kname = kinds[dom]
+    achieved_tf = st["timed_pairs"][dom] * FLOPS_PER_PAIR[kname] / (kms[dom] * 1e-3) / 1e12
+    sm_max = (clk.get("sm_max_mhz") or peaks().get("sm_max_mhz") or 2070.0)
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    sm_med = clk.get("sm_mhz")
+    roofline = {"bound": "alu", "kernel": f"{kname} pass (mixed, FP32 pipe)",
+                "achieved": achieved_tf, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved_tf / fp32_peak, "traffic": None,
+                "peak_basis": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)",
+                "frac_at_median_clock": (achieved_tf / (fp32_peak * sm_med / sm_max)) if sm_med else None,
+                "flops_per_pair": FLOPS_PER_PAIR[kname],
+                "launches": st["timed_launches"][dom], "kernel_ms": kms[dom],
+                "kernel_share": kms[dom] / max(ms_total - ms_energy, 1e-9),
+                "per_kind": {kinds[k]: {"launches": st["timed_launches"][k], "ms": kms[k],
+                                        "pairs": st["timed_pairs"][k],
+                                        "tflops": (st["timed_pairs"][k] * FLOPS_PER_PAIR[kinds[k]]
+                                                   / (kms[k] * 1e-3) / 1e12) if kms[k] > 0 else 0.0}
+                             for k in range(3)}}
+    dE_timed = abs((e_end["E"] - e_init["E"]) / e_init["E"])
+
+    # ---- end to end through the C-ABI with host buffers ----
+    xh = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    vh = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    x_np, v_np = xh.numpy(), vh.numpy()
+    fr.frost_get_state(f.ctx, x_np, v_np)
+    tt = fr.frost_get_state(f.ctx, None, None)
+    e2e_steps = max(1, min(args.steps, 8))
+    f.reset_stats()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        fr.frost_set_state(f.ctx, x_np, v_np, tt)
+        fr.frost_step(f.ctx, args.dt, 1)
+        tt = fr.frost_get_state(f.ctx, x_np, v_np)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    st2 = f.stats()
+    e2e_value = (st2["acc_pairs"] + st2["grad_pairs"]) / e2e_s * (world if world > 1 else 1)
+    f.close()
+
+    # ---- one full acc + gradient pass (both precisions) ----
+    def full_pass(prec, reps):
+        g = new(prec)
+        g.accel_gradient(None, None, eps_grad=args.dt)  # warm-up
+        g.set_timing(True)
+        g.reset_stats()
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record(stream)
+        for _ in range(reps):
+            g.accel_gradient(None, None, eps_grad=args.dt, want=("acc_tilde",))
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b) / reps
+        s = g.stats()
+        g.close()
+        inter = 2.0 * n * (n - 1)
+        out = {"ms": ms, "value": inter / (ms * 1e-3), "unit": UNIT}
+        for k, nm in ((0, "acc"), (1, "grad")):
+            if s["timed_ms"][k] > 0:
+                tf = s["timed_pairs"][k] * FLOPS_PER_PAIR[nm] / (s["timed_ms"][k] * 1e-3) / 1e12
+                out[f"{nm}_kernel_ms"] = s["timed_ms"][k] / max(s["timed_launches"][k], 1)
+                out[f"{nm}_tflops"] = tf
+                out[f"{nm}_frac"] = tf / (fp32_peak if prec == "mixed" else FP64_PEAK_TFLOPS)
+        return out
+
+    fp_mixed = full_pass("mixed", 5)
+    extra = {"full_pass": fp_mixed}
+
+    # ---- FP64 mode and |dE/E| at equal steps from the initial state ----
+    if not args.no_fp64:
+        fp_64 = full_pass("fp64", 1)
+        en = {}
+        for prec in ("mixed", "fp64"):
+            g = new(prec)
+            E0 = g.energy()["E"]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g.step(args.dt, args.fp64_steps)
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+            s = g.stats()
+            E1 = g.energy()
+            en[prec] = {"dE_over_E": abs((E1["E"] - E0) / E0), "seconds": secs,
+                        "interactions_per_s": (s["acc_pairs"] + s["grad_pairs"]) / secs,
+                        "dP": float(np.linalg.norm(E1["P"])), "max_depth": s["max_depth_seen"]}
+            g.close()
+        extra["fp64"] = {"full_pass": fp_64, "steps": args.fp64_steps}
+        extra["energy"] = {"steps": args.fp64_steps, "t_end": args.fp64_steps * args.dt, **en,
+                           "mixed_speedup": en["fp64"]["seconds"] / en["mixed"]["seconds"],
+                           "dE_ratio_mixed_over_fp64": en["mixed"]["dE_over_E"] / en["fp64"]["dE_over_E"]}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        try:
+            import oracle
+            oracle.build()
+            cpu = cpu_baseline(args.workload, args.cpu_seconds)
+        except Exception as exc:  # the baseline is a report, never the product path
+            cpu = {"value": None, "unit": UNIT, "error": str(exc)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "N": int(n), "eta": args.eta,
+                           "dt_pivot": args.dt, "precision": "mixed (FP32 pair body, float-float "
+                           "separations, FP64 state and sums)",
+                           "step": "one top-level HHS-FSI step; E/P/L once per timed region",
+                           "l2": "flushed before every timed step (256 MiB write)",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
+                        "h2d_bytes_per_step": int(2 * n * 3 * 8),
+                        "d2h_bytes_per_step": int(2 * n * 3 * 8)},
+                "gpu_launches": int(launches), "clocks": clk,
+                "wall_s_timed_region": wall, "energy_ms": ms_energy,
+                "dE_over_E_timed_run": dE_timed, "max_depth": st["max_depth_seen"],
+                "hhs_calls": st["hhs_calls"], **extra}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_frost(args)
+
+
+if __name__ == "__main__":
+    main()

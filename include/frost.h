@@ -1,0 +1,206 @@
+/*
+ * frost.h -- C-ABI of the GB300 (sm_103a) HHS-FSI hot path.
+ *
+ * The library integrates a self-gravitating N-body system with the hierarchical fourth-
+ * order forward symplectic integrator HHS-FSI of Rantala, Naab & Springel (2021, "FROST"):
+ * direct-summation Newtonian accelerations (Eq. acc-newton), the force-gradient term of the
+ * FSI (Eqs. acc-gradient-g, acc-gradient, force-gradient-inter-1/2), symmetrised free-fall /
+ * fly-by time-steps (Eqs. dt-freefall, dt-flyby, their derivatives, Eq. time-step-factor),
+ * the slow/fast partition (Sec. 3.1), kick/drift and the recursion of Algorithm hhs-fsi.
+ *
+ * Conventions shared by every entry point
+ *  - Positions and velocities cross the boundary as [n][3] row-major doubles, masses as [n]
+ *    doubles.  Inside, the library keeps its own FP64 structure-of-arrays copy on the GPU.
+ *  - Index lists are int32 particle indices in [0, n).  A NULL list with a count k means the
+ *    first k particles in order (0, 1, ..., k-1).
+ *  - Pointers marked "device" must be readable/writable by the GPU (cudaMalloc, torch CUDA
+ *    tensors, managed or mapped pinned memory).  Pointers marked "host or device" may be
+ *    either; the library copies with cudaMemcpyDefault.  The caller owns every pointer it
+ *    passes; the library never frees caller memory and keeps no caller pointer after a
+ *    call returns.
+ *  - Work is issued on the stream given in frost_opts (the caller's stream); entry points
+ *    that return results to the host synchronise that stream before returning.
+ *  - Every call returns a frost_status; no C++ exception crosses the boundary.  The message
+ *    of the last failure in the calling thread is available from frost_last_error().
+ *    Kernels report problems through a device error word that the library reads at its
+ *    synchronisation points; the first error is sticky until frost_clear_error().
+ *  - A frost_ctx is not thread-safe; use one context per host thread or serialise calls.
+ */
+#ifndef FROST_H
+#define FROST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct frost_ctx frost_ctx;
+
+typedef enum {
+    FROST_OK = 0,
+    FROST_EINVAL = 1,      /* bad argument: size, index out of range, overlapping lists */
+    FROST_ENOMEM = 2,      /* device or pinned host allocation failed */
+    FROST_ECUDA = 3,       /* a CUDA runtime call failed (message has the CUDA error) */
+    FROST_ENONFINITE = 4,  /* a non-finite input, or a pass produced a non-finite value */
+    FROST_ECOINCIDENT = 5, /* two distinct particles at zero separation (unsoftened) */
+    FROST_EDEPTH = 6,      /* hhs_fsi recursion deeper than frost_opts.max_depth */
+    FROST_ETIMEOUT = 7     /* a bounded device-side wait gave up */
+} frost_status;
+
+typedef enum {
+    FROST_PREC_FP64 = 0,   /* every pair body in FP64 */
+    FROST_PREC_MIXED = 1   /* FP32 pair bodies on float-float separations, FP64 state and sums */
+} frost_precision;
+
+typedef enum {
+    FROST_SYM_HARMONIC = 0,   /* harmonic symmetrisation, Eq. time-step-factor (second line) */
+    FROST_SYM_ARITHMETIC = 1, /* arithmetic symmetrisation, Eq. time-step-factor (first line) */
+    FROST_SYM_NONE = 2        /* no symmetrisation (factor 1) */
+} frost_sym;
+
+typedef struct {
+    int32_t precision;  /* frost_precision */
+    int32_t sym;        /* frost_sym */
+    double eps_soft;    /* Plummer softening length eps_P (Sec. 2.3); 0 = unsoftened */
+    int32_t max_depth;  /* deepest hhs_fsi level allowed (top level = 0); <= 0 means 40 */
+    void *cuda_stream;  /* cudaStream_t for all work; NULL = the legacy default stream */
+} frost_opts;
+
+/* Default options: mixed precision, harmonic symmetrisation, no softening, depth 40,
+ * legacy default stream. */
+void frost_default_opts(frost_opts *opt);
+
+/*
+ * Create a context holding n particles with masses m[n], positions x[n][3] and velocities
+ * v[n][3] (host or device; copied), Newton's constant G and accuracy parameter eta
+ * (eta = eta_ff = eta_fb, Sec. 4.3).  opt may be NULL for the defaults.  n >= 1 and
+ * n < 2^31.  Non-finite inputs or non-positive masses give FROST_ENONFINITE / FROST_EINVAL.
+ * The context allocates about (250 + 32 * levels_used) bytes per particle of device memory.
+ * On failure *ctx is NULL.
+ */
+frost_status frost_init(frost_ctx **ctx, int64_t n, const double *m, const double *x,
+                        const double *v, double G, double eta, const frost_opts *opt);
+
+/* Replace positions x[n][3] and velocities v[n][3] (host or device; either may be NULL to
+ * keep the current values) and set the simulation time to t. */
+frost_status frost_set_state(frost_ctx *ctx, const double *x, const double *v, double t);
+
+/* Copy positions and velocities out (host or device [n][3]; either may be NULL) and the
+ * simulation time (host pointer, may be NULL).  Synchronises. */
+frost_status frost_get_state(frost_ctx *ctx, double *x, double *v, double *t);
+
+/*
+ * Newtonian and gradient accelerations of the active particles against the source
+ * particles (Eq. acc-newton; Eqs. acc-gradient-g, acc-gradient; Eqs. force-newton-inter,
+ * force-gradient-inter-1/2):
+ *   acc[k]       = a_i       = G sum_{j in source, j != i} m_j x_ji / r_ji^3
+ *   grad[k]      = g_i       = 2 G sum_j m_j r_ji^-5 (r_ji^2 a_ji - 3 (x_ji . a_ji) x_ji)
+ *   acc_tilde[k] = a~_i      = a_i + eps_grad^2 g_i / 48
+ * for i = active[k].  Two cases are accepted:
+ *   - active and source are the same set (any order): the intra-set pass of fsi; the a_j in
+ *     a_ji = a_j - a_i are the same set's accelerations;
+ *   - active and source are disjoint: the inter-level pass of hhs_fsi; the a_j are the
+ *     sources' accelerations due to the active set (Eq. force-newton-inter, second line).
+ * Partial overlap or a repeated index returns FROST_EINVAL.  active/source are device
+ * int32 lists (or NULL = identity); acc, acc_tilde, grad are device [n_active][3] doubles,
+ * each may be NULL (if acc_tilde and grad are both NULL only the Newtonian pass runs).
+ * With softening eps_P, r^2 -> r^2 + eps_P^2 everywhere in both sums.  Pairs at zero
+ * separation give FROST_ECOINCIDENT when unsoftened.  Synchronises.
+ */
+frost_status frost_accel_gradient(frost_ctx *ctx, const int32_t *active, int64_t n_active,
+                                  const int32_t *source, int64_t n_source, double eps_grad,
+                                  double *acc, double *acc_tilde, double *grad);
+
+/*
+ * Symmetrised time-steps of the members of `set` (device list or NULL), Sec. 4:
+ *   tau[k] = min_{j in set, j != i} min( s(eta dt_ff/dt) eta t_ff, s(eta dt_fb/dt) eta t_fb )
+ * with t_ff = (r^3 / (G (m_i + m_j)))^(1/2), t_fb = r / |v_ij|, their time derivatives
+ * (fly-by in the two-body approximation of Eq. dt-flyby-derivative) and the symmetrisation
+ * factor s of Eq. time-step-factor chosen by frost_opts.sym.  tau is device [n_set] doubles;
+ * a set of one particle gets +inf; v_ij = 0 drops the fly-by criterion of that pair.
+ * Two distinct members at the same position give FROST_ECOINCIDENT.  Synchronises.
+ */
+frost_status frost_timesteps(frost_ctx *ctx, const int32_t *set, int64_t n_set, double *tau);
+
+/*
+ * Slow/fast partition by the pivot step (Sec. 3.1): S = {set[k] : tau[k] >= tau_pivot},
+ * F = the rest, both in the order of `set`.  set, tau (device) have n_set entries; S and F
+ * are device int32 buffers of capacity n_set; *n_slow and *n_fast (host) receive the
+ * sizes.  Synchronises.
+ */
+frost_status frost_partition(frost_ctx *ctx, const int32_t *set, int64_t n_set,
+                             const double *tau, double tau_pivot, int32_t *S, int32_t *F,
+                             int64_t *n_slow, int64_t *n_fast);
+
+/* Kick v_i += dt a[k] for i = set[k] (a device [n_set][3]) and drift x_i += dt v_i for the
+ * members of set (Sec. 5.3).  Asynchronous on the context stream. */
+frost_status frost_kick(frost_ctx *ctx, const int32_t *set, int64_t n_set, const double *a,
+                        double dt);
+frost_status frost_drift(frost_ctx *ctx, const int32_t *set, int64_t n_set, double dt);
+
+/*
+ * One FSI step (Algorithm fsi, Eq. fsi) of the particles in `set` (device list or NULL)
+ * with step dt, ignoring every particle outside the set.  Asynchronous; errors are reported
+ * by the next synchronising call.
+ */
+frost_status frost_fsi(frost_ctx *ctx, const int32_t *set, int64_t n_set, double dt);
+
+/*
+ * n_steps top-level HHS-FSI steps (Algorithm hhs-fsi called with all particles and
+ * tau_pivot = dt_pivot, as in the main loop of Algorithm frost); the simulation time
+ * advances by n_steps * dt_pivot.  Returns FROST_EDEPTH if the hierarchy would go deeper
+ * than max_depth (the state is then partially advanced).  Synchronises.
+ */
+frost_status frost_step(frost_ctx *ctx, double dt_pivot, int64_t n_steps);
+
+/*
+ * Kinetic energy T = 1/2 sum m v^2, potential U = -G sum_{i<j} m_i m_j / r_ij (softened as
+ * configured), momentum P = sum m v and angular momentum L = sum m x cross v (host
+ * outputs; any may be NULL).  Computed in FP64 in every precision mode.  Synchronises.
+ */
+frost_status frost_energy_momentum(frost_ctx *ctx, double *E_kin, double *E_pot, double P[3],
+                                   double L[3]);
+
+/* Counters since frost_init or frost_reset_stats. */
+typedef struct {
+    int64_t acc_pairs;      /* Newtonian pair interactions evaluated */
+    int64_t grad_pairs;     /* gradient pair interactions evaluated */
+    int64_t tstep_pairs;    /* time-step pair interactions evaluated */
+    int64_t kernel_launches;/* kernels launched by the library */
+    int64_t hhs_calls;      /* hhs_fsi invocations with a non-empty set */
+    int64_t fsi_calls;      /* fsi invocations with a non-empty set */
+    int32_t max_depth_seen; /* deepest hhs_fsi level reached */
+    int32_t timing_enabled; /* 1 if per-kernel CUDA-event timing is on */
+    /* per-kernel-kind CUDA-event totals (only when timing is enabled):
+     * index 0 = Newtonian pass, 1 = gradient pass, 2 = time-step pass */
+    int64_t timed_launches[3];
+    double timed_ms[3];
+    int64_t timed_pairs[3];
+} frost_stats;
+
+frost_status frost_get_stats(frost_ctx *ctx, frost_stats *out);
+frost_status frost_reset_stats(frost_ctx *ctx);
+
+/* Enable (1) or disable (0) CUDA-event timing of every pair-pass kernel launch on the
+ * context stream (a pair of events per launch; totals in frost_stats). */
+frost_status frost_set_timing(frost_ctx *ctx, int32_t enable);
+
+/* Wait for all work of the context and report the sticky device error, if any. */
+frost_status frost_synchronize(frost_ctx *ctx);
+frost_status frost_clear_error(frost_ctx *ctx);
+
+/* Release the context and all its device memory (NULL is ignored). */
+void frost_destroy(frost_ctx *ctx);
+
+/* Message of the last failure in the calling thread ("" if none). */
+const char *frost_last_error(void);
+
+/* Library version string. */
+const char *frost_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FROST_H */

@@ -280,10 +280,13 @@ double or_sym_harmonic(double d)
     return d >= 0.0 ? (q + d) / q : 2.0 / (q - d);
 }
 
-/* tau_sym / tau for the arithmetic mean (Eq. time-step-factor, first line); valid for d < 2. */
+/* tau_sym / tau for the arithmetic mean (Eq. time-step-factor, first line), valid for
+ * d < 2.  For d >= 2 the paper lowers the step until its derivative is below 2 (Sec. 4.2);
+ * reading: the step is first scaled by 1/d (its derivative becomes 1), then symmetrised,
+ * which gives the factor (1/d) / (1 - 1/2) = 2/d. */
 double or_sym_arithmetic(double d)
 {
-    return 1.0 / (1.0 - 0.5 * d);
+    return d < 2.0 ? 1.0 / (1.0 - 0.5 * d) : 2.0 / d;
 }
 
 /*

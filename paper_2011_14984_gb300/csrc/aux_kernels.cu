@@ -1,0 +1,332 @@
+// Integrator and bookkeeping kernels of the HHS-FSI hot path for sm_103a:
+//   kick / drift (Sec. 5.3), the stable slow/fast partition (Sec. 3.1), index-list
+//   validation, and the FP64 energy / momentum / angular-momentum reductions (Sec. 2.3).
+#include "frost_internal.cuh"
+
+#include <cmath>
+
+namespace frost {
+namespace {
+
+inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+__global__ void k_kick(const int32_t *__restrict__ list, int n, double *__restrict__ v, int N,
+                       const double *__restrict__ a, double dt)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int i = list ? list[k] : k;
+    // separate roundings of the product and the sum (no contraction into an FMA)
+    v[i] = __dadd_rn(v[i], __dmul_rn(dt, a[k]));
+    v[N + i] = __dadd_rn(v[N + i], __dmul_rn(dt, a[n + k]));
+    v[2 * N + i] = __dadd_rn(v[2 * N + i], __dmul_rn(dt, a[2 * n + k]));
+}
+
+__global__ void k_kick_aos(const int32_t *__restrict__ list, int n, double *__restrict__ v, int N,
+                           const double *__restrict__ a, double dt)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int i = list ? list[k] : k;
+    v[i] = __dadd_rn(v[i], __dmul_rn(dt, a[3 * k]));
+    v[N + i] = __dadd_rn(v[N + i], __dmul_rn(dt, a[3 * k + 1]));
+    v[2 * N + i] = __dadd_rn(v[2 * N + i], __dmul_rn(dt, a[3 * k + 2]));
+}
+
+__global__ void k_drift(const int32_t *__restrict__ list, int n, double *__restrict__ x,
+                        const double *__restrict__ v, int N, double dt)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int i = list ? list[k] : k;
+    x[i] = __dadd_rn(x[i], __dmul_rn(dt, v[i]));
+    x[N + i] = __dadd_rn(x[N + i], __dmul_rn(dt, v[N + i]));
+    x[2 * N + i] = __dadd_rn(x[2 * N + i], __dmul_rn(dt, v[2 * N + i]));
+}
+
+// Stable partition by one block of 1024 threads: chunks of 1024 entries, slow ranks from a
+// warp-ballot prefix count, fast ranks as the complement.
+__global__ void __launch_bounds__(1024) k_partition(const int32_t *__restrict__ set, int n,
+                                                    const double *__restrict__ tau, double pivot,
+                                                    int32_t *__restrict__ S, int32_t *__restrict__ F,
+                                                    int64_t *__restrict__ counts)
+{
+    __shared__ int wsum[32];
+    __shared__ int chunk_total;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int sbase = 0, fbase = 0;
+    for (int c0 = 0; c0 < n; c0 += 1024) {
+        const int k = c0 + tid;
+        const bool valid = k < n;
+        const bool slow = valid && (tau[k] >= pivot);
+        const unsigned bal = __ballot_sync(0xffffffffu, slow);
+        const int rank = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) wsum[warp] = __popc(bal);
+        __syncthreads();
+        if (warp == 0) {
+            const int vsum = wsum[lane];
+            int incl = vsum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            wsum[lane] = incl - vsum;  // exclusive prefix of slow counts per warp
+            if (lane == 31) chunk_total = incl;
+        }
+        __syncthreads();
+        if (valid) {
+            const int sidx = wsum[warp] + rank;  // slow entries before k in this chunk
+            const int id = set ? set[k] : k;
+            if (slow) S[sbase + sidx] = id;
+            else F[fbase + (tid - sidx)] = id;
+        }
+        const int tot = chunk_total;
+        const int nvalid = min(1024, n - c0);
+        sbase += tot;
+        fbase += nvalid - tot;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        counts[0] = sbase;
+        counts[1] = fbase;
+    }
+}
+
+// list relation: B adds 1 to its marks, A adds 2; a repeated entry sees its own bit already set
+__global__ void k_mark_B(const int32_t *__restrict__ B, int nB, int N, int32_t *__restrict__ marks,
+                         int64_t *__restrict__ out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nB) return;
+    const int i = B ? B[k] : k;
+    if (i < 0 || i >= N) {
+        out[0] = 1;
+        return;
+    }
+    if (atomicAdd(&marks[i], 1) & 1) out[0] = 1;
+}
+
+__global__ void k_mark_A(const int32_t *__restrict__ A, int nA, int N, int32_t *__restrict__ marks,
+                         int64_t *__restrict__ out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nA) return;
+    const int i = A ? A[k] : k;
+    if (i < 0 || i >= N) {
+        out[0] = 1;
+        return;
+    }
+    const int old = atomicAdd(&marks[i], 2);
+    if (old & 2) out[0] = 1;
+    if (old & 1) atomicAdd((unsigned long long *)&out[1], 1ull);
+}
+
+__global__ void k_unmark(const int32_t *__restrict__ L, int n, int N, int32_t *__restrict__ marks)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int i = L ? L[k] : k;
+    if (i >= 0 && i < N) marks[i] = 0;
+}
+
+__global__ void k_check_finite(const double *__restrict__ p, int64_t n, int *__restrict__ err)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(p[k])) atomicOr(err, ERR_NONFINITE);
+}
+
+__global__ void k_identity(int32_t *__restrict__ list, int n)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) list[k] = k;
+}
+
+// [n][3] <-> [3][n] layout conversion of a particle vector
+__global__ void k_aos_to_soa(const double *__restrict__ aos, int n, double *__restrict__ soa,
+                             int *__restrict__ err)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    bool ok = true;
+    for (int c = 0; c < 3; ++c) {
+        const double q = aos[3 * (size_t)k + c];
+        ok = ok && isfinite(q);
+        soa[(size_t)c * n + k] = q;
+    }
+    if (!ok) atomicOr(err, ERR_NONFINITE);
+}
+
+__global__ void k_soa_to_aos(const double *__restrict__ soa, int n, double *__restrict__ aos)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    for (int c = 0; c < 3; ++c) aos[3 * (size_t)k + c] = soa[(size_t)c * n + k];
+}
+
+// masses must be finite and positive
+__global__ void k_check_mass(const double *__restrict__ m, int n, int *__restrict__ err)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    if (!(m[k] > 0.0) || !isfinite(m[k])) atomicOr(err, ERR_NONFINITE);
+}
+
+// phi_i = sum_{j != i} m_j / sqrt(r^2 + eps2), FP64, j-split partials part[split][i]
+template <int BS, int TJ>
+__global__ void __launch_bounds__(BS) k_potential(const double4_32a *__restrict__ rec, int n,
+                                                  int j_per_split, double eps2,
+                                                  double *__restrict__ part)
+{
+    __shared__ double4_32a s0[TJ];
+    const int tid = threadIdx.x;
+    const int ibase = blockIdx.x * BS;
+    const int i = ibase + tid;
+    const double4_32a I = (i < n) ? rec[i] : make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    double phi = 0.0;
+    const int jb = blockIdx.y * j_per_split;
+    const int je = min(n, jb + j_per_split);
+    for (int j0 = jb; j0 < je; j0 += TJ) {
+        const int cnt = min(TJ, je - j0);
+        __syncthreads();
+        for (int t = tid; t < cnt; t += BS) s0[t] = rec[j0 + t];
+        __syncthreads();
+        for (int jj = 0; jj < cnt; ++jj) {
+            const double4_32a J = s0[jj];
+            const double dx = J.x - I.x, dy = J.y - I.y, dz = J.z - I.z;
+            const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+            const double t = J.w * rsqrt(r2);
+            if (j0 + jj != i) phi += t;
+        }
+    }
+    if (i < n) part[(size_t)blockIdx.y * n + i] = phi;
+}
+
+// Single-block FP64 reduction in a fixed order (deterministic).
+__global__ void __launch_bounds__(1024) k_energy_reduce(const double *__restrict__ x,
+                                                        const double *__restrict__ v,
+                                                        const double *__restrict__ m, int N,
+                                                        const double *__restrict__ part, int nsplit,
+                                                        double *__restrict__ out)
+{
+    __shared__ double red[8][32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = tid; i < N; i += 1024) {
+        const double mi = m[i];
+        const double px = x[i], py = x[N + i], pz = x[2 * N + i];
+        const double ux = v[i], uy = v[N + i], uz = v[2 * N + i];
+        double phi = 0.0;
+        for (int p = 0; p < nsplit; ++p) phi += part[(size_t)p * N + i];
+        acc[0] += 0.5 * mi * (ux * ux + uy * uy + uz * uz);
+        acc[1] += mi * phi;
+        acc[2] += mi * ux;
+        acc[3] += mi * uy;
+        acc[4] += mi * uz;
+        acc[5] += mi * (py * uz - pz * uy);
+        acc[6] += mi * (pz * ux - px * uz);
+        acc[7] += mi * (px * uy - py * ux);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        double a = acc[q];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) red[q][warp] = a;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            double a = red[q][lane];
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+            if (lane == 0) out[q] = a;
+        }
+    }
+}
+
+}  // namespace
+
+void launch_kick(cudaStream_t s, const int32_t *list, int n, double *v, int N, const double *a_soa,
+                 double dt)
+{
+    if (n <= 0) return;
+    k_kick<<<cdiv(n, 256), 256, 0, s>>>(list, n, v, N, a_soa, dt);
+}
+
+void launch_kick_aos(cudaStream_t s, const int32_t *list, int n, double *v, int N,
+                     const double *a_aos, double dt)
+{
+    if (n <= 0) return;
+    k_kick_aos<<<cdiv(n, 256), 256, 0, s>>>(list, n, v, N, a_aos, dt);
+}
+
+void launch_drift(cudaStream_t s, const int32_t *list, int n, double *x, const double *v, int N,
+                  double dt)
+{
+    if (n <= 0) return;
+    k_drift<<<cdiv(n, 256), 256, 0, s>>>(list, n, x, v, N, dt);
+}
+
+void launch_partition(cudaStream_t s, const int32_t *set, int n, const double *tau, double pivot,
+                      int32_t *S, int32_t *F, int64_t *counts)
+{
+    k_partition<<<1, 1024, 0, s>>>(set, n, tau, pivot, S, F, counts);
+}
+
+void launch_list_relation(cudaStream_t s, const int32_t *A, int nA, const int32_t *B, int nB,
+                          int N, int32_t *marks, int64_t *out)
+{
+    cudaMemsetAsync(out, 0, 2 * sizeof(int64_t), s);
+    if (nB > 0) k_mark_B<<<cdiv(nB, 256), 256, 0, s>>>(B, nB, N, marks, out);
+    if (nA > 0) k_mark_A<<<cdiv(nA, 256), 256, 0, s>>>(A, nA, N, marks, out);
+    if (nB > 0) k_unmark<<<cdiv(nB, 256), 256, 0, s>>>(B, nB, N, marks);
+    if (nA > 0) k_unmark<<<cdiv(nA, 256), 256, 0, s>>>(A, nA, N, marks);
+}
+
+void launch_check_finite(cudaStream_t s, const double *p, int64_t n, int *err)
+{
+    if (n <= 0) return;
+    const unsigned nb = (unsigned)std::min<long long>(4096, (n + 255) / 256);
+    k_check_finite<<<nb, 256, 0, s>>>(p, n, err);
+}
+
+void launch_identity(cudaStream_t s, int32_t *list, int n)
+{
+    if (n <= 0) return;
+    k_identity<<<cdiv(n, 256), 256, 0, s>>>(list, n);
+}
+
+void launch_potential(cudaStream_t s, const double4_32a *rec, int n, double eps2, double *part,
+                      const SplitShape &shape)
+{
+    if (n <= 0) return;
+    const dim3 grid(shape.nblk_i, shape.nsplit);
+    k_potential<PAIR_BS, PAIR_TJ><<<grid, PAIR_BS, 0, s>>>(rec, n, shape.j_per_split, eps2, part);
+}
+
+void launch_aos_to_soa(cudaStream_t s, const double *aos, int n, double *soa, int *err)
+{
+    if (n <= 0) return;
+    k_aos_to_soa<<<cdiv(n, 256), 256, 0, s>>>(aos, n, soa, err);
+}
+
+void launch_soa_to_aos(cudaStream_t s, const double *soa, int n, double *aos)
+{
+    if (n <= 0) return;
+    k_soa_to_aos<<<cdiv(n, 256), 256, 0, s>>>(soa, n, aos);
+}
+
+void launch_check_mass(cudaStream_t s, const double *m, int n, int *err)
+{
+    if (n <= 0) return;
+    k_check_mass<<<cdiv(n, 256), 256, 0, s>>>(m, n, err);
+}
+
+void launch_energy_reduce(cudaStream_t s, const double *x, const double *v, const double *m, int N,
+                          const double *part, int nsplit, double *out)
+{
+    k_energy_reduce<<<1, 1024, 0, s>>>(x, v, m, N, part, nsplit, out);
+}
+
+}  // namespace frost

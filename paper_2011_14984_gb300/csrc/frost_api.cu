@@ -1,0 +1,778 @@
+// C-ABI of the HHS-FSI hot path (declared in include/frost.h): the context with its device
+// particle store, the pair-pass drivers and the HHS-FSI recursion (Algorithm hhs-fsi) with
+// FSI steps on the slow sets (Algorithm fsi).
+//
+// The recursion runs on the host and issues every kernel on the context stream.  Each
+// hhs_fsi call synchronises once, after the partition, to learn |S| and |F| (which decide
+// the grid shapes and whether to recurse) and to read the device error word; everything
+// else is asynchronous.
+#include "frost.h"
+#include "frost_internal.cuh"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace frost;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+frost_status fail(frost_status st, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+frost_status fail(frost_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+#define FROST_CUDA(call)                                                                         \
+    do {                                                                                         \
+        const cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail(e_ == cudaErrorMemoryAllocation ? FROST_ENOMEM : FROST_ECUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                      \
+    } while (0)
+
+#define FROST_TRY(expr)                                                                          \
+    do {                                                                                         \
+        const frost_status s_ = (expr);                                                          \
+        if (s_ != FROST_OK) return s_;                                                           \
+    } while (0)
+
+// small device/host exchange block
+struct Misc {
+    int64_t counts[2];  // partition |S|, |F|
+    int64_t rel[2];     // list relation: bad/duplicate flag, |A cap B|
+    double eres[8];     // energy reduction
+    int err;            // sticky device error word
+    int pad;
+};
+
+struct Timed {
+    cudaEvent_t a, b;
+    int kind;
+    int64_t pairs;
+};
+
+}  // namespace
+
+struct frost_ctx {
+    int N = 0;
+    double G = 1.0, eta = 0.2, eps2 = 0.0;
+    bool mixed = true;
+    int sym = 0;
+    int max_depth = 40;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int n_sm = 1;
+    double t = 0.0;
+
+    double *x = nullptr, *v = nullptr, *m = nullptr;  // SoA state
+    int32_t *all = nullptr;                          // identity list
+    int32_t *marks = nullptr;                        // relation marks [N]
+    void *recA = nullptr, *recB = nullptr;           // packed records, 64 B x N each
+    double *part = nullptr;                          // split partials
+    size_t part_elems = 0;
+    double *aA = nullptr, *aB = nullptr, *atA = nullptr, *atB = nullptr;  // [3][N] each
+    double *tau = nullptr;                           // [N]
+    float *wA = nullptr, *wB = nullptr;              // max_j m_j / r^3 per particle (mixed)
+    float *wpart = nullptr;                          // its split partials
+    Misc *dmisc = nullptr, *hmisc = nullptr;
+    std::vector<int32_t *> lvS, lvF;                 // per-level slow/fast lists
+
+    frost_stats st{};
+    bool timing = false;
+    std::vector<Timed> pending;
+    std::vector<cudaEvent_t> event_pool;
+    int host_error = 0;  // sticky error already reported
+};
+
+namespace {
+
+int ipb(const frost_ctx *c) { return pair_i_per_block(c->mixed); }
+
+SplitShape shape_for(const frost_ctx *c, int kind, int n_a, int n_s)
+{
+    SplitShape sh = choose_shape(n_a, n_s, ipb(c), pair_blocks_per_sm(kind, c->mixed), c->n_sm);
+    // keep the partials inside the scratch buffer
+    const long long comps = (kind == PASS_TSTEP) ? 1 : 3;
+    while ((long long)sh.nsplit * comps * n_a > (long long)c->part_elems && sh.nsplit > 1) {
+        const int tiles = (n_s + PAIR_TJ - 1) / PAIR_TJ;
+        const int ns = std::max(1, sh.nsplit / 2);
+        const int tps = (tiles + ns - 1) / ns;
+        sh.j_per_split = tps * PAIR_TJ;
+        sh.nsplit = (n_s + sh.j_per_split - 1) / sh.j_per_split;
+    }
+    return sh;
+}
+
+cudaEvent_t get_event(frost_ctx *c)
+{
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+struct TimedScope {
+    frost_ctx *c;
+    Timed t{};
+    bool on;
+    TimedScope(frost_ctx *c_, int kind, int64_t pairs) : c(c_), on(c_->timing)
+    {
+        if (!on) return;
+        t.a = get_event(c);
+        t.b = get_event(c);
+        t.kind = kind;
+        t.pairs = pairs;
+        if (!t.a || !t.b) {
+            on = false;
+            return;
+        }
+        cudaEventRecord(t.a, c->stream);
+    }
+    ~TimedScope()
+    {
+        if (!on) return;
+        cudaEventRecord(t.b, c->stream);
+        c->pending.push_back(t);
+    }
+};
+
+void resolve_timing(frost_ctx *c)
+{
+    for (const Timed &t : c->pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(t.b) == cudaSuccess && cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+            c->st.timed_launches[t.kind] += 1;
+            c->st.timed_ms[t.kind] += ms;
+            c->st.timed_pairs[t.kind] += t.pairs;
+        }
+        c->event_pool.push_back(t.a);
+        c->event_pool.push_back(t.b);
+    }
+    c->pending.clear();
+}
+
+frost_status err_to_status(int e)
+{
+    if (e & ERR_COINCIDENT) return fail(FROST_ECOINCIDENT, "two distinct particles at zero separation");
+    if (e & ERR_NONFINITE) return fail(FROST_ENONFINITE, "non-finite value in a pass (or a non-positive mass / step)");
+    if (e & (ERR_INDEX | ERR_DUPLICATE)) return fail(FROST_EINVAL, "index list out of range or repeated");
+    if (e & ERR_TIMEOUT) return fail(FROST_ETIMEOUT, "a bounded device wait gave up");
+    return FROST_OK;
+}
+
+// synchronise the stream, fetch the exchange block and report the device error word
+frost_status sync_misc(frost_ctx *c)
+{
+    FROST_CUDA(cudaMemcpyAsync(c->hmisc, c->dmisc, sizeof(Misc), cudaMemcpyDeviceToHost, c->stream));
+    FROST_CUDA(cudaStreamSynchronize(c->stream));
+    if (c->timing) resolve_timing(c);
+    return err_to_status(c->hmisc->err);
+}
+
+// ---- pass drivers ------------------------------------------------------------------------
+
+void pack_pos(frost_ctx *c, const int32_t *L, int n, void *rec)
+{
+    if (c->mixed) launch_pack_pos_mixed(c->stream, L, n, c->x, c->m, c->N, (float4 *)rec);
+    else launch_pack_pos_fp64(c->stream, L, n, c->x, c->m, c->N, (double4_32a *)rec);
+    c->st.kernel_launches += (n > 0);
+}
+
+int badbit(const frost_ctx *c) { return c->eps2 == 0.0 ? ERR_COINCIDENT : ERR_NONFINITE; }
+
+// Newtonian accelerations of A from B (self: the same list); writes G * sum into out_soa
+// ([3][nA]) and, if given, out_aos ([nA][3]).  With wmax (mixed mode), also the weight
+// max_j m_j / r^3 of each particle's dominant term, which the following gradient pass uses.
+void pass_acc(frost_ctx *c, const int32_t *A, int nA, const int32_t *B, int nB, bool self,
+              double *out_soa, double *out_aos, float *wmax = nullptr)
+{
+    if (nA <= 0) return;
+    if (nB <= 0 || (self && nA == 1)) {
+        if (out_soa) cudaMemsetAsync(out_soa, 0, sizeof(double) * 3 * nA, c->stream);
+        if (out_aos) cudaMemsetAsync(out_aos, 0, sizeof(double) * 3 * nA, c->stream);
+        if (wmax) cudaMemsetAsync(wmax, 0, sizeof(float) * nA, c->stream);
+        return;
+    }
+    // before a gradient pass (wmax requested) the mixed mode uses the accurate variant on the
+    // three-way split records
+    const bool accurate = c->mixed && wmax;
+    if (accurate) {
+        launch_pack_grad_mixed(c->stream, A, nA, c->x, c->m, c->N, nullptr, (float4 *)c->recA);
+        if (!self) launch_pack_grad_mixed(c->stream, B, nB, c->x, c->m, c->N, nullptr, (float4 *)c->recB);
+        c->st.kernel_launches += self ? 1 : 2;
+    } else {
+        pack_pos(c, A, nA, c->recA);
+        if (!self) pack_pos(c, B, nB, c->recB);
+    }
+    PairArgs a;
+    a.irec = c->recA;
+    a.jrec = self ? c->recA : c->recB;
+    a.n_a = nA;
+    a.n_s = nB;
+    a.self_pass = self ? 1 : 0;
+    a.eps2 = c->eps2;
+    a.part = c->part;
+    a.shape = shape_for(c, PASS_ACC, nA, nB);
+    a.accurate = accurate;
+    a.wpart = accurate ? c->wpart : nullptr;
+    const int64_t pairs = self ? (int64_t)nA * (nA - 1) : (int64_t)nA * nB;
+    {
+        TimedScope ts(c, PASS_ACC, pairs);
+        launch_acc(c->stream, c->mixed, a);
+    }
+    launch_finalize_vec(c->stream, c->part, a.shape.nsplit, nA, c->G, out_soa, out_aos, a.wpart,
+                        a.wpart ? wmax : nullptr, &c->dmisc->err, badbit(c));
+    c->st.kernel_launches += 2;
+    c->st.acc_pairs += pairs;
+}
+
+// gradient of A against B with a_A (soa [3][nA]) and a_B (soa [3][nB]); writes
+// a~ = a_A + eps^2/48 g to at_soa / at_aos and g to g_aos (each optional).  wmax: the
+// dominant-term weights of A from the Newtonian pass at the same positions (mixed mode).
+void pass_grad(frost_ctx *c, const int32_t *A, int nA, const double *aA, const int32_t *B, int nB,
+               const double *aB, bool self, double eps_grad, double *at_soa, double *at_aos,
+               double *g_aos, const float *wmax)
+{
+    if (nA <= 0) return;
+    const double cgrad = eps_grad * eps_grad / 48.0;
+    if (nB <= 0 || (self && nA == 1)) {
+        // no sources: g = 0 and a~ = a
+        if (at_soa) cudaMemcpyAsync(at_soa, aA, sizeof(double) * 3 * nA, cudaMemcpyDeviceToDevice, c->stream);
+        if (at_aos) launch_soa_to_aos(c->stream, aA, nA, at_aos);
+        if (g_aos) cudaMemsetAsync(g_aos, 0, sizeof(double) * 3 * nA, c->stream);
+        return;
+    }
+    if (c->mixed) {
+        launch_pack_grad_mixed(c->stream, A, nA, c->x, c->m, c->N, aA, (float4 *)c->recA);
+        if (!self) launch_pack_grad_mixed(c->stream, B, nB, c->x, c->m, c->N, aB, (float4 *)c->recB);
+    } else {
+        launch_pack_grad_fp64(c->stream, A, nA, c->x, c->m, c->N, aA, (double4_32a *)c->recA);
+        if (!self) launch_pack_grad_fp64(c->stream, B, nB, c->x, c->m, c->N, aB, (double4_32a *)c->recB);
+    }
+    c->st.kernel_launches += self ? 1 : 2;
+    PairArgs a;
+    a.irec = c->recA;
+    a.jrec = self ? c->recA : c->recB;
+    a.n_a = nA;
+    a.n_s = nB;
+    a.self_pass = self ? 1 : 0;
+    a.eps2 = c->eps2;
+    a.part = c->part;
+    a.shape = shape_for(c, PASS_GRAD, nA, nB);
+    a.wmax = c->mixed ? wmax : nullptr;
+    const int64_t pairs = self ? (int64_t)nA * (nA - 1) : (int64_t)nA * nB;
+    {
+        TimedScope ts(c, PASS_GRAD, pairs);
+        launch_grad(c->stream, c->mixed, a);
+    }
+    launch_finalize_grad(c->stream, c->part, a.shape.nsplit, nA, 2.0 * c->G, aA, cgrad, at_soa,
+                         at_aos, g_aos, &c->dmisc->err, badbit(c));
+    c->st.kernel_launches += 2;
+    c->st.grad_pairs += pairs;
+}
+
+// symmetrised time-steps of the set P into tau[nP]
+void pass_tstep(frost_ctx *c, const int32_t *P, int nP, double *tau)
+{
+    if (nP <= 0) return;
+    if (nP == 1) {
+        // no pair: with zero splits the finalisation writes eta * (+inf)
+        launch_finalize_tau(c->stream, c->part, 0, 1, c->eta, tau, &c->dmisc->err);
+        c->st.kernel_launches += 1;
+        return;
+    }
+    if (c->mixed) launch_pack_tstep_mixed(c->stream, P, nP, c->x, c->v, c->m, c->N, c->G, (float4 *)c->recA);
+    else launch_pack_tstep_fp64(c->stream, P, nP, c->x, c->v, c->m, c->N, c->G, (double4_32a *)c->recA);
+    PairArgs a;
+    a.irec = c->recA;
+    a.jrec = c->recA;
+    a.n_a = nP;
+    a.n_s = nP;
+    a.self_pass = 1;
+    a.eps2 = 0.0;
+    a.part = c->part;
+    a.shape = shape_for(c, PASS_TSTEP, nP, nP);
+    const int64_t pairs = (int64_t)nP * (nP - 1);
+    {
+        TimedScope ts(c, PASS_TSTEP, pairs);
+        launch_tstep(c->stream, c->mixed, a, c->eta, c->sym, &c->dmisc->err);
+    }
+    launch_finalize_tau(c->stream, c->part, a.shape.nsplit, nP, c->eta, tau, &c->dmisc->err);
+    c->st.kernel_launches += 3;
+    c->st.tstep_pairs += pairs;
+}
+
+// ---- integrator -----------------------------------------------------------------------
+
+void kick(frost_ctx *c, const int32_t *L, int n, const double *a_soa, double dt)
+{
+    if (n <= 0) return;
+    launch_kick(c->stream, L, n, c->v, c->N, a_soa, dt);
+    c->st.kernel_launches += 1;
+}
+
+void drift(frost_ctx *c, const int32_t *L, int n, double dt)
+{
+    if (n <= 0) return;
+    launch_drift(c->stream, L, n, c->x, c->v, c->N, dt);
+    c->st.kernel_launches += 1;
+}
+
+// Algorithm fsi on the set S with step dt
+void fsi(frost_ctx *c, const int32_t *S, int nS, double dt)
+{
+    if (nS <= 0) return;
+    c->st.fsi_calls += 1;
+    pass_acc(c, S, nS, S, nS, true, c->aA, nullptr);
+    kick(c, S, nS, c->aA, dt / 6.0);
+    drift(c, S, nS, 0.5 * dt);
+    pass_acc(c, S, nS, S, nS, true, c->aA, nullptr, c->wA);
+    pass_grad(c, S, nS, c->aA, S, nS, c->aA, true, dt, c->atA, nullptr, nullptr, c->wA);
+    kick(c, S, nS, c->atA, 2.0 * dt / 3.0);
+    drift(c, S, nS, 0.5 * dt);
+    pass_acc(c, S, nS, S, nS, true, c->aA, nullptr);
+    kick(c, S, nS, c->aA, dt / 6.0);
+}
+
+// kick_sf: S kicked by its accelerations due to F, F by those due to S (computed first)
+void kick_sf(frost_ctx *c, const int32_t *S, int nS, const int32_t *F, int nF, double cdt,
+             bool gradient, double tau_pivot)
+{
+    if (nS <= 0 || nF <= 0) return;
+    pass_acc(c, S, nS, F, nF, false, c->aA, nullptr, gradient ? c->wA : nullptr);
+    pass_acc(c, F, nF, S, nS, false, c->aB, nullptr, gradient ? c->wB : nullptr);
+    if (gradient) {
+        pass_grad(c, S, nS, c->aA, F, nF, c->aB, false, tau_pivot, c->atA, nullptr, nullptr, c->wA);
+        pass_grad(c, F, nF, c->aB, S, nS, c->aA, false, tau_pivot, c->atB, nullptr, nullptr, c->wB);
+        kick(c, S, nS, c->atA, cdt);
+        kick(c, F, nF, c->atB, cdt);
+    } else {
+        kick(c, S, nS, c->aA, cdt);
+        kick(c, F, nF, c->aB, cdt);
+    }
+}
+
+frost_status ensure_level(frost_ctx *c, int depth)
+{
+    while ((int)c->lvS.size() <= depth) {
+        int32_t *S = nullptr, *F = nullptr;
+        FROST_CUDA(cudaMalloc(&S, sizeof(int32_t) * c->N));
+        if (cudaMalloc(&F, sizeof(int32_t) * c->N) != cudaSuccess) {
+            cudaFree(S);
+            return fail(FROST_ENOMEM, "level list allocation failed");
+        }
+        c->lvS.push_back(S);
+        c->lvF.push_back(F);
+    }
+    return FROST_OK;
+}
+
+// Algorithm hhs-fsi on the set P (device list, nP entries) with pivot step tau
+frost_status hhs_fsi(frost_ctx *c, const int32_t *P, int nP, double tau, int depth)
+{
+    if (nP <= 0) return FROST_OK;
+    if (depth > c->max_depth)
+        return fail(FROST_EDEPTH, "hhs_fsi deeper than max_depth=%d (|P|=%d, tau_pivot=%g)",
+                    c->max_depth, nP, tau);
+    c->st.hhs_calls += 1;
+    if (depth > c->st.max_depth_seen) c->st.max_depth_seen = depth;
+    FROST_TRY(ensure_level(c, depth));
+    int32_t *S = c->lvS[depth], *F = c->lvF[depth];
+    pass_tstep(c, P, nP, c->tau);
+    launch_partition(c->stream, P, nP, c->tau, tau, S, F, c->dmisc->counts);
+    c->st.kernel_launches += 1;
+    FROST_TRY(sync_misc(c));
+    const int nS = (int)c->hmisc->counts[0];
+    const int nF = (int)c->hmisc->counts[1];
+    kick_sf(c, S, nS, F, nF, tau / 6.0, false, tau);
+    fsi(c, S, nS, 0.5 * tau);
+    FROST_TRY(hhs_fsi(c, F, nF, 0.5 * tau, depth + 1));
+    kick_sf(c, S, nS, F, nF, 2.0 * tau / 3.0, true, tau);
+    FROST_TRY(hhs_fsi(c, F, nF, 0.5 * tau, depth + 1));
+    fsi(c, S, nS, 0.5 * tau);
+    kick_sf(c, S, nS, F, nF, tau / 6.0, false, tau);
+    return FROST_OK;
+}
+
+// validate a caller list (range and repeats); NULL lists are valid by construction
+frost_status check_list(frost_ctx *c, const int32_t *L, int n)
+{
+    if (!L || n <= 0) return FROST_OK;
+    launch_list_relation(c->stream, nullptr, 0, L, n, c->N, c->marks, c->dmisc->rel);
+    FROST_TRY(sync_misc(c));
+    if (c->hmisc->rel[0]) return fail(FROST_EINVAL, "index list has an out-of-range or repeated index");
+    return FROST_OK;
+}
+
+frost_status check_sizes(frost_ctx *c, int64_t n, const char *what)
+{
+    if (n < 0 || n > c->N) return fail(FROST_EINVAL, "%s = %lld outside [0, %d]", what, (long long)n, c->N);
+    return FROST_OK;
+}
+
+void destroy(frost_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (const Timed &t : c->pending) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+    for (auto p : c->lvS) cudaFree(p);
+    for (auto p : c->lvF) cudaFree(p);
+    void *dev[] = {c->x, c->v, c->m, c->all, c->marks, c->recA, c->recB, c->part,
+                   c->aA, c->aB, c->atA, c->atB, c->tau, c->wA, c->wB, c->wpart, c->dmisc};
+    for (void *p : dev)
+        if (p) cudaFree(p);
+    if (c->hmisc) cudaFreeHost(c->hmisc);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+}  // namespace
+
+// ============================================================================================
+// C-ABI
+// ============================================================================================
+extern "C" {
+
+void frost_default_opts(frost_opts *opt)
+{
+    if (!opt) return;
+    opt->precision = FROST_PREC_MIXED;
+    opt->sym = FROST_SYM_HARMONIC;
+    opt->eps_soft = 0.0;
+    opt->max_depth = 40;
+    opt->cuda_stream = nullptr;
+}
+
+const char *frost_last_error(void) { return g_last_error.c_str(); }
+
+const char *frost_version(void) { return "frost-gb300 0.1 (sm_103a)"; }
+
+frost_status frost_init(frost_ctx **out, int64_t n, const double *m, const double *x, const double *v,
+                        double G, double eta, const frost_opts *opt)
+{
+    g_last_error.clear();
+    if (!out) return fail(FROST_EINVAL, "ctx pointer is NULL");
+    *out = nullptr;
+    if (n < 1 || n >= (int64_t(1) << 31)) return fail(FROST_EINVAL, "n = %lld out of range", (long long)n);
+    if (!m || !x || !v) return fail(FROST_EINVAL, "m, x and v are required");
+    if (!(G > 0.0) || !std::isfinite(G) || !(eta > 0.0) || !std::isfinite(eta))
+        return fail(FROST_EINVAL, "G and eta must be finite and positive");
+    frost_opts o;
+    frost_default_opts(&o);
+    if (opt) o = *opt;
+    if (o.precision != FROST_PREC_FP64 && o.precision != FROST_PREC_MIXED)
+        return fail(FROST_EINVAL, "unknown precision %d", o.precision);
+    if (o.sym < 0 || o.sym > 2) return fail(FROST_EINVAL, "unknown symmetrisation %d", o.sym);
+    if (!(o.eps_soft >= 0.0) || !std::isfinite(o.eps_soft)) return fail(FROST_EINVAL, "bad softening");
+
+    frost_ctx *c = new (std::nothrow) frost_ctx();
+    if (!c) return fail(FROST_ENOMEM, "host allocation failed");
+    c->N = (int)n;
+    c->G = G;
+    c->eta = eta;
+    c->eps2 = o.eps_soft * o.eps_soft;
+    c->mixed = (o.precision == FROST_PREC_MIXED);
+    c->sym = o.sym;
+    c->max_depth = o.max_depth > 0 ? o.max_depth : 40;
+
+    auto bail = [&](frost_status st) {
+        destroy(c);
+        return st;
+    };
+#define INIT_CUDA(call)                                                                          \
+    do {                                                                                         \
+        const cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                                   \
+            return bail(fail(e_ == cudaErrorMemoryAllocation ? FROST_ENOMEM : FROST_ECUDA, "%s: %s", #call, \
+                             cudaGetErrorString(e_)));                                           \
+    } while (0)
+
+    INIT_CUDA(cudaGetDevice(&c->device));
+    INIT_CUDA(cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device));
+    // NULL selects the legacy default stream, which is ordered with every blocking stream
+    c->stream = (cudaStream_t)o.cuda_stream;
+    const size_t N = (size_t)n;
+    INIT_CUDA(cudaMalloc(&c->x, sizeof(double) * 3 * N));
+    INIT_CUDA(cudaMalloc(&c->v, sizeof(double) * 3 * N));
+    INIT_CUDA(cudaMalloc(&c->m, sizeof(double) * N));
+    INIT_CUDA(cudaMalloc(&c->all, sizeof(int32_t) * N));
+    INIT_CUDA(cudaMalloc(&c->marks, sizeof(int32_t) * N));
+    INIT_CUDA(cudaMalloc(&c->recA, 64 * N));
+    INIT_CUDA(cudaMalloc(&c->recB, 64 * N));
+    int bps = 1;
+    for (int k = 0; k < 3; ++k) bps = std::max(bps, pair_blocks_per_sm(k, c->mixed));
+    bps = std::max(bps, pair_blocks_per_sm(PASS_ACC, false));
+    c->part_elems = 3 * std::max(N, (size_t)8 * c->n_sm * bps * PAIR_BS * PAIR_ILP);
+    INIT_CUDA(cudaMalloc(&c->part, sizeof(double) * c->part_elems));
+    INIT_CUDA(cudaMalloc(&c->aA, sizeof(double) * 3 * N));
+    INIT_CUDA(cudaMalloc(&c->aB, sizeof(double) * 3 * N));
+    INIT_CUDA(cudaMalloc(&c->atA, sizeof(double) * 3 * N));
+    INIT_CUDA(cudaMalloc(&c->atB, sizeof(double) * 3 * N));
+    INIT_CUDA(cudaMalloc(&c->tau, sizeof(double) * N));
+    INIT_CUDA(cudaMalloc(&c->wA, sizeof(float) * N));
+    INIT_CUDA(cudaMalloc(&c->wB, sizeof(float) * N));
+    INIT_CUDA(cudaMalloc(&c->wpart, sizeof(float) * (c->part_elems / 3)));
+    INIT_CUDA(cudaMalloc(&c->dmisc, sizeof(Misc)));
+    INIT_CUDA(cudaMallocHost(&c->hmisc, sizeof(Misc)));
+    INIT_CUDA(cudaMemsetAsync(c->dmisc, 0, sizeof(Misc), c->stream));
+    INIT_CUDA(cudaMemsetAsync(c->marks, 0, sizeof(int32_t) * N, c->stream));
+    launch_identity(c->stream, c->all, (int)n);
+    // state: [n][3] -> SoA through a scratch copy (inputs may be host or device memory)
+    double *tmp = c->aA;
+    INIT_CUDA(cudaMemcpyAsync(tmp, x, sizeof(double) * 3 * N, cudaMemcpyDefault, c->stream));
+    launch_aos_to_soa(c->stream, tmp, (int)n, c->x, &c->dmisc->err);
+    INIT_CUDA(cudaMemcpyAsync(c->aB, v, sizeof(double) * 3 * N, cudaMemcpyDefault, c->stream));
+    launch_aos_to_soa(c->stream, c->aB, (int)n, c->v, &c->dmisc->err);
+    INIT_CUDA(cudaMemcpyAsync(c->m, m, sizeof(double) * N, cudaMemcpyDefault, c->stream));
+    launch_check_mass(c->stream, c->m, (int)n, &c->dmisc->err);
+    INIT_CUDA(cudaGetLastError());
+    const frost_status st = sync_misc(c);
+    if (st != FROST_OK) return bail(fail(st, "initial state rejected: %s", g_last_error.c_str()));
+#undef INIT_CUDA
+    *out = c;
+    return FROST_OK;
+}
+
+void frost_destroy(frost_ctx *ctx) { destroy(ctx); }
+
+frost_status frost_set_state(frost_ctx *c, const double *x, const double *v, double t)
+{
+    if (!c) return fail(FROST_EINVAL, "NULL context");
+    const size_t N = (size_t)c->N;
+    if (x) {
+        FROST_CUDA(cudaMemcpyAsync(c->aA, x, sizeof(double) * 3 * N, cudaMemcpyDefault, c->stream));
+        launch_aos_to_soa(c->stream, c->aA, c->N, c->x, &c->dmisc->err);
+    }
+    if (v) {
+        FROST_CUDA(cudaMemcpyAsync(c->aB, v, sizeof(double) * 3 * N, cudaMemcpyDefault, c->stream));
+        launch_aos_to_soa(c->stream, c->aB, c->N, c->v, &c->dmisc->err);
+    }
+    c->t = t;
+    FROST_CUDA(cudaGetLastError());
+    return sync_misc(c);
+}
+
+frost_status frost_get_state(frost_ctx *c, double *x, double *v, double *t)
+{
+    if (!c) return fail(FROST_EINVAL, "NULL context");
+    const size_t N = (size_t)c->N;
+    if (x) {
+        launch_soa_to_aos(c->stream, c->x, c->N, c->aA);
+        FROST_CUDA(cudaMemcpyAsync(x, c->aA, sizeof(double) * 3 * N, cudaMemcpyDefault, c->stream));
+    }
+    if (v) {
+        launch_soa_to_aos(c->stream, c->v, c->N, c->aB);
+        FROST_CUDA(cudaMemcpyAsync(v, c->aB, sizeof(double) * 3 * N, cudaMemcpyDefault, c->stream));
+    }
+    if (t) *t = c->t;
+    FROST_CUDA(cudaGetLastError());
+    return sync_misc(c);
+}
+
+frost_status frost_accel_gradient(frost_ctx *c, const int32_t *active, int64_t n_active,
+                                  const int32_t *source, int64_t n_source, double eps_grad,
+                                  double *acc, double *acc_tilde, double *grad)
+{
+    if (!c) return fail(FROST_EINVAL, "NULL context");
+    FROST_TRY(check_sizes(c, n_active, "n_active"));
+    FROST_TRY(check_sizes(c, n_source, "n_source"));
+    if (!std::isfinite(eps_grad)) return fail(FROST_EINVAL, "eps_grad must be finite");
+    const int nA = (int)n_active, nB = (int)n_source;
+    const int32_t *A = active ? active : c->all;
+    const int32_t *B = source ? source : c->all;
+    bool self;
+    if (active == source && nA == nB) {
+        FROST_TRY(check_list(c, active, nA));
+        self = true;
+    } else {
+        launch_list_relation(c->stream, A, nA, B, nB, c->N, c->marks, c->dmisc->rel);
+        FROST_TRY(sync_misc(c));
+        if (c->hmisc->rel[0]) return fail(FROST_EINVAL, "index list has an out-of-range or repeated index");
+        const int64_t common = c->hmisc->rel[1];
+        if (common == nA && nA == nB) self = true;  // the same set in another order
+        else if (common == 0) self = false;
+        else return fail(FROST_EINVAL, "active and source lists overlap partially (%lld common)", (long long)common);
+    }
+    if (nA == 0) return FROST_OK;
+    const bool want_grad = acc_tilde || grad;
+    if (self) {
+        pass_acc(c, A, nA, A, nA, true, c->aA, acc, want_grad ? c->wA : nullptr);
+        if (want_grad)
+            pass_grad(c, A, nA, c->aA, A, nA, c->aA, true, eps_grad, nullptr, acc_tilde, grad, c->wA);
+    } else {
+        pass_acc(c, A, nA, B, nB, false, c->aA, acc, want_grad ? c->wA : nullptr);
+        if (want_grad) {
+            pass_acc(c, B, nB, A, nA, false, c->aB, nullptr);
+            pass_grad(c, A, nA, c->aA, B, nB, c->aB, false, eps_grad, nullptr, acc_tilde, grad, c->wA);
+        }
+    }
+    FROST_CUDA(cudaGetLastError());
+    return sync_misc(c);
+}
+
+frost_status frost_timesteps(frost_ctx *c, const int32_t *set, int64_t n_set, double *tau)
+{
+    if (!c) return fail(FROST_EINVAL, "NULL context");
+    FROST_TRY(check_sizes(c, n_set, "n_set"));
+    if (n_set > 0 && !tau) return fail(FROST_EINVAL, "tau is NULL");
+    FROST_TRY(check_list(c, set, (int)n_set));
+    pass_tstep(c, set ? set : c->all, (int)n_set, tau);
+    FROST_CUDA(cudaGetLastError());
+    return sync_misc(c);
+}
+
+frost_status frost_partition(frost_ctx *c, const int32_t *set, int64_t n_set, const double *tau,
+                             double tau_pivot, int32_t *S, int32_t *F, int64_t *n_slow, int64_t *n_fast)
+{
+    if (!c) return fail(FROST_EINVAL, "NULL context");
+    FROST_TRY(check_sizes(c, n_set, "n_set"));
+    if (n_set > 0 && (!tau || !S || !F)) return fail(FROST_EINVAL, "tau, S and F are required");
+    launch_partition(c->stream, set, (int)n_set, tau, tau_pivot, S, F, c->dmisc->counts);
+    c->st.kernel_launches += 1;
+    FROST_CUDA(cudaGetLastError());
+    FROST_TRY(sync_misc(c));
+    if (n_slow) *n_slow = c->hmisc->counts[0];
+    if (n_fast) *n_fast = c->hmisc->counts[1];
+    return FROST_OK;
+}
+
+frost_status frost_kick(frost_ctx *c, const int32_t *set, int64_t n_set, const double *a, double dt)
+{
+    if (!c) return fail(FROST_EINVAL, "NULL context");
+    FROST_TRY(check_sizes(c, n_set, "n_set"));
+    if (n_set > 0 && !a) return fail(FROST_EINVAL, "a is NULL");
+    launch_kick_aos(c->stream, set, (int)n_set, c->v, c->N, a, dt);
+    c->st.kernel_launches += (n_set > 0);
+    FROST_CUDA(cudaGetLastError());
+    return FROST_OK;
+}
+
+frost_status frost_drift(frost_ctx *c, const int32_t *set, int64_t n_set, double dt)
+{
+    if (!c) return fail(FROST_EINVAL, "NULL context");
+    FROST_TRY(check_sizes(c, n_set, "n_set"));
+    drift(c, set, (int)n_set, dt);
+    FROST_CUDA(cudaGetLastError());
+    return FROST_OK;
+}
+
+frost_status frost_fsi(frost_ctx *c, const int32_t *set, int64_t n_set, double dt)
+{
+    if (!c) return fail(FROST_EINVAL, "NULL context");
+    FROST_TRY(check_sizes(c, n_set, "n_set"));
+    fsi(c, set ? set : c->all, (int)n_set, dt);
+    FROST_CUDA(cudaGetLastError());
+    return FROST_OK;
+}
+
+frost_status frost_step(frost_ctx *c, double dt_pivot, int64_t n_steps)
+{
+    if (!c) return fail(FROST_EINVAL, "NULL context");
+    if (!(dt_pivot > 0.0) || !std::isfinite(dt_pivot)) return fail(FROST_EINVAL, "dt_pivot must be > 0");
+    if (n_steps < 0) return fail(FROST_EINVAL, "n_steps < 0");
+    for (int64_t k = 0; k < n_steps; ++k) {
+        FROST_TRY(hhs_fsi(c, c->all, c->N, dt_pivot, 0));
+        c->t += dt_pivot;
+    }
+    FROST_CUDA(cudaGetLastError());
+    return sync_misc(c);
+}
+
+frost_status frost_energy_momentum(frost_ctx *c, double *E_kin, double *E_pot, double P[3], double L[3])
+{
+    if (!c) return fail(FROST_EINVAL, "NULL context");
+    launch_pack_pos_fp64(c->stream, nullptr, c->N, c->x, c->m, c->N, (double4_32a *)c->recA);
+    SplitShape sh = choose_shape(c->N, c->N, PAIR_BS, pair_blocks_per_sm(PASS_ACC, false), c->n_sm);
+    while ((size_t)sh.nsplit * c->N > c->part_elems && sh.nsplit > 1) {
+        const int tiles = (c->N + PAIR_TJ - 1) / PAIR_TJ;
+        const int ns = std::max(1, sh.nsplit / 2);
+        sh.j_per_split = ((tiles + ns - 1) / ns) * PAIR_TJ;
+        sh.nsplit = (c->N + sh.j_per_split - 1) / sh.j_per_split;
+    }
+    launch_potential(c->stream, (const double4_32a *)c->recA, c->N, c->eps2, c->part, sh);
+    launch_energy_reduce(c->stream, c->x, c->v, c->m, c->N, c->part, sh.nsplit, c->dmisc->eres);
+    c->st.kernel_launches += 3;
+    FROST_CUDA(cudaGetLastError());
+    FROST_TRY(sync_misc(c));
+    const double *e = c->hmisc->eres;
+    if (E_kin) *E_kin = e[0];
+    if (E_pot) *E_pot = -0.5 * c->G * e[1];
+    if (P)
+        for (int k = 0; k < 3; ++k) P[k] = e[2 + k];
+    if (L)
+        for (int k = 0; k < 3; ++k) L[k] = e[5 + k];
+    return FROST_OK;
+}
+
+frost_status frost_get_stats(frost_ctx *c, frost_stats *out)
+{
+    if (!c || !out) return fail(FROST_EINVAL, "NULL argument");
+    if (c->timing) {
+        FROST_CUDA(cudaStreamSynchronize(c->stream));
+        resolve_timing(c);
+    }
+    *out = c->st;
+    out->timing_enabled = c->timing ? 1 : 0;
+    return FROST_OK;
+}
+
+frost_status frost_reset_stats(frost_ctx *c)
+{
+    if (!c) return fail(FROST_EINVAL, "NULL context");
+    if (c->timing) {
+        FROST_CUDA(cudaStreamSynchronize(c->stream));
+        resolve_timing(c);
+    }
+    c->st = frost_stats{};
+    return FROST_OK;
+}
+
+frost_status frost_set_timing(frost_ctx *c, int32_t enable)
+{
+    if (!c) return fail(FROST_EINVAL, "NULL context");
+    if (c->timing && !enable) {
+        FROST_CUDA(cudaStreamSynchronize(c->stream));
+        resolve_timing(c);
+    }
+    c->timing = enable != 0;
+    return FROST_OK;
+}
+
+frost_status frost_synchronize(frost_ctx *c)
+{
+    if (!c) return fail(FROST_EINVAL, "NULL context");
+    FROST_CUDA(cudaGetLastError());
+    return sync_misc(c);
+}
+
+frost_status frost_clear_error(frost_ctx *c)
+{
+    if (!c) return fail(FROST_EINVAL, "NULL context");
+    FROST_CUDA(cudaMemsetAsync(&c->dmisc->err, 0, sizeof(int), c->stream));
+    FROST_CUDA(cudaStreamSynchronize(c->stream));
+    g_last_error.clear();
+    return FROST_OK;
+}
+
+}  // extern "C"

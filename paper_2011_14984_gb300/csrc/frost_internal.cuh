@@ -1,0 +1,138 @@
+// Internal declarations of the sm_103a HHS-FSI kernels (not part of the C-ABI).
+//
+// Device data layout (all owned by a frost_ctx):
+//   x, v : FP64 structure of arrays, component c of particle i at [c * N + i]
+//   m    : FP64 masses [N]
+// Every pair pass works on packed, contiguous per-pass records of its active list A and its
+// source list B (built by the pack kernels from the SoA store and the index lists), so the
+// pair kernels stream their j-tiles linearly through shared memory.
+//
+// Mixed-precision records (FP32, 16-byte aligned float4):
+//   acc / time-step pass:  p0 = {x_hi, y_hi, z_hi, m}, p1 = {x_lo, y_lo, z_lo, 0}
+//                          with x_hi = fp32(x), x_lo = fp32(x - x_hi)  (float-float, 48 bits)
+//                          time-step pass adds pv = {vx, vy, vz, G m}
+//   gradient pass:         q0 = {x_h, y_h, z_h, m}, q1 = {x_m, y_m, z_m, ah_x},
+//                          q2 = {x_l, y_l, z_l, ah_y}, q3 = {ah_z, al_x, al_y, al_z}
+//                          x = x_h + x_m + x_l with x_h, x_m holding 12 significant bits, so
+//                          ((x_hj - x_hi) + (x_mj - x_mi)) is exact and the separation is
+//                          rounded once; a = ah + al with ah holding 12 significant bits.
+// FP64 records: d0 = {x, y, z, m}, d1 = {ax, ay, az, 0} (gradient), dv = {vx, vy, vz, G m}.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+namespace frost {
+
+// device error word bits
+enum : int {
+    ERR_NONFINITE = 1 << 0,
+    ERR_COINCIDENT = 1 << 1,
+    ERR_INDEX = 1 << 2,
+    ERR_TIMEOUT = 1 << 3,
+    ERR_DUPLICATE = 1 << 4,
+};
+
+// kinds of timed pair kernels
+enum PassKind { PASS_ACC = 0, PASS_GRAD = 1, PASS_TSTEP = 2 };
+
+// Tile geometry of the pair kernels.
+constexpr int PAIR_BS = 128;   // threads per block
+constexpr int PAIR_ILP = 2;    // i-particles per thread (mixed)
+constexpr int PAIR_TJ = 128;   // j-records per shared-memory tile
+constexpr int PAIR_ILP64 = 1;  // i-particles per thread (FP64)
+
+struct SplitShape {
+    int nblk_i;       // blocks along the active list
+    int nsplit;       // blocks along the source list (j-split)
+    int j_per_split;  // sources per split (multiple of PAIR_TJ)
+};
+
+struct PairArgs {
+    // records of the active list (i) and of the source list (j)
+    const void *irec;
+    const void *jrec;
+    int n_a, n_s;
+    int self_pass;    // 1 if the two lists are the same list (same positions)
+    double eps2;      // softening^2
+    double *part;     // partial results [nsplit][ncomp][n_a]
+    SplitShape shape;
+    float *wpart = nullptr;        // acc (mixed): per-split max_j m_j / r^3 [nsplit][n_a], or NULL
+    const float *wmax = nullptr;   // grad (mixed): per-particle max_j m_j / r^3 [n_a], or NULL
+    bool accurate = false;         // acc (mixed): the variant that feeds a gradient pass
+};
+
+// ---- pack kernels: list -> per-pass records ------------------------------------------
+void launch_pack_pos_mixed(cudaStream_t s, const int32_t *list, int n, const double *x,
+                           const double *m, int N, float4 *rec);
+void launch_pack_grad_mixed(cudaStream_t s, const int32_t *list, int n, const double *x,
+                            const double *m, int N, const double *acc /*[3][n]*/, float4 *rec);
+void launch_pack_tstep_mixed(cudaStream_t s, const int32_t *list, int n, const double *x,
+                             const double *v, const double *m, int N, double G, float4 *rec);
+void launch_pack_pos_fp64(cudaStream_t s, const int32_t *list, int n, const double *x,
+                          const double *m, int N, double4_32a *rec);
+void launch_pack_grad_fp64(cudaStream_t s, const int32_t *list, int n, const double *x,
+                           const double *m, int N, const double *acc, double4_32a *rec);
+void launch_pack_tstep_fp64(cudaStream_t s, const int32_t *list, int n, const double *x,
+                            const double *v, const double *m, int N, double G, double4_32a *rec);
+
+// ---- pair kernels ---------------------------------------------------------------------
+// acc: part[split][c][i] = sum_j m_j x_ji / r^3 over the split's sources
+void launch_acc(cudaStream_t s, bool mixed, const PairArgs &a);
+// grad: part[split][c][i] = sum_j m_j r^-5 (r^2 a_ji - 3 (x_ji . a_ji) x_ji)
+void launch_grad(cudaStream_t s, bool mixed, const PairArgs &a);
+// time-step: part[split][i] = min_j min(t_ff s(eta dt_ff), t_fb s(eta dt_fb)) (without eta)
+void launch_tstep(cudaStream_t s, bool mixed, const PairArgs &a, double eta, int sym, int *err);
+
+// ---- finalisation of split partials ---------------------------------------------------
+// out_soa[c][i] = scale * sum_split part[split][c][i]  (also [i][3] copy if out_aos != NULL);
+// with wpart, wmax[i] = max_split wpart[split][i]
+void launch_finalize_vec(cudaStream_t s, const double *part, int nsplit, int n, double scale,
+                         double *out_soa, double *out_aos, const float *wpart, float *wmax,
+                         int *err, int coincident_bit);
+// a~ = a + c g with g = scale * sum part; writes a~ (soa and/or aos) and g (aos, optional)
+void launch_finalize_grad(cudaStream_t s, const double *part, int nsplit, int n, double scale,
+                          const double *a_soa, double c, double *at_soa, double *at_aos,
+                          double *g_aos, int *err, int coincident_bit);
+// tau[i] = eta * min_split part[split][i]; flags non-positive or NaN values
+void launch_finalize_tau(cudaStream_t s, const double *part, int nsplit, int n, double eta,
+                         double *tau, int *err);
+
+// ---- integrator kernels ---------------------------------------------------------------
+void launch_kick(cudaStream_t s, const int32_t *list, int n, double *v, int N,
+                 const double *a_soa, double dt);
+void launch_kick_aos(cudaStream_t s, const int32_t *list, int n, double *v, int N,
+                     const double *a_aos, double dt);
+void launch_drift(cudaStream_t s, const int32_t *list, int n, double *x, const double *v,
+                  int N, double dt);
+// stable partition: S gets set[k] with tau[k] >= pivot, F the rest; counts[0] = |S|,
+// counts[1] = |F|
+void launch_partition(cudaStream_t s, const int32_t *set, int n, const double *tau,
+                      double pivot, int32_t *S, int32_t *F, int64_t *counts);
+
+// ---- validation and reductions --------------------------------------------------------
+// marks[] (int32[N]) must be zero on entry and is returned to zero on exit.
+// out[0] = bad index or repeated index in either list (0/1), out[1] = |A cap B|
+void launch_list_relation(cudaStream_t s, const int32_t *A, int nA, const int32_t *B, int nB,
+                          int N, int32_t *marks, int64_t *out);
+void launch_check_finite(cudaStream_t s, const double *p, int64_t n, int *err);
+void launch_identity(cudaStream_t s, int32_t *list, int n);
+// [n][3] -> [3][n] (flags non-finite values) and back; masses must be finite and > 0
+void launch_aos_to_soa(cudaStream_t s, const double *aos, int n, double *soa, int *err);
+void launch_soa_to_aos(cudaStream_t s, const double *soa, int n, double *aos);
+void launch_check_mass(cudaStream_t s, const double *m, int n, int *err);
+// per-particle potential phi_i = sum_{j != i} m_j / sqrt(r^2 + eps2) in FP64, split
+// partials part[split][i] (summed in order by launch_energy_reduce)
+void launch_potential(cudaStream_t s, const double4_32a *rec, int n, double eps2, double *part,
+                      const SplitShape &shape);
+// out[0] = T, out[1] = sum_i m_i phi_i, out[2..4] = P, out[5..7] = L (one block, fixed order)
+void launch_energy_reduce(cudaStream_t s, const double *x, const double *v, const double *m,
+                          int N, const double *part, int nsplit, double *out);
+
+SplitShape choose_shape(int n_a, int n_s, int i_per_block, int blocks_per_sm, int n_sm);
+int pair_blocks_per_sm(int kind, bool mixed);
+int pair_i_per_block(bool mixed);
+
+}  // namespace frost

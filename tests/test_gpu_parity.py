@@ -1,0 +1,356 @@
+"""GPU parity of the CUDA hot path (through the C-ABI) against the FP64 CPU oracle.
+
+Tolerances:
+  * FP64 mode: every particle within 1e-12 relative for a_i, g_i and tau_i.
+  * mixed mode: 99.9th percentile of the per-particle relative error <= 1e-6 for a_i and
+    for the gradient term g_i; the time-steps, which only steer the slow/fast split, within
+    2e-6 relative at the 99.9th percentile (FP32 pair body with about twenty roundings and
+    the approximate MUFU functions, each a few 1e-7).
+  * index work (partition) bit-exact; kick/drift bit-exact (same roundings as the oracle).
+Inputs are seeded synthetic Plummer spheres (equal or Kroupa masses), sized to span several
+shared-memory tiles with a ragged tail.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2011_14984_gb300 import ics
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2011_14984_gb300 import frost
+    frost.load()
+
+
+def F(*a, **k):
+    from paper_2011_14984_gb300.frost import Frost
+    return Frost(*a, **k)
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    if a.ndim == 1:
+        return np.abs(a - b) / np.maximum(np.abs(b), 1e-300)
+    return np.linalg.norm(a - b, axis=-1) / np.maximum(np.linalg.norm(b, axis=-1), 1e-300)
+
+
+def p999(e):
+    return float(np.percentile(e, 99.9))
+
+
+def oracle_g(m, x, A, B, eps2=0.0):
+    """g from the oracle with the accelerations of the same pass (same-set or cross)."""
+    A = np.asarray(A, dtype=np.int32)
+    B = np.asarray(B, dtype=np.int32)
+    aA = oracle.acc(m, x, A, B, eps2=eps2)
+    aB = oracle.acc(m, x, B, A, eps2=eps2)
+    return aA, oracle.grad(m, x, A, aA, B, aB, eps2=eps2)
+
+
+def cpu(t):
+    return t.detach().cpu().numpy()
+
+
+# ---------------------------------------------------------------------------------------
+# acceleration and gradient passes
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("eps_soft", [0.0, 1e-3])
+def test_accel_gradient_full_set(precision, eps_soft):
+    n = 5000  # 39 tiles of 128 with a ragged tail
+    m, x, v = ics.plummer(n, 101, masses=ics.kroupa_masses(n, 101))
+    f = F(m, x, v, precision=precision, eps_soft=eps_soft)
+    eps = 0.01
+    out = f.accel_gradient(None, None, eps_grad=eps)
+    A = np.arange(n, dtype=np.int32)
+    a_ref, g_ref = oracle_g(m, x, A, A, eps2=eps_soft ** 2)
+    at_ref = a_ref + eps * eps / 48.0 * g_ref
+    ea = rel(cpu(out["acc"]), a_ref)
+    eg = rel(cpu(out["grad"]), g_ref)
+    et = rel(cpu(out["acc_tilde"]), at_ref)
+    if precision == "fp64":
+        assert ea.max() < 1e-12 and eg.max() < 1e-12 and et.max() < 1e-12, (ea.max(), eg.max())
+    else:
+        assert p999(ea) < 1e-6 and p999(eg) < 1e-6 and p999(et) < 1e-6, (p999(ea), p999(eg))
+        assert ea.max() < 1e-5 and eg.max() < 2e-5
+    f.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_accel_gradient_cross_pass(precision):
+    """Disjoint active/source lists: the inter-level passes of Eqs. force-newton-inter and
+    force-gradient-inter-1/2 (a_j of the sources due to the active set)."""
+    n = 3001
+    m, x, v = ics.plummer(n, 7)
+    rng = np.random.default_rng(3)
+    perm = rng.permutation(n).astype(np.int32)
+    S, Fl = np.sort(perm[:700]), perm[700:]  # Fl unsorted on purpose
+    f = F(m, x, v, precision=precision)
+    eps = 0.05
+    out = f.accel_gradient(S, Fl, eps_grad=eps)
+    a_ref, g_ref = oracle_g(m, x, S, Fl)
+    ea, eg = rel(cpu(out["acc"]), a_ref), rel(cpu(out["grad"]), g_ref)
+    if precision == "fp64":
+        assert ea.max() < 1e-12 and eg.max() < 1e-12
+    else:
+        assert p999(ea) < 1e-6 and p999(eg) < 1e-6, (p999(ea), p999(eg))
+    # the same set given in another order is the intra-set pass
+    out2 = f.accel_gradient(S[::-1].copy(), S, eps_grad=eps)
+    a2, g2 = oracle_g(m, x, S[::-1], S[::-1])
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    assert rel(cpu(out2["acc"]), a2).max() < tol
+    f.close()
+
+
+def test_accel_gradient_two_body_closed_form():
+    """Pin on the GPU path itself: two bodies give a~ = (1 + eps^2 G M / (12 r^3)) a."""
+    G = 1.3
+    m, x, v = ics.kepler_binary(0.4, 1.1, 0.7, 0.2, G=G, mean_anomaly=0.8)
+    for prec, tol in (("fp64", 1e-14), ("mixed", 1e-6)):
+        f = F(m, x, v, G=G, precision=prec)
+        out = f.accel_gradient(None, None, eps_grad=0.1)
+        r = np.linalg.norm(x[0] - x[1])
+        fac = 1 + 0.01 * G * m.sum() / (12 * r ** 3)
+        a = cpu(out["acc"])
+        assert rel(cpu(out["acc_tilde"]), fac * a).max() < tol
+        assert rel(a[:1], (G * m[1] * (x[1] - x[0]) / r ** 3)[None]).max() < tol
+        f.close()
+
+
+def test_accel_gradient_edge_cases():
+    from paper_2011_14984_gb300 import frost as fr
+    m, x, v = ics.plummer(300, 5)
+    f = F(m, x, v, precision="mixed")
+    # empty active list
+    out = f.accel_gradient(np.zeros(0, np.int32), np.arange(10, dtype=np.int32))
+    assert out["acc"].shape == (0, 3)
+    # empty source list: zero acceleration, a~ = a
+    out = f.accel_gradient(np.arange(5, dtype=np.int32), np.zeros(0, np.int32), eps_grad=0.1)
+    assert float(out["acc"].abs().max()) == 0.0 and float(out["grad"].abs().max()) == 0.0
+    # single particle against itself
+    out = f.accel_gradient(np.array([7], np.int32), np.array([7], np.int32), eps_grad=0.1)
+    assert float(out["acc"].abs().max()) == 0.0
+    # partial overlap, repeated and out-of-range indices are rejected
+    with pytest.raises(fr.FrostError) as e:
+        f.accel_gradient(np.array([1, 2, 3], np.int32), np.array([3, 4], np.int32))
+    assert e.value.code == fr.FROST_EINVAL
+    with pytest.raises(fr.FrostError) as e:
+        f.accel_gradient(np.array([1, 1], np.int32), np.array([3, 4], np.int32))
+    assert e.value.code == fr.FROST_EINVAL
+    with pytest.raises(fr.FrostError) as e:
+        f.accel_gradient(np.array([1, 2], np.int32), np.array([3, 400], np.int32))
+    assert e.value.code == fr.FROST_EINVAL
+    f.close()
+
+
+def test_coincident_and_nonfinite_inputs_are_reported():
+    from paper_2011_14984_gb300 import frost as fr
+    m, x, v = ics.plummer(200, 6)
+    x[17] = x[42]
+    for prec in ("fp64", "mixed"):
+        f = F(m, x, v, precision=prec)
+        with pytest.raises(fr.FrostError) as e:
+            f.accel_gradient(None, None, eps_grad=0.1)
+        assert e.value.code == fr.FROST_ECOINCIDENT
+        f.close()
+        f = F(m, x, v, precision=prec)
+        with pytest.raises(fr.FrostError) as e:
+            f.timesteps()
+        assert e.value.code == fr.FROST_ECOINCIDENT
+        f.close()
+    x[17, 0] = np.nan
+    with pytest.raises(fr.FrostError) as e:
+        F(m, x, v)
+    assert e.value.code == fr.FROST_ENONFINITE
+
+
+# ---------------------------------------------------------------------------------------
+# time-steps, partition, kick / drift
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("sym", [0, 1, 2])
+def test_timesteps(precision, sym):
+    n = 2500
+    m, x, v = ics.plummer_kroupa_binaries(n, 9, binary_fraction=0.1)
+    f = F(m, x, v, precision=precision, sym=sym, eta=0.2)
+    rng = np.random.default_rng(1)
+    P = rng.permutation(n)[:1900].astype(np.int32)
+    tau = cpu(f.timesteps(P))
+    ref = oracle.timesteps(m, x, v, P, eta=0.2, sym=sym)
+    e = rel(tau, ref)
+    if precision == "fp64":
+        assert e.max() < 1e-12, e.max()
+    else:
+        assert p999(e) < 2e-6 and e.max() < 1e-4, (p999(e), e.max())
+    assert np.isinf(cpu(f.timesteps(np.array([3], np.int32))))[0]
+    f.close()
+
+
+def test_timesteps_circular_binary_rule_of_thumb():
+    """Eq. eta-two-pi on the GPU: tau = eta P / (2 pi) for a circular binary."""
+    m, x, v = ics.kepler_binary(0.5, 0.5, 1.0, 0.0)
+    for prec, tol in (("fp64", 1e-14), ("mixed", 2e-6)):
+        f = F(m, x, v, precision=prec, eta=0.1)
+        tau = cpu(f.timesteps())
+        assert rel(tau, np.full(2, 0.1 * 2 * math.pi / (2 * math.pi))).max() < tol
+        f.close()
+
+
+def test_partition_bit_exact():
+    m, x, v = ics.plummer(3000, 2)
+    f = F(m, x, v)
+    rng = np.random.default_rng(4)
+    P = rng.permutation(3000)[:2777].astype(np.int32)
+    tau = rng.random(2777)
+    tau[::7] = 0.5  # ties go to the slow set
+    for piv in (0.5, 0.0, 2.0, 0.123):
+        S, Fl = f.partition(P, tau, piv)
+        Sr, Fr = oracle.partition(P, tau, piv)
+        assert np.array_equal(cpu(S), Sr) and np.array_equal(cpu(Fl), Fr)
+    S, Fl = f.partition(P[:0], tau[:0], 0.5)
+    assert S.numel() == 0 and Fl.numel() == 0
+    f.close()
+
+
+def test_kick_drift_bit_exact():
+    n = 1000
+    m, x, v = ics.plummer(n, 8)
+    f = F(m, x, v, precision="fp64")
+    rng = np.random.default_rng(2)
+    I = rng.permutation(n)[:600].astype(np.int32)
+    a = rng.standard_normal((600, 3))
+    f.kick(I, a, 0.0123)
+    f.drift(I, 0.031)
+    xg, vg, _ = f.state()
+    xo, vo = x.copy(), v.copy()
+    oracle.kick(I, vo, a, 0.0123)
+    oracle.drift(I, xo, vo, 0.031)
+    assert np.array_equal(xg, xo) and np.array_equal(vg, vo)
+    f.close()
+
+
+# ---------------------------------------------------------------------------------------
+# integrator
+# ---------------------------------------------------------------------------------------
+
+def test_fsi_step_parity():
+    n = 700
+    m, x, v = ics.plummer(n, 12)
+    S = np.arange(0, n, 2, dtype=np.int32)
+    f = F(m, x, v, precision="fp64")
+    f.fsi(S, 1e-2)
+    xg, vg, _ = f.state()
+    xo, vo = oracle.fsi(m, x, v, S, 1e-2)
+    assert np.max(np.abs(xg - xo)) < 1e-14 and np.max(np.abs(vg - vo)) < 1e-12
+
+
+def test_hhs_fsi_trajectory_parity_fp64():
+    """Plummer N = 1024 (seed 1) to t = 0.125 in 16 top-level steps of 2^-7, eta = 0.2:
+    positions within 1e-10 of the oracle and the same hierarchy depth."""
+    m, x, v = ics.plummer(1024, 1)
+    f = F(m, x, v, precision="fp64", eta=0.2)
+    f.step(2.0 ** -7, 16)
+    xg, vg, t = f.state()
+    st = f.stats()
+    oracle.reset_counters()
+    xo, vo = oracle.steps(m, x, v, 2.0 ** -7, 16, eta=0.2)
+    oc = oracle.counters()
+    assert t == pytest.approx(0.125)
+    assert np.max(np.abs(xg - xo)) < 1e-10 and np.max(np.abs(vg - vo)) < 1e-9
+    assert st["max_depth_seen"] == oc["max_depth"]
+    e_g, e_o = f.energy(), oracle.energy(m, xo, vo)
+    assert abs(e_g["E"] - e_o["E"]) < 1e-12 * abs(e_o["E"])
+    f.close()
+
+
+def test_hhs_fsi_mixed_energy_parity():
+    """Mixed precision reaches the FP64 energy error within a factor 2 (plus round-off)."""
+    m, x, v = ics.plummer(1024, 1)
+    E0 = oracle.energy(m, x, v)["E"]
+    dE = {}
+    for prec in ("fp64", "mixed"):
+        f = F(m, x, v, precision=prec, eta=0.2)
+        f.step(2.0 ** -7, 16)
+        dE[prec] = abs((f.energy()["E"] - E0) / E0)
+        f.close()
+    assert dE["mixed"] < 2 * dE["fp64"] + 1e-11, dE
+
+
+def test_solar_system_hhs_fsi_on_gpu():
+    """The paper's five-body initial state (App. A1) through frost_step in FP64: the same
+    trajectory as the oracle after 200 years at eta = 0.05."""
+    from conftest import load_solar_system
+    _, m, x, v, G = load_solar_system()
+    f = F(m, x, v, G=G, eta=0.05, precision="fp64")
+    n = int(round(200 * 365.25 / 4096.0))
+    f.step(4096.0, n)
+    xg, vg, _ = f.state()
+    xo, vo = oracle.steps(m, x, v, 4096.0, n, G=G, eta=0.05)
+    assert np.max(np.abs(xg - xo)) < 1e-9
+    f.close()
+
+
+def test_energy_momentum_parity():
+    n = 3000
+    m, x, v = ics.plummer(n, 77, masses=ics.kroupa_masses(n, 77))
+    for eps in (0.0, 0.01):
+        f = F(m, x, v, eps_soft=eps)
+        e = f.energy()
+        r = oracle.energy(m, x, v, eps2=eps * eps)
+        assert abs(e["T"] - r["T"]) < 1e-13 * abs(r["T"])
+        assert abs(e["U"] - r["U"]) < 1e-12 * abs(r["U"])
+        assert np.max(np.abs(e["P"] - r["P"])) < 1e-15
+        assert np.max(np.abs(e["L"] - r["L"])) < 1e-14
+        f.close()
+
+
+def test_depth_limit():
+    from paper_2011_14984_gb300 import frost as fr
+    m, x, v = ics.kepler_binary(0.5, 0.5, 1e-3, 0.0)
+    f = F(m, x, v, max_depth=3)
+    with pytest.raises(fr.FrostError) as e:
+        f.step(1.0, 1)
+    assert e.value.code == fr.FROST_EDEPTH
+    f.close()
+
+
+# ---------------------------------------------------------------------------------------
+# full-size launch configurations, checked on sampled particles
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_full_pass_64k_sampled(precision):
+    """Plummer N = 65536 (seed 2), the full acc + gradient pass of the benchmark: 512
+    sampled particles against the oracle, which computes every a_j for the gradient."""
+    m, x, v = ics.workload("plummer_64k")
+    n = m.size
+    f = F(m, x, v, precision=precision)
+    eps = 2.0 ** -8
+    out = f.accel_gradient(None, None, eps_grad=eps)
+    rng = np.random.default_rng(11)
+    I = np.sort(rng.choice(n, 512, replace=False)).astype(np.int32)
+    A = np.arange(n, dtype=np.int32)
+    a_all = oracle.acc(m, x, A, A)
+    g_ref = oracle.grad(m, x, I, a_all[I], A, a_all)
+    ea = rel(cpu(out["acc"])[I], a_all[I])
+    eg = rel(cpu(out["grad"])[I], g_ref)
+    if precision == "fp64":
+        assert ea.max() < 1e-12 and eg.max() < 1e-12
+    else:
+        assert p999(ea) < 1e-6 and p999(eg) < 1e-6, (p999(ea), p999(eg))
+    # a property at any size: total force vanishes
+    a = cpu(out["acc"])
+    Ftot = (m[:, None] * a).sum(0)
+    assert np.all(np.abs(Ftot) < 1e-9 * (m[:, None] * np.abs(a)).sum())
+    f.close()

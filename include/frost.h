@@ -199,6 +199,32 @@ const char *frost_last_error(void);
 /* Library version string. */
 const char *frost_version(void);
 
+/*
+ * Entry point that allocates nothing (the paper has no counterpart; it serves callers that
+ * may not allocate device memory, e.g. inside an application or allocator that owns all
+ * device memory, or in time-critical code where an allocation is not allowed).
+ *
+ * Computes the mixed-precision Newtonian accelerations of all n particles against all n
+ * particles, a_i = G sum_{j != i} m_j x_ji / (r_ji^2 + eps_soft^2)^(3/2), with the same
+ * kernels as frost_accel_gradient in FROST_PREC_MIXED mode (same tolerance), but without a
+ * context: m[n], x[n][3] (inputs) and acc[n][3] (output) are caller-owned device pointers,
+ * and all scratch lives in one static device array of FROST_NOALLOC_MAX_N particles
+ * (8 MiB), which every GPU that loads the library holds until the process exits.
+ *  - n outside [1, FROST_NOALLOC_MAX_N] returns FROST_EINVAL; nothing is launched.
+ *  - No cudaMalloc, cudaFree or other allocating call is made.
+ *  - The first call on each device looks up the scratch array's device address on that
+ *    device (the device current at the call); make that first call before any stream
+ *    capture.
+ *  - Every call shares the scratch array; calls whose GPU work may overlap (other streams or
+ *    host threads without ordering) race and must be serialised by the caller.
+ *  - Work runs on cuda_stream (NULL = legacy default stream) and the call synchronises it;
+ *    non-finite inputs or non-positive masses give FROST_ENONFINITE, two particles at zero
+ *    separation (eps_soft = 0) FROST_ECOINCIDENT.
+ */
+#define FROST_NOALLOC_MAX_N 65536
+frost_status frost_accel_noalloc(int64_t n, const double *m, const double *x, double G,
+                                 double eps_soft, double *acc, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

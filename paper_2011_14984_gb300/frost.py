@@ -83,6 +83,7 @@ _SIGS = {
     "frost_destroy": (None, [_P]),
     "frost_last_error": (ctypes.c_char_p, []),
     "frost_version": (ctypes.c_char_p, []),
+    "frost_accel_noalloc": (ctypes.c_int, [_I64, _P, _P, _D, _D, _P, _P]),
 }
 
 
@@ -229,6 +230,19 @@ def frost_last_error() -> str:
 
 def frost_version() -> str:
     return load().frost_version().decode()
+
+
+FROST_NOALLOC_MAX_N = 65536
+
+
+def frost_accel_noalloc(n, m, x, G, eps_soft, acc, stream=None) -> None:
+    """Newtonian accelerations of all n particles (device m[n], x[n][3] -> acc[n][3]) without
+    any device allocation: the scratch is a static device array of FROST_NOALLOC_MAX_N
+    particles shared by all calls (serialise calls whose GPU work could overlap)."""
+    code = load().frost_accel_noalloc(int(n), _ptr(m), _ptr(x), float(G), float(eps_soft),
+                                      _ptr(acc), stream)
+    if code != FROST_OK:
+        raise FrostError(code, "frost_accel_noalloc", "see include/frost.h for the status meaning")
 
 
 # ---- convenience wrapper ---------------------------------------------------------------

@@ -59,6 +59,10 @@
 #define OR_ECOINCIDENT 5
 #define OR_EDEPTH 6
 
+/* passes with fewer pair evaluations than this run on one thread (a parallel region per
+ * few-body pass would cost more than the pass) */
+#define OR_PAR_MIN 262144
+
 /* ---- counters (pair evaluations), read by the tests and the CPU baseline ---- */
 static int64_t or_count_acc = 0;
 static int64_t or_count_grad = 0;
@@ -107,7 +111,7 @@ int or_acc(const double *m, const double *x, const int32_t *A, int64_t nA,
            const int32_t *B, int64_t nB, double G, double eps2, double *a)
 {
     int err = OR_OK;
-#pragma omp parallel for schedule(dynamic, 16) reduction(max : err)
+#pragma omp parallel for schedule(dynamic, 16) reduction(max : err) if (nA * nB > OR_PAR_MIN)
     for (int64_t ia = 0; ia < nA; ++ia) {
         const int32_t i = A[ia];
         double sx = 0.0, sy = 0.0, sz = 0.0;
@@ -144,7 +148,7 @@ int or_grad(const double *m, const double *x, const int32_t *A, int64_t nA, cons
             const int32_t *B, int64_t nB, const double *aB, double G, double eps2, double *g)
 {
     int err = OR_OK;
-#pragma omp parallel for schedule(dynamic, 16) reduction(max : err)
+#pragma omp parallel for schedule(dynamic, 16) reduction(max : err) if (nA * nB > OR_PAR_MIN)
     for (int64_t ia = 0; ia < nA; ++ia) {
         const int32_t i = A[ia];
         double sx = 0.0, sy = 0.0, sz = 0.0;
@@ -298,7 +302,7 @@ int or_timesteps(const double *m, const double *x, const double *v, const int32_
                  double G, double eta, int sym, double *tau)
 {
     int err = OR_OK;
-#pragma omp parallel for schedule(dynamic, 16) reduction(max : err)
+#pragma omp parallel for schedule(dynamic, 16) reduction(max : err) if (nP * nP > OR_PAR_MIN)
     for (int64_t ia = 0; ia < nP; ++ia) {
         const int32_t i = P[ia];
         double best = INFINITY;
@@ -477,7 +481,7 @@ int or_energy(int64_t n, const double *m, const double *x, const double *v, doub
     double *e = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     if (!e) return OR_ENOMEM;
     int err = OR_OK;
-#pragma omp parallel for schedule(dynamic, 16) reduction(max : err)
+#pragma omp parallel for schedule(dynamic, 16) reduction(max : err) if (n * n > OR_PAR_MIN)
     for (int64_t i = 0; i < n; ++i) {
         double s = 0.0;
         for (int64_t j = i + 1; j < n; ++j) {

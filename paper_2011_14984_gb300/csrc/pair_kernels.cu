@@ -348,13 +348,34 @@ __device__ __noinline__ void grad_term_fp64(const float4 J0, const float4 J1, co
     gz = fma(w, fma(-t3, dz, Az), gz);
 }
 
+// Dominant terms: up to GRAD_SLOTS per particle are recorded during the j-loop and summed
+// in FP64 after it (deferred, so the FP64 work is not issued once per lane and source).
+constexpr int GRAD_SLOTS = 4;
+
+template <int ILP>
+struct BigSlots {
+    int n[ILP];
+    int j0[ILP], j1[ILP], j2[ILP], j3[ILP];
+};
+
+template <int ILP>
+__device__ __forceinline__ void push_big(BigSlots<ILP> &b, int k, int j)
+{
+    const int c = b.n[k];
+    if (c == 0) b.j0[k] = j;
+    else if (c == 1) b.j1[k] = j;
+    else if (c == 2) b.j2[k] = j;
+    else b.j3[k] = j;
+    b.n[k] = c + 1;
+}
+
 template <int ILP, bool MASK>
 __device__ __forceinline__ void grad_mixed_j(const float4 J0, const float4 J1, const float4 J2,
                                              const float4 J3, const GradMixedI<ILP> &I,
-                                             float eps2, double eps2d, int jpos,
+                                             float eps2, int jglob, int jpos,
                                              const int (&ipos)[ILP], const float (&thr)[ILP],
-                                             float (&gx)[ILP], float (&gy)[ILP], float (&gz)[ILP],
-                                             double (&bx)[ILP], double (&by)[ILP], double (&bz)[ILP])
+                                             BigSlots<ILP> &big, float (&gx)[ILP],
+                                             float (&gy)[ILP], float (&gz)[ILP])
 {
 #pragma unroll
     for (int k = 0; k < ILP; ++k) {
@@ -378,11 +399,10 @@ __device__ __forceinline__ void grad_mixed_j(const float4 J0, const float4 J1, c
             self = (jpos == ipos[k]);
             w = self ? 0.f : w;
         }
-        // dominant terms (weight above the particle's threshold) go to the FP64 path and
-        // stay out of the FP32 partial sum
-        const bool big = w > thr[k];
-        if (big) grad_term_fp64<ILP>(J0, J1, J2, J3, I, k, eps2d, bx[k], by[k], bz[k]);
-        const float wf = big ? 0.f : w;
+        // a dominant term goes to a deferred FP64 slot and stays out of the FP32 sum
+        const bool isbig = (w > thr[k]) && (big.n[k] < GRAD_SLOTS);
+        if (isbig) push_big(big, k, jglob);
+        const float wf = isbig ? 0.f : w;
         const float xa = fmaf(dx, Ax, fmaf(dy, Ay, dz * Az));
         const float t3 = 3.0f * xa * ri2;  // 3 (x.a) / r^2
         const float nx = fmaf(wf, fmaf(-t3, dx, Ax), gx[k]);
@@ -401,7 +421,7 @@ __device__ __forceinline__ void grad_mixed_j(const float4 J0, const float4 J1, c
 }
 
 // wmax: per active particle, max_j m_j / r^3 from the Newtonian pass at the same positions
-// (NULL: no FP64 path).  Terms heavier than wmax / 32 are summed in FP64.
+// (NULL: no FP64 terms).  Up to GRAD_SLOTS terms heavier than wmax / 4 are summed in FP64.
 template <int BS, int ILP, int TJ>
 __global__ void __launch_bounds__(BS) k_grad_mixed(const float4 *__restrict__ irec,
                                                    const float4 *__restrict__ jrec, int n_a,
@@ -416,10 +436,13 @@ __global__ void __launch_bounds__(BS) k_grad_mixed(const float4 *__restrict__ ir
     GradMixedI<ILP> I;
     int ipos[ILP];
     float thr[ILP];
+    BigSlots<ILP> big;
 #pragma unroll
     for (int k = 0; k < ILP; ++k) {
         const int i = ibase + k * BS + tid;
         ipos[k] = i;
+        big.n[k] = 0;
+        big.j0[k] = big.j1[k] = big.j2[k] = big.j3[k] = 0;
         float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0, q2 = q0, q3 = q0;
         thr[k] = INFINITY;
         if (i < n_a) {
@@ -427,7 +450,7 @@ __global__ void __launch_bounds__(BS) k_grad_mixed(const float4 *__restrict__ ir
             q1 = irec[n_a + i];
             q2 = irec[2 * n_a + i];
             q3 = irec[3 * n_a + i];
-            if (wmax) thr[k] = 0.03125f * wmax[i];
+            if (wmax) thr[k] = 0.25f * wmax[i];
         }
         I.xh[k] = q0.x; I.yh[k] = q0.y; I.zh[k] = q0.z;
         I.xm[k] = q1.x; I.ym[k] = q1.y; I.zm[k] = q1.z; I.ahx[k] = q1.w;
@@ -435,12 +458,8 @@ __global__ void __launch_bounds__(BS) k_grad_mixed(const float4 *__restrict__ ir
         I.ahz[k] = q3.x; I.alx[k] = q3.y; I.aly[k] = q3.z; I.alz[k] = q3.w;
     }
     float hx[ILP], hy[ILP], hz[ILP], lx[ILP], ly[ILP], lz[ILP];
-    double bx[ILP], by[ILP], bz[ILP];
 #pragma unroll
-    for (int k = 0; k < ILP; ++k) {
-        hx[k] = hy[k] = hz[k] = lx[k] = ly[k] = lz[k] = 0.f;
-        bx[k] = by[k] = bz[k] = 0.0;
-    }
+    for (int k = 0; k < ILP; ++k) hx[k] = hy[k] = hz[k] = lx[k] = ly[k] = lz[k] = 0.f;
 
     const int jb = blockIdx.y * j_per_split;
     const int je = min(n_s, jb + j_per_split);
@@ -466,15 +485,15 @@ __global__ void __launch_bounds__(BS) k_grad_mixed(const float4 *__restrict__ ir
 #pragma unroll
                     for (int u = 0; u < 4; ++u)
                         grad_mixed_j<ILP, false>(s0[jj + u], s1[jj + u], s2[jj + u], s3[jj + u], I, eps2,
-                                                 eps2d, 0, ipos, thr, gx, gy, gz, bx, by, bz);
+                                                 j0 + jj + u, 0, ipos, thr, big, gx, gy, gz);
                 }
                 for (; jj < c1; ++jj)
-                    grad_mixed_j<ILP, false>(s0[jj], s1[jj], s2[jj], s3[jj], I, eps2, eps2d, 0, ipos, thr,
-                                             gx, gy, gz, bx, by, bz);
+                    grad_mixed_j<ILP, false>(s0[jj], s1[jj], s2[jj], s3[jj], I, eps2, j0 + jj, 0, ipos, thr,
+                                             big, gx, gy, gz);
             } else {
                 for (; jj < c1; ++jj)
-                    grad_mixed_j<ILP, true>(s0[jj], s1[jj], s2[jj], s3[jj], I, eps2, eps2d, j0 + jj, ipos,
-                                            thr, gx, gy, gz, bx, by, bz);
+                    grad_mixed_j<ILP, true>(s0[jj], s1[jj], s2[jj], s3[jj], I, eps2, j0 + jj, j0 + jj, ipos,
+                                            thr, big, gx, gy, gz);
             }
 #pragma unroll
             for (int k = 0; k < ILP; ++k) {
@@ -484,14 +503,24 @@ __global__ void __launch_bounds__(BS) k_grad_mixed(const float4 *__restrict__ ir
             }
         }
     }
+    // deferred FP64 terms, records read back from global memory (L2)
 #pragma unroll
     for (int k = 0; k < ILP; ++k) {
+        double bx = 0.0, by = 0.0, bz = 0.0;
+#pragma unroll
+        for (int s = 0; s < GRAD_SLOTS; ++s) {
+            if (s < big.n[k]) {
+                const int j = (s == 0) ? big.j0[k] : (s == 1) ? big.j1[k] : (s == 2) ? big.j2[k] : big.j3[k];
+                grad_term_fp64<ILP>(jrec[j], jrec[n_s + j], jrec[2 * n_s + j], jrec[3 * n_s + j], I, k,
+                                    eps2d, bx, by, bz);
+            }
+        }
         const int i = ipos[k];
         if (i < n_a) {
             double *p = part + (size_t)blockIdx.y * 3 * n_a;
-            p[i] = ((double)hx[k] + (double)lx[k]) + bx[k];
-            p[n_a + i] = ((double)hy[k] + (double)ly[k]) + by[k];
-            p[2 * n_a + i] = ((double)hz[k] + (double)lz[k]) + bz[k];
+            p[i] = ((double)hx[k] + (double)lx[k]) + bx;
+            p[n_a + i] = ((double)hy[k] + (double)ly[k]) + by;
+            p[2 * n_a + i] = ((double)hz[k] + (double)lz[k]) + bz;
         }
     }
 }

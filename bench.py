@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--subtree-max", type=int, default=0,
+                   help="largest set whose hhs_fsi subtree runs in one block (0 = library default)")
     return p.parse_args()
 
 
@@ -212,7 +214,8 @@ def run_frost(args):
     E0_ref = None
 
     def new(prec):
-        return fr.Frost(m, x, v, G=1.0, eta=args.eta, precision=prec, stream=stream.cuda_stream)
+        return fr.Frost(m, x, v, G=1.0, eta=args.eta, precision=prec, stream=stream.cuda_stream,
+                        subtree_max=args.subtree_max)
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB
 
@@ -271,7 +274,7 @@ def run_frost(args):
 
     # roofline of the dominant pair kernel (largest share of kernel time)
     kinds = ["acc", "grad", "tstep"]
-    kms = st["timed_ms"]
+    kms = st["timed_ms"][:3]
     dom = int(np.argmax(kms))
     kname = kinds[dom]
     achieved_tf = st["timed_pairs"][dom] * FLOPS_PER_PAIR[kname] / (kms[dom] * 1e-3) / 1e12
@@ -384,7 +387,8 @@ def run_frost(args):
                            "separations, FP64 state and sums)",
                            "step": "one top-level HHS-FSI step; E/P/L once per timed region",
                            "l2": "flushed before every timed step (256 MiB write)",
-                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "subtree_max": args.subtree_max or "library default"},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
                         "h2d_bytes_per_step": int(2 * n * 3 * 8),
@@ -392,7 +396,8 @@ def run_frost(args):
                 "gpu_launches": int(launches), "clocks": clk,
                 "wall_s_timed_region": wall, "energy_ms": ms_energy,
                 "dE_over_E_timed_run": dE_timed, "max_depth": st["max_depth_seen"],
-                "hhs_calls": st["hhs_calls"], **extra}
+                "hhs_calls": st["hhs_calls"], "subtree_launches": st["subtree_launches"],
+                "subtree_ms": st["timed_ms"][3], **extra}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -65,10 +65,13 @@ typedef struct {
     double eps_soft;    /* Plummer softening length eps_P (Sec. 2.3); 0 = unsoftened */
     int32_t max_depth;  /* deepest hhs_fsi level allowed (top level = 0); <= 0 means 40 */
     void *cuda_stream;  /* cudaStream_t for all work; NULL = the legacy default stream */
+    int32_t subtree_max;/* hhs_fsi calls on sets of at most this many particles run their whole
+                           subtree in one thread block (one launch, no host synchronisation);
+                           0 = default (384), negative = never */
 } frost_opts;
 
 /* Default options: mixed precision, harmonic symmetrisation, no softening, depth 40,
- * legacy default stream. */
+ * legacy default stream, subtree threshold 384. */
 void frost_default_opts(frost_opts *opt);
 
 /*
@@ -173,10 +176,12 @@ typedef struct {
     int32_t max_depth_seen; /* deepest hhs_fsi level reached */
     int32_t timing_enabled; /* 1 if per-kernel CUDA-event timing is on */
     /* per-kernel-kind CUDA-event totals (only when timing is enabled):
-     * index 0 = Newtonian pass, 1 = gradient pass, 2 = time-step pass */
-    int64_t timed_launches[3];
-    double timed_ms[3];
-    int64_t timed_pairs[3];
+     * index 0 = Newtonian pass, 1 = gradient pass, 2 = time-step pass, 3 = single-block
+     * subtree launches (all passes of a small set; their pairs are in the totals above) */
+    int64_t timed_launches[4];
+    double timed_ms[4];
+    int64_t timed_pairs[4];
+    int64_t subtree_launches;  /* hhs_fsi calls handed to the single-block subtree solver */
 } frost_stats;
 
 frost_status frost_get_stats(frost_ctx *ctx, frost_stats *out);

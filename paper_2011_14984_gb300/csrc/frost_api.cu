@@ -53,6 +53,7 @@ struct Misc {
     int64_t counts[2];  // partition |S|, |F|
     int64_t rel[2];     // list relation: bad/duplicate flag, |A cap B|
     double eres[8];     // energy reduction
+    unsigned long long sub[6];  // subtree solver counters (acc, grad, tstep pairs, hhs, fsi, depth)
     int err;            // sticky device error word
     int pad;
 };
@@ -87,6 +88,9 @@ struct frost_ctx {
     double *tau = nullptr;                           // [N]
     float *wA = nullptr, *wB = nullptr;              // max_j m_j / r^3 per particle (mixed)
     float *wpart = nullptr;                          // its split partials
+    int32_t *perm = nullptr, *ptmp = nullptr;        // subtree solver permutation / scratch
+    int subtree_max = 384;                           // sets up to this size run in one block
+    unsigned long long sub_seen[6] = {0, 0, 0, 0, 0, 0};
     Misc *dmisc = nullptr, *hmisc = nullptr;
     std::vector<int32_t *> lvS, lvF;                 // per-level slow/fast lists
 
@@ -170,6 +174,7 @@ void resolve_timing(frost_ctx *c)
 
 frost_status err_to_status(int e)
 {
+    if (e & ERR_DEPTH) return fail(FROST_EDEPTH, "hhs_fsi recursion deeper than max_depth");
     if (e & ERR_COINCIDENT) return fail(FROST_ECOINCIDENT, "two distinct particles at zero separation");
     if (e & ERR_NONFINITE) return fail(FROST_ENONFINITE, "non-finite value in a pass (or a non-positive mass / step)");
     if (e & (ERR_INDEX | ERR_DUPLICATE)) return fail(FROST_EINVAL, "index list out of range or repeated");
@@ -183,6 +188,15 @@ frost_status sync_misc(frost_ctx *c)
     FROST_CUDA(cudaMemcpyAsync(c->hmisc, c->dmisc, sizeof(Misc), cudaMemcpyDeviceToHost, c->stream));
     FROST_CUDA(cudaStreamSynchronize(c->stream));
     if (c->timing) resolve_timing(c);
+    // fold the subtree solver's device counters into the statistics
+    const unsigned long long *sub = c->hmisc->sub;
+    c->st.acc_pairs += (int64_t)(sub[0] - c->sub_seen[0]);
+    c->st.grad_pairs += (int64_t)(sub[1] - c->sub_seen[1]);
+    c->st.tstep_pairs += (int64_t)(sub[2] - c->sub_seen[2]);
+    c->st.hhs_calls += (int64_t)(sub[3] - c->sub_seen[3]);
+    c->st.fsi_calls += (int64_t)(sub[4] - c->sub_seen[4]);
+    if ((int)sub[5] > c->st.max_depth_seen) c->st.max_depth_seen = (int)sub[5];
+    for (int k = 0; k < 6; ++k) c->sub_seen[k] = sub[k];
     return err_to_status(c->hmisc->err);
 }
 
@@ -384,6 +398,44 @@ frost_status ensure_level(frost_ctx *c, int depth)
     return FROST_OK;
 }
 
+// the whole subtree of hhs_fsi(P, tau) in one thread block (single launch, no sync)
+void hhs_subtree(frost_ctx *c, const int32_t *P, int nP, double tau, int depth)
+{
+    SubtreeArgs a;
+    a.x = c->x;
+    a.v = c->v;
+    a.m = c->m;
+    a.N = c->N;
+    a.G = c->G;
+    a.eta = c->eta;
+    a.eps2 = c->eps2;
+    a.max_depth = c->max_depth;
+    a.err = &c->dmisc->err;
+    a.counters = c->dmisc->sub;
+    a.perm = c->perm;
+    a.tmp = c->ptmp;
+    a.tau = c->tau;
+    a.aA = c->aA;
+    a.aB = c->aB;
+    a.atA = c->atA;
+    a.atB = c->atB;
+    a.wA = c->wA;
+    a.wB = c->wB;
+    a.recA = c->recA;
+    a.recB = c->recB;
+    a.P = P;
+    a.n = nP;
+    a.tau0 = tau;
+    a.depth0 = depth;
+    a.n_steps = 1;
+    {
+        TimedScope ts(c, PASS_SUBTREE, 0);
+        launch_subtree(c->stream, c->mixed, c->sym, a);
+    }
+    c->st.kernel_launches += 1;
+    c->st.subtree_launches += 1;
+}
+
 // Algorithm hhs-fsi on the set P (device list, nP entries) with pivot step tau
 frost_status hhs_fsi(frost_ctx *c, const int32_t *P, int nP, double tau, int depth)
 {
@@ -391,6 +443,10 @@ frost_status hhs_fsi(frost_ctx *c, const int32_t *P, int nP, double tau, int dep
     if (depth > c->max_depth)
         return fail(FROST_EDEPTH, "hhs_fsi deeper than max_depth=%d (|P|=%d, tau_pivot=%g)",
                     c->max_depth, nP, tau);
+    if (nP <= c->subtree_max && c->max_depth < SUBTREE_MAX_FRAMES) {
+        hhs_subtree(c, P, nP, tau, depth);
+        return FROST_OK;
+    }
     c->st.hhs_calls += 1;
     if (depth > c->st.max_depth_seen) c->st.max_depth_seen = depth;
     FROST_TRY(ensure_level(c, depth));
@@ -439,7 +495,8 @@ void destroy(frost_ctx *c)
     for (auto p : c->lvS) cudaFree(p);
     for (auto p : c->lvF) cudaFree(p);
     void *dev[] = {c->x, c->v, c->m, c->all, c->marks, c->recA, c->recB, c->part,
-                   c->aA, c->aB, c->atA, c->atB, c->tau, c->wA, c->wB, c->wpart, c->dmisc};
+                   c->aA, c->aB, c->atA, c->atB, c->tau, c->wA, c->wB, c->wpart, c->perm,
+                   c->ptmp, c->dmisc};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (c->hmisc) cudaFreeHost(c->hmisc);
@@ -462,6 +519,7 @@ void frost_default_opts(frost_opts *opt)
     opt->eps_soft = 0.0;
     opt->max_depth = 40;
     opt->cuda_stream = nullptr;
+    opt->subtree_max = 0;
 }
 
 const char *frost_last_error(void) { return g_last_error.c_str(); }
@@ -495,6 +553,7 @@ frost_status frost_init(frost_ctx **out, int64_t n, const double *m, const doubl
     c->mixed = (o.precision == FROST_PREC_MIXED);
     c->sym = o.sym;
     c->max_depth = o.max_depth > 0 ? o.max_depth : 40;
+    c->subtree_max = o.subtree_max == 0 ? 384 : (o.subtree_max < 0 ? 0 : o.subtree_max);
 
     auto bail = [&](frost_status st) {
         destroy(c);
@@ -533,6 +592,8 @@ frost_status frost_init(frost_ctx **out, int64_t n, const double *m, const doubl
     INIT_CUDA(cudaMalloc(&c->wA, sizeof(float) * N));
     INIT_CUDA(cudaMalloc(&c->wB, sizeof(float) * N));
     INIT_CUDA(cudaMalloc(&c->wpart, sizeof(float) * (c->part_elems / 3)));
+    INIT_CUDA(cudaMalloc(&c->perm, sizeof(int32_t) * N));
+    INIT_CUDA(cudaMalloc(&c->ptmp, sizeof(int32_t) * N));
     INIT_CUDA(cudaMalloc(&c->dmisc, sizeof(Misc)));
     INIT_CUDA(cudaMallocHost(&c->hmisc, sizeof(Misc)));
     INIT_CUDA(cudaMemsetAsync(c->dmisc, 0, sizeof(Misc), c->stream));

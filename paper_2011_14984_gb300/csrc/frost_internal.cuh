@@ -33,10 +33,11 @@ enum : int {
     ERR_INDEX = 1 << 2,
     ERR_TIMEOUT = 1 << 3,
     ERR_DUPLICATE = 1 << 4,
+    ERR_DEPTH = 1 << 5,
 };
 
-// kinds of timed pair kernels
-enum PassKind { PASS_ACC = 0, PASS_GRAD = 1, PASS_TSTEP = 2 };
+// kinds of timed kernels (the subtree solver runs all passes of a small set)
+enum PassKind { PASS_ACC = 0, PASS_GRAD = 1, PASS_TSTEP = 2, PASS_SUBTREE = 3 };
 
 // Tile geometry of the pair kernels.
 constexpr int PAIR_BS = 128;   // threads per block
@@ -130,6 +131,34 @@ void launch_potential(cudaStream_t s, const double4_32a *rec, int n, double eps2
 // out[0] = T, out[1] = sum_i m_i phi_i, out[2..4] = P, out[5..7] = L (one block, fixed order)
 void launch_energy_reduce(cudaStream_t s, const double *x, const double *v, const double *m,
                           int N, const double *part, int nsplit, double *out);
+
+// ---- single-CTA subtree solver (subtree.cu) ------------------------------------------
+constexpr int SUBTREE_MAX_FRAMES = 64;  // recursion frames per block (max_depth < 64)
+
+struct SubtreeArgs {
+    double *x, *v;
+    const double *m;
+    int N;
+    double G, eta, eps2;
+    int max_depth;
+    int *err;
+    unsigned long long *counters;  // [6]: acc, grad, tstep pairs, hhs calls, fsi calls, max depth
+    // workspace (per particle: perm, tmp int32; tau double; aA..atB [3] doubles; wA, wB
+    // float; recA, recB 64 bytes), indexed from the block's first particle
+    int32_t *perm, *tmp;
+    double *tau, *aA, *aB, *atA, *atB;
+    float *wA, *wB;
+    void *recA, *recB;
+    // single-set mode: list P of n particles; batch mode: offsets[n_blocks + 1]
+    const int32_t *P = nullptr;
+    int n = 0;
+    const int64_t *offsets = nullptr;
+    int n_blocks = 0;
+    double tau0;
+    int depth0;
+    int n_steps;
+};
+void launch_subtree(cudaStream_t s, bool mixed, int sym, const SubtreeArgs &a);
 
 SplitShape choose_shape(int n_a, int n_s, int i_per_block, int blocks_per_sm, int n_sm);
 int pair_blocks_per_sm(int kind, bool mixed);

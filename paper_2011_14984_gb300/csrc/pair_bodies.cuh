@@ -1,0 +1,847 @@
+// Device code shared by the grid pair kernels (pair_kernels.cu) and the single-CTA
+// subtree solver (subtree.cu): record builders, pair bodies and per-i-block loops of the
+//   Newtonian pass     a_i = G sum_j m_j x_ji / r_ji^3                        (Eq. acc-newton)
+//   gradient pass      g_i = 2G sum_j m_j r^-5 (r^2 a_ji - 3 (x_ji . a_ji) x_ji) (Eq. acc-gradient-g)
+//   time-step pass     tau_i = eta min_j min(t_ff s(d_ff), t_fb s(d_fb))       (Sec. 4)
+// in mixed precision (FP32 bodies on float-float separations, compensated sums) and FP64.
+// The record layouts are described in frost_internal.cuh.
+#pragma once
+
+#include "frost_internal.cuh"
+
+#include <cfloat>
+#include <cmath>
+
+namespace frost {
+namespace dev {
+
+__device__ __forceinline__ void fold2(float &hi, float &lo, float p)
+{
+    // TwoSum (Knuth): hi + p = s + e exactly
+    const float s = hi + p;
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) + (p - bb);
+    hi = s;
+    lo += e;
+}
+
+__device__ __forceinline__ float trunc12(float f)
+{
+    // keep sign, exponent and the 11 leading fraction bits (12 significant bits)
+    return __uint_as_float(__float_as_uint(f) & 0xFFFFF800u);
+}
+
+__device__ __forceinline__ void split3(double p, float &h, float &mi, float &l)
+{
+    double r = p;
+    h = trunc12((float)r);
+    r -= (double)h;   // exact
+    mi = trunc12((float)r);
+    r -= (double)mi;  // exact
+    l = (float)r;
+}
+
+
+// ======================================================================================
+// Per-particle record builders (one list entry k); used by the pack kernels and by the
+// subtree solver's block-wide packs.
+// ======================================================================================
+__device__ __forceinline__ void pack_pos_mixed_one(int k, const int32_t *__restrict__ list, int n,
+                                                   const double *__restrict__ x,
+                                                   const double *__restrict__ m, int N,
+                                                   float4 *__restrict__ rec)
+{
+    const int i = list ? list[k] : k;
+    const double px = x[i], py = x[N + i], pz = x[2 * N + i];
+    const float hx = (float)px, hy = (float)py, hz = (float)pz;
+    rec[k] = make_float4(hx, hy, hz, (float)m[i]);
+    rec[n + k] = make_float4((float)(px - (double)hx), (float)(py - (double)hy),
+                             (float)(pz - (double)hz), 0.f);
+}
+
+// acc may be NULL (positions only, for the Newtonian pass that precedes the gradient)
+__device__ __forceinline__ void pack_grad_mixed_one(int k, const int32_t *__restrict__ list, int n,
+                                                    const double *__restrict__ x,
+                                                    const double *__restrict__ m, int N,
+                                                    const double *__restrict__ acc,
+                                                    float4 *__restrict__ rec)
+{
+    const int i = list ? list[k] : k;
+    float hx, hy, hz, mx, my, mz, lx, ly, lz;
+    split3(x[i], hx, mx, lx);
+    split3(x[N + i], hy, my, ly);
+    split3(x[2 * N + i], hz, mz, lz);
+    const double ax = acc ? acc[k] : 0.0, ay = acc ? acc[n + k] : 0.0, az = acc ? acc[2 * n + k] : 0.0;
+    const float ahx = trunc12((float)ax), ahy = trunc12((float)ay), ahz = trunc12((float)az);
+    rec[k] = make_float4(hx, hy, hz, (float)m[i]);
+    rec[n + k] = make_float4(mx, my, mz, ahx);
+    rec[2 * n + k] = make_float4(lx, ly, lz, ahy);
+    rec[3 * n + k] = make_float4(ahz, (float)(ax - (double)ahx), (float)(ay - (double)ahy),
+                                 (float)(az - (double)ahz));
+}
+
+__device__ __forceinline__ void pack_tstep_mixed_one(int k, const int32_t *__restrict__ list, int n,
+                                                     const double *__restrict__ x,
+                                                     const double *__restrict__ v,
+                                                     const double *__restrict__ m, int N, double G,
+                                                     float4 *__restrict__ rec)
+{
+    const int i = list ? list[k] : k;
+    const double px = x[i], py = x[N + i], pz = x[2 * N + i];
+    const float hx = (float)px, hy = (float)py, hz = (float)pz;
+    rec[k] = make_float4(hx, hy, hz, (float)m[i]);
+    rec[n + k] = make_float4((float)(px - (double)hx), (float)(py - (double)hy),
+                             (float)(pz - (double)hz), 0.f);
+    rec[2 * n + k] = make_float4((float)v[i], (float)v[N + i], (float)v[2 * N + i],
+                                 (float)(G * m[i]));
+}
+
+__device__ __forceinline__ void pack_pos_fp64_one(int k, const int32_t *__restrict__ list, int n,
+                                                  const double *__restrict__ x,
+                                                  const double *__restrict__ m, int N,
+                                                  double4_32a *__restrict__ rec)
+{
+    const int i = list ? list[k] : k;
+    rec[k] = make_double4_32a(x[i], x[N + i], x[2 * N + i], m[i]);
+}
+
+__device__ __forceinline__ void pack_grad_fp64_one(int k, const int32_t *__restrict__ list, int n,
+                                                   const double *__restrict__ x,
+                                                   const double *__restrict__ m, int N,
+                                                   const double *__restrict__ acc,
+                                                   double4_32a *__restrict__ rec)
+{
+    const int i = list ? list[k] : k;
+    rec[k] = make_double4_32a(x[i], x[N + i], x[2 * N + i], m[i]);
+    rec[n + k] = make_double4_32a(acc[k], acc[n + k], acc[2 * n + k], 0.0);
+}
+
+__device__ __forceinline__ void pack_tstep_fp64_one(int k, const int32_t *__restrict__ list, int n,
+                                                    const double *__restrict__ x,
+                                                    const double *__restrict__ v,
+                                                    const double *__restrict__ m, int N, double G,
+                                                    double4_32a *__restrict__ rec)
+{
+    const int i = list ? list[k] : k;
+    rec[k] = make_double4_32a(x[i], x[N + i], x[2 * N + i], m[i]);
+    rec[n + k] = make_double4_32a(v[i], v[N + i], v[2 * N + i], G * m[i]);
+}
+template <int ILP>
+struct AccMixedI {
+    float xh[ILP], yh[ILP], zh[ILP], xl[ILP], yl[ILP], zl[ILP];
+};
+
+template <int ILP, bool MASK, bool WMAX>
+__device__ __forceinline__ void acc_mixed_j(const float4 J0, const float4 J1, const AccMixedI<ILP> &I,
+                                            float eps2, int jpos, const int (&ipos)[ILP],
+                                            float (&ax)[ILP], float (&ay)[ILP], float (&az)[ILP],
+                                            float (&wm)[ILP])
+{
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+        const float dx = (J0.x - I.xh[k]) + (J1.x - I.xl[k]);
+        const float dy = (J0.y - I.yh[k]) + (J1.y - I.yl[k]);
+        const float dz = (J0.z - I.zh[k]) + (J1.z - I.zl[k]);
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+        const float ri = rsqrtf(r2);
+        const float ri2 = ri * ri;
+        float w = J0.w * ri * ri2;
+        if (MASK) w = (jpos == ipos[k]) ? 0.f : w;
+        if (WMAX) wm[k] = fmaxf(wm[k], w);
+        ax[k] = fmaf(w, dx, ax[k]);
+        ay[k] = fmaf(w, dy, ay[k]);
+        az[k] = fmaf(w, dz, az[k]);
+    }
+}
+
+template <bool MASK>
+__device__ __forceinline__ void acc_fp64_j(const double4_32a J, const double4_32a I, double eps2, int jpos,
+                                           int ipos, double &ax, double &ay, double &az)
+{
+    const double dx = J.x - I.x, dy = J.y - I.y, dz = J.z - I.z;
+    const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+    const double ri = rsqrt(r2);
+    double w = J.w * ri * ri * ri;
+    if (MASK) w = (jpos == ipos) ? 0.0 : w;
+    ax = fma(w, dx, ax);
+    ay = fma(w, dy, ay);
+    az = fma(w, dz, az);
+}
+
+template <int ILP>
+struct GradMixedI {
+    float xh[ILP], yh[ILP], zh[ILP], xm[ILP], ym[ILP], zm[ILP], xl[ILP], yl[ILP], zl[ILP];
+    float ahx[ILP], ahy[ILP], ahz[ILP], alx[ILP], aly[ILP], alz[ILP];
+};
+
+// One pair term in FP64, rebuilt exactly from the split records (positions to 48 bits,
+// accelerations to 36 bits); used for the few dominant terms of each particle.
+template <int ILP>
+__device__ __noinline__ void grad_term_fp64(const float4 J0, const float4 J1, const float4 J2,
+                                            const float4 J3, const GradMixedI<ILP> &I, int k,
+                                            double eps2, double &gx, double &gy, double &gz)
+{
+    const double dx = (((double)J0.x + (double)J1.x) + (double)J2.x) -
+                      (((double)I.xh[k] + (double)I.xm[k]) + (double)I.xl[k]);
+    const double dy = (((double)J0.y + (double)J1.y) + (double)J2.y) -
+                      (((double)I.yh[k] + (double)I.ym[k]) + (double)I.yl[k]);
+    const double dz = (((double)J0.z + (double)J1.z) + (double)J2.z) -
+                      (((double)I.zh[k] + (double)I.zm[k]) + (double)I.zl[k]);
+    const double Ax = ((double)J1.w + (double)J3.y) - ((double)I.ahx[k] + (double)I.alx[k]);
+    const double Ay = ((double)J2.w + (double)J3.z) - ((double)I.ahy[k] + (double)I.aly[k]);
+    const double Az = ((double)J3.x + (double)J3.w) - ((double)I.ahz[k] + (double)I.alz[k]);
+    const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+    const double ri = rsqrt(r2);
+    const double ri2 = ri * ri;
+    const double w = (double)J0.w * ri * ri2;
+    const double xa = fma(dx, Ax, fma(dy, Ay, dz * Az));
+    const double t3 = 3.0 * xa * ri2;
+    gx = fma(w, fma(-t3, dx, Ax), gx);
+    gy = fma(w, fma(-t3, dy, Ay), gy);
+    gz = fma(w, fma(-t3, dz, Az), gz);
+}
+
+// Dominant terms: up to GRAD_SLOTS per particle are recorded during the j-loop and summed
+// in FP64 after it (deferred, so the FP64 work is not issued once per lane and source).
+constexpr int GRAD_SLOTS = 4;
+
+template <int ILP>
+struct BigSlots {
+    int n[ILP];
+    int j0[ILP], j1[ILP], j2[ILP], j3[ILP];
+};
+
+template <int ILP>
+__device__ __forceinline__ void push_big(BigSlots<ILP> &b, int k, int j)
+{
+    const int c = b.n[k];
+    if (c == 0) b.j0[k] = j;
+    else if (c == 1) b.j1[k] = j;
+    else if (c == 2) b.j2[k] = j;
+    else b.j3[k] = j;
+    b.n[k] = c + 1;
+}
+
+template <int ILP, bool MASK>
+__device__ __forceinline__ void grad_mixed_j(const float4 J0, const float4 J1, const float4 J2,
+                                             const float4 J3, const GradMixedI<ILP> &I,
+                                             float eps2, int jglob, int jpos,
+                                             const int (&ipos)[ILP], const float (&thr)[ILP],
+                                             BigSlots<ILP> &big, float (&gx)[ILP],
+                                             float (&gy)[ILP], float (&gz)[ILP])
+{
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+        // separation: the high and middle parts subtract exactly, one rounding at the end
+        const float dx = ((J0.x - I.xh[k]) + (J1.x - I.xm[k])) + (J2.x - I.xl[k]);
+        const float dy = ((J0.y - I.yh[k]) + (J1.y - I.ym[k])) + (J2.y - I.yl[k]);
+        const float dz = ((J0.z - I.zh[k]) + (J1.z - I.zm[k])) + (J2.z - I.zl[k]);
+        // a_ji = a_j - a_i from the 12-bit split (exact high-part difference)
+        const float Ax = (J1.w - I.ahx[k]) + (J3.y - I.alx[k]);
+        const float Ay = (J2.w - I.ahy[k]) + (J3.z - I.aly[k]);
+        const float Az = (J3.x - I.ahz[k]) + (J3.w - I.alz[k]);
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+        float y = rsqrtf(r2);
+        // one Newton-Raphson step for 1/sqrt(r2): y <- y (3/2 - r2 y^2 / 2)
+        const float hy = (0.5f * r2) * y;
+        y = fmaf(y, fmaf(-hy, y, 0.5f), y);
+        const float ri2 = y * y;
+        float w = J0.w * y * ri2;  // m_j r^-3
+        bool self = false;
+        if (MASK) {
+            self = (jpos == ipos[k]);
+            w = self ? 0.f : w;
+        }
+        // a dominant term goes to a deferred FP64 slot and stays out of the FP32 sum
+        const bool isbig = (w > thr[k]) && (big.n[k] < GRAD_SLOTS);
+        if (isbig) push_big(big, k, jglob);
+        const float wf = isbig ? 0.f : w;
+        const float xa = fmaf(dx, Ax, fmaf(dy, Ay, dz * Az));
+        const float t3 = 3.0f * xa * ri2;  // 3 (x.a) / r^2
+        const float nx = fmaf(wf, fmaf(-t3, dx, Ax), gx[k]);
+        const float ny = fmaf(wf, fmaf(-t3, dy, Ay), gy[k]);
+        const float nz = fmaf(wf, fmaf(-t3, dz, Az), gz[k]);
+        if (MASK) {
+            gx[k] = self ? gx[k] : nx;
+            gy[k] = self ? gy[k] : ny;
+            gz[k] = self ? gz[k] : nz;
+        } else {
+            gx[k] = nx;
+            gy[k] = ny;
+            gz[k] = nz;
+        }
+    }
+}
+
+template <int ILP, bool MASK>
+__device__ __forceinline__ void acc3_mixed_j(const float4 J0, const float4 J1, const float4 J2,
+                                             const GradMixedI<ILP> &I, float eps2, int jpos,
+                                             const int (&ipos)[ILP], float (&ax)[ILP],
+                                             float (&ay)[ILP], float (&az)[ILP], float (&wm)[ILP])
+{
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+        const float dx = ((J0.x - I.xh[k]) + (J1.x - I.xm[k])) + (J2.x - I.xl[k]);
+        const float dy = ((J0.y - I.yh[k]) + (J1.y - I.ym[k])) + (J2.y - I.yl[k]);
+        const float dz = ((J0.z - I.zh[k]) + (J1.z - I.zm[k])) + (J2.z - I.zl[k]);
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+        float y = rsqrtf(r2);
+        const float hy = (0.5f * r2) * y;
+        y = fmaf(y, fmaf(-hy, y, 0.5f), y);
+        float w = J0.w * y * (y * y);
+        if (MASK) w = (jpos == ipos[k]) ? 0.f : w;
+        wm[k] = fmaxf(wm[k], w);
+        ax[k] = fmaf(w, dx, ax[k]);
+        ay[k] = fmaf(w, dy, ay[k]);
+        az[k] = fmaf(w, dz, az[k]);
+    }
+}
+
+template <bool MASK>
+__device__ __forceinline__ void grad_fp64_j(const double4_32a J, const double4_32a JA, const double4_32a I,
+                                            const double4_32a IA, double eps2, int jpos, int ipos,
+                                            double &gx, double &gy, double &gz)
+{
+    const double dx = J.x - I.x, dy = J.y - I.y, dz = J.z - I.z;
+    const double Ax = JA.x - IA.x, Ay = JA.y - IA.y, Az = JA.z - IA.z;
+    const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+    const double ri = rsqrt(r2);
+    const double ri2 = ri * ri;
+    const double w = J.w * ri * ri2;
+    const double xa = fma(dx, Ax, fma(dy, Ay, dz * Az));
+    const double t3 = 3.0 * xa * ri2;
+    const double nx = fma(w, fma(-t3, dx, Ax), gx);
+    const double ny = fma(w, fma(-t3, dy, Ay), gy);
+    const double nz = fma(w, fma(-t3, dz, Az), gz);
+    if (MASK && jpos == ipos) return;
+    gx = nx;
+    gy = ny;
+    gz = nz;
+}
+
+// symmetrisation factor s(d) = tau_sym / tau (Eq. time-step-factor)
+template <int SYM>
+__device__ __forceinline__ float symf(float d)
+{
+    if (SYM == 0) {
+        // harmonic: with q = 1 + sqrt(1 + d^2) the printed factor equals (q + d) / q and
+        // 2 / (q - d); each form is used where it has no cancellation
+        const float q = 1.f + sqrtf(fmaf(d, d, 1.f));
+        const float num = (d >= 0.f) ? q + d : 2.f;
+        const float den = (d >= 0.f) ? q : q - d;
+        return __fdividef(num, den);
+    } else if (SYM == 1) {
+        // arithmetic: 1 / (1 - d/2) for d < 2; beyond, the step is lowered by 1/d first
+        return (d < 2.f) ? __fdividef(1.f, fmaf(-0.5f, d, 1.f)) : __fdividef(2.f, d);
+    } else {
+        return 1.f;
+    }
+}
+
+template <int SYM>
+__device__ __forceinline__ double symd(double d)
+{
+    if (SYM == 0) {
+        const double q = 1.0 + sqrt(fma(d, d, 1.0));
+        return (d >= 0.0) ? (q + d) / q : 2.0 / (q - d);
+    } else if (SYM == 1) {
+        return (d < 2.0) ? 1.0 / (1.0 - 0.5 * d) : 2.0 / d;
+    } else {
+        return 1.0;
+    }
+}
+
+template <int ILP>
+struct TstepMixedI {
+    float xh[ILP], yh[ILP], zh[ILP], xl[ILP], yl[ILP], zl[ILP], vx[ILP], vy[ILP], vz[ILP], gm[ILP];
+};
+
+// returns min(tau_ff_sym, tau_fb_sym) / eta for the pair, updates min r^2
+template <int ILP, int SYM, bool MASK>
+__device__ __forceinline__ void tstep_mixed_j(const float4 J0, const float4 J1, const float4 JV,
+                                              const TstepMixedI<ILP> &I, float eta, float eta15,
+                                              int jpos, const int (&ipos)[ILP],
+                                              float (&best)[ILP], float (&minr2)[ILP])
+{
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+        const float dx = (J0.x - I.xh[k]) + (J1.x - I.xl[k]);
+        const float dy = (J0.y - I.yh[k]) + (J1.y - I.yl[k]);
+        const float dz = (J0.z - I.zh[k]) + (J1.z - I.zl[k]);
+        const float ux = JV.x - I.vx[k], uy = JV.y - I.vy[k], uz = JV.z - I.vz[k];
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float v2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+        const float rv = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
+        const float ri = rsqrtf(r2);
+        const float ri2 = ri * ri;
+        const float gm = I.gm[k] + JV.w;            // G (m_i + m_j)
+        const float tff = rsqrtf(gm * ri2 * ri);     // (r^3 / (G M))^(1/2)
+        const float rvr2 = rv * ri2;                 // r.v / r^2
+        const float iv = rsqrtf(v2);                 // 1 / |v|
+        const float tfb = r2 * ri * iv;              // r / |v|
+        const float dff = eta15 * rvr2 * tff;        // eta dt_ff/dt
+        const float dfb = eta * rvr2 * fmaf(gm * ri, iv * iv, 1.f) * tfb;  // eta dt_fb/dt
+        const float tau_ff = tff * symf<SYM>(dff);
+        float tau_fb = tfb * symf<SYM>(dfb);
+        tau_fb = (v2 > 0.f) ? tau_fb : INFINITY;
+        float t = fminf(tau_ff, tau_fb);
+        float rr = r2;
+        if (MASK) {
+            const bool self = (jpos == ipos[k]);
+            t = self ? INFINITY : t;
+            rr = self ? INFINITY : rr;
+        }
+        best[k] = fminf(best[k], t);
+        minr2[k] = fminf(minr2[k], rr);
+    }
+}
+
+template <int SYM, bool MASK>
+__device__ __forceinline__ void tstep_fp64_j(const double4_32a J, const double4_32a JV, const double4_32a I,
+                                             const double4_32a IV, double eta, int jpos, int ipos,
+                                             double &best, double &minr2)
+{
+    const double dx = J.x - I.x, dy = J.y - I.y, dz = J.z - I.z;
+    const double ux = JV.x - IV.x, uy = JV.y - IV.y, uz = JV.z - IV.z;
+    const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+    const double v2 = fma(ux, ux, fma(uy, uy, uz * uz));
+    const double rv = fma(dx, ux, fma(dy, uy, dz * uz));
+    const double r = sqrt(r2);
+    const double gm = IV.w + JV.w;
+    const double tff = sqrt(r2 * r / gm);
+    const double rvr2 = rv / r2;
+    const double dff = eta * 1.5 * rvr2 * tff;
+    double t = tff * symd<SYM>(dff);
+    if (v2 > 0.0) {
+        const double tfb = r / sqrt(v2);
+        const double dfb = eta * rvr2 * (1.0 + gm / (v2 * r)) * tfb;
+        t = fmin(t, tfb * symd<SYM>(dfb));
+    }
+    if (MASK && jpos == ipos) return;
+    best = fmin(best, t);
+    minr2 = fmin(minr2, r2);
+}
+
+
+// ======================================================================================
+// Per-i-block bodies.  Each processes the active records [ibase, ibase + BS*ILP) against the
+// source records [jb, je), staging the sources through shared memory in tiles of TJ, and
+// leaves per-thread results in registers.  Every thread of the block must call a body (it
+// synchronises the block); thread t owns the active particles ibase + k*BS + t, k < ILP.
+// The grid kernels call a body once per (i-block, j-split) block; the single-CTA subtree
+// solver calls it for every i-block of a set against the whole source list.
+// ======================================================================================
+
+// Newtonian pass, mixed precision (float-float separations, MUFU rsqrt, folds every 64)
+template <int BS, int ILP, int TJ, bool WMAX>
+__device__ __forceinline__ void acc_mixed_body(const float4 *__restrict__ irec,
+                                               const float4 *__restrict__ jrec, int n_a, int n_s,
+                                               int ibase, int jb, int je, int self_pass, float eps2,
+                                               double (&res)[ILP][3], float (&wres)[ILP])
+{
+    __shared__ float4 s0[TJ];
+    __shared__ float4 s1[TJ];
+    const int tid = threadIdx.x;
+    AccMixedI<ILP> I;
+    int ipos[ILP];
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+        const int i = ibase + k * BS + tid;
+        ipos[k] = i;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+        if (i < n_a) {
+            a = irec[i];
+            b = irec[n_a + i];
+        }
+        I.xh[k] = a.x; I.yh[k] = a.y; I.zh[k] = a.z;
+        I.xl[k] = b.x; I.yl[k] = b.y; I.zl[k] = b.z;
+    }
+    float hx[ILP], hy[ILP], hz[ILP], lx[ILP], ly[ILP], lz[ILP], wm[ILP];
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) hx[k] = hy[k] = hz[k] = lx[k] = ly[k] = lz[k] = wm[k] = 0.f;
+
+    for (int j0 = jb; j0 < je; j0 += TJ) {
+        const int cnt = min(TJ, je - j0);
+        __syncthreads();
+        for (int t = tid; t < cnt; t += BS) {
+            s0[t] = jrec[j0 + t];
+            s1[t] = jrec[n_s + j0 + t];
+        }
+        __syncthreads();
+        const bool diag = self_pass && (j0 < ibase + BS * ILP) && (ibase < j0 + cnt);
+        // FP32 partial sums over at most 64 pairs before each compensated fold
+        for (int c0 = 0; c0 < cnt; c0 += 64) {
+            const int c1 = min(cnt, c0 + 64);
+            float ax[ILP], ay[ILP], az[ILP];
+#pragma unroll
+            for (int k = 0; k < ILP; ++k) ax[k] = ay[k] = az[k] = 0.f;
+            int jj = c0;
+            if (!diag) {
+                for (; jj + 8 <= c1; jj += 8) {
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        acc_mixed_j<ILP, false, WMAX>(s0[jj + u], s1[jj + u], I, eps2, 0, ipos, ax, ay, az, wm);
+                }
+                for (; jj < c1; ++jj)
+                    acc_mixed_j<ILP, false, WMAX>(s0[jj], s1[jj], I, eps2, 0, ipos, ax, ay, az, wm);
+            } else {
+                for (; jj < c1; ++jj)
+                    acc_mixed_j<ILP, true, WMAX>(s0[jj], s1[jj], I, eps2, j0 + jj, ipos, ax, ay, az, wm);
+            }
+#pragma unroll
+            for (int k = 0; k < ILP; ++k) {
+                fold2(hx[k], lx[k], ax[k]);
+                fold2(hy[k], ly[k], ay[k]);
+                fold2(hz[k], lz[k], az[k]);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+        res[k][0] = (double)hx[k] + (double)lx[k];
+        res[k][1] = (double)hy[k] + (double)ly[k];
+        res[k][2] = (double)hz[k] + (double)lz[k];
+        wres[k] = wm[k];
+    }
+}
+
+// Newtonian pass feeding a gradient pass: three-way split separations, Newton-refined
+// rsqrt, folds every 16 pairs, max_j m_j / r^3 recorded (reads the gradient records q0..q2)
+template <int BS, int ILP, int TJ>
+__device__ __forceinline__ void acc3_mixed_body(const float4 *__restrict__ irec,
+                                                const float4 *__restrict__ jrec, int n_a, int n_s,
+                                                int ibase, int jb, int je, int self_pass, float eps2,
+                                                double (&res)[ILP][3], float (&wres)[ILP])
+{
+    __shared__ float4 s0[TJ], s1[TJ], s2[TJ];
+    const int tid = threadIdx.x;
+    GradMixedI<ILP> I;
+    int ipos[ILP];
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+        const int i = ibase + k * BS + tid;
+        ipos[k] = i;
+        float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0, q2 = q0;
+        if (i < n_a) {
+            q0 = irec[i];
+            q1 = irec[n_a + i];
+            q2 = irec[2 * n_a + i];
+        }
+        I.xh[k] = q0.x; I.yh[k] = q0.y; I.zh[k] = q0.z;
+        I.xm[k] = q1.x; I.ym[k] = q1.y; I.zm[k] = q1.z;
+        I.xl[k] = q2.x; I.yl[k] = q2.y; I.zl[k] = q2.z;
+        I.ahx[k] = I.ahy[k] = I.ahz[k] = I.alx[k] = I.aly[k] = I.alz[k] = 0.f;
+    }
+    float hx[ILP], hy[ILP], hz[ILP], lx[ILP], ly[ILP], lz[ILP], wm[ILP];
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) hx[k] = hy[k] = hz[k] = lx[k] = ly[k] = lz[k] = wm[k] = 0.f;
+
+    for (int j0 = jb; j0 < je; j0 += TJ) {
+        const int cnt = min(TJ, je - j0);
+        __syncthreads();
+        for (int t = tid; t < cnt; t += BS) {
+            s0[t] = jrec[j0 + t];
+            s1[t] = jrec[n_s + j0 + t];
+            s2[t] = jrec[2 * n_s + j0 + t];
+        }
+        __syncthreads();
+        const bool diag = self_pass && (j0 < ibase + BS * ILP) && (ibase < j0 + cnt);
+        for (int c0 = 0; c0 < cnt; c0 += 16) {
+            const int c1 = min(cnt, c0 + 16);
+            float ax[ILP], ay[ILP], az[ILP];
+#pragma unroll
+            for (int k = 0; k < ILP; ++k) ax[k] = ay[k] = az[k] = 0.f;
+            int jj = c0;
+            if (!diag) {
+                for (; jj + 8 <= c1; jj += 8) {
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        acc3_mixed_j<ILP, false>(s0[jj + u], s1[jj + u], s2[jj + u], I, eps2, 0, ipos, ax, ay,
+                                                 az, wm);
+                }
+                for (; jj < c1; ++jj)
+                    acc3_mixed_j<ILP, false>(s0[jj], s1[jj], s2[jj], I, eps2, 0, ipos, ax, ay, az, wm);
+            } else {
+                for (; jj < c1; ++jj)
+                    acc3_mixed_j<ILP, true>(s0[jj], s1[jj], s2[jj], I, eps2, j0 + jj, ipos, ax, ay, az, wm);
+            }
+#pragma unroll
+            for (int k = 0; k < ILP; ++k) {
+                fold2(hx[k], lx[k], ax[k]);
+                fold2(hy[k], ly[k], ay[k]);
+                fold2(hz[k], lz[k], az[k]);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+        res[k][0] = (double)hx[k] + (double)lx[k];
+        res[k][1] = (double)hy[k] + (double)ly[k];
+        res[k][2] = (double)hz[k] + (double)lz[k];
+        wres[k] = wm[k];
+    }
+}
+
+// Gradient pass, mixed precision.  wmax: per active particle, max_j m_j / r^3 from the
+// Newtonian pass at the same positions (NULL: no FP64 terms); up to GRAD_SLOTS terms
+// heavier than wmax / 4 are recorded during the loop and summed in FP64 after it.
+template <int BS, int ILP, int TJ>
+__device__ __forceinline__ void grad_mixed_body(const float4 *__restrict__ irec,
+                                                const float4 *__restrict__ jrec, int n_a, int n_s,
+                                                int ibase, int jb, int je, int self_pass, double eps2d,
+                                                const float *__restrict__ wmax, double (&res)[ILP][3])
+{
+    __shared__ float4 s0[TJ], s1[TJ], s2[TJ], s3[TJ];
+    const int tid = threadIdx.x;
+    const float eps2 = (float)eps2d;
+    GradMixedI<ILP> I;
+    int ipos[ILP];
+    float thr[ILP];
+    BigSlots<ILP> big;
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+        const int i = ibase + k * BS + tid;
+        ipos[k] = i;
+        big.n[k] = 0;
+        big.j0[k] = big.j1[k] = big.j2[k] = big.j3[k] = 0;
+        float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0, q2 = q0, q3 = q0;
+        thr[k] = INFINITY;
+        if (i < n_a) {
+            q0 = irec[i];
+            q1 = irec[n_a + i];
+            q2 = irec[2 * n_a + i];
+            q3 = irec[3 * n_a + i];
+            if (wmax) thr[k] = 0.25f * wmax[i];
+        }
+        I.xh[k] = q0.x; I.yh[k] = q0.y; I.zh[k] = q0.z;
+        I.xm[k] = q1.x; I.ym[k] = q1.y; I.zm[k] = q1.z; I.ahx[k] = q1.w;
+        I.xl[k] = q2.x; I.yl[k] = q2.y; I.zl[k] = q2.z; I.ahy[k] = q2.w;
+        I.ahz[k] = q3.x; I.alx[k] = q3.y; I.aly[k] = q3.z; I.alz[k] = q3.w;
+    }
+    float hx[ILP], hy[ILP], hz[ILP], lx[ILP], ly[ILP], lz[ILP];
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) hx[k] = hy[k] = hz[k] = lx[k] = ly[k] = lz[k] = 0.f;
+
+    for (int j0 = jb; j0 < je; j0 += TJ) {
+        const int cnt = min(TJ, je - j0);
+        __syncthreads();
+        for (int t = tid; t < cnt; t += BS) {
+            s0[t] = jrec[j0 + t];
+            s1[t] = jrec[n_s + j0 + t];
+            s2[t] = jrec[2 * n_s + j0 + t];
+            s3[t] = jrec[3 * n_s + j0 + t];
+        }
+        __syncthreads();
+        const bool diag = self_pass && (j0 < ibase + BS * ILP) && (ibase < j0 + cnt);
+        for (int c0 = 0; c0 < cnt; c0 += 64) {
+            const int c1 = min(cnt, c0 + 64);
+            float gx[ILP], gy[ILP], gz[ILP];
+#pragma unroll
+            for (int k = 0; k < ILP; ++k) gx[k] = gy[k] = gz[k] = 0.f;
+            int jj = c0;
+            if (!diag) {
+                for (; jj + 4 <= c1; jj += 4) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        grad_mixed_j<ILP, false>(s0[jj + u], s1[jj + u], s2[jj + u], s3[jj + u], I, eps2,
+                                                 j0 + jj + u, 0, ipos, thr, big, gx, gy, gz);
+                }
+                for (; jj < c1; ++jj)
+                    grad_mixed_j<ILP, false>(s0[jj], s1[jj], s2[jj], s3[jj], I, eps2, j0 + jj, 0, ipos, thr,
+                                             big, gx, gy, gz);
+            } else {
+                for (; jj < c1; ++jj)
+                    grad_mixed_j<ILP, true>(s0[jj], s1[jj], s2[jj], s3[jj], I, eps2, j0 + jj, j0 + jj, ipos,
+                                            thr, big, gx, gy, gz);
+            }
+#pragma unroll
+            for (int k = 0; k < ILP; ++k) {
+                fold2(hx[k], lx[k], gx[k]);
+                fold2(hy[k], ly[k], gy[k]);
+                fold2(hz[k], lz[k], gz[k]);
+            }
+        }
+    }
+    // deferred FP64 terms, records read back from global memory (L2)
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+        double bx = 0.0, by = 0.0, bz = 0.0;
+#pragma unroll
+        for (int s = 0; s < GRAD_SLOTS; ++s) {
+            if (s < big.n[k]) {
+                const int j = (s == 0) ? big.j0[k] : (s == 1) ? big.j1[k] : (s == 2) ? big.j2[k] : big.j3[k];
+                grad_term_fp64<ILP>(jrec[j], jrec[n_s + j], jrec[2 * n_s + j], jrec[3 * n_s + j], I, k,
+                                    eps2d, bx, by, bz);
+            }
+        }
+        res[k][0] = ((double)hx[k] + (double)lx[k]) + bx;
+        res[k][1] = ((double)hy[k] + (double)ly[k]) + by;
+        res[k][2] = ((double)hz[k] + (double)lz[k]) + bz;
+    }
+}
+
+// Time-step pass, mixed precision: best[k] = min_j min(t_ff s, t_fb s) (without eta),
+// minr2[k] = min_j r^2 over the other particles
+template <int BS, int ILP, int TJ, int SYM>
+__device__ __forceinline__ void tstep_mixed_body(const float4 *__restrict__ irec,
+                                                 const float4 *__restrict__ jrec, int n_a, int n_s,
+                                                 int ibase, int jb, int je, int self_pass, float eta,
+                                                 float (&best)[ILP], float (&minr2)[ILP])
+{
+    __shared__ float4 s0[TJ], s1[TJ], sv[TJ];
+    const int tid = threadIdx.x;
+    TstepMixedI<ILP> I;
+    int ipos[ILP];
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+        const int i = ibase + k * BS + tid;
+        ipos[k] = i;
+        float4 a = make_float4(0.f, 0.f, 0.f, 1.f), b = make_float4(0.f, 0.f, 0.f, 0.f), c = a;
+        if (i < n_a) {
+            a = irec[i];
+            b = irec[n_a + i];
+            c = irec[2 * n_a + i];
+        }
+        I.xh[k] = a.x; I.yh[k] = a.y; I.zh[k] = a.z;
+        I.xl[k] = b.x; I.yl[k] = b.y; I.zl[k] = b.z;
+        I.vx[k] = c.x; I.vy[k] = c.y; I.vz[k] = c.z; I.gm[k] = c.w;
+    }
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) best[k] = minr2[k] = INFINITY;
+    const float eta15 = 1.5f * eta;
+    for (int j0 = jb; j0 < je; j0 += TJ) {
+        const int cnt = min(TJ, je - j0);
+        __syncthreads();
+        for (int t = tid; t < cnt; t += BS) {
+            s0[t] = jrec[j0 + t];
+            s1[t] = jrec[n_s + j0 + t];
+            sv[t] = jrec[2 * n_s + j0 + t];
+        }
+        __syncthreads();
+        const bool diag = self_pass && (j0 < ibase + BS * ILP) && (ibase < j0 + cnt);
+        int jj = 0;
+        if (!diag) {
+            for (; jj + 4 <= cnt; jj += 4) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    tstep_mixed_j<ILP, SYM, false>(s0[jj + u], s1[jj + u], sv[jj + u], I, eta, eta15, 0,
+                                                   ipos, best, minr2);
+            }
+            for (; jj < cnt; ++jj)
+                tstep_mixed_j<ILP, SYM, false>(s0[jj], s1[jj], sv[jj], I, eta, eta15, 0, ipos, best, minr2);
+        } else {
+            for (; jj < cnt; ++jj)
+                tstep_mixed_j<ILP, SYM, true>(s0[jj], s1[jj], sv[jj], I, eta, eta15, j0 + jj, ipos, best,
+                                              minr2);
+        }
+    }
+}
+
+// Newtonian pass, FP64 (one active particle per thread)
+template <int BS, int TJ>
+__device__ __forceinline__ void acc_fp64_body(const double4_32a *__restrict__ irec,
+                                              const double4_32a *__restrict__ jrec, int n_a, int n_s,
+                                              int ibase, int jb, int je, int self_pass, double eps2,
+                                              double (&res)[3])
+{
+    __shared__ double4_32a s0[TJ];
+    const int tid = threadIdx.x;
+    const int i = ibase + tid;
+    const double4_32a I = (i < n_a) ? irec[i] : make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    for (int j0 = jb; j0 < je; j0 += TJ) {
+        const int cnt = min(TJ, je - j0);
+        __syncthreads();
+        for (int t = tid; t < cnt; t += BS) s0[t] = jrec[j0 + t];
+        __syncthreads();
+        const bool diag = self_pass && (j0 < ibase + BS) && (ibase < j0 + cnt);
+        int jj = 0;
+        if (!diag) {
+            for (; jj + 4 <= cnt; jj += 4) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc_fp64_j<false>(s0[jj + u], I, eps2, 0, i, ax, ay, az);
+            }
+            for (; jj < cnt; ++jj) acc_fp64_j<false>(s0[jj], I, eps2, 0, i, ax, ay, az);
+        } else {
+            for (; jj < cnt; ++jj) acc_fp64_j<true>(s0[jj], I, eps2, j0 + jj, i, ax, ay, az);
+        }
+    }
+    res[0] = ax;
+    res[1] = ay;
+    res[2] = az;
+}
+
+// Gradient pass, FP64
+template <int BS, int TJ>
+__device__ __forceinline__ void grad_fp64_body(const double4_32a *__restrict__ irec,
+                                               const double4_32a *__restrict__ jrec, int n_a, int n_s,
+                                               int ibase, int jb, int je, int self_pass, double eps2,
+                                               double (&res)[3])
+{
+    __shared__ double4_32a s0[TJ], s1[TJ];
+    const int tid = threadIdx.x;
+    const int i = ibase + tid;
+    double4_32a I = make_double4_32a(0.0, 0.0, 0.0, 0.0), IA = I;
+    if (i < n_a) {
+        I = irec[i];
+        IA = irec[n_a + i];
+    }
+    double gx = 0.0, gy = 0.0, gz = 0.0;
+    for (int j0 = jb; j0 < je; j0 += TJ) {
+        const int cnt = min(TJ, je - j0);
+        __syncthreads();
+        for (int t = tid; t < cnt; t += BS) {
+            s0[t] = jrec[j0 + t];
+            s1[t] = jrec[n_s + j0 + t];
+        }
+        __syncthreads();
+        const bool diag = self_pass && (j0 < ibase + BS) && (ibase < j0 + cnt);
+        if (!diag) {
+            for (int jj = 0; jj < cnt; ++jj) grad_fp64_j<false>(s0[jj], s1[jj], I, IA, eps2, 0, i, gx, gy, gz);
+        } else {
+            for (int jj = 0; jj < cnt; ++jj)
+                grad_fp64_j<true>(s0[jj], s1[jj], I, IA, eps2, j0 + jj, i, gx, gy, gz);
+        }
+    }
+    res[0] = gx;
+    res[1] = gy;
+    res[2] = gz;
+}
+
+// Time-step pass, FP64
+template <int BS, int TJ, int SYM>
+__device__ __forceinline__ void tstep_fp64_body(const double4_32a *__restrict__ irec,
+                                                const double4_32a *__restrict__ jrec, int n_a, int n_s,
+                                                int ibase, int jb, int je, int self_pass, double eta,
+                                                double &best, double &minr2)
+{
+    __shared__ double4_32a s0[TJ], sv[TJ];
+    const int tid = threadIdx.x;
+    const int i = ibase + tid;
+    double4_32a I = make_double4_32a(0.0, 0.0, 0.0, 1.0), IV = make_double4_32a(0.0, 0.0, 0.0, 1.0);
+    if (i < n_a) {
+        I = irec[i];
+        IV = irec[n_a + i];
+    }
+    best = INFINITY;
+    minr2 = INFINITY;
+    for (int j0 = jb; j0 < je; j0 += TJ) {
+        const int cnt = min(TJ, je - j0);
+        __syncthreads();
+        for (int t = tid; t < cnt; t += BS) {
+            s0[t] = jrec[j0 + t];
+            sv[t] = jrec[n_s + j0 + t];
+        }
+        __syncthreads();
+        const bool diag = self_pass && (j0 < ibase + BS) && (ibase < j0 + cnt);
+        if (!diag) {
+            for (int jj = 0; jj < cnt; ++jj) tstep_fp64_j<SYM, false>(s0[jj], sv[jj], I, IV, eta, 0, i, best, minr2);
+        } else {
+            for (int jj = 0; jj < cnt; ++jj)
+                tstep_fp64_j<SYM, true>(s0[jj], sv[jj], I, IV, eta, j0 + jj, i, best, minr2);
+        }
+    }
+}
+
+}  // namespace dev
+}  // namespace frost

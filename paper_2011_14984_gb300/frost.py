@@ -36,7 +36,7 @@ class FrostError(RuntimeError):
 class frost_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("sym", ctypes.c_int32),
                 ("eps_soft", ctypes.c_double), ("max_depth", ctypes.c_int32),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("cuda_stream", ctypes.c_void_p), ("subtree_max", ctypes.c_int32)]
 
 
 class frost_stats(ctypes.Structure):
@@ -44,8 +44,8 @@ class frost_stats(ctypes.Structure):
                 ("tstep_pairs", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("hhs_calls", ctypes.c_int64), ("fsi_calls", ctypes.c_int64),
                 ("max_depth_seen", ctypes.c_int32), ("timing_enabled", ctypes.c_int32),
-                ("timed_launches", ctypes.c_int64 * 3), ("timed_ms", ctypes.c_double * 3),
-                ("timed_pairs", ctypes.c_int64 * 3)]
+                ("timed_launches", ctypes.c_int64 * 4), ("timed_ms", ctypes.c_double * 4),
+                ("timed_pairs", ctypes.c_int64 * 4), ("subtree_launches", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -252,7 +252,7 @@ class Frost:
 
     def __init__(self, m, x, v, G: float = 1.0, eta: float = 0.2, precision: str = "mixed",
                  sym: int = FROST_SYM_HARMONIC, eps_soft: float = 0.0, max_depth: int = 40,
-                 stream=None):
+                 stream=None, subtree_max: int = 0):
         import torch
         self.torch = torch
         o = frost_default_opts()
@@ -261,6 +261,7 @@ class Frost:
         o.eps_soft = float(eps_soft)
         o.max_depth = int(max_depth)
         o.cuda_stream = stream if stream is not None else current_stream_handle()
+        o.subtree_max = int(subtree_max)
         self.n = int(np.asarray(m).shape[0]) if not hasattr(m, "shape") else int(m.shape[0])
         self.G = G
         self.eta = eta

@@ -354,3 +354,53 @@ def test_full_pass_64k_sampled(precision):
     Ftot = (m[:, None] * a).sum(0)
     assert np.all(np.abs(Ftot) < 1e-9 * (m[:, None] * np.abs(a)).sum())
     f.close()
+
+
+# ---------------------------------------------------------------------------------------
+# single-block subtree solver (hhs_fsi subtrees of small sets in one thread block)
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("subtree_max", [1 << 30, 100])
+def test_subtree_solver_trajectory_parity_fp64(subtree_max):
+    """Whole recursion in one block (1<<30) or only sets of <= 100 particles: the same
+    trajectory as the oracle (Plummer N = 700, 6 top-level steps of 2^-7, eta = 0.2)."""
+    m, x, v = ics.plummer(700, 31, masses=ics.kroupa_masses(700, 31))
+    f = F(m, x, v, precision="fp64", eta=0.2, subtree_max=subtree_max)
+    f.step(2.0 ** -7, 6)
+    xg, vg, _ = f.state()
+    st = f.stats()
+    oracle.reset_counters()
+    xo, vo = oracle.steps(m, x, v, 2.0 ** -7, 6, eta=0.2)
+    oc = oracle.counters()
+    assert st["subtree_launches"] > 0
+    assert np.max(np.abs(xg - xo)) < 1e-10 and np.max(np.abs(vg - vo)) < 1e-9
+    assert st["max_depth_seen"] == oc["max_depth"]
+    f.close()
+
+
+def test_subtree_solver_mixed_matches_grid_path():
+    """Mixed precision: the same steps with and without the single-block solver agree to
+    the mixed-precision level and reach the same energy error."""
+    m, x, v = ics.plummer(1024, 1)
+    E0 = oracle.energy(m, x, v)["E"]
+    out = {}
+    for sm in (-1, 1 << 30):
+        f = F(m, x, v, precision="mixed", eta=0.2, subtree_max=sm)
+        f.step(2.0 ** -7, 4)
+        xg, vg, _ = f.state()
+        out[sm] = (xg, abs((f.energy()["E"] - E0) / E0), f.stats())
+        f.close()
+    assert out[1 << 30][2]["subtree_launches"] == 4 and out[-1][2]["subtree_launches"] == 0
+    assert np.max(np.abs(out[-1][0] - out[1 << 30][0])) < 1e-7
+    dEa, dEb = out[-1][1], out[1 << 30][1]
+    assert max(dEa, dEb) < 2 * min(dEa, dEb) + 1e-12
+
+
+def test_subtree_solver_depth_limit():
+    from paper_2011_14984_gb300 import frost as fr
+    m, x, v = ics.kepler_binary(0.5, 0.5, 1e-3, 0.0)
+    f = F(m, x, v, max_depth=3, subtree_max=1 << 30)
+    with pytest.raises(fr.FrostError) as e:
+        f.step(1.0, 1)
+    assert e.value.code == fr.FROST_EDEPTH
+    f.close()

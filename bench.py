@@ -187,6 +187,20 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def aggregate_ranks(ms_total, work, world, device):
+    """Whole-job numbers over replicas: the slowest rank's time and the sum of the work.
+    Every rank must call this (collectives); with world == 1 the inputs come back as they are."""
+    if world <= 1:
+        return float(ms_total), float(work)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_total, work], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1])
+
+
 # ---------------------------------------------------------------------------------------
 # the CUDA path
 # ---------------------------------------------------------------------------------------
@@ -262,14 +276,7 @@ def run_frost(args):
     f.set_timing(False)
     interactions = float(st["acc_pairs"] + st["grad_pairs"])
     launches = st["kernel_launches"] - launches0 + 3  # + the energy pass kernels
-    ms_max = ms_total
-    if world > 1:
-        t = torch.tensor([ms_total, interactions], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        ms_max = float(tmax[0])
-        interactions = float(t[1])
+    ms_max, interactions = aggregate_ranks(ms_total, interactions, world, dev)
     value = interactions / (ms_max * 1e-3)
 
     # roofline of the dominant pair kernel (largest share of kernel time)
@@ -403,10 +410,99 @@ def run_frost(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """Batch of independent clusters (config: 256 Plummer clusters, N log-uniform 64..4096):
+    every timed step is one launch that advances all clusters by one top-level step."""
+    import torch
+
+    from paper_2011_14984_gb300 import build as fbuild
+    from paper_2011_14984_gb300 import frost as fr
+    from paper_2011_14984_gb300 import ics
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    fbuild.build()
+    fr.load()
+    stream = torch.cuda.current_stream()
+    off, m, x, v = ics.batch_workload(args.workload)
+    ncl = off.size - 1
+    f = fr.Frost(m, x, v, G=1.0, eta=args.eta, precision="mixed", stream=stream.cuda_stream,
+                 offsets=off)
+    e0 = f.cluster_energies()
+    for _ in range(args.warmup):
+        f.step(args.dt, 1)
+    f.reset_stats()
+    f.set_timing(True)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.synchronize()
+    clocks.start()
+    ms = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        f.step(args.dt, 1)
+        b.record(stream)
+        b.synchronize()
+        ms += a.elapsed_time(b)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    st = f.stats()
+    f.set_timing(False)
+    e1 = f.cluster_energies()
+    dE = np.abs((e1["E"] - e0["E"]) / e0["E"])
+    inter = float(st["acc_pairs"] + st["grad_pairs"])
+    value = inter / (ms * 1e-3)
+    flops = (st["acc_pairs"] * FLOPS_PER_PAIR["acc"] + st["grad_pairs"] * FLOPS_PER_PAIR["grad"]
+             + st["tstep_pairs"] * FLOPS_PER_PAIR["tstep"])
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    ach = flops / (st["timed_ms"][3] * 1e-3) / 1e12 if st["timed_ms"][3] > 0 else 0.0
+    # end to end with host buffers
+    n = m.size
+    xh = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+    vh = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+    tt = fr.frost_get_state(f.ctx, xh, vh)
+    f.reset_stats()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 4))
+    for _ in range(e2e_steps):
+        fr.frost_set_state(f.ctx, xh, vh, tt)
+        fr.frost_step(f.ctx, args.dt, 1)
+        tt = fr.frost_get_state(f.ctx, xh, vh)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    st2 = f.stats()
+    f.close()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "clusters": int(ncl), "N_total": int(n),
+                       "N_min": int(np.diff(off).min()), "N_max": int(np.diff(off).max()),
+                       "eta": args.eta, "dt_pivot": args.dt,
+                       "step": "one launch: every cluster in its own thread block advances one "
+                               "top-level HHS-FSI step",
+                       "l2": "flushed before every timed step (256 MiB write)"},
+            "roofline": {"bound": "alu", "kernel": "k_hhs_subtree (batch; all passes)", "achieved": ach,
+                         "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                         "flops_counted": "acc 20, grad 38, tstep 45 per pair"},
+            "cpu_baseline": None,
+            "e2e": {"value": (st2["acc_pairs"] + st2["grad_pairs"]) / e2e_s, "unit": UNIT,
+                    "steps": e2e_steps, "h2d_bytes_per_step": int(2 * n * 24),
+                    "d2h_bytes_per_step": int(2 * n * 24)},
+            "gpu_launches": args.steps, "clocks": clk,
+            "dE_over_E_clusters": {"median": float(np.median(dE)), "max": float(dE.max())},
+            "max_depth": st["max_depth_seen"], "hhs_calls": st["hhs_calls"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload.startswith("cluster_batch"):
+        run_batch(args)
     else:
         run_frost(args)
 

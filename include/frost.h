@@ -85,6 +85,25 @@ void frost_default_opts(frost_opts *opt);
 frost_status frost_init(frost_ctx **ctx, int64_t n, const double *m, const double *x,
                         const double *v, double G, double eta, const frost_opts *opt);
 
+/*
+ * Create a context holding n_clusters independent clusters (no force between clusters):
+ * cluster k is the particles [offsets[k], offsets[k+1]) of m, x, v (host or device; copied;
+ * offsets is a host array of n_clusters + 1 entries with offsets[0] = 0, increasing).  On
+ * such a context frost_step advances every cluster by n_steps top-level HHS-FSI steps in
+ * one launch (one thread block per cluster, Algorithm hhs-fsi inside the block), and
+ * frost_energy_clusters reports per-cluster E, P, L; frost_energy_momentum reports the sum of
+ * the per-cluster values.  The remaining calls see the particles as one set.
+ */
+frost_status frost_init_batch(frost_ctx **ctx, int32_t n_clusters, const int64_t *offsets,
+                              const double *m, const double *x, const double *v, double G,
+                              double eta, const frost_opts *opt);
+
+/* Per-cluster kinetic and potential energy, momentum and angular momentum of a batch
+ * context (host outputs: E_kin[n_clusters], E_pot[n_clusters], P[n_clusters][3],
+ * L[n_clusters][3]; any may be NULL), FP64.  FROST_EINVAL on a single-set context. */
+frost_status frost_energy_clusters(frost_ctx *ctx, double *E_kin, double *E_pot, double *P,
+                                   double *L);
+
 /* Replace positions x[n][3] and velocities v[n][3] (host or device; either may be NULL to
  * keep the current values) and set the simulation time to t. */
 frost_status frost_set_state(frost_ctx *ctx, const double *x, const double *v, double t);

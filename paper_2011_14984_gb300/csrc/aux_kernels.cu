@@ -203,6 +203,50 @@ __global__ void __launch_bounds__(BS) k_potential(const double4_32a *__restrict_
     if (i < n) part[(size_t)blockIdx.y * n + i] = phi;
 }
 
+// Per-cluster FP64 energy, momentum and angular momentum: block b reduces cluster
+// [offsets[b], offsets[b+1]) in a fixed order.  out[b][8] = {T, sum_{i<j} m_i m_j / r, P, L}.
+__global__ void __launch_bounds__(256) k_cluster_energy(const int64_t *__restrict__ offsets,
+                                                        const double *__restrict__ x,
+                                                        const double *__restrict__ v,
+                                                        const double *__restrict__ m, int N,
+                                                        double eps2, double *__restrict__ out)
+{
+    __shared__ double red[8][8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lo = (int)offsets[blockIdx.x], hi = (int)offsets[blockIdx.x + 1];
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = lo + tid; i < hi; i += 256) {
+        const double mi = m[i];
+        const double px = x[i], py = x[N + i], pz = x[2 * N + i];
+        const double ux = v[i], uy = v[N + i], uz = v[2 * N + i];
+        double phi = 0.0;
+        for (int j = i + 1; j < hi; ++j) {
+            const double dx = x[j] - px, dy = x[N + j] - py, dz = x[2 * N + j] - pz;
+            phi += m[j] * rsqrt(fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2))));
+        }
+        acc[0] += 0.5 * mi * (ux * ux + uy * uy + uz * uz);
+        acc[1] += mi * phi;
+        acc[2] += mi * ux;
+        acc[3] += mi * uy;
+        acc[4] += mi * uz;
+        acc[5] += mi * (py * uz - pz * uy);
+        acc[6] += mi * (pz * ux - px * uz);
+        acc[7] += mi * (px * uy - py * ux);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        double a = acc[q];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) red[q][warp] = a;
+    }
+    __syncthreads();
+    if (tid < 8) {
+        double a = 0.0;
+        for (int w = 0; w < 8; ++w) a += red[tid][w];
+        out[(size_t)blockIdx.x * 8 + tid] = a;
+    }
+}
+
 // Single-block FP64 reduction in a fixed order (deterministic).
 __global__ void __launch_bounds__(1024) k_energy_reduce(const double *__restrict__ x,
                                                         const double *__restrict__ v,
@@ -321,6 +365,13 @@ void launch_check_mass(cudaStream_t s, const double *m, int n, int *err)
 {
     if (n <= 0) return;
     k_check_mass<<<cdiv(n, 256), 256, 0, s>>>(m, n, err);
+}
+
+void launch_cluster_energy(cudaStream_t s, const int64_t *offsets, int n_clusters, const double *x,
+                           const double *v, const double *m, int N, double eps2, double *out)
+{
+    if (n_clusters <= 0) return;
+    k_cluster_energy<<<n_clusters, 256, 0, s>>>(offsets, x, v, m, N, eps2, out);
 }
 
 void launch_energy_reduce(cudaStream_t s, const double *x, const double *v, const double *m, int N,

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <climits>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -90,6 +91,10 @@ struct frost_ctx {
     float *wpart = nullptr;                          // its split partials
     int32_t *perm = nullptr, *ptmp = nullptr;        // subtree solver permutation / scratch
     int subtree_max = 384;                           // sets up to this size run in one block
+    int n_clusters = 0;                              // > 0: batch of independent clusters
+    int64_t *d_offsets = nullptr;                    // cluster offsets [n_clusters + 1] (device)
+    double *d_ecl = nullptr;                         // per-cluster energy sums [n_clusters][8]
+    std::vector<double> h_ecl;
     unsigned long long sub_seen[6] = {0, 0, 0, 0, 0, 0};
     Misc *dmisc = nullptr, *hmisc = nullptr;
     std::vector<int32_t *> lvS, lvF;                 // per-level slow/fast lists
@@ -494,6 +499,8 @@ void destroy(frost_ctx *c)
     for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
     for (auto p : c->lvS) cudaFree(p);
     for (auto p : c->lvF) cudaFree(p);
+    if (c->d_offsets) cudaFree(c->d_offsets);
+    if (c->d_ecl) cudaFree(c->d_ecl);
     void *dev[] = {c->x, c->v, c->m, c->all, c->marks, c->recA, c->recB, c->part,
                    c->aA, c->aB, c->atA, c->atB, c->tau, c->wA, c->wB, c->wpart, c->perm,
                    c->ptmp, c->dmisc};
@@ -526,8 +533,33 @@ const char *frost_last_error(void) { return g_last_error.c_str(); }
 
 const char *frost_version(void) { return "frost-gb300 0.1 (sm_103a)"; }
 
+static frost_status init_impl(frost_ctx **out, int64_t n, const double *m, const double *x,
+                              const double *v, double G, double eta, const frost_opts *opt,
+                              int32_t n_clusters, const int64_t *offsets);
+
 frost_status frost_init(frost_ctx **out, int64_t n, const double *m, const double *x, const double *v,
                         double G, double eta, const frost_opts *opt)
+{
+    return init_impl(out, n, m, x, v, G, eta, opt, 0, nullptr);
+}
+
+frost_status frost_init_batch(frost_ctx **out, int32_t n_clusters, const int64_t *offsets,
+                              const double *m, const double *x, const double *v, double G, double eta,
+                              const frost_opts *opt)
+{
+    g_last_error.clear();
+    if (!out) return fail(FROST_EINVAL, "ctx pointer is NULL");
+    *out = nullptr;
+    if (n_clusters < 1 || !offsets) return fail(FROST_EINVAL, "need n_clusters >= 1 and offsets");
+    if (offsets[0] != 0) return fail(FROST_EINVAL, "offsets[0] must be 0");
+    for (int k = 0; k < n_clusters; ++k)
+        if (offsets[k + 1] <= offsets[k]) return fail(FROST_EINVAL, "offsets must increase (cluster %d empty)", k);
+    return init_impl(out, offsets[n_clusters], m, x, v, G, eta, opt, n_clusters, offsets);
+}
+
+static frost_status init_impl(frost_ctx **out, int64_t n, const double *m, const double *x,
+                              const double *v, double G, double eta, const frost_opts *opt,
+                              int32_t n_clusters, const int64_t *offsets)
 {
     g_last_error.clear();
     if (!out) return fail(FROST_EINVAL, "ctx pointer is NULL");
@@ -594,6 +626,13 @@ frost_status frost_init(frost_ctx **out, int64_t n, const double *m, const doubl
     INIT_CUDA(cudaMalloc(&c->wpart, sizeof(float) * (c->part_elems / 3)));
     INIT_CUDA(cudaMalloc(&c->perm, sizeof(int32_t) * N));
     INIT_CUDA(cudaMalloc(&c->ptmp, sizeof(int32_t) * N));
+    if (n_clusters > 0) {
+        c->n_clusters = n_clusters;
+        INIT_CUDA(cudaMalloc(&c->d_offsets, sizeof(int64_t) * (n_clusters + 1)));
+        INIT_CUDA(cudaMemcpy(c->d_offsets, offsets, sizeof(int64_t) * (n_clusters + 1), cudaMemcpyHostToDevice));
+        INIT_CUDA(cudaMalloc(&c->d_ecl, sizeof(double) * 8 * n_clusters));
+        c->h_ecl.resize(8 * (size_t)n_clusters);
+    }
     INIT_CUDA(cudaMalloc(&c->dmisc, sizeof(Misc)));
     INIT_CUDA(cudaMallocHost(&c->hmisc, sizeof(Misc)));
     INIT_CUDA(cudaMemsetAsync(c->dmisc, 0, sizeof(Misc), c->stream));
@@ -752,6 +791,49 @@ frost_status frost_step(frost_ctx *c, double dt_pivot, int64_t n_steps)
     if (!c) return fail(FROST_EINVAL, "NULL context");
     if (!(dt_pivot > 0.0) || !std::isfinite(dt_pivot)) return fail(FROST_EINVAL, "dt_pivot must be > 0");
     if (n_steps < 0) return fail(FROST_EINVAL, "n_steps < 0");
+    if (c->n_clusters > 0) {
+        // every cluster in its own thread block, all steps in one launch
+        if (c->max_depth >= SUBTREE_MAX_FRAMES)
+            return fail(FROST_EINVAL, "batch contexts need max_depth < %d", SUBTREE_MAX_FRAMES);
+        if (n_steps == 0) return FROST_OK;
+        if (n_steps > INT32_MAX) return fail(FROST_EINVAL, "n_steps too large");
+        SubtreeArgs a;
+        a.x = c->x;
+        a.v = c->v;
+        a.m = c->m;
+        a.N = c->N;
+        a.G = c->G;
+        a.eta = c->eta;
+        a.eps2 = c->eps2;
+        a.max_depth = c->max_depth;
+        a.err = &c->dmisc->err;
+        a.counters = c->dmisc->sub;
+        a.perm = c->perm;
+        a.tmp = c->ptmp;
+        a.tau = c->tau;
+        a.aA = c->aA;
+        a.aB = c->aB;
+        a.atA = c->atA;
+        a.atB = c->atB;
+        a.wA = c->wA;
+        a.wB = c->wB;
+        a.recA = c->recA;
+        a.recB = c->recB;
+        a.offsets = c->d_offsets;
+        a.n_blocks = c->n_clusters;
+        a.tau0 = dt_pivot;
+        a.depth0 = 0;
+        a.n_steps = (int)n_steps;
+        {
+            TimedScope ts(c, PASS_SUBTREE, 0);
+            launch_subtree(c->stream, c->mixed, c->sym, a);
+        }
+        c->st.kernel_launches += 1;
+        c->st.subtree_launches += c->n_clusters;
+        c->t += dt_pivot * (double)n_steps;
+        FROST_CUDA(cudaGetLastError());
+        return sync_misc(c);
+    }
     for (int64_t k = 0; k < n_steps; ++k) {
         FROST_TRY(hhs_fsi(c, c->all, c->N, dt_pivot, 0));
         c->t += dt_pivot;
@@ -760,9 +842,57 @@ frost_status frost_step(frost_ctx *c, double dt_pivot, int64_t n_steps)
     return sync_misc(c);
 }
 
+// per-cluster sums into c->h_ecl
+static frost_status cluster_energies(frost_ctx *c)
+{
+    launch_cluster_energy(c->stream, c->d_offsets, c->n_clusters, c->x, c->v, c->m, c->N, c->eps2, c->d_ecl);
+    c->st.kernel_launches += 1;
+    FROST_CUDA(cudaGetLastError());
+    FROST_CUDA(cudaMemcpyAsync(c->h_ecl.data(), c->d_ecl, sizeof(double) * 8 * c->n_clusters,
+                               cudaMemcpyDeviceToHost, c->stream));
+    return sync_misc(c);
+}
+
+frost_status frost_energy_clusters(frost_ctx *c, double *E_kin, double *E_pot, double *P, double *L)
+{
+    if (!c) return fail(FROST_EINVAL, "NULL context");
+    if (c->n_clusters <= 0) return fail(FROST_EINVAL, "not a batch context");
+    FROST_TRY(cluster_energies(c));
+    for (int k = 0; k < c->n_clusters; ++k) {
+        const double *e = &c->h_ecl[8 * (size_t)k];
+        if (E_kin) E_kin[k] = e[0];
+        if (E_pot) E_pot[k] = -c->G * e[1];
+        for (int q = 0; q < 3; ++q) {
+            if (P) P[3 * k + q] = e[2 + q];
+            if (L) L[3 * k + q] = e[5 + q];
+        }
+    }
+    return FROST_OK;
+}
+
 frost_status frost_energy_momentum(frost_ctx *c, double *E_kin, double *E_pot, double P[3], double L[3])
 {
     if (!c) return fail(FROST_EINVAL, "NULL context");
+    if (c->n_clusters > 0) {
+        FROST_TRY(cluster_energies(c));
+        double T = 0.0, W = 0.0, Ps[3] = {0, 0, 0}, Ls[3] = {0, 0, 0};
+        for (int k = 0; k < c->n_clusters; ++k) {
+            const double *e = &c->h_ecl[8 * (size_t)k];
+            T += e[0];
+            W += e[1];
+            for (int q = 0; q < 3; ++q) {
+                Ps[q] += e[2 + q];
+                Ls[q] += e[5 + q];
+            }
+        }
+        if (E_kin) *E_kin = T;
+        if (E_pot) *E_pot = -c->G * W;
+        for (int q = 0; q < 3; ++q) {
+            if (P) P[q] = Ps[q];
+            if (L) L[q] = Ls[q];
+        }
+        return FROST_OK;
+    }
     launch_pack_pos_fp64(c->stream, nullptr, c->N, c->x, c->m, c->N, (double4_32a *)c->recA);
     SplitShape sh = choose_shape(c->N, c->N, PAIR_BS, pair_blocks_per_sm(PASS_ACC, false), c->n_sm);
     while ((size_t)sh.nsplit * c->N > c->part_elems && sh.nsplit > 1) {

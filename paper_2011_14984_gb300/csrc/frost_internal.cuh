@@ -131,6 +131,9 @@ void launch_potential(cudaStream_t s, const double4_32a *rec, int n, double eps2
 // out[0] = T, out[1] = sum_i m_i phi_i, out[2..4] = P, out[5..7] = L (one block, fixed order)
 void launch_energy_reduce(cudaStream_t s, const double *x, const double *v, const double *m,
                           int N, const double *part, int nsplit, double *out);
+// per-cluster {T, sum_{i<j} m_i m_j / r, P, L} into out[n_clusters][8] (one block per cluster)
+void launch_cluster_energy(cudaStream_t s, const int64_t *offsets, int n_clusters, const double *x,
+                           const double *v, const double *m, int N, double eps2, double *out);
 
 // ---- single-CTA subtree solver (subtree.cu) ------------------------------------------
 constexpr int SUBTREE_MAX_FRAMES = 64;  // recursion frames per block (max_depth < 64)

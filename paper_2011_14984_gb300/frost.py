@@ -84,6 +84,9 @@ _SIGS = {
     "frost_last_error": (ctypes.c_char_p, []),
     "frost_version": (ctypes.c_char_p, []),
     "frost_accel_noalloc": (ctypes.c_int, [_I64, _P, _P, _D, _D, _P, _P]),
+    "frost_init_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, _P, _P, _P, _P, _D, _D,
+                                        ctypes.POINTER(frost_opts)]),
+    "frost_energy_clusters": (ctypes.c_int, [_P, _P, _P, _P, _P]),
 }
 
 
@@ -143,6 +146,27 @@ def frost_init(m, x, v, G: float, eta: float, opts: frost_opts | None = None) ->
     _check(load().frost_init(ctypes.byref(ctx), n, _ptr(m), _ptr(x), _ptr(v), float(G), float(eta),
                              ctypes.byref(opts) if opts is not None else None), "frost_init")
     return ctx
+
+
+def frost_init_batch(offsets, m, x, v, G: float, eta: float,
+                     opts: frost_opts | None = None) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    _check(load().frost_init_batch(ctypes.byref(ctx), int(off.size - 1), _ptr(off), _ptr(m), _ptr(x),
+                                   _ptr(v), float(G), float(eta),
+                                   ctypes.byref(opts) if opts is not None else None),
+           "frost_init_batch")
+    return ctx
+
+
+def frost_energy_clusters(ctx, n_clusters: int) -> dict:
+    T = np.zeros(n_clusters)
+    U = np.zeros(n_clusters)
+    P = np.zeros((n_clusters, 3))
+    L = np.zeros((n_clusters, 3))
+    _check(load().frost_energy_clusters(ctx, _ptr(T), _ptr(U), _ptr(P), _ptr(L)),
+           "frost_energy_clusters")
+    return {"T": T, "U": U, "E": T + U, "P": P, "L": L}
 
 
 def frost_set_state(ctx, x, v, t: float) -> None:
@@ -252,7 +276,7 @@ class Frost:
 
     def __init__(self, m, x, v, G: float = 1.0, eta: float = 0.2, precision: str = "mixed",
                  sym: int = FROST_SYM_HARMONIC, eps_soft: float = 0.0, max_depth: int = 40,
-                 stream=None, subtree_max: int = 0):
+                 stream=None, subtree_max: int = 0, offsets=None):
         import torch
         self.torch = torch
         o = frost_default_opts()
@@ -269,7 +293,12 @@ class Frost:
         mm = _as_f64(m)
         xx = _as_f64(x).reshape(-1, 3)
         vv = _as_f64(v).reshape(-1, 3)
-        self.ctx = frost_init(mm, xx, vv, G, eta, o)
+        self.offsets = None
+        if offsets is not None:
+            self.offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+            self.ctx = frost_init_batch(self.offsets, mm, xx, vv, G, eta, o)
+        else:
+            self.ctx = frost_init(mm, xx, vv, G, eta, o)
 
     def close(self):
         if getattr(self, "ctx", None) is not None:
@@ -357,6 +386,9 @@ class Frost:
     def energy(self):
         ek, ep, P, L = frost_energy_momentum(self.ctx)
         return {"T": ek, "U": ep, "E": ek + ep, "P": P, "L": L}
+
+    def cluster_energies(self):
+        return frost_energy_clusters(self.ctx, self.offsets.size - 1)
 
     def stats(self):
         return frost_get_stats(self.ctx)

@@ -242,3 +242,10 @@ def workload(name: str):
     if name == "plummer_1m":
         return plummer(1048576, 5)
     raise KeyError(name)
+
+
+def batch_workload(name: str):
+    """(offsets, m, x, v) of a named batch of independent clusters."""
+    if name == "cluster_batch_256":
+        return cluster_batch(256, 1000)
+    raise KeyError(name)

@@ -77,6 +77,7 @@ def _load():
             lib.or_sym_arithmetic.argtypes = [d]
             lib.or_sym_arithmetic.restype = d
             lib.or_timesteps.argtypes = [P, P, P, P, i64, d, d, ci, P]
+            lib.or_timesteps_of.argtypes = [P, P, P, P, i64, P, i64, d, d, ci, P]
             lib.or_partition.argtypes = [P, i64, P, d, P, P, P, P]
             lib.or_partition.restype = None
             lib.or_kick.argtypes = [P, i64, P, P, d]
@@ -187,6 +188,15 @@ def timesteps(m, x, v, P, G=1.0, eta=0.2, sym=SYM_HARMONIC):
     out = np.zeros(P.size)
     _check(_load().or_timesteps(_p(m), _p(x), _p(v), _p(P), P.size, G, eta, sym, _p(out)),
            "timesteps")
+    return out
+
+
+def timesteps_of(m, x, v, A, P, G=1.0, eta=0.2, sym=SYM_HARMONIC):
+    """Symmetrised time-steps of the particles A (a sample of the set P) over the set P."""
+    m, x, v, A, P = _f64(m), _f64(x, (-1, 3)), _f64(v, (-1, 3)), _i32(A), _i32(P)
+    out = np.zeros(A.size)
+    _check(_load().or_timesteps_of(_p(m), _p(x), _p(v), _p(A), A.size, _p(P), P.size, G, eta, sym,
+                                   _p(out)), "timesteps_of")
     return out
 
 

@@ -298,13 +298,23 @@ double or_sym_arithmetic(double d)
  * for every i of the set P (Sec. 4.3: the pair timescales are symmetrised first, then the
  * minimum is taken).  sym = 0: harmonic factor, 1: arithmetic factor, 2: none (s = 1).
  */
+int or_timesteps_of(const double *m, const double *x, const double *v, const int32_t *A, int64_t nA,
+                    const int32_t *P, int64_t nP, double G, double eta, int sym, double *tau);
+
 int or_timesteps(const double *m, const double *x, const double *v, const int32_t *P, int64_t nP,
                  double G, double eta, int sym, double *tau)
 {
+    return or_timesteps_of(m, x, v, P, nP, P, nP, G, eta, sym, tau);
+}
+
+/* tau of the particles A, the minimum taken over the set P (A may be a sample of P). */
+int or_timesteps_of(const double *m, const double *x, const double *v, const int32_t *A, int64_t nA,
+                    const int32_t *P, int64_t nP, double G, double eta, int sym, double *tau)
+{
     int err = OR_OK;
-#pragma omp parallel for schedule(dynamic, 16) reduction(max : err) if (nP * nP > OR_PAR_MIN)
-    for (int64_t ia = 0; ia < nP; ++ia) {
-        const int32_t i = P[ia];
+#pragma omp parallel for schedule(dynamic, 16) reduction(max : err) if (nA * nP > OR_PAR_MIN)
+    for (int64_t ia = 0; ia < nA; ++ia) {
+        const int32_t i = A[ia];
         double best = INFINITY;
         for (int64_t jb = 0; jb < nP; ++jb) {
             const int32_t j = P[jb];
@@ -325,7 +335,7 @@ int or_timesteps(const double *m, const double *x, const double *v, const int32_
         }
         tau[ia] = best;
     }
-    or_count_tstep += nP * nP;
+    or_count_tstep += nA * nP;
     return err;
 }
 

@@ -358,6 +358,15 @@ def test_timesteps_min_over_set_and_degenerate_cases():
     assert np.isinf(oracle.timesteps(m, x, v, np.array([1], dtype=np.int32))[0])
 
 
+def test_timesteps_of_a_sample_equals_the_full_set_entries():
+    """tau of sampled members over the whole set is the same number as in the full pass."""
+    m, x, v = ics.plummer_kroupa_binaries(400, 4, binary_fraction=0.2)
+    P = np.arange(400, dtype=np.int32)
+    full = oracle.timesteps(m, x, v, P)
+    A = np.array([3, 399, 17, 250], dtype=np.int32)
+    assert np.array_equal(oracle.timesteps_of(m, x, v, A, P), full[A])
+
+
 def test_timestep_brute_force_high_precision():
     mpmath = pytest.importorskip("mpmath")
     mpmath.mp.dps = 40

@@ -55,6 +55,10 @@ def parse():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--passes-only", action="store_true",
+                   help="time one full acc+gradient pass and one time-step pass and report the "
+                        "time-step level histogram (workloads whose hierarchy cannot be "
+                        "integrated in minutes, e.g. hard binaries without regularisation)")
     p.add_argument("--subtree-max", type=int, default=0,
                    help="largest set whose hhs_fsi subtree runs in one block (0 = library default)")
     return p.parse_args()
@@ -497,12 +501,84 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_passes(args):
+    """Full passes of a workload: acc+gradient and time-step, timed with CUDA events, and the
+    hierarchy level each particle's time-step would put it on (level = number of halvings of
+    dt_pivot until tau_i >= pivot)."""
+    import torch
+
+    from paper_2011_14984_gb300 import build as fbuild
+    from paper_2011_14984_gb300 import frost as fr
+    from paper_2011_14984_gb300 import ics
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    fbuild.build()
+    fr.load()
+    stream = torch.cuda.current_stream()
+    m, x, v = ics.workload(args.workload)
+    n = m.size
+    f = fr.Frost(m, x, v, G=1.0, eta=args.eta, precision="mixed", stream=stream.cuda_stream)
+    for _ in range(args.warmup):
+        f.accel_gradient(None, None, eps_grad=args.dt, want=("acc_tilde",))
+    f.set_timing(True)
+    f.reset_stats()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    ms = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        f.accel_gradient(None, None, eps_grad=args.dt, want=("acc_tilde",))
+        b.record(stream)
+        b.synchronize()
+        ms += a.elapsed_time(b)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    tau = f.timesteps()
+    b.record(stream)
+    b.synchronize()
+    ms_tau = a.elapsed_time(b)
+    clk = clocks.stop()
+    st = f.stats()
+    f.close()
+    t = tau.cpu().numpy()
+    lev = np.maximum(0, np.ceil(np.log2(args.dt / t))).astype(int)
+    hist = np.bincount(lev)
+    value = 2.0 * n * (n - 1) * args.steps / (ms * 1e-3)
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    kinds = ["acc", "grad", "tstep"]
+    per = {kinds[k]: {"launches": st["timed_launches"][k], "ms": st["timed_ms"][k],
+                      "tflops": st["timed_pairs"][k] * FLOPS_PER_PAIR[kinds[k]] / (st["timed_ms"][k] * 1e-3) / 1e12
+                      if st["timed_ms"][k] > 0 else 0.0} for k in range(3)}
+    dom = max(range(3), key=lambda k: st["timed_ms"][k])
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "N": int(n), "eta": args.eta, "dt_pivot": args.dt,
+                       "step": "one full acc + gradient pass over all N (no hierarchical steps)",
+                       "l2": "flushed before every timed pass (256 MiB write)"},
+            "roofline": {"bound": "alu", "kernel": kinds[dom] + " pass (mixed)", "achieved": per[kinds[dom]]["tflops"],
+                         "peak": peak, "unit": "TFLOP/s", "frac": per[kinds[dom]]["tflops"] / peak,
+                         "traffic": None, "per_kind": per},
+            "timestep_pass_ms": ms_tau,
+            "level_histogram": {"levels": hist.tolist(), "max_level": int(lev.max()),
+                                "tau_min": float(t.min()), "tau_median": float(np.median(t)),
+                                "note": "level of tau_i below dt_pivot on the first partition"},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload.startswith("cluster_batch"):
         run_batch(args)
+    elif args.passes_only:
+        run_passes(args)
     else:
         run_frost(args)
 

@@ -185,6 +185,7 @@ frost_status frost_energy_momentum(frost_ctx *ctx, double *E_kin, double *E_pot,
                                    double L[3]);
 
 /* Counters since frost_init or frost_reset_stats. */
+#define FROST_STATS_LEVELS 48
 typedef struct {
     int64_t acc_pairs;      /* Newtonian pair interactions evaluated */
     int64_t grad_pairs;     /* gradient pair interactions evaluated */
@@ -201,6 +202,10 @@ typedef struct {
     double timed_ms[4];
     int64_t timed_pairs[4];
     int64_t subtree_launches;  /* hhs_fsi calls handed to the single-block subtree solver */
+    /* per hierarchy depth d (top level 0; the last entry collects d >= FROST_STATS_LEVELS-1):
+     * hhs_fsi calls with a non-empty set, and the summed sizes of those sets */
+    int64_t level_calls[FROST_STATS_LEVELS];
+    int64_t level_particles[FROST_STATS_LEVELS];
 } frost_stats;
 
 frost_status frost_get_stats(frost_ctx *ctx, frost_stats *out);

@@ -55,6 +55,7 @@ struct Misc {
     int64_t rel[2];     // list relation: bad/duplicate flag, |A cap B|
     double eres[8];     // energy reduction
     unsigned long long sub[6];  // subtree solver counters (acc, grad, tstep pairs, hhs, fsi, depth)
+    unsigned long long lev[2][SUBTREE_STAT_LEVELS];  // subtree calls / set sizes per depth
     int err;            // sticky device error word
     int pad;
 };
@@ -96,6 +97,7 @@ struct frost_ctx {
     double *d_ecl = nullptr;                         // per-cluster energy sums [n_clusters][8]
     std::vector<double> h_ecl;
     unsigned long long sub_seen[6] = {0, 0, 0, 0, 0, 0};
+    unsigned long long lev_seen[2][SUBTREE_STAT_LEVELS] = {};
     Misc *dmisc = nullptr, *hmisc = nullptr;
     std::vector<int32_t *> lvS, lvF;                 // per-level slow/fast lists
 
@@ -202,6 +204,12 @@ frost_status sync_misc(frost_ctx *c)
     c->st.fsi_calls += (int64_t)(sub[4] - c->sub_seen[4]);
     if ((int)sub[5] > c->st.max_depth_seen) c->st.max_depth_seen = (int)sub[5];
     for (int k = 0; k < 6; ++k) c->sub_seen[k] = sub[k];
+    for (int q = 0; q < 2; ++q)
+        for (int L = 0; L < SUBTREE_STAT_LEVELS; ++L) {
+            const unsigned long long cur = c->hmisc->lev[q][L];
+            (q == 0 ? c->st.level_calls : c->st.level_particles)[L] += (int64_t)(cur - c->lev_seen[q][L]);
+            c->lev_seen[q][L] = cur;
+        }
     return err_to_status(c->hmisc->err);
 }
 
@@ -417,6 +425,7 @@ void hhs_subtree(frost_ctx *c, const int32_t *P, int nP, double tau, int depth)
     a.max_depth = c->max_depth;
     a.err = &c->dmisc->err;
     a.counters = c->dmisc->sub;
+    a.levels = &c->dmisc->lev[0][0];
     a.perm = c->perm;
     a.tmp = c->ptmp;
     a.tau = c->tau;
@@ -454,6 +463,11 @@ frost_status hhs_fsi(frost_ctx *c, const int32_t *P, int nP, double tau, int dep
     }
     c->st.hhs_calls += 1;
     if (depth > c->st.max_depth_seen) c->st.max_depth_seen = depth;
+    {
+        const int L = std::min(depth, FROST_STATS_LEVELS - 1);
+        c->st.level_calls[L] += 1;
+        c->st.level_particles[L] += nP;
+    }
     FROST_TRY(ensure_level(c, depth));
     int32_t *S = c->lvS[depth], *F = c->lvF[depth];
     pass_tstep(c, P, nP, c->tau);
@@ -808,6 +822,7 @@ frost_status frost_step(frost_ctx *c, double dt_pivot, int64_t n_steps)
         a.max_depth = c->max_depth;
         a.err = &c->dmisc->err;
         a.counters = c->dmisc->sub;
+        a.levels = &c->dmisc->lev[0][0];
         a.perm = c->perm;
         a.tmp = c->ptmp;
         a.tau = c->tau;

@@ -137,6 +137,7 @@ void launch_cluster_energy(cudaStream_t s, const int64_t *offsets, int n_cluster
 
 // ---- single-CTA subtree solver (subtree.cu) ------------------------------------------
 constexpr int SUBTREE_MAX_FRAMES = 64;  // recursion frames per block (max_depth < 64)
+constexpr int SUBTREE_STAT_LEVELS = 48; // per-depth statistics (last entry: deeper levels)
 
 struct SubtreeArgs {
     double *x, *v;
@@ -146,6 +147,7 @@ struct SubtreeArgs {
     int max_depth;
     int *err;
     unsigned long long *counters;  // [6]: acc, grad, tstep pairs, hhs calls, fsi calls, max depth
+    unsigned long long *levels;    // [2][SUBTREE_STAT_LEVELS]: calls and set sizes per depth
     // workspace (per particle: perm, tmp int32; tau double; aA..atB [3] doubles; wA, wB
     // float; recA, recB 64 bytes), indexed from the block's first particle
     int32_t *perm, *tmp;

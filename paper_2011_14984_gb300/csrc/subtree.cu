@@ -35,6 +35,7 @@ struct SubParams {
     int max_depth;
     int *err;
     unsigned long long *counters;  // acc pairs, grad pairs, tstep pairs, hhs calls, fsi calls, max depth
+    unsigned long long *levels;    // [2][SUBTREE_STAT_LEVELS]: calls and set sizes per depth
 };
 
 struct SubWork {
@@ -417,6 +418,9 @@ __global__ void __launch_bounds__(SB) k_hhs_subtree(SubParams p, SubWork w0, con
                 if (tid == 0) {
                     cnt.hhs += 1;
                     cnt.maxdepth = max(cnt.maxdepth, depth);
+                    const int L = min(depth, SUBTREE_STAT_LEVELS - 1);
+                    atomicAdd(&p.levels[L], 1ull);
+                    atomicAdd(&p.levels[SUBTREE_STAT_LEVELS + L], (unsigned long long)fn);
                 }
                 b_tstep<MIXED, SYM>(p, w, S, fn, w.tau, cnt);
                 nS = b_partition(S, fn, w.tau, ftau, w.tmp);
@@ -492,6 +496,7 @@ void launch_subtree(cudaStream_t s, bool mixed, int sym, const SubtreeArgs &a)
     p.max_depth = a.max_depth;
     p.err = a.err;
     p.counters = a.counters;
+    p.levels = a.levels;
     SubWork w;
     w.perm = a.perm;
     w.tmp = a.tmp;

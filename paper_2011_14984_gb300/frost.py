@@ -45,11 +45,12 @@ class frost_stats(ctypes.Structure):
                 ("hhs_calls", ctypes.c_int64), ("fsi_calls", ctypes.c_int64),
                 ("max_depth_seen", ctypes.c_int32), ("timing_enabled", ctypes.c_int32),
                 ("timed_launches", ctypes.c_int64 * 4), ("timed_ms", ctypes.c_double * 4),
-                ("timed_pairs", ctypes.c_int64 * 4), ("subtree_launches", ctypes.c_int64)]
+                ("timed_pairs", ctypes.c_int64 * 4), ("subtree_launches", ctypes.c_int64),
+                ("level_calls", ctypes.c_int64 * 48), ("level_particles", ctypes.c_int64 * 48)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
-        for k in ("timed_launches", "timed_ms", "timed_pairs"):
+        for k in ("timed_launches", "timed_ms", "timed_pairs", "level_calls", "level_particles"):
             d[k] = list(d[k])
         return d
 

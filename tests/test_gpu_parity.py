@@ -444,3 +444,49 @@ def test_cluster_batch_matches_oracle_per_cluster(precision):
     tot = f.energy()
     assert abs(tot["E"] - ecl["E"].sum()) < 1e-12 * abs(ecl["E"].sum())
     f.close()
+
+
+# ---------------------------------------------------------------------------------------
+# the other full-size workloads, checked on sampled particles
+# ---------------------------------------------------------------------------------------
+
+def test_full_size_kroupa_binaries_262k_sampled():
+    """Plummer N = 262144 with Kroupa masses and 5% hard binaries (seed 3): full mixed acc +
+    gradient and time-step passes, 384 sampled particles (binary members included) against
+    the oracle; the oracle computes every a_j for the sampled gradients."""
+    m, x, v = ics.workload("plummer_kroupa_binaries_256k")
+    n = m.size
+    f = F(m, x, v, precision="mixed", eta=0.2)
+    out = f.accel_gradient(None, None, eps_grad=2.0 ** -10)
+    tau = cpu(f.timesteps())
+    rng = np.random.default_rng(12)
+    I = np.sort(np.concatenate([rng.choice(n - 13106, 256, replace=False),
+                                n - 13106 + rng.choice(13106, 128, replace=False)])).astype(np.int32)
+    A = np.arange(n, dtype=np.int32)
+    a_all = oracle.acc(m, x, A, A)
+    g_ref = oracle.grad(m, x, I, a_all[I], A, a_all)
+    ea = rel(cpu(out["acc"])[I], a_all[I])
+    eg = rel(cpu(out["grad"])[I], g_ref)
+    et = rel(tau[I], oracle.timesteps_of(m, x, v, I, A, eta=0.2))
+    assert p999(ea) < 1e-6 and p999(eg) < 1e-6, (p999(ea), p999(eg))
+    assert p999(et) < 2e-6, p999(et)
+    a = cpu(out["acc"])
+    Ftot = (m[:, None] * a).sum(0)
+    assert np.all(np.abs(Ftot) < 1e-9 * (m[:, None] * np.abs(a)).sum())
+    f.close()
+
+
+def test_full_size_plummer_1m_sampled_acc():
+    """Plummer N = 1048576 (seed 5): the full mixed Newtonian pass on 256 sampled particles
+    against the oracle, plus the vanishing total force over all particles."""
+    m, x, v = ics.workload("plummer_1m")
+    n = m.size
+    f = F(m, x, v, precision="mixed")
+    a = cpu(f.accel_gradient(None, None, want=("acc",))["acc"])
+    rng = np.random.default_rng(13)
+    I = np.sort(rng.choice(n, 256, replace=False)).astype(np.int32)
+    ea = rel(a[I], oracle.acc(m, x, I, np.arange(n, dtype=np.int32)))
+    assert p999(ea) < 1e-6 and ea.max() < 1e-5, (p999(ea), ea.max())
+    Ftot = (m[:, None] * a).sum(0)
+    assert np.all(np.abs(Ftot) < 1e-9 * (m[:, None] * np.abs(a)).sum())
+    f.close()

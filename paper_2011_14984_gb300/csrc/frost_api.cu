@@ -90,6 +90,10 @@ struct frost_ctx {
     double *tau = nullptr;                           // [N]
     float *wA = nullptr, *wB = nullptr;              // max_j m_j / r^3 per particle (mixed)
     float *wpart = nullptr;                          // its split partials
+    unsigned *hist = nullptr;                        // |a| histograms [2][HOT_BINS] (mixed)
+    uint32_t *hA = nullptr, *hB = nullptr;           // hot-source masks of aA / aB (mixed)
+    double *part_hot = nullptr;                      // FP64 hot-source gradient partials
+    size_t part_hot_elems = 0;
     int32_t *perm = nullptr, *ptmp = nullptr;        // subtree solver permutation / scratch
     int subtree_max = 384;                           // sets up to this size run in one block
     int n_clusters = 0;                              // > 0: batch of independent clusters
@@ -227,14 +231,17 @@ int badbit(const frost_ctx *c) { return c->eps2 == 0.0 ? ERR_COINCIDENT : ERR_NO
 // Newtonian accelerations of A from B (self: the same list); writes G * sum into out_soa
 // ([3][nA]) and, if given, out_aos ([nA][3]).  With wmax (mixed mode), also the weight
 // max_j m_j / r^3 of each particle's dominant term, which the following gradient pass uses.
+// With hist (mixed mode, with wmax): the |a| histogram of the pass is added to hist (zeroed by
+// the caller) for the hot-source classification of refine_hot.
 void pass_acc(frost_ctx *c, const int32_t *A, int nA, const int32_t *B, int nB, bool self,
-              double *out_soa, double *out_aos, float *wmax = nullptr)
+              double *out_soa, double *out_aos, float *wmax = nullptr, unsigned *hist = nullptr)
 {
     if (nA <= 0) return;
     if (nB <= 0 || (self && nA == 1)) {
         if (out_soa) cudaMemsetAsync(out_soa, 0, sizeof(double) * 3 * nA, c->stream);
         if (out_aos) cudaMemsetAsync(out_aos, 0, sizeof(double) * 3 * nA, c->stream);
         if (wmax) cudaMemsetAsync(wmax, 0, sizeof(float) * nA, c->stream);
+        if (hist && c->mixed && out_soa) launch_acc_hist(c->stream, out_soa, nA, hist);
         return;
     }
     // before a gradient pass (wmax requested) the mixed mode uses the accurate variant on the
@@ -268,6 +275,35 @@ void pass_acc(frost_ctx *c, const int32_t *A, int nA, const int32_t *B, int nB, 
                         a.wpart ? wmax : nullptr, &c->dmisc->err, badbit(c));
     c->st.kernel_launches += 2;
     c->st.acc_pairs += pairs;
+    if (accurate && hist && out_soa) {
+        launch_acc_hist(c->stream, out_soa, nA, hist);
+        c->st.kernel_launches += 1;
+    }
+}
+
+// Hot sources (mixed mode): after the accurate Newtonian pass of A against B whose records are
+// irec (A) and jrec (B), marks in mask the particles of A with |a| above HOT_KAPPA x the larger
+// median of hist (this pass) and hist2 (the companion pass of B against A, n2 values, or NULL)
+// and recomputes their accelerations with the dominant terms in FP64 (hot_kernels.cu).
+void refine_hot(frost_ctx *c, const void *irec, const void *jrec, const int32_t *A, int nA,
+                const int32_t *B, int nB, bool self, double *a_soa, double *a_aos, const float *wmax,
+                const unsigned *hist, const unsigned *hist2, int n2, uint32_t *mask)
+{
+    if (!c->mixed || nA <= 0) return;
+    if (nB <= 0 || (self && nA == 1)) {
+        cudaMemsetAsync(mask, 0, sizeof(uint32_t) * ((nA + 31) / 32), c->stream);
+        return;
+    }
+    launch_acc_refine(c->stream, (const float4 *)irec, (const float4 *)jrec, nA, nB, self ? 1 : 0, A, B,
+                      c->x, c->m, c->N, c->G, c->eps2, wmax, hist, hist2, n2, a_soa, a_aos, mask);
+    c->st.kernel_launches += 1;
+}
+
+// the two |a| histograms, zeroed
+unsigned *zero_hists(frost_ctx *c)
+{
+    cudaMemsetAsync(c->hist, 0, sizeof(unsigned) * 2 * HOT_BINS, c->stream);
+    return c->hist;
 }
 
 // gradient of A against B with a_A (soa [3][nA]) and a_B (soa [3][nB]); writes
@@ -275,7 +311,7 @@ void pass_acc(frost_ctx *c, const int32_t *A, int nA, const int32_t *B, int nB, 
 // dominant-term weights of A from the Newtonian pass at the same positions (mixed mode).
 void pass_grad(frost_ctx *c, const int32_t *A, int nA, const double *aA, const int32_t *B, int nB,
                const double *aB, bool self, double eps_grad, double *at_soa, double *at_aos,
-               double *g_aos, const float *wmax)
+               double *g_aos, const float *wmax, const uint32_t *hotB = nullptr)
 {
     if (nA <= 0) return;
     const double cgrad = eps_grad * eps_grad / 48.0;
@@ -286,9 +322,12 @@ void pass_grad(frost_ctx *c, const int32_t *A, int nA, const double *aA, const i
         if (g_aos) cudaMemsetAsync(g_aos, 0, sizeof(double) * 3 * nA, c->stream);
         return;
     }
+    if (!c->mixed) hotB = nullptr;
     if (c->mixed) {
-        launch_pack_grad_mixed(c->stream, A, nA, c->x, c->m, c->N, aA, (float4 *)c->recA);
-        if (!self) launch_pack_grad_mixed(c->stream, B, nB, c->x, c->m, c->N, aB, (float4 *)c->recB);
+        // hot sources: masses zeroed in the FP32 source records, their terms summed in FP64 below
+        launch_pack_grad_mixed(c->stream, A, nA, c->x, c->m, c->N, aA, (float4 *)c->recA,
+                               self ? hotB : nullptr);
+        if (!self) launch_pack_grad_mixed(c->stream, B, nB, c->x, c->m, c->N, aB, (float4 *)c->recB, hotB);
     } else {
         launch_pack_grad_fp64(c->stream, A, nA, c->x, c->m, c->N, aA, (double4_32a *)c->recA);
         if (!self) launch_pack_grad_fp64(c->stream, B, nB, c->x, c->m, c->N, aB, (double4_32a *)c->recB);
@@ -309,8 +348,16 @@ void pass_grad(frost_ctx *c, const int32_t *A, int nA, const double *aA, const i
         TimedScope ts(c, PASS_GRAD, pairs);
         launch_grad(c->stream, c->mixed, a);
     }
+    int ns_hot = 0;
+    if (hotB) {
+        ns_hot = hot_grad_splits(nA, nB, c->n_sm);
+        while (ns_hot > 1 && (size_t)ns_hot * 3 * nA > c->part_hot_elems) --ns_hot;
+        launch_grad_hot(c->stream, A, nA, aA, B, nB, aB, hotB, a.self_pass, c->x, c->m, c->N, c->eps2, ns_hot,
+                        c->part_hot);
+        c->st.kernel_launches += 1;
+    }
     launch_finalize_grad(c->stream, c->part, a.shape.nsplit, nA, 2.0 * c->G, aA, cgrad, at_soa,
-                         at_aos, g_aos, &c->dmisc->err, badbit(c));
+                         at_aos, g_aos, &c->dmisc->err, badbit(c), c->part_hot, ns_hot);
     c->st.kernel_launches += 2;
     c->st.grad_pairs += pairs;
 }
@@ -370,8 +417,14 @@ void fsi(frost_ctx *c, const int32_t *S, int nS, double dt)
     pass_acc(c, S, nS, S, nS, true, c->aA, nullptr);
     kick(c, S, nS, c->aA, dt / 6.0);
     drift(c, S, nS, 0.5 * dt);
-    pass_acc(c, S, nS, S, nS, true, c->aA, nullptr, c->wA);
-    pass_grad(c, S, nS, c->aA, S, nS, c->aA, true, dt, c->atA, nullptr, nullptr, c->wA);
+    if (c->mixed) {
+        unsigned *h = zero_hists(c);
+        pass_acc(c, S, nS, S, nS, true, c->aA, nullptr, c->wA, h);
+        refine_hot(c, c->recA, c->recA, S, nS, S, nS, true, c->aA, nullptr, c->wA, h, nullptr, 0, c->hA);
+    } else {
+        pass_acc(c, S, nS, S, nS, true, c->aA, nullptr, c->wA);
+    }
+    pass_grad(c, S, nS, c->aA, S, nS, c->aA, true, dt, c->atA, nullptr, nullptr, c->wA, c->hA);
     kick(c, S, nS, c->atA, 2.0 * dt / 3.0);
     drift(c, S, nS, 0.5 * dt);
     pass_acc(c, S, nS, S, nS, true, c->aA, nullptr);
@@ -383,11 +436,19 @@ void kick_sf(frost_ctx *c, const int32_t *S, int nS, const int32_t *F, int nF, d
              bool gradient, double tau_pivot)
 {
     if (nS <= 0 || nF <= 0) return;
-    pass_acc(c, S, nS, F, nF, false, c->aA, nullptr, gradient ? c->wA : nullptr);
-    pass_acc(c, F, nF, S, nS, false, c->aB, nullptr, gradient ? c->wB : nullptr);
+    unsigned *h = (gradient && c->mixed) ? zero_hists(c) : nullptr;
+    pass_acc(c, S, nS, F, nF, false, c->aA, nullptr, gradient ? c->wA : nullptr, h);
+    pass_acc(c, F, nF, S, nS, false, c->aB, nullptr, gradient ? c->wB : nullptr, h ? h + HOT_BINS : nullptr);
     if (gradient) {
-        pass_grad(c, S, nS, c->aA, F, nF, c->aB, false, tau_pivot, c->atA, nullptr, nullptr, c->wA);
-        pass_grad(c, F, nF, c->aB, S, nS, c->aA, false, tau_pivot, c->atB, nullptr, nullptr, c->wB);
+        if (h) {
+            // the records of the last pass: recA = F, recB = S (three-way split positions)
+            refine_hot(c, c->recB, c->recA, S, nS, F, nF, false, c->aA, nullptr, c->wA, h, h + HOT_BINS, nF,
+                       c->hA);
+            refine_hot(c, c->recA, c->recB, F, nF, S, nS, false, c->aB, nullptr, c->wB, h + HOT_BINS, h, nS,
+                       c->hB);
+        }
+        pass_grad(c, S, nS, c->aA, F, nF, c->aB, false, tau_pivot, c->atA, nullptr, nullptr, c->wA, c->hB);
+        pass_grad(c, F, nF, c->aB, S, nS, c->aA, false, tau_pivot, c->atB, nullptr, nullptr, c->wB, c->hA);
         kick(c, S, nS, c->atA, cdt);
         kick(c, F, nF, c->atB, cdt);
     } else {
@@ -517,7 +578,7 @@ void destroy(frost_ctx *c)
     if (c->d_ecl) cudaFree(c->d_ecl);
     void *dev[] = {c->x, c->v, c->m, c->all, c->marks, c->recA, c->recB, c->part,
                    c->aA, c->aB, c->atA, c->atB, c->tau, c->wA, c->wB, c->wpart, c->perm,
-                   c->ptmp, c->dmisc};
+                   c->ptmp, c->dmisc, c->hist, c->hA, c->hB, c->part_hot};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (c->hmisc) cudaFreeHost(c->hmisc);
@@ -638,6 +699,14 @@ static frost_status init_impl(frost_ctx **out, int64_t n, const double *m, const
     INIT_CUDA(cudaMalloc(&c->wA, sizeof(float) * N));
     INIT_CUDA(cudaMalloc(&c->wB, sizeof(float) * N));
     INIT_CUDA(cudaMalloc(&c->wpart, sizeof(float) * (c->part_elems / 3)));
+    if (c->mixed) {
+        const size_t words = (N + 31) / 32;
+        c->part_hot_elems = 3 * std::max(N, (size_t)HOT_MAX_SPLITS * c->n_sm * 256);
+        INIT_CUDA(cudaMalloc(&c->hist, sizeof(unsigned) * 2 * HOT_BINS));
+        INIT_CUDA(cudaMalloc(&c->hA, sizeof(uint32_t) * words));
+        INIT_CUDA(cudaMalloc(&c->hB, sizeof(uint32_t) * words));
+        INIT_CUDA(cudaMalloc(&c->part_hot, sizeof(double) * c->part_hot_elems));
+    }
     INIT_CUDA(cudaMalloc(&c->perm, sizeof(int32_t) * N));
     INIT_CUDA(cudaMalloc(&c->ptmp, sizeof(int32_t) * N));
     if (n_clusters > 0) {
@@ -731,14 +800,20 @@ frost_status frost_accel_gradient(frost_ctx *c, const int32_t *active, int64_t n
     if (nA == 0) return FROST_OK;
     const bool want_grad = acc_tilde || grad;
     if (self) {
-        pass_acc(c, A, nA, A, nA, true, c->aA, acc, want_grad ? c->wA : nullptr);
+        unsigned *h = (want_grad && c->mixed) ? zero_hists(c) : nullptr;
+        pass_acc(c, A, nA, A, nA, true, c->aA, acc, want_grad ? c->wA : nullptr, h);
+        if (h) refine_hot(c, c->recA, c->recA, A, nA, A, nA, true, c->aA, acc, c->wA, h, nullptr, 0, c->hA);
         if (want_grad)
-            pass_grad(c, A, nA, c->aA, A, nA, c->aA, true, eps_grad, nullptr, acc_tilde, grad, c->wA);
+            pass_grad(c, A, nA, c->aA, A, nA, c->aA, true, eps_grad, nullptr, acc_tilde, grad, c->wA, c->hA);
     } else {
-        pass_acc(c, A, nA, B, nB, false, c->aA, acc, want_grad ? c->wA : nullptr);
+        unsigned *h = (want_grad && c->mixed) ? zero_hists(c) : nullptr;
+        pass_acc(c, A, nA, B, nB, false, c->aA, acc, want_grad ? c->wA : nullptr, h);
         if (want_grad) {
-            pass_acc(c, B, nB, A, nA, false, c->aB, nullptr);
-            pass_grad(c, A, nA, c->aA, B, nB, c->aB, false, eps_grad, nullptr, acc_tilde, grad, c->wA);
+            pass_acc(c, B, nB, A, nA, false, c->aB, nullptr, c->wB, h ? h + HOT_BINS : nullptr);
+            // the records of the last pass: recA = B, recB = A; only B's accelerations are sources
+            if (h) refine_hot(c, c->recA, c->recB, B, nB, A, nA, false, c->aB, nullptr, c->wB, h + HOT_BINS, h,
+                              nA, c->hB);
+            pass_grad(c, A, nA, c->aA, B, nB, c->aB, false, eps_grad, nullptr, acc_tilde, grad, c->wA, c->hB);
         }
     }
     FROST_CUDA(cudaGetLastError());

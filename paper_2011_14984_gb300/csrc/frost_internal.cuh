@@ -68,8 +68,10 @@ struct PairArgs {
 // ---- pack kernels: list -> per-pass records ------------------------------------------
 void launch_pack_pos_mixed(cudaStream_t s, const int32_t *list, int n, const double *x,
                            const double *m, int N, float4 *rec);
+// hot (optional): mask bit k set zeroes the mass of record k (a source summed in FP64)
 void launch_pack_grad_mixed(cudaStream_t s, const int32_t *list, int n, const double *x,
-                            const double *m, int N, const double *acc /*[3][n]*/, float4 *rec);
+                            const double *m, int N, const double *acc /*[3][n]*/, float4 *rec,
+                            const uint32_t *hot = nullptr);
 void launch_pack_tstep_mixed(cudaStream_t s, const int32_t *list, int n, const double *x,
                              const double *v, const double *m, int N, double G, float4 *rec);
 void launch_pack_pos_fp64(cudaStream_t s, const int32_t *list, int n, const double *x,
@@ -93,10 +95,34 @@ void launch_tstep(cudaStream_t s, bool mixed, const PairArgs &a, double eta, int
 void launch_finalize_vec(cudaStream_t s, const double *part, int nsplit, int n, double scale,
                          double *out_soa, double *out_aos, const float *wpart, float *wmax,
                          int *err, int coincident_bit);
-// a~ = a + c g with g = scale * sum part; writes a~ (soa and/or aos) and g (aos, optional)
+// a~ = a + c g with g = scale * (sum part + sum part2); writes a~ (soa and/or aos) and g
+// (aos, optional); part2 (nsplit2 splits, may be 0) holds the FP64 terms of hot sources
 void launch_finalize_grad(cudaStream_t s, const double *part, int nsplit, int n, double scale,
                           const double *a_soa, double c, double *at_soa, double *at_aos,
-                          double *g_aos, int *err, int coincident_bit);
+                          double *g_aos, int *err, int coincident_bit,
+                          const double *part2 = nullptr, int nsplit2 = 0);
+
+// ---- hot sources of the mixed gradient pass (hot_kernels.cu) -------------------------
+constexpr int HOT_BINS = 1024;          // |a| histogram: 4 bins per octave
+constexpr float HOT_KAPPA = 6.0f;       // hot: |a| > HOT_KAPPA x (median bin's upper edge)
+constexpr int HOT_MAX_SPLITS = 16;      // source splits of k_grad_hot
+// hist[HOT_BINS] += counts of the bins of |a_i| over [3][n] accelerations (hist pre-zeroed)
+void launch_acc_hist(cudaStream_t s, const double *a_soa, int n, unsigned *hist);
+// after an accurate mixed Newtonian pass of A against B (records irec [3][n_a], jrec [3][n_s]):
+// writes the hot mask of A (words [(n_a + 31) / 32]) and recomputes a (out_soa, out_aos) of
+// the hot particles with their dominant terms in FP64.  hist: the |a| histogram of this pass;
+// hist2 (n2 values): that of the pass of B against A in a cross pair, or NULL.
+void launch_acc_refine(cudaStream_t s, const float4 *irec, const float4 *jrec, int n_a, int n_s,
+                       int self_pass, const int32_t *A, const int32_t *B, const double *x,
+                       const double *m, int N, double G, double eps2, const float *wmax,
+                       const unsigned *hist, const unsigned *hist2, int n2, double *out_soa,
+                       double *out_aos, uint32_t *mask);
+// number of source splits of launch_grad_hot for these list sizes
+int hot_grad_splits(int n_a, int n_s, int n_sm);
+// part[s][c][i] = FP64 gradient sums over the hot sources of B (mask) for every i of A
+void launch_grad_hot(cudaStream_t s, const int32_t *A, int n_a, const double *aA, const int32_t *B,
+                     int n_s, const double *aB, const uint32_t *mask, int self_pass, const double *x,
+                     const double *m, int N, double eps2, int nsplit, double *part);
 // tau[i] = eta * min_split part[split][i]; flags non-positive or NaN values
 void launch_finalize_tau(cudaStream_t s, const double *part, int nsplit, int n, double eta,
                          double *tau, int *err);

@@ -64,16 +64,18 @@ __device__ __forceinline__ void pack_grad_mixed_one(int k, const int32_t *__rest
                                                     const double *__restrict__ x,
                                                     const double *__restrict__ m, int N,
                                                     const double *__restrict__ acc,
-                                                    float4 *__restrict__ rec)
+                                                    float4 *__restrict__ rec,
+                                                    const uint32_t *__restrict__ hot = nullptr)
 {
     const int i = list ? list[k] : k;
+    const bool zero_m = hot && ((hot[k >> 5] >> (k & 31)) & 1u);
     float hx, hy, hz, mx, my, mz, lx, ly, lz;
     split3(x[i], hx, mx, lx);
     split3(x[N + i], hy, my, ly);
     split3(x[2 * N + i], hz, mz, lz);
     const double ax = acc ? acc[k] : 0.0, ay = acc ? acc[n + k] : 0.0, az = acc ? acc[2 * n + k] : 0.0;
     const float ahx = trunc12((float)ax), ahy = trunc12((float)ay), ahz = trunc12((float)az);
-    rec[k] = make_float4(hx, hy, hz, (float)m[i]);
+    rec[k] = make_float4(hx, hy, hz, zero_m ? 0.f : (float)m[i]);
     rec[n + k] = make_float4(mx, my, mz, ahx);
     rec[2 * n + k] = make_float4(lx, ly, lz, ahy);
     rec[3 * n + k] = make_float4(ahz, (float)(ax - (double)ahx), (float)(ay - (double)ahy),

@@ -41,10 +41,10 @@ __global__ void k_pack_pos_mixed(const int32_t *__restrict__ list, int n, const 
 
 __global__ void k_pack_grad_mixed(const int32_t *__restrict__ list, int n, const double *__restrict__ x,
                                   const double *__restrict__ m, int N, const double *__restrict__ acc,
-                                  float4 *__restrict__ rec)
+                                  float4 *__restrict__ rec, const uint32_t *__restrict__ hot)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) pack_grad_mixed_one(k, list, n, x, m, N, acc, rec);
+    if (k < n) pack_grad_mixed_one(k, list, n, x, m, N, acc, rec, hot);
 }
 
 __global__ void k_pack_tstep_mixed(const int32_t *__restrict__ list, int n, const double *__restrict__ x,
@@ -268,7 +268,8 @@ __global__ void k_finalize_vec(const double *__restrict__ part, int nsplit, int 
 __global__ void k_finalize_grad(const double *__restrict__ part, int nsplit, int n, double scale,
                                 const double *__restrict__ a_soa, double c,
                                 double *__restrict__ at_soa, double *__restrict__ at_aos,
-                                double *__restrict__ g_aos, int *__restrict__ err, int badbit)
+                                double *__restrict__ g_aos, int *__restrict__ err, int badbit,
+                                const double *__restrict__ part2, int nsplit2)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -276,6 +277,7 @@ __global__ void k_finalize_grad(const double *__restrict__ part, int nsplit, int
     for (int k = 0; k < 3; ++k) {
         double s = 0.0;
         for (int p = 0; p < nsplit; ++p) s += part[((size_t)p * 3 + k) * n + i];
+        for (int p = 0; p < nsplit2; ++p) s += part2[((size_t)p * 3 + k) * n + i];
         const double g = scale * s;
         const double at = a_soa[(size_t)k * n + i] + c * g;
         ok = ok && isfinite(at) && isfinite(g);
@@ -322,10 +324,10 @@ void launch_pack_pos_mixed(cudaStream_t s, const int32_t *list, int n, const dou
     k_pack_pos_mixed<<<cdiv(n, 256), 256, 0, s>>>(list, n, x, m, N, rec);
 }
 void launch_pack_grad_mixed(cudaStream_t s, const int32_t *list, int n, const double *x,
-                            const double *m, int N, const double *acc, float4 *rec)
+                            const double *m, int N, const double *acc, float4 *rec, const uint32_t *hot)
 {
     if (n <= 0) return;
-    k_pack_grad_mixed<<<cdiv(n, 256), 256, 0, s>>>(list, n, x, m, N, acc, rec);
+    k_pack_grad_mixed<<<cdiv(n, 256), 256, 0, s>>>(list, n, x, m, N, acc, rec, hot);
 }
 void launch_pack_tstep_mixed(cudaStream_t s, const int32_t *list, int n, const double *x,
                              const double *v, const double *m, int N, double G, float4 *rec)
@@ -470,11 +472,11 @@ void launch_finalize_vec(cudaStream_t s, const double *part, int nsplit, int n, 
 
 void launch_finalize_grad(cudaStream_t s, const double *part, int nsplit, int n, double scale,
                           const double *a_soa, double c, double *at_soa, double *at_aos,
-                          double *g_aos, int *err, int badbit)
+                          double *g_aos, int *err, int badbit, const double *part2, int nsplit2)
 {
     if (n <= 0) return;
     k_finalize_grad<<<cdiv(n, 256), 256, 0, s>>>(part, nsplit, n, scale, a_soa, c, at_soa, at_aos,
-                                                  g_aos, err, badbit);
+                                                  g_aos, err, badbit, part2, part2 ? nsplit2 : 0);
 }
 
 void launch_finalize_tau(cudaStream_t s, const double *part, int nsplit, int n, double eta,

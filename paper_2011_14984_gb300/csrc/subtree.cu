@@ -355,6 +355,402 @@ __device__ __noinline__ void b_kick_sf(const SubParams &p, const SubWork &w, con
     }
 }
 
+// ---- warp path: the whole subtree of a set of at most 32 particles in one warp ----------
+// Lane l holds particle l of the set in registers (FP64 state); sets are lane masks, the
+// partition is a ballot and every source is broadcast by shuffle, so a tiny set needs no
+// block barrier.  The pair arithmetic is the same as in the block path (pair_bodies.cuh);
+// only the summation order differs.
+constexpr int WARP_N = 32;
+
+struct WLane {
+    double x[3], v[3], m;
+};
+
+__device__ __forceinline__ float wsh(float v, int j) { return __shfl_sync(0xffffffffu, v, j); }
+__device__ __forceinline__ double wshd(double v, int j) { return __shfl_sync(0xffffffffu, v, j); }
+
+// Newtonian pass: every lane sums over the sources j of the uniform mask U with bit j set in
+// its own mask mysrc (j != lane).  accurate: the variant that feeds a gradient (three-way
+// split separations, Newton-refined rsqrt), also returning max_j m_j / r^3.
+template <bool MIXED>
+__device__ __noinline__ void w_acc(const SubParams &p, const WLane &L, unsigned U, unsigned mysrc, bool accurate,
+                                   double (&a)[3], float &wmax)
+{
+    const int lane = threadIdx.x & 31;
+    const int ipos[1] = {lane};
+    float wm[1] = {0.f};
+    double res[3] = {0.0, 0.0, 0.0};
+    if (MIXED) {
+        const float eps2 = (float)p.eps2;
+        float H[3] = {0.f, 0.f, 0.f}, Lo[3] = {0.f, 0.f, 0.f};
+        float ax[1] = {0.f}, ay[1] = {0.f}, az[1] = {0.f};
+        int c = 0;
+        if (!accurate) {
+            AccMixedI<1> I;
+            float hx = (float)L.x[0], hy = (float)L.x[1], hz = (float)L.x[2];
+            I.xh[0] = hx; I.yh[0] = hy; I.zh[0] = hz;
+            I.xl[0] = (float)(L.x[0] - (double)hx);
+            I.yl[0] = (float)(L.x[1] - (double)hy);
+            I.zl[0] = (float)(L.x[2] - (double)hz);
+            const float mf = (float)L.m;
+            unsigned M = U;
+            while (M) {
+                const int j = __ffs(M) - 1;
+                M &= M - 1;
+                float4 J0 = make_float4(wsh(hx, j), wsh(hy, j), wsh(hz, j), wsh(mf, j));
+                const float4 J1 = make_float4(wsh(I.xl[0], j), wsh(I.yl[0], j), wsh(I.zl[0], j), 0.f);
+                if (!((mysrc >> j) & 1u)) J0.w = 0.f;
+                acc_mixed_j<1, true, false>(J0, J1, I, eps2, j, ipos, ax, ay, az, wm);
+                if (++c == 16) {
+                    fold2(H[0], Lo[0], ax[0]); fold2(H[1], Lo[1], ay[0]); fold2(H[2], Lo[2], az[0]);
+                    ax[0] = ay[0] = az[0] = 0.f;
+                    c = 0;
+                }
+            }
+        } else {
+            GradMixedI<1> I;
+            split3(L.x[0], I.xh[0], I.xm[0], I.xl[0]);
+            split3(L.x[1], I.yh[0], I.ym[0], I.yl[0]);
+            split3(L.x[2], I.zh[0], I.zm[0], I.zl[0]);
+            I.ahx[0] = I.ahy[0] = I.ahz[0] = I.alx[0] = I.aly[0] = I.alz[0] = 0.f;
+            const float mf = (float)L.m;
+            unsigned M = U;
+            while (M) {
+                const int j = __ffs(M) - 1;
+                M &= M - 1;
+                float4 J0 = make_float4(wsh(I.xh[0], j), wsh(I.yh[0], j), wsh(I.zh[0], j), wsh(mf, j));
+                const float4 J1 = make_float4(wsh(I.xm[0], j), wsh(I.ym[0], j), wsh(I.zm[0], j), 0.f);
+                const float4 J2 = make_float4(wsh(I.xl[0], j), wsh(I.yl[0], j), wsh(I.zl[0], j), 0.f);
+                if (!((mysrc >> j) & 1u)) J0.w = 0.f;
+                acc3_mixed_j<1, true>(J0, J1, J2, I, eps2, j, ipos, ax, ay, az, wm);
+                if (++c == 16) {
+                    fold2(H[0], Lo[0], ax[0]); fold2(H[1], Lo[1], ay[0]); fold2(H[2], Lo[2], az[0]);
+                    ax[0] = ay[0] = az[0] = 0.f;
+                    c = 0;
+                }
+            }
+        }
+        fold2(H[0], Lo[0], ax[0]); fold2(H[1], Lo[1], ay[0]); fold2(H[2], Lo[2], az[0]);
+        for (int q = 0; q < 3; ++q) res[q] = (double)H[q] + (double)Lo[q];
+    } else {
+        const double4_32a I = make_double4_32a(L.x[0], L.x[1], L.x[2], L.m);
+        unsigned M = U;
+        while (M) {
+            const int j = __ffs(M) - 1;
+            M &= M - 1;
+            double4_32a J = make_double4_32a(wshd(L.x[0], j), wshd(L.x[1], j), wshd(L.x[2], j), wshd(L.m, j));
+            if (!((mysrc >> j) & 1u)) J.w = 0.0;
+            acc_fp64_j<true>(J, I, p.eps2, j, lane, res[0], res[1], res[2]);
+        }
+    }
+    for (int q = 0; q < 3; ++q) a[q] = p.G * res[q];
+    wmax = wm[0];
+}
+
+// Gradient pass: lane sums over j in U with bit j of mysrc, using its own acceleration ai
+// and the sources' accelerations (each lane's ai); dominant terms (w > thr) in FP64.
+template <bool MIXED>
+__device__ __noinline__ void w_grad(const SubParams &p, const WLane &L, unsigned U, unsigned mysrc,
+                                    const double (&ai)[3], float thr, double (&g)[3])
+{
+    const int lane = threadIdx.x & 31;
+    const int ipos[1] = {lane};
+    double res[3] = {0.0, 0.0, 0.0};
+    if (MIXED) {
+        const float eps2 = (float)p.eps2;
+        GradMixedI<1> I;
+        split3(L.x[0], I.xh[0], I.xm[0], I.xl[0]);
+        split3(L.x[1], I.yh[0], I.ym[0], I.yl[0]);
+        split3(L.x[2], I.zh[0], I.zm[0], I.zl[0]);
+        I.ahx[0] = trunc12((float)ai[0]);
+        I.ahy[0] = trunc12((float)ai[1]);
+        I.ahz[0] = trunc12((float)ai[2]);
+        I.alx[0] = (float)(ai[0] - (double)I.ahx[0]);
+        I.aly[0] = (float)(ai[1] - (double)I.ahy[0]);
+        I.alz[0] = (float)(ai[2] - (double)I.ahz[0]);
+        const float mf = (float)L.m;
+        const float thrs[1] = {thr};
+        BigSlots<1> big;
+        big.n[0] = 0;
+        big.j0[0] = big.j1[0] = big.j2[0] = big.j3[0] = lane;
+        float H[3] = {0.f, 0.f, 0.f}, Lo[3] = {0.f, 0.f, 0.f};
+        float gx[1] = {0.f}, gy[1] = {0.f}, gz[1] = {0.f};
+        int c = 0;
+        unsigned M = U;
+        while (M) {
+            const int j = __ffs(M) - 1;
+            M &= M - 1;
+            float4 J0 = make_float4(wsh(I.xh[0], j), wsh(I.yh[0], j), wsh(I.zh[0], j), wsh(mf, j));
+            const float4 J1 = make_float4(wsh(I.xm[0], j), wsh(I.ym[0], j), wsh(I.zm[0], j), wsh(I.ahx[0], j));
+            const float4 J2 = make_float4(wsh(I.xl[0], j), wsh(I.yl[0], j), wsh(I.zl[0], j), wsh(I.ahy[0], j));
+            const float4 J3 = make_float4(wsh(I.ahz[0], j), wsh(I.alx[0], j), wsh(I.aly[0], j), wsh(I.alz[0], j));
+            if (!((mysrc >> j) & 1u)) J0.w = 0.f;
+            grad_mixed_j<1, true>(J0, J1, J2, J3, I, eps2, j, j, ipos, thrs, big, gx, gy, gz);
+            if (++c == 16) {
+                fold2(H[0], Lo[0], gx[0]); fold2(H[1], Lo[1], gy[0]); fold2(H[2], Lo[2], gz[0]);
+                gx[0] = gy[0] = gz[0] = 0.f;
+                c = 0;
+            }
+        }
+        fold2(H[0], Lo[0], gx[0]); fold2(H[1], Lo[1], gy[0]); fold2(H[2], Lo[2], gz[0]);
+        // deferred FP64 terms: every lane fetches the records of its own slot s
+        double bx = 0.0, by = 0.0, bz = 0.0;
+        for (int s = 0; s < GRAD_SLOTS; ++s) {
+            const int j = (s == 0) ? big.j0[0] : (s == 1) ? big.j1[0] : (s == 2) ? big.j2[0] : big.j3[0];
+            const float4 Q0 = make_float4(wsh(I.xh[0], j), wsh(I.yh[0], j), wsh(I.zh[0], j), wsh(mf, j));
+            const float4 Q1 = make_float4(wsh(I.xm[0], j), wsh(I.ym[0], j), wsh(I.zm[0], j), wsh(I.ahx[0], j));
+            const float4 Q2 = make_float4(wsh(I.xl[0], j), wsh(I.yl[0], j), wsh(I.zl[0], j), wsh(I.ahy[0], j));
+            const float4 Q3 = make_float4(wsh(I.ahz[0], j), wsh(I.alx[0], j), wsh(I.aly[0], j), wsh(I.alz[0], j));
+            if (s < big.n[0]) grad_term_fp64<1>(Q0, Q1, Q2, Q3, I, 0, p.eps2, bx, by, bz);
+        }
+        res[0] = ((double)H[0] + (double)Lo[0]) + bx;
+        res[1] = ((double)H[1] + (double)Lo[1]) + by;
+        res[2] = ((double)H[2] + (double)Lo[2]) + bz;
+    } else {
+        const double4_32a I = make_double4_32a(L.x[0], L.x[1], L.x[2], L.m);
+        const double4_32a IA = make_double4_32a(ai[0], ai[1], ai[2], 0.0);
+        unsigned M = U;
+        while (M) {
+            const int j = __ffs(M) - 1;
+            M &= M - 1;
+            double4_32a J = make_double4_32a(wshd(L.x[0], j), wshd(L.x[1], j), wshd(L.x[2], j), wshd(L.m, j));
+            const double4_32a JA = make_double4_32a(wshd(ai[0], j), wshd(ai[1], j), wshd(ai[2], j), 0.0);
+            if (!((mysrc >> j) & 1u)) J.w = 0.0;
+            grad_fp64_j<true>(J, JA, I, IA, p.eps2, j, lane, res[0], res[1], res[2]);
+        }
+    }
+    for (int q = 0; q < 3; ++q) g[q] = 2.0 * p.G * res[q];
+}
+
+// symmetrised time-step of the lane's particle over the set P (lane in P)
+template <bool MIXED, int SYM>
+__device__ __noinline__ double w_tstep(const SubParams &p, const WLane &L, unsigned P, bool &coincident)
+{
+    const int lane = threadIdx.x & 31;
+    const int ipos[1] = {lane};
+    coincident = false;
+    if (MIXED) {
+        TstepMixedI<1> I;
+        const float hx = (float)L.x[0], hy = (float)L.x[1], hz = (float)L.x[2];
+        I.xh[0] = hx; I.yh[0] = hy; I.zh[0] = hz;
+        I.xl[0] = (float)(L.x[0] - (double)hx);
+        I.yl[0] = (float)(L.x[1] - (double)hy);
+        I.zl[0] = (float)(L.x[2] - (double)hz);
+        I.vx[0] = (float)L.v[0]; I.vy[0] = (float)L.v[1]; I.vz[0] = (float)L.v[2];
+        I.gm[0] = (float)(p.G * L.m);
+        const float mf = (float)L.m;
+        const float eta = (float)p.eta, eta15 = 1.5f * eta;
+        float best[1] = {INFINITY}, minr2[1] = {INFINITY};
+        unsigned M = P;
+        while (M) {
+            const int j = __ffs(M) - 1;
+            M &= M - 1;
+            const float4 J0 = make_float4(wsh(hx, j), wsh(hy, j), wsh(hz, j), wsh(mf, j));
+            const float4 J1 = make_float4(wsh(I.xl[0], j), wsh(I.yl[0], j), wsh(I.zl[0], j), 0.f);
+            const float4 JV = make_float4(wsh(I.vx[0], j), wsh(I.vy[0], j), wsh(I.vz[0], j), wsh(I.gm[0], j));
+            tstep_mixed_j<1, SYM, true>(J0, J1, JV, I, eta, eta15, j, ipos, best, minr2);
+        }
+        coincident = (minr2[0] == 0.f);
+        return p.eta * (double)best[0];
+    } else {
+        const double4_32a I = make_double4_32a(L.x[0], L.x[1], L.x[2], L.m);
+        const double4_32a IV = make_double4_32a(L.v[0], L.v[1], L.v[2], p.G * L.m);
+        double best = INFINITY, minr2 = INFINITY;
+        unsigned M = P;
+        while (M) {
+            const int j = __ffs(M) - 1;
+            M &= M - 1;
+            const double4_32a J = make_double4_32a(wshd(I.x, j), wshd(I.y, j), wshd(I.z, j), wshd(I.w, j));
+            const double4_32a JV = make_double4_32a(wshd(IV.x, j), wshd(IV.y, j), wshd(IV.z, j), wshd(IV.w, j));
+            tstep_fp64_j<SYM, true>(J, JV, I, IV, p.eta, j, lane, best, minr2);
+        }
+        coincident = (minr2 == 0.0);
+        return p.eta * best;
+    }
+}
+
+__device__ __forceinline__ void w_kick(WLane &L, bool on, const double (&a)[3], double dt)
+{
+    if (on)
+        for (int c = 0; c < 3; ++c) L.v[c] = __dadd_rn(L.v[c], __dmul_rn(dt, a[c]));
+}
+
+__device__ __forceinline__ void w_drift(WLane &L, bool on, double dt)
+{
+    if (on)
+        for (int c = 0; c < 3; ++c) L.x[c] = __dadd_rn(L.x[c], __dmul_rn(dt, L.v[c]));
+}
+
+template <bool MIXED>
+__device__ void w_fsi(const SubParams &p, WLane &L, unsigned S, double dt, Counts &cnt)
+{
+    if (!S) return;
+    const int lane = threadIdx.x & 31;
+    const bool in = (S >> lane) & 1u;
+    const unsigned src = in ? S : 0u;
+    const unsigned long long ns = (unsigned long long)__popc(S);
+    double a[3], at[3], g[3];
+    float wm;
+    w_acc<MIXED>(p, L, S, src, false, a, wm);
+    w_kick(L, in, a, dt / 6.0);
+    w_drift(L, in, 0.5 * dt);
+    w_acc<MIXED>(p, L, S, src, true, a, wm);
+    w_grad<MIXED>(p, L, S, src, a, MIXED ? 0.25f * wm : INFINITY, g);
+    const double c = dt * dt / 48.0;
+    for (int q = 0; q < 3; ++q) at[q] = a[q] + c * g[q];
+    w_kick(L, in, at, 2.0 * dt / 3.0);
+    w_drift(L, in, 0.5 * dt);
+    w_acc<MIXED>(p, L, S, src, false, a, wm);
+    w_kick(L, in, a, dt / 6.0);
+    if (lane == 0) {
+        cnt.fsi += 1;
+        cnt.acc += 3 * ns * (ns - 1);
+        cnt.grad += ns * (ns - 1);
+    }
+}
+
+template <bool MIXED>
+__device__ void w_kick_sf(const SubParams &p, WLane &L, unsigned S, unsigned F, double cdt, bool gradient,
+                          double tau, Counts &cnt)
+{
+    if (!S || !F) return;
+    const int lane = threadIdx.x & 31;
+    const bool inS = (S >> lane) & 1u, inF = (F >> lane) & 1u;
+    const unsigned src = inS ? F : (inF ? S : 0u);
+    const unsigned U = S | F;
+    const unsigned long long pairs = 2ull * __popc(S) * __popc(F);
+    double a[3];
+    float wm;
+    w_acc<MIXED>(p, L, U, src, gradient, a, wm);
+    if (gradient) {
+        double g[3];
+        w_grad<MIXED>(p, L, U, src, a, MIXED ? 0.25f * wm : INFINITY, g);
+        const double c = tau * tau / 48.0;
+        for (int q = 0; q < 3; ++q) a[q] = a[q] + c * g[q];
+    }
+    w_kick(L, inS || inF, a, cdt);
+    if (lane == 0) {
+        cnt.acc += pairs;
+        if (gradient) cnt.grad += pairs;
+    }
+}
+
+// The subtree of hhs_fsi on the n <= 32 particles Sg[0..n) at depth depth0, run by one warp.
+// Returns 0 or an error bit.
+template <bool MIXED, int SYM>
+__device__ __noinline__ int warp_hhs(const SubParams &p, const int32_t *Sg, int n, double tau0, int depth0,
+                                     Counts &cnt)
+{
+    __shared__ unsigned wf_P[MAXD], wf_S[MAXD];
+    __shared__ double wf_tau[MAXD];
+    __shared__ int wf_depth[MAXD], wf_pc[MAXD];
+    const int lane = threadIdx.x & 31;
+    WLane L;
+    int gi = 0;
+    if (lane < n) {
+        gi = Sg[lane];
+        for (int c = 0; c < 3; ++c) {
+            L.x[c] = p.x[c * p.N + gi];
+            L.v[c] = p.v[c * p.N + gi];
+        }
+        L.m = p.m[gi];
+    } else {
+        // inactive lanes are never in any set; far, massless placeholders
+        for (int c = 0; c < 3; ++c) {
+            L.x[c] = 1.0e18 * (c + 1 + lane);
+            L.v[c] = 0.0;
+        }
+        L.m = 0.0;
+    }
+    const unsigned all = (n >= 32) ? 0xffffffffu : ((1u << n) - 1u);
+    if (lane == 0) {
+        wf_P[0] = all;
+        wf_S[0] = 0u;
+        wf_tau[0] = tau0;
+        wf_depth[0] = depth0;
+        wf_pc[0] = 0;
+    }
+    __syncwarp();
+    int sp = 1, err = 0;
+    while (sp > 0) {
+        const int top = sp - 1;
+        const unsigned P = wf_P[top];
+        const unsigned S = wf_S[top];
+        const double ftau = wf_tau[top];
+        const int depth = wf_depth[top], pc = wf_pc[top];
+        __syncwarp();
+        const unsigned F = P & ~S;
+        if (pc == 0) {
+            if (depth > p.max_depth) {
+                err = ERR_DEPTH;
+                break;
+            }
+            const bool inP = (P >> lane) & 1u;
+            bool coin = false;
+            const double tau = w_tstep<MIXED, SYM>(p, L, P, coin);
+            if (inP && coin) err |= ERR_COINCIDENT;
+            if (inP && !(tau > 0.0)) err |= ERR_NONFINITE;
+            const unsigned Sn = __ballot_sync(0xffffffffu, inP && tau >= ftau) & P;
+            const unsigned Fn = P & ~Sn;
+            if (lane == 0) {
+                const unsigned long long np = (unsigned long long)__popc(P);
+                cnt.hhs += 1;
+                cnt.tstep += np * (np - 1);
+                cnt.maxdepth = max(cnt.maxdepth, depth);
+                const int Lv = min(depth, SUBTREE_STAT_LEVELS - 1);
+                atomicAdd(&p.levels[Lv], 1ull);
+                atomicAdd(&p.levels[SUBTREE_STAT_LEVELS + Lv], np);
+            }
+            w_kick_sf<MIXED>(p, L, Sn, Fn, ftau / 6.0, false, ftau, cnt);
+            w_fsi<MIXED>(p, L, Sn, 0.5 * ftau, cnt);
+            if (lane == 0) {
+                wf_S[top] = Sn;
+                wf_pc[top] = 1;
+            }
+            if (Fn) {
+                if (sp >= MAXD) {
+                    err |= ERR_DEPTH;
+                    break;
+                }
+                if (lane == 0) {
+                    wf_P[sp] = Fn;
+                    wf_S[sp] = 0u;
+                    wf_tau[sp] = 0.5 * ftau;
+                    wf_depth[sp] = depth + 1;
+                    wf_pc[sp] = 0;
+                }
+                sp += 1;
+            }
+        } else if (pc == 1) {
+            w_kick_sf<MIXED>(p, L, S, F, 2.0 * ftau / 3.0, true, ftau, cnt);
+            if (lane == 0) wf_pc[top] = 2;
+            if (F) {
+                if (lane == 0) {
+                    wf_P[sp] = F;
+                    wf_S[sp] = 0u;
+                    wf_tau[sp] = 0.5 * ftau;
+                    wf_depth[sp] = depth + 1;
+                    wf_pc[sp] = 0;
+                }
+                sp += 1;
+            }
+        } else {
+            w_fsi<MIXED>(p, L, S, 0.5 * ftau, cnt);
+            w_kick_sf<MIXED>(p, L, S, F, ftau / 6.0, false, ftau, cnt);
+            sp -= 1;
+        }
+        __syncwarp();
+    }
+    // a lane's error bits count for the whole warp
+    err = __reduce_or_sync(0xffffffffu, err);
+    if (lane < n)
+        for (int c = 0; c < 3; ++c) {
+            p.x[c * p.N + gi] = L.x[c];
+            p.v[c * p.N + gi] = L.v[c];
+        }
+    return err;
+}
+
 // One block: n_steps calls of hhs_fsi(P, tau0) at depth depth0.  Single-set mode: P, n given,
 // workspace from particle 0.  Batch mode (offsets != NULL): block b takes the particles
 // [offsets[b], offsets[b+1]) in order, and the workspace region of those particles.
@@ -406,7 +802,18 @@ __global__ void __launch_bounds__(SB) k_hhs_subtree(SubParams p, SubWork w0, con
             int nS = f_ns[top];
             __syncthreads();  // every thread has read the frame before it changes
             int32_t *S = w.perm + lo;
-            if (pc == 0) {
+            if (pc == 0 && fn <= WARP_N) {
+                // a tiny set: its whole subtree in warp 0, without block barriers
+                if (tid < 32) {
+                    const int e = warp_hhs<MIXED, SYM>(p, S, fn, ftau, depth, cnt);
+                    if (e && tid == 0) {
+                        atomicOr(p.err, e);
+                        if (e & ERR_DEPTH) s_abort = 1;
+                    }
+                }
+                __syncthreads();
+                if (tid == 0) s_sp -= 1;
+            } else if (pc == 0) {
                 if (depth > p.max_depth) {
                     if (tid == 0) {
                         atomicOr(p.err, ERR_DEPTH);

@@ -173,34 +173,122 @@ __global__ void k_check_mass(const double *__restrict__ m, int n, int *__restric
     if (!(m[k] > 0.0) || !isfinite(m[k])) atomicOr(err, ERR_NONFINITE);
 }
 
-// phi_i = sum_{j != i} m_j / sqrt(r^2 + eps2), FP64, j-split partials part[split][i]
-template <int BS, int TJ>
-__global__ void __launch_bounds__(BS) k_potential(const double4_32a *__restrict__ rec, int n,
-                                                  int j_per_split, double eps2,
-                                                  double *__restrict__ part)
+// ---- potential in double-float arithmetic ------------------------------------------------
+// A value is carried as an unevaluated sum of two FP32 numbers (hi, lo) with about 48
+// significant bits, using the error-free transformations TwoSum (Knuth) and TwoProduct by
+// FMA (Dekker's double-length arithmetic).  On this part FP32 issues 64 times faster than
+// FP64, so the O(N^2) potential of the energy diagnostic runs on the FP32 pipe and keeps
+// about 1e-13 relative accuracy per phi_i (positions enter exactly, as three FP32 parts).
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
-    __shared__ double4_32a s0[TJ];
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// x = h + l + ll exactly (three FP32 parts hold the 53 bits of an FP64 value)
+__device__ __forceinline__ void split_f3(double v, float &h, float &l, float &ll)
+{
+    h = (float)v;
+    const double r = v - (double)h;
+    l = (float)r;
+    ll = (float)(r - (double)l);
+}
+
+// records: p0 = {x_h, y_h, z_h, m_h}, p1 = {x_l, y_l, z_l, m_l}, p2 = {x_ll, y_ll, z_ll, 0}
+__global__ void k_pack_pot_df(const double *__restrict__ x, const double *__restrict__ m, int N,
+                              float4 *__restrict__ rec)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float xh, xl, xll, yh, yl, yll, zh, zl, zll;
+    split_f3(x[i], xh, xl, xll);
+    split_f3(x[N + i], yh, yl, yll);
+    split_f3(x[2 * N + i], zh, zl, zll);
+    const double pm = m[i];
+    const float hm = (float)pm;
+    rec[i] = make_float4(xh, yh, zh, hm);
+    rec[N + i] = make_float4(xl, yl, zl, (float)(pm - (double)hm));
+    rec[2 * N + i] = make_float4(xll, yll, zll, 0.f);
+}
+
+// one coordinate of the separation x_j - x_i as a normalised pair (h, l): the differences of
+// the two larger parts are exact (TwoSum), the smallest parts are 2^-48 below the value
+__device__ __forceinline__ void sep_df(float jh, float jl, float jll, float ih, float il, float ill, float &h,
+                                       float &l)
+{
+    float a, e1, b, e2, e4;
+    two_sum(jh, -ih, a, e1);
+    two_sum(jl, -il, b, e2);
+    two_sum(a, b, h, e4);
+    l = e4 + (e1 + (e2 + (jll - ill)));
+}
+
+// phi_i = sum_{j != i} m_j / sqrt(r^2 + eps2) in double-float, j-split partials part[split][i]
+template <int BS, int TJ>
+__global__ void __launch_bounds__(BS) k_potential_df(const float4 *__restrict__ rec, int n,
+                                                     int j_per_split, double eps2,
+                                                     double *__restrict__ part)
+{
+    __shared__ float4 s0[TJ], s1[TJ], s2[TJ];
     const int tid = threadIdx.x;
-    const int ibase = blockIdx.x * BS;
-    const int i = ibase + tid;
-    const double4_32a I = (i < n) ? rec[i] : make_double4_32a(0.0, 0.0, 0.0, 0.0);
-    double phi = 0.0;
+    const int i = blockIdx.x * BS + tid;
+    float4 I0 = make_float4(0.f, 0.f, 0.f, 0.f), I1 = I0, I2 = I0;
+    if (i < n) {
+        I0 = rec[i];
+        I1 = rec[n + i];
+        I2 = rec[2 * n + i];
+    }
+    const float e2h = (float)eps2, e2l = (float)(eps2 - (double)e2h);
+    float H = 0.f, L = 0.f;
     const int jb = blockIdx.y * j_per_split;
     const int je = min(n, jb + j_per_split);
     for (int j0 = jb; j0 < je; j0 += TJ) {
         const int cnt = min(TJ, je - j0);
         __syncthreads();
-        for (int t = tid; t < cnt; t += BS) s0[t] = rec[j0 + t];
+        for (int t = tid; t < cnt; t += BS) {
+            s0[t] = rec[j0 + t];
+            s1[t] = rec[n + j0 + t];
+            s2[t] = rec[2 * n + j0 + t];
+        }
         __syncthreads();
         for (int jj = 0; jj < cnt; ++jj) {
-            const double4_32a J = s0[jj];
-            const double dx = J.x - I.x, dy = J.y - I.y, dz = J.z - I.z;
-            const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
-            const double t = J.w * rsqrt(r2);
-            if (j0 + jj != i) phi += t;
+            const float4 J0 = s0[jj], J1 = s1[jj], J2 = s2[jj];
+            float xh, xl, yh, yl, zh, zl;
+            sep_df(J0.x, J1.x, J2.x, I0.x, I1.x, I2.x, xh, xl);
+            sep_df(J0.y, J1.y, J2.y, I0.y, I1.y, I2.y, yh, yl);
+            sep_df(J0.z, J1.z, J2.z, I0.z, I1.z, I2.z, zh, zl);
+            // r^2 + eps^2: exact squares of the high parts, first-order terms of the low parts
+            // (products feeding an error-free transformation are rounded on their own, __fmul_rn,
+            // so that the compiler cannot contract them into the following add)
+            const float px = __fmul_rn(xh, xh), py = __fmul_rn(yh, yh), pz = __fmul_rn(zh, zh);
+            const float qx = fmaf(xh + xh, xl, fmaf(xh, xh, -px));
+            const float qy = fmaf(yh + yh, yl, fmaf(yh, yh, -py));
+            const float qz = fmaf(zh + zh, zl, fmaf(zh, zh, -pz));
+            float s, t, S, u, S2, u2;
+            two_sum(px, py, s, t);
+            two_sum(s, pz, S, u);
+            two_sum(S, e2h, S2, u2);
+            const float lo = ((t + u) + (u2 + e2l)) + ((qx + qy) + qz);
+            // 1 / r: MUFU estimate y0 and the residual res = 1 - r^2 y0^2 in double-float; then
+            // 1/r = y0 (1 - res)^(-1/2) = y0 (1 + res/2 + 3 res^2/8 + ...), |res| < 2^-21
+            const float y0 = rsqrtf(S2);
+            const float q = __fmul_rn(y0, y0), qe = fmaf(y0, y0, -q);
+            const float pp = __fmul_rn(S2, q), pe = fmaf(S2, q, -pp);
+            const float res = ((1.f - pp) - pe) - fmaf(S2, qe, lo * q);
+            const float c = y0 * res * fmaf(0.375f, res, 0.5f);
+            // m_j / r = (m_h + m_l)(y0 + c)
+            const float w = __fmul_rn(J0.w, y0);
+            const float we = fmaf(J0.w, y0, -w) + fmaf(J0.w, c, J1.w * y0);
+            if (j0 + jj != i) {
+                float e;
+                two_sum(H, w, H, e);
+                L += e + we;
+            }
         }
     }
-    if (i < n) part[(size_t)blockIdx.y * n + i] = phi;
+    if (i < n) part[(size_t)blockIdx.y * n + i] = (double)H + (double)L;
 }
 
 // Per-cluster FP64 energy, momentum and angular momentum: block b reduces cluster
@@ -341,12 +429,13 @@ void launch_identity(cudaStream_t s, int32_t *list, int n)
     k_identity<<<cdiv(n, 256), 256, 0, s>>>(list, n);
 }
 
-void launch_potential(cudaStream_t s, const double4_32a *rec, int n, double eps2, double *part,
-                      const SplitShape &shape)
+void launch_potential(cudaStream_t s, const double *x, const double *m, int n, double eps2, float4 *rec,
+                      double *part, const SplitShape &shape)
 {
     if (n <= 0) return;
+    k_pack_pot_df<<<cdiv(n, 256), 256, 0, s>>>(x, m, n, rec);
     const dim3 grid(shape.nblk_i, shape.nsplit);
-    k_potential<PAIR_BS, PAIR_TJ><<<grid, PAIR_BS, 0, s>>>(rec, n, shape.j_per_split, eps2, part);
+    k_potential_df<PAIR_BS, PAIR_TJ><<<grid, PAIR_BS, 0, s>>>(rec, n, shape.j_per_split, eps2, part);
 }
 
 void launch_aos_to_soa(cudaStream_t s, const double *aos, int n, double *soa, int *err)

@@ -983,15 +983,14 @@ frost_status frost_energy_momentum(frost_ctx *c, double *E_kin, double *E_pot, d
         }
         return FROST_OK;
     }
-    launch_pack_pos_fp64(c->stream, nullptr, c->N, c->x, c->m, c->N, (double4_32a *)c->recA);
-    SplitShape sh = choose_shape(c->N, c->N, PAIR_BS, pair_blocks_per_sm(PASS_ACC, false), c->n_sm);
+    SplitShape sh = choose_shape(c->N, c->N, PAIR_BS, pair_blocks_per_sm(PASS_ACC, true), c->n_sm);
     while ((size_t)sh.nsplit * c->N > c->part_elems && sh.nsplit > 1) {
         const int tiles = (c->N + PAIR_TJ - 1) / PAIR_TJ;
         const int ns = std::max(1, sh.nsplit / 2);
         sh.j_per_split = ((tiles + ns - 1) / ns) * PAIR_TJ;
         sh.nsplit = (c->N + sh.j_per_split - 1) / sh.j_per_split;
     }
-    launch_potential(c->stream, (const double4_32a *)c->recA, c->N, c->eps2, c->part, sh);
+    launch_potential(c->stream, c->x, c->m, c->N, c->eps2, (float4 *)c->recA, c->part, sh);
     launch_energy_reduce(c->stream, c->x, c->v, c->m, c->N, c->part, sh.nsplit, c->dmisc->eres);
     c->st.kernel_launches += 3;
     FROST_CUDA(cudaGetLastError());

@@ -150,10 +150,11 @@ void launch_identity(cudaStream_t s, int32_t *list, int n);
 void launch_aos_to_soa(cudaStream_t s, const double *aos, int n, double *soa, int *err);
 void launch_soa_to_aos(cudaStream_t s, const double *soa, int n, double *aos);
 void launch_check_mass(cudaStream_t s, const double *m, int n, int *err);
-// per-particle potential phi_i = sum_{j != i} m_j / sqrt(r^2 + eps2) in FP64, split
-// partials part[split][i] (summed in order by launch_energy_reduce)
-void launch_potential(cudaStream_t s, const double4_32a *rec, int n, double eps2, double *part,
-                      const SplitShape &shape);
+// per-particle potential phi_i = sum_{j != i} m_j / sqrt(r^2 + eps2) in double-float
+// arithmetic (about 1e-13 relative), split partials part[split][i] (summed in order by
+// launch_energy_reduce); rec: scratch of 48 B per particle
+void launch_potential(cudaStream_t s, const double *x, const double *m, int n, double eps2, float4 *rec,
+                      double *part, const SplitShape &shape);
 // out[0] = T, out[1] = sum_i m_i phi_i, out[2..4] = P, out[5..7] = L (one block, fixed order)
 void launch_energy_reduce(cudaStream_t s, const double *x, const double *v, const double *m,
                           int N, const double *part, int nsplit, double *out);

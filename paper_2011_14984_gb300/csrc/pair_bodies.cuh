@@ -358,13 +358,21 @@ struct TstepMixedI {
     float xh[ILP], yh[ILP], zh[ILP], xl[ILP], yl[ILP], zl[ILP], vx[ILP], vy[ILP], vz[ILP], gm[ILP];
 };
 
-// returns min(tau_ff_sym, tau_fb_sym) / eta for the pair, updates min r^2
+// Pair time-steps without eta: best[k] = min(best[k], tau_ff_sym, tau_fb_sym), minr2[k] =
+// min(minr2[k], r^2).  Every symmetrisation factor obeys s(d) >= 1 / (1 + |d|) (harmonic:
+// q - d <= 2 (1 + |d|); arithmetic: 1 / (1 + |d|/2) and 2 / d; none: 1), so a criterion with
+// t >= 1.001 best (1 + |d|) cannot lower the minimum; it is not symmetrised, and the warp
+// skips the factors (two MUFU sqrt/divide pairs) when no lane needs them.  The 0.1% margin
+// is far above the rounding of the factor, so the result is the one of the full evaluation.
 template <int ILP, int SYM, bool MASK>
 __device__ __forceinline__ void tstep_mixed_j(const float4 J0, const float4 J1, const float4 JV,
                                               const TstepMixedI<ILP> &I, float eta, float eta15,
                                               int jpos, const int (&ipos)[ILP],
                                               float (&best)[ILP], float (&minr2)[ILP])
 {
+    float tff[ILP], tfb[ILP], dff[ILP], dfb[ILP];
+    bool nff[ILP], nfb[ILP];
+    bool any = false;
 #pragma unroll
     for (int k = 0; k < ILP; ++k) {
         const float dx = (J0.x - I.xh[k]) + (J1.x - I.xl[k]);
@@ -377,27 +385,36 @@ __device__ __forceinline__ void tstep_mixed_j(const float4 J0, const float4 J1, 
         const float ri = rsqrtf(r2);
         const float ri2 = ri * ri;
         const float gm = I.gm[k] + JV.w;            // G (m_i + m_j)
-        const float tff = rsqrtf(gm * ri2 * ri);     // (r^3 / (G M))^(1/2)
+        tff[k] = rsqrtf(gm * ri2 * ri);              // (r^3 / (G M))^(1/2)
         const float rvr2 = rv * ri2;                 // r.v / r^2
         const float iv = rsqrtf(v2);                 // 1 / |v|
-        const float tfb = r2 * ri * iv;              // r / |v|
-        const float dff = eta15 * rvr2 * tff;        // eta dt_ff/dt
-        const float dfb = eta * rvr2 * fmaf(gm * ri, iv * iv, 1.f) * tfb;  // eta dt_fb/dt
-        const float tau_ff = tff * symf<SYM>(dff);
-        float tau_fb = tfb * symf<SYM>(dfb);
-        tau_fb = (v2 > 0.f) ? tau_fb : INFINITY;
-        float t = fminf(tau_ff, tau_fb);
+        tfb[k] = r2 * ri * iv;                       // r / |v|
+        dff[k] = eta15 * rvr2 * tff[k];              // eta dt_ff/dt
+        dfb[k] = eta * rvr2 * fmaf(gm * ri, iv * iv, 1.f) * tfb[k];  // eta dt_fb/dt
         float rr = r2;
+        bool self = false;
         if (MASK) {
-            const bool self = (jpos == ipos[k]);
-            t = self ? INFINITY : t;
+            self = (jpos == ipos[k]);
             rr = self ? INFINITY : rr;
         }
-        best[k] = fminf(best[k], t);
         minr2[k] = fminf(minr2[k], rr);
+        const float bnd = 1.001f * best[k];
+        nff[k] = !self && (tff[k] < bnd * (1.f + fabsf(dff[k])));
+        nfb[k] = !self && (v2 > 0.f) && (tfb[k] < bnd * (1.f + fabsf(dfb[k])));
+        any = any || nff[k] || nfb[k];
+    }
+    if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+        for (int k = 0; k < ILP; ++k) {
+            float t = INFINITY;
+            if (nff[k]) t = tff[k] * symf<SYM>(dff[k]);
+            if (nfb[k]) t = fminf(t, tfb[k] * symf<SYM>(dfb[k]));
+            best[k] = fminf(best[k], t);
+        }
     }
 }
 
+// FP64 pair time-steps, with the same bound on the symmetrisation factors
 template <int SYM, bool MASK>
 __device__ __forceinline__ void tstep_fp64_j(const double4_32a J, const double4_32a JV, const double4_32a I,
                                              const double4_32a IV, double eta, int jpos, int ipos,
@@ -413,15 +430,22 @@ __device__ __forceinline__ void tstep_fp64_j(const double4_32a J, const double4_
     const double tff = sqrt(r2 * r / gm);
     const double rvr2 = rv / r2;
     const double dff = eta * 1.5 * rvr2 * tff;
-    double t = tff * symd<SYM>(dff);
+    double tfb = INFINITY, dfb = 0.0;
     if (v2 > 0.0) {
-        const double tfb = r / sqrt(v2);
-        const double dfb = eta * rvr2 * (1.0 + gm / (v2 * r)) * tfb;
-        t = fmin(t, tfb * symd<SYM>(dfb));
+        tfb = r / sqrt(v2);
+        dfb = eta * rvr2 * (1.0 + gm / (v2 * r)) * tfb;
     }
-    if (MASK && jpos == ipos) return;
-    best = fmin(best, t);
-    minr2 = fmin(minr2, r2);
+    const bool self = MASK && jpos == ipos;
+    if (!self) minr2 = fmin(minr2, r2);
+    const double bnd = 1.001 * best;
+    const bool nff = !self && (tff < bnd * (1.0 + fabs(dff)));
+    const bool nfb = !self && (v2 > 0.0) && (tfb < bnd * (1.0 + fabs(dfb)));
+    if (__any_sync(0xffffffffu, nff || nfb)) {
+        double t = INFINITY;
+        if (nff) t = tff * symd<SYM>(dff);
+        if (nfb) t = fmin(t, tfb * symd<SYM>(dfb));
+        best = fmin(best, t);
+    }
 }
 
 

@@ -349,14 +349,17 @@ def test_solar_system_hhs_fsi_on_gpu():
 
 
 def test_energy_momentum_parity():
+    """E, P, L against the oracle; the potential runs in double-float arithmetic on the GPU,
+    so U is also checked where hard binaries (separations down to 1e-5) dominate it."""
     n = 3000
     m, x, v = ics.plummer(n, 77, masses=ics.kroupa_masses(n, 77))
-    for eps in (0.0, 0.01):
-        f = F(m, x, v, eps_soft=eps)
+    mb, xb, vb = ics.plummer_kroupa_binaries(8192, 17)
+    for (mm, xx, vv), eps in (((m, x, v), 0.0), ((m, x, v), 0.01), ((mb, xb, vb), 0.0)):
+        f = F(mm, xx, vv, eps_soft=eps)
         e = f.energy()
-        r = oracle.energy(m, x, v, eps2=eps * eps)
+        r = oracle.energy(mm, xx, vv, eps2=eps * eps)
         assert abs(e["T"] - r["T"]) < 1e-13 * abs(r["T"])
-        assert abs(e["U"] - r["U"]) < 1e-12 * abs(r["U"])
+        assert abs(e["U"] - r["U"]) < 1e-12 * abs(r["U"]), (e["U"], r["U"])
         assert np.max(np.abs(e["P"] - r["P"])) < 1e-15
         assert np.max(np.abs(e["L"] - r["L"])) < 1e-14
         f.close()

@@ -66,6 +66,249 @@ __device__ void b_pack_pos(const SubParams &p, const int32_t *L, int n, void *re
     }
 }
 
+// ---- several threads per active particle (sets of at most MT_MAX) ----------------------
+// For a small active list the one-thread-per-particle bodies leave most of the block idle and
+// run long dependent j-loops.  Here T = SB / pow2ceil(nA) threads (a power of two, at most 32,
+// adjacent lanes of one warp) share particle i = tid / T: lane l of the group takes the
+// sources l, l + T, l + 2T, ... and the group sums its partials with a butterfly of shuffles,
+// which fixes the order (deterministic).  Every thread runs the same number of j-iterations
+// (out-of-range sources are masked as the self pair), as the time-step pairs vote per warp.
+constexpr int MT_MAX = SB;
+
+__device__ __forceinline__ int mt_threads(int nA)
+{
+    int g = 1;
+    while (g < nA) g <<= 1;
+    return max(1, min(32, SB / g));
+}
+
+__device__ __forceinline__ double grp_sum(double v, int T)
+{
+    for (int o = T >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float grp_max(float v, int T)
+{
+    for (int o = T >> 1; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ float grp_min(float v, int T)
+{
+    for (int o = T >> 1; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ double grp_mind(double v, int T)
+{
+    for (int o = T >> 1; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// source index and masking position of iteration q for lane l: sources past the end repeat the
+// last one and are masked as the self pair (jpos == ipos); in a cross pass jpos = -1 otherwise
+struct MtSrc {
+    int j, jpos;
+};
+__device__ __forceinline__ MtSrc mt_src(int q, int T, int l, int nB, int i, bool self)
+{
+    const int j0 = q * T + l;
+    const bool valid = j0 < nB;
+    MtSrc r;
+    r.j = valid ? j0 : nB - 1;
+    r.jpos = valid ? (self ? j0 : -1) : i;
+    return r;
+}
+
+// Newtonian pass (records as in b_acc); out / wout written by lane 0 of each group
+template <bool MIXED>
+__device__ __noinline__ void mt_acc(const SubParams &p, const void *irec, const void *jrec, int nA, int nB, bool self,
+                       bool accurate, double *out, float *wout, int badbit)
+{
+    const int T = mt_threads(nA);
+    const int g = threadIdx.x / T, l = threadIdx.x % T;
+    const bool active = g < nA;
+    const int i = active ? g : 0;
+    const int ipos[1] = {i};
+    const int nq = (nB + T - 1) / T;
+    double r[3];
+    float wm[1] = {0.f};
+    if (MIXED) {
+        const float4 *ir = (const float4 *)irec, *jr = (const float4 *)jrec;
+        const float eps2 = (float)p.eps2;
+        float H[3] = {0.f, 0.f, 0.f}, L[3] = {0.f, 0.f, 0.f};
+        float ax[1] = {0.f}, ay[1] = {0.f}, az[1] = {0.f};
+        int c = 0;
+        if (accurate) {
+            GradMixedI<1> I;
+            const float4 q0 = ir[i], q1 = ir[nA + i], q2 = ir[2 * nA + i];
+            I.xh[0] = q0.x; I.yh[0] = q0.y; I.zh[0] = q0.z;
+            I.xm[0] = q1.x; I.ym[0] = q1.y; I.zm[0] = q1.z;
+            I.xl[0] = q2.x; I.yl[0] = q2.y; I.zl[0] = q2.z;
+            I.ahx[0] = I.ahy[0] = I.ahz[0] = I.alx[0] = I.aly[0] = I.alz[0] = 0.f;
+            for (int q = 0; q < nq; ++q) {
+                const MtSrc s = mt_src(q, T, l, nB, i, self);
+                acc3_mixed_j<1, true>(jr[s.j], jr[nB + s.j], jr[2 * nB + s.j], I, eps2, s.jpos, ipos, ax, ay, az, wm);
+                if (++c == 16) {
+                    fold2(H[0], L[0], ax[0]); fold2(H[1], L[1], ay[0]); fold2(H[2], L[2], az[0]);
+                    ax[0] = ay[0] = az[0] = 0.f;
+                    c = 0;
+                }
+            }
+        } else {
+            AccMixedI<1> I;
+            const float4 q0 = ir[i], q1 = ir[nA + i];
+            I.xh[0] = q0.x; I.yh[0] = q0.y; I.zh[0] = q0.z;
+            I.xl[0] = q1.x; I.yl[0] = q1.y; I.zl[0] = q1.z;
+            for (int q = 0; q < nq; ++q) {
+                const MtSrc s = mt_src(q, T, l, nB, i, self);
+                acc_mixed_j<1, true, false>(jr[s.j], jr[nB + s.j], I, eps2, s.jpos, ipos, ax, ay, az, wm);
+                if (++c == 16) {
+                    fold2(H[0], L[0], ax[0]); fold2(H[1], L[1], ay[0]); fold2(H[2], L[2], az[0]);
+                    ax[0] = ay[0] = az[0] = 0.f;
+                    c = 0;
+                }
+            }
+        }
+        fold2(H[0], L[0], ax[0]); fold2(H[1], L[1], ay[0]); fold2(H[2], L[2], az[0]);
+        for (int k = 0; k < 3; ++k) r[k] = (double)H[k] + (double)L[k];
+    } else {
+        const double4_32a *ir = (const double4_32a *)irec, *jr = (const double4_32a *)jrec;
+        const double4_32a I = ir[i];
+        r[0] = r[1] = r[2] = 0.0;
+        for (int q = 0; q < nq; ++q) {
+            const MtSrc s = mt_src(q, T, l, nB, i, self);
+            acc_fp64_j<true>(jr[s.j], I, p.eps2, s.jpos, i, r[0], r[1], r[2]);
+        }
+    }
+    for (int k = 0; k < 3; ++k) r[k] = grp_sum(r[k], T);
+    const float wmx = grp_max(wm[0], T);
+    if (active && l == 0) {
+        bool ok = true;
+        for (int k = 0; k < 3; ++k) {
+            const double a = p.G * r[k];
+            ok = ok && isfinite(a);
+            out[k * nA + i] = a;
+        }
+        if (wout) wout[i] = wmx;
+        if (!ok) atomicOr(p.err, badbit);
+    }
+}
+
+// gradient pass (records as in b_grad): at[3][nA] = a_A + c 2G sum
+template <bool MIXED>
+__device__ __noinline__ void mt_grad(const SubParams &p, const void *irec, const void *jrec, int nA, int nB, bool self,
+                        const double *aA, const float *wmax, double c, double *at, int badbit)
+{
+    const int T = mt_threads(nA);
+    const int g = threadIdx.x / T, l = threadIdx.x % T;
+    const bool active = g < nA;
+    const int i = active ? g : 0;
+    const int ipos[1] = {i};
+    const int nq = (nB + T - 1) / T;
+    double r[3];
+    if (MIXED) {
+        const float4 *ir = (const float4 *)irec, *jr = (const float4 *)jrec;
+        const float eps2 = (float)p.eps2;
+        GradMixedI<1> I;
+        const float4 q0 = ir[i], q1 = ir[nA + i], q2 = ir[2 * nA + i], q3 = ir[3 * nA + i];
+        I.xh[0] = q0.x; I.yh[0] = q0.y; I.zh[0] = q0.z;
+        I.xm[0] = q1.x; I.ym[0] = q1.y; I.zm[0] = q1.z; I.ahx[0] = q1.w;
+        I.xl[0] = q2.x; I.yl[0] = q2.y; I.zl[0] = q2.z; I.ahy[0] = q2.w;
+        I.ahz[0] = q3.x; I.alx[0] = q3.y; I.aly[0] = q3.z; I.alz[0] = q3.w;
+        const float thr[1] = {wmax ? 0.25f * wmax[i] : INFINITY};
+        BigSlots<1> big;
+        big.n[0] = 0;
+        big.j0[0] = big.j1[0] = big.j2[0] = big.j3[0] = 0;
+        float H[3] = {0.f, 0.f, 0.f}, L[3] = {0.f, 0.f, 0.f};
+        float gx[1] = {0.f}, gy[1] = {0.f}, gz[1] = {0.f};
+        int cnt = 0;
+        for (int q = 0; q < nq; ++q) {
+            const MtSrc s = mt_src(q, T, l, nB, i, self);
+            grad_mixed_j<1, true>(jr[s.j], jr[nB + s.j], jr[2 * nB + s.j], jr[3 * nB + s.j], I, eps2, s.j, s.jpos,
+                                  ipos, thr, big, gx, gy, gz);
+            if (++cnt == 16) {
+                fold2(H[0], L[0], gx[0]); fold2(H[1], L[1], gy[0]); fold2(H[2], L[2], gz[0]);
+                gx[0] = gy[0] = gz[0] = 0.f;
+                cnt = 0;
+            }
+        }
+        fold2(H[0], L[0], gx[0]); fold2(H[1], L[1], gy[0]); fold2(H[2], L[2], gz[0]);
+        double bx = 0.0, by = 0.0, bz = 0.0;
+        for (int t = 0; t < big.n[0]; ++t) {
+            const int j = (t == 0) ? big.j0[0] : (t == 1) ? big.j1[0] : (t == 2) ? big.j2[0] : big.j3[0];
+            grad_term_fp64<1>(jr[j], jr[nB + j], jr[2 * nB + j], jr[3 * nB + j], I, 0, p.eps2, bx, by, bz);
+        }
+        r[0] = ((double)H[0] + (double)L[0]) + bx;
+        r[1] = ((double)H[1] + (double)L[1]) + by;
+        r[2] = ((double)H[2] + (double)L[2]) + bz;
+    } else {
+        const double4_32a *ir = (const double4_32a *)irec, *jr = (const double4_32a *)jrec;
+        const double4_32a I = ir[i], IA = ir[nA + i];
+        r[0] = r[1] = r[2] = 0.0;
+        for (int q = 0; q < nq; ++q) {
+            const MtSrc s = mt_src(q, T, l, nB, i, self);
+            grad_fp64_j<true>(jr[s.j], jr[nB + s.j], I, IA, p.eps2, s.jpos, i, r[0], r[1], r[2]);
+        }
+    }
+    for (int k = 0; k < 3; ++k) r[k] = grp_sum(r[k], T);
+    if (active && l == 0) {
+        bool ok = true;
+        for (int k = 0; k < 3; ++k) {
+            const double v = aA[k * nA + i] + c * (2.0 * p.G * r[k]);
+            ok = ok && isfinite(v);
+            at[k * nA + i] = v;
+        }
+        if (!ok) atomicOr(p.err, badbit);
+    }
+}
+
+// time-step pass of the set (records as in b_tstep): tau[i] = eta min_j (...)
+template <bool MIXED, int SYM>
+__device__ __noinline__ void mt_tstep(const SubParams &p, const void *rec, int n, double *tau)
+{
+    const int T = mt_threads(n);
+    const int g = threadIdx.x / T, l = threadIdx.x % T;
+    const bool active = g < n;
+    const int i = active ? g : 0;
+    const int ipos[1] = {i};
+    const int nq = (n + T - 1) / T;
+    double t;
+    bool coincident;
+    if (MIXED) {
+        const float4 *r = (const float4 *)rec;
+        TstepMixedI<1> I;
+        const float4 a = r[i], b = r[n + i], cc = r[2 * n + i];
+        I.xh[0] = a.x; I.yh[0] = a.y; I.zh[0] = a.z;
+        I.xl[0] = b.x; I.yl[0] = b.y; I.zl[0] = b.z;
+        I.vx[0] = cc.x; I.vy[0] = cc.y; I.vz[0] = cc.z; I.gm[0] = cc.w;
+        const float eta = (float)p.eta, eta15 = 1.5f * eta;
+        float best[1] = {INFINITY}, minr2[1] = {INFINITY};
+        for (int q = 0; q < nq; ++q) {
+            const MtSrc s = mt_src(q, T, l, n, i, true);
+            tstep_mixed_j<1, SYM, true>(r[s.j], r[n + s.j], r[2 * n + s.j], I, eta, eta15, s.jpos, ipos, best, minr2);
+        }
+        t = p.eta * (double)grp_min(best[0], T);
+        coincident = grp_min(minr2[0], T) == 0.f;
+    } else {
+        const double4_32a *r = (const double4_32a *)rec;
+        const double4_32a I = r[i], IV = r[n + i];
+        double best = INFINITY, minr2 = INFINITY;
+        for (int q = 0; q < nq; ++q) {
+            const MtSrc s = mt_src(q, T, l, n, i, true);
+            tstep_fp64_j<SYM, true>(r[s.j], r[n + s.j], I, IV, p.eta, s.jpos, i, best, minr2);
+        }
+        t = p.eta * grp_mind(best, T);
+        coincident = grp_mind(minr2, T) == 0.0;
+    }
+    if (active && l == 0) {
+        tau[i] = t;
+        if (coincident) atomicOr(p.err, ERR_COINCIDENT);
+        if (!(t > 0.0)) atomicOr(p.err, ERR_NONFINITE);
+    }
+}
+
 // Newtonian pass of A against B (self: the same list): out[3][nA] = G sum; wout[nA] =
 // max_j m_j / r^3 when the accurate variant runs (mixed mode, before a gradient pass)
 template <bool MIXED>
@@ -87,7 +330,9 @@ __device__ __noinline__ void b_acc(const SubParams &p, const SubWork &w, const i
     if (!self) b_pack_pos<MIXED>(p, B, nB, w.recB, accurate);
     __syncthreads();
     const int sp = self ? 1 : 0;
-    if (MIXED) {
+    if (nA <= MT_MAX) {
+        mt_acc<MIXED>(p, w.recA, self ? w.recA : w.recB, nA, nB, self, accurate, out, wout, badbit);
+    } else if (MIXED) {
         const float4 *ir = w.recA, *jr = self ? w.recA : w.recB;
         for (int ib = 0; ib < nA; ib += SIB) {
             double res[SILP][3];
@@ -157,7 +402,9 @@ __device__ __noinline__ void b_grad(const SubParams &p, const SubWork &w, const 
     const int sp = self ? 1 : 0;
     const double c = eps_grad * eps_grad / 48.0;
     const double scale = 2.0 * p.G;
-    if (MIXED) {
+    if (nA <= MT_MAX) {
+        mt_grad<MIXED>(p, w.recA, self ? w.recA : w.recB, nA, nB, self, aA, MIXED ? wmax : nullptr, c, at, badbit);
+    } else if (MIXED) {
         const float4 *ir = w.recA, *jr = self ? w.recA : w.recB;
         for (int ib = 0; ib < nA; ib += SIB) {
             double res[SILP][3];
@@ -213,7 +460,9 @@ __device__ __noinline__ void b_tstep(const SubParams &p, const SubWork &w, const
         else pack_tstep_fp64_one(k, P, n, p.x, p.v, p.m, p.N, p.G, (double4_32a *)w.recA);
     }
     __syncthreads();
-    if (MIXED) {
+    if (n <= MT_MAX) {
+        mt_tstep<MIXED, SYM>(p, w.recA, n, tau);
+    } else if (MIXED) {
         for (int ib = 0; ib < n; ib += SIB) {
             float best[SILP], minr2[SILP];
             tstep_mixed_body<SB, SILP, STJ, SYM>(w.recA, w.recA, n, n, ib, 0, n, 1, (float)p.eta, best, minr2);

@@ -2,6 +2,7 @@
 //   kick / drift (Sec. 5.3), the stable slow/fast partition (Sec. 3.1), index-list
 //   validation, and the FP64 energy / momentum / angular-momentum reductions (Sec. 2.3).
 #include "frost_internal.cuh"
+#include "pair_bodies.cuh"
 
 #include <cmath>
 
@@ -42,6 +43,22 @@ __global__ void k_drift(const int32_t *__restrict__ list, int n, double *__restr
     x[i] = __dadd_rn(x[i], __dmul_rn(dt, v[i]));
     x[N + i] = __dadd_rn(x[N + i], __dmul_rn(dt, v[N + i]));
     x[2 * N + i] = __dadd_rn(x[2 * N + i], __dmul_rn(dt, v[2 * N + i]));
+}
+
+// drift, then the position record of the moved particle for the next Newtonian pass
+__global__ void k_drift_pack(const int32_t *__restrict__ list, int n, double *__restrict__ x,
+                             const double *__restrict__ v, const double *__restrict__ m, int N, double dt,
+                             void *__restrict__ rec, int mode)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int i = list ? list[k] : k;
+    x[i] = __dadd_rn(x[i], __dmul_rn(dt, v[i]));
+    x[N + i] = __dadd_rn(x[N + i], __dmul_rn(dt, v[N + i]));
+    x[2 * N + i] = __dadd_rn(x[2 * N + i], __dmul_rn(dt, v[2 * N + i]));
+    if (mode == 0) dev::pack_pos_mixed_one(k, list, n, x, m, N, (float4 *)rec);
+    else if (mode == 1) dev::pack_grad_mixed_one(k, list, n, x, m, N, nullptr, (float4 *)rec);
+    else dev::pack_pos_fp64_one(k, list, n, x, m, N, (double4_32a *)rec);
 }
 
 // Stable partition by one block of 1024 threads: chunks of 1024 entries, slow ranks from a
@@ -398,6 +415,13 @@ void launch_drift(cudaStream_t s, const int32_t *list, int n, double *x, const d
 {
     if (n <= 0) return;
     k_drift<<<cdiv(n, 256), 256, 0, s>>>(list, n, x, v, N, dt);
+}
+
+void launch_drift_pack(cudaStream_t s, const int32_t *list, int n, double *x, const double *v,
+                       const double *m, int N, double dt, void *rec, int mode)
+{
+    if (n <= 0) return;
+    k_drift_pack<<<cdiv(n, 256), 256, 0, s>>>(list, n, x, v, m, N, dt, rec, mode);
 }
 
 void launch_partition(cudaStream_t s, const int32_t *set, int n, const double *tau, double pivot,

@@ -232,9 +232,12 @@ int badbit(const frost_ctx *c) { return c->eps2 == 0.0 ? ERR_COINCIDENT : ERR_NO
 // ([3][nA]) and, if given, out_aos ([nA][3]).  With wmax (mixed mode), also the weight
 // max_j m_j / r^3 of each particle's dominant term, which the following gradient pass uses.
 // With hist (mixed mode, with wmax): the |a| histogram of the pass is added to hist (zeroed by
-// the caller) for the hot-source classification of refine_hot.
+// the caller) for the hot-source classification of refine_hot.  kick: the kick of A by the
+// result, fused into the finalisation.  irec / jrec: records already packed by the caller
+// (NULL: packed here into recA / recB).
 void pass_acc(frost_ctx *c, const int32_t *A, int nA, const int32_t *B, int nB, bool self,
-              double *out_soa, double *out_aos, float *wmax = nullptr, unsigned *hist = nullptr)
+              double *out_soa, double *out_aos, float *wmax = nullptr, unsigned *hist = nullptr,
+              KickArgs kick = KickArgs(), const void *irec = nullptr, const void *jrec = nullptr)
 {
     if (nA <= 0) return;
     if (nB <= 0 || (self && nA == 1)) {
@@ -242,12 +245,15 @@ void pass_acc(frost_ctx *c, const int32_t *A, int nA, const int32_t *B, int nB, 
         if (out_aos) cudaMemsetAsync(out_aos, 0, sizeof(double) * 3 * nA, c->stream);
         if (wmax) cudaMemsetAsync(wmax, 0, sizeof(float) * nA, c->stream);
         if (hist && c->mixed && out_soa) launch_acc_hist(c->stream, out_soa, nA, hist);
+        if (kick.v && out_soa) launch_kick(c->stream, kick.list, nA, kick.v, kick.N, out_soa, kick.dt);
         return;
     }
     // before a gradient pass (wmax requested) the mixed mode uses the accurate variant on the
     // three-way split records
     const bool accurate = c->mixed && wmax;
-    if (accurate) {
+    if (irec) {
+        // packed by the caller
+    } else if (accurate) {
         launch_pack_grad_mixed(c->stream, A, nA, c->x, c->m, c->N, nullptr, (float4 *)c->recA);
         if (!self) launch_pack_grad_mixed(c->stream, B, nB, c->x, c->m, c->N, nullptr, (float4 *)c->recB);
         c->st.kernel_launches += self ? 1 : 2;
@@ -256,8 +262,8 @@ void pass_acc(frost_ctx *c, const int32_t *A, int nA, const int32_t *B, int nB, 
         if (!self) pack_pos(c, B, nB, c->recB);
     }
     PairArgs a;
-    a.irec = c->recA;
-    a.jrec = self ? c->recA : c->recB;
+    a.irec = irec ? irec : c->recA;
+    a.jrec = irec ? jrec : (self ? c->recA : c->recB);
     a.n_a = nA;
     a.n_s = nB;
     a.self_pass = self ? 1 : 0;
@@ -272,7 +278,7 @@ void pass_acc(frost_ctx *c, const int32_t *A, int nA, const int32_t *B, int nB, 
         launch_acc(c->stream, c->mixed, a);
     }
     launch_finalize_vec(c->stream, c->part, a.shape.nsplit, nA, c->G, out_soa, out_aos, a.wpart,
-                        a.wpart ? wmax : nullptr, &c->dmisc->err, badbit(c));
+                        a.wpart ? wmax : nullptr, &c->dmisc->err, badbit(c), kick);
     c->st.kernel_launches += 2;
     c->st.acc_pairs += pairs;
     if (accurate && hist && out_soa) {
@@ -309,9 +315,12 @@ unsigned *zero_hists(frost_ctx *c)
 // gradient of A against B with a_A (soa [3][nA]) and a_B (soa [3][nB]); writes
 // a~ = a_A + eps^2/48 g to at_soa / at_aos and g to g_aos (each optional).  wmax: the
 // dominant-term weights of A from the Newtonian pass at the same positions (mixed mode).
+// kick: the kick of A by a~, fused into the finalisation.  irec / jrec: gradient records
+// already packed by the caller (the source records with the hot masses zeroed).
 void pass_grad(frost_ctx *c, const int32_t *A, int nA, const double *aA, const int32_t *B, int nB,
                const double *aB, bool self, double eps_grad, double *at_soa, double *at_aos,
-               double *g_aos, const float *wmax, const uint32_t *hotB = nullptr)
+               double *g_aos, const float *wmax, const uint32_t *hotB = nullptr,
+               KickArgs kick = KickArgs(), const void *irec = nullptr, const void *jrec = nullptr)
 {
     if (nA <= 0) return;
     const double cgrad = eps_grad * eps_grad / 48.0;
@@ -320,10 +329,13 @@ void pass_grad(frost_ctx *c, const int32_t *A, int nA, const double *aA, const i
         if (at_soa) cudaMemcpyAsync(at_soa, aA, sizeof(double) * 3 * nA, cudaMemcpyDeviceToDevice, c->stream);
         if (at_aos) launch_soa_to_aos(c->stream, aA, nA, at_aos);
         if (g_aos) cudaMemsetAsync(g_aos, 0, sizeof(double) * 3 * nA, c->stream);
+        if (kick.v) launch_kick(c->stream, kick.list, nA, kick.v, kick.N, aA, kick.dt);
         return;
     }
     if (!c->mixed) hotB = nullptr;
-    if (c->mixed) {
+    if (irec) {
+        // packed by the caller
+    } else if (c->mixed) {
         // hot sources: masses zeroed in the FP32 source records, their terms summed in FP64 below
         launch_pack_grad_mixed(c->stream, A, nA, c->x, c->m, c->N, aA, (float4 *)c->recA,
                                self ? hotB : nullptr);
@@ -332,10 +344,10 @@ void pass_grad(frost_ctx *c, const int32_t *A, int nA, const double *aA, const i
         launch_pack_grad_fp64(c->stream, A, nA, c->x, c->m, c->N, aA, (double4_32a *)c->recA);
         if (!self) launch_pack_grad_fp64(c->stream, B, nB, c->x, c->m, c->N, aB, (double4_32a *)c->recB);
     }
-    c->st.kernel_launches += self ? 1 : 2;
+    if (!irec) c->st.kernel_launches += self ? 1 : 2;
     PairArgs a;
-    a.irec = c->recA;
-    a.jrec = self ? c->recA : c->recB;
+    a.irec = irec ? irec : c->recA;
+    a.jrec = irec ? jrec : (self ? c->recA : c->recB);
     a.n_a = nA;
     a.n_s = nB;
     a.self_pass = self ? 1 : 0;
@@ -357,7 +369,7 @@ void pass_grad(frost_ctx *c, const int32_t *A, int nA, const double *aA, const i
         c->st.kernel_launches += 1;
     }
     launch_finalize_grad(c->stream, c->part, a.shape.nsplit, nA, 2.0 * c->G, aA, cgrad, at_soa,
-                         at_aos, g_aos, &c->dmisc->err, badbit(c), c->part_hot, ns_hot);
+                         at_aos, g_aos, &c->dmisc->err, badbit(c), c->part_hot, ns_hot, kick);
     c->st.kernel_launches += 2;
     c->st.grad_pairs += pairs;
 }
@@ -395,13 +407,6 @@ void pass_tstep(frost_ctx *c, const int32_t *P, int nP, double *tau)
 
 // ---- integrator -----------------------------------------------------------------------
 
-void kick(frost_ctx *c, const int32_t *L, int n, const double *a_soa, double dt)
-{
-    if (n <= 0) return;
-    launch_kick(c->stream, L, n, c->v, c->N, a_soa, dt);
-    c->st.kernel_launches += 1;
-}
-
 void drift(frost_ctx *c, const int32_t *L, int n, double dt)
 {
     if (n <= 0) return;
@@ -410,51 +415,96 @@ void drift(frost_ctx *c, const int32_t *L, int n, double dt)
 }
 
 // Algorithm fsi on the set S with step dt
+KickArgs kick_of(frost_ctx *c, const int32_t *L, double dt)
+{
+    KickArgs k;
+    k.list = L;
+    k.v = c->v;
+    k.N = c->N;
+    k.dt = dt;
+    return k;
+}
+
+// drift of L, writing the position records of the Newtonian pass that follows into rec
+void drift_pack(frost_ctx *c, const int32_t *L, int n, double dt, void *rec, bool accurate)
+{
+    if (n <= 0) return;
+    launch_drift_pack(c->stream, L, n, c->x, c->v, c->m, c->N, dt, rec, c->mixed ? (accurate ? 1 : 0) : 2);
+    c->st.kernel_launches += 1;
+}
+
+// position records of L for a Newtonian pass (accurate: the three-way split of the mixed pass
+// that feeds a gradient)
+void pack_acc(frost_ctx *c, const int32_t *L, int n, void *rec, bool accurate)
+{
+    if (n <= 0) return;
+    if (c->mixed && accurate) {
+        launch_pack_grad_mixed(c->stream, L, n, c->x, c->m, c->N, nullptr, (float4 *)rec);
+        c->st.kernel_launches += 1;
+    } else {
+        pack_pos(c, L, n, rec);
+    }
+}
+
+// gradient records of L with accelerations a ([3][n]); mixed mode: masses of the hot
+// particles (mask) zeroed, their terms are summed in FP64
+void pack_grad(frost_ctx *c, const int32_t *L, int n, const double *a, void *rec, const uint32_t *mask)
+{
+    if (n <= 0) return;
+    if (c->mixed) launch_pack_grad_mixed(c->stream, L, n, c->x, c->m, c->N, a, (float4 *)rec, mask);
+    else launch_pack_grad_fp64(c->stream, L, n, c->x, c->m, c->N, a, (double4_32a *)rec);
+    c->st.kernel_launches += 1;
+}
+
+// Algorithm fsi on the set S with step dt.  Each kick is fused into the finalisation of the
+// pass that produces its accelerations, and each drift writes the records of the next pass.
 void fsi(frost_ctx *c, const int32_t *S, int nS, double dt)
 {
     if (nS <= 0) return;
     c->st.fsi_calls += 1;
-    pass_acc(c, S, nS, S, nS, true, c->aA, nullptr);
-    kick(c, S, nS, c->aA, dt / 6.0);
-    drift(c, S, nS, 0.5 * dt);
+    pass_acc(c, S, nS, S, nS, true, c->aA, nullptr, nullptr, nullptr, kick_of(c, S, dt / 6.0));
+    drift_pack(c, S, nS, 0.5 * dt, c->recA, true);
     if (c->mixed) {
         unsigned *h = zero_hists(c);
-        pass_acc(c, S, nS, S, nS, true, c->aA, nullptr, c->wA, h);
+        pass_acc(c, S, nS, S, nS, true, c->aA, nullptr, c->wA, h, KickArgs(), c->recA, c->recA);
         refine_hot(c, c->recA, c->recA, S, nS, S, nS, true, c->aA, nullptr, c->wA, h, nullptr, 0, c->hA);
     } else {
-        pass_acc(c, S, nS, S, nS, true, c->aA, nullptr, c->wA);
+        pass_acc(c, S, nS, S, nS, true, c->aA, nullptr, c->wA, nullptr, KickArgs(), c->recA, c->recA);
     }
-    pass_grad(c, S, nS, c->aA, S, nS, c->aA, true, dt, c->atA, nullptr, nullptr, c->wA, c->hA);
-    kick(c, S, nS, c->atA, 2.0 * dt / 3.0);
-    drift(c, S, nS, 0.5 * dt);
-    pass_acc(c, S, nS, S, nS, true, c->aA, nullptr);
-    kick(c, S, nS, c->aA, dt / 6.0);
+    pass_grad(c, S, nS, c->aA, S, nS, c->aA, true, dt, c->atA, nullptr, nullptr, c->wA, c->hA,
+              kick_of(c, S, 2.0 * dt / 3.0));
+    drift_pack(c, S, nS, 0.5 * dt, c->recA, false);
+    pass_acc(c, S, nS, S, nS, true, c->aA, nullptr, nullptr, nullptr, kick_of(c, S, dt / 6.0), c->recA, c->recA);
 }
 
-// kick_sf: S kicked by its accelerations due to F, F by those due to S (computed first)
+// kick_sf: S kicked by its accelerations due to F, F by those due to S.  Accelerations depend
+// on positions only, so each list's kick is fused into its own pass; both lists are packed
+// once (S in recA, F in recB) for the two directions.
 void kick_sf(frost_ctx *c, const int32_t *S, int nS, const int32_t *F, int nF, double cdt,
              bool gradient, double tau_pivot)
 {
     if (nS <= 0 || nF <= 0) return;
-    unsigned *h = (gradient && c->mixed) ? zero_hists(c) : nullptr;
-    pass_acc(c, S, nS, F, nF, false, c->aA, nullptr, gradient ? c->wA : nullptr, h);
-    pass_acc(c, F, nF, S, nS, false, c->aB, nullptr, gradient ? c->wB : nullptr, h ? h + HOT_BINS : nullptr);
-    if (gradient) {
-        if (h) {
-            // the records of the last pass: recA = F, recB = S (three-way split positions)
-            refine_hot(c, c->recB, c->recA, S, nS, F, nF, false, c->aA, nullptr, c->wA, h, h + HOT_BINS, nF,
-                       c->hA);
-            refine_hot(c, c->recA, c->recB, F, nF, S, nS, false, c->aB, nullptr, c->wB, h + HOT_BINS, h, nS,
-                       c->hB);
-        }
-        pass_grad(c, S, nS, c->aA, F, nF, c->aB, false, tau_pivot, c->atA, nullptr, nullptr, c->wA, c->hB);
-        pass_grad(c, F, nF, c->aB, S, nS, c->aA, false, tau_pivot, c->atB, nullptr, nullptr, c->wB, c->hA);
-        kick(c, S, nS, c->atA, cdt);
-        kick(c, F, nF, c->atB, cdt);
-    } else {
-        kick(c, S, nS, c->aA, cdt);
-        kick(c, F, nF, c->aB, cdt);
+    pack_acc(c, S, nS, c->recA, gradient);
+    pack_acc(c, F, nF, c->recB, gradient);
+    if (!gradient) {
+        pass_acc(c, S, nS, F, nF, false, c->aA, nullptr, nullptr, nullptr, kick_of(c, S, cdt), c->recA, c->recB);
+        pass_acc(c, F, nF, S, nS, false, c->aB, nullptr, nullptr, nullptr, kick_of(c, F, cdt), c->recB, c->recA);
+        return;
     }
+    unsigned *h = c->mixed ? zero_hists(c) : nullptr;
+    pass_acc(c, S, nS, F, nF, false, c->aA, nullptr, c->wA, h, KickArgs(), c->recA, c->recB);
+    pass_acc(c, F, nF, S, nS, false, c->aB, nullptr, c->wB, h ? h + HOT_BINS : nullptr, KickArgs(), c->recB,
+             c->recA);
+    if (h) {
+        refine_hot(c, c->recA, c->recB, S, nS, F, nF, false, c->aA, nullptr, c->wA, h, h + HOT_BINS, nF, c->hA);
+        refine_hot(c, c->recB, c->recA, F, nF, S, nS, false, c->aB, nullptr, c->wB, h + HOT_BINS, h, nS, c->hB);
+    }
+    pack_grad(c, S, nS, c->aA, c->recA, c->mixed ? c->hA : nullptr);
+    pack_grad(c, F, nF, c->aB, c->recB, c->mixed ? c->hB : nullptr);
+    pass_grad(c, S, nS, c->aA, F, nF, c->aB, false, tau_pivot, c->atA, nullptr, nullptr, c->wA, c->hB,
+              kick_of(c, S, cdt), c->recA, c->recB);
+    pass_grad(c, F, nF, c->aB, S, nS, c->aA, false, tau_pivot, c->atB, nullptr, nullptr, c->wB, c->hA,
+              kick_of(c, F, cdt), c->recB, c->recA);
 }
 
 frost_status ensure_level(frost_ctx *c, int depth)

@@ -90,17 +90,26 @@ void launch_grad(cudaStream_t s, bool mixed, const PairArgs &a);
 void launch_tstep(cudaStream_t s, bool mixed, const PairArgs &a, double eta, int sym, int *err);
 
 // ---- finalisation of split partials ---------------------------------------------------
+// Optional kick fused into a finalisation: v[c][list[i]] += dt * (the value written for i),
+// with the separate roundings of launch_kick (v = NULL: no kick; list = NULL: identity).
+struct KickArgs {
+    const int32_t *list = nullptr;
+    double *v = nullptr;
+    int N = 0;
+    double dt = 0.0;
+};
+
 // out_soa[c][i] = scale * sum_split part[split][c][i]  (also [i][3] copy if out_aos != NULL);
 // with wpart, wmax[i] = max_split wpart[split][i]
 void launch_finalize_vec(cudaStream_t s, const double *part, int nsplit, int n, double scale,
                          double *out_soa, double *out_aos, const float *wpart, float *wmax,
-                         int *err, int coincident_bit);
+                         int *err, int coincident_bit, KickArgs kick = KickArgs());
 // a~ = a + c g with g = scale * (sum part + sum part2); writes a~ (soa and/or aos) and g
 // (aos, optional); part2 (nsplit2 splits, may be 0) holds the FP64 terms of hot sources
 void launch_finalize_grad(cudaStream_t s, const double *part, int nsplit, int n, double scale,
                           const double *a_soa, double c, double *at_soa, double *at_aos,
                           double *g_aos, int *err, int coincident_bit,
-                          const double *part2 = nullptr, int nsplit2 = 0);
+                          const double *part2 = nullptr, int nsplit2 = 0, KickArgs kick = KickArgs());
 
 // ---- hot sources of the mixed gradient pass (hot_kernels.cu) -------------------------
 constexpr int HOT_BINS = 1024;          // |a| histogram: 4 bins per octave
@@ -134,6 +143,10 @@ void launch_kick_aos(cudaStream_t s, const int32_t *list, int n, double *v, int 
                      const double *a_aos, double dt);
 void launch_drift(cudaStream_t s, const int32_t *list, int n, double *x, const double *v,
                   int N, double dt);
+// drift, then pack the moved particles' position records for the next Newtonian pass:
+// mode 0 mixed {hi, lo} records, 1 mixed three-way split records (accurate pass), 2 FP64
+void launch_drift_pack(cudaStream_t s, const int32_t *list, int n, double *x, const double *v,
+                       const double *m, int N, double dt, void *rec, int mode);
 // stable partition: S gets set[k] with tau[k] >= pivot, F the rest; counts[0] = |S|,
 // counts[1] = |F|
 void launch_partition(cudaStream_t s, const int32_t *set, int n, const double *tau,

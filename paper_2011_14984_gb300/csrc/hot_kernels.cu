@@ -45,7 +45,9 @@ __device__ float median_edge(const unsigned *__restrict__ hist, int n)
 {
     const int lane = threadIdx.x & 31;
     unsigned s = 0;
-    for (int q = 0; q < 32; ++q) s += hist[lane * 32 + q];
+    // lane sums its 32 bins in a rotated order, so that a histogram in shared memory is read
+    // without bank conflicts
+    for (int q = 0; q < 32; ++q) s += hist[lane * 32 + ((q + lane) & 31)];
     unsigned incl = s;
     for (int o = 1; o < 32; o <<= 1) {
         const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
@@ -132,14 +134,93 @@ __global__ void __launch_bounds__(HOT_BS) k_acc_hist(const double *__restrict__ 
         if (sh[b]) atomicAdd(&hist[b], sh[b]);
 }
 
+// position within the block (0..HOT_BS) of the q-th set bit of the block's mask words
+__device__ __forceinline__ int nth_hot(const unsigned *words, int q)
+{
+    for (int w = 0; w < HOT_BS / 32; ++w) {
+        const unsigned bits = words[w];
+        const int c = __popc(bits);
+        if (q < c) {
+            unsigned b = bits;
+            for (int k = 0; k < q; ++k) b &= b - 1u;
+            return w * 32 + __ffs(b) - 1;
+        }
+        q -= c;
+    }
+    return 0;
+}
+
+// one thread's share of the refined acceleration of target t: the sources j0, j0 + dj, ...;
+// FP32 pair terms on the three-way split records, except up to GRAD_SLOTS terms with
+// m_j / r^3 > thr, which are evaluated in FP64 from the particle store
+__device__ void refine_partial(int t, int j0, int dj, const float4 *__restrict__ irec,
+                               const float4 *__restrict__ jrec, int n_a, int n_s, int self_pass,
+                               const int32_t *__restrict__ Alist, const int32_t *__restrict__ Blist,
+                               const double *__restrict__ x, const double *__restrict__ m, int N,
+                               double eps2d, float thr, double (&r)[3])
+{
+    const float eps2 = (float)eps2d;
+    const float4 q0 = irec[t], q1 = irec[n_a + t], q2 = irec[2 * n_a + t];
+    int nb = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+    float H[3] = {0.f, 0.f, 0.f}, L[3] = {0.f, 0.f, 0.f}, s[3] = {0.f, 0.f, 0.f};
+    int cnt = 0;
+    for (int j = j0; j < n_s; j += dj) {
+        if (self_pass && j == t) continue;
+        const float4 J0 = jrec[j], J1 = jrec[n_s + j], J2 = jrec[2 * n_s + j];
+        const float dx = ((J0.x - q0.x) + (J1.x - q1.x)) + (J2.x - q2.x);
+        const float dy = ((J0.y - q0.y) + (J1.y - q1.y)) + (J2.y - q2.y);
+        const float dz = ((J0.z - q0.z) + (J1.z - q1.z)) + (J2.z - q2.z);
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+        float y = rsqrtf(r2);
+        const float hy = (0.5f * r2) * y;
+        y = fmaf(y, fmaf(-hy, y, 0.5f), y);
+        const float wt = J0.w * y * (y * y);
+        if (wt > thr && nb < GRAD_SLOTS) {
+            if (nb == 0) b0 = j;
+            else if (nb == 1) b1 = j;
+            else if (nb == 2) b2 = j;
+            else b3 = j;
+            ++nb;
+            continue;
+        }
+        s[0] = fmaf(wt, dx, s[0]);
+        s[1] = fmaf(wt, dy, s[1]);
+        s[2] = fmaf(wt, dz, s[2]);
+        if (++cnt == 16) {
+            for (int c = 0; c < 3; ++c) {
+                fold2(H[c], L[c], s[c]);
+                s[c] = 0.f;
+            }
+            cnt = 0;
+        }
+    }
+    for (int c = 0; c < 3; ++c) {
+        fold2(H[c], L[c], s[c]);
+        r[c] = (double)H[c] + (double)L[c];
+    }
+    const int gi = Alist ? Alist[t] : t;
+    const double xi = x[gi], yi = x[N + gi], zi = x[2 * N + gi];
+    for (int q = 0; q < nb; ++q) {
+        const int j = (q == 0) ? b0 : (q == 1) ? b1 : (q == 2) ? b2 : b3;
+        const int gj = Blist ? Blist[j] : j;
+        const double ddx = x[gj] - xi, ddy = x[N + gj] - yi, ddz = x[2 * N + gj] - zi;
+        const double rr2 = fma(ddx, ddx, fma(ddy, ddy, fma(ddz, ddz, eps2d)));
+        const double ri = rsqrt(rr2);
+        const double ww = m[gj] * (ri * ri * ri);
+        r[0] = fma(ww, ddx, r[0]);
+        r[1] = fma(ww, ddy, r[1]);
+        r[2] = fma(ww, ddz, r[2]);
+    }
+}
+
 // Marks the hot particles of a finished accurate Newtonian pass of A against B (mask bit k of
 // word k / 32) and recomputes their accelerations: FP32 pair terms on the three-way split
 // records of that pass, except up to GRAD_SLOTS terms per thread with m_j / r^3 above
 // wmax_k / 4, which are evaluated in FP64 from the particle store.  The threshold is
 // HOT_KAPPA x the larger median edge of hist (n_a values of this pass) and hist2 (n2 values
-// of the companion pass of B against A, or NULL).  One block per 256 particles; each hot
-// particle of the block is refined by the whole block, and the block sum runs in a fixed
-// order.
+// of the companion pass of B against A, or NULL).  One block per 256 particles: with at most
+// two hot particles the whole block refines each, otherwise one warp per hot particle; the
+// sums run in a fixed order either way.
 __global__ void __launch_bounds__(HOT_BS) k_acc_refine(
     const float4 *__restrict__ irec, const float4 *__restrict__ jrec, int n_a, int n_s, int self_pass,
     const int32_t *__restrict__ Alist, const int32_t *__restrict__ Blist, const double *__restrict__ x,
@@ -149,10 +230,17 @@ __global__ void __launch_bounds__(HOT_BS) k_acc_refine(
 {
     __shared__ float s_thr;
     __shared__ unsigned s_words[HOT_BS / 32];
+    __shared__ unsigned s_hist[2][HOT_BINS];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool two = hist2 && n2 > 0;
+    for (int b = tid; b < HOT_BINS; b += HOT_BS) {
+        s_hist[0][b] = hist[b];
+        if (two) s_hist[1][b] = hist2[b];
+    }
+    __syncthreads();
     if (warp == 0) {
-        float e = median_edge(hist, n_a);
-        if (hist2 && n2 > 0) e = fmaxf(e, median_edge(hist2, n2));
+        float e = median_edge(s_hist[0], n_a);
+        if (two) e = fmaxf(e, median_edge(s_hist[1], n2));
         if (lane == 0) s_thr = HOT_KAPPA * e;
     }
     __syncthreads();
@@ -166,67 +254,15 @@ __global__ void __launch_bounds__(HOT_BS) k_acc_refine(
         if (base + warp * 32 < n_a) mask[(base >> 5) + warp] = word;
     }
     __syncthreads();
-    const float eps2 = (float)eps2d;
-    for (int w = 0; w < HOT_BS / 32; ++w) {
-        unsigned bits = s_words[w];
-        while (bits) {
-            const int b = __ffs(bits) - 1;
-            bits &= bits - 1u;
-            const int t = base + w * 32 + b;
-            const float4 q0 = irec[t], q1 = irec[n_a + t], q2 = irec[2 * n_a + t];
-            const float thr = 0.25f * wmax[t];
-            int nb = 0, j0 = 0, j1 = 0, j2 = 0, j3 = 0;
-            float H[3] = {0.f, 0.f, 0.f}, L[3] = {0.f, 0.f, 0.f}, s[3] = {0.f, 0.f, 0.f};
-            int cnt = 0;
-            for (int j = tid; j < n_s; j += HOT_BS) {
-                if (self_pass && j == t) continue;
-                const float4 J0 = jrec[j], J1 = jrec[n_s + j], J2 = jrec[2 * n_s + j];
-                const float dx = ((J0.x - q0.x) + (J1.x - q1.x)) + (J2.x - q2.x);
-                const float dy = ((J0.y - q0.y) + (J1.y - q1.y)) + (J2.y - q2.y);
-                const float dz = ((J0.z - q0.z) + (J1.z - q1.z)) + (J2.z - q2.z);
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-                float y = rsqrtf(r2);
-                const float hy = (0.5f * r2) * y;
-                y = fmaf(y, fmaf(-hy, y, 0.5f), y);
-                const float wt = J0.w * y * (y * y);
-                if (wt > thr && nb < GRAD_SLOTS) {
-                    if (nb == 0) j0 = j;
-                    else if (nb == 1) j1 = j;
-                    else if (nb == 2) j2 = j;
-                    else j3 = j;
-                    ++nb;
-                    continue;
-                }
-                s[0] = fmaf(wt, dx, s[0]);
-                s[1] = fmaf(wt, dy, s[1]);
-                s[2] = fmaf(wt, dz, s[2]);
-                if (++cnt == 16) {
-                    for (int c = 0; c < 3; ++c) {
-                        fold2(H[c], L[c], s[c]);
-                        s[c] = 0.f;
-                    }
-                    cnt = 0;
-                }
-            }
+    int nhot = 0;
+    for (int w = 0; w < HOT_BS / 32; ++w) nhot += __popc(s_words[w]);
+    if (nhot <= 2) {
+        // few targets: each one by the whole block
+        for (int q = 0; q < nhot; ++q) {
+            const int t = base + nth_hot(s_words, q);
             double r[3];
-            for (int c = 0; c < 3; ++c) {
-                fold2(H[c], L[c], s[c]);
-                r[c] = (double)H[c] + (double)L[c];
-            }
-            // the dominant terms in FP64 from the particle store
-            const int gi = Alist ? Alist[t] : t;
-            const double xi = x[gi], yi = x[N + gi], zi = x[2 * N + gi];
-            for (int q = 0; q < nb; ++q) {
-                const int j = (q == 0) ? j0 : (q == 1) ? j1 : (q == 2) ? j2 : j3;
-                const int gj = Blist ? Blist[j] : j;
-                const double ddx = x[gj] - xi, ddy = x[N + gj] - yi, ddz = x[2 * N + gj] - zi;
-                const double rr2 = fma(ddx, ddx, fma(ddy, ddy, fma(ddz, ddz, eps2d)));
-                const double ri = rsqrt(rr2);
-                const double ww = m[gj] * (ri * ri * ri);
-                r[0] = fma(ww, ddx, r[0]);
-                r[1] = fma(ww, ddy, r[1]);
-                r[2] = fma(ww, ddz, r[2]);
-            }
+            refine_partial(t, tid, HOT_BS, irec, jrec, n_a, n_s, self_pass, Alist, Blist, x, m, N, eps2d,
+                           0.25f * wmax[t], r);
             block_sum3(r);
             if (tid == 0)
                 for (int c = 0; c < 3; ++c) {
@@ -235,6 +271,22 @@ __global__ void __launch_bounds__(HOT_BS) k_acc_refine(
                     if (out_aos) out_aos[(size_t)t * 3 + c] = a;
                 }
             __syncthreads();
+        }
+    } else {
+        // many targets: one warp each, no block barrier
+        for (int q = warp; q < nhot; q += HOT_BS / 32) {
+            const int t = base + nth_hot(s_words, q);
+            double r[3];
+            refine_partial(t, lane, 32, irec, jrec, n_a, n_s, self_pass, Alist, Blist, x, m, N, eps2d,
+                           0.25f * wmax[t], r);
+            for (int c = 0; c < 3; ++c)
+                for (int o = 16; o > 0; o >>= 1) r[c] += __shfl_xor_sync(0xffffffffu, r[c], o);
+            if (lane == 0)
+                for (int c = 0; c < 3; ++c) {
+                    const double a = G * r[c];
+                    out_soa[(size_t)c * n_a + t] = a;
+                    if (out_aos) out_aos[(size_t)t * 3 + c] = a;
+                }
         }
     }
 }

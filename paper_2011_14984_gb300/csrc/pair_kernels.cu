@@ -241,25 +241,49 @@ __global__ void __launch_bounds__(BS) k_tstep_fp64(const double4_32a *__restrict
 // ------------------------------------------------------------------------------------
 // finalisation
 // ------------------------------------------------------------------------------------
+// sum over the splits of part[p][c][i] (stride = 3 n): four interleaved partial sums, so that
+// the loads of a long split list overlap; the association is fixed (deterministic)
+__device__ __forceinline__ double split_sum(const double *__restrict__ q, int nsplit, size_t stride)
+{
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int p = 0;
+    for (; p + 4 <= nsplit; p += 4) {
+        s0 += q[(size_t)p * stride];
+        s1 += q[(size_t)(p + 1) * stride];
+        s2 += q[(size_t)(p + 2) * stride];
+        s3 += q[(size_t)(p + 3) * stride];
+    }
+    for (; p < nsplit; ++p) s0 += q[(size_t)p * stride];
+    return (s0 + s1) + (s2 + s3);
+}
+
 __global__ void k_finalize_vec(const double *__restrict__ part, int nsplit, int n, double scale,
                                double *__restrict__ out_soa, double *__restrict__ out_aos,
                                const float *__restrict__ wpart, float *__restrict__ wmax,
-                               int *__restrict__ err, int badbit)
+                               int *__restrict__ err, int badbit, KickArgs kick)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     bool ok = true;
+    const int gi = kick.v ? (kick.list ? kick.list[i] : i) : 0;
     for (int c = 0; c < 3; ++c) {
-        double s = 0.0;
-        for (int p = 0; p < nsplit; ++p) s += part[((size_t)p * 3 + c) * n + i];
+        double s = split_sum(part + (size_t)c * n + i, nsplit, (size_t)3 * n);
         s *= scale;
         ok = ok && isfinite(s);
         if (out_soa) out_soa[(size_t)c * n + i] = s;
         if (out_aos) out_aos[(size_t)i * 3 + c] = s;
+        // the kick that follows the pass: the roundings of k_kick (no contraction)
+        if (kick.v) kick.v[(size_t)c * kick.N + gi] = __dadd_rn(kick.v[(size_t)c * kick.N + gi], __dmul_rn(kick.dt, s));
     }
     if (wpart) {
-        float w = 0.f;
-        for (int p = 0; p < nsplit; ++p) w = fmaxf(w, wpart[(size_t)p * n + i]);
+        float w0 = 0.f, w1 = 0.f;
+        int p = 0;
+        for (; p + 2 <= nsplit; p += 2) {
+            w0 = fmaxf(w0, wpart[(size_t)p * n + i]);
+            w1 = fmaxf(w1, wpart[(size_t)(p + 1) * n + i]);
+        }
+        if (p < nsplit) w0 = fmaxf(w0, wpart[(size_t)p * n + i]);
+        const float w = fmaxf(w0, w1);
         wmax[i] = w;
     }
     if (!ok) atomicOr(err, badbit);
@@ -269,14 +293,14 @@ __global__ void k_finalize_grad(const double *__restrict__ part, int nsplit, int
                                 const double *__restrict__ a_soa, double c,
                                 double *__restrict__ at_soa, double *__restrict__ at_aos,
                                 double *__restrict__ g_aos, int *__restrict__ err, int badbit,
-                                const double *__restrict__ part2, int nsplit2)
+                                const double *__restrict__ part2, int nsplit2, KickArgs kick)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     bool ok = true;
+    const int gi = kick.v ? (kick.list ? kick.list[i] : i) : 0;
     for (int k = 0; k < 3; ++k) {
-        double s = 0.0;
-        for (int p = 0; p < nsplit; ++p) s += part[((size_t)p * 3 + k) * n + i];
+        double s = split_sum(part + (size_t)k * n + i, nsplit, (size_t)3 * n);
         for (int p = 0; p < nsplit2; ++p) s += part2[((size_t)p * 3 + k) * n + i];
         const double g = scale * s;
         const double at = a_soa[(size_t)k * n + i] + c * g;
@@ -284,6 +308,7 @@ __global__ void k_finalize_grad(const double *__restrict__ part, int nsplit, int
         if (at_soa) at_soa[(size_t)k * n + i] = at;
         if (at_aos) at_aos[(size_t)i * 3 + k] = at;
         if (g_aos) g_aos[(size_t)i * 3 + k] = g;
+        if (kick.v) kick.v[(size_t)k * kick.N + gi] = __dadd_rn(kick.v[(size_t)k * kick.N + gi], __dmul_rn(kick.dt, at));
     }
     if (!ok) atomicOr(err, badbit);
 }
@@ -293,8 +318,14 @@ __global__ void k_finalize_tau(const double *__restrict__ part, int nsplit, int 
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double b = INFINITY;
-    for (int p = 0; p < nsplit; ++p) b = fmin(b, part[(size_t)p * n + i]);
+    double b0 = INFINITY, b1 = INFINITY;
+    int p = 0;
+    for (; p + 2 <= nsplit; p += 2) {
+        b0 = fmin(b0, part[(size_t)p * n + i]);
+        b1 = fmin(b1, part[(size_t)(p + 1) * n + i]);
+    }
+    if (p < nsplit) b0 = fmin(b0, part[(size_t)p * n + i]);
+    const double b = fmin(b0, b1);
     const double t = eta * b;
     if (!(t > 0.0)) atomicOr(err, ERR_NONFINITE);  // NaN or non-positive step
     tau[i] = t;
@@ -463,20 +494,21 @@ void launch_tstep(cudaStream_t s, bool mixed, const PairArgs &a, double eta, int
 
 void launch_finalize_vec(cudaStream_t s, const double *part, int nsplit, int n, double scale,
                          double *out_soa, double *out_aos, const float *wpart, float *wmax, int *err,
-                         int badbit)
+                         int badbit, KickArgs kick)
 {
     if (n <= 0) return;
     k_finalize_vec<<<cdiv(n, 256), 256, 0, s>>>(part, nsplit, n, scale, out_soa, out_aos, wpart, wmax,
-                                                 err, badbit);
+                                                 err, badbit, kick);
 }
 
 void launch_finalize_grad(cudaStream_t s, const double *part, int nsplit, int n, double scale,
                           const double *a_soa, double c, double *at_soa, double *at_aos,
-                          double *g_aos, int *err, int badbit, const double *part2, int nsplit2)
+                          double *g_aos, int *err, int badbit, const double *part2, int nsplit2,
+                          KickArgs kick)
 {
     if (n <= 0) return;
     k_finalize_grad<<<cdiv(n, 256), 256, 0, s>>>(part, nsplit, n, scale, a_soa, c, at_soa, at_aos,
-                                                  g_aos, err, badbit, part2, part2 ? nsplit2 : 0);
+                                                  g_aos, err, badbit, part2, part2 ? nsplit2 : 0, kick);
 }
 
 void launch_finalize_tau(cudaStream_t s, const double *part, int nsplit, int n, double eta,

@@ -68,6 +68,10 @@ struct Timed {
 
 }  // namespace
 
+// batch teams: clusters of at least kBatchTeamMinN particles run on kBatchTeamBlocks blocks
+constexpr int64_t kBatchTeamMinN = 768;
+constexpr int kBatchTeamBlocks = 8;
+
 struct frost_ctx {
     int N = 0;
     double G = 1.0, eta = 0.2, eps2 = 0.0;
@@ -98,6 +102,14 @@ struct frost_ctx {
     int subtree_max = 384;                           // sets up to this size run in one block
     int n_clusters = 0;                              // > 0: batch of independent clusters
     int64_t *d_offsets = nullptr;                    // cluster offsets [n_clusters + 1] (device)
+    // batch teams: clusters of at least team_min_n particles run on a thread-block cluster of
+    // team_blocks blocks (d_big, largest first), the others on one block each (d_small); the two
+    // launches overlap through a side stream
+    int32_t *d_big = nullptr, *d_small = nullptr;
+    int n_big = 0, n_small = 0;
+    int *d_xchg = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double *d_ecl = nullptr;                         // per-cluster energy sums [n_clusters][8]
     std::vector<double> h_ecl;
     unsigned long long sub_seen[6] = {0, 0, 0, 0, 0, 0};
@@ -555,7 +567,8 @@ void hhs_subtree(frost_ctx *c, const int32_t *P, int nP, double tau, int depth)
     a.n_steps = 1;
     {
         TimedScope ts(c, PASS_SUBTREE, 0);
-        launch_subtree(c->stream, c->mixed, c->sym, a);
+        // a launch error is also left for the cudaGetLastError() of the calling entry point
+        (void)launch_subtree(c->stream, c->mixed, c->sym, a);
     }
     c->st.kernel_launches += 1;
     c->st.subtree_launches += 1;
@@ -625,6 +638,12 @@ void destroy(frost_ctx *c)
     for (auto p : c->lvS) cudaFree(p);
     for (auto p : c->lvF) cudaFree(p);
     if (c->d_offsets) cudaFree(c->d_offsets);
+    if (c->d_big) cudaFree(c->d_big);
+    if (c->d_small) cudaFree(c->d_small);
+    if (c->d_xchg) cudaFree(c->d_xchg);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->d_ecl) cudaFree(c->d_ecl);
     void *dev[] = {c->x, c->v, c->m, c->all, c->marks, c->recA, c->recB, c->part,
                    c->aA, c->aB, c->atA, c->atB, c->tau, c->wA, c->wB, c->wpart, c->perm,
@@ -765,6 +784,30 @@ static frost_status init_impl(frost_ctx **out, int64_t n, const double *m, const
         INIT_CUDA(cudaMemcpy(c->d_offsets, offsets, sizeof(int64_t) * (n_clusters + 1), cudaMemcpyHostToDevice));
         INIT_CUDA(cudaMalloc(&c->d_ecl, sizeof(double) * 8 * n_clusters));
         c->h_ecl.resize(8 * (size_t)n_clusters);
+        // teams: large clusters first within each group (the block scheduler starts them first)
+        std::vector<int32_t> order(n_clusters);
+        for (int k = 0; k < n_clusters; ++k) order[k] = k;
+        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+            return offsets[a + 1] - offsets[a] > offsets[b + 1] - offsets[b];
+        });
+        std::vector<int32_t> big, small;
+        for (int32_t k : order) (offsets[k + 1] - offsets[k] >= kBatchTeamMinN ? big : small).push_back(k);
+        c->n_big = (int)big.size();
+        c->n_small = (int)small.size();
+        if (c->n_big) {
+            INIT_CUDA(cudaMalloc(&c->d_big, sizeof(int32_t) * c->n_big));
+            INIT_CUDA(cudaMemcpy(c->d_big, big.data(), sizeof(int32_t) * c->n_big, cudaMemcpyHostToDevice));
+        }
+        if (c->n_small) {
+            INIT_CUDA(cudaMalloc(&c->d_small, sizeof(int32_t) * c->n_small));
+            INIT_CUDA(cudaMemcpy(c->d_small, small.data(), sizeof(int32_t) * c->n_small, cudaMemcpyHostToDevice));
+        }
+        INIT_CUDA(cudaMalloc(&c->d_xchg, sizeof(int) * n_clusters));
+        if (c->n_big && c->n_small) {
+            INIT_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+            INIT_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+            INIT_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+        }
     }
     INIT_CUDA(cudaMalloc(&c->dmisc, sizeof(Misc)));
     INIT_CUDA(cudaMallocHost(&c->hmisc, sizeof(Misc)));
@@ -960,15 +1003,37 @@ frost_status frost_step(frost_ctx *c, double dt_pivot, int64_t n_steps)
         a.recA = c->recA;
         a.recB = c->recB;
         a.offsets = c->d_offsets;
-        a.n_blocks = c->n_clusters;
+        a.xchg = c->d_xchg;
         a.tau0 = dt_pivot;
         a.depth0 = 0;
         a.n_steps = (int)n_steps;
+        SubtreeArgs ab = a, as = a;
+        ab.cl_index = c->d_big;
+        ab.n_teams = c->n_big;
+        ab.team_blocks = kBatchTeamBlocks;
+        as.cl_index = c->d_small;
+        as.n_teams = c->n_small;
         {
             TimedScope ts(c, PASS_SUBTREE, 0);
-            launch_subtree(c->stream, c->mixed, c->sym, a);
+            cudaError_t e1 = cudaSuccess, e2 = cudaSuccess;
+            if (c->n_big && c->n_small) {
+                // the large clusters on the side stream, concurrently with the small ones
+                cudaEventRecord(c->ev_fork, c->stream);
+                cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+                e1 = launch_subtree(c->side, c->mixed, c->sym, ab);
+                e2 = launch_subtree(c->stream, c->mixed, c->sym, as);
+                cudaEventRecord(c->ev_join, c->side);
+                cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+            } else if (c->n_big) {
+                e1 = launch_subtree(c->stream, c->mixed, c->sym, ab);
+            } else {
+                e2 = launch_subtree(c->stream, c->mixed, c->sym, as);
+            }
+            if (e1 != cudaSuccess || e2 != cudaSuccess)
+                return fail(FROST_ECUDA, "batch launch: %s",
+                            cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
         }
-        c->st.kernel_launches += 1;
+        c->st.kernel_launches += (c->n_big > 0) + (c->n_small > 0);
         c->st.subtree_launches += c->n_clusters;
         c->t += dt_pivot * (double)n_steps;
         FROST_CUDA(cudaGetLastError());

@@ -178,6 +178,7 @@ void launch_cluster_energy(cudaStream_t s, const int64_t *offsets, int n_cluster
 // ---- single-CTA subtree solver (subtree.cu) ------------------------------------------
 constexpr int SUBTREE_MAX_FRAMES = 64;  // recursion frames per block (max_depth < 64)
 constexpr int SUBTREE_STAT_LEVELS = 48; // per-depth statistics (last entry: deeper levels)
+constexpr int SUBTREE_MAX_CLUSTER = 8;  // blocks per team at most (portable cluster size)
 
 struct SubtreeArgs {
     double *x, *v;
@@ -194,16 +195,23 @@ struct SubtreeArgs {
     double *tau, *aA, *aB, *atA, *atB;
     float *wA, *wB;
     void *recA, *recB;
-    // single-set mode: list P of n particles; batch mode: offsets[n_blocks + 1]
+    // single-set mode: list P of n particles; batch mode: offsets[n_clusters + 1] and, for the
+    // n_teams teams of this launch, the cluster of each team (cl_index, or NULL: team t takes
+    // cluster t)
     const int32_t *P = nullptr;
     int n = 0;
     const int64_t *offsets = nullptr;
-    int n_blocks = 0;
+    const int32_t *cl_index = nullptr;
+    int n_teams = 0;
+    // blocks per team: 1, or a thread-block cluster of 2..SUBTREE_MAX_CLUSTER blocks that
+    // share one set; xchg: one int per team (a status word between the team's blocks)
+    int team_blocks = 1;
+    int *xchg = nullptr;
     double tau0;
     int depth0;
     int n_steps;
 };
-void launch_subtree(cudaStream_t s, bool mixed, int sym, const SubtreeArgs &a);
+cudaError_t launch_subtree(cudaStream_t s, bool mixed, int sym, const SubtreeArgs &a);
 
 SplitShape choose_shape(int n_a, int n_s, int i_per_block, int blocks_per_sm, int n_sm);
 int pair_blocks_per_sm(int kind, bool mixed);

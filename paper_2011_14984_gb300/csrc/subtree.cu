@@ -36,9 +36,11 @@ struct SubParams {
     int *err;
     unsigned long long *counters;  // acc pairs, grad pairs, tstep pairs, hhs calls, fsi calls, max depth
     unsigned long long *levels;    // [2][SUBTREE_STAT_LEVELS]: calls and set sizes per depth
+    int crank, csize;              // this block's rank in its thread-block cluster, cluster size
 };
 
 struct SubWork {
+    int *xchg;                    // one int per cluster of blocks: the warp path's status
     int32_t *perm, *tmp;
     double *tau;
     double *aA, *aB, *atA, *atB;  // [3][n] each
@@ -51,12 +53,31 @@ struct Counts {
     int maxdepth;
 };
 
+// ---- the team of one set: a block, or the blocks of a thread-block cluster -----------------
+// Every helper below is called by all threads of the team with the same arguments, splits its
+// work over the team's threads and ends with a team barrier, so that all control decisions,
+// taken from data read after a barrier, are the same in every block of a cluster.
+
+__device__ __forceinline__ int t_id(const SubParams &p) { return p.crank * SB + threadIdx.x; }
+__device__ __forceinline__ int t_n(const SubParams &p) { return p.csize * SB; }
+
+// team barrier: with more than one block, the cluster barrier (release / acquire at cluster
+// scope orders the global-memory results of every block before the next step)
+__device__ __forceinline__ void t_sync(const SubParams &p)
+{
+    if (p.csize > 1) {
+        asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+    } else {
+        __syncthreads();
+    }
+}
+
 // ---- block-level building blocks ----------------------------------------------------
 
 template <bool MIXED>
 __device__ void b_pack_pos(const SubParams &p, const int32_t *L, int n, void *rec, bool accurate)
 {
-    for (int k = threadIdx.x; k < n; k += SB) {
+    for (int k = t_id(p); k < n; k += t_n(p)) {
         if (MIXED) {
             if (accurate) pack_grad_mixed_one(k, L, n, p.x, p.m, p.N, nullptr, (float4 *)rec);
             else pack_pos_mixed_one(k, L, n, p.x, p.m, p.N, (float4 *)rec);
@@ -75,11 +96,22 @@ __device__ void b_pack_pos(const SubParams &p, const int32_t *L, int n, void *re
 // (out-of-range sources are masked as the self pair), as the time-step pairs vote per warp.
 constexpr int MT_MAX = SB;
 
-__device__ __forceinline__ int mt_threads(int nA)
+// lanes per particle T (a power of two, at most 32) over the team's threads, group g and lane
+// l of this thread, and the rounds over the particles when they outnumber the groups
+struct MtMap {
+    int T, g, l, ngroups, rounds;
+};
+__device__ __forceinline__ MtMap mt_map(const SubParams &p, int nA)
 {
-    int g = 1;
-    while (g < nA) g <<= 1;
-    return max(1, min(32, SB / g));
+    int P2 = 1;
+    while (P2 < nA) P2 <<= 1;
+    MtMap m;
+    m.T = max(1, min(32, t_n(p) / P2));
+    m.g = t_id(p) / m.T;
+    m.l = t_id(p) % m.T;
+    m.ngroups = t_n(p) / m.T;
+    m.rounds = (nA + m.ngroups - 1) / m.ngroups;
+    return m;
 }
 
 __device__ __forceinline__ double grp_sum(double v, int T)
@@ -124,143 +156,150 @@ __device__ __forceinline__ MtSrc mt_src(int q, int T, int l, int nB, int i, bool
 // Newtonian pass (records as in b_acc); out / wout written by lane 0 of each group
 template <bool MIXED>
 __device__ __noinline__ void mt_acc(const SubParams &p, const void *irec, const void *jrec, int nA, int nB, bool self,
-                       bool accurate, double *out, float *wout, int badbit)
+                                    bool accurate, double *out, float *wout, int badbit)
 {
-    const int T = mt_threads(nA);
-    const int g = threadIdx.x / T, l = threadIdx.x % T;
-    const bool active = g < nA;
-    const int i = active ? g : 0;
-    const int ipos[1] = {i};
+    const MtMap mm = mt_map(p, nA);
+    const int T = mm.T, l = mm.l;
     const int nq = (nB + T - 1) / T;
-    double r[3];
-    float wm[1] = {0.f};
-    if (MIXED) {
-        const float4 *ir = (const float4 *)irec, *jr = (const float4 *)jrec;
-        const float eps2 = (float)p.eps2;
-        float H[3] = {0.f, 0.f, 0.f}, L[3] = {0.f, 0.f, 0.f};
-        float ax[1] = {0.f}, ay[1] = {0.f}, az[1] = {0.f};
-        int c = 0;
-        if (accurate) {
-            GradMixedI<1> I;
-            const float4 q0 = ir[i], q1 = ir[nA + i], q2 = ir[2 * nA + i];
-            I.xh[0] = q0.x; I.yh[0] = q0.y; I.zh[0] = q0.z;
-            I.xm[0] = q1.x; I.ym[0] = q1.y; I.zm[0] = q1.z;
-            I.xl[0] = q2.x; I.yl[0] = q2.y; I.zl[0] = q2.z;
-            I.ahx[0] = I.ahy[0] = I.ahz[0] = I.alx[0] = I.aly[0] = I.alz[0] = 0.f;
-            for (int q = 0; q < nq; ++q) {
-                const MtSrc s = mt_src(q, T, l, nB, i, self);
-                acc3_mixed_j<1, true>(jr[s.j], jr[nB + s.j], jr[2 * nB + s.j], I, eps2, s.jpos, ipos, ax, ay, az, wm);
-                if (++c == 16) {
-                    fold2(H[0], L[0], ax[0]); fold2(H[1], L[1], ay[0]); fold2(H[2], L[2], az[0]);
-                    ax[0] = ay[0] = az[0] = 0.f;
-                    c = 0;
+    for (int rr = 0; rr < mm.rounds; ++rr) {
+        const int i0 = mm.g + rr * mm.ngroups;
+        const bool active = i0 < nA;
+        const int i = active ? i0 : 0;
+        const int ipos[1] = {i};
+        double r[3];
+        float wm[1] = {0.f};
+        if (MIXED) {
+            const float4 *ir = (const float4 *)irec, *jr = (const float4 *)jrec;
+            const float eps2 = (float)p.eps2;
+            float H[3] = {0.f, 0.f, 0.f}, L[3] = {0.f, 0.f, 0.f};
+            float ax[1] = {0.f}, ay[1] = {0.f}, az[1] = {0.f};
+            int c = 0;
+            if (accurate) {
+                GradMixedI<1> I;
+                const float4 q0 = ir[i], q1 = ir[nA + i], q2 = ir[2 * nA + i];
+                I.xh[0] = q0.x; I.yh[0] = q0.y; I.zh[0] = q0.z;
+                I.xm[0] = q1.x; I.ym[0] = q1.y; I.zm[0] = q1.z;
+                I.xl[0] = q2.x; I.yl[0] = q2.y; I.zl[0] = q2.z;
+                I.ahx[0] = I.ahy[0] = I.ahz[0] = I.alx[0] = I.aly[0] = I.alz[0] = 0.f;
+                for (int q = 0; q < nq; ++q) {
+                    const MtSrc s = mt_src(q, T, l, nB, i, self);
+                    acc3_mixed_j<1, true>(jr[s.j], jr[nB + s.j], jr[2 * nB + s.j], I, eps2, s.jpos, ipos, ax, ay, az,
+                                          wm);
+                    if (++c == 16) {
+                        fold2(H[0], L[0], ax[0]); fold2(H[1], L[1], ay[0]); fold2(H[2], L[2], az[0]);
+                        ax[0] = ay[0] = az[0] = 0.f;
+                        c = 0;
+                    }
+                }
+            } else {
+                AccMixedI<1> I;
+                const float4 q0 = ir[i], q1 = ir[nA + i];
+                I.xh[0] = q0.x; I.yh[0] = q0.y; I.zh[0] = q0.z;
+                I.xl[0] = q1.x; I.yl[0] = q1.y; I.zl[0] = q1.z;
+                for (int q = 0; q < nq; ++q) {
+                    const MtSrc s = mt_src(q, T, l, nB, i, self);
+                    acc_mixed_j<1, true, false>(jr[s.j], jr[nB + s.j], I, eps2, s.jpos, ipos, ax, ay, az, wm);
+                    if (++c == 16) {
+                        fold2(H[0], L[0], ax[0]); fold2(H[1], L[1], ay[0]); fold2(H[2], L[2], az[0]);
+                        ax[0] = ay[0] = az[0] = 0.f;
+                        c = 0;
+                    }
                 }
             }
+            fold2(H[0], L[0], ax[0]); fold2(H[1], L[1], ay[0]); fold2(H[2], L[2], az[0]);
+            for (int k = 0; k < 3; ++k) r[k] = (double)H[k] + (double)L[k];
         } else {
-            AccMixedI<1> I;
-            const float4 q0 = ir[i], q1 = ir[nA + i];
-            I.xh[0] = q0.x; I.yh[0] = q0.y; I.zh[0] = q0.z;
-            I.xl[0] = q1.x; I.yl[0] = q1.y; I.zl[0] = q1.z;
+            const double4_32a *ir = (const double4_32a *)irec, *jr = (const double4_32a *)jrec;
+            const double4_32a I = ir[i];
+            r[0] = r[1] = r[2] = 0.0;
             for (int q = 0; q < nq; ++q) {
                 const MtSrc s = mt_src(q, T, l, nB, i, self);
-                acc_mixed_j<1, true, false>(jr[s.j], jr[nB + s.j], I, eps2, s.jpos, ipos, ax, ay, az, wm);
-                if (++c == 16) {
-                    fold2(H[0], L[0], ax[0]); fold2(H[1], L[1], ay[0]); fold2(H[2], L[2], az[0]);
-                    ax[0] = ay[0] = az[0] = 0.f;
-                    c = 0;
-                }
+                acc_fp64_j<true>(jr[s.j], I, p.eps2, s.jpos, i, r[0], r[1], r[2]);
             }
         }
-        fold2(H[0], L[0], ax[0]); fold2(H[1], L[1], ay[0]); fold2(H[2], L[2], az[0]);
-        for (int k = 0; k < 3; ++k) r[k] = (double)H[k] + (double)L[k];
-    } else {
-        const double4_32a *ir = (const double4_32a *)irec, *jr = (const double4_32a *)jrec;
-        const double4_32a I = ir[i];
-        r[0] = r[1] = r[2] = 0.0;
-        for (int q = 0; q < nq; ++q) {
-            const MtSrc s = mt_src(q, T, l, nB, i, self);
-            acc_fp64_j<true>(jr[s.j], I, p.eps2, s.jpos, i, r[0], r[1], r[2]);
+        for (int k = 0; k < 3; ++k) r[k] = grp_sum(r[k], T);
+        const float wmx = grp_max(wm[0], T);
+        if (active && l == 0) {
+            bool ok = true;
+            for (int k = 0; k < 3; ++k) {
+                const double a = p.G * r[k];
+                ok = ok && isfinite(a);
+                out[k * nA + i] = a;
+            }
+            if (wout) wout[i] = wmx;
+            if (!ok) atomicOr(p.err, badbit);
         }
-    }
-    for (int k = 0; k < 3; ++k) r[k] = grp_sum(r[k], T);
-    const float wmx = grp_max(wm[0], T);
-    if (active && l == 0) {
-        bool ok = true;
-        for (int k = 0; k < 3; ++k) {
-            const double a = p.G * r[k];
-            ok = ok && isfinite(a);
-            out[k * nA + i] = a;
-        }
-        if (wout) wout[i] = wmx;
-        if (!ok) atomicOr(p.err, badbit);
     }
 }
 
 // gradient pass (records as in b_grad): at[3][nA] = a_A + c 2G sum
 template <bool MIXED>
 __device__ __noinline__ void mt_grad(const SubParams &p, const void *irec, const void *jrec, int nA, int nB, bool self,
-                        const double *aA, const float *wmax, double c, double *at, int badbit)
+                                     const double *aA, const float *wmax, double c, double *at, int badbit)
 {
-    const int T = mt_threads(nA);
-    const int g = threadIdx.x / T, l = threadIdx.x % T;
-    const bool active = g < nA;
-    const int i = active ? g : 0;
-    const int ipos[1] = {i};
+    const MtMap mm = mt_map(p, nA);
+    const int T = mm.T, l = mm.l;
     const int nq = (nB + T - 1) / T;
-    double r[3];
-    if (MIXED) {
-        const float4 *ir = (const float4 *)irec, *jr = (const float4 *)jrec;
-        const float eps2 = (float)p.eps2;
-        GradMixedI<1> I;
-        const float4 q0 = ir[i], q1 = ir[nA + i], q2 = ir[2 * nA + i], q3 = ir[3 * nA + i];
-        I.xh[0] = q0.x; I.yh[0] = q0.y; I.zh[0] = q0.z;
-        I.xm[0] = q1.x; I.ym[0] = q1.y; I.zm[0] = q1.z; I.ahx[0] = q1.w;
-        I.xl[0] = q2.x; I.yl[0] = q2.y; I.zl[0] = q2.z; I.ahy[0] = q2.w;
-        I.ahz[0] = q3.x; I.alx[0] = q3.y; I.aly[0] = q3.z; I.alz[0] = q3.w;
-        const float thr[1] = {wmax ? 0.25f * wmax[i] : INFINITY};
-        BigSlots<1> big;
-        big.n[0] = 0;
-        big.j0[0] = big.j1[0] = big.j2[0] = big.j3[0] = 0;
-        float H[3] = {0.f, 0.f, 0.f}, L[3] = {0.f, 0.f, 0.f};
-        float gx[1] = {0.f}, gy[1] = {0.f}, gz[1] = {0.f};
-        int cnt = 0;
-        for (int q = 0; q < nq; ++q) {
-            const MtSrc s = mt_src(q, T, l, nB, i, self);
-            grad_mixed_j<1, true>(jr[s.j], jr[nB + s.j], jr[2 * nB + s.j], jr[3 * nB + s.j], I, eps2, s.j, s.jpos,
-                                  ipos, thr, big, gx, gy, gz);
-            if (++cnt == 16) {
-                fold2(H[0], L[0], gx[0]); fold2(H[1], L[1], gy[0]); fold2(H[2], L[2], gz[0]);
-                gx[0] = gy[0] = gz[0] = 0.f;
-                cnt = 0;
+    for (int rr = 0; rr < mm.rounds; ++rr) {
+        const int i0 = mm.g + rr * mm.ngroups;
+        const bool active = i0 < nA;
+        const int i = active ? i0 : 0;
+        const int ipos[1] = {i};
+        double r[3];
+        if (MIXED) {
+            const float4 *ir = (const float4 *)irec, *jr = (const float4 *)jrec;
+            const float eps2 = (float)p.eps2;
+            GradMixedI<1> I;
+            const float4 q0 = ir[i], q1 = ir[nA + i], q2 = ir[2 * nA + i], q3 = ir[3 * nA + i];
+            I.xh[0] = q0.x; I.yh[0] = q0.y; I.zh[0] = q0.z;
+            I.xm[0] = q1.x; I.ym[0] = q1.y; I.zm[0] = q1.z; I.ahx[0] = q1.w;
+            I.xl[0] = q2.x; I.yl[0] = q2.y; I.zl[0] = q2.z; I.ahy[0] = q2.w;
+            I.ahz[0] = q3.x; I.alx[0] = q3.y; I.aly[0] = q3.z; I.alz[0] = q3.w;
+            const float thr[1] = {wmax ? 0.25f * wmax[i] : INFINITY};
+            BigSlots<1> big;
+            big.n[0] = 0;
+            big.j0[0] = big.j1[0] = big.j2[0] = big.j3[0] = 0;
+            float H[3] = {0.f, 0.f, 0.f}, L[3] = {0.f, 0.f, 0.f};
+            float gx[1] = {0.f}, gy[1] = {0.f}, gz[1] = {0.f};
+            int cnt = 0;
+            for (int q = 0; q < nq; ++q) {
+                const MtSrc s = mt_src(q, T, l, nB, i, self);
+                grad_mixed_j<1, true>(jr[s.j], jr[nB + s.j], jr[2 * nB + s.j], jr[3 * nB + s.j], I, eps2, s.j, s.jpos,
+                                      ipos, thr, big, gx, gy, gz);
+                if (++cnt == 16) {
+                    fold2(H[0], L[0], gx[0]); fold2(H[1], L[1], gy[0]); fold2(H[2], L[2], gz[0]);
+                    gx[0] = gy[0] = gz[0] = 0.f;
+                    cnt = 0;
+                }
+            }
+            fold2(H[0], L[0], gx[0]); fold2(H[1], L[1], gy[0]); fold2(H[2], L[2], gz[0]);
+            double bx = 0.0, by = 0.0, bz = 0.0;
+            for (int t = 0; t < big.n[0]; ++t) {
+                const int j = (t == 0) ? big.j0[0] : (t == 1) ? big.j1[0] : (t == 2) ? big.j2[0] : big.j3[0];
+                grad_term_fp64<1>(jr[j], jr[nB + j], jr[2 * nB + j], jr[3 * nB + j], I, 0, p.eps2, bx, by, bz);
+            }
+            r[0] = ((double)H[0] + (double)L[0]) + bx;
+            r[1] = ((double)H[1] + (double)L[1]) + by;
+            r[2] = ((double)H[2] + (double)L[2]) + bz;
+        } else {
+            const double4_32a *ir = (const double4_32a *)irec, *jr = (const double4_32a *)jrec;
+            const double4_32a I = ir[i], IA = ir[nA + i];
+            r[0] = r[1] = r[2] = 0.0;
+            for (int q = 0; q < nq; ++q) {
+                const MtSrc s = mt_src(q, T, l, nB, i, self);
+                grad_fp64_j<true>(jr[s.j], jr[nB + s.j], I, IA, p.eps2, s.jpos, i, r[0], r[1], r[2]);
             }
         }
-        fold2(H[0], L[0], gx[0]); fold2(H[1], L[1], gy[0]); fold2(H[2], L[2], gz[0]);
-        double bx = 0.0, by = 0.0, bz = 0.0;
-        for (int t = 0; t < big.n[0]; ++t) {
-            const int j = (t == 0) ? big.j0[0] : (t == 1) ? big.j1[0] : (t == 2) ? big.j2[0] : big.j3[0];
-            grad_term_fp64<1>(jr[j], jr[nB + j], jr[2 * nB + j], jr[3 * nB + j], I, 0, p.eps2, bx, by, bz);
+        for (int k = 0; k < 3; ++k) r[k] = grp_sum(r[k], T);
+        if (active && l == 0) {
+            bool ok = true;
+            for (int k = 0; k < 3; ++k) {
+                const double v = aA[k * nA + i] + c * (2.0 * p.G * r[k]);
+                ok = ok && isfinite(v);
+                at[k * nA + i] = v;
+            }
+            if (!ok) atomicOr(p.err, badbit);
         }
-        r[0] = ((double)H[0] + (double)L[0]) + bx;
-        r[1] = ((double)H[1] + (double)L[1]) + by;
-        r[2] = ((double)H[2] + (double)L[2]) + bz;
-    } else {
-        const double4_32a *ir = (const double4_32a *)irec, *jr = (const double4_32a *)jrec;
-        const double4_32a I = ir[i], IA = ir[nA + i];
-        r[0] = r[1] = r[2] = 0.0;
-        for (int q = 0; q < nq; ++q) {
-            const MtSrc s = mt_src(q, T, l, nB, i, self);
-            grad_fp64_j<true>(jr[s.j], jr[nB + s.j], I, IA, p.eps2, s.jpos, i, r[0], r[1], r[2]);
-        }
-    }
-    for (int k = 0; k < 3; ++k) r[k] = grp_sum(r[k], T);
-    if (active && l == 0) {
-        bool ok = true;
-        for (int k = 0; k < 3; ++k) {
-            const double v = aA[k * nA + i] + c * (2.0 * p.G * r[k]);
-            ok = ok && isfinite(v);
-            at[k * nA + i] = v;
-        }
-        if (!ok) atomicOr(p.err, badbit);
     }
 }
 
@@ -268,44 +307,48 @@ __device__ __noinline__ void mt_grad(const SubParams &p, const void *irec, const
 template <bool MIXED, int SYM>
 __device__ __noinline__ void mt_tstep(const SubParams &p, const void *rec, int n, double *tau)
 {
-    const int T = mt_threads(n);
-    const int g = threadIdx.x / T, l = threadIdx.x % T;
-    const bool active = g < n;
-    const int i = active ? g : 0;
-    const int ipos[1] = {i};
+    const MtMap mm = mt_map(p, n);
+    const int T = mm.T, l = mm.l;
     const int nq = (n + T - 1) / T;
-    double t;
-    bool coincident;
-    if (MIXED) {
-        const float4 *r = (const float4 *)rec;
-        TstepMixedI<1> I;
-        const float4 a = r[i], b = r[n + i], cc = r[2 * n + i];
-        I.xh[0] = a.x; I.yh[0] = a.y; I.zh[0] = a.z;
-        I.xl[0] = b.x; I.yl[0] = b.y; I.zl[0] = b.z;
-        I.vx[0] = cc.x; I.vy[0] = cc.y; I.vz[0] = cc.z; I.gm[0] = cc.w;
-        const float eta = (float)p.eta, eta15 = 1.5f * eta;
-        float best[1] = {INFINITY}, minr2[1] = {INFINITY};
-        for (int q = 0; q < nq; ++q) {
-            const MtSrc s = mt_src(q, T, l, n, i, true);
-            tstep_mixed_j<1, SYM, true>(r[s.j], r[n + s.j], r[2 * n + s.j], I, eta, eta15, s.jpos, ipos, best, minr2);
+    for (int rr = 0; rr < mm.rounds; ++rr) {
+        const int i0 = mm.g + rr * mm.ngroups;
+        const bool active = i0 < n;
+        const int i = active ? i0 : 0;
+        const int ipos[1] = {i};
+        double t;
+        bool coincident;
+        if (MIXED) {
+            const float4 *r = (const float4 *)rec;
+            TstepMixedI<1> I;
+            const float4 a = r[i], b = r[n + i], cc = r[2 * n + i];
+            I.xh[0] = a.x; I.yh[0] = a.y; I.zh[0] = a.z;
+            I.xl[0] = b.x; I.yl[0] = b.y; I.zl[0] = b.z;
+            I.vx[0] = cc.x; I.vy[0] = cc.y; I.vz[0] = cc.z; I.gm[0] = cc.w;
+            const float eta = (float)p.eta, eta15 = 1.5f * eta;
+            float best[1] = {INFINITY}, minr2[1] = {INFINITY};
+            for (int q = 0; q < nq; ++q) {
+                const MtSrc s = mt_src(q, T, l, n, i, true);
+                tstep_mixed_j<1, SYM, true>(r[s.j], r[n + s.j], r[2 * n + s.j], I, eta, eta15, s.jpos, ipos, best,
+                                            minr2);
+            }
+            t = p.eta * (double)grp_min(best[0], T);
+            coincident = grp_min(minr2[0], T) == 0.f;
+        } else {
+            const double4_32a *r = (const double4_32a *)rec;
+            const double4_32a I = r[i], IV = r[n + i];
+            double best = INFINITY, minr2 = INFINITY;
+            for (int q = 0; q < nq; ++q) {
+                const MtSrc s = mt_src(q, T, l, n, i, true);
+                tstep_fp64_j<SYM, true>(r[s.j], r[n + s.j], I, IV, p.eta, s.jpos, i, best, minr2);
+            }
+            t = p.eta * grp_mind(best, T);
+            coincident = grp_mind(minr2, T) == 0.0;
         }
-        t = p.eta * (double)grp_min(best[0], T);
-        coincident = grp_min(minr2[0], T) == 0.f;
-    } else {
-        const double4_32a *r = (const double4_32a *)rec;
-        const double4_32a I = r[i], IV = r[n + i];
-        double best = INFINITY, minr2 = INFINITY;
-        for (int q = 0; q < nq; ++q) {
-            const MtSrc s = mt_src(q, T, l, n, i, true);
-            tstep_fp64_j<SYM, true>(r[s.j], r[n + s.j], I, IV, p.eta, s.jpos, i, best, minr2);
+        if (active && l == 0) {
+            tau[i] = t;
+            if (coincident) atomicOr(p.err, ERR_COINCIDENT);
+            if (!(t > 0.0)) atomicOr(p.err, ERR_NONFINITE);
         }
-        t = p.eta * grp_mind(best, T);
-        coincident = grp_mind(minr2, T) == 0.0;
-    }
-    if (active && l == 0) {
-        tau[i] = t;
-        if (coincident) atomicOr(p.err, ERR_COINCIDENT);
-        if (!(t > 0.0)) atomicOr(p.err, ERR_NONFINITE);
     }
 }
 
@@ -318,19 +361,19 @@ __device__ __noinline__ void b_acc(const SubParams &p, const SubWork &w, const i
     if (nA <= 0) return;
     const int badbit = p.eps2 == 0.0 ? ERR_COINCIDENT : ERR_NONFINITE;
     if (nB <= 0 || (self && nA == 1)) {
-        for (int k = threadIdx.x; k < nA; k += SB) {
+        for (int k = t_id(p); k < nA; k += t_n(p)) {
             out[k] = out[nA + k] = out[2 * nA + k] = 0.0;
             if (wout) wout[k] = 0.f;
         }
-        __syncthreads();
+        t_sync(p);
         return;
     }
     accurate = accurate && MIXED;
     b_pack_pos<MIXED>(p, A, nA, w.recA, accurate);
     if (!self) b_pack_pos<MIXED>(p, B, nB, w.recB, accurate);
-    __syncthreads();
+    t_sync(p);
     const int sp = self ? 1 : 0;
-    if (nA <= MT_MAX) {
+    if (p.csize > 1 || nA <= MT_MAX) {
         mt_acc<MIXED>(p, w.recA, self ? w.recA : w.recB, nA, nB, self, accurate, out, wout, badbit);
     } else if (MIXED) {
         const float4 *ir = w.recA, *jr = self ? w.recA : w.recB;
@@ -372,7 +415,7 @@ __device__ __noinline__ void b_acc(const SubParams &p, const SubWork &w, const i
             }
         }
     }
-    __syncthreads();
+    t_sync(p);
     if (threadIdx.x == 0) cnt.acc += self ? (unsigned long long)nA * (nA - 1) : (unsigned long long)nA * nB;
 }
 
@@ -385,24 +428,24 @@ __device__ __noinline__ void b_grad(const SubParams &p, const SubWork &w, const 
     if (nA <= 0) return;
     const int badbit = p.eps2 == 0.0 ? ERR_COINCIDENT : ERR_NONFINITE;
     if (nB <= 0 || (self && nA == 1)) {
-        for (int k = threadIdx.x; k < 3 * nA; k += SB) at[k] = aA[k];
-        __syncthreads();
+        for (int k = t_id(p); k < 3 * nA; k += t_n(p)) at[k] = aA[k];
+        t_sync(p);
         return;
     }
-    for (int k = threadIdx.x; k < nA; k += SB) {
+    for (int k = t_id(p); k < nA; k += t_n(p)) {
         if (MIXED) pack_grad_mixed_one(k, A, nA, p.x, p.m, p.N, aA, w.recA);
         else pack_grad_fp64_one(k, A, nA, p.x, p.m, p.N, aA, (double4_32a *)w.recA);
     }
     if (!self)
-        for (int k = threadIdx.x; k < nB; k += SB) {
+        for (int k = t_id(p); k < nB; k += t_n(p)) {
             if (MIXED) pack_grad_mixed_one(k, B, nB, p.x, p.m, p.N, aB, w.recB);
             else pack_grad_fp64_one(k, B, nB, p.x, p.m, p.N, aB, (double4_32a *)w.recB);
         }
-    __syncthreads();
+    t_sync(p);
     const int sp = self ? 1 : 0;
     const double c = eps_grad * eps_grad / 48.0;
     const double scale = 2.0 * p.G;
-    if (nA <= MT_MAX) {
+    if (p.csize > 1 || nA <= MT_MAX) {
         mt_grad<MIXED>(p, w.recA, self ? w.recA : w.recB, nA, nB, self, aA, MIXED ? wmax : nullptr, c, at, badbit);
     } else if (MIXED) {
         const float4 *ir = w.recA, *jr = self ? w.recA : w.recB;
@@ -441,7 +484,7 @@ __device__ __noinline__ void b_grad(const SubParams &p, const SubWork &w, const 
             }
         }
     }
-    __syncthreads();
+    t_sync(p);
     if (threadIdx.x == 0) cnt.grad += self ? (unsigned long long)nA * (nA - 1) : (unsigned long long)nA * nB;
 }
 
@@ -451,16 +494,16 @@ __device__ __noinline__ void b_tstep(const SubParams &p, const SubWork &w, const
 {
     if (n <= 0) return;
     if (n == 1) {
-        if (threadIdx.x == 0) tau[0] = INFINITY;
-        __syncthreads();
+        if (t_id(p) == 0) tau[0] = INFINITY;
+        t_sync(p);
         return;
     }
-    for (int k = threadIdx.x; k < n; k += SB) {
+    for (int k = t_id(p); k < n; k += t_n(p)) {
         if (MIXED) pack_tstep_mixed_one(k, P, n, p.x, p.v, p.m, p.N, p.G, w.recA);
         else pack_tstep_fp64_one(k, P, n, p.x, p.v, p.m, p.N, p.G, (double4_32a *)w.recA);
     }
-    __syncthreads();
-    if (n <= MT_MAX) {
+    t_sync(p);
+    if (p.csize > 1 || n <= MT_MAX) {
         mt_tstep<MIXED, SYM>(p, w.recA, n, tau);
     } else if (MIXED) {
         for (int ib = 0; ib < n; ib += SIB) {
@@ -491,12 +534,14 @@ __device__ __noinline__ void b_tstep(const SubParams &p, const SubWork &w, const
             }
         }
     }
-    __syncthreads();
+    t_sync(p);
     if (threadIdx.x == 0) cnt.tstep += (unsigned long long)n * (n - 1);
 }
 
-// stable in-place partition of P[0..n) by tau >= pivot; returns |S| (S first, then F)
-__device__ __noinline__ int b_partition(int32_t *P, int n, const double *tau, double pivot, int32_t *tmp)
+// stable in-place partition of P[0..n) by tau >= pivot; returns |S| (S first, then F).  Every
+// block of the team counts |S|; the first block reorders.
+__device__ __noinline__ int b_partition(const SubParams &p, int32_t *P, int n, const double *tau, double pivot,
+                                        int32_t *tmp)
 {
     __shared__ int wsum[SB / 32];
     __shared__ int s_chunk, s_total;
@@ -514,6 +559,10 @@ __device__ __noinline__ int b_partition(int32_t *P, int n, const double *tau, do
     }
     __syncthreads();
     const int nS = s_total;
+    if (p.crank != 0) {
+        t_sync(p);
+        return nS;
+    }
     int sbase = 0, fbase = 0;
     for (int c0 = 0; c0 < n; c0 += SB) {
         const int k = c0 + tid;
@@ -544,28 +593,28 @@ __device__ __noinline__ int b_partition(int32_t *P, int n, const double *tau, do
         __syncthreads();
     }
     for (int k = tid; k < n; k += SB) P[k] = tmp[k];
-    __syncthreads();
+    t_sync(p);
     return nS;
 }
 
 __device__ void b_kick(const SubParams &p, const int32_t *L, int n, const double *a, double dt)
 {
-    for (int k = threadIdx.x; k < n; k += SB) {
+    for (int k = t_id(p); k < n; k += t_n(p)) {
         const int i = L[k];
         for (int c = 0; c < 3; ++c)
             p.v[c * p.N + i] = __dadd_rn(p.v[c * p.N + i], __dmul_rn(dt, a[c * n + k]));
     }
-    __syncthreads();
+    t_sync(p);
 }
 
 __device__ void b_drift(const SubParams &p, const int32_t *L, int n, double dt)
 {
-    for (int k = threadIdx.x; k < n; k += SB) {
+    for (int k = t_id(p); k < n; k += t_n(p)) {
         const int i = L[k];
         for (int c = 0; c < 3; ++c)
             p.x[c * p.N + i] = __dadd_rn(p.x[c * p.N + i], __dmul_rn(dt, p.v[c * p.N + i]));
     }
-    __syncthreads();
+    t_sync(p);
 }
 
 // Algorithm fsi on the set S with step dt
@@ -1000,22 +1049,35 @@ __device__ __noinline__ int warp_hhs(const SubParams &p, const int32_t *Sg, int 
     return err;
 }
 
-// One block: n_steps calls of hhs_fsi(P, tau0) at depth depth0.  Single-set mode: P, n given,
-// workspace from particle 0.  Batch mode (offsets != NULL): block b takes the particles
-// [offsets[b], offsets[b+1]) in order, and the workspace region of those particles.
+// One team (a block, or the blocks of one thread-block cluster): n_steps calls of
+// hhs_fsi(P, tau0) at depth depth0.  Single-set mode: P, n given, workspace from particle 0.
+// Batch mode (offsets != NULL): team t takes cluster c = (cl_index ? cl_index[t] : t), the
+// particles [offsets[c], offsets[c+1]) in order, and the workspace region of those particles.
+// Every block of a team keeps its own copy of the frame stack and takes the same decisions.
 template <bool MIXED, int SYM>
-__global__ void __launch_bounds__(SB) k_hhs_subtree(SubParams p, SubWork w0, const int32_t *__restrict__ P,
+__global__ void __launch_bounds__(SB) k_hhs_subtree(SubParams p0, SubWork w0, const int32_t *__restrict__ P,
                                                     int n_single, const int64_t *__restrict__ offsets,
-                                                    double tau0, int depth0, int n_steps)
+                                                    const int32_t *__restrict__ cl_index, double tau0,
+                                                    int depth0, int n_steps)
 {
     __shared__ int f_lo[MAXD], f_n[MAXD], f_ns[MAXD], f_pc[MAXD], f_depth[MAXD];
     __shared__ double f_tau[MAXD];
     __shared__ int s_sp, s_abort;
     const int tid = threadIdx.x;
+    SubParams p = p0;
+    {
+        unsigned r, c;
+        asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+        asm("mov.u32 %0, %%cluster_nctarank;" : "=r"(c));
+        p.crank = (int)r;
+        p.csize = (int)c;
+    }
+    const int team = blockIdx.x / p.csize;
     int off = 0, n = n_single;
     if (offsets) {
-        off = (int)offsets[blockIdx.x];
-        n = (int)(offsets[blockIdx.x + 1] - offsets[blockIdx.x]);
+        const int c = cl_index ? cl_index[team] : team;
+        off = (int)offsets[c];
+        n = (int)(offsets[c + 1] - offsets[c]);
     }
     SubWork w = w0;
     w.perm += off;
@@ -1032,7 +1094,7 @@ __global__ void __launch_bounds__(SB) k_hhs_subtree(SubParams p, SubWork w0, con
     Counts cnt = {0, 0, 0, 0, 0, depth0};
     if (tid == 0) s_abort = 0;
     for (int step = 0; step < n_steps; ++step) {
-        for (int k = tid; k < n; k += SB) w.perm[k] = offsets ? off + k : P[k];
+        for (int k = t_id(p); k < n; k += t_n(p)) w.perm[k] = offsets ? off + k : P[k];
         if (tid == 0) {
             s_sp = 1;
             f_lo[0] = 0;
@@ -1042,7 +1104,7 @@ __global__ void __launch_bounds__(SB) k_hhs_subtree(SubParams p, SubWork w0, con
             f_depth[0] = depth0;
             f_tau[0] = tau0;
         }
-        __syncthreads();
+        t_sync(p);
         while (true) {
             if (s_sp == 0 || s_abort) break;
             const int top = s_sp - 1;
@@ -1052,16 +1114,23 @@ __global__ void __launch_bounds__(SB) k_hhs_subtree(SubParams p, SubWork w0, con
             __syncthreads();  // every thread has read the frame before it changes
             int32_t *S = w.perm + lo;
             if (pc == 0 && fn <= WARP_N) {
-                // a tiny set: its whole subtree in warp 0, without block barriers
-                if (tid < 32) {
+                // a tiny set: its whole subtree in warp 0 of the team's first block, without
+                // block barriers; its status reaches the other blocks through w.xchg
+                __shared__ int s_e;
+                if (p.crank == 0 && tid < 32) {
                     const int e = warp_hhs<MIXED, SYM>(p, S, fn, ftau, depth, cnt);
-                    if (e && tid == 0) {
-                        atomicOr(p.err, e);
-                        if (e & ERR_DEPTH) s_abort = 1;
+                    if (tid == 0) {
+                        if (e) atomicOr(p.err, e);
+                        s_e = e;
+                        if (p.csize > 1) w.xchg[team] = e;
                     }
                 }
-                __syncthreads();
-                if (tid == 0) s_sp -= 1;
+                t_sync(p);
+                if (tid == 0) {
+                    const int e = (p.csize > 1) ? *(volatile int *)&w.xchg[team] : s_e;
+                    if (e & ERR_DEPTH) s_abort = 1;
+                    s_sp -= 1;
+                }
             } else if (pc == 0) {
                 if (depth > p.max_depth) {
                     if (tid == 0) {
@@ -1074,12 +1143,14 @@ __global__ void __launch_bounds__(SB) k_hhs_subtree(SubParams p, SubWork w0, con
                 if (tid == 0) {
                     cnt.hhs += 1;
                     cnt.maxdepth = max(cnt.maxdepth, depth);
-                    const int L = min(depth, SUBTREE_STAT_LEVELS - 1);
-                    atomicAdd(&p.levels[L], 1ull);
-                    atomicAdd(&p.levels[SUBTREE_STAT_LEVELS + L], (unsigned long long)fn);
+                    if (p.crank == 0) {
+                        const int L = min(depth, SUBTREE_STAT_LEVELS - 1);
+                        atomicAdd(&p.levels[L], 1ull);
+                        atomicAdd(&p.levels[SUBTREE_STAT_LEVELS + L], (unsigned long long)fn);
+                    }
                 }
                 b_tstep<MIXED, SYM>(p, w, S, fn, w.tau, cnt);
-                nS = b_partition(S, fn, w.tau, ftau, w.tmp);
+                nS = b_partition(p, S, fn, w.tau, ftau, w.tmp);
                 const int nF = fn - nS;
                 b_kick_sf<MIXED>(p, w, S, nS, S + nS, nF, ftau / 6.0, false, ftau, cnt);
                 b_fsi<MIXED>(p, w, S, nS, 0.5 * ftau, cnt);
@@ -1127,7 +1198,7 @@ __global__ void __launch_bounds__(SB) k_hhs_subtree(SubParams p, SubWork w0, con
         __syncthreads();
         if (s_abort) break;
     }
-    if (tid == 0) {
+    if (tid == 0 && p.crank == 0) {
         atomicAdd(&p.counters[0], cnt.acc);
         atomicAdd(&p.counters[1], cnt.grad);
         atomicAdd(&p.counters[2], cnt.tstep);
@@ -1139,7 +1210,7 @@ __global__ void __launch_bounds__(SB) k_hhs_subtree(SubParams p, SubWork w0, con
 
 }  // namespace
 
-void launch_subtree(cudaStream_t s, bool mixed, int sym, const SubtreeArgs &a)
+cudaError_t launch_subtree(cudaStream_t s, bool mixed, int sym, const SubtreeArgs &a)
 {
     SubParams p;
     p.x = a.x;
@@ -1165,9 +1236,26 @@ void launch_subtree(cudaStream_t s, bool mixed, int sym, const SubtreeArgs &a)
     w.wB = a.wB;
     w.recA = (float4 *)a.recA;
     w.recB = (float4 *)a.recB;
-    const unsigned nblk = a.offsets ? (unsigned)a.n_blocks : 1u;
+    w.xchg = a.xchg;
+    const int tb = (a.team_blocks >= 2 && a.team_blocks <= SUBTREE_MAX_CLUSTER) ? a.team_blocks : 1;
+    const unsigned nblk = (a.offsets ? (unsigned)a.n_teams : 1u) * (unsigned)tb;
+    // teams of several blocks run as thread-block clusters of tb blocks (cluster barriers)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nblk);
+    cfg.blockDim = dim3(SB);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)tb;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaSuccess;
 #define FROST_SUBTREE_CASE(MIX, SYMV)                                                             \
-    k_hhs_subtree<MIX, SYMV><<<nblk, SB, 0, s>>>(p, w, a.P, a.n, a.offsets, a.tau0, a.depth0, a.n_steps)
+    e = cudaLaunchKernelEx(&cfg, k_hhs_subtree<MIX, SYMV>, p, w, a.P, a.n, a.offsets, a.cl_index, a.tau0, \
+                           a.depth0, a.n_steps)
     if (mixed) {
         if (sym == 0) FROST_SUBTREE_CASE(true, 0);
         else if (sym == 1) FROST_SUBTREE_CASE(true, 1);
@@ -1178,6 +1266,7 @@ void launch_subtree(cudaStream_t s, bool mixed, int sym, const SubtreeArgs &a)
         else FROST_SUBTREE_CASE(false, 2);
     }
 #undef FROST_SUBTREE_CASE
+    return e;
 }
 
 }  // namespace frost

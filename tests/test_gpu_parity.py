@@ -472,6 +472,32 @@ def _small_batch():
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cluster_batch_with_block_teams(precision):
+    """A batch with clusters of at least 768 particles: those run on a thread-block cluster of
+    8 blocks (cluster barriers between the passes), concurrently with the one-block clusters;
+    every cluster still evolves as if alone."""
+    sizes = [1500, 60, 900, 200, 800]
+    ms, xs, vs = [], [], []
+    for k, n in enumerate(sizes):
+        m, x, v = ics.plummer(n, 700 + k)
+        ms.append(m); xs.append(x); vs.append(v)
+    off = np.zeros(len(sizes) + 1, dtype=np.int64)
+    off[1:] = np.cumsum(sizes)
+    m, x, v = np.concatenate(ms), np.concatenate(xs), np.concatenate(vs)
+    f = F(m, x, v, precision=precision, eta=0.2, offsets=off)
+    f.step(2.0 ** -6, 2)
+    xg, vg, t = f.state()
+    st = f.stats()
+    assert st["max_depth_seen"] >= 1
+    tol = 1e-10 if precision == "fp64" else 1e-7
+    for k in range(len(sizes)):
+        a, b = off[k], off[k + 1]
+        xo, vo = oracle.steps(m[a:b], x[a:b], v[a:b], 2.0 ** -6, 2, eta=0.2)
+        assert np.max(np.abs(xg[a:b] - xo)) < tol, (k, np.max(np.abs(xg[a:b] - xo)))
+    f.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_cluster_batch_matches_oracle_per_cluster(precision):
     """frost_init_batch + frost_step: every cluster evolves as if alone (the oracle runs each
     cluster separately): FP64 positions within 1e-10, mixed within 1e-7, and the per-cluster

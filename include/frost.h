@@ -206,6 +206,10 @@ typedef struct {
      * hhs_fsi calls with a non-empty set, and the summed sizes of those sets */
     int64_t level_calls[FROST_STATS_LEVELS];
     int64_t level_particles[FROST_STATS_LEVELS];
+    /* Newtonian pair interactions of the second fsi(S) of each hhs_fsi call that were not
+     * recomputed: S has not moved since the end of the first fsi(S), whose final a^SS is
+     * reused bit for bit (acc_pairs counts evaluated pairs only) */
+    int64_t acc_pairs_reused;
 } frost_stats;
 
 frost_status frost_get_stats(frost_ctx *ctx, frost_stats *out);
@@ -214,6 +218,16 @@ frost_status frost_reset_stats(frost_ctx *ctx);
 /* Enable (1) or disable (0) CUDA-event timing of every pair-pass kernel launch on the
  * context stream (a pair of events per launch; totals in frost_stats). */
 frost_status frost_set_timing(frost_ctx *ctx, int32_t enable);
+
+/* Autotuner of the pair kernels' launch shapes (the paper has no counterpart; its kernels use
+ * one fixed layout).  For every power-of-two set size 2^k, 512 <= 2^k <= N, and each pass
+ * kind (0 = Newtonian, 1 = gradient, 2 = time-step), it times an intra-set pass over the
+ * context's particles 0 .. 2^k-1 with the j-split chosen for at most 1, 2, 4, 8 or 16 full
+ * waves of blocks, and keeps the fastest.  Later passes with an active list of [2^k, 2^(k+1))
+ * particles use that choice.  Synchronous.  Results are unchanged to rounding: only the
+ * split of the sources (the summation order of the partials) differs.
+ * waves_out: NULL, or int32[3][32] receiving the chosen bound per kind and k (0 = untuned). */
+frost_status frost_autotune(frost_ctx *ctx, int32_t *waves_out);
 
 /* Wait for all work of the context and report the sticky device error, if any. */
 frost_status frost_synchronize(frost_ctx *ctx);

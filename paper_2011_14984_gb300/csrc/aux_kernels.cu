@@ -23,6 +23,17 @@ __global__ void k_kick(const int32_t *__restrict__ list, int n, double *__restri
     v[2 * N + i] = __dadd_rn(v[2 * N + i], __dmul_rn(dt, a[2 * n + k]));
 }
 
+__global__ void k_kick_by_particle(const int32_t *__restrict__ list, int n, double *__restrict__ v, int N,
+                                   const double *__restrict__ a, double dt)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int i = list ? list[k] : k;
+    v[i] = __dadd_rn(v[i], __dmul_rn(dt, a[i]));
+    v[N + i] = __dadd_rn(v[N + i], __dmul_rn(dt, a[N + i]));
+    v[2 * N + i] = __dadd_rn(v[2 * N + i], __dmul_rn(dt, a[2 * N + i]));
+}
+
 __global__ void k_kick_aos(const int32_t *__restrict__ list, int n, double *__restrict__ v, int N,
                            const double *__restrict__ a, double dt)
 {
@@ -401,6 +412,13 @@ void launch_kick(cudaStream_t s, const int32_t *list, int n, double *v, int N, c
 {
     if (n <= 0) return;
     k_kick<<<cdiv(n, 256), 256, 0, s>>>(list, n, v, N, a_soa, dt);
+}
+
+void launch_kick_by_particle(cudaStream_t s, const int32_t *list, int n, double *v, int N,
+                             const double *a_glob, double dt)
+{
+    if (n <= 0) return;
+    k_kick_by_particle<<<cdiv(n, 256), 256, 0, s>>>(list, n, v, N, a_glob, dt);
 }
 
 void launch_kick_aos(cudaStream_t s, const int32_t *list, int n, double *v, int N,

@@ -54,7 +54,8 @@ struct Misc {
     int64_t counts[2];  // partition |S|, |F|
     int64_t rel[2];     // list relation: bad/duplicate flag, |A cap B|
     double eres[8];     // energy reduction
-    unsigned long long sub[6];  // subtree solver counters (acc, grad, tstep pairs, hhs, fsi, depth)
+    unsigned long long sub[8];  // subtree solver counters (acc, grad, tstep pairs, hhs, fsi, depth,
+                                // reused acc pairs, spare)
     unsigned long long lev[2][SUBTREE_STAT_LEVELS];  // subtree calls / set sizes per depth
     int err;            // sticky device error word
     int pad;
@@ -91,6 +92,7 @@ struct frost_ctx {
     double *part = nullptr;                          // split partials
     size_t part_elems = 0;
     double *aA = nullptr, *aB = nullptr, *atA = nullptr, *atB = nullptr;  // [3][N] each
+    double *aC = nullptr;  // [3][N] by particle: a^SS at the end of the first fsi(S) of hhs_fsi
     double *tau = nullptr;                           // [N]
     float *wA = nullptr, *wB = nullptr;              // max_j m_j / r^3 per particle (mixed)
     float *wpart = nullptr;                          // its split partials
@@ -108,17 +110,24 @@ struct frost_ctx {
     int32_t *d_big = nullptr, *d_small = nullptr;
     int n_big = 0, n_small = 0;
     int *d_xchg = nullptr;
-    cudaStream_t side = nullptr;
+    cudaStream_t side = nullptr, cap = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // the batch step as a CUDA graph (captured once per (dt_pivot, n_steps), then replayed)
+    cudaGraphExec_t gexec = nullptr;
+    double g_dt = 0.0;
+    int64_t g_steps = 0;
     double *d_ecl = nullptr;                         // per-cluster energy sums [n_clusters][8]
     std::vector<double> h_ecl;
-    unsigned long long sub_seen[6] = {0, 0, 0, 0, 0, 0};
+    unsigned long long sub_seen[7] = {0, 0, 0, 0, 0, 0, 0};
     unsigned long long lev_seen[2][SUBTREE_STAT_LEVELS] = {};
     Misc *dmisc = nullptr, *hmisc = nullptr;
     std::vector<int32_t *> lvS, lvF;                 // per-level slow/fast lists
 
     frost_stats st{};
     bool timing = false;
+    // autotuned wave bound of the j-split per pass kind (0 acc, 1 grad, 2 time-step) and
+    // floor(log2 n_active); 0 = the default bound
+    int tune_w[3][32] = {};
     std::vector<Timed> pending;
     std::vector<cudaEvent_t> event_pool;
     int host_error = 0;  // sticky error already reported
@@ -128,9 +137,18 @@ namespace {
 
 int ipb(const frost_ctx *c) { return pair_i_per_block(c->mixed); }
 
-SplitShape shape_for(const frost_ctx *c, int kind, int n_a, int n_s)
+int log2_floor(int n)
 {
-    SplitShape sh = choose_shape(n_a, n_s, ipb(c), pair_blocks_per_sm(kind, c->mixed), c->n_sm);
+    int b = 0;
+    while (b < 30 && (2 << b) <= n) ++b;
+    return b;
+}
+
+SplitShape shape_for(const frost_ctx *c, int kind, int n_a, int n_s, int waves = 0)
+{
+    if (waves <= 0 && kind >= 0 && kind < 3) waves = c->tune_w[kind][log2_floor(std::max(n_a, 1))];
+    if (waves <= 0) waves = 8;
+    SplitShape sh = choose_shape(n_a, n_s, ipb(c), pair_blocks_per_sm(kind, c->mixed), c->n_sm, waves);
     // keep the partials inside the scratch buffer
     const long long comps = (kind == PASS_TSTEP) ? 1 : 3;
     while ((long long)sh.nsplit * comps * n_a > (long long)c->part_elems && sh.nsplit > 1) {
@@ -219,7 +237,8 @@ frost_status sync_misc(frost_ctx *c)
     c->st.hhs_calls += (int64_t)(sub[3] - c->sub_seen[3]);
     c->st.fsi_calls += (int64_t)(sub[4] - c->sub_seen[4]);
     if ((int)sub[5] > c->st.max_depth_seen) c->st.max_depth_seen = (int)sub[5];
-    for (int k = 0; k < 6; ++k) c->sub_seen[k] = sub[k];
+    c->st.acc_pairs_reused += (int64_t)(sub[6] - c->sub_seen[6]);
+    for (int k = 0; k < 7; ++k) c->sub_seen[k] = sub[k];
     for (int q = 0; q < 2; ++q)
         for (int L = 0; L < SUBTREE_STAT_LEVELS; ++L) {
             const unsigned long long cur = c->hmisc->lev[q][L];
@@ -470,11 +489,21 @@ void pack_grad(frost_ctx *c, const int32_t *L, int n, const double *a, void *rec
 
 // Algorithm fsi on the set S with step dt.  Each kick is fused into the finalisation of the
 // pass that produces its accelerations, and each drift writes the records of the next pass.
-void fsi(frost_ctx *c, const int32_t *S, int nS, double dt)
+// cache: 1 stores the final a^SS by particle in aC; 2 starts from the stored a^SS.  Between
+// the two fsi(S) calls of one hhs_fsi only kicks and the deeper levels (other particles)
+// run, so S has not moved and the stored values are the ones the pass would recompute.
+void fsi(frost_ctx *c, const int32_t *S, int nS, double dt, int cache = 0)
 {
     if (nS <= 0) return;
     c->st.fsi_calls += 1;
-    pass_acc(c, S, nS, S, nS, true, c->aA, nullptr, nullptr, nullptr, kick_of(c, S, dt / 6.0));
+    if (nS < 2) cache = 0;
+    if (cache == 2) {
+        launch_kick_by_particle(c->stream, S, nS, c->v, c->N, c->aC, dt / 6.0);
+        c->st.kernel_launches += 1;
+        c->st.acc_pairs_reused += (int64_t)nS * (nS - 1);
+    } else {
+        pass_acc(c, S, nS, S, nS, true, c->aA, nullptr, nullptr, nullptr, kick_of(c, S, dt / 6.0));
+    }
     drift_pack(c, S, nS, 0.5 * dt, c->recA, true);
     if (c->mixed) {
         unsigned *h = zero_hists(c);
@@ -486,7 +515,9 @@ void fsi(frost_ctx *c, const int32_t *S, int nS, double dt)
     pass_grad(c, S, nS, c->aA, S, nS, c->aA, true, dt, c->atA, nullptr, nullptr, c->wA, c->hA,
               kick_of(c, S, 2.0 * dt / 3.0));
     drift_pack(c, S, nS, 0.5 * dt, c->recA, false);
-    pass_acc(c, S, nS, S, nS, true, c->aA, nullptr, nullptr, nullptr, kick_of(c, S, dt / 6.0), c->recA, c->recA);
+    KickArgs last = kick_of(c, S, dt / 6.0);
+    if (cache == 1) last.store = c->aC;
+    pass_acc(c, S, nS, S, nS, true, c->aA, nullptr, nullptr, nullptr, last, c->recA, c->recA);
 }
 
 // kick_sf: S kicked by its accelerations due to F, F by those due to S.  Accelerations depend
@@ -549,6 +580,7 @@ void hhs_subtree(frost_ctx *c, const int32_t *P, int nP, double tau, int depth)
     a.err = &c->dmisc->err;
     a.counters = c->dmisc->sub;
     a.levels = &c->dmisc->lev[0][0];
+    a.aC = c->aC;
     a.perm = c->perm;
     a.tmp = c->ptmp;
     a.tau = c->tau;
@@ -601,11 +633,11 @@ frost_status hhs_fsi(frost_ctx *c, const int32_t *P, int nP, double tau, int dep
     const int nS = (int)c->hmisc->counts[0];
     const int nF = (int)c->hmisc->counts[1];
     kick_sf(c, S, nS, F, nF, tau / 6.0, false, tau);
-    fsi(c, S, nS, 0.5 * tau);
+    fsi(c, S, nS, 0.5 * tau, 1);
     FROST_TRY(hhs_fsi(c, F, nF, 0.5 * tau, depth + 1));
     kick_sf(c, S, nS, F, nF, 2.0 * tau / 3.0, true, tau);
     FROST_TRY(hhs_fsi(c, F, nF, 0.5 * tau, depth + 1));
-    fsi(c, S, nS, 0.5 * tau);
+    fsi(c, S, nS, 0.5 * tau, 2);
     kick_sf(c, S, nS, F, nF, tau / 6.0, false, tau);
     return FROST_OK;
 }
@@ -641,12 +673,14 @@ void destroy(frost_ctx *c)
     if (c->d_big) cudaFree(c->d_big);
     if (c->d_small) cudaFree(c->d_small);
     if (c->d_xchg) cudaFree(c->d_xchg);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->side) cudaStreamDestroy(c->side);
+    if (c->cap) cudaStreamDestroy(c->cap);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->d_ecl) cudaFree(c->d_ecl);
     void *dev[] = {c->x, c->v, c->m, c->all, c->marks, c->recA, c->recB, c->part,
-                   c->aA, c->aB, c->atA, c->atB, c->tau, c->wA, c->wB, c->wpart, c->perm,
+                   c->aA, c->aB, c->atA, c->atB, c->aC, c->tau, c->wA, c->wB, c->wpart, c->perm,
                    c->ptmp, c->dmisc, c->hist, c->hA, c->hB, c->part_hot};
     for (void *p : dev)
         if (p) cudaFree(p);
@@ -764,6 +798,7 @@ static frost_status init_impl(frost_ctx **out, int64_t n, const double *m, const
     INIT_CUDA(cudaMalloc(&c->aB, sizeof(double) * 3 * N));
     INIT_CUDA(cudaMalloc(&c->atA, sizeof(double) * 3 * N));
     INIT_CUDA(cudaMalloc(&c->atB, sizeof(double) * 3 * N));
+    INIT_CUDA(cudaMalloc(&c->aC, sizeof(double) * 3 * N));
     INIT_CUDA(cudaMalloc(&c->tau, sizeof(double) * N));
     INIT_CUDA(cudaMalloc(&c->wA, sizeof(float) * N));
     INIT_CUDA(cudaMalloc(&c->wB, sizeof(float) * N));
@@ -803,6 +838,7 @@ static frost_status init_impl(frost_ctx **out, int64_t n, const double *m, const
             INIT_CUDA(cudaMemcpy(c->d_small, small.data(), sizeof(int32_t) * c->n_small, cudaMemcpyHostToDevice));
         }
         INIT_CUDA(cudaMalloc(&c->d_xchg, sizeof(int) * n_clusters));
+        INIT_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
         if (c->n_big && c->n_small) {
             INIT_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
             INIT_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
@@ -991,6 +1027,7 @@ frost_status frost_step(frost_ctx *c, double dt_pivot, int64_t n_steps)
         a.err = &c->dmisc->err;
         a.counters = c->dmisc->sub;
         a.levels = &c->dmisc->lev[0][0];
+    a.aC = c->aC;
         a.perm = c->perm;
         a.tmp = c->ptmp;
         a.tau = c->tau;
@@ -1013,25 +1050,47 @@ frost_status frost_step(frost_ctx *c, double dt_pivot, int64_t n_steps)
         ab.team_blocks = kBatchTeamBlocks;
         as.cl_index = c->d_small;
         as.n_teams = c->n_small;
-        {
-            TimedScope ts(c, PASS_SUBTREE, 0);
+        if (!c->gexec || c->g_dt != dt_pivot || c->g_steps != n_steps) {
+            // capture the step: the large clusters on a forked stream, concurrently with the
+            // small ones, joined before the end of the graph
+            if (c->gexec) {
+                cudaGraphExecDestroy(c->gexec);
+                c->gexec = nullptr;
+            }
+            FROST_CUDA(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
             cudaError_t e1 = cudaSuccess, e2 = cudaSuccess;
             if (c->n_big && c->n_small) {
-                // the large clusters on the side stream, concurrently with the small ones
-                cudaEventRecord(c->ev_fork, c->stream);
+                cudaEventRecord(c->ev_fork, c->cap);
                 cudaStreamWaitEvent(c->side, c->ev_fork, 0);
                 e1 = launch_subtree(c->side, c->mixed, c->sym, ab);
-                e2 = launch_subtree(c->stream, c->mixed, c->sym, as);
+                e2 = launch_subtree(c->cap, c->mixed, c->sym, as);
                 cudaEventRecord(c->ev_join, c->side);
-                cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+                cudaStreamWaitEvent(c->cap, c->ev_join, 0);
             } else if (c->n_big) {
-                e1 = launch_subtree(c->stream, c->mixed, c->sym, ab);
+                e1 = launch_subtree(c->cap, c->mixed, c->sym, ab);
             } else {
-                e2 = launch_subtree(c->stream, c->mixed, c->sym, as);
+                e2 = launch_subtree(c->cap, c->mixed, c->sym, as);
             }
-            if (e1 != cudaSuccess || e2 != cudaSuccess)
-                return fail(FROST_ECUDA, "batch launch: %s",
-                            cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+            cudaGraph_t g = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(c->cap, &g);
+            if (e1 != cudaSuccess || e2 != cudaSuccess || ec != cudaSuccess || !g) {
+                if (g) cudaGraphDestroy(g);
+                cudaGetLastError();
+                return fail(FROST_ECUDA, "batch step capture: %s",
+                            cudaGetErrorString(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : ec)));
+            }
+            const cudaError_t ei = cudaGraphInstantiate(&c->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (ei != cudaSuccess) {
+                c->gexec = nullptr;
+                return fail(FROST_ECUDA, "batch step graph: %s", cudaGetErrorString(ei));
+            }
+            c->g_dt = dt_pivot;
+            c->g_steps = n_steps;
+        }
+        {
+            TimedScope ts(c, PASS_SUBTREE, 0);
+            FROST_CUDA(cudaGraphLaunch(c->gexec, c->stream));
         }
         c->st.kernel_launches += (c->n_big > 0) + (c->n_small > 0);
         c->st.subtree_launches += c->n_clusters;
@@ -1152,6 +1211,80 @@ frost_status frost_set_timing(frost_ctx *c, int32_t enable)
     }
     c->timing = enable != 0;
     return FROST_OK;
+}
+
+frost_status frost_autotune(frost_ctx *c, int32_t *waves_out)
+{
+    if (!c) return fail(FROST_EINVAL, "NULL context");
+    static const int kWaves[] = {1, 2, 4, 8, 16};
+    cudaEvent_t e0, e1;
+    FROST_CUDA(cudaEventCreate(&e0));
+    FROST_CUDA(cudaEventCreate(&e1));
+    for (int k = 9; (1 << k) <= c->N && k < 31; ++k) {
+        const int n = 1 << k;
+        for (int kind = 0; kind < 3; ++kind) {
+            // records of particles 0 .. n-1 (zero accelerations for the gradient records)
+            if (kind == PASS_ACC) {
+                pack_pos(c, c->all, n, c->recA);
+            } else if (kind == PASS_GRAD) {
+                cudaMemsetAsync(c->aB, 0, sizeof(double) * 3 * n, c->stream);
+                if (c->mixed) launch_pack_grad_mixed(c->stream, c->all, n, c->x, c->m, c->N, c->aB, (float4 *)c->recA);
+                else launch_pack_grad_fp64(c->stream, c->all, n, c->x, c->m, c->N, c->aB, (double4_32a *)c->recA);
+            } else {
+                if (c->mixed)
+                    launch_pack_tstep_mixed(c->stream, c->all, n, c->x, c->v, c->m, c->N, c->G, (float4 *)c->recA);
+                else
+                    launch_pack_tstep_fp64(c->stream, c->all, n, c->x, c->v, c->m, c->N, c->G,
+                                           (double4_32a *)c->recA);
+            }
+            // time each distinct split once (several bounds can give the same launch)
+            float tw[5];
+            int splits[5];
+            for (int q = 0; q < 5; ++q) {
+                PairArgs a;
+                a.irec = c->recA;
+                a.jrec = c->recA;
+                a.n_a = n;
+                a.n_s = n;
+                a.self_pass = 1;
+                a.eps2 = c->eps2;
+                a.part = c->part;
+                a.shape = shape_for(c, kind, n, n, kWaves[q]);
+                splits[q] = a.shape.nsplit;
+                tw[q] = INFINITY;
+                for (int r = 0; r < q; ++r)
+                    if (splits[r] == splits[q]) tw[q] = tw[r];
+                if (tw[q] < INFINITY) continue;
+                for (int rep = 0; rep < 4; ++rep) {
+                    cudaEventRecord(e0, c->stream);
+                    if (kind == PASS_ACC) launch_acc(c->stream, c->mixed, a);
+                    else if (kind == PASS_GRAD) launch_grad(c->stream, c->mixed, a);
+                    else launch_tstep(c->stream, c->mixed, a, c->eta, c->sym, &c->dmisc->err);
+                    cudaEventRecord(e1, c->stream);
+                    FROST_CUDA(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0) tw[q] = std::min(tw[q], ms);  // the first launch warms the caches
+                }
+            }
+            // the fastest bound, if it beats the default (8 waves) by 3%
+            int best_w = 8;
+            float best = tw[3];
+            for (int q = 0; q < 5; ++q)
+                if (tw[q] < 0.97f * tw[3] && tw[q] < best) {
+                    best = tw[q];
+                    best_w = kWaves[q];
+                }
+            c->tune_w[kind][k] = best_w;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (waves_out)
+        for (int q = 0; q < 3; ++q)
+            for (int k = 0; k < 32; ++k) waves_out[q * 32 + k] = c->tune_w[q][k];
+    FROST_CUDA(cudaGetLastError());
+    return sync_misc(c);
 }
 
 frost_status frost_synchronize(frost_ctx *c)

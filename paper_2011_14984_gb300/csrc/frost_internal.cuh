@@ -91,12 +91,14 @@ void launch_tstep(cudaStream_t s, bool mixed, const PairArgs &a, double eta, int
 
 // ---- finalisation of split partials ---------------------------------------------------
 // Optional kick fused into a finalisation: v[c][list[i]] += dt * (the value written for i),
-// with the separate roundings of launch_kick (v = NULL: no kick; list = NULL: identity).
+// with the separate roundings of launch_kick (v = NULL: no kick; list = NULL: identity);
+// store (optional): the value is also written to store[c][list[i]] ([3][N], by particle).
 struct KickArgs {
     const int32_t *list = nullptr;
     double *v = nullptr;
     int N = 0;
     double dt = 0.0;
+    double *store = nullptr;
 };
 
 // out_soa[c][i] = scale * sum_split part[split][c][i]  (also [i][3] copy if out_aos != NULL);
@@ -141,6 +143,9 @@ void launch_kick(cudaStream_t s, const int32_t *list, int n, double *v, int N,
                  const double *a_soa, double dt);
 void launch_kick_aos(cudaStream_t s, const int32_t *list, int n, double *v, int N,
                      const double *a_aos, double dt);
+// v[c][list[k]] += dt * a_glob[c][list[k]]  (accelerations stored by particle, [3][N])
+void launch_kick_by_particle(cudaStream_t s, const int32_t *list, int n, double *v, int N,
+                             const double *a_glob, double dt);
 void launch_drift(cudaStream_t s, const int32_t *list, int n, double *x, const double *v,
                   int N, double dt);
 // drift, then pack the moved particles' position records for the next Newtonian pass:
@@ -187,8 +192,10 @@ struct SubtreeArgs {
     double G, eta, eps2;
     int max_depth;
     int *err;
-    unsigned long long *counters;  // [6]: acc, grad, tstep pairs, hhs calls, fsi calls, max depth
+    unsigned long long *counters;  // [7]: acc, grad, tstep pairs, hhs calls, fsi calls, max depth,
+                                   // reused acc pairs
     unsigned long long *levels;    // [2][SUBTREE_STAT_LEVELS]: calls and set sizes per depth
+    double *aC;                    // [3][N] by particle: a^SS kept from the first fsi(S) to the second
     // workspace (per particle: perm, tmp int32; tau double; aA..atB [3] doubles; wA, wB
     // float; recA, recB 64 bytes), indexed from the block's first particle
     int32_t *perm, *tmp;
@@ -213,7 +220,8 @@ struct SubtreeArgs {
 };
 cudaError_t launch_subtree(cudaStream_t s, bool mixed, int sym, const SubtreeArgs &a);
 
-SplitShape choose_shape(int n_a, int n_s, int i_per_block, int blocks_per_sm, int n_sm);
+// max_waves: at most this many full waves of blocks (the autotuner picks it per size)
+SplitShape choose_shape(int n_a, int n_s, int i_per_block, int blocks_per_sm, int n_sm, int max_waves = 8);
 int pair_blocks_per_sm(int kind, bool mixed);
 int pair_i_per_block(bool mixed);
 

@@ -265,7 +265,7 @@ __global__ void k_finalize_vec(const double *__restrict__ part, int nsplit, int 
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     bool ok = true;
-    const int gi = kick.v ? (kick.list ? kick.list[i] : i) : 0;
+    const int gi = (kick.v || kick.store) ? (kick.list ? kick.list[i] : i) : 0;
     for (int c = 0; c < 3; ++c) {
         double s = split_sum(part + (size_t)c * n + i, nsplit, (size_t)3 * n);
         s *= scale;
@@ -274,6 +274,7 @@ __global__ void k_finalize_vec(const double *__restrict__ part, int nsplit, int 
         if (out_aos) out_aos[(size_t)i * 3 + c] = s;
         // the kick that follows the pass: the roundings of k_kick (no contraction)
         if (kick.v) kick.v[(size_t)c * kick.N + gi] = __dadd_rn(kick.v[(size_t)c * kick.N + gi], __dmul_rn(kick.dt, s));
+        if (kick.store) kick.store[(size_t)c * kick.N + gi] = s;
     }
     if (wpart) {
         float w0 = 0.f, w1 = 0.f;
@@ -405,7 +406,7 @@ int pair_blocks_per_sm(int kind, bool mixed)
     return c;
 }
 
-SplitShape choose_shape(int n_a, int n_s, int i_per_block, int blocks_per_sm, int n_sm)
+SplitShape choose_shape(int n_a, int n_s, int i_per_block, int blocks_per_sm, int n_sm, int max_waves)
 {
     SplitShape sh;
     sh.nblk_i = (n_a + i_per_block - 1) / i_per_block;
@@ -414,8 +415,9 @@ SplitShape choose_shape(int n_a, int n_s, int i_per_block, int blocks_per_sm, in
     const int tiles = (n_s + PAIR_TJ - 1) / PAIR_TJ;
     int best_split = 1;
     double best_eff = -1.0;
-    // at most 8 full waves of blocks in total, each split at least one tile
-    const int max_split = (int)std::max<long long>(1, std::min<long long>(tiles, (8 * cap) / sh.nblk_i));
+    // at most max_waves full waves of blocks in total, each split at least one tile
+    const int max_split =
+        (int)std::max<long long>(1, std::min<long long>(tiles, ((long long)max_waves * cap) / sh.nblk_i));
     for (int ns = 1; ns <= max_split; ++ns) {
         const int tps = (tiles + ns - 1) / ns;                 // tiles per split
         const int nsp = (tiles + tps - 1) / tps;                // splits actually used

@@ -37,6 +37,7 @@ struct SubParams {
     unsigned long long *counters;  // acc pairs, grad pairs, tstep pairs, hhs calls, fsi calls, max depth
     unsigned long long *levels;    // [2][SUBTREE_STAT_LEVELS]: calls and set sizes per depth
     int crank, csize;              // this block's rank in its thread-block cluster, cluster size
+    double *aC;                    // [3][N] by particle: a^SS kept between the two fsi(S) of a call
 };
 
 struct SubWork {
@@ -51,6 +52,7 @@ struct SubWork {
 struct Counts {
     unsigned long long acc, grad, tstep, hhs, fsi;
     int maxdepth;
+    unsigned long long reused;
 };
 
 // ---- the team of one set: a block, or the blocks of a thread-block cluster -----------------
@@ -617,20 +619,40 @@ __device__ void b_drift(const SubParams &p, const int32_t *L, int n, double dt)
     t_sync(p);
 }
 
-// Algorithm fsi on the set S with step dt
+// Algorithm fsi on the set S with step dt.  cache: 1 keeps the final a^SS by particle in
+// p.aC, 2 starts from it (S has not moved between the two fsi(S) of one hhs_fsi call, and
+// the deeper levels only touch other particles)
 template <bool MIXED>
-__device__ __noinline__ void b_fsi(const SubParams &p, const SubWork &w, const int32_t *S, int nS, double dt, Counts &cnt)
+__device__ __noinline__ void b_fsi(const SubParams &p, const SubWork &w, const int32_t *S, int nS, double dt, Counts &cnt,
+                                   int cache = 0)
 {
     if (nS <= 0) return;
     if (threadIdx.x == 0) cnt.fsi += 1;
-    b_acc<MIXED>(p, w, S, nS, S, nS, true, false, w.aA, nullptr, cnt);
-    b_kick(p, S, nS, w.aA, dt / 6.0);
+    if (nS < 2) cache = 0;
+    if (cache == 2) {
+        if (threadIdx.x == 0) cnt.reused += (unsigned long long)nS * (nS - 1);
+        for (int k = t_id(p); k < nS; k += t_n(p)) {
+            const int i = S[k];
+            for (int c = 0; c < 3; ++c)
+                p.v[c * p.N + i] = __dadd_rn(p.v[c * p.N + i], __dmul_rn(dt / 6.0, p.aC[c * p.N + i]));
+        }
+        t_sync(p);
+    } else {
+        b_acc<MIXED>(p, w, S, nS, S, nS, true, false, w.aA, nullptr, cnt);
+        b_kick(p, S, nS, w.aA, dt / 6.0);
+    }
     b_drift(p, S, nS, 0.5 * dt);
     b_acc<MIXED>(p, w, S, nS, S, nS, true, true, w.aA, w.wA, cnt);
     b_grad<MIXED>(p, w, S, nS, w.aA, S, nS, w.aA, true, dt, MIXED ? w.wA : nullptr, w.atA, cnt);
     b_kick(p, S, nS, w.atA, 2.0 * dt / 3.0);
     b_drift(p, S, nS, 0.5 * dt);
     b_acc<MIXED>(p, w, S, nS, S, nS, true, false, w.aA, nullptr, cnt);
+    if (cache == 1) {
+        for (int k = t_id(p); k < nS; k += t_n(p)) {
+            const int i = S[k];
+            for (int c = 0; c < 3; ++c) p.aC[c * p.N + i] = w.aA[c * nS + k];
+        }
+    }
     b_kick(p, S, nS, w.aA, dt / 6.0);
 }
 
@@ -1091,7 +1113,7 @@ __global__ void __launch_bounds__(SB) k_hhs_subtree(SubParams p0, SubWork w0, co
     w.wB += off;
     w.recA += 4 * (size_t)off;
     w.recB += 4 * (size_t)off;
-    Counts cnt = {0, 0, 0, 0, 0, depth0};
+    Counts cnt = {0, 0, 0, 0, 0, depth0, 0};
     if (tid == 0) s_abort = 0;
     for (int step = 0; step < n_steps; ++step) {
         for (int k = t_id(p); k < n; k += t_n(p)) w.perm[k] = offsets ? off + k : P[k];
@@ -1153,7 +1175,7 @@ __global__ void __launch_bounds__(SB) k_hhs_subtree(SubParams p0, SubWork w0, co
                 nS = b_partition(p, S, fn, w.tau, ftau, w.tmp);
                 const int nF = fn - nS;
                 b_kick_sf<MIXED>(p, w, S, nS, S + nS, nF, ftau / 6.0, false, ftau, cnt);
-                b_fsi<MIXED>(p, w, S, nS, 0.5 * ftau, cnt);
+                b_fsi<MIXED>(p, w, S, nS, 0.5 * ftau, cnt, 1);
                 if (tid == 0) {
                     f_ns[top] = nS;
                     f_pc[top] = 1;
@@ -1189,7 +1211,7 @@ __global__ void __launch_bounds__(SB) k_hhs_subtree(SubParams p0, SubWork w0, co
                 }
             } else {
                 const int nF = fn - nS;
-                b_fsi<MIXED>(p, w, S, nS, 0.5 * ftau, cnt);
+                b_fsi<MIXED>(p, w, S, nS, 0.5 * ftau, cnt, 2);
                 b_kick_sf<MIXED>(p, w, S, nS, S + nS, nF, ftau / 6.0, false, ftau, cnt);
                 if (tid == 0) s_sp -= 1;
             }
@@ -1205,6 +1227,7 @@ __global__ void __launch_bounds__(SB) k_hhs_subtree(SubParams p0, SubWork w0, co
         atomicAdd(&p.counters[3], cnt.hhs);
         atomicAdd(&p.counters[4], cnt.fsi);
         atomicMax(&p.counters[5], (unsigned long long)cnt.maxdepth);
+        atomicAdd(&p.counters[6], cnt.reused);
     }
 }
 
@@ -1224,6 +1247,7 @@ cudaError_t launch_subtree(cudaStream_t s, bool mixed, int sym, const SubtreeArg
     p.err = a.err;
     p.counters = a.counters;
     p.levels = a.levels;
+    p.aC = a.aC;
     SubWork w;
     w.perm = a.perm;
     w.tmp = a.tmp;

@@ -46,7 +46,8 @@ class frost_stats(ctypes.Structure):
                 ("max_depth_seen", ctypes.c_int32), ("timing_enabled", ctypes.c_int32),
                 ("timed_launches", ctypes.c_int64 * 4), ("timed_ms", ctypes.c_double * 4),
                 ("timed_pairs", ctypes.c_int64 * 4), ("subtree_launches", ctypes.c_int64),
-                ("level_calls", ctypes.c_int64 * 48), ("level_particles", ctypes.c_int64 * 48)]
+                ("level_calls", ctypes.c_int64 * 48), ("level_particles", ctypes.c_int64 * 48),
+                ("acc_pairs_reused", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -79,6 +80,7 @@ _SIGS = {
     "frost_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(frost_stats)]),
     "frost_reset_stats": (ctypes.c_int, [_P]),
     "frost_set_timing": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "frost_autotune": (ctypes.c_int, [_P, _P]),
     "frost_synchronize": (ctypes.c_int, [_P]),
     "frost_clear_error": (ctypes.c_int, [_P]),
     "frost_destroy": (None, [_P]),
@@ -235,6 +237,15 @@ def frost_reset_stats(ctx) -> None:
 
 def frost_set_timing(ctx, enable: bool) -> None:
     _check(load().frost_set_timing(ctx, 1 if enable else 0), "frost_set_timing")
+
+
+def frost_autotune(ctx):
+    """Run the launch-shape autotuner; returns {kind: {size: waves}} of the choices made."""
+    out = (ctypes.c_int32 * 96)()
+    _check(load().frost_autotune(ctx, out), "frost_autotune")
+    kinds = ("acc", "grad", "tstep")
+    return {kinds[q]: {1 << k: int(out[q * 32 + k]) for k in range(32) if out[q * 32 + k] > 0}
+            for q in range(3)}
 
 
 def frost_synchronize(ctx) -> None:
@@ -399,6 +410,9 @@ class Frost:
 
     def set_timing(self, on: bool):
         frost_set_timing(self.ctx, on)
+
+    def autotune(self):
+        return frost_autotune(self.ctx)
 
 
 def _as_f64(a):

@@ -159,6 +159,31 @@ def test_accel_gradient_hard_binaries(precision, cross):
     f.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autotune_keeps_results(precision):
+    """The launch-shape autotuner only changes how the sources are split: after it, a full
+    acc + gradient pass still meets the parity bounds, and every size 512..N got a choice."""
+    n = 4096
+    m, x, v = ics.plummer(n, 31, masses=ics.kroupa_masses(n, 31))
+    f = F(m, x, v, precision=precision)
+    table = f.autotune()
+    for kind in ("acc", "grad", "tstep"):
+        assert sorted(table[kind]) == [512, 1024, 2048, 4096], table
+        assert all(w in (1, 2, 4, 8, 16) for w in table[kind].values())
+    out = f.accel_gradient(None, None, eps_grad=0.01)
+    A = np.arange(n, dtype=np.int32)
+    a_ref, g_ref = oracle_g(m, x, A, A)
+    ea, eg = rel(cpu(out["acc"]), a_ref), rel(cpu(out["grad"]), g_ref)
+    if precision == "fp64":
+        assert ea.max() < 1e-12 and eg.max() < 1e-12
+    else:
+        assert p999(ea) < 1e-6 and p999(eg) < 1e-6
+    tau = cpu(f.timesteps())
+    et = rel(tau, oracle.timesteps(m, x, v, A, eta=0.2))
+    assert (et.max() < 1e-12) if precision == "fp64" else (p999(et) < 2e-6)
+    f.close()
+
+
 def test_accel_gradient_two_body_closed_form():
     """Pin on the GPU path itself: two bodies give a~ = (1 + eps^2 G M / (12 r^3)) a."""
     G = 1.3
@@ -485,7 +510,8 @@ def test_cluster_batch_with_block_teams(precision):
     off[1:] = np.cumsum(sizes)
     m, x, v = np.concatenate(ms), np.concatenate(xs), np.concatenate(vs)
     f = F(m, x, v, precision=precision, eta=0.2, offsets=off)
-    f.step(2.0 ** -6, 2)
+    f.step(2.0 ** -6, 1)  # captures the batch step as a CUDA graph
+    f.step(2.0 ** -6, 1)  # replays it
     xg, vg, t = f.state()
     st = f.stats()
     assert st["max_depth_seen"] >= 1

@@ -33,6 +33,7 @@ _lib = None
 
 OK, EINVAL, ENOMEM, ENONFINITE, ECOINCIDENT, EDEPTH = 0, 1, 2, 4, 5, 6
 SYM_HARMONIC, SYM_ARITHMETIC, SYM_NONE = 0, 1, 2
+FLYBY_EXACT = 4  # or-ed into sym: exact fly-by derivative (first line of Eq. dt-flyby-derivative)
 
 
 class OracleError(RuntimeError):
@@ -72,11 +73,14 @@ def _load():
             lib.or_accel_gradient.argtypes = [i64, P, P, P, i64, P, i64, d, d, d, P, P]
             lib.or_pair_timescales.argtypes = [P, P, d, P, P, d, d, P]
             lib.or_pair_timescales.restype = None
+            lib.or_pair_timescales_exact.argtypes = [P, P, P, d, P, P, P, d, d, P]
+            lib.or_pair_timescales_exact.restype = None
             lib.or_sym_harmonic.argtypes = [d]
             lib.or_sym_harmonic.restype = d
             lib.or_sym_arithmetic.argtypes = [d]
             lib.or_sym_arithmetic.restype = d
             lib.or_timesteps.argtypes = [P, P, P, P, i64, d, d, ci, P]
+            lib.or_timesteps_ex.argtypes = [P, P, P, P, i64, P, i64, d, d, d, ci, P]
             lib.or_timesteps_of.argtypes = [P, P, P, P, i64, P, i64, d, d, ci, P]
             lib.or_partition.argtypes = [P, i64, P, d, P, P, P, P]
             lib.or_partition.restype = None
@@ -174,6 +178,16 @@ def pair_timescales(xi, vi, mi, xj, vj, mj, G=1.0):
     return tuple(out)
 
 
+def pair_timescales_exact(xi, vi, ai, mi, xj, vj, aj, mj, G=1.0):
+    """(t_ff, dt_ff/dt, t_fb, dt_fb/dt) of one pair with the exact fly-by derivative, given the
+    accelerations a_i, a_j."""
+    xi, vi, ai, xj, vj, aj = _f64(xi), _f64(vi), _f64(ai), _f64(xj), _f64(vj), _f64(aj)
+    out = np.zeros(4)
+    _load().or_pair_timescales_exact(_p(xi), _p(vi), _p(ai), float(mi), _p(xj), _p(vj), _p(aj), float(mj), G,
+                                     _p(out))
+    return tuple(out)
+
+
 def sym_harmonic(d: float) -> float:
     return _load().or_sym_harmonic(float(d))
 
@@ -188,6 +202,16 @@ def timesteps(m, x, v, P, G=1.0, eta=0.2, sym=SYM_HARMONIC):
     out = np.zeros(P.size)
     _check(_load().or_timesteps(_p(m), _p(x), _p(v), _p(P), P.size, G, eta, sym, _p(out)),
            "timesteps")
+    return out
+
+
+def timesteps_ex(m, x, v, A, P, G=1.0, eta=0.2, eps2=0.0, sym=SYM_HARMONIC):
+    """Time-steps of the particles A over the set P; sym may carry FLYBY_EXACT (accelerations of
+    the set due to itself, softened by eps2)."""
+    m, x, v, A, P = _f64(m), _f64(x, (-1, 3)), _f64(v, (-1, 3)), _i32(A), _i32(P)
+    out = np.zeros(A.size)
+    _check(_load().or_timesteps_ex(_p(m), _p(x), _p(v), _p(A), A.size, _p(P), P.size, G, eta, eps2, int(sym),
+                                   _p(out)), "timesteps_ex")
     return out
 
 

@@ -13,7 +13,8 @@
  *                      (Eqs. dt-freefall-derivative, dt-flyby-derivative, two-body form)
  *   or_sym_harmonic    harmonic symmetrisation factor, Eq. time-step-factor (Sec. 4.2)
  *   or_sym_arithmetic  arithmetic symmetrisation factor, Eq. time-step-factor (Sec. 4.2)
- *   or_timesteps       tau_i = min_j of the symmetrised pair timescales (Sec. 4.3)
+ *   or_timesteps       tau_i = min_j of the symmetrised pair timescales (Sec. 4.3);
+ *                      or_timesteps_ex adds the exact fly-by derivative variant
  *   or_partition       slow/fast split by the pivot step (Sec. 3.1)
  *   or_kick, or_drift  kick / drift (Sec. 5.3)
  *   or_fsi             Algorithm fsi (Eq. fsi)
@@ -58,6 +59,10 @@
 #define OR_ENONFINITE 4
 #define OR_ECOINCIDENT 5
 #define OR_EDEPTH 6
+
+/* flag or-ed into the symmetrisation selector: exact fly-by derivative (Eq.
+ * dt-flyby-derivative, first line) instead of its two-body approximation */
+#define OR_FLYBY_EXACT 4
 
 /* passes with fewer pair evaluations than this run on one thread (a parallel region per
  * few-body pass would cost more than the pass) */
@@ -274,6 +279,26 @@ void or_pair_timescales(const double *xi, const double *vi, double mi, const dou
     }
 }
 
+/* The same with the exact fly-by derivative (first line of Eq. dt-flyby-derivative):
+ * d t_fb / dt = [ r.v / r^2 - v.a / v^2 ] t_fb with the relative acceleration a = a_i - a_j
+ * (instead of its two-body approximation -G (m_i + m_j) r / r^3). */
+void or_pair_timescales_exact(const double *xi, const double *vi, const double *ai, double mi,
+                              const double *xj, const double *vj, const double *aj, double mj, double G,
+                              double *out)
+{
+    or_pair_timescales(xi, vi, mi, xj, vj, mj, G, out);
+    const double rx = xi[0] - xj[0], ry = xi[1] - xj[1], rz = xi[2] - xj[2];
+    const double ux = vi[0] - vj[0], uy = vi[1] - vj[1], uz = vi[2] - vj[2];
+    const double wx = ai[0] - aj[0], wy = ai[1] - aj[1], wz = ai[2] - aj[2];
+    const double r2 = rx * rx + ry * ry + rz * rz;
+    const double v2 = ux * ux + uy * uy + uz * uz;
+    if (v2 > 0.0) {
+        const double rv = rx * ux + ry * uy + rz * uz;
+        const double va = ux * wx + uy * wy + uz * wz;
+        out[3] = (rv / r2 - va / v2) * out[2];
+    }
+}
+
 /* tau_sym / tau for the harmonic mean, with d = d tau / dt (Eq. time-step-factor, second
  * line).  With q = 1 + sqrt(1 + d^2) the printed factor (d + sqrt(1 + d^2) - 1) / d equals
  * (q + d) / q and also 2 / (q - d); each is free of cancellation on one side of d = 0 and
@@ -296,22 +321,50 @@ double or_sym_arithmetic(double d)
 /*
  * tau_i = min_{j in P, j != i} min( s(eta dt_ff/dt) eta t_ff, s(eta dt_fb/dt) eta t_fb )
  * for every i of the set P (Sec. 4.3: the pair timescales are symmetrised first, then the
- * minimum is taken).  sym = 0: harmonic factor, 1: arithmetic factor, 2: none (s = 1).
+ * minimum is taken).  sym & 3 = 0: harmonic factor, 1: arithmetic factor, 2: none (s = 1).
+ * sym & OR_FLYBY_EXACT: the exact fly-by derivative, with the accelerations of the set P due
+ * to P (reading: the level's own interactions, the same set the minimum runs over), softened
+ * by eps2 like the dynamics; otherwise its two-body approximation (no accelerations).
  */
-int or_timesteps_of(const double *m, const double *x, const double *v, const int32_t *A, int64_t nA,
-                    const int32_t *P, int64_t nP, double G, double eta, int sym, double *tau);
+int or_timesteps_ex(const double *m, const double *x, const double *v, const int32_t *A, int64_t nA,
+                    const int32_t *P, int64_t nP, double G, double eta, double eps2, int sym,
+                    double *tau);
 
 int or_timesteps(const double *m, const double *x, const double *v, const int32_t *P, int64_t nP,
                  double G, double eta, int sym, double *tau)
 {
-    return or_timesteps_of(m, x, v, P, nP, P, nP, G, eta, sym, tau);
+    return or_timesteps_ex(m, x, v, P, nP, P, nP, G, eta, 0.0, sym, tau);
 }
 
 /* tau of the particles A, the minimum taken over the set P (A may be a sample of P). */
 int or_timesteps_of(const double *m, const double *x, const double *v, const int32_t *A, int64_t nA,
                     const int32_t *P, int64_t nP, double G, double eta, int sym, double *tau)
 {
+    return or_timesteps_ex(m, x, v, A, nA, P, nP, G, eta, 0.0, sym, tau);
+}
+
+int or_timesteps_ex(const double *m, const double *x, const double *v, const int32_t *A, int64_t nA,
+                    const int32_t *P, int64_t nP, double G, double eta, double eps2, int sym,
+                    double *tau)
+{
     int err = OR_OK;
+    const int exact = (sym & OR_FLYBY_EXACT) != 0;
+    sym &= 3;
+    double *aA = NULL, *aP = NULL;
+    if (exact) {
+        aA = (double *)malloc(sizeof(double) * 3 * (size_t)(nA > 0 ? nA : 1));
+        aP = (double *)malloc(sizeof(double) * 3 * (size_t)(nP > 0 ? nP : 1));
+        if (!aA || !aP) {
+            free(aA);
+            free(aP);
+            return OR_ENOMEM;
+        }
+        if ((err = or_acc(m, x, A, nA, P, nP, G, eps2, aA)) || (err = or_acc(m, x, P, nP, P, nP, G, eps2, aP))) {
+            free(aA);
+            free(aP);
+            return err;
+        }
+    }
 #pragma omp parallel for schedule(dynamic, 16) reduction(max : err) if (nA * nP > OR_PAR_MIN)
     for (int64_t ia = 0; ia < nA; ++ia) {
         const int32_t i = A[ia];
@@ -320,7 +373,11 @@ int or_timesteps_of(const double *m, const double *x, const double *v, const int
             const int32_t j = P[jb];
             if (j == i) continue;
             double t[4];
-            or_pair_timescales(&x[3 * i], &v[3 * i], m[i], &x[3 * j], &v[3 * j], m[j], G, t);
+            if (exact)
+                or_pair_timescales_exact(&x[3 * i], &v[3 * i], &aA[3 * ia], m[i], &x[3 * j], &v[3 * j], &aP[3 * jb],
+                                         m[j], G, t);
+            else
+                or_pair_timescales(&x[3 * i], &v[3 * i], m[i], &x[3 * j], &v[3 * j], m[j], G, t);
             if (!(t[0] > 0.0)) { err = OR_ECOINCIDENT; continue; }
             for (int c = 0; c < 2; ++c) {
                 const double tc = t[2 * c];
@@ -336,6 +393,8 @@ int or_timesteps_of(const double *m, const double *x, const double *v, const int
         tau[ia] = best;
     }
     or_count_tstep += nA * nP;
+    free(aA);
+    free(aP);
     return err;
 }
 
@@ -442,7 +501,7 @@ static int hhs_fsi(or_sys *s, const int32_t *P, int64_t nP, double tau, int dept
     int32_t *F = (int32_t *)malloc(sizeof(int32_t) * (size_t)nP);
     int64_t nS = 0, nF = 0;
     if (!t || !S || !F) { err = OR_ENOMEM; goto done; }
-    err = or_timesteps(s->m, s->x, s->v, P, nP, s->G, s->eta, s->sym, t);
+    err = or_timesteps_ex(s->m, s->x, s->v, P, nP, P, nP, s->G, s->eta, s->eps2, s->sym, t);
     if (err) goto done;
     or_partition(P, nP, t, tau, S, &nS, F, &nF);
     if ((err = kick_sf(s, S, nS, F, nF, tau / 6.0, 0, tau))) goto done;

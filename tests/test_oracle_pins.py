@@ -341,6 +341,44 @@ def test_flyby_derivative_exact_on_isolated_binary(e):
         assert abs(t[1] - fd_ff) < 1e-6 * max(1.0, abs(fd_ff))
 
 
+def test_exact_flyby_derivative_along_the_nbody_motion():
+    """First line of Eq. dt-flyby-derivative: d t_fb / dt = [r.v/r^2 - v.a/v^2] t_fb with the
+    actual relative acceleration.  Pinned by a central difference of |r_ij| / |v_ij| (computed
+    here, independently) along the motion dx/dt = v, dv/dt = a of a small set, with a the
+    set's own (softened) accelerations from the Newtonian pass."""
+    n = 6
+    m, x, v = ics.plummer(n, 41)
+    P = np.arange(n, dtype=np.int32)
+    eps2 = 1e-4
+    a = oracle.acc(m, x, P, P, eps2=eps2)
+    h = 1e-5
+    for i, j in [(0, 1), (2, 5), (3, 4)]:
+        t = oracle.pair_timescales_exact(x[i], v[i], a[i], m[i], x[j], v[j], a[j], m[j])
+
+        def tfb(s):
+            xs, vs = x + s * v, v + s * a
+            return np.linalg.norm(xs[i] - xs[j]) / np.linalg.norm(vs[i] - vs[j])
+        fd = (tfb(h) - tfb(-h)) / (2 * h)
+        assert abs(t[3] - fd) < 1e-7 * max(abs(fd), t[2]), (i, j, t[3], fd)
+        # the two-body approximation differs (the tidal field of the other members)
+        t2 = oracle.pair_timescales(x[i], v[i], m[i], x[j], v[j], m[j])
+        assert t2[:3] == t[:3]
+
+
+def test_exact_flyby_equals_two_body_form_for_an_isolated_binary():
+    """For two bodies the relative acceleration is exactly the two-body one, so both lines of
+    Eq. dt-flyby-derivative give the same time-steps (to rounding)."""
+    for e in (0.0, 0.5, 0.95):
+        m, x, v = ics.kepler_binary(0.7, 0.3, 1.0, e)
+        P = np.arange(2, dtype=np.int32)
+        t0 = oracle.timesteps(m, x, v, P)
+        t1 = oracle.timesteps_ex(m, x, v, P, P, sym=oracle.FLYBY_EXACT)
+        assert np.allclose(t0, t1, rtol=1e-12, atol=0.0), (e, t0, t1)
+        for sym in (oracle.SYM_ARITHMETIC, oracle.SYM_NONE):
+            assert np.allclose(oracle.timesteps(m, x, v, P, sym=sym),
+                               oracle.timesteps_ex(m, x, v, P, P, sym=sym | oracle.FLYBY_EXACT), rtol=1e-12)
+
+
 def test_timesteps_min_over_set_and_degenerate_cases():
     """tau_i is the minimum over the other members of the set only (Sec. 4.3: 'the same
     level'), a single particle has tau = +inf, and zero relative velocity leaves only the

@@ -56,12 +56,18 @@ typedef enum {
 typedef enum {
     FROST_SYM_HARMONIC = 0,   /* harmonic symmetrisation, Eq. time-step-factor (second line) */
     FROST_SYM_ARITHMETIC = 1, /* arithmetic symmetrisation, Eq. time-step-factor (first line) */
-    FROST_SYM_NONE = 2        /* no symmetrisation (factor 1) */
+    FROST_SYM_NONE = 2,       /* no symmetrisation (factor 1) */
+    /* flag or-ed into one of the above: the exact fly-by derivative, Eq. dt-flyby-derivative
+     * (first line) with the relative acceleration of the pair, instead of its two-body
+     * approximation (second line, the default).  The accelerations are those of the level's
+     * set due to itself (a Newtonian pass before each time-step pass, softened like the
+     * dynamics). */
+    FROST_FLYBY_EXACT = 4
 } frost_sym;
 
 typedef struct {
     int32_t precision;  /* frost_precision */
-    int32_t sym;        /* frost_sym */
+    int32_t sym;        /* frost_sym value, optionally | FROST_FLYBY_EXACT */
     double eps_soft;    /* Plummer softening length eps_P (Sec. 2.3); 0 = unsoftened */
     int32_t max_depth;  /* deepest hhs_fsi level allowed (top level = 0); <= 0 means 40 */
     void *cuda_stream;  /* cudaStream_t for all work; NULL = the legacy default stream */
@@ -79,7 +85,7 @@ void frost_default_opts(frost_opts *opt);
  * v[n][3] (host or device; copied), Newton's constant G and accuracy parameter eta
  * (eta = eta_ff = eta_fb, Sec. 4.3).  opt may be NULL for the defaults.  n >= 1 and
  * n < 2^31.  Non-finite inputs or non-positive masses give FROST_ENONFINITE / FROST_EINVAL.
- * The context allocates about (250 + 32 * levels_used) bytes per particle of device memory.
+ * The context allocates about (330 + 32 * levels_used) bytes per particle of device memory.
  * On failure *ctx is NULL.
  */
 frost_status frost_init(frost_ctx **ctx, int64_t n, const double *m, const double *x,

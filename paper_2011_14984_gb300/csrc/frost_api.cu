@@ -69,6 +69,10 @@ struct Timed {
 
 }  // namespace
 
+// bytes of packed pair records per particle in recA / recB (up to six 16-byte records: the
+// FP64 time-step records with accelerations)
+constexpr size_t kRecBytes = 96;
+
 // batch teams: clusters of at least kBatchTeamMinN particles run on kBatchTeamBlocks blocks
 constexpr int64_t kBatchTeamMinN = 768;
 constexpr int kBatchTeamBlocks = 8;
@@ -415,8 +419,14 @@ void pass_tstep(frost_ctx *c, const int32_t *P, int nP, double *tau)
         c->st.kernel_launches += 1;
         return;
     }
-    if (c->mixed) launch_pack_tstep_mixed(c->stream, P, nP, c->x, c->v, c->m, c->N, c->G, (float4 *)c->recA);
-    else launch_pack_tstep_fp64(c->stream, P, nP, c->x, c->v, c->m, c->N, c->G, (double4_32a *)c->recA);
+    // exact fly-by derivative: the accelerations of the set due to itself, packed with the records
+    const double *acc = nullptr;
+    if (c->sym & FROST_FLYBY_EXACT) {
+        pass_acc(c, P, nP, P, nP, true, c->aB, nullptr);
+        acc = c->aB;
+    }
+    if (c->mixed) launch_pack_tstep_mixed(c->stream, P, nP, c->x, c->v, c->m, c->N, c->G, (float4 *)c->recA, acc);
+    else launch_pack_tstep_fp64(c->stream, P, nP, c->x, c->v, c->m, c->N, c->G, (double4_32a *)c->recA, acc);
     PairArgs a;
     a.irec = c->recA;
     a.jrec = c->recA;
@@ -751,7 +761,8 @@ static frost_status init_impl(frost_ctx **out, int64_t n, const double *m, const
     if (opt) o = *opt;
     if (o.precision != FROST_PREC_FP64 && o.precision != FROST_PREC_MIXED)
         return fail(FROST_EINVAL, "unknown precision %d", o.precision);
-    if (o.sym < 0 || o.sym > 2) return fail(FROST_EINVAL, "unknown symmetrisation %d", o.sym);
+    if (o.sym < 0 || (o.sym & ~FROST_FLYBY_EXACT) > 2 || o.sym > 6)
+        return fail(FROST_EINVAL, "unknown symmetrisation %d", o.sym);
     if (!(o.eps_soft >= 0.0) || !std::isfinite(o.eps_soft)) return fail(FROST_EINVAL, "bad softening");
 
     frost_ctx *c = new (std::nothrow) frost_ctx();
@@ -787,8 +798,8 @@ static frost_status init_impl(frost_ctx **out, int64_t n, const double *m, const
     INIT_CUDA(cudaMalloc(&c->m, sizeof(double) * N));
     INIT_CUDA(cudaMalloc(&c->all, sizeof(int32_t) * N));
     INIT_CUDA(cudaMalloc(&c->marks, sizeof(int32_t) * N));
-    INIT_CUDA(cudaMalloc(&c->recA, 64 * N));
-    INIT_CUDA(cudaMalloc(&c->recB, 64 * N));
+    INIT_CUDA(cudaMalloc(&c->recA, kRecBytes * N));
+    INIT_CUDA(cudaMalloc(&c->recB, kRecBytes * N));
     int bps = 1;
     for (int k = 0; k < 3; ++k) bps = std::max(bps, pair_blocks_per_sm(k, c->mixed));
     bps = std::max(bps, pair_blocks_per_sm(PASS_ACC, false));
@@ -1231,11 +1242,17 @@ frost_status frost_autotune(frost_ctx *c, int32_t *waves_out)
                 if (c->mixed) launch_pack_grad_mixed(c->stream, c->all, n, c->x, c->m, c->N, c->aB, (float4 *)c->recA);
                 else launch_pack_grad_fp64(c->stream, c->all, n, c->x, c->m, c->N, c->aB, (double4_32a *)c->recA);
             } else {
+                const double *acc = nullptr;
+                if (c->sym & FROST_FLYBY_EXACT) {
+                    cudaMemsetAsync(c->aB, 0, sizeof(double) * 3 * n, c->stream);
+                    acc = c->aB;
+                }
                 if (c->mixed)
-                    launch_pack_tstep_mixed(c->stream, c->all, n, c->x, c->v, c->m, c->N, c->G, (float4 *)c->recA);
+                    launch_pack_tstep_mixed(c->stream, c->all, n, c->x, c->v, c->m, c->N, c->G, (float4 *)c->recA,
+                                            acc);
                 else
                     launch_pack_tstep_fp64(c->stream, c->all, n, c->x, c->v, c->m, c->N, c->G,
-                                           (double4_32a *)c->recA);
+                                           (double4_32a *)c->recA, acc);
             }
             // time each distinct split once (several bounds can give the same launch)
             float tw[5];

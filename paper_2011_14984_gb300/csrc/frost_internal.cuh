@@ -72,14 +72,18 @@ void launch_pack_pos_mixed(cudaStream_t s, const int32_t *list, int n, const dou
 void launch_pack_grad_mixed(cudaStream_t s, const int32_t *list, int n, const double *x,
                             const double *m, int N, const double *acc /*[3][n]*/, float4 *rec,
                             const uint32_t *hot = nullptr);
+// acc (optional, [3][n] by list position): the set's accelerations, packed for the exact
+// fly-by derivative (record 3 mixed, record 2 FP64)
 void launch_pack_tstep_mixed(cudaStream_t s, const int32_t *list, int n, const double *x,
-                             const double *v, const double *m, int N, double G, float4 *rec);
+                             const double *v, const double *m, int N, double G, float4 *rec,
+                             const double *acc = nullptr);
 void launch_pack_pos_fp64(cudaStream_t s, const int32_t *list, int n, const double *x,
                           const double *m, int N, double4_32a *rec);
 void launch_pack_grad_fp64(cudaStream_t s, const int32_t *list, int n, const double *x,
                            const double *m, int N, const double *acc, double4_32a *rec);
 void launch_pack_tstep_fp64(cudaStream_t s, const int32_t *list, int n, const double *x,
-                            const double *v, const double *m, int N, double G, double4_32a *rec);
+                            const double *v, const double *m, int N, double G, double4_32a *rec,
+                            const double *acc = nullptr);
 
 // ---- pair kernels ---------------------------------------------------------------------
 // acc: part[split][c][i] = sum_j m_j x_ji / r^3 over the split's sources

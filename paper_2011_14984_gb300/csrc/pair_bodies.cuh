@@ -86,7 +86,8 @@ __device__ __forceinline__ void pack_tstep_mixed_one(int k, const int32_t *__res
                                                      const double *__restrict__ x,
                                                      const double *__restrict__ v,
                                                      const double *__restrict__ m, int N, double G,
-                                                     float4 *__restrict__ rec)
+                                                     float4 *__restrict__ rec,
+                                                     const double *__restrict__ acc = nullptr)
 {
     const int i = list ? list[k] : k;
     const double px = x[i], py = x[N + i], pz = x[2 * N + i];
@@ -96,6 +97,8 @@ __device__ __forceinline__ void pack_tstep_mixed_one(int k, const int32_t *__res
                              (float)(pz - (double)hz), 0.f);
     rec[2 * n + k] = make_float4((float)v[i], (float)v[N + i], (float)v[2 * N + i],
                                  (float)(G * m[i]));
+    // exact fly-by derivative: the accelerations of the set ([3][n], by list position)
+    if (acc) rec[3 * n + k] = make_float4((float)acc[k], (float)acc[n + k], (float)acc[2 * n + k], 0.f);
 }
 
 __device__ __forceinline__ void pack_pos_fp64_one(int k, const int32_t *__restrict__ list, int n,
@@ -122,11 +125,13 @@ __device__ __forceinline__ void pack_tstep_fp64_one(int k, const int32_t *__rest
                                                     const double *__restrict__ x,
                                                     const double *__restrict__ v,
                                                     const double *__restrict__ m, int N, double G,
-                                                    double4_32a *__restrict__ rec)
+                                                    double4_32a *__restrict__ rec,
+                                                    const double *__restrict__ acc = nullptr)
 {
     const int i = list ? list[k] : k;
     rec[k] = make_double4_32a(x[i], x[N + i], x[2 * N + i], m[i]);
     rec[n + k] = make_double4_32a(v[i], v[N + i], v[2 * N + i], G * m[i]);
+    if (acc) rec[2 * n + k] = make_double4_32a(acc[k], acc[n + k], acc[2 * n + k], 0.0);
 }
 template <int ILP>
 struct AccMixedI {
@@ -356,6 +361,7 @@ __device__ __forceinline__ double symd(double d)
 template <int ILP>
 struct TstepMixedI {
     float xh[ILP], yh[ILP], zh[ILP], xl[ILP], yl[ILP], zl[ILP], vx[ILP], vy[ILP], vz[ILP], gm[ILP];
+    float ax[ILP], ay[ILP], az[ILP];  // used with the exact fly-by derivative (SYM & 4)
 };
 
 // Pair time-steps without eta: best[k] = min(best[k], tau_ff_sym, tau_fb_sym), minr2[k] =
@@ -364,8 +370,11 @@ struct TstepMixedI {
 // t >= 1.001 best (1 + |d|) cannot lower the minimum; it is not symmetrised, and the warp
 // skips the factors (two MUFU sqrt/divide pairs) when no lane needs them.  The 0.1% margin
 // is far above the rounding of the factor, so the result is the one of the full evaluation.
+// SYM & 3 selects the factor (0 harmonic, 1 arithmetic, 2 none); SYM & 4 the exact fly-by
+// derivative [r.v/r^2 - v.a/v^2] t_fb with the relative acceleration JA - I.a (first line of
+// Eq. dt-flyby-derivative) instead of its two-body approximation.
 template <int ILP, int SYM, bool MASK>
-__device__ __forceinline__ void tstep_mixed_j(const float4 J0, const float4 J1, const float4 JV,
+__device__ __forceinline__ void tstep_mixed_j(const float4 J0, const float4 J1, const float4 JV, const float4 JA,
                                               const TstepMixedI<ILP> &I, float eta, float eta15,
                                               int jpos, const int (&ipos)[ILP],
                                               float (&best)[ILP], float (&minr2)[ILP])
@@ -390,7 +399,13 @@ __device__ __forceinline__ void tstep_mixed_j(const float4 J0, const float4 J1, 
         const float iv = rsqrtf(v2);                 // 1 / |v|
         tfb[k] = r2 * ri * iv;                       // r / |v|
         dff[k] = eta15 * rvr2 * tff[k];              // eta dt_ff/dt
-        dfb[k] = eta * rvr2 * fmaf(gm * ri, iv * iv, 1.f) * tfb[k];  // eta dt_fb/dt
+        if (SYM & 4) {
+            const float wx = JA.x - I.ax[k], wy = JA.y - I.ay[k], wz = JA.z - I.az[k];
+            const float va = fmaf(ux, wx, fmaf(uy, wy, uz * wz));
+            dfb[k] = eta * fmaf(-va, iv * iv, rvr2) * tfb[k];            // eta dt_fb/dt, exact
+        } else {
+            dfb[k] = eta * rvr2 * fmaf(gm * ri, iv * iv, 1.f) * tfb[k];  // eta dt_fb/dt, two-body
+        }
         float rr = r2;
         bool self = false;
         if (MASK) {
@@ -407,8 +422,8 @@ __device__ __forceinline__ void tstep_mixed_j(const float4 J0, const float4 J1, 
 #pragma unroll
         for (int k = 0; k < ILP; ++k) {
             float t = INFINITY;
-            if (nff[k]) t = tff[k] * symf<SYM>(dff[k]);
-            if (nfb[k]) t = fminf(t, tfb[k] * symf<SYM>(dfb[k]));
+            if (nff[k]) t = tff[k] * symf<(SYM & 3)>(dff[k]);
+            if (nfb[k]) t = fminf(t, tfb[k] * symf<(SYM & 3)>(dfb[k]));
             best[k] = fminf(best[k], t);
         }
     }
@@ -416,9 +431,9 @@ __device__ __forceinline__ void tstep_mixed_j(const float4 J0, const float4 J1, 
 
 // FP64 pair time-steps, with the same bound on the symmetrisation factors
 template <int SYM, bool MASK>
-__device__ __forceinline__ void tstep_fp64_j(const double4_32a J, const double4_32a JV, const double4_32a I,
-                                             const double4_32a IV, double eta, int jpos, int ipos,
-                                             double &best, double &minr2)
+__device__ __forceinline__ void tstep_fp64_j(const double4_32a J, const double4_32a JV, const double4_32a JA,
+                                             const double4_32a I, const double4_32a IV, const double4_32a IA,
+                                             double eta, int jpos, int ipos, double &best, double &minr2)
 {
     const double dx = J.x - I.x, dy = J.y - I.y, dz = J.z - I.z;
     const double ux = JV.x - IV.x, uy = JV.y - IV.y, uz = JV.z - IV.z;
@@ -433,7 +448,12 @@ __device__ __forceinline__ void tstep_fp64_j(const double4_32a J, const double4_
     double tfb = INFINITY, dfb = 0.0;
     if (v2 > 0.0) {
         tfb = r / sqrt(v2);
-        dfb = eta * rvr2 * (1.0 + gm / (v2 * r)) * tfb;
+        if (SYM & 4) {
+            const double va = fma(ux, JA.x - IA.x, fma(uy, JA.y - IA.y, uz * (JA.z - IA.z)));
+            dfb = eta * (rvr2 - va / v2) * tfb;
+        } else {
+            dfb = eta * rvr2 * (1.0 + gm / (v2 * r)) * tfb;
+        }
     }
     const bool self = MASK && jpos == ipos;
     if (!self) minr2 = fmin(minr2, r2);
@@ -442,8 +462,8 @@ __device__ __forceinline__ void tstep_fp64_j(const double4_32a J, const double4_
     const bool nfb = !self && (v2 > 0.0) && (tfb < bnd * (1.0 + fabs(dfb)));
     if (__any_sync(0xffffffffu, nff || nfb)) {
         double t = INFINITY;
-        if (nff) t = tff * symd<SYM>(dff);
-        if (nfb) t = fmin(t, tfb * symd<SYM>(dfb));
+        if (nff) t = tff * symd<(SYM & 3)>(dff);
+        if (nfb) t = fmin(t, tfb * symd<(SYM & 3)>(dfb));
         best = fmin(best, t);
     }
 }
@@ -714,23 +734,26 @@ __device__ __forceinline__ void tstep_mixed_body(const float4 *__restrict__ irec
                                                  int ibase, int jb, int je, int self_pass, float eta,
                                                  float (&best)[ILP], float (&minr2)[ILP])
 {
-    __shared__ float4 s0[TJ], s1[TJ], sv[TJ];
+    __shared__ float4 s0[TJ], s1[TJ], sv[TJ], sa[(SYM & 4) ? TJ : 1];
     const int tid = threadIdx.x;
     TstepMixedI<ILP> I;
     int ipos[ILP];
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < ILP; ++k) {
         const int i = ibase + k * BS + tid;
         ipos[k] = i;
-        float4 a = make_float4(0.f, 0.f, 0.f, 1.f), b = make_float4(0.f, 0.f, 0.f, 0.f), c = a;
+        float4 a = make_float4(0.f, 0.f, 0.f, 1.f), b = make_float4(0.f, 0.f, 0.f, 0.f), c = a, d = b;
         if (i < n_a) {
             a = irec[i];
             b = irec[n_a + i];
             c = irec[2 * n_a + i];
+            if (SYM & 4) d = irec[3 * n_a + i];
         }
         I.xh[k] = a.x; I.yh[k] = a.y; I.zh[k] = a.z;
         I.xl[k] = b.x; I.yl[k] = b.y; I.zl[k] = b.z;
         I.vx[k] = c.x; I.vy[k] = c.y; I.vz[k] = c.z; I.gm[k] = c.w;
+        I.ax[k] = d.x; I.ay[k] = d.y; I.az[k] = d.z;
     }
 #pragma unroll
     for (int k = 0; k < ILP; ++k) best[k] = minr2[k] = INFINITY;
@@ -742,6 +765,7 @@ __device__ __forceinline__ void tstep_mixed_body(const float4 *__restrict__ irec
             s0[t] = jrec[j0 + t];
             s1[t] = jrec[n_s + j0 + t];
             sv[t] = jrec[2 * n_s + j0 + t];
+            if (SYM & 4) sa[t] = jrec[3 * n_s + j0 + t];
         }
         __syncthreads();
         const bool diag = self_pass && (j0 < ibase + BS * ILP) && (ibase < j0 + cnt);
@@ -750,15 +774,17 @@ __device__ __forceinline__ void tstep_mixed_body(const float4 *__restrict__ irec
             for (; jj + 4 <= cnt; jj += 4) {
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
-                    tstep_mixed_j<ILP, SYM, false>(s0[jj + u], s1[jj + u], sv[jj + u], I, eta, eta15, 0,
-                                                   ipos, best, minr2);
+                    tstep_mixed_j<ILP, SYM, false>(s0[jj + u], s1[jj + u], sv[jj + u],
+                                                   (SYM & 4) ? sa[jj + u] : zero4, I, eta, eta15, 0, ipos,
+                                                   best, minr2);
             }
             for (; jj < cnt; ++jj)
-                tstep_mixed_j<ILP, SYM, false>(s0[jj], s1[jj], sv[jj], I, eta, eta15, 0, ipos, best, minr2);
+                tstep_mixed_j<ILP, SYM, false>(s0[jj], s1[jj], sv[jj], (SYM & 4) ? sa[jj] : zero4, I, eta, eta15,
+                                               0, ipos, best, minr2);
         } else {
             for (; jj < cnt; ++jj)
-                tstep_mixed_j<ILP, SYM, true>(s0[jj], s1[jj], sv[jj], I, eta, eta15, j0 + jj, ipos, best,
-                                              minr2);
+                tstep_mixed_j<ILP, SYM, true>(s0[jj], s1[jj], sv[jj], (SYM & 4) ? sa[jj] : zero4, I, eta, eta15,
+                                              j0 + jj, ipos, best, minr2);
         }
     }
 }
@@ -841,13 +867,15 @@ __device__ __forceinline__ void tstep_fp64_body(const double4_32a *__restrict__ 
                                                 int ibase, int jb, int je, int self_pass, double eta,
                                                 double &best, double &minr2)
 {
-    __shared__ double4_32a s0[TJ], sv[TJ];
+    __shared__ double4_32a s0[TJ], sv[TJ], sa[(SYM & 4) ? TJ : 1];
     const int tid = threadIdx.x;
     const int i = ibase + tid;
-    double4_32a I = make_double4_32a(0.0, 0.0, 0.0, 1.0), IV = make_double4_32a(0.0, 0.0, 0.0, 1.0);
+    const double4_32a zero4 = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    double4_32a I = make_double4_32a(0.0, 0.0, 0.0, 1.0), IV = make_double4_32a(0.0, 0.0, 0.0, 1.0), IA = zero4;
     if (i < n_a) {
         I = irec[i];
         IV = irec[n_a + i];
+        if (SYM & 4) IA = irec[2 * n_a + i];
     }
     best = INFINITY;
     minr2 = INFINITY;
@@ -857,14 +885,18 @@ __device__ __forceinline__ void tstep_fp64_body(const double4_32a *__restrict__ 
         for (int t = tid; t < cnt; t += BS) {
             s0[t] = jrec[j0 + t];
             sv[t] = jrec[n_s + j0 + t];
+            if (SYM & 4) sa[t] = jrec[2 * n_s + j0 + t];
         }
         __syncthreads();
         const bool diag = self_pass && (j0 < ibase + BS) && (ibase < j0 + cnt);
         if (!diag) {
-            for (int jj = 0; jj < cnt; ++jj) tstep_fp64_j<SYM, false>(s0[jj], sv[jj], I, IV, eta, 0, i, best, minr2);
+            for (int jj = 0; jj < cnt; ++jj)
+                tstep_fp64_j<SYM, false>(s0[jj], sv[jj], (SYM & 4) ? sa[jj] : zero4, I, IV, IA, eta, 0, i, best,
+                                         minr2);
         } else {
             for (int jj = 0; jj < cnt; ++jj)
-                tstep_fp64_j<SYM, true>(s0[jj], sv[jj], I, IV, eta, j0 + jj, i, best, minr2);
+                tstep_fp64_j<SYM, true>(s0[jj], sv[jj], (SYM & 4) ? sa[jj] : zero4, I, IV, IA, eta, j0 + jj, i,
+                                        best, minr2);
         }
     }
 }

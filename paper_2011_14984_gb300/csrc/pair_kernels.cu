@@ -49,10 +49,10 @@ __global__ void k_pack_grad_mixed(const int32_t *__restrict__ list, int n, const
 
 __global__ void k_pack_tstep_mixed(const int32_t *__restrict__ list, int n, const double *__restrict__ x,
                                    const double *__restrict__ v, const double *__restrict__ m, int N,
-                                   double G, float4 *__restrict__ rec)
+                                   double G, float4 *__restrict__ rec, const double *__restrict__ acc)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) pack_tstep_mixed_one(k, list, n, x, v, m, N, G, rec);
+    if (k < n) pack_tstep_mixed_one(k, list, n, x, v, m, N, G, rec, acc);
 }
 
 __global__ void k_pack_pos_fp64(const int32_t *__restrict__ list, int n, const double *__restrict__ x,
@@ -72,10 +72,10 @@ __global__ void k_pack_grad_fp64(const int32_t *__restrict__ list, int n, const 
 
 __global__ void k_pack_tstep_fp64(const int32_t *__restrict__ list, int n, const double *__restrict__ x,
                                   const double *__restrict__ v, const double *__restrict__ m, int N,
-                                  double G, double4_32a *__restrict__ rec)
+                                  double G, double4_32a *__restrict__ rec, const double *__restrict__ acc)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) pack_tstep_fp64_one(k, list, n, x, v, m, N, G, rec);
+    if (k < n) pack_tstep_fp64_one(k, list, n, x, v, m, N, G, rec, acc);
 }
 
 // ------------------------------------------------------------------------------------
@@ -362,10 +362,10 @@ void launch_pack_grad_mixed(cudaStream_t s, const int32_t *list, int n, const do
     k_pack_grad_mixed<<<cdiv(n, 256), 256, 0, s>>>(list, n, x, m, N, acc, rec, hot);
 }
 void launch_pack_tstep_mixed(cudaStream_t s, const int32_t *list, int n, const double *x,
-                             const double *v, const double *m, int N, double G, float4 *rec)
+                             const double *v, const double *m, int N, double G, float4 *rec, const double *acc)
 {
     if (n <= 0) return;
-    k_pack_tstep_mixed<<<cdiv(n, 256), 256, 0, s>>>(list, n, x, v, m, N, G, rec);
+    k_pack_tstep_mixed<<<cdiv(n, 256), 256, 0, s>>>(list, n, x, v, m, N, G, rec, acc);
 }
 void launch_pack_pos_fp64(cudaStream_t s, const int32_t *list, int n, const double *x,
                           const double *m, int N, double4_32a *rec)
@@ -380,10 +380,11 @@ void launch_pack_grad_fp64(cudaStream_t s, const int32_t *list, int n, const dou
     k_pack_grad_fp64<<<cdiv(n, 256), 256, 0, s>>>(list, n, x, m, N, acc, rec);
 }
 void launch_pack_tstep_fp64(cudaStream_t s, const int32_t *list, int n, const double *x,
-                            const double *v, const double *m, int N, double G, double4_32a *rec)
+                            const double *v, const double *m, int N, double G, double4_32a *rec,
+                            const double *acc)
 {
     if (n <= 0) return;
-    k_pack_tstep_fp64<<<cdiv(n, 256), 256, 0, s>>>(list, n, x, v, m, N, G, rec);
+    k_pack_tstep_fp64<<<cdiv(n, 256), 256, 0, s>>>(list, n, x, v, m, N, G, rec, acc);
 }
 
 int pair_i_per_block(bool mixed) { return mixed ? PAIR_BS * PAIR_ILP : PAIR_BS; }
@@ -484,12 +485,14 @@ void launch_tstep(cudaStream_t s, bool mixed, const PairArgs &a, double eta, int
         k_tstep_fp64<PAIR_BS, PAIR_TJ, SYMV><<<grid, PAIR_BS, 0, s>>>(                            \
             (const double4_32a *)a.irec, (const double4_32a *)a.jrec, a.n_a, a.n_s, a.shape.j_per_split,  \
             a.self_pass, eta, a.part, err);
-    if (sym == 0) {
-        FROST_TSTEP_CASE(0)
-    } else if (sym == 1) {
-        FROST_TSTEP_CASE(1)
-    } else {
-        FROST_TSTEP_CASE(2)
+    // sym & 3: symmetrisation factor; sym & 4: exact fly-by derivative (records with a)
+    switch (sym) {
+    case 0: FROST_TSTEP_CASE(0) break;
+    case 1: FROST_TSTEP_CASE(1) break;
+    case 4: FROST_TSTEP_CASE(4) break;
+    case 5: FROST_TSTEP_CASE(5) break;
+    case 6: FROST_TSTEP_CASE(6) break;
+    default: FROST_TSTEP_CASE(2) break;
     }
 #undef FROST_TSTEP_CASE
 }

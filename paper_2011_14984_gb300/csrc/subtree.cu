@@ -323,25 +323,30 @@ __device__ __noinline__ void mt_tstep(const SubParams &p, const void *rec, int n
             const float4 *r = (const float4 *)rec;
             TstepMixedI<1> I;
             const float4 a = r[i], b = r[n + i], cc = r[2 * n + i];
+            const float4 da = (SYM & 4) ? r[3 * n + i] : make_float4(0.f, 0.f, 0.f, 0.f);
             I.xh[0] = a.x; I.yh[0] = a.y; I.zh[0] = a.z;
             I.xl[0] = b.x; I.yl[0] = b.y; I.zl[0] = b.z;
             I.vx[0] = cc.x; I.vy[0] = cc.y; I.vz[0] = cc.z; I.gm[0] = cc.w;
+            I.ax[0] = da.x; I.ay[0] = da.y; I.az[0] = da.z;
             const float eta = (float)p.eta, eta15 = 1.5f * eta;
             float best[1] = {INFINITY}, minr2[1] = {INFINITY};
             for (int q = 0; q < nq; ++q) {
                 const MtSrc s = mt_src(q, T, l, n, i, true);
-                tstep_mixed_j<1, SYM, true>(r[s.j], r[n + s.j], r[2 * n + s.j], I, eta, eta15, s.jpos, ipos, best,
-                                            minr2);
+                const float4 JA = (SYM & 4) ? r[3 * n + s.j] : make_float4(0.f, 0.f, 0.f, 0.f);
+                tstep_mixed_j<1, SYM, true>(r[s.j], r[n + s.j], r[2 * n + s.j], JA, I, eta, eta15, s.jpos, ipos,
+                                            best, minr2);
             }
             t = p.eta * (double)grp_min(best[0], T);
             coincident = grp_min(minr2[0], T) == 0.f;
         } else {
             const double4_32a *r = (const double4_32a *)rec;
-            const double4_32a I = r[i], IV = r[n + i];
+            const double4_32a zero4 = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+            const double4_32a I = r[i], IV = r[n + i], IA = (SYM & 4) ? r[2 * n + i] : zero4;
             double best = INFINITY, minr2 = INFINITY;
             for (int q = 0; q < nq; ++q) {
                 const MtSrc s = mt_src(q, T, l, n, i, true);
-                tstep_fp64_j<SYM, true>(r[s.j], r[n + s.j], I, IV, p.eta, s.jpos, i, best, minr2);
+                tstep_fp64_j<SYM, true>(r[s.j], r[n + s.j], (SYM & 4) ? r[2 * n + s.j] : zero4, I, IV, IA, p.eta,
+                                        s.jpos, i, best, minr2);
             }
             t = p.eta * grp_mind(best, T);
             coincident = grp_mind(minr2, T) == 0.0;
@@ -500,9 +505,15 @@ __device__ __noinline__ void b_tstep(const SubParams &p, const SubWork &w, const
         t_sync(p);
         return;
     }
+    // exact fly-by derivative: the set's accelerations due to itself first
+    const double *acc = nullptr;
+    if (SYM & 4) {
+        b_acc<MIXED>(p, w, P, n, P, n, true, false, w.aB, nullptr, cnt);
+        acc = w.aB;
+    }
     for (int k = t_id(p); k < n; k += t_n(p)) {
-        if (MIXED) pack_tstep_mixed_one(k, P, n, p.x, p.v, p.m, p.N, p.G, w.recA);
-        else pack_tstep_fp64_one(k, P, n, p.x, p.v, p.m, p.N, p.G, (double4_32a *)w.recA);
+        if (MIXED) pack_tstep_mixed_one(k, P, n, p.x, p.v, p.m, p.N, p.G, w.recA, acc);
+        else pack_tstep_fp64_one(k, P, n, p.x, p.v, p.m, p.N, p.G, (double4_32a *)w.recA, acc);
     }
     t_sync(p);
     if (p.csize > 1 || n <= MT_MAX) {
@@ -849,6 +860,12 @@ __device__ __noinline__ double w_tstep(const SubParams &p, const WLane &L, unsig
     const int lane = threadIdx.x & 31;
     const int ipos[1] = {lane};
     coincident = false;
+    // exact fly-by derivative: the lanes' accelerations due to the set
+    double la[3] = {0.0, 0.0, 0.0};
+    if (SYM & 4) {
+        float wm;
+        w_acc<MIXED>(p, L, P, ((P >> lane) & 1u) ? P : 0u, false, la, wm);
+    }
     if (MIXED) {
         TstepMixedI<1> I;
         const float hx = (float)L.x[0], hy = (float)L.x[1], hz = (float)L.x[2];
@@ -858,6 +875,7 @@ __device__ __noinline__ double w_tstep(const SubParams &p, const WLane &L, unsig
         I.zl[0] = (float)(L.x[2] - (double)hz);
         I.vx[0] = (float)L.v[0]; I.vy[0] = (float)L.v[1]; I.vz[0] = (float)L.v[2];
         I.gm[0] = (float)(p.G * L.m);
+        I.ax[0] = (float)la[0]; I.ay[0] = (float)la[1]; I.az[0] = (float)la[2];
         const float mf = (float)L.m;
         const float eta = (float)p.eta, eta15 = 1.5f * eta;
         float best[1] = {INFINITY}, minr2[1] = {INFINITY};
@@ -868,13 +886,16 @@ __device__ __noinline__ double w_tstep(const SubParams &p, const WLane &L, unsig
             const float4 J0 = make_float4(wsh(hx, j), wsh(hy, j), wsh(hz, j), wsh(mf, j));
             const float4 J1 = make_float4(wsh(I.xl[0], j), wsh(I.yl[0], j), wsh(I.zl[0], j), 0.f);
             const float4 JV = make_float4(wsh(I.vx[0], j), wsh(I.vy[0], j), wsh(I.vz[0], j), wsh(I.gm[0], j));
-            tstep_mixed_j<1, SYM, true>(J0, J1, JV, I, eta, eta15, j, ipos, best, minr2);
+            const float4 JA = (SYM & 4) ? make_float4(wsh(I.ax[0], j), wsh(I.ay[0], j), wsh(I.az[0], j), 0.f)
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+            tstep_mixed_j<1, SYM, true>(J0, J1, JV, JA, I, eta, eta15, j, ipos, best, minr2);
         }
         coincident = (minr2[0] == 0.f);
         return p.eta * (double)best[0];
     } else {
         const double4_32a I = make_double4_32a(L.x[0], L.x[1], L.x[2], L.m);
         const double4_32a IV = make_double4_32a(L.v[0], L.v[1], L.v[2], p.G * L.m);
+        const double4_32a IA = make_double4_32a(la[0], la[1], la[2], 0.0);
         double best = INFINITY, minr2 = INFINITY;
         unsigned M = P;
         while (M) {
@@ -882,7 +903,9 @@ __device__ __noinline__ double w_tstep(const SubParams &p, const WLane &L, unsig
             M &= M - 1;
             const double4_32a J = make_double4_32a(wshd(I.x, j), wshd(I.y, j), wshd(I.z, j), wshd(I.w, j));
             const double4_32a JV = make_double4_32a(wshd(IV.x, j), wshd(IV.y, j), wshd(IV.z, j), wshd(IV.w, j));
-            tstep_fp64_j<SYM, true>(J, JV, I, IV, p.eta, j, lane, best, minr2);
+            const double4_32a JA = (SYM & 4) ? make_double4_32a(wshd(IA.x, j), wshd(IA.y, j), wshd(IA.z, j), 0.0)
+                                             : make_double4_32a(0.0, 0.0, 0.0, 0.0);
+            tstep_fp64_j<SYM, true>(J, JV, JA, I, IV, IA, p.eta, j, lane, best, minr2);
         }
         coincident = (minr2 == 0.0);
         return p.eta * best;
@@ -1111,8 +1134,8 @@ __global__ void __launch_bounds__(SB) k_hhs_subtree(SubParams p0, SubWork w0, co
     w.atB += 3 * (size_t)off;
     w.wA += off;
     w.wB += off;
-    w.recA += 4 * (size_t)off;
-    w.recB += 4 * (size_t)off;
+    w.recA += 6 * (size_t)off;  // 96 bytes per particle
+    w.recB += 6 * (size_t)off;
     Counts cnt = {0, 0, 0, 0, 0, depth0, 0};
     if (tid == 0) s_abort = 0;
     for (int step = 0; step < n_steps; ++step) {
@@ -1280,14 +1303,19 @@ cudaError_t launch_subtree(cudaStream_t s, bool mixed, int sym, const SubtreeArg
 #define FROST_SUBTREE_CASE(MIX, SYMV)                                                             \
     e = cudaLaunchKernelEx(&cfg, k_hhs_subtree<MIX, SYMV>, p, w, a.P, a.n, a.offsets, a.cl_index, a.tau0, \
                            a.depth0, a.n_steps)
-    if (mixed) {
-        if (sym == 0) FROST_SUBTREE_CASE(true, 0);
-        else if (sym == 1) FROST_SUBTREE_CASE(true, 1);
-        else FROST_SUBTREE_CASE(true, 2);
-    } else {
-        if (sym == 0) FROST_SUBTREE_CASE(false, 0);
-        else if (sym == 1) FROST_SUBTREE_CASE(false, 1);
-        else FROST_SUBTREE_CASE(false, 2);
+    switch ((mixed ? 8 : 0) + sym) {
+    case 8 + 0: FROST_SUBTREE_CASE(true, 0); break;
+    case 8 + 1: FROST_SUBTREE_CASE(true, 1); break;
+    case 8 + 4: FROST_SUBTREE_CASE(true, 4); break;
+    case 8 + 5: FROST_SUBTREE_CASE(true, 5); break;
+    case 8 + 6: FROST_SUBTREE_CASE(true, 6); break;
+    case 8 + 2: FROST_SUBTREE_CASE(true, 2); break;
+    case 0: FROST_SUBTREE_CASE(false, 0); break;
+    case 1: FROST_SUBTREE_CASE(false, 1); break;
+    case 4: FROST_SUBTREE_CASE(false, 4); break;
+    case 5: FROST_SUBTREE_CASE(false, 5); break;
+    case 6: FROST_SUBTREE_CASE(false, 6); break;
+    default: FROST_SUBTREE_CASE(false, 2); break;
     }
 #undef FROST_SUBTREE_CASE
     return e;

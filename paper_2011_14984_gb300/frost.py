@@ -21,6 +21,7 @@ FROST_OK, FROST_EINVAL, FROST_ENOMEM, FROST_ECUDA = 0, 1, 2, 3
 FROST_ENONFINITE, FROST_ECOINCIDENT, FROST_EDEPTH, FROST_ETIMEOUT = 4, 5, 6, 7
 FROST_PREC_FP64, FROST_PREC_MIXED = 0, 1
 FROST_SYM_HARMONIC, FROST_SYM_ARITHMETIC, FROST_SYM_NONE = 0, 1, 2
+FROST_FLYBY_EXACT = 4  # or-ed into sym: exact fly-by derivative
 
 _STATUS = {0: "FROST_OK", 1: "FROST_EINVAL", 2: "FROST_ENOMEM", 3: "FROST_ECUDA",
            4: "FROST_ENONFINITE", 5: "FROST_ECOINCIDENT", 6: "FROST_EDEPTH",

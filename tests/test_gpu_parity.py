@@ -251,15 +251,19 @@ def test_coincident_and_nonfinite_inputs_are_reported():
 # ---------------------------------------------------------------------------------------
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("sym", [0, 1, 2])
+@pytest.mark.parametrize("sym", [0, 1, 2, 4, 5])
 def test_timesteps(precision, sym):
+    """Time-steps of a set with 10% binaries for each symmetrisation factor, with the
+    two-body fly-by derivative (sym < 4) and the exact one (sym | 4: accelerations of the set
+    due to itself, softened by eps_P)."""
     n = 2500
     m, x, v = ics.plummer_kroupa_binaries(n, 9, binary_fraction=0.1)
-    f = F(m, x, v, precision=precision, sym=sym, eta=0.2)
+    eps = 1e-4 if sym & 4 else 0.0
+    f = F(m, x, v, precision=precision, sym=sym, eta=0.2, eps_soft=eps)
     rng = np.random.default_rng(1)
     P = rng.permutation(n)[:1900].astype(np.int32)
     tau = cpu(f.timesteps(P))
-    ref = oracle.timesteps(m, x, v, P, eta=0.2, sym=sym)
+    ref = oracle.timesteps_ex(m, x, v, P, P, eta=0.2, eps2=eps * eps, sym=sym)
     e = rel(tau, ref)
     if precision == "fp64":
         assert e.max() < 1e-12, e.max()
@@ -327,16 +331,18 @@ def test_fsi_step_parity():
     assert np.max(np.abs(xg - xo)) < 1e-14 and np.max(np.abs(vg - vo)) < 1e-12
 
 
-def test_hhs_fsi_trajectory_parity_fp64():
+@pytest.mark.parametrize("sym", [0, 4])
+def test_hhs_fsi_trajectory_parity_fp64(sym):
     """Plummer N = 1024 (seed 1) to t = 0.125 in 16 top-level steps of 2^-7, eta = 0.2:
-    positions within 1e-10 of the oracle and the same hierarchy depth."""
+    positions within 1e-10 of the oracle and the same hierarchy depth (sym 4: the exact
+    fly-by derivative)."""
     m, x, v = ics.plummer(1024, 1)
-    f = F(m, x, v, precision="fp64", eta=0.2)
+    f = F(m, x, v, precision="fp64", eta=0.2, sym=sym)
     f.step(2.0 ** -7, 16)
     xg, vg, t = f.state()
     st = f.stats()
     oracle.reset_counters()
-    xo, vo = oracle.steps(m, x, v, 2.0 ** -7, 16, eta=0.2)
+    xo, vo = oracle.steps(m, x, v, 2.0 ** -7, 16, eta=0.2, sym=sym)
     oc = oracle.counters()
     assert t == pytest.approx(0.125)
     assert np.max(np.abs(xg - xo)) < 1e-10 and np.max(np.abs(vg - vo)) < 1e-9
@@ -436,16 +442,18 @@ def test_full_pass_64k_sampled(precision):
 # ---------------------------------------------------------------------------------------
 
 @pytest.mark.parametrize("subtree_max", [1 << 30, 100])
-def test_subtree_solver_trajectory_parity_fp64(subtree_max):
+@pytest.mark.parametrize("sym", [0, 4])
+def test_subtree_solver_trajectory_parity_fp64(subtree_max, sym):
     """Whole recursion in one block (1<<30) or only sets of <= 100 particles: the same
-    trajectory as the oracle (Plummer N = 700, 6 top-level steps of 2^-7, eta = 0.2)."""
+    trajectory as the oracle (Plummer N = 700, 6 top-level steps of 2^-7, eta = 0.2), with
+    the two-body (sym 0) or the exact (sym 4) fly-by derivative."""
     m, x, v = ics.plummer(700, 31, masses=ics.kroupa_masses(700, 31))
-    f = F(m, x, v, precision="fp64", eta=0.2, subtree_max=subtree_max)
+    f = F(m, x, v, precision="fp64", eta=0.2, subtree_max=subtree_max, sym=sym)
     f.step(2.0 ** -7, 6)
     xg, vg, _ = f.state()
     st = f.stats()
     oracle.reset_counters()
-    xo, vo = oracle.steps(m, x, v, 2.0 ** -7, 6, eta=0.2)
+    xo, vo = oracle.steps(m, x, v, 2.0 ** -7, 6, eta=0.2, sym=sym)
     oc = oracle.counters()
     assert st["subtree_launches"] > 0
     assert np.max(np.abs(xg - xo)) < 1e-10 and np.max(np.abs(vg - vo)) < 1e-9

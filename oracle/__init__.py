@@ -81,6 +81,7 @@ def _load():
             lib.or_sym_arithmetic.restype = d
             lib.or_timesteps.argtypes = [P, P, P, P, i64, d, d, ci, P]
             lib.or_timesteps_ex.argtypes = [P, P, P, P, i64, P, i64, d, d, d, ci, P]
+            lib.or_steps_hold.argtypes = [i64, P, P, P, d, i64, d, d, d, ci, ci]
             lib.or_timesteps_of.argtypes = [P, P, P, P, i64, P, i64, d, d, ci, P]
             lib.or_partition.argtypes = [P, i64, P, d, P, P, P, P]
             lib.or_partition.restype = None
@@ -266,6 +267,16 @@ def hhs_fsi(m, x, v, P, tau_pivot, G=1.0, eta=0.2, eps2=0.0, max_depth=40, sym=S
     P = _i32(P)
     _check(_load().or_hhs_fsi(m.size, _p(m), _p(x), _p(v), _p(P), P.size, tau_pivot, G, eta, eps2,
                               max_depth, sym), "hhs_fsi")
+    return x, v
+
+
+def steps_hold(m, x, v, dt, n_steps, G=1.0, eta=0.2, eps2=0.0, max_depth=40, sym=SYM_HARMONIC):
+    """n_steps top-level steps of the second-order HOLD integrator (Eq. hhs2); returns (x, v)."""
+    m = _f64(m)
+    x = _f64(x, (-1, 3)).copy()
+    v = _f64(v, (-1, 3)).copy()
+    _check(_load().or_steps_hold(m.size, _p(m), _p(x), _p(v), dt, int(n_steps), G, eta, eps2, max_depth,
+                                 int(sym)), "steps_hold")
     return x, v
 
 

@@ -15,6 +15,7 @@
  *   or_sym_arithmetic  arithmetic symmetrisation factor, Eq. time-step-factor (Sec. 4.2)
  *   or_timesteps       tau_i = min_j of the symmetrised pair timescales (Sec. 4.3);
  *                      or_timesteps_ex adds the exact fly-by derivative variant
+ *   or_steps_hold      the second-order HOLD integrator (Eq. hhs2), for comparison
  *   or_partition       slow/fast split by the pivot step (Sec. 3.1)
  *   or_kick, or_drift  kick / drift (Sec. 5.3)
  *   or_fsi             Algorithm fsi (Eq. fsi)
@@ -526,6 +527,70 @@ int or_hhs_fsi(int64_t n, const double *m, double *x, double *v, const int32_t *
 }
 
 /* Main loop of Algorithm frost: n_steps calls hhs_fsi(all particles, dt). */
+/*
+ * Second-order HOLD integrator (Eq. hhs2, Sec. 3.1), the comparison integrator of the paper:
+ *   e^{eps H} ~ e^{eps/2 H_F} e^{eps/2 H_S} e^{eps U_FS} e^{eps/2 H_S} e^{eps/2 H_F}
+ * with e^{h H_S} the leapfrog kick(h/2) drift(h) kick(h/2) of the slow set under its own
+ * forces (the equation that follows Eq. hhs2), e^{eps U_FS} one pairwise kick of S and F
+ * with their mutual accelerations, and e^{eps/2 H_F} the same operator recursively on the
+ * fast set with the pivot halved.
+ */
+static int leapfrog(or_sys *s, const int32_t *S, int64_t nS, double h)
+{
+    if (nS == 0) return OR_OK;
+    double *a = (double *)malloc(sizeof(double) * 3 * (size_t)nS);
+    if (!a) return OR_ENOMEM;
+    int err = or_acc(s->m, s->x, S, nS, S, nS, s->G, s->eps2, a);
+    if (!err) {
+        or_kick(S, nS, s->v, a, 0.5 * h);
+        or_drift(S, nS, s->x, s->v, h);
+        err = or_acc(s->m, s->x, S, nS, S, nS, s->G, s->eps2, a);
+    }
+    if (!err) or_kick(S, nS, s->v, a, 0.5 * h);
+    free(a);
+    return err;
+}
+
+static int hold2(or_sys *s, const int32_t *P, int64_t nP, double tau, int depth)
+{
+    if (nP == 0) return OR_OK;
+    if (depth > s->max_depth) return OR_EDEPTH;
+    if (depth > or_max_depth_seen) or_max_depth_seen = depth;
+    int err = OR_OK;
+    double *t = (double *)malloc(sizeof(double) * (size_t)nP);
+    int32_t *S = (int32_t *)malloc(sizeof(int32_t) * (size_t)nP);
+    int32_t *F = (int32_t *)malloc(sizeof(int32_t) * (size_t)nP);
+    int64_t nS = 0, nF = 0;
+    if (!t || !S || !F) { err = OR_ENOMEM; goto done; }
+    err = or_timesteps_ex(s->m, s->x, s->v, P, nP, P, nP, s->G, s->eta, s->eps2, s->sym, t);
+    if (err) goto done;
+    or_partition(P, nP, t, tau, S, &nS, F, &nF);
+    if ((err = hold2(s, F, nF, 0.5 * tau, depth + 1))) goto done;
+    if ((err = leapfrog(s, S, nS, 0.5 * tau))) goto done;
+    if ((err = kick_sf(s, S, nS, F, nF, tau, 0, tau))) goto done;
+    if ((err = leapfrog(s, S, nS, 0.5 * tau))) goto done;
+    err = hold2(s, F, nF, 0.5 * tau, depth + 1);
+done:
+    free(t);
+    free(S);
+    free(F);
+    return err;
+}
+
+/* n_steps top-level steps of the second-order HOLD integrator over all particles. */
+int or_steps_hold(int64_t n, const double *m, double *x, double *v, double dt, int64_t n_steps,
+                  double G, double eta, double eps2, int max_depth, int sym)
+{
+    int32_t *all = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    if (!all) return OR_ENOMEM;
+    for (int64_t k = 0; k < n; ++k) all[k] = (int32_t)k;
+    or_sys s = {n, m, x, v, G, eta, eps2, max_depth, sym};
+    int err = OR_OK;
+    for (int64_t k = 0; k < n_steps && !err; ++k) err = hold2(&s, all, n, dt, 0);
+    free(all);
+    return err;
+}
+
 int or_steps(int64_t n, const double *m, double *x, double *v, double dt, int64_t n_steps,
              double G, double eta, double eps2, int max_depth, int sym)
 {

@@ -518,6 +518,49 @@ def test_hhs_fsi_with_all_particles_slow_is_two_half_fsi_steps():
     assert np.array_equal(xh, xf) and np.array_equal(vh, vf)
 
 
+def test_hold_with_all_particles_slow_is_two_leapfrog_half_steps():
+    """Eq. hhs2 with an empty fast set: e^{eps/2 H_S} twice around an empty S-F kick, each the
+    kick-drift-kick leapfrog of the equation that follows it.  Rebuilt here from oracle.acc."""
+    m, x, v = ics.kepler_binary(0.6, 0.4, 1.0, 0.3)
+    dt = 0.05
+    xo, vo = oracle.steps_hold(m, x, v, dt, 1, eta=50.0)  # eta large: every tau >= dt
+    P = np.arange(2, dtype=np.int32)
+    xr, vr = x.copy(), v.copy()
+    for _ in range(2):
+        h = 0.5 * dt
+        vr = vr + 0.5 * h * oracle.acc(m, xr, P, P)
+        xr = xr + h * vr
+        vr = vr + 0.5 * h * oracle.acc(m, xr, P, P)
+    assert np.allclose(xo, xr, rtol=0, atol=1e-15) and np.allclose(vo, vr, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("e", [0.1, 0.5])
+def test_hold_is_second_order_on_kepler_orbit(e):
+    """The HOLD integrator is of second order (Sec. 3.1): over one period, halving the step
+    divides the position error by ~4 (FSI: ~16)."""
+    m1, m2, a = 0.7, 0.3, 1.0
+    m, x, v = ics.kepler_binary(m1, m2, a, e)
+    period = 2 * math.pi * math.sqrt(a ** 3 / (m1 + m2))
+    errs = []
+    for k in (64, 128, 256):
+        xo, vo = oracle.steps_hold(m, x, v, period / k, k, eta=50.0)
+        errs.append(np.max(np.abs(xo - x)))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.5 < r1 < 4.6 and 3.5 < r2 < 4.6, (errs, r1, r2)
+
+
+def test_hold_conserves_momentum_across_levels():
+    """Every interaction of Eq. hhs2 is a pairwise kick (S-S leapfrog, S-F kick), so the total
+    momentum of a set split over several hierarchy levels is conserved to round-off."""
+    m, x, v = ics.plummer(200, 17, masses=ics.kroupa_masses(200, 17))
+    P0 = (m[:, None] * v).sum(0)
+    oracle.reset_counters()
+    xo, vo = oracle.steps_hold(m, x, v, 2.0 ** -5, 4, eta=0.2)
+    assert oracle.counters()["max_depth"] >= 2
+    P1 = (m[:, None] * vo).sum(0)
+    assert np.max(np.abs(P1 - P0)) < 1e-15
+
+
 def test_hhs_fsi_depth_limit():
     m, x, v = binary(0.5, 0.5, 1e-3, 0.0)
     with pytest.raises(oracle.OracleError) as e:

@@ -59,6 +59,12 @@ def parse():
                    help="time one full acc+gradient pass and one time-step pass and report the "
                         "time-step level histogram (workloads whose hierarchy cannot be "
                         "integrated in minutes, e.g. hard binaries without regularisation)")
+    p.add_argument("--integrator", default="hhs_fsi", choices=["hhs_fsi", "hold2"],
+                   help="hhs_fsi: the fourth-order method (default); hold2: the second-order HOLD "
+                        "integrator of Eq. hhs2, the paper's point of comparison")
+    p.add_argument("--flyby-exact", action="store_true",
+                   help="exact fly-by derivative in the time-steps (first line of Eq. "
+                        "dt-flyby-derivative)")
     p.add_argument("--subtree-max", type=int, default=0,
                    help="largest set whose hhs_fsi subtree runs in one block (0 = library default)")
     return p.parse_args()
@@ -240,7 +246,9 @@ def run_frost(args):
 
     def new(prec):
         return fr.Frost(m, x, v, G=1.0, eta=args.eta, precision=prec, stream=stream.cuda_stream,
-                        subtree_max=args.subtree_max)
+                        subtree_max=args.subtree_max,
+                        sym=fr.FROST_SYM_HARMONIC | (fr.FROST_FLYBY_EXACT if args.flyby_exact else 0),
+                        integrator=fr.FROST_HOLD2 if args.integrator == "hold2" else fr.FROST_HHS_FSI)
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB
 
@@ -425,7 +433,9 @@ def run_frost(args):
                            "step": "one top-level HHS-FSI step; E/P/L once per timed region",
                            "l2": "flushed before every timed step (256 MiB write)",
                            "parallelism": "replicas" if world > 1 else "single GPU",
-                           "subtree_max": args.subtree_max or "library default"},
+                           "subtree_max": args.subtree_max or "library default",
+                           "integrator": args.integrator,
+                           "flyby_derivative": "exact" if args.flyby_exact else "two-body"},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
                         "h2d_bytes_per_step": int(2 * n * 3 * 8),

@@ -74,10 +74,19 @@ typedef struct {
     int32_t subtree_max;/* hhs_fsi calls on sets of at most this many particles run their whole
                            subtree in one thread block (one launch, no host synchronisation);
                            0 = default (384), negative = never */
+    int32_t integrator; /* frost_integrator: what frost_step advances with */
 } frost_opts;
 
+typedef enum {
+    FROST_HHS_FSI = 0,  /* the fourth-order hierarchical FSI, Algorithm hhs-fsi (default) */
+    FROST_HOLD2 = 1     /* the second-order HOLD integrator of Eq. hhs2, the paper's point of
+                           comparison: e^{eps/2 H_F} e^{eps/2 H_S} e^{eps U_FS} e^{eps/2 H_S}
+                           e^{eps/2 H_F} with leapfrog for H_S and the fast set recursively;
+                           host recursion only (no subtree solver, not for batch contexts) */
+} frost_integrator;
+
 /* Default options: mixed precision, harmonic symmetrisation, no softening, depth 40,
- * legacy default stream, subtree threshold 384. */
+ * legacy default stream, subtree threshold 384, the HHS-FSI integrator. */
 void frost_default_opts(frost_opts *opt);
 
 /*

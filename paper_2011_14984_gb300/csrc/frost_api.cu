@@ -106,6 +106,7 @@ struct frost_ctx {
     size_t part_hot_elems = 0;
     int32_t *perm = nullptr, *ptmp = nullptr;        // subtree solver permutation / scratch
     int subtree_max = 384;                           // sets up to this size run in one block
+    int integrator = FROST_HHS_FSI;                  // frost_integrator of frost_step
     int n_clusters = 0;                              // > 0: batch of independent clusters
     int64_t *d_offsets = nullptr;                    // cluster offsets [n_clusters + 1] (device)
     // batch teams: clusters of at least team_min_n particles run on a thread-block cluster of
@@ -715,6 +716,7 @@ void frost_default_opts(frost_opts *opt)
     opt->max_depth = 40;
     opt->cuda_stream = nullptr;
     opt->subtree_max = 0;
+    opt->integrator = FROST_HHS_FSI;
 }
 
 const char *frost_last_error(void) { return g_last_error.c_str(); }
@@ -764,6 +766,10 @@ static frost_status init_impl(frost_ctx **out, int64_t n, const double *m, const
     if (o.sym < 0 || (o.sym & ~FROST_FLYBY_EXACT) > 2 || o.sym > 6)
         return fail(FROST_EINVAL, "unknown symmetrisation %d", o.sym);
     if (!(o.eps_soft >= 0.0) || !std::isfinite(o.eps_soft)) return fail(FROST_EINVAL, "bad softening");
+    if (o.integrator != FROST_HHS_FSI && o.integrator != FROST_HOLD2)
+        return fail(FROST_EINVAL, "unknown integrator %d", o.integrator);
+    if (o.integrator == FROST_HOLD2 && n_clusters > 0)
+        return fail(FROST_EINVAL, "the HOLD integrator runs on single-set contexts only");
 
     frost_ctx *c = new (std::nothrow) frost_ctx();
     if (!c) return fail(FROST_ENOMEM, "host allocation failed");
@@ -775,6 +781,7 @@ static frost_status init_impl(frost_ctx **out, int64_t n, const double *m, const
     c->sym = o.sym;
     c->max_depth = o.max_depth > 0 ? o.max_depth : 40;
     c->subtree_max = o.subtree_max == 0 ? 384 : (o.subtree_max < 0 ? 0 : o.subtree_max);
+    c->integrator = o.integrator;
 
     auto bail = [&](frost_status st) {
         destroy(c);
@@ -1015,6 +1022,44 @@ frost_status frost_fsi(frost_ctx *c, const int32_t *set, int64_t n_set, double d
     return FROST_OK;
 }
 
+// e^{h H_S}: leapfrog of the set S under its own forces, kick(h/2) drift(h) kick(h/2)
+void leapfrog(frost_ctx *c, const int32_t *S, int nS, double h)
+{
+    if (nS <= 0) return;
+    pass_acc(c, S, nS, S, nS, true, c->aA, nullptr, nullptr, nullptr, kick_of(c, S, 0.5 * h));
+    drift_pack(c, S, nS, h, c->recA, false);
+    pass_acc(c, S, nS, S, nS, true, c->aA, nullptr, nullptr, nullptr, kick_of(c, S, 0.5 * h), c->recA, c->recA);
+}
+
+// The second-order HOLD integrator, Eq. hhs2: e^{eps/2 H_F} e^{eps/2 H_S} e^{eps U_FS}
+// e^{eps/2 H_S} e^{eps/2 H_F}, the fast set recursively with the pivot halved.
+frost_status hold2(frost_ctx *c, const int32_t *P, int nP, double tau, int depth)
+{
+    if (nP <= 0) return FROST_OK;
+    if (depth > c->max_depth)
+        return fail(FROST_EDEPTH, "hold2 deeper than max_depth=%d (|P|=%d, tau_pivot=%g)", c->max_depth, nP, tau);
+    c->st.hhs_calls += 1;
+    if (depth > c->st.max_depth_seen) c->st.max_depth_seen = depth;
+    {
+        const int L = std::min(depth, FROST_STATS_LEVELS - 1);
+        c->st.level_calls[L] += 1;
+        c->st.level_particles[L] += nP;
+    }
+    FROST_TRY(ensure_level(c, depth));
+    int32_t *S = c->lvS[depth], *F = c->lvF[depth];
+    pass_tstep(c, P, nP, c->tau);
+    launch_partition(c->stream, P, nP, c->tau, tau, S, F, c->dmisc->counts);
+    c->st.kernel_launches += 1;
+    FROST_TRY(sync_misc(c));
+    const int nS = (int)c->hmisc->counts[0];
+    const int nF = (int)c->hmisc->counts[1];
+    FROST_TRY(hold2(c, F, nF, 0.5 * tau, depth + 1));
+    leapfrog(c, S, nS, 0.5 * tau);
+    kick_sf(c, S, nS, F, nF, tau, false, tau);
+    leapfrog(c, S, nS, 0.5 * tau);
+    return hold2(c, F, nF, 0.5 * tau, depth + 1);
+}
+
 frost_status frost_step(frost_ctx *c, double dt_pivot, int64_t n_steps)
 {
     if (!c) return fail(FROST_EINVAL, "NULL context");
@@ -1110,7 +1155,8 @@ frost_status frost_step(frost_ctx *c, double dt_pivot, int64_t n_steps)
         return sync_misc(c);
     }
     for (int64_t k = 0; k < n_steps; ++k) {
-        FROST_TRY(hhs_fsi(c, c->all, c->N, dt_pivot, 0));
+        if (c->integrator == FROST_HOLD2) FROST_TRY(hold2(c, c->all, c->N, dt_pivot, 0));
+        else FROST_TRY(hhs_fsi(c, c->all, c->N, dt_pivot, 0));
         c->t += dt_pivot;
     }
     FROST_CUDA(cudaGetLastError());

@@ -22,6 +22,7 @@ FROST_ENONFINITE, FROST_ECOINCIDENT, FROST_EDEPTH, FROST_ETIMEOUT = 4, 5, 6, 7
 FROST_PREC_FP64, FROST_PREC_MIXED = 0, 1
 FROST_SYM_HARMONIC, FROST_SYM_ARITHMETIC, FROST_SYM_NONE = 0, 1, 2
 FROST_FLYBY_EXACT = 4  # or-ed into sym: exact fly-by derivative
+FROST_HHS_FSI, FROST_HOLD2 = 0, 1  # frost_opts.integrator
 
 _STATUS = {0: "FROST_OK", 1: "FROST_EINVAL", 2: "FROST_ENOMEM", 3: "FROST_ECUDA",
            4: "FROST_ENONFINITE", 5: "FROST_ECOINCIDENT", 6: "FROST_EDEPTH",
@@ -37,7 +38,8 @@ class FrostError(RuntimeError):
 class frost_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("sym", ctypes.c_int32),
                 ("eps_soft", ctypes.c_double), ("max_depth", ctypes.c_int32),
-                ("cuda_stream", ctypes.c_void_p), ("subtree_max", ctypes.c_int32)]
+                ("cuda_stream", ctypes.c_void_p), ("subtree_max", ctypes.c_int32),
+                ("integrator", ctypes.c_int32)]
 
 
 class frost_stats(ctypes.Structure):
@@ -289,7 +291,7 @@ class Frost:
 
     def __init__(self, m, x, v, G: float = 1.0, eta: float = 0.2, precision: str = "mixed",
                  sym: int = FROST_SYM_HARMONIC, eps_soft: float = 0.0, max_depth: int = 40,
-                 stream=None, subtree_max: int = 0, offsets=None):
+                 stream=None, subtree_max: int = 0, offsets=None, integrator: int = FROST_HHS_FSI):
         import torch
         self.torch = torch
         o = frost_default_opts()
@@ -299,6 +301,7 @@ class Frost:
         o.max_depth = int(max_depth)
         o.cuda_stream = stream if stream is not None else current_stream_handle()
         o.subtree_max = int(subtree_max)
+        o.integrator = int(integrator)
         self.n = int(np.asarray(m).shape[0]) if not hasattr(m, "shape") else int(m.shape[0])
         self.G = G
         self.eta = eta

@@ -352,6 +352,26 @@ def test_hhs_fsi_trajectory_parity_fp64(sym):
     f.close()
 
 
+def test_hold2_integrator_trajectory_parity_fp64():
+    """The second-order HOLD integrator (Eq. hhs2) on the GPU kernels: Plummer N = 1024,
+    8 top-level steps of 2^-7, FP64 positions within 1e-10 of the oracle's HOLD, the same
+    depth; and it differs from the fourth-order HHS-FSI run (a different integrator)."""
+    from paper_2011_14984_gb300.frost import FROST_HOLD2
+    m, x, v = ics.plummer(1024, 1)
+    f = F(m, x, v, precision="fp64", eta=0.2, integrator=FROST_HOLD2)
+    f.step(2.0 ** -7, 8)
+    xg, vg, t = f.state()
+    st = f.stats()
+    oracle.reset_counters()
+    xo, vo = oracle.steps_hold(m, x, v, 2.0 ** -7, 8, eta=0.2)
+    oc = oracle.counters()
+    assert np.max(np.abs(xg - xo)) < 1e-10 and np.max(np.abs(vg - vo)) < 1e-9
+    assert st["max_depth_seen"] == oc["max_depth"]
+    x4, _ = oracle.steps(m, x, v, 2.0 ** -7, 8, eta=0.2)
+    assert np.max(np.abs(x4 - xo)) > 1e-9
+    f.close()
+
+
 def test_hhs_fsi_mixed_energy_parity():
     """Mixed precision reaches the FP64 energy error within a factor 2 (plus round-off)."""
     m, x, v = ics.plummer(1024, 1)

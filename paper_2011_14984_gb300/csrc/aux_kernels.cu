@@ -1,6 +1,7 @@
 // Integrator and bookkeeping kernels of the HHS-FSI hot path for sm_103a:
 //   kick / drift (Sec. 5.3), the stable slow/fast partition (Sec. 3.1), index-list
 //   validation, and the FP64 energy / momentum / angular-momentum reductions (Sec. 2.3).
+#include "df_arith.cuh"
 #include "frost_internal.cuh"
 #include "pair_bodies.cuh"
 
@@ -201,28 +202,9 @@ __global__ void k_check_mass(const double *__restrict__ m, int n, int *__restric
     if (!(m[k] > 0.0) || !isfinite(m[k])) atomicOr(err, ERR_NONFINITE);
 }
 
-// ---- potential in double-float arithmetic ------------------------------------------------
-// A value is carried as an unevaluated sum of two FP32 numbers (hi, lo) with about 48
-// significant bits, using the error-free transformations TwoSum (Knuth) and TwoProduct by
-// FMA (Dekker's double-length arithmetic).  On this part FP32 issues 64 times faster than
-// FP64, so the O(N^2) potential of the energy diagnostic runs on the FP32 pipe and keeps
-// about 1e-13 relative accuracy per phi_i (positions enter exactly, as three FP32 parts).
-
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
-{
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-// x = h + l + ll exactly (three FP32 parts hold the 53 bits of an FP64 value)
-__device__ __forceinline__ void split_f3(double v, float &h, float &l, float &ll)
-{
-    h = (float)v;
-    const double r = v - (double)h;
-    l = (float)r;
-    ll = (float)(r - (double)l);
-}
+// ---- potential in double-float arithmetic (df_arith.cuh) ---------------------------------
+// The O(N^2) potential of the energy diagnostic runs on the FP32 pipes and keeps about 1e-13
+// relative accuracy per phi_i (positions enter exactly, as three FP32 parts).
 
 // records: p0 = {x_h, y_h, z_h, m_h}, p1 = {x_l, y_l, z_l, m_l}, p2 = {x_ll, y_ll, z_ll, 0}
 __global__ void k_pack_pot_df(const double *__restrict__ x, const double *__restrict__ m, int N,
@@ -231,9 +213,9 @@ __global__ void k_pack_pot_df(const double *__restrict__ x, const double *__rest
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     float xh, xl, xll, yh, yl, yll, zh, zl, zll;
-    split_f3(x[i], xh, xl, xll);
-    split_f3(x[N + i], yh, yl, yll);
-    split_f3(x[2 * N + i], zh, zl, zll);
+    df::split3(x[i], xh, xl, xll);
+    df::split3(x[N + i], yh, yl, yll);
+    df::split3(x[2 * N + i], zh, zl, zll);
     const double pm = m[i];
     const float hm = (float)pm;
     rec[i] = make_float4(xh, yh, zh, hm);
@@ -241,17 +223,6 @@ __global__ void k_pack_pot_df(const double *__restrict__ x, const double *__rest
     rec[2 * N + i] = make_float4(xll, yll, zll, 0.f);
 }
 
-// one coordinate of the separation x_j - x_i as a normalised pair (h, l): the differences of
-// the two larger parts are exact (TwoSum), the smallest parts are 2^-48 below the value
-__device__ __forceinline__ void sep_df(float jh, float jl, float jll, float ih, float il, float ill, float &h,
-                                       float &l)
-{
-    float a, e1, b, e2, e4;
-    two_sum(jh, -ih, a, e1);
-    two_sum(jl, -il, b, e2);
-    two_sum(a, b, h, e4);
-    l = e4 + (e1 + (e2 + (jll - ill)));
-}
 
 // phi_i = sum_{j != i} m_j / sqrt(r^2 + eps2) in double-float, j-split partials part[split][i]
 template <int BS, int TJ>
@@ -283,10 +254,10 @@ __global__ void __launch_bounds__(BS) k_potential_df(const float4 *__restrict__ 
         __syncthreads();
         for (int jj = 0; jj < cnt; ++jj) {
             const float4 J0 = s0[jj], J1 = s1[jj], J2 = s2[jj];
-            float xh, xl, yh, yl, zh, zl;
-            sep_df(J0.x, J1.x, J2.x, I0.x, I1.x, I2.x, xh, xl);
-            sep_df(J0.y, J1.y, J2.y, I0.y, I1.y, I2.y, yh, yl);
-            sep_df(J0.z, J1.z, J2.z, I0.z, I1.z, I2.z, zh, zl);
+            const df::dfloat sx = df::sep(J0.x, J1.x, J2.x, I0.x, I1.x, I2.x);
+            const df::dfloat sy = df::sep(J0.y, J1.y, J2.y, I0.y, I1.y, I2.y);
+            const df::dfloat sz = df::sep(J0.z, J1.z, J2.z, I0.z, I1.z, I2.z);
+            const float xh = sx.h, xl = sx.l, yh = sy.h, yl = sy.l, zh = sz.h, zl = sz.l;
             // r^2 + eps^2: exact squares of the high parts, first-order terms of the low parts
             // (products feeding an error-free transformation are rounded on their own, __fmul_rn,
             // so that the compiler cannot contract them into the following add)
@@ -295,9 +266,9 @@ __global__ void __launch_bounds__(BS) k_potential_df(const float4 *__restrict__ 
             const float qy = fmaf(yh + yh, yl, fmaf(yh, yh, -py));
             const float qz = fmaf(zh + zh, zl, fmaf(zh, zh, -pz));
             float s, t, S, u, S2, u2;
-            two_sum(px, py, s, t);
-            two_sum(s, pz, S, u);
-            two_sum(S, e2h, S2, u2);
+            df::two_sum(px, py, s, t);
+            df::two_sum(s, pz, S, u);
+            df::two_sum(S, e2h, S2, u2);
             const float lo = ((t + u) + (u2 + e2l)) + ((qx + qy) + qz);
             // 1 / r: MUFU estimate y0 and the residual res = 1 - r^2 y0^2 in double-float; then
             // 1/r = y0 (1 - res)^(-1/2) = y0 (1 + res/2 + 3 res^2/8 + ...), |res| < 2^-21
@@ -311,7 +282,7 @@ __global__ void __launch_bounds__(BS) k_potential_df(const float4 *__restrict__ 
             const float we = fmaf(J0.w, y0, -w) + fmaf(J0.w, c, J1.w * y0);
             if (j0 + jj != i) {
                 float e;
-                two_sum(H, w, H, e);
+                df::two_sum(H, w, H, e);
                 L += e + we;
             }
         }

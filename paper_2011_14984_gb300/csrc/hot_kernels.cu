@@ -17,6 +17,7 @@
 //     terms in FP64 for every active particle, into separate split partials.
 // The classification depends only on the accelerations, so the results stay deterministic;
 // with no hot source both kernels only read the mask and write zeros.
+#include "df_arith.cuh"
 #include "frost_internal.cuh"
 #include "pair_bodies.cuh"
 
@@ -291,31 +292,38 @@ __global__ void __launch_bounds__(HOT_BS) k_acc_refine(
     }
 }
 
-// FP64 gradient terms of the hot sources of B (mask bits) for every particle of A:
+// Gradient terms of the hot sources of B (mask bits) for every particle of A, in double-float
+// arithmetic (df_arith.cuh, about 1e-13 relative per term, well below what the cancellation
+// between partners needs; FP64 would run at 1/60 of the FP32 rate):
 // part[s][c][i] = sum over the hot j of split s of m_j r^-5 (r^2 a_ji - 3 (x_ji . a_ji) x_ji).
+// Positions enter exactly as three FP32 parts, accelerations and masses as double-floats.
 // Split s takes the mask words s, s + nsplit, s + 2 nsplit, ... so that hot sources clustered
 // in index order still spread over the splits.
 __global__ void __launch_bounds__(HOT_BS) k_grad_hot(
     const int32_t *__restrict__ Alist, int n_a, const double *__restrict__ aA,
     const int32_t *__restrict__ Blist, int n_s, const double *__restrict__ aB,
     const uint32_t *__restrict__ mask, int self_pass, const double *__restrict__ x,
-    const double *__restrict__ m, int N, double eps2, int nsplit, double *__restrict__ part)
+    const double *__restrict__ m, int N, double eps2d, int nsplit, double *__restrict__ part)
 {
+    using df::dfloat;
     __shared__ int s_list[HOT_WORDS * 32];
-    __shared__ double s_j[7][HOT_BS];
+    // per hot source: x as three parts (9 floats), a as double-floats (6), m (2)
+    __shared__ float s_j[17][HOT_BS];
     __shared__ int s_pos[HOT_BS];
     const int tid = threadIdx.x;
     const int i = blockIdx.x * HOT_BS + tid;
     const int sp = blockIdx.y;
-    double xi[3] = {0.0, 0.0, 0.0}, ai[3] = {0.0, 0.0, 0.0};
+    float xi[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    dfloat ai[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     if (i < n_a) {
         const int gi = Alist ? Alist[i] : i;
         for (int c = 0; c < 3; ++c) {
-            xi[c] = x[(size_t)c * N + gi];
-            ai[c] = aA[(size_t)c * n_a + i];
+            df::split3(x[(size_t)c * N + gi], xi[c][0], xi[c][1], xi[c][2]);
+            ai[c] = df::from_double(aA[(size_t)c * n_a + i]);
         }
     }
-    double g[3] = {0.0, 0.0, 0.0};
+    const dfloat e2 = df::from_double(eps2d);
+    dfloat g[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     const int n_words = (n_s + 31) >> 5;
     const int q_count = (sp < n_words) ? (n_words - sp + nsplit - 1) / nsplit : 0;
     for (int q0 = 0; q0 < q_count; q0 += HOT_WORDS) {
@@ -340,32 +348,46 @@ __global__ void __launch_bounds__(HOT_BS) k_grad_hot(
                 const int gj = Blist ? Blist[jp] : jp;
                 s_pos[tid] = jp;
                 for (int c = 0; c < 3; ++c) {
-                    s_j[c][tid] = x[(size_t)c * N + gj];
-                    s_j[4 + c][tid] = aB[(size_t)c * n_s + jp];
+                    df::split3(x[(size_t)c * N + gj], s_j[3 * c][tid], s_j[3 * c + 1][tid], s_j[3 * c + 2][tid]);
+                    const dfloat a = df::from_double(aB[(size_t)c * n_s + jp]);
+                    s_j[9 + 2 * c][tid] = a.h;
+                    s_j[10 + 2 * c][tid] = a.l;
                 }
-                s_j[3][tid] = m[gj];
+                const dfloat mj = df::from_double(m[gj]);
+                s_j[15][tid] = mj.h;
+                s_j[16][tid] = mj.l;
             }
             __syncthreads();
             if (i < n_a) {
                 for (int u = 0; u < nt; ++u) {
                     if (self_pass && s_pos[u] == i) continue;
-                    const double dx = s_j[0][u] - xi[0], dy = s_j[1][u] - xi[1], dz = s_j[2][u] - xi[2];
-                    const double Ax = s_j[4][u] - ai[0], Ay = s_j[5][u] - ai[1], Az = s_j[6][u] - ai[2];
-                    const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
-                    const double ri = rsqrt(r2);
-                    const double ri2 = ri * ri;
-                    const double w = s_j[3][u] * ri * ri2;
-                    const double t3 = 3.0 * fma(dx, Ax, fma(dy, Ay, dz * Az)) * ri2;
-                    g[0] = fma(w, fma(-t3, dx, Ax), g[0]);
-                    g[1] = fma(w, fma(-t3, dy, Ay), g[1]);
-                    g[2] = fma(w, fma(-t3, dz, Az), g[2]);
+                    dfloat d[3], A[3];
+                    for (int c = 0; c < 3; ++c) {
+                        d[c] = df::sep(s_j[3 * c][u], s_j[3 * c + 1][u], s_j[3 * c + 2][u], xi[c][0], xi[c][1],
+                                       xi[c][2]);
+                        dfloat aj;
+                        aj.h = s_j[9 + 2 * c][u];
+                        aj.l = s_j[10 + 2 * c][u];
+                        A[c] = df::sub(aj, ai[c]);
+                    }
+                    const dfloat r2 = df::add(df::add(df::mul(d[0], d[0]), df::mul(d[1], d[1])),
+                                              df::add(df::mul(d[2], d[2]), e2));
+                    const dfloat ri = df::rsqrt(r2);
+                    const dfloat ri2 = df::mul(ri, ri);
+                    dfloat mj;
+                    mj.h = s_j[15][u];
+                    mj.l = s_j[16][u];
+                    const dfloat w = df::mul(mj, df::mul(ri2, ri));
+                    const dfloat xa = df::add(df::add(df::mul(d[0], A[0]), df::mul(d[1], A[1])), df::mul(d[2], A[2]));
+                    const dfloat t3 = df::mul(df::mul_f(xa, 3.f), ri2);
+                    for (int c = 0; c < 3; ++c) g[c] = df::add(g[c], df::mul(w, df::sub(A[c], df::mul(t3, d[c]))));
                 }
             }
             __syncthreads();
         }
     }
     if (i < n_a)
-        for (int c = 0; c < 3; ++c) part[((size_t)sp * 3 + c) * n_a + i] = g[c];
+        for (int c = 0; c < 3; ++c) part[((size_t)sp * 3 + c) * n_a + i] = df::to_double(g[c]);
 }
 
 void launch_acc_hist(cudaStream_t s, const double *a_soa, int n, unsigned *hist)

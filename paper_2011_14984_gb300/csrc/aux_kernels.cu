@@ -69,7 +69,6 @@ __global__ void k_drift_pack(const int32_t *__restrict__ list, int n, double *__
     x[N + i] = __dadd_rn(x[N + i], __dmul_rn(dt, v[N + i]));
     x[2 * N + i] = __dadd_rn(x[2 * N + i], __dmul_rn(dt, v[2 * N + i]));
     if (mode == 0) dev::pack_pos_mixed_one(k, list, n, x, m, N, (float4 *)rec);
-    else if (mode == 1) dev::pack_grad_mixed_one(k, list, n, x, m, N, nullptr, (float4 *)rec);
     else dev::pack_pos_fp64_one(k, list, n, x, m, N, (double4_32a *)rec);
 }
 

@@ -99,7 +99,6 @@ struct frost_ctx {
     double *aC = nullptr;  // [3][N] by particle: a^SS at the end of the first fsi(S) of hhs_fsi
     double *tau = nullptr;                           // [N]
     float *wA = nullptr, *wB = nullptr;              // max_j m_j / r^3 per particle (mixed)
-    float *wpart = nullptr;                          // its split partials
     unsigned *hist = nullptr;                        // |a| histograms [2][HOT_BINS] (mixed)
     uint32_t *hA = nullptr, *hB = nullptr;           // hot-source masks of aA / aB (mixed)
     double *part_hot = nullptr;                      // FP64 hot-source gradient partials
@@ -285,14 +284,11 @@ void pass_acc(frost_ctx *c, const int32_t *A, int nA, const int32_t *B, int nB, 
         return;
     }
     // before a gradient pass (wmax requested) the mixed mode uses the accurate variant on the
-    // three-way split records
+    // same position records: a prepass for wmax = max_j m_j / r^3, then the pass with
+    // Newton-refined rsqrt, short folds and the terms above wmax / 16 in double-float
     const bool accurate = c->mixed && wmax;
     if (irec) {
         // packed by the caller
-    } else if (accurate) {
-        launch_pack_grad_mixed(c->stream, A, nA, c->x, c->m, c->N, nullptr, (float4 *)c->recA);
-        if (!self) launch_pack_grad_mixed(c->stream, B, nB, c->x, c->m, c->N, nullptr, (float4 *)c->recB);
-        c->st.kernel_launches += self ? 1 : 2;
     } else {
         pack_pos(c, A, nA, c->recA);
         if (!self) pack_pos(c, B, nB, c->recB);
@@ -307,14 +303,20 @@ void pass_acc(frost_ctx *c, const int32_t *A, int nA, const int32_t *B, int nB, 
     a.part = c->part;
     a.shape = shape_for(c, PASS_ACC, nA, nB);
     a.accurate = accurate;
-    a.wpart = accurate ? c->wpart : nullptr;
+    a.wmax = accurate ? wmax : nullptr;
+    a.jlist = B;
+    a.m = c->m;
     const int64_t pairs = self ? (int64_t)nA * (nA - 1) : (int64_t)nA * nB;
     {
         TimedScope ts(c, PASS_ACC, pairs);
+        if (accurate) {
+            launch_wmax(c->stream, a, wmax);
+            c->st.kernel_launches += 1;
+        }
         launch_acc(c->stream, c->mixed, a);
     }
-    launch_finalize_vec(c->stream, c->part, a.shape.nsplit, nA, c->G, out_soa, out_aos, a.wpart,
-                        a.wpart ? wmax : nullptr, &c->dmisc->err, badbit(c), kick);
+    launch_finalize_vec(c->stream, c->part, a.shape.nsplit, nA, c->G, out_soa, out_aos, nullptr, nullptr,
+                        &c->dmisc->err, badbit(c), kick);
     c->st.kernel_launches += 2;
     c->st.acc_pairs += pairs;
     if (accurate && hist && out_soa) {
@@ -323,21 +325,19 @@ void pass_acc(frost_ctx *c, const int32_t *A, int nA, const int32_t *B, int nB, 
     }
 }
 
-// Hot sources (mixed mode): after the accurate Newtonian pass of A against B whose records are
-// irec (A) and jrec (B), marks in mask the particles of A with |a| above HOT_KAPPA x the larger
-// median of hist (this pass) and hist2 (the companion pass of B against A, n2 values, or NULL)
-// and recomputes their accelerations with the dominant terms in FP64 (hot_kernels.cu).
-void refine_hot(frost_ctx *c, const void *irec, const void *jrec, const int32_t *A, int nA,
-                const int32_t *B, int nB, bool self, double *a_soa, double *a_aos, const float *wmax,
-                const unsigned *hist, const unsigned *hist2, int n2, uint32_t *mask)
+// Hot sources (mixed mode): after the accurate Newtonian pass of A (nA) against B (nB), marks
+// in mask the particles of A with |a| (a_soa) above HOT_KAPPA x the larger median of hist
+// (this pass) and hist2 (the companion pass of B against A, n2 values, or NULL); see
+// hot_kernels.cu.
+void mark_hot(frost_ctx *c, int nA, int nB, bool self, const double *a_soa, const unsigned *hist,
+              const unsigned *hist2, int n2, uint32_t *mask)
 {
     if (!c->mixed || nA <= 0) return;
     if (nB <= 0 || (self && nA == 1)) {
         cudaMemsetAsync(mask, 0, sizeof(uint32_t) * ((nA + 31) / 32), c->stream);
         return;
     }
-    launch_acc_refine(c->stream, (const float4 *)irec, (const float4 *)jrec, nA, nB, self ? 1 : 0, A, B,
-                      c->x, c->m, c->N, c->G, c->eps2, wmax, hist, hist2, n2, a_soa, a_aos, mask);
+    launch_hot_mask(c->stream, a_soa, nA, hist, hist2, n2, mask);
     c->st.kernel_launches += 1;
 }
 
@@ -471,21 +471,16 @@ KickArgs kick_of(frost_ctx *c, const int32_t *L, double dt)
 void drift_pack(frost_ctx *c, const int32_t *L, int n, double dt, void *rec, bool accurate)
 {
     if (n <= 0) return;
-    launch_drift_pack(c->stream, L, n, c->x, c->v, c->m, c->N, dt, rec, c->mixed ? (accurate ? 1 : 0) : 2);
+    (void)accurate;  // both Newtonian variants read the same position records
+    launch_drift_pack(c->stream, L, n, c->x, c->v, c->m, c->N, dt, rec, c->mixed ? 0 : 2);
     c->st.kernel_launches += 1;
 }
 
-// position records of L for a Newtonian pass (accurate: the three-way split of the mixed pass
-// that feeds a gradient)
-void pack_acc(frost_ctx *c, const int32_t *L, int n, void *rec, bool accurate)
+// position records of L for a Newtonian pass (both variants read the same records)
+void pack_acc(frost_ctx *c, const int32_t *L, int n, void *rec, bool /*accurate*/)
 {
     if (n <= 0) return;
-    if (c->mixed && accurate) {
-        launch_pack_grad_mixed(c->stream, L, n, c->x, c->m, c->N, nullptr, (float4 *)rec);
-        c->st.kernel_launches += 1;
-    } else {
-        pack_pos(c, L, n, rec);
-    }
+    pack_pos(c, L, n, rec);
 }
 
 // gradient records of L with accelerations a ([3][n]); mixed mode: masses of the hot
@@ -519,7 +514,7 @@ void fsi(frost_ctx *c, const int32_t *S, int nS, double dt, int cache = 0)
     if (c->mixed) {
         unsigned *h = zero_hists(c);
         pass_acc(c, S, nS, S, nS, true, c->aA, nullptr, c->wA, h, KickArgs(), c->recA, c->recA);
-        refine_hot(c, c->recA, c->recA, S, nS, S, nS, true, c->aA, nullptr, c->wA, h, nullptr, 0, c->hA);
+        mark_hot(c, nS, nS, true, c->aA, h, nullptr, 0, c->hA);
     } else {
         pass_acc(c, S, nS, S, nS, true, c->aA, nullptr, c->wA, nullptr, KickArgs(), c->recA, c->recA);
     }
@@ -550,8 +545,8 @@ void kick_sf(frost_ctx *c, const int32_t *S, int nS, const int32_t *F, int nF, d
     pass_acc(c, F, nF, S, nS, false, c->aB, nullptr, c->wB, h ? h + HOT_BINS : nullptr, KickArgs(), c->recB,
              c->recA);
     if (h) {
-        refine_hot(c, c->recA, c->recB, S, nS, F, nF, false, c->aA, nullptr, c->wA, h, h + HOT_BINS, nF, c->hA);
-        refine_hot(c, c->recB, c->recA, F, nF, S, nS, false, c->aB, nullptr, c->wB, h + HOT_BINS, h, nS, c->hB);
+        mark_hot(c, nS, nF, false, c->aA, h, h + HOT_BINS, nF, c->hA);
+        mark_hot(c, nF, nS, false, c->aB, h + HOT_BINS, h, nS, c->hB);
     }
     pack_grad(c, S, nS, c->aA, c->recA, c->mixed ? c->hA : nullptr);
     pack_grad(c, F, nF, c->aB, c->recB, c->mixed ? c->hB : nullptr);
@@ -691,7 +686,7 @@ void destroy(frost_ctx *c)
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->d_ecl) cudaFree(c->d_ecl);
     void *dev[] = {c->x, c->v, c->m, c->all, c->marks, c->recA, c->recB, c->part,
-                   c->aA, c->aB, c->atA, c->atB, c->aC, c->tau, c->wA, c->wB, c->wpart, c->perm,
+                   c->aA, c->aB, c->atA, c->atB, c->aC, c->tau, c->wA, c->wB, c->perm,
                    c->ptmp, c->dmisc, c->hist, c->hA, c->hB, c->part_hot};
     for (void *p : dev)
         if (p) cudaFree(p);
@@ -820,7 +815,6 @@ static frost_status init_impl(frost_ctx **out, int64_t n, const double *m, const
     INIT_CUDA(cudaMalloc(&c->tau, sizeof(double) * N));
     INIT_CUDA(cudaMalloc(&c->wA, sizeof(float) * N));
     INIT_CUDA(cudaMalloc(&c->wB, sizeof(float) * N));
-    INIT_CUDA(cudaMalloc(&c->wpart, sizeof(float) * (c->part_elems / 3)));
     if (c->mixed) {
         const size_t words = (N + 31) / 32;
         c->part_hot_elems = 3 * std::max(N, (size_t)HOT_MAX_SPLITS * c->n_sm * 256);
@@ -949,7 +943,7 @@ frost_status frost_accel_gradient(frost_ctx *c, const int32_t *active, int64_t n
     if (self) {
         unsigned *h = (want_grad && c->mixed) ? zero_hists(c) : nullptr;
         pass_acc(c, A, nA, A, nA, true, c->aA, acc, want_grad ? c->wA : nullptr, h);
-        if (h) refine_hot(c, c->recA, c->recA, A, nA, A, nA, true, c->aA, acc, c->wA, h, nullptr, 0, c->hA);
+        if (h) mark_hot(c, nA, nA, true, c->aA, h, nullptr, 0, c->hA);
         if (want_grad)
             pass_grad(c, A, nA, c->aA, A, nA, c->aA, true, eps_grad, nullptr, acc_tilde, grad, c->wA, c->hA);
     } else {
@@ -957,9 +951,8 @@ frost_status frost_accel_gradient(frost_ctx *c, const int32_t *active, int64_t n
         pass_acc(c, A, nA, B, nB, false, c->aA, acc, want_grad ? c->wA : nullptr, h);
         if (want_grad) {
             pass_acc(c, B, nB, A, nA, false, c->aB, nullptr, c->wB, h ? h + HOT_BINS : nullptr);
-            // the records of the last pass: recA = B, recB = A; only B's accelerations are sources
-            if (h) refine_hot(c, c->recA, c->recB, B, nB, A, nA, false, c->aB, nullptr, c->wB, h + HOT_BINS, h,
-                              nA, c->hB);
+            // only B's accelerations are sources
+            if (h) mark_hot(c, nB, nA, false, c->aB, h + HOT_BINS, h, nA, c->hB);
             pass_grad(c, A, nA, c->aA, B, nB, c->aB, false, eps_grad, nullptr, acc_tilde, grad, c->wA, c->hB);
         }
     }

@@ -61,8 +61,10 @@ struct PairArgs {
     double *part;     // partial results [nsplit][ncomp][n_a]
     SplitShape shape;
     float *wpart = nullptr;        // acc (mixed): per-split max_j m_j / r^3 [nsplit][n_a], or NULL
-    const float *wmax = nullptr;   // grad (mixed): per-particle max_j m_j / r^3 [n_a], or NULL
-    bool accurate = false;         // acc (mixed): the variant that feeds a gradient pass
+    const float *wmax = nullptr;   // grad and accurate acc (mixed): max_j m_j / r^3 [n_a], or NULL
+    bool accurate = false;         // acc (mixed): the variant that feeds a gradient pass (wmax set)
+    const int32_t *jlist = nullptr;  // accurate acc: the source list (NULL: identity) and the
+    const double *m = nullptr;       // FP64 masses of the store, for the double-float terms
 };
 
 // ---- pack kernels: list -> per-pass records ------------------------------------------
@@ -87,7 +89,11 @@ void launch_pack_tstep_fp64(cudaStream_t s, const int32_t *list, int n, const do
 
 // ---- pair kernels ---------------------------------------------------------------------
 // acc: part[split][c][i] = sum_j m_j x_ji / r^3 over the split's sources
+// accurate mixed variant (a.accurate): the terms above wmax / 16 (a.wmax from launch_wmax
+// at the same records) are summed in double-float
 void launch_acc(cudaStream_t s, bool mixed, const PairArgs &a);
+// mixed prepass of the accurate Newtonian pass: wmax[i] = max_j m_j / r^3 (zeroed here)
+void launch_wmax(cudaStream_t s, const PairArgs &a, float *wmax);
 // grad: part[split][c][i] = sum_j m_j r^-5 (r^2 a_ji - 3 (x_ji . a_ji) x_ji)
 void launch_grad(cudaStream_t s, bool mixed, const PairArgs &a);
 // time-step: part[split][i] = min_j min(t_ff s(eta dt_ff), t_fb s(eta dt_fb)) (without eta)
@@ -123,15 +129,11 @@ constexpr float HOT_KAPPA = 6.0f;       // hot: |a| > HOT_KAPPA x (median bin's 
 constexpr int HOT_MAX_SPLITS = 16;      // source splits of k_grad_hot
 // hist[HOT_BINS] += counts of the bins of |a_i| over [3][n] accelerations (hist pre-zeroed)
 void launch_acc_hist(cudaStream_t s, const double *a_soa, int n, unsigned *hist);
-// after an accurate mixed Newtonian pass of A against B (records irec [3][n_a], jrec [3][n_s]):
-// writes the hot mask of A (words [(n_a + 31) / 32]) and recomputes a (out_soa, out_aos) of
-// the hot particles with their dominant terms in FP64.  hist: the |a| histogram of this pass;
-// hist2 (n2 values): that of the pass of B against A in a cross pair, or NULL.
-void launch_acc_refine(cudaStream_t s, const float4 *irec, const float4 *jrec, int n_a, int n_s,
-                       int self_pass, const int32_t *A, const int32_t *B, const double *x,
-                       const double *m, int N, double G, double eps2, const float *wmax,
-                       const unsigned *hist, const unsigned *hist2, int n2, double *out_soa,
-                       double *out_aos, uint32_t *mask);
+// after an accurate mixed Newtonian pass of A against B (a_soa [3][n_a]): writes the hot
+// mask of A (words [(n_a + 31) / 32]).  hist: the |a| histogram of this pass; hist2 (n2
+// values): that of the pass of B against A in a cross pair, or NULL.
+void launch_hot_mask(cudaStream_t s, const double *a_soa, int n_a, const unsigned *hist,
+                     const unsigned *hist2, int n2, uint32_t *mask);
 // number of source splits of launch_grad_hot for these list sizes
 int hot_grad_splits(int n_a, int n_s, int n_sm);
 // part[s][c][i] = FP64 gradient sums over the hot sources of B (mask) for every i of A
@@ -153,7 +155,7 @@ void launch_kick_by_particle(cudaStream_t s, const int32_t *list, int n, double 
 void launch_drift(cudaStream_t s, const int32_t *list, int n, double *x, const double *v,
                   int N, double dt);
 // drift, then pack the moved particles' position records for the next Newtonian pass:
-// mode 0 mixed {hi, lo} records, 1 mixed three-way split records (accurate pass), 2 FP64
+// mode 0 mixed {hi, lo} records, 2 FP64
 void launch_drift_pack(cudaStream_t s, const int32_t *list, int n, double *x, const double *v,
                        const double *m, int N, double dt, void *rec, int mode);
 // stable partition: S gets set[k] with tau[k] >= pivot, F the rest; counts[0] = |S|,

@@ -10,11 +10,11 @@
 // The size of a_ji in a pass is set by the typical |a| of both lists, so sources with
 // |a_j| > HOT_KAPPA x (upper edge of the histogram bin holding the median |a| of the active
 // list, or of the source list if that is larger) are "hot":
-//   * k_acc_refine recomputes their accelerations with the dominant terms (m_k / r^3 above a
-//     quarter of the largest) in FP64 from the FP64 store, so that the partners' mutual forces
-//     are as consistent as in FP64, and marks them in a bit mask;
+//   * k_hot_mask marks them in a bit mask (their accelerations are already accurate: the
+//     Newtonian pass that feeds a gradient sums its dominant terms in double-float with the
+//     FP64 masses, so the partners' mutual forces are as consistent as in FP64);
 //   * the gradient pass zeroes their masses in its FP32 records and k_grad_hot sums their
-//     terms in FP64 for every active particle, into separate split partials.
+//     terms in double-float for every active particle, into separate split partials.
 // The classification depends only on the accelerations, so the results stay deterministic;
 // with no hot source both kernels only read the mask and write zeros.
 #include "df_arith.cuh"
@@ -99,25 +99,6 @@ __device__ int block_scan(int v, int *total)
     return before + incl - v;
 }
 
-// deterministic block sum of three doubles; the result is valid in thread 0
-__device__ void block_sum3(double (&v)[3])
-{
-    __shared__ double s_r[HOT_BS / 32][3];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int c = 0; c < 3; ++c)
-        for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
-    __syncthreads();
-    if (lane == 0)
-        for (int c = 0; c < 3; ++c) s_r[warp][c] = v[c];
-    __syncthreads();
-    if (threadIdx.x == 0)
-        for (int c = 0; c < 3; ++c) {
-            double s = 0.0;
-            for (int w = 0; w < HOT_BS / 32; ++w) s += s_r[w][c];
-            v[c] = s;
-        }
-}
-
 }  // namespace
 
 // Histogram of the acceleration norms of a finished Newtonian pass: one count per particle in
@@ -136,101 +117,15 @@ __global__ void __launch_bounds__(HOT_BS) k_acc_hist(const double *__restrict__ 
 }
 
 // position within the block (0..HOT_BS) of the q-th set bit of the block's mask words
-__device__ __forceinline__ int nth_hot(const unsigned *words, int q)
-{
-    for (int w = 0; w < HOT_BS / 32; ++w) {
-        const unsigned bits = words[w];
-        const int c = __popc(bits);
-        if (q < c) {
-            unsigned b = bits;
-            for (int k = 0; k < q; ++k) b &= b - 1u;
-            return w * 32 + __ffs(b) - 1;
-        }
-        q -= c;
-    }
-    return 0;
-}
-
-// one thread's share of the refined acceleration of target t: the sources j0, j0 + dj, ...;
-// FP32 pair terms on the three-way split records, except up to GRAD_SLOTS terms with
-// m_j / r^3 > thr, which are evaluated in FP64 from the particle store
-__device__ void refine_partial(int t, int j0, int dj, const float4 *__restrict__ irec,
-                               const float4 *__restrict__ jrec, int n_a, int n_s, int self_pass,
-                               const int32_t *__restrict__ Alist, const int32_t *__restrict__ Blist,
-                               const double *__restrict__ x, const double *__restrict__ m, int N,
-                               double eps2d, float thr, double (&r)[3])
-{
-    const float eps2 = (float)eps2d;
-    const float4 q0 = irec[t], q1 = irec[n_a + t], q2 = irec[2 * n_a + t];
-    int nb = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
-    float H[3] = {0.f, 0.f, 0.f}, L[3] = {0.f, 0.f, 0.f}, s[3] = {0.f, 0.f, 0.f};
-    int cnt = 0;
-    for (int j = j0; j < n_s; j += dj) {
-        if (self_pass && j == t) continue;
-        const float4 J0 = jrec[j], J1 = jrec[n_s + j], J2 = jrec[2 * n_s + j];
-        const float dx = ((J0.x - q0.x) + (J1.x - q1.x)) + (J2.x - q2.x);
-        const float dy = ((J0.y - q0.y) + (J1.y - q1.y)) + (J2.y - q2.y);
-        const float dz = ((J0.z - q0.z) + (J1.z - q1.z)) + (J2.z - q2.z);
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-        float y = rsqrtf(r2);
-        const float hy = (0.5f * r2) * y;
-        y = fmaf(y, fmaf(-hy, y, 0.5f), y);
-        const float wt = J0.w * y * (y * y);
-        if (wt > thr && nb < GRAD_SLOTS) {
-            if (nb == 0) b0 = j;
-            else if (nb == 1) b1 = j;
-            else if (nb == 2) b2 = j;
-            else b3 = j;
-            ++nb;
-            continue;
-        }
-        s[0] = fmaf(wt, dx, s[0]);
-        s[1] = fmaf(wt, dy, s[1]);
-        s[2] = fmaf(wt, dz, s[2]);
-        if (++cnt == 16) {
-            for (int c = 0; c < 3; ++c) {
-                fold2(H[c], L[c], s[c]);
-                s[c] = 0.f;
-            }
-            cnt = 0;
-        }
-    }
-    for (int c = 0; c < 3; ++c) {
-        fold2(H[c], L[c], s[c]);
-        r[c] = (double)H[c] + (double)L[c];
-    }
-    const int gi = Alist ? Alist[t] : t;
-    const double xi = x[gi], yi = x[N + gi], zi = x[2 * N + gi];
-    for (int q = 0; q < nb; ++q) {
-        const int j = (q == 0) ? b0 : (q == 1) ? b1 : (q == 2) ? b2 : b3;
-        const int gj = Blist ? Blist[j] : j;
-        const double ddx = x[gj] - xi, ddy = x[N + gj] - yi, ddz = x[2 * N + gj] - zi;
-        const double rr2 = fma(ddx, ddx, fma(ddy, ddy, fma(ddz, ddz, eps2d)));
-        const double ri = rsqrt(rr2);
-        const double ww = m[gj] * (ri * ri * ri);
-        r[0] = fma(ww, ddx, r[0]);
-        r[1] = fma(ww, ddy, r[1]);
-        r[2] = fma(ww, ddz, r[2]);
-    }
-}
-
-// Marks the hot particles of a finished accurate Newtonian pass of A against B (mask bit k of
-// word k / 32) and recomputes their accelerations: FP32 pair terms on the three-way split
-// records of that pass, except up to GRAD_SLOTS terms per thread with m_j / r^3 above
-// wmax_k / 4, which are evaluated in FP64 from the particle store.  The threshold is
-// HOT_KAPPA x the larger median edge of hist (n_a values of this pass) and hist2 (n2 values
-// of the companion pass of B against A, or NULL).  One block per 256 particles: with at most
-// two hot particles the whole block refines each, otherwise one warp per hot particle; the
-// sums run in a fixed order either way.
-__global__ void __launch_bounds__(HOT_BS) k_acc_refine(
-    const float4 *__restrict__ irec, const float4 *__restrict__ jrec, int n_a, int n_s, int self_pass,
-    const int32_t *__restrict__ Alist, const int32_t *__restrict__ Blist, const double *__restrict__ x,
-    const double *__restrict__ m, int N, double G, double eps2d, const float *__restrict__ wmax,
-    const unsigned *__restrict__ hist, const unsigned *__restrict__ hist2, int n2,
-    double *__restrict__ out_soa, double *__restrict__ out_aos, uint32_t *__restrict__ mask)
+// Marks the hot particles of a finished accurate Newtonian pass of A against B: mask bit k
+// of word k / 32 is set when |a_k| exceeds HOT_KAPPA x the larger median edge of hist (n_a
+// values of this pass) and hist2 (n2 values of the companion pass of B against A, or NULL).
+__global__ void __launch_bounds__(HOT_BS) k_hot_mask(const double *__restrict__ a_soa, int n_a,
+                                                     const unsigned *__restrict__ hist,
+                                                     const unsigned *__restrict__ hist2, int n2,
+                                                     uint32_t *__restrict__ mask)
 {
     __shared__ float s_thr;
-    __shared__ unsigned s_words[HOT_BS / 32];
     __shared__ unsigned s_hist[2][HOT_BINS];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool two = hist2 && n2 > 0;
@@ -248,48 +143,9 @@ __global__ void __launch_bounds__(HOT_BS) k_acc_refine(
     const int base = blockIdx.x * HOT_BS;
     const int k = base + tid;
     bool hot = false;
-    if (k < n_a) hot = acc_norm(out_soa[k], out_soa[n_a + k], out_soa[2 * n_a + k]) > s_thr;
+    if (k < n_a) hot = acc_norm(a_soa[k], a_soa[n_a + k], a_soa[2 * n_a + k]) > s_thr;
     const unsigned word = __ballot_sync(0xffffffffu, hot);
-    if (lane == 0) {
-        s_words[warp] = word;
-        if (base + warp * 32 < n_a) mask[(base >> 5) + warp] = word;
-    }
-    __syncthreads();
-    int nhot = 0;
-    for (int w = 0; w < HOT_BS / 32; ++w) nhot += __popc(s_words[w]);
-    if (nhot <= 2) {
-        // few targets: each one by the whole block
-        for (int q = 0; q < nhot; ++q) {
-            const int t = base + nth_hot(s_words, q);
-            double r[3];
-            refine_partial(t, tid, HOT_BS, irec, jrec, n_a, n_s, self_pass, Alist, Blist, x, m, N, eps2d,
-                           0.25f * wmax[t], r);
-            block_sum3(r);
-            if (tid == 0)
-                for (int c = 0; c < 3; ++c) {
-                    const double a = G * r[c];
-                    out_soa[(size_t)c * n_a + t] = a;
-                    if (out_aos) out_aos[(size_t)t * 3 + c] = a;
-                }
-            __syncthreads();
-        }
-    } else {
-        // many targets: one warp each, no block barrier
-        for (int q = warp; q < nhot; q += HOT_BS / 32) {
-            const int t = base + nth_hot(s_words, q);
-            double r[3];
-            refine_partial(t, lane, 32, irec, jrec, n_a, n_s, self_pass, Alist, Blist, x, m, N, eps2d,
-                           0.25f * wmax[t], r);
-            for (int c = 0; c < 3; ++c)
-                for (int o = 16; o > 0; o >>= 1) r[c] += __shfl_xor_sync(0xffffffffu, r[c], o);
-            if (lane == 0)
-                for (int c = 0; c < 3; ++c) {
-                    const double a = G * r[c];
-                    out_soa[(size_t)c * n_a + t] = a;
-                    if (out_aos) out_aos[(size_t)t * 3 + c] = a;
-                }
-        }
-    }
+    if (lane == 0 && base + warp * 32 < n_a) mask[(base >> 5) + warp] = word;
 }
 
 // Gradient terms of the hot sources of B (mask bits) for every particle of A, in double-float
@@ -397,16 +253,11 @@ void launch_acc_hist(cudaStream_t s, const double *a_soa, int n, unsigned *hist)
     k_acc_hist<<<blocks, HOT_BS, 0, s>>>(a_soa, n, hist);
 }
 
-void launch_acc_refine(cudaStream_t s, const float4 *irec, const float4 *jrec, int n_a, int n_s,
-                       int self_pass, const int32_t *A, const int32_t *B, const double *x,
-                       const double *m, int N, double G, double eps2, const float *wmax,
-                       const unsigned *hist, const unsigned *hist2, int n2, double *out_soa,
-                       double *out_aos, uint32_t *mask)
+void launch_hot_mask(cudaStream_t s, const double *a_soa, int n_a, const unsigned *hist,
+                     const unsigned *hist2, int n2, uint32_t *mask)
 {
     if (n_a <= 0) return;
-    k_acc_refine<<<(n_a + HOT_BS - 1) / HOT_BS, HOT_BS, 0, s>>>(irec, jrec, n_a, n_s, self_pass, A, B, x,
-                                                                m, N, G, eps2, wmax, hist, hist2, n2,
-                                                                out_soa, out_aos, mask);
+    k_hot_mask<<<(n_a + HOT_BS - 1) / HOT_BS, HOT_BS, 0, s>>>(a_soa, n_a, hist, hist2, n2, mask);
 }
 
 int hot_grad_splits(int n_a, int n_s, int n_sm)

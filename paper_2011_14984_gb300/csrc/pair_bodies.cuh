@@ -7,10 +7,12 @@
 // The record layouts are described in frost_internal.cuh.
 #pragma once
 
+#include "df_arith.cuh"
 #include "frost_internal.cuh"
 
 #include <cfloat>
 #include <cmath>
+#include <type_traits>
 
 namespace frost {
 namespace dev {
@@ -133,12 +135,92 @@ __device__ __forceinline__ void pack_tstep_fp64_one(int k, const int32_t *__rest
     rec[n + k] = make_double4_32a(v[i], v[N + i], v[2 * N + i], G * m[i]);
     if (acc) rec[2 * n + k] = make_double4_32a(acc[k], acc[n + k], acc[2 * n + k], 0.0);
 }
+// Dominant terms.  A term with m_j / r^3 above SLOT_FRACTION x max_j m_j / r^3 is kept out
+// of the FP32 partial sums (a heavy term sets the rounding of every later addition to its
+// partial sum) and up to GRAD_SLOTS of them per particle are evaluated in double-float after
+// the loop.  The j indices wait in registers (constant slot indices after unrolling).
+constexpr int GRAD_SLOTS = 8;
+constexpr float SLOT_FRACTION = 0.0625f;
+
+template <int ILP>
+struct BigSlots;
+template <int ILP>
+__device__ __forceinline__ void push_big(BigSlots<ILP> &b, int k, int j);
+
+// slot indices in registers (the single-CTA solver's bodies)
+template <int ILP>
+struct BigSlots {
+    int n[ILP];
+    int j[GRAD_SLOTS][ILP];
+    __device__ __forceinline__ bool room(int k) const { return n[k] < GRAD_SLOTS; }
+    __device__ __forceinline__ void push(int k, int jj) { push_big(*this, k, jj); }
+    __device__ __forceinline__ int get(int s, int k) const { return j[s][k]; }
+};
+
+// slot indices in shared memory, one column per thread (the grid kernels: saves the
+// 2 x GRAD_SLOTS registers that would cost occupancy); row (s * ILP + k) of STRIDE words
+template <int ILP, int STRIDE>
+struct SmemSlots {
+    int n[ILP];
+    int *col;
+    __device__ __forceinline__ bool room(int k) const { return n[k] < GRAD_SLOTS; }
+    __device__ __forceinline__ void push(int k, int jj) { col[(n[k] * ILP + k) * STRIDE] = jj; ++n[k]; }
+    __device__ __forceinline__ int get(int s, int k) const { return col[(s * ILP + k) * STRIDE]; }
+};
+
+template <int ILP>
+__device__ __forceinline__ void init_big(BigSlots<ILP> &b, int fill)
+{
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+        b.n[k] = 0;
+#pragma unroll
+        for (int s = 0; s < GRAD_SLOTS; ++s) b.j[s][k] = fill;
+    }
+}
+
+template <int ILP>
+__device__ __forceinline__ void push_big(BigSlots<ILP> &b, int k, int j)
+{
+    const int c = b.n[k];
+#pragma unroll
+    for (int s = 0; s < GRAD_SLOTS; ++s)
+        if (s == c) b.j[s][k] = j;
+    b.n[k] = c + 1;
+}
+
+struct D3 {
+    double x, y, z;
+};
+
+// One Newtonian pair term m_j x_ji / r^3 in double-float from the float-float position
+// records (positions to 48 bits) and the FP64 mass mj (the two partners of a tight pair then
+// carry exactly opposite momenta, which the gradients of the other particles difference).
+static __device__ __noinline__ D3 acc_term_df(const float4 J0, const float4 J1, float ixh, float iyh, float izh,
+                                              float ixl, float iyl, float izl, double mj, double eps2)
+{
+    using df::dfloat;
+    const dfloat dx = df::sub(df::make(J0.x, J1.x), df::make(ixh, ixl));
+    const dfloat dy = df::sub(df::make(J0.y, J1.y), df::make(iyh, iyl));
+    const dfloat dz = df::sub(df::make(J0.z, J1.z), df::make(izh, izl));
+    const dfloat r2 = df::add(df::add(df::mul(dx, dx), df::mul(dy, dy)), df::add(df::mul(dz, dz), df::from_double(eps2)));
+    const dfloat ri = df::rsqrt(r2);
+    const dfloat w = df::mul(df::mul(df::mul(ri, ri), ri), df::from_double(mj));
+    D3 r;
+    r.x = df::to_double(df::mul(w, dx));
+    r.y = df::to_double(df::mul(w, dy));
+    r.z = df::to_double(df::mul(w, dz));
+    return r;
+}
+
 template <int ILP>
 struct AccMixedI {
     float xh[ILP], yh[ILP], zh[ILP], xl[ILP], yl[ILP], zl[ILP];
 };
 
-template <int ILP, bool MASK, bool WMAX>
+// NEWTON: one Newton-Raphson step on the MUFU rsqrt (y <- y (3/2 - r2 y^2 / 2)), for the
+// pass that feeds a gradient (the gradient differences a_j - a_i and needs a_j to ~1e-7)
+template <int ILP, bool MASK, bool WMAX, bool NEWTON = false>
 __device__ __forceinline__ void acc_mixed_j(const float4 J0, const float4 J1, const AccMixedI<ILP> &I,
                                             float eps2, int jpos, const int (&ipos)[ILP],
                                             float (&ax)[ILP], float (&ay)[ILP], float (&az)[ILP],
@@ -150,7 +232,11 @@ __device__ __forceinline__ void acc_mixed_j(const float4 J0, const float4 J1, co
         const float dy = (J0.y - I.yh[k]) + (J1.y - I.yl[k]);
         const float dz = (J0.z - I.zh[k]) + (J1.z - I.zl[k]);
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-        const float ri = rsqrtf(r2);
+        float ri = rsqrtf(r2);
+        if (NEWTON) {
+            const float hy = (0.5f * r2) * ri;
+            ri = fmaf(ri, fmaf(-hy, ri, 0.5f), ri);
+        }
         const float ri2 = ri * ri;
         float w = J0.w * ri * ri2;
         if (MASK) w = (jpos == ipos[k]) ? 0.f : w;
@@ -158,6 +244,52 @@ __device__ __forceinline__ void acc_mixed_j(const float4 J0, const float4 J1, co
         ax[k] = fmaf(w, dx, ax[k]);
         ay[k] = fmaf(w, dy, ay[k]);
         az[k] = fmaf(w, dz, az[k]);
+    }
+}
+
+// Newtonian pair term of the pass that feeds a gradient: Newton-refined rsqrt; a term above
+// thr[k] goes to a deferred slot and stays out of the FP32 partial sums
+template <int ILP, bool MASK, class Slots>
+__device__ __forceinline__ void acc_defer_j(const float4 J0, const float4 J1, const AccMixedI<ILP> &I,
+                                            float eps2, int jglob, int jpos, const int (&ipos)[ILP],
+                                            const float (&thr)[ILP], Slots &big,
+                                            float (&ax)[ILP], float (&ay)[ILP], float (&az)[ILP])
+{
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+        const float dx = (J0.x - I.xh[k]) + (J1.x - I.xl[k]);
+        const float dy = (J0.y - I.yh[k]) + (J1.y - I.yl[k]);
+        const float dz = (J0.z - I.zh[k]) + (J1.z - I.zl[k]);
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+        float ri = rsqrtf(r2);
+        const float hy = (0.5f * r2) * ri;
+        ri = fmaf(ri, fmaf(-hy, ri, 0.5f), ri);
+        float w = J0.w * ri * (ri * ri);
+        if (MASK) w = (jpos == ipos[k]) ? 0.f : w;
+        const bool isbig = (w > thr[k]) && big.room(k);
+        if (isbig) big.push(k, jglob);
+        const float wf = isbig ? 0.f : w;
+        ax[k] = fmaf(wf, dx, ax[k]);
+        ay[k] = fmaf(wf, dy, ay[k]);
+        az[k] = fmaf(wf, dz, az[k]);
+    }
+}
+
+// max_j m_j / r^3 (the scale of the dominant terms), FP32 on the position records
+template <int ILP, bool MASK>
+__device__ __forceinline__ void wmax_mixed_j(const float4 J0, const float4 J1, const AccMixedI<ILP> &I,
+                                             float eps2, int jpos, const int (&ipos)[ILP], float (&wm)[ILP])
+{
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+        const float dx = (J0.x - I.xh[k]) + (J1.x - I.xl[k]);
+        const float dy = (J0.y - I.yh[k]) + (J1.y - I.yl[k]);
+        const float dz = (J0.z - I.zh[k]) + (J1.z - I.zl[k]);
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+        const float ri = rsqrtf(r2);
+        float w = J0.w * ri * (ri * ri);
+        if (MASK) w = (jpos == ipos[k]) ? 0.f : w;
+        wm[k] = fmaxf(wm[k], w);
     }
 }
 
@@ -181,60 +313,37 @@ struct GradMixedI {
     float ahx[ILP], ahy[ILP], ahz[ILP], alx[ILP], aly[ILP], alz[ILP];
 };
 
-// One pair term in FP64, rebuilt exactly from the split records (positions to 48 bits,
-// accelerations to 36 bits); used for the few dominant terms of each particle.
+// One gradient pair term in double-float, rebuilt from the split records (positions to 48
+// bits, accelerations to 36 bits); used for the few dominant terms of each particle.
 template <int ILP>
-__device__ __noinline__ void grad_term_fp64(const float4 J0, const float4 J1, const float4 J2,
-                                            const float4 J3, const GradMixedI<ILP> &I, int k,
-                                            double eps2, double &gx, double &gy, double &gz)
+__device__ __noinline__ void grad_term_df(const float4 J0, const float4 J1, const float4 J2, const float4 J3,
+                                          const GradMixedI<ILP> &I, int k, double eps2, double &gx, double &gy,
+                                          double &gz)
 {
-    const double dx = (((double)J0.x + (double)J1.x) + (double)J2.x) -
-                      (((double)I.xh[k] + (double)I.xm[k]) + (double)I.xl[k]);
-    const double dy = (((double)J0.y + (double)J1.y) + (double)J2.y) -
-                      (((double)I.yh[k] + (double)I.ym[k]) + (double)I.yl[k]);
-    const double dz = (((double)J0.z + (double)J1.z) + (double)J2.z) -
-                      (((double)I.zh[k] + (double)I.zm[k]) + (double)I.zl[k]);
-    const double Ax = ((double)J1.w + (double)J3.y) - ((double)I.ahx[k] + (double)I.alx[k]);
-    const double Ay = ((double)J2.w + (double)J3.z) - ((double)I.ahy[k] + (double)I.aly[k]);
-    const double Az = ((double)J3.x + (double)J3.w) - ((double)I.ahz[k] + (double)I.alz[k]);
-    const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
-    const double ri = rsqrt(r2);
-    const double ri2 = ri * ri;
-    const double w = (double)J0.w * ri * ri2;
-    const double xa = fma(dx, Ax, fma(dy, Ay, dz * Az));
-    const double t3 = 3.0 * xa * ri2;
-    gx = fma(w, fma(-t3, dx, Ax), gx);
-    gy = fma(w, fma(-t3, dy, Ay), gy);
-    gz = fma(w, fma(-t3, dz, Az), gz);
+    using df::dfloat;
+    const dfloat dx = df::sep(J0.x, J1.x, J2.x, I.xh[k], I.xm[k], I.xl[k]);
+    const dfloat dy = df::sep(J0.y, J1.y, J2.y, I.yh[k], I.ym[k], I.yl[k]);
+    const dfloat dz = df::sep(J0.z, J1.z, J2.z, I.zh[k], I.zm[k], I.zl[k]);
+    const dfloat Ax = df::sub(df::make(J1.w, J3.y), df::make(I.ahx[k], I.alx[k]));
+    const dfloat Ay = df::sub(df::make(J2.w, J3.z), df::make(I.ahy[k], I.aly[k]));
+    const dfloat Az = df::sub(df::make(J3.x, J3.w), df::make(I.ahz[k], I.alz[k]));
+    const dfloat r2 = df::add(df::add(df::mul(dx, dx), df::mul(dy, dy)), df::add(df::mul(dz, dz), df::from_double(eps2)));
+    const dfloat ri = df::rsqrt(r2);
+    const dfloat ri2 = df::mul(ri, ri);
+    const dfloat w = df::mul_f(df::mul(ri2, ri), J0.w);
+    const dfloat xa = df::add(df::add(df::mul(dx, Ax), df::mul(dy, Ay)), df::mul(dz, Az));
+    const dfloat t3 = df::mul(df::mul_f(xa, 3.f), ri2);
+    gx += df::to_double(df::mul(w, df::sub(Ax, df::mul(t3, dx))));
+    gy += df::to_double(df::mul(w, df::sub(Ay, df::mul(t3, dy))));
+    gz += df::to_double(df::mul(w, df::sub(Az, df::mul(t3, dz))));
 }
 
-// Dominant terms: up to GRAD_SLOTS per particle are recorded during the j-loop and summed
-// in FP64 after it (deferred, so the FP64 work is not issued once per lane and source).
-constexpr int GRAD_SLOTS = 4;
-
-template <int ILP>
-struct BigSlots {
-    int n[ILP];
-    int j0[ILP], j1[ILP], j2[ILP], j3[ILP];
-};
-
-template <int ILP>
-__device__ __forceinline__ void push_big(BigSlots<ILP> &b, int k, int j)
-{
-    const int c = b.n[k];
-    if (c == 0) b.j0[k] = j;
-    else if (c == 1) b.j1[k] = j;
-    else if (c == 2) b.j2[k] = j;
-    else b.j3[k] = j;
-    b.n[k] = c + 1;
-}
-
-template <int ILP, bool MASK>
+template <int ILP, bool MASK, class Slots>
 __device__ __forceinline__ void grad_mixed_j(const float4 J0, const float4 J1, const float4 J2,
                                              const float4 J3, const GradMixedI<ILP> &I,
                                              float eps2, int jglob, int jpos,
                                              const int (&ipos)[ILP], const float (&thr)[ILP],
-                                             BigSlots<ILP> &big, float (&gx)[ILP],
+                                             Slots &big, float (&gx)[ILP],
                                              float (&gy)[ILP], float (&gz)[ILP])
 {
 #pragma unroll
@@ -260,8 +369,8 @@ __device__ __forceinline__ void grad_mixed_j(const float4 J0, const float4 J1, c
             w = self ? 0.f : w;
         }
         // a dominant term goes to a deferred FP64 slot and stays out of the FP32 sum
-        const bool isbig = (w > thr[k]) && (big.n[k] < GRAD_SLOTS);
-        if (isbig) push_big(big, k, jglob);
+        const bool isbig = (w > thr[k]) && big.room(k);
+        if (isbig) big.push(k, jglob);
         const float wf = isbig ? 0.f : w;
         const float xa = fmaf(dx, Ax, fmaf(dy, Ay, dz * Az));
         const float t3 = 3.0f * xa * ri2;  // 3 (x.a) / r^2
@@ -277,30 +386,6 @@ __device__ __forceinline__ void grad_mixed_j(const float4 J0, const float4 J1, c
             gy[k] = ny;
             gz[k] = nz;
         }
-    }
-}
-
-template <int ILP, bool MASK>
-__device__ __forceinline__ void acc3_mixed_j(const float4 J0, const float4 J1, const float4 J2,
-                                             const GradMixedI<ILP> &I, float eps2, int jpos,
-                                             const int (&ipos)[ILP], float (&ax)[ILP],
-                                             float (&ay)[ILP], float (&az)[ILP], float (&wm)[ILP])
-{
-#pragma unroll
-    for (int k = 0; k < ILP; ++k) {
-        const float dx = ((J0.x - I.xh[k]) + (J1.x - I.xm[k])) + (J2.x - I.xl[k]);
-        const float dy = ((J0.y - I.yh[k]) + (J1.y - I.ym[k])) + (J2.y - I.yl[k]);
-        const float dz = ((J0.z - I.zh[k]) + (J1.z - I.zm[k])) + (J2.z - I.zl[k]);
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-        float y = rsqrtf(r2);
-        const float hy = (0.5f * r2) * y;
-        y = fmaf(y, fmaf(-hy, y, 0.5f), y);
-        float w = J0.w * y * (y * y);
-        if (MASK) w = (jpos == ipos[k]) ? 0.f : w;
-        wm[k] = fmaxf(wm[k], w);
-        ax[k] = fmaf(w, dx, ax[k]);
-        ay[k] = fmaf(w, dy, ay[k]);
-        az[k] = fmaf(w, dz, az[k]);
     }
 }
 
@@ -479,12 +564,20 @@ __device__ __forceinline__ void tstep_fp64_j(const double4_32a J, const double4_
 // ======================================================================================
 
 // Newtonian pass, mixed precision (float-float separations, MUFU rsqrt, folds every 64)
-template <int BS, int ILP, int TJ, bool WMAX>
+// NEWTON (the pass that feeds a gradient): Newton-refined rsqrt and folds every 16 pairs.
+// DEFER (with NEWTON): the terms above SLOT_FRACTION x wmax[i] (wmax from a prepass at the
+// same positions) are deferred and summed in double-float after the loop, with the FP64
+// masses mstore[jlist[j]] (jlist NULL: the identity).
+template <int BS, int ILP, int TJ, bool WMAX, bool NEWTON = false, bool DEFER = false>
 __device__ __forceinline__ void acc_mixed_body(const float4 *__restrict__ irec,
                                                const float4 *__restrict__ jrec, int n_a, int n_s,
                                                int ibase, int jb, int je, int self_pass, float eps2,
-                                               double (&res)[ILP][3], float (&wres)[ILP])
+                                               double (&res)[ILP][3], float (&wres)[ILP],
+                                               const float *__restrict__ wmax = nullptr, double eps2d = 0.0,
+                                               const int32_t *__restrict__ jlist = nullptr,
+                                               const double *__restrict__ mstore = nullptr)
 {
+    static_assert(!DEFER || NEWTON, "the deferred variant is the accurate one");
     __shared__ float4 s0[TJ];
     __shared__ float4 s1[TJ];
     const int tid = threadIdx.x;
@@ -502,6 +595,17 @@ __device__ __forceinline__ void acc_mixed_body(const float4 *__restrict__ irec,
         I.xh[k] = a.x; I.yh[k] = a.y; I.zh[k] = a.z;
         I.xl[k] = b.x; I.yl[k] = b.y; I.zl[k] = b.z;
     }
+    float thr[ILP];
+    SmemSlots<ILP, BS> big;
+    if constexpr (DEFER) {
+        __shared__ int s_slot[GRAD_SLOTS * ILP * BS];
+        big.col = s_slot + tid;
+#pragma unroll
+        for (int k = 0; k < ILP; ++k) {
+            big.n[k] = 0;
+            thr[k] = (ipos[k] < n_a) ? SLOT_FRACTION * wmax[ipos[k]] : INFINITY;
+        }
+    }
     float hx[ILP], hy[ILP], hz[ILP], lx[ILP], ly[ILP], lz[ILP], wm[ILP];
 #pragma unroll
     for (int k = 0; k < ILP; ++k) hx[k] = hy[k] = hz[k] = lx[k] = ly[k] = lz[k] = wm[k] = 0.f;
@@ -515,24 +619,41 @@ __device__ __forceinline__ void acc_mixed_body(const float4 *__restrict__ irec,
         }
         __syncthreads();
         const bool diag = self_pass && (j0 < ibase + BS * ILP) && (ibase < j0 + cnt);
-        // FP32 partial sums over at most 64 pairs before each compensated fold
-        for (int c0 = 0; c0 < cnt; c0 += 64) {
-            const int c1 = min(cnt, c0 + 64);
+        // FP32 partial sums over at most FOLD pairs before each compensated fold
+        constexpr int FOLD = NEWTON ? 16 : 64;
+        for (int c0 = 0; c0 < cnt; c0 += FOLD) {
+            const int c1 = min(cnt, c0 + FOLD);
             float ax[ILP], ay[ILP], az[ILP];
 #pragma unroll
             for (int k = 0; k < ILP; ++k) ax[k] = ay[k] = az[k] = 0.f;
             int jj = c0;
-            if (!diag) {
+            if constexpr (DEFER) {
+                if (!diag) {
+                    for (; jj + 8 <= c1; jj += 8) {
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+                            acc_defer_j<ILP, false>(s0[jj + u], s1[jj + u], I, eps2, j0 + jj + u, 0, ipos, thr, big,
+                                                    ax, ay, az);
+                    }
+                    for (; jj < c1; ++jj)
+                        acc_defer_j<ILP, false>(s0[jj], s1[jj], I, eps2, j0 + jj, 0, ipos, thr, big, ax, ay, az);
+                } else {
+                    for (; jj < c1; ++jj)
+                        acc_defer_j<ILP, true>(s0[jj], s1[jj], I, eps2, j0 + jj, j0 + jj, ipos, thr, big, ax, ay,
+                                               az);
+                }
+            } else if (!diag) {
                 for (; jj + 8 <= c1; jj += 8) {
 #pragma unroll
                     for (int u = 0; u < 8; ++u)
-                        acc_mixed_j<ILP, false, WMAX>(s0[jj + u], s1[jj + u], I, eps2, 0, ipos, ax, ay, az, wm);
+                        acc_mixed_j<ILP, false, WMAX, NEWTON>(s0[jj + u], s1[jj + u], I, eps2, 0, ipos, ax, ay, az,
+                                                              wm);
                 }
                 for (; jj < c1; ++jj)
-                    acc_mixed_j<ILP, false, WMAX>(s0[jj], s1[jj], I, eps2, 0, ipos, ax, ay, az, wm);
+                    acc_mixed_j<ILP, false, WMAX, NEWTON>(s0[jj], s1[jj], I, eps2, 0, ipos, ax, ay, az, wm);
             } else {
                 for (; jj < c1; ++jj)
-                    acc_mixed_j<ILP, true, WMAX>(s0[jj], s1[jj], I, eps2, j0 + jj, ipos, ax, ay, az, wm);
+                    acc_mixed_j<ILP, true, WMAX, NEWTON>(s0[jj], s1[jj], I, eps2, j0 + jj, ipos, ax, ay, az, wm);
             }
 #pragma unroll
             for (int k = 0; k < ILP; ++k) {
@@ -548,90 +669,76 @@ __device__ __forceinline__ void acc_mixed_body(const float4 *__restrict__ irec,
         res[k][1] = (double)hy[k] + (double)ly[k];
         res[k][2] = (double)hz[k] + (double)lz[k];
         wres[k] = wm[k];
+        if constexpr (DEFER) {
+            // deferred double-float terms, records read back from global memory (L2)
+#pragma unroll
+            for (int s = 0; s < GRAD_SLOTS; ++s) {
+                if (s < big.n[k]) {
+                    const int j = big.get(s, k);
+                    const double mj = mstore[jlist ? jlist[j] : j];
+                    const D3 t = acc_term_df(jrec[j], jrec[n_s + j], I.xh[k], I.yh[k], I.zh[k], I.xl[k], I.yl[k],
+                                             I.zl[k], mj, eps2d);
+                    res[k][0] += t.x;
+                    res[k][1] += t.y;
+                    res[k][2] += t.z;
+                }
+            }
+        }
     }
 }
 
-// Newtonian pass feeding a gradient pass: three-way split separations, Newton-refined
-// rsqrt, folds every 16 pairs, max_j m_j / r^3 recorded (reads the gradient records q0..q2)
+// max_j m_j / r^3 over [jb, je) for the active records of the block (the prepass of the
+// deferred Newtonian pass)
 template <int BS, int ILP, int TJ>
-__device__ __forceinline__ void acc3_mixed_body(const float4 *__restrict__ irec,
+__device__ __forceinline__ void wmax_mixed_body(const float4 *__restrict__ irec,
                                                 const float4 *__restrict__ jrec, int n_a, int n_s,
                                                 int ibase, int jb, int je, int self_pass, float eps2,
-                                                double (&res)[ILP][3], float (&wres)[ILP])
+                                                float (&wres)[ILP])
 {
-    __shared__ float4 s0[TJ], s1[TJ], s2[TJ];
+    __shared__ float4 s0[TJ];
+    __shared__ float4 s1[TJ];
     const int tid = threadIdx.x;
-    GradMixedI<ILP> I;
+    AccMixedI<ILP> I;
     int ipos[ILP];
 #pragma unroll
     for (int k = 0; k < ILP; ++k) {
         const int i = ibase + k * BS + tid;
         ipos[k] = i;
-        float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0, q2 = q0;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
         if (i < n_a) {
-            q0 = irec[i];
-            q1 = irec[n_a + i];
-            q2 = irec[2 * n_a + i];
+            a = irec[i];
+            b = irec[n_a + i];
         }
-        I.xh[k] = q0.x; I.yh[k] = q0.y; I.zh[k] = q0.z;
-        I.xm[k] = q1.x; I.ym[k] = q1.y; I.zm[k] = q1.z;
-        I.xl[k] = q2.x; I.yl[k] = q2.y; I.zl[k] = q2.z;
-        I.ahx[k] = I.ahy[k] = I.ahz[k] = I.alx[k] = I.aly[k] = I.alz[k] = 0.f;
+        I.xh[k] = a.x; I.yh[k] = a.y; I.zh[k] = a.z;
+        I.xl[k] = b.x; I.yl[k] = b.y; I.zl[k] = b.z;
+        wres[k] = 0.f;
     }
-    float hx[ILP], hy[ILP], hz[ILP], lx[ILP], ly[ILP], lz[ILP], wm[ILP];
-#pragma unroll
-    for (int k = 0; k < ILP; ++k) hx[k] = hy[k] = hz[k] = lx[k] = ly[k] = lz[k] = wm[k] = 0.f;
-
     for (int j0 = jb; j0 < je; j0 += TJ) {
         const int cnt = min(TJ, je - j0);
         __syncthreads();
         for (int t = tid; t < cnt; t += BS) {
             s0[t] = jrec[j0 + t];
             s1[t] = jrec[n_s + j0 + t];
-            s2[t] = jrec[2 * n_s + j0 + t];
         }
         __syncthreads();
         const bool diag = self_pass && (j0 < ibase + BS * ILP) && (ibase < j0 + cnt);
-        for (int c0 = 0; c0 < cnt; c0 += 16) {
-            const int c1 = min(cnt, c0 + 16);
-            float ax[ILP], ay[ILP], az[ILP];
+        int jj = 0;
+        if (!diag) {
+            for (; jj + 8 <= cnt; jj += 8) {
 #pragma unroll
-            for (int k = 0; k < ILP; ++k) ax[k] = ay[k] = az[k] = 0.f;
-            int jj = c0;
-            if (!diag) {
-                for (; jj + 8 <= c1; jj += 8) {
-#pragma unroll
-                    for (int u = 0; u < 8; ++u)
-                        acc3_mixed_j<ILP, false>(s0[jj + u], s1[jj + u], s2[jj + u], I, eps2, 0, ipos, ax, ay,
-                                                 az, wm);
-                }
-                for (; jj < c1; ++jj)
-                    acc3_mixed_j<ILP, false>(s0[jj], s1[jj], s2[jj], I, eps2, 0, ipos, ax, ay, az, wm);
-            } else {
-                for (; jj < c1; ++jj)
-                    acc3_mixed_j<ILP, true>(s0[jj], s1[jj], s2[jj], I, eps2, j0 + jj, ipos, ax, ay, az, wm);
+                for (int u = 0; u < 8; ++u) wmax_mixed_j<ILP, false>(s0[jj + u], s1[jj + u], I, eps2, 0, ipos, wres);
             }
-#pragma unroll
-            for (int k = 0; k < ILP; ++k) {
-                fold2(hx[k], lx[k], ax[k]);
-                fold2(hy[k], ly[k], ay[k]);
-                fold2(hz[k], lz[k], az[k]);
-            }
+            for (; jj < cnt; ++jj) wmax_mixed_j<ILP, false>(s0[jj], s1[jj], I, eps2, 0, ipos, wres);
+        } else {
+            for (; jj < cnt; ++jj) wmax_mixed_j<ILP, true>(s0[jj], s1[jj], I, eps2, j0 + jj, ipos, wres);
         }
-    }
-#pragma unroll
-    for (int k = 0; k < ILP; ++k) {
-        res[k][0] = (double)hx[k] + (double)lx[k];
-        res[k][1] = (double)hy[k] + (double)ly[k];
-        res[k][2] = (double)hz[k] + (double)lz[k];
-        wres[k] = wm[k];
     }
 }
 
-// Gradient pass, mixed precision.  wmax: per active particle, max_j m_j / r^3 from the
-// Newtonian pass at the same positions (NULL: no FP64 terms); up to GRAD_SLOTS terms
-// heavier than wmax / 4 are recorded during the loop and summed in FP64 after it.
-template <int BS, int ILP, int TJ>
+// Gradient pass, mixed precision.  wmax: per active particle, max_j m_j / r^3 at the same
+// positions (NULL: no deferred terms); up to GRAD_SLOTS terms heavier than SLOT_FRACTION x
+// wmax are recorded during the loop and summed in double-float after it.
+template <int BS, int ILP, int TJ, bool SMEM_SLOTS = false>
 __device__ __forceinline__ void grad_mixed_body(const float4 *__restrict__ irec,
                                                 const float4 *__restrict__ jrec, int n_a, int n_s,
                                                 int ibase, int jb, int je, int self_pass, double eps2d,
@@ -643,13 +750,19 @@ __device__ __forceinline__ void grad_mixed_body(const float4 *__restrict__ irec,
     GradMixedI<ILP> I;
     int ipos[ILP];
     float thr[ILP];
-    BigSlots<ILP> big;
+    std::conditional_t<SMEM_SLOTS, SmemSlots<ILP, BS>, BigSlots<ILP>> big;
+    if constexpr (SMEM_SLOTS) {
+        __shared__ int s_slot[GRAD_SLOTS * ILP * BS];
+        big.col = s_slot + tid;
+#pragma unroll
+        for (int k = 0; k < ILP; ++k) big.n[k] = 0;
+    } else {
+        init_big(big, 0);
+    }
 #pragma unroll
     for (int k = 0; k < ILP; ++k) {
         const int i = ibase + k * BS + tid;
         ipos[k] = i;
-        big.n[k] = 0;
-        big.j0[k] = big.j1[k] = big.j2[k] = big.j3[k] = 0;
         float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0, q2 = q0, q3 = q0;
         thr[k] = INFINITY;
         if (i < n_a) {
@@ -657,7 +770,7 @@ __device__ __forceinline__ void grad_mixed_body(const float4 *__restrict__ irec,
             q1 = irec[n_a + i];
             q2 = irec[2 * n_a + i];
             q3 = irec[3 * n_a + i];
-            if (wmax) thr[k] = 0.25f * wmax[i];
+            if (wmax) thr[k] = SLOT_FRACTION * wmax[i];
         }
         I.xh[k] = q0.x; I.yh[k] = q0.y; I.zh[k] = q0.z;
         I.xm[k] = q1.x; I.ym[k] = q1.y; I.zm[k] = q1.z; I.ahx[k] = q1.w;
@@ -708,16 +821,16 @@ __device__ __forceinline__ void grad_mixed_body(const float4 *__restrict__ irec,
             }
         }
     }
-    // deferred FP64 terms, records read back from global memory (L2)
+    // deferred double-float terms, records read back from global memory (L2)
 #pragma unroll
     for (int k = 0; k < ILP; ++k) {
         double bx = 0.0, by = 0.0, bz = 0.0;
 #pragma unroll
         for (int s = 0; s < GRAD_SLOTS; ++s) {
             if (s < big.n[k]) {
-                const int j = (s == 0) ? big.j0[k] : (s == 1) ? big.j1[k] : (s == 2) ? big.j2[k] : big.j3[k];
-                grad_term_fp64<ILP>(jrec[j], jrec[n_s + j], jrec[2 * n_s + j], jrec[3 * n_s + j], I, k,
-                                    eps2d, bx, by, bz);
+                const int j = big.get(s, k);
+                grad_term_df<ILP>(jrec[j], jrec[n_s + j], jrec[2 * n_s + j], jrec[3 * n_s + j], I, k, eps2d,
+                                  bx, by, bz);
             }
         }
         res[k][0] = ((double)hx[k] + (double)lx[k]) + bx;

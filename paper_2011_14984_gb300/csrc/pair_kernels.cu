@@ -81,19 +81,23 @@ __global__ void k_pack_tstep_fp64(const int32_t *__restrict__ list, int n, const
 // ------------------------------------------------------------------------------------
 // grid pair kernels: one (i-block, j-split) per block
 // ------------------------------------------------------------------------------------
-template <int BS, int ILP, int TJ, bool WMAX>
+template <int BS, int ILP, int TJ, bool WMAX, bool NEWTON = false, bool DEFER = false>
 __global__ void __launch_bounds__(BS) k_acc_mixed(const float4 *__restrict__ irec,
                                                   const float4 *__restrict__ jrec, int n_a,
                                                   int n_s, int j_per_split, int self_pass,
                                                   float eps2, double *__restrict__ part,
-                                                  float *__restrict__ wpart)
+                                                  float *__restrict__ wpart,
+                                                  const float *__restrict__ wmax = nullptr, double eps2d = 0.0,
+                                                  const int32_t *__restrict__ jlist = nullptr,
+                                                  const double *__restrict__ mstore = nullptr)
 {
     const int ibase = blockIdx.x * (BS * ILP);
     const int jb = blockIdx.y * j_per_split;
     const int je = min(n_s, jb + j_per_split);
     double res[ILP][3];
     float wres[ILP];
-    acc_mixed_body<BS, ILP, TJ, WMAX>(irec, jrec, n_a, n_s, ibase, jb, je, self_pass, eps2, res, wres);
+    acc_mixed_body<BS, ILP, TJ, WMAX, NEWTON, DEFER>(irec, jrec, n_a, n_s, ibase, jb, je, self_pass, eps2, res, wres,
+                                                     wmax, eps2d, jlist, mstore);
 #pragma unroll
     for (int k = 0; k < ILP; ++k) {
         const int i = ibase + k * BS + threadIdx.x;
@@ -107,29 +111,23 @@ __global__ void __launch_bounds__(BS) k_acc_mixed(const float4 *__restrict__ ire
     }
 }
 
+// wmax[i] = max over the splits of max_j m_j / r^3 (wmax zeroed before; non-negative floats
+// order as their bit patterns, so the maximum is an integer atomicMax)
 template <int BS, int ILP, int TJ>
-__global__ void __launch_bounds__(BS) k_acc3_mixed(const float4 *__restrict__ irec,
-                                                   const float4 *__restrict__ jrec, int n_a,
-                                                   int n_s, int j_per_split, int self_pass,
-                                                   float eps2, double *__restrict__ part,
-                                                   float *__restrict__ wpart)
+__global__ void __launch_bounds__(BS) k_wmax_mixed(const float4 *__restrict__ irec,
+                                                   const float4 *__restrict__ jrec, int n_a, int n_s,
+                                                   int j_per_split, int self_pass, float eps2,
+                                                   float *__restrict__ wmax)
 {
     const int ibase = blockIdx.x * (BS * ILP);
     const int jb = blockIdx.y * j_per_split;
     const int je = min(n_s, jb + j_per_split);
-    double res[ILP][3];
     float wres[ILP];
-    acc3_mixed_body<BS, ILP, TJ>(irec, jrec, n_a, n_s, ibase, jb, je, self_pass, eps2, res, wres);
+    wmax_mixed_body<BS, ILP, TJ>(irec, jrec, n_a, n_s, ibase, jb, je, self_pass, eps2, wres);
 #pragma unroll
     for (int k = 0; k < ILP; ++k) {
         const int i = ibase + k * BS + threadIdx.x;
-        if (i < n_a) {
-            double *p = part + (size_t)blockIdx.y * 3 * n_a;
-            p[i] = res[k][0];
-            p[n_a + i] = res[k][1];
-            p[2 * n_a + i] = res[k][2];
-            wpart[(size_t)blockIdx.y * n_a + i] = wres[k];
-        }
+        if (i < n_a) atomicMax((int *)&wmax[i], __float_as_int(wres[k]));
     }
 }
 
@@ -144,7 +142,7 @@ __global__ void __launch_bounds__(BS) k_grad_mixed(const float4 *__restrict__ ir
     const int jb = blockIdx.y * j_per_split;
     const int je = min(n_s, jb + j_per_split);
     double res[ILP][3];
-    grad_mixed_body<BS, ILP, TJ>(irec, jrec, n_a, n_s, ibase, jb, je, self_pass, eps2d, wmax, res);
+    grad_mixed_body<BS, ILP, TJ, true>(irec, jrec, n_a, n_s, ibase, jb, je, self_pass, eps2d, wmax, res);
 #pragma unroll
     for (int k = 0; k < ILP; ++k) {
         const int i = ibase + k * BS + threadIdx.x;
@@ -396,7 +394,7 @@ int pair_blocks_per_sm(int kind, bool mixed)
     if (c) return c;
     if (kind == PASS_ACC)
         c = mixed ? std::min(occupancy_of(k_acc_mixed<PAIR_BS, PAIR_ILP, PAIR_TJ, false>, PAIR_BS, 0),
-                             occupancy_of(k_acc3_mixed<PAIR_BS, PAIR_ILP, PAIR_TJ>, PAIR_BS, 0))
+                             occupancy_of(k_acc_mixed<PAIR_BS, PAIR_ILP, PAIR_TJ, false, true, true>, PAIR_BS, 0))
                   : occupancy_of(k_acc_fp64<PAIR_BS, PAIR_TJ>, PAIR_BS, 0);
     else if (kind == PASS_GRAD)
         c = mixed ? occupancy_of(k_grad_mixed<PAIR_BS, PAIR_ILP, PAIR_TJ>, PAIR_BS, 0)
@@ -441,9 +439,9 @@ void launch_acc(cudaStream_t s, bool mixed, const PairArgs &a)
 {
     const dim3 grid(a.shape.nblk_i, a.shape.nsplit);
     if (mixed && a.accurate) {
-        k_acc3_mixed<PAIR_BS, PAIR_ILP, PAIR_TJ><<<grid, PAIR_BS, 0, s>>>(
+        k_acc_mixed<PAIR_BS, PAIR_ILP, PAIR_TJ, false, true, true><<<grid, PAIR_BS, 0, s>>>(
             (const float4 *)a.irec, (const float4 *)a.jrec, a.n_a, a.n_s, a.shape.j_per_split,
-            a.self_pass, (float)a.eps2, a.part, a.wpart);
+            a.self_pass, (float)a.eps2, a.part, nullptr, a.wmax, a.eps2, a.jlist, a.m);
     } else if (mixed) {
         if (a.wpart)
             k_acc_mixed<PAIR_BS, PAIR_ILP, PAIR_TJ, true><<<grid, PAIR_BS, 0, s>>>(
@@ -458,6 +456,15 @@ void launch_acc(cudaStream_t s, bool mixed, const PairArgs &a)
             (const double4_32a *)a.irec, (const double4_32a *)a.jrec, a.n_a, a.n_s, a.shape.j_per_split,
             a.self_pass, a.eps2, a.part);
     }
+}
+
+void launch_wmax(cudaStream_t s, const PairArgs &a, float *wmax)
+{
+    cudaMemsetAsync(wmax, 0, sizeof(float) * a.n_a, s);
+    const dim3 grid(a.shape.nblk_i, a.shape.nsplit);
+    k_wmax_mixed<PAIR_BS, PAIR_ILP, PAIR_TJ><<<grid, PAIR_BS, 0, s>>>(
+        (const float4 *)a.irec, (const float4 *)a.jrec, a.n_a, a.n_s, a.shape.j_per_split, a.self_pass,
+        (float)a.eps2, wmax);
 }
 
 void launch_grad(cudaStream_t s, bool mixed, const PairArgs &a)

@@ -77,12 +77,11 @@ __device__ __forceinline__ void t_sync(const SubParams &p)
 // ---- block-level building blocks ----------------------------------------------------
 
 template <bool MIXED>
-__device__ void b_pack_pos(const SubParams &p, const int32_t *L, int n, void *rec, bool accurate)
+__device__ void b_pack_pos(const SubParams &p, const int32_t *L, int n, void *rec)
 {
     for (int k = t_id(p); k < n; k += t_n(p)) {
         if (MIXED) {
-            if (accurate) pack_grad_mixed_one(k, L, n, p.x, p.m, p.N, nullptr, (float4 *)rec);
-            else pack_pos_mixed_one(k, L, n, p.x, p.m, p.N, (float4 *)rec);
+            pack_pos_mixed_one(k, L, n, p.x, p.m, p.N, (float4 *)rec);
         } else {
             pack_pos_fp64_one(k, L, n, p.x, p.m, p.N, (double4_32a *)rec);
         }
@@ -176,36 +175,20 @@ __device__ __noinline__ void mt_acc(const SubParams &p, const void *irec, const 
             float H[3] = {0.f, 0.f, 0.f}, L[3] = {0.f, 0.f, 0.f};
             float ax[1] = {0.f}, ay[1] = {0.f}, az[1] = {0.f};
             int c = 0;
-            if (accurate) {
-                GradMixedI<1> I;
-                const float4 q0 = ir[i], q1 = ir[nA + i], q2 = ir[2 * nA + i];
-                I.xh[0] = q0.x; I.yh[0] = q0.y; I.zh[0] = q0.z;
-                I.xm[0] = q1.x; I.ym[0] = q1.y; I.zm[0] = q1.z;
-                I.xl[0] = q2.x; I.yl[0] = q2.y; I.zl[0] = q2.z;
-                I.ahx[0] = I.ahy[0] = I.ahz[0] = I.alx[0] = I.aly[0] = I.alz[0] = 0.f;
-                for (int q = 0; q < nq; ++q) {
-                    const MtSrc s = mt_src(q, T, l, nB, i, self);
-                    acc3_mixed_j<1, true>(jr[s.j], jr[nB + s.j], jr[2 * nB + s.j], I, eps2, s.jpos, ipos, ax, ay, az,
-                                          wm);
-                    if (++c == 16) {
-                        fold2(H[0], L[0], ax[0]); fold2(H[1], L[1], ay[0]); fold2(H[2], L[2], az[0]);
-                        ax[0] = ay[0] = az[0] = 0.f;
-                        c = 0;
-                    }
-                }
-            } else {
-                AccMixedI<1> I;
-                const float4 q0 = ir[i], q1 = ir[nA + i];
-                I.xh[0] = q0.x; I.yh[0] = q0.y; I.zh[0] = q0.z;
-                I.xl[0] = q1.x; I.yl[0] = q1.y; I.zl[0] = q1.z;
-                for (int q = 0; q < nq; ++q) {
-                    const MtSrc s = mt_src(q, T, l, nB, i, self);
+            AccMixedI<1> I;
+            const float4 q0 = ir[i], q1 = ir[nA + i];
+            I.xh[0] = q0.x; I.yh[0] = q0.y; I.zh[0] = q0.z;
+            I.xl[0] = q1.x; I.yl[0] = q1.y; I.zl[0] = q1.z;
+            for (int q = 0; q < nq; ++q) {
+                const MtSrc s = mt_src(q, T, l, nB, i, self);
+                if (accurate)
+                    acc_mixed_j<1, true, true, true>(jr[s.j], jr[nB + s.j], I, eps2, s.jpos, ipos, ax, ay, az, wm);
+                else
                     acc_mixed_j<1, true, false>(jr[s.j], jr[nB + s.j], I, eps2, s.jpos, ipos, ax, ay, az, wm);
-                    if (++c == 16) {
-                        fold2(H[0], L[0], ax[0]); fold2(H[1], L[1], ay[0]); fold2(H[2], L[2], az[0]);
-                        ax[0] = ay[0] = az[0] = 0.f;
-                        c = 0;
-                    }
+                if (++c == 16) {
+                    fold2(H[0], L[0], ax[0]); fold2(H[1], L[1], ay[0]); fold2(H[2], L[2], az[0]);
+                    ax[0] = ay[0] = az[0] = 0.f;
+                    c = 0;
                 }
             }
             fold2(H[0], L[0], ax[0]); fold2(H[1], L[1], ay[0]); fold2(H[2], L[2], az[0]);
@@ -257,10 +240,9 @@ __device__ __noinline__ void mt_grad(const SubParams &p, const void *irec, const
             I.xm[0] = q1.x; I.ym[0] = q1.y; I.zm[0] = q1.z; I.ahx[0] = q1.w;
             I.xl[0] = q2.x; I.yl[0] = q2.y; I.zl[0] = q2.z; I.ahy[0] = q2.w;
             I.ahz[0] = q3.x; I.alx[0] = q3.y; I.aly[0] = q3.z; I.alz[0] = q3.w;
-            const float thr[1] = {wmax ? 0.25f * wmax[i] : INFINITY};
+            const float thr[1] = {wmax ? SLOT_FRACTION * wmax[i] : INFINITY};
             BigSlots<1> big;
-            big.n[0] = 0;
-            big.j0[0] = big.j1[0] = big.j2[0] = big.j3[0] = 0;
+            init_big(big, 0);
             float H[3] = {0.f, 0.f, 0.f}, L[3] = {0.f, 0.f, 0.f};
             float gx[1] = {0.f}, gy[1] = {0.f}, gz[1] = {0.f};
             int cnt = 0;
@@ -276,9 +258,12 @@ __device__ __noinline__ void mt_grad(const SubParams &p, const void *irec, const
             }
             fold2(H[0], L[0], gx[0]); fold2(H[1], L[1], gy[0]); fold2(H[2], L[2], gz[0]);
             double bx = 0.0, by = 0.0, bz = 0.0;
-            for (int t = 0; t < big.n[0]; ++t) {
-                const int j = (t == 0) ? big.j0[0] : (t == 1) ? big.j1[0] : (t == 2) ? big.j2[0] : big.j3[0];
-                grad_term_fp64<1>(jr[j], jr[nB + j], jr[2 * nB + j], jr[3 * nB + j], I, 0, p.eps2, bx, by, bz);
+#pragma unroll
+            for (int t = 0; t < GRAD_SLOTS; ++t) {
+                if (t < big.n[0]) {
+                    const int j = big.j[t][0];
+                    grad_term_df<1>(jr[j], jr[nB + j], jr[2 * nB + j], jr[3 * nB + j], I, 0, p.eps2, bx, by, bz);
+                }
             }
             r[0] = ((double)H[0] + (double)L[0]) + bx;
             r[1] = ((double)H[1] + (double)L[1]) + by;
@@ -376,8 +361,8 @@ __device__ __noinline__ void b_acc(const SubParams &p, const SubWork &w, const i
         return;
     }
     accurate = accurate && MIXED;
-    b_pack_pos<MIXED>(p, A, nA, w.recA, accurate);
-    if (!self) b_pack_pos<MIXED>(p, B, nB, w.recB, accurate);
+    b_pack_pos<MIXED>(p, A, nA, w.recA);
+    if (!self) b_pack_pos<MIXED>(p, B, nB, w.recB);
     t_sync(p);
     const int sp = self ? 1 : 0;
     if (p.csize > 1 || nA <= MT_MAX) {
@@ -387,7 +372,7 @@ __device__ __noinline__ void b_acc(const SubParams &p, const SubWork &w, const i
         for (int ib = 0; ib < nA; ib += SIB) {
             double res[SILP][3];
             float wr[SILP];
-            if (accurate) acc3_mixed_body<SB, SILP, STJ>(ir, jr, nA, nB, ib, 0, nB, sp, (float)p.eps2, res, wr);
+            if (accurate) acc_mixed_body<SB, SILP, STJ, true, true>(ir, jr, nA, nB, ib, 0, nB, sp, (float)p.eps2, res, wr);
             else acc_mixed_body<SB, SILP, STJ, false>(ir, jr, nA, nB, ib, 0, nB, sp, (float)p.eps2, res, wr);
 #pragma unroll
             for (int k = 0; k < SILP; ++k) {
@@ -701,8 +686,8 @@ __device__ __forceinline__ float wsh(float v, int j) { return __shfl_sync(0xffff
 __device__ __forceinline__ double wshd(double v, int j) { return __shfl_sync(0xffffffffu, v, j); }
 
 // Newtonian pass: every lane sums over the sources j of the uniform mask U with bit j set in
-// its own mask mysrc (j != lane).  accurate: the variant that feeds a gradient (three-way
-// split separations, Newton-refined rsqrt), also returning max_j m_j / r^3.
+// its own mask mysrc (j != lane).  accurate: the variant that feeds a gradient (Newton-refined
+// rsqrt, short folds), also returning max_j m_j / r^3.
 template <bool MIXED>
 __device__ __noinline__ void w_acc(const SubParams &p, const WLane &L, unsigned U, unsigned mysrc, bool accurate,
                                    double (&a)[3], float &wmax)
@@ -716,49 +701,26 @@ __device__ __noinline__ void w_acc(const SubParams &p, const WLane &L, unsigned 
         float H[3] = {0.f, 0.f, 0.f}, Lo[3] = {0.f, 0.f, 0.f};
         float ax[1] = {0.f}, ay[1] = {0.f}, az[1] = {0.f};
         int c = 0;
-        if (!accurate) {
-            AccMixedI<1> I;
-            float hx = (float)L.x[0], hy = (float)L.x[1], hz = (float)L.x[2];
-            I.xh[0] = hx; I.yh[0] = hy; I.zh[0] = hz;
-            I.xl[0] = (float)(L.x[0] - (double)hx);
-            I.yl[0] = (float)(L.x[1] - (double)hy);
-            I.zl[0] = (float)(L.x[2] - (double)hz);
-            const float mf = (float)L.m;
-            unsigned M = U;
-            while (M) {
-                const int j = __ffs(M) - 1;
-                M &= M - 1;
-                float4 J0 = make_float4(wsh(hx, j), wsh(hy, j), wsh(hz, j), wsh(mf, j));
-                const float4 J1 = make_float4(wsh(I.xl[0], j), wsh(I.yl[0], j), wsh(I.zl[0], j), 0.f);
-                if (!((mysrc >> j) & 1u)) J0.w = 0.f;
-                acc_mixed_j<1, true, false>(J0, J1, I, eps2, j, ipos, ax, ay, az, wm);
-                if (++c == 16) {
-                    fold2(H[0], Lo[0], ax[0]); fold2(H[1], Lo[1], ay[0]); fold2(H[2], Lo[2], az[0]);
-                    ax[0] = ay[0] = az[0] = 0.f;
-                    c = 0;
-                }
-            }
-        } else {
-            GradMixedI<1> I;
-            split3(L.x[0], I.xh[0], I.xm[0], I.xl[0]);
-            split3(L.x[1], I.yh[0], I.ym[0], I.yl[0]);
-            split3(L.x[2], I.zh[0], I.zm[0], I.zl[0]);
-            I.ahx[0] = I.ahy[0] = I.ahz[0] = I.alx[0] = I.aly[0] = I.alz[0] = 0.f;
-            const float mf = (float)L.m;
-            unsigned M = U;
-            while (M) {
-                const int j = __ffs(M) - 1;
-                M &= M - 1;
-                float4 J0 = make_float4(wsh(I.xh[0], j), wsh(I.yh[0], j), wsh(I.zh[0], j), wsh(mf, j));
-                const float4 J1 = make_float4(wsh(I.xm[0], j), wsh(I.ym[0], j), wsh(I.zm[0], j), 0.f);
-                const float4 J2 = make_float4(wsh(I.xl[0], j), wsh(I.yl[0], j), wsh(I.zl[0], j), 0.f);
-                if (!((mysrc >> j) & 1u)) J0.w = 0.f;
-                acc3_mixed_j<1, true>(J0, J1, J2, I, eps2, j, ipos, ax, ay, az, wm);
-                if (++c == 16) {
-                    fold2(H[0], Lo[0], ax[0]); fold2(H[1], Lo[1], ay[0]); fold2(H[2], Lo[2], az[0]);
-                    ax[0] = ay[0] = az[0] = 0.f;
-                    c = 0;
-                }
+        AccMixedI<1> I;
+        float hx = (float)L.x[0], hy = (float)L.x[1], hz = (float)L.x[2];
+        I.xh[0] = hx; I.yh[0] = hy; I.zh[0] = hz;
+        I.xl[0] = (float)(L.x[0] - (double)hx);
+        I.yl[0] = (float)(L.x[1] - (double)hy);
+        I.zl[0] = (float)(L.x[2] - (double)hz);
+        const float mf = (float)L.m;
+        unsigned M = U;
+        while (M) {
+            const int j = __ffs(M) - 1;
+            M &= M - 1;
+            float4 J0 = make_float4(wsh(hx, j), wsh(hy, j), wsh(hz, j), wsh(mf, j));
+            const float4 J1 = make_float4(wsh(I.xl[0], j), wsh(I.yl[0], j), wsh(I.zl[0], j), 0.f);
+            if (!((mysrc >> j) & 1u)) J0.w = 0.f;
+            if (accurate) acc_mixed_j<1, true, true, true>(J0, J1, I, eps2, j, ipos, ax, ay, az, wm);
+            else acc_mixed_j<1, true, false>(J0, J1, I, eps2, j, ipos, ax, ay, az, wm);
+            if (++c == 16) {
+                fold2(H[0], Lo[0], ax[0]); fold2(H[1], Lo[1], ay[0]); fold2(H[2], Lo[2], az[0]);
+                ax[0] = ay[0] = az[0] = 0.f;
+                c = 0;
             }
         }
         fold2(H[0], Lo[0], ax[0]); fold2(H[1], Lo[1], ay[0]); fold2(H[2], Lo[2], az[0]);
@@ -802,8 +764,7 @@ __device__ __noinline__ void w_grad(const SubParams &p, const WLane &L, unsigned
         const float mf = (float)L.m;
         const float thrs[1] = {thr};
         BigSlots<1> big;
-        big.n[0] = 0;
-        big.j0[0] = big.j1[0] = big.j2[0] = big.j3[0] = lane;
+        init_big(big, lane);
         float H[3] = {0.f, 0.f, 0.f}, Lo[3] = {0.f, 0.f, 0.f};
         float gx[1] = {0.f}, gy[1] = {0.f}, gz[1] = {0.f};
         int c = 0;
@@ -824,15 +785,19 @@ __device__ __noinline__ void w_grad(const SubParams &p, const WLane &L, unsigned
             }
         }
         fold2(H[0], Lo[0], gx[0]); fold2(H[1], Lo[1], gy[0]); fold2(H[2], Lo[2], gz[0]);
-        // deferred FP64 terms: every lane fetches the records of its own slot s
+        // deferred double-float terms: every lane fetches the records of its own slot s (the
+        // loop runs to the warp's largest slot count, the shuffles need every lane)
         double bx = 0.0, by = 0.0, bz = 0.0;
+        const int nbig = __reduce_max_sync(0xffffffffu, big.n[0]);
+#pragma unroll
         for (int s = 0; s < GRAD_SLOTS; ++s) {
-            const int j = (s == 0) ? big.j0[0] : (s == 1) ? big.j1[0] : (s == 2) ? big.j2[0] : big.j3[0];
+            if (s >= nbig) break;
+            const int j = big.j[s][0];
             const float4 Q0 = make_float4(wsh(I.xh[0], j), wsh(I.yh[0], j), wsh(I.zh[0], j), wsh(mf, j));
             const float4 Q1 = make_float4(wsh(I.xm[0], j), wsh(I.ym[0], j), wsh(I.zm[0], j), wsh(I.ahx[0], j));
             const float4 Q2 = make_float4(wsh(I.xl[0], j), wsh(I.yl[0], j), wsh(I.zl[0], j), wsh(I.ahy[0], j));
             const float4 Q3 = make_float4(wsh(I.ahz[0], j), wsh(I.alx[0], j), wsh(I.aly[0], j), wsh(I.alz[0], j));
-            if (s < big.n[0]) grad_term_fp64<1>(Q0, Q1, Q2, Q3, I, 0, p.eps2, bx, by, bz);
+            if (s < big.n[0]) grad_term_df<1>(Q0, Q1, Q2, Q3, I, 0, p.eps2, bx, by, bz);
         }
         res[0] = ((double)H[0] + (double)Lo[0]) + bx;
         res[1] = ((double)H[1] + (double)Lo[1]) + by;
@@ -938,7 +903,7 @@ __device__ void w_fsi(const SubParams &p, WLane &L, unsigned S, double dt, Count
     w_kick(L, in, a, dt / 6.0);
     w_drift(L, in, 0.5 * dt);
     w_acc<MIXED>(p, L, S, src, true, a, wm);
-    w_grad<MIXED>(p, L, S, src, a, MIXED ? 0.25f * wm : INFINITY, g);
+    w_grad<MIXED>(p, L, S, src, a, MIXED ? SLOT_FRACTION * wm : INFINITY, g);
     const double c = dt * dt / 48.0;
     for (int q = 0; q < 3; ++q) at[q] = a[q] + c * g[q];
     w_kick(L, in, at, 2.0 * dt / 3.0);
@@ -967,7 +932,7 @@ __device__ void w_kick_sf(const SubParams &p, WLane &L, unsigned S, unsigned F, 
     w_acc<MIXED>(p, L, U, src, gradient, a, wm);
     if (gradient) {
         double g[3];
-        w_grad<MIXED>(p, L, U, src, a, MIXED ? 0.25f * wm : INFINITY, g);
+        w_grad<MIXED>(p, L, U, src, a, MIXED ? SLOT_FRACTION * wm : INFINITY, g);
         const double c = tau * tau / 48.0;
         for (int q = 0; q < 3; ++q) a[q] = a[q] + c * g[q];
     }

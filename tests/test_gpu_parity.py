@@ -112,14 +112,38 @@ def test_accel_gradient_cross_pass(precision):
     f.close()
 
 
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_accel_gradient_mixed_across_seeds(seed):
+    """The mixed bar on four equal-mass Plummer spheres of N = 8192 (a full-set pass and a
+    cross pass with |A| = N/4), so that the 99.9th percentile does not rest on one lucky
+    draw.  The relative error of g_i is conditioned by sum_j |term_ij| / |g_i|, which is large
+    where the gradient nearly vanishes; the dominant terms in double-float keep that tail
+    near 5e-7 here."""
+    n = 8192
+    m, x, v = ics.plummer(n, seed)
+    f = F(m, x, v, precision="mixed")
+    A = np.arange(n, dtype=np.int32)
+    out = f.accel_gradient(None, None, eps_grad=0.05)
+    a_ref, g_ref = oracle_g(m, x, A, A)
+    ea, eg = rel(cpu(out["acc"]), a_ref), rel(cpu(out["grad"]), g_ref)
+    assert p999(ea) < 1e-6 and p999(eg) < 1e-6, (p999(ea), p999(eg))
+    perm = np.random.default_rng(3).permutation(n).astype(np.int32)
+    S, Fl = np.sort(perm[: n // 4]), perm[n // 4:]
+    out = f.accel_gradient(S, Fl, eps_grad=0.05)
+    a_ref, g_ref = oracle_g(m, x, S, Fl)
+    ea, eg = rel(cpu(out["acc"]), a_ref), rel(cpu(out["grad"]), g_ref)
+    assert p999(ea) < 1e-6 and p999(eg) < 1e-6, (p999(ea), p999(eg))
+    f.close()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("cross", [False, True])
 def test_accel_gradient_hard_binaries(precision, cross):
     """Plummer N = 8192 with Kroupa masses and 5% hard binaries (a = 1e-5..1e-3, thermal e):
     members' accelerations exceed the median by up to ~1e7 and the terms of the two partners
     cancel in every other particle's gradient, which amplifies FP32 rounding by the ratio of
-    distances; the mixed pass sums these hot sources in FP64 and must still meet 1e-6 at the
-    99.9th percentile.  cross: disjoint lists that split binaries between them."""
+    distances; the mixed pass sums these hot sources in double-float and must still meet 1e-6
+    at the 99.9th percentile.  cross: disjoint lists that split binaries between them."""
     n = 8192
     m, x, v = ics.plummer_kroupa_binaries(n, 17)
     f = F(m, x, v, precision=precision)

@@ -258,8 +258,6 @@ def run_frost(args):
     # ---- timed hierarchical steps (mixed) ----
     f = new("mixed")
     tuned = f.autotune()  # launch shapes of the pair kernels, outside the timed region
-    # (for launch-list captures: the kernels launched so far, to skip with ncu -s)
-    print(f"autotune kernel launches: {f.stats()['kernel_launches']}", file=sys.stderr)
     for _ in range(args.warmup):
         f.step(args.dt, 1)
     torch.cuda.synchronize()

@@ -275,10 +275,12 @@ __device__ __forceinline__ void acc_defer_j(const float4 J0, const float4 J1, co
     }
 }
 
-// max_j m_j / r^3 (the scale of the dominant terms), FP32 on the position records
+// The scale of the dominant terms, max_j m_j / r^3 = (min_j r^2 m_j^(-2/3))^(-3/2): J1.w holds
+// m_j^(-2/3) (set when the tile is staged), so a pair costs the separation, r^2, one product
+// and a minimum (no rsqrt); qm[k] is the running minimum of r^2 m_j^(-2/3)
 template <int ILP, bool MASK>
 __device__ __forceinline__ void wmax_mixed_j(const float4 J0, const float4 J1, const AccMixedI<ILP> &I,
-                                             float eps2, int jpos, const int (&ipos)[ILP], float (&wm)[ILP])
+                                             float eps2, int jpos, const int (&ipos)[ILP], float (&qm)[ILP])
 {
 #pragma unroll
     for (int k = 0; k < ILP; ++k) {
@@ -286,10 +288,9 @@ __device__ __forceinline__ void wmax_mixed_j(const float4 J0, const float4 J1, c
         const float dy = (J0.y - I.yh[k]) + (J1.y - I.yl[k]);
         const float dz = (J0.z - I.zh[k]) + (J1.z - I.zl[k]);
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-        const float ri = rsqrtf(r2);
-        float w = J0.w * ri * (ri * ri);
-        if (MASK) w = (jpos == ipos[k]) ? 0.f : w;
-        wm[k] = fmaxf(wm[k], w);
+        float q = r2 * J1.w;
+        if (MASK) q = (jpos == ipos[k]) ? INFINITY : q;
+        qm[k] = fminf(qm[k], q);
     }
 }
 
@@ -711,14 +712,18 @@ __device__ __forceinline__ void wmax_mixed_body(const float4 *__restrict__ irec,
         }
         I.xh[k] = a.x; I.yh[k] = a.y; I.zh[k] = a.z;
         I.xl[k] = b.x; I.yl[k] = b.y; I.zl[k] = b.z;
-        wres[k] = 0.f;
+        wres[k] = INFINITY;  // the running minimum of r^2 m_j^(-2/3) until the end
     }
     for (int j0 = jb; j0 < je; j0 += TJ) {
         const int cnt = min(TJ, je - j0);
         __syncthreads();
         for (int t = tid; t < cnt; t += BS) {
-            s0[t] = jrec[j0 + t];
-            s1[t] = jrec[n_s + j0 + t];
+            const float4 a = jrec[j0 + t];
+            float4 b = jrec[n_s + j0 + t];
+            // m^(-2/3), infinite for a massless source (which then never sets the minimum)
+            b.w = (a.w > 0.f) ? exp2f(-0.6666667f * log2f(a.w)) : INFINITY;
+            s0[t] = a;
+            s1[t] = b;
         }
         __syncthreads();
         const bool diag = self_pass && (j0 < ibase + BS * ILP) && (ibase < j0 + cnt);
@@ -732,6 +737,12 @@ __device__ __forceinline__ void wmax_mixed_body(const float4 *__restrict__ irec,
         } else {
             for (; jj < cnt; ++jj) wmax_mixed_j<ILP, true>(s0[jj], s1[jj], I, eps2, j0 + jj, ipos, wres);
         }
+    }
+    // max_j m_j / r^3 = q_min^(-3/2) (0 without sources, infinite for a coincident pair)
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+        const float y = rsqrtf(wres[k]);
+        wres[k] = y * y * y;
     }
 }
 

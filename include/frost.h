@@ -144,6 +144,12 @@ frost_status frost_get_state(frost_ctx *ctx, double *x, double *v, double *t);
  * each may be NULL (if acc_tilde and grad are both NULL only the Newtonian pass runs).
  * With softening eps_P, r^2 -> r^2 + eps_P^2 everywhere in both sums.  Pairs at zero
  * separation give FROST_ECOINCIDENT when unsoftened.  Synchronises.
+ * Accuracy: FP64 mode, 1e-12 relative.  Mixed mode: the Newtonian pass runs a prepass for
+ * max_j m_j / r^3 and sums the terms above 1/16 of it (up to 8 per particle) in
+ * double-float, and so does the gradient pass; the rest are FP32 terms in compensated sums.
+ * That gives a_i to about 1e-7 and g_i to below 1e-6 at the 99.9th percentile of a set of a
+ * few thousand particles or more.  The relative error of one g_i grows as
+ * sum_j |term_ij| / |g_i| where the gradient nearly vanishes.
  */
 frost_status frost_accel_gradient(frost_ctx *ctx, const int32_t *active, int64_t n_active,
                                   const int32_t *source, int64_t n_source, double eps_grad,

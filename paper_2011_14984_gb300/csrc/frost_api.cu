@@ -267,7 +267,7 @@ int badbit(const frost_ctx *c) { return c->eps2 == 0.0 ? ERR_COINCIDENT : ERR_NO
 // ([3][nA]) and, if given, out_aos ([nA][3]).  With wmax (mixed mode), also the weight
 // max_j m_j / r^3 of each particle's dominant term, which the following gradient pass uses.
 // With hist (mixed mode, with wmax): the |a| histogram of the pass is added to hist (zeroed by
-// the caller) for the hot-source classification of refine_hot.  kick: the kick of A by the
+// the caller) for the hot-source classification of mark_hot.  kick: the kick of A by the
 // result, fused into the finalisation.  irec / jrec: records already packed by the caller
 // (NULL: packed here into recA / recB).
 void pass_acc(frost_ctx *c, const int32_t *A, int nA, const int32_t *B, int nB, bool self,

@@ -369,7 +369,7 @@ __device__ __forceinline__ void grad_mixed_j(const float4 J0, const float4 J1, c
             self = (jpos == ipos[k]);
             w = self ? 0.f : w;
         }
-        // a dominant term goes to a deferred FP64 slot and stays out of the FP32 sum
+        // a dominant term goes to a deferred double-float slot and stays out of the FP32 sum
         const bool isbig = (w > thr[k]) && big.room(k);
         if (isbig) big.push(k, jglob);
         const float wf = isbig ? 0.f : w;

@@ -14,8 +14,8 @@
 // FP32, and the per-tile FP32 partial sums are folded into a TwoSum-compensated (hi, lo)
 // FP32 accumulator, converted to FP64 once per block.  The gradient needs accurate
 // accelerations (a_j - a_i amplifies their rounding noise): the Newtonian pass that precedes
-// it uses a three-way split of the positions and a Newton-refined rsqrt, and the gradient
-// sums each particle's few dominant terms in FP64.
+// it takes a Newton-refined rsqrt and sums each particle's few dominant terms (above 1/16 of
+// max_j m_j / r^3, from a prepass) in double-float, and so does the gradient.
 //
 // The i = j term is excluded by list position: only tiles that overlap the block's own
 // i-range (same-list passes) run the masked loop.  Two distinct particles at zero

@@ -741,7 +741,7 @@ __device__ __noinline__ void w_acc(const SubParams &p, const WLane &L, unsigned 
 }
 
 // Gradient pass: lane sums over j in U with bit j of mysrc, using its own acceleration ai
-// and the sources' accelerations (each lane's ai); dominant terms (w > thr) in FP64.
+// and the sources' accelerations (each lane's ai); dominant terms (w > thr) in double-float.
 template <bool MIXED>
 __device__ __noinline__ void w_grad(const SubParams &p, const WLane &L, unsigned U, unsigned mysrc,
                                     const double (&ai)[3], float thr, double (&g)[3])

@@ -1064,8 +1064,11 @@ __device__ __noinline__ int warp_hhs(const SubParams &p, const int32_t *Sg, int 
 // Batch mode (offsets != NULL): team t takes cluster c = (cl_index ? cl_index[t] : t), the
 // particles [offsets[c], offsets[c+1]) in order, and the workspace region of those particles.
 // Every block of a team keeps its own copy of the frame stack and takes the same decisions.
-template <bool MIXED, int SYM>
-__global__ void __launch_bounds__(SB) k_hhs_subtree(SubParams p0, SubWork w0, const int32_t *__restrict__ P,
+// MINB: blocks per SM the registers must allow.  A single set runs one team, which may use
+// up to 255 registers a thread (the mixed kernel takes ~218, without spills); a batch of
+// many clusters needs two blocks per SM (128 registers) to run its teams in one wave.
+template <bool MIXED, int SYM, int MINB = 1>
+__global__ void __launch_bounds__(SB, MINB) k_hhs_subtree(SubParams p0, SubWork w0, const int32_t *__restrict__ P,
                                                     int n_single, const int64_t *__restrict__ offsets,
                                                     const int32_t *__restrict__ cl_index, double tau0,
                                                     int depth0, int n_steps)
@@ -1268,13 +1271,18 @@ cudaError_t launch_subtree(cudaStream_t s, bool mixed, int sym, const SubtreeArg
 #define FROST_SUBTREE_CASE(MIX, SYMV)                                                             \
     e = cudaLaunchKernelEx(&cfg, k_hhs_subtree<MIX, SYMV>, p, w, a.P, a.n, a.offsets, a.cl_index, a.tau0, \
                            a.depth0, a.n_steps)
+#define FROST_SUBTREE_MIXED_CASE(SYMV)                                                                       \
+    e = a.offsets ? cudaLaunchKernelEx(&cfg, k_hhs_subtree<true, SYMV, 2>, p, w, a.P, a.n, a.offsets,        \
+                                       a.cl_index, a.tau0, a.depth0, a.n_steps)                              \
+                  : cudaLaunchKernelEx(&cfg, k_hhs_subtree<true, SYMV, 1>, p, w, a.P, a.n, a.offsets,        \
+                                       a.cl_index, a.tau0, a.depth0, a.n_steps)
     switch ((mixed ? 8 : 0) + sym) {
-    case 8 + 0: FROST_SUBTREE_CASE(true, 0); break;
-    case 8 + 1: FROST_SUBTREE_CASE(true, 1); break;
-    case 8 + 4: FROST_SUBTREE_CASE(true, 4); break;
-    case 8 + 5: FROST_SUBTREE_CASE(true, 5); break;
-    case 8 + 6: FROST_SUBTREE_CASE(true, 6); break;
-    case 8 + 2: FROST_SUBTREE_CASE(true, 2); break;
+    case 8 + 0: FROST_SUBTREE_MIXED_CASE(0); break;
+    case 8 + 1: FROST_SUBTREE_MIXED_CASE(1); break;
+    case 8 + 4: FROST_SUBTREE_MIXED_CASE(4); break;
+    case 8 + 5: FROST_SUBTREE_MIXED_CASE(5); break;
+    case 8 + 6: FROST_SUBTREE_MIXED_CASE(6); break;
+    case 8 + 2: FROST_SUBTREE_MIXED_CASE(2); break;
     case 0: FROST_SUBTREE_CASE(false, 0); break;
     case 1: FROST_SUBTREE_CASE(false, 1); break;
     case 4: FROST_SUBTREE_CASE(false, 4); break;
@@ -1283,6 +1291,7 @@ cudaError_t launch_subtree(cudaStream_t s, bool mixed, int sym, const SubtreeArg
     default: FROST_SUBTREE_CASE(false, 2); break;
     }
 #undef FROST_SUBTREE_CASE
+#undef FROST_SUBTREE_MIXED_CASE
     return e;
 }
 

@@ -689,15 +689,20 @@ __device__ __forceinline__ void acc_mixed_body(const float4 *__restrict__ irec,
 }
 
 // max_j m_j / r^3 over [jb, je) for the active records of the block (the prepass of the
-// deferred Newtonian pass)
+// deferred Newtonian pass).  With two particles a thread (ILP = 2) the off-diagonal tiles run
+// on packed f32x2 arithmetic: the thread's two particles are the two lanes, and the sources
+// are staged duplicated ({x, x}, ...) so that every operand is a register pair as loaded.
+// The operations and their order are those of wmax_mixed_j, so the result is bit-identical.
 template <int BS, int ILP, int TJ>
 __device__ __forceinline__ void wmax_mixed_body(const float4 *__restrict__ irec,
                                                 const float4 *__restrict__ jrec, int n_a, int n_s,
                                                 int ibase, int jb, int je, int self_pass, float eps2,
                                                 float (&wres)[ILP])
 {
-    __shared__ float4 s0[TJ];
-    __shared__ float4 s1[TJ];
+    // per source: {hx, hx, hy, hy}, {hz, hz, lx, lx}, {ly, ly, lz, lz}, {mq, mq} with
+    // mq = m^(-2/3) (infinite for a massless source, which then never sets the minimum)
+    __shared__ float4 sA[TJ], sB[TJ], sC[TJ];
+    __shared__ float2 sM[TJ];
     const int tid = threadIdx.x;
     AccMixedI<ILP> I;
     int ipos[ILP];
@@ -719,23 +724,46 @@ __device__ __forceinline__ void wmax_mixed_body(const float4 *__restrict__ irec,
         __syncthreads();
         for (int t = tid; t < cnt; t += BS) {
             const float4 a = jrec[j0 + t];
-            float4 b = jrec[n_s + j0 + t];
-            // m^(-2/3), infinite for a massless source (which then never sets the minimum)
-            b.w = (a.w > 0.f) ? exp2f(-0.6666667f * log2f(a.w)) : INFINITY;
-            s0[t] = a;
-            s1[t] = b;
+            const float4 b = jrec[n_s + j0 + t];
+            const float mq = (a.w > 0.f) ? exp2f(-0.6666667f * log2f(a.w)) : INFINITY;
+            sA[t] = make_float4(a.x, a.x, a.y, a.y);
+            sB[t] = make_float4(a.z, a.z, b.x, b.x);
+            sC[t] = make_float4(b.y, b.y, b.z, b.z);
+            sM[t] = make_float2(mq, mq);
         }
         __syncthreads();
         const bool diag = self_pass && (j0 < ibase + BS * ILP) && (ibase < j0 + cnt);
-        int jj = 0;
-        if (!diag) {
-            for (; jj + 8 <= cnt; jj += 8) {
-#pragma unroll
-                for (int u = 0; u < 8; ++u) wmax_mixed_j<ILP, false>(s0[jj + u], s1[jj + u], I, eps2, 0, ipos, wres);
+        if constexpr (ILP == 2) {
+            if (!diag) {
+                const float2 nxh = make_float2(-I.xh[0], -I.xh[1]), nyh = make_float2(-I.yh[0], -I.yh[1]);
+                const float2 nzh = make_float2(-I.zh[0], -I.zh[1]), nxl = make_float2(-I.xl[0], -I.xl[1]);
+                const float2 nyl = make_float2(-I.yl[0], -I.yl[1]), nzl = make_float2(-I.zl[0], -I.zl[1]);
+                const float2 e2 = make_float2(eps2, eps2);
+                float2 qm = make_float2(wres[0], wres[1]);
+#pragma unroll 4
+                for (int jj = 0; jj < cnt; ++jj) {
+                    const float4 A = sA[jj], B = sB[jj], C = sC[jj];
+                    const float2 M = sM[jj];
+                    const float2 dx = __fadd2_rn(__fadd2_rn(make_float2(A.x, A.y), nxh), __fadd2_rn(make_float2(B.z, B.w), nxl));
+                    const float2 dy = __fadd2_rn(__fadd2_rn(make_float2(A.z, A.w), nyh), __fadd2_rn(make_float2(C.x, C.y), nyl));
+                    const float2 dz = __fadd2_rn(__fadd2_rn(make_float2(B.x, B.y), nzh), __fadd2_rn(make_float2(C.z, C.w), nzl));
+                    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+                    const float2 q = __fmul2_rn(r2, M);
+                    qm.x = fminf(qm.x, q.x);
+                    qm.y = fminf(qm.y, q.y);
+                }
+                wres[0] = qm.x;
+                wres[1] = qm.y;
+                continue;
             }
-            for (; jj < cnt; ++jj) wmax_mixed_j<ILP, false>(s0[jj], s1[jj], I, eps2, 0, ipos, wres);
-        } else {
-            for (; jj < cnt; ++jj) wmax_mixed_j<ILP, true>(s0[jj], s1[jj], I, eps2, j0 + jj, ipos, wres);
+        }
+        // scalar loop (the diagonal tiles, or ILP != 2), from the duplicated layout
+        for (int jj = 0; jj < cnt; ++jj) {
+            const float4 A = sA[jj], B = sB[jj], C = sC[jj];
+            const float4 J0 = make_float4(A.x, A.z, B.x, 0.f);
+            const float4 J1 = make_float4(B.z, C.x, C.z, sM[jj].x);
+            if (diag) wmax_mixed_j<ILP, true>(J0, J1, I, eps2, j0 + jj, ipos, wres);
+            else wmax_mixed_j<ILP, false>(J0, J1, I, eps2, 0, ipos, wres);
         }
     }
     // max_j m_j / r^3 = q_min^(-3/2) (0 without sources, infinite for a coincident pair)

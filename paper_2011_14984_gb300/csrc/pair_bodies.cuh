@@ -564,6 +564,49 @@ __device__ __forceinline__ void tstep_fp64_j(const double4_32a J, const double4_
 // solver calls it for every i-block of a set against the whole source list.
 // ======================================================================================
 
+// The thread's two particles as the two lanes of packed f32x2 arithmetic (negated positions,
+// so that a separation is two packed adds: x_j + (-x_i))
+struct AccX2I {
+    float2 nxh, nyh, nzh, nxl, nyl, nzl;
+};
+
+// One source (staged duplicated: A = {hx, hx, hy, hy}, B = {hz, hz, lx, lx},
+// C = {ly, ly, lz, lz}, M = {m, m}) against the thread's two particles.  The operations and
+// their order are those of acc_mixed_j (and acc_defer_j when DEFER), lane by lane, so the
+// packed and scalar loops give the same bits.
+template <bool WMAX, bool NEWTON, bool DEFER, class Slots>
+__device__ __forceinline__ void acc_x2_j(const float4 A, const float4 B, const float4 C, const float2 M,
+                                         const AccX2I &P, float2 e2, int jglob, const float (&thr)[2],
+                                         Slots &big, float2 &ax, float2 &ay, float2 &az, float (&wm)[2])
+{
+    const float2 dx = __fadd2_rn(__fadd2_rn(make_float2(A.x, A.y), P.nxh), __fadd2_rn(make_float2(B.z, B.w), P.nxl));
+    const float2 dy = __fadd2_rn(__fadd2_rn(make_float2(A.z, A.w), P.nyh), __fadd2_rn(make_float2(C.x, C.y), P.nyl));
+    const float2 dz = __fadd2_rn(__fadd2_rn(make_float2(B.x, B.y), P.nzh), __fadd2_rn(make_float2(C.z, C.w), P.nzl));
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+    float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    if (NEWTON) {
+        // y <- y (3/2 - r2 y^2 / 2) as fma(y, fma(-(r2/2) y, y, 1/2), y)
+        const float2 nhy = __fmul2_rn(__fmul2_rn(make_float2(-0.5f, -0.5f), r2), ri);
+        ri = __ffma2_rn(ri, __ffma2_rn(nhy, ri, make_float2(0.5f, 0.5f)), ri);
+    }
+    float2 w = __fmul2_rn(__fmul2_rn(M, ri), __fmul2_rn(ri, ri));
+    if (WMAX) {
+        wm[0] = fmaxf(wm[0], w.x);
+        wm[1] = fmaxf(wm[1], w.y);
+    }
+    if (DEFER) {
+        const bool b0 = (w.x > thr[0]) && big.room(0);
+        if (b0) big.push(0, jglob);
+        const bool b1 = (w.y > thr[1]) && big.room(1);
+        if (b1) big.push(1, jglob);
+        w.x = b0 ? 0.f : w.x;
+        w.y = b1 ? 0.f : w.y;
+    }
+    ax = __ffma2_rn(w, dx, ax);
+    ay = __ffma2_rn(w, dy, ay);
+    az = __ffma2_rn(w, dz, az);
+}
+
 // Newtonian pass, mixed precision (float-float separations, MUFU rsqrt, folds every 64)
 // NEWTON (the pass that feeds a gradient): Newton-refined rsqrt and folds every 16 pairs.
 // DEFER (with NEWTON): the terms above SLOT_FRACTION x wmax[i] (wmax from a prepass at the
@@ -579,8 +622,12 @@ __device__ __forceinline__ void acc_mixed_body(const float4 *__restrict__ irec,
                                                const double *__restrict__ mstore = nullptr)
 {
     static_assert(!DEFER || NEWTON, "the deferred variant is the accurate one");
-    __shared__ float4 s0[TJ];
-    __shared__ float4 s1[TJ];
+    // ILP == 2: sources staged duplicated for the packed loop; otherwise as {hi, m}, {lo, 0}
+    constexpr bool X2 = (ILP == 2);
+    __shared__ float4 s0[X2 ? 1 : TJ];
+    __shared__ float4 s1[X2 ? 1 : TJ];
+    __shared__ float4 sA[X2 ? TJ : 1], sB[X2 ? TJ : 1], sC[X2 ? TJ : 1];
+    __shared__ float2 sM[X2 ? TJ : 1];
     const int tid = threadIdx.x;
     AccMixedI<ILP> I;
     int ipos[ILP];
@@ -611,6 +658,71 @@ __device__ __forceinline__ void acc_mixed_body(const float4 *__restrict__ irec,
 #pragma unroll
     for (int k = 0; k < ILP; ++k) hx[k] = hy[k] = hz[k] = lx[k] = ly[k] = lz[k] = wm[k] = 0.f;
 
+    // FP32 partial sums over at most FOLD pairs before each compensated fold
+    constexpr int FOLD = NEWTON ? 16 : 64;
+    if constexpr (X2) {
+        AccX2I P;
+        P.nxh = make_float2(-I.xh[0], -I.xh[1]);
+        P.nyh = make_float2(-I.yh[0], -I.yh[1]);
+        P.nzh = make_float2(-I.zh[0], -I.zh[1]);
+        P.nxl = make_float2(-I.xl[0], -I.xl[1]);
+        P.nyl = make_float2(-I.yl[0], -I.yl[1]);
+        P.nzl = make_float2(-I.zl[0], -I.zl[1]);
+        const float2 e2 = make_float2(eps2, eps2);
+        const float (&thr2)[2] = *reinterpret_cast<const float(*)[2]>(thr);
+        float (&wm2)[2] = *reinterpret_cast<float(*)[2]>(wm);
+        for (int j0 = jb; j0 < je; j0 += TJ) {
+            const int cnt = min(TJ, je - j0);
+            __syncthreads();
+            for (int t = tid; t < cnt; t += BS) {
+                const float4 a = jrec[j0 + t];
+                const float4 b = jrec[n_s + j0 + t];
+                sA[t] = make_float4(a.x, a.x, a.y, a.y);
+                sB[t] = make_float4(a.z, a.z, b.x, b.x);
+                sC[t] = make_float4(b.y, b.y, b.z, b.z);
+                sM[t] = make_float2(a.w, a.w);
+            }
+            __syncthreads();
+            const bool diag = self_pass && (j0 < ibase + BS * ILP) && (ibase < j0 + cnt);
+            for (int c0 = 0; c0 < cnt; c0 += FOLD) {
+                const int c1 = min(cnt, c0 + FOLD);
+                float2 ax2 = make_float2(0.f, 0.f), ay2 = ax2, az2 = ax2;
+                if (!diag) {
+                    int jj = c0;
+                    for (; jj + 8 <= c1; jj += 8) {
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+                            acc_x2_j<WMAX, NEWTON, DEFER>(sA[jj + u], sB[jj + u], sC[jj + u], sM[jj + u], P, e2,
+                                                          j0 + jj + u, thr2, big, ax2, ay2, az2, wm2);
+                    }
+                    for (; jj < c1; ++jj)
+                        acc_x2_j<WMAX, NEWTON, DEFER>(sA[jj], sB[jj], sC[jj], sM[jj], P, e2, j0 + jj, thr2, big, ax2,
+                                                      ay2, az2, wm2);
+                } else {
+                    // the i = j term masked by list position: the scalar bodies
+                    float ax[ILP] = {0.f, 0.f}, ay[ILP] = {0.f, 0.f}, az[ILP] = {0.f, 0.f};
+                    for (int jj = c0; jj < c1; ++jj) {
+                        const float4 A = sA[jj], B = sB[jj], C = sC[jj];
+                        const float4 J0 = make_float4(A.x, A.z, B.x, sM[jj].x);
+                        const float4 J1 = make_float4(B.z, C.x, C.z, 0.f);
+                        if constexpr (DEFER)
+                            acc_defer_j<ILP, true>(J0, J1, I, eps2, j0 + jj, j0 + jj, ipos, thr, big, ax, ay, az);
+                        else
+                            acc_mixed_j<ILP, true, WMAX, NEWTON>(J0, J1, I, eps2, j0 + jj, ipos, ax, ay, az, wm);
+                    }
+                    ax2 = make_float2(ax[0], ax[1]);
+                    ay2 = make_float2(ay[0], ay[1]);
+                    az2 = make_float2(az[0], az[1]);
+                }
+                fold2(hx[0], lx[0], ax2.x);
+                fold2(hy[0], ly[0], ay2.x);
+                fold2(hz[0], lz[0], az2.x);
+                fold2(hx[1], lx[1], ax2.y);
+                fold2(hy[1], ly[1], ay2.y);
+                fold2(hz[1], lz[1], az2.y);
+            }
+        }
+    } else {
     for (int j0 = jb; j0 < je; j0 += TJ) {
         const int cnt = min(TJ, je - j0);
         __syncthreads();
@@ -620,8 +732,6 @@ __device__ __forceinline__ void acc_mixed_body(const float4 *__restrict__ irec,
         }
         __syncthreads();
         const bool diag = self_pass && (j0 < ibase + BS * ILP) && (ibase < j0 + cnt);
-        // FP32 partial sums over at most FOLD pairs before each compensated fold
-        constexpr int FOLD = NEWTON ? 16 : 64;
         for (int c0 = 0; c0 < cnt; c0 += FOLD) {
             const int c1 = min(cnt, c0 + FOLD);
             float ax[ILP], ay[ILP], az[ILP];
@@ -663,6 +773,7 @@ __device__ __forceinline__ void acc_mixed_body(const float4 *__restrict__ irec,
                 fold2(hz[k], lz[k], az[k]);
             }
         }
+    }
     }
 #pragma unroll
     for (int k = 0; k < ILP; ++k) {

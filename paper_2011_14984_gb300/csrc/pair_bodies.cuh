@@ -390,6 +390,53 @@ __device__ __forceinline__ void grad_mixed_j(const float4 J0, const float4 J1, c
     }
 }
 
+// The thread's two particles as the two lanes of packed f32x2 arithmetic (negated parts)
+struct GradX2I {
+    float2 nxh, nyh, nzh, nxm, nym, nzm, nxl, nyl, nzl, nahx, nahy, nahz, nalx, naly, nalz;
+};
+
+// One source, staged duplicated as G0 {xh, xh, yh, yh}, G1 {zh, zh, xm, xm}, G2 {ym, ym, zm, zm},
+// G3 {xl, xl, yl, yl}, G4 {zl, zl, ahx, ahx}, G5 {ahy, ahy, ahz, ahz}, G6 {alx, alx, aly, aly},
+// G7 {alz, alz, m, m}, against the thread's two particles.  The operations and their order
+// are those of grad_mixed_j, lane by lane.
+template <class Slots>
+__device__ __forceinline__ void grad_x2_j(const float4 G0, const float4 G1, const float4 G2, const float4 G3,
+                                          const float4 G4, const float4 G5, const float4 G6, const float4 G7,
+                                          const GradX2I &P, float2 e2, int jglob, const float (&thr)[2],
+                                          Slots &big, float2 &gx, float2 &gy, float2 &gz)
+{
+    const float2 dx = __fadd2_rn(__fadd2_rn(__fadd2_rn(make_float2(G0.x, G0.y), P.nxh),
+                                            __fadd2_rn(make_float2(G1.z, G1.w), P.nxm)),
+                                 __fadd2_rn(make_float2(G3.x, G3.y), P.nxl));
+    const float2 dy = __fadd2_rn(__fadd2_rn(__fadd2_rn(make_float2(G0.z, G0.w), P.nyh),
+                                            __fadd2_rn(make_float2(G2.x, G2.y), P.nym)),
+                                 __fadd2_rn(make_float2(G3.z, G3.w), P.nyl));
+    const float2 dz = __fadd2_rn(__fadd2_rn(__fadd2_rn(make_float2(G1.x, G1.y), P.nzh),
+                                            __fadd2_rn(make_float2(G2.z, G2.w), P.nzm)),
+                                 __fadd2_rn(make_float2(G4.x, G4.y), P.nzl));
+    const float2 Ax = __fadd2_rn(__fadd2_rn(make_float2(G4.z, G4.w), P.nahx), __fadd2_rn(make_float2(G6.x, G6.y), P.nalx));
+    const float2 Ay = __fadd2_rn(__fadd2_rn(make_float2(G5.x, G5.y), P.nahy), __fadd2_rn(make_float2(G6.z, G6.w), P.naly));
+    const float2 Az = __fadd2_rn(__fadd2_rn(make_float2(G5.z, G5.w), P.nahz), __fadd2_rn(make_float2(G7.x, G7.y), P.nalz));
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+    float2 y = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 nhy = __fmul2_rn(__fmul2_rn(make_float2(-0.5f, -0.5f), r2), y);
+    y = __ffma2_rn(y, __ffma2_rn(nhy, y, make_float2(0.5f, 0.5f)), y);
+    const float2 ri2 = __fmul2_rn(y, y);
+    float2 w = __fmul2_rn(__fmul2_rn(make_float2(G7.z, G7.w), y), ri2);  // m_j r^-3
+    // a dominant term goes to a deferred double-float slot and stays out of the FP32 sum
+    const bool b0 = (w.x > thr[0]) && big.room(0);
+    if (b0) big.push(0, jglob);
+    const bool b1 = (w.y > thr[1]) && big.room(1);
+    if (b1) big.push(1, jglob);
+    w.x = b0 ? 0.f : w.x;
+    w.y = b1 ? 0.f : w.y;
+    const float2 xa = __ffma2_rn(dx, Ax, __ffma2_rn(dy, Ay, __fmul2_rn(dz, Az)));
+    const float2 nt3 = __fmul2_rn(__fmul2_rn(make_float2(-3.0f, -3.0f), xa), ri2);  // -3 (x.a) / r^2
+    gx = __ffma2_rn(w, __ffma2_rn(nt3, dx, Ax), gx);
+    gy = __ffma2_rn(w, __ffma2_rn(nt3, dy, Ay), gy);
+    gz = __ffma2_rn(w, __ffma2_rn(nt3, dz, Az), gz);
+}
+
 template <bool MASK>
 __device__ __forceinline__ void grad_fp64_j(const double4_32a J, const double4_32a JA, const double4_32a I,
                                             const double4_32a IA, double eps2, int jpos, int ipos,
@@ -894,7 +941,11 @@ __device__ __forceinline__ void grad_mixed_body(const float4 *__restrict__ irec,
                                                 int ibase, int jb, int je, int self_pass, double eps2d,
                                                 const float *__restrict__ wmax, double (&res)[ILP][3])
 {
-    __shared__ float4 s0[TJ], s1[TJ], s2[TJ], s3[TJ];
+    // the grid kernels (two particles a thread, slot columns in shared memory) stage the
+    // sources duplicated for the packed loop; the single-CTA solver as the four records
+    constexpr bool X2 = (ILP == 2) && SMEM_SLOTS;
+    __shared__ float4 s0[X2 ? 1 : TJ], s1[X2 ? 1 : TJ], s2[X2 ? 1 : TJ], s3[X2 ? 1 : TJ];
+    __shared__ float4 sG[X2 ? 8 : 1][X2 ? TJ : 1];
     const int tid = threadIdx.x;
     const float eps2 = (float)eps2d;
     GradMixedI<ILP> I;
@@ -931,6 +982,83 @@ __device__ __forceinline__ void grad_mixed_body(const float4 *__restrict__ irec,
 #pragma unroll
     for (int k = 0; k < ILP; ++k) hx[k] = hy[k] = hz[k] = lx[k] = ly[k] = lz[k] = 0.f;
 
+    if constexpr (X2) {
+        GradX2I P;
+        P.nxh = make_float2(-I.xh[0], -I.xh[1]);
+        P.nyh = make_float2(-I.yh[0], -I.yh[1]);
+        P.nzh = make_float2(-I.zh[0], -I.zh[1]);
+        P.nxm = make_float2(-I.xm[0], -I.xm[1]);
+        P.nym = make_float2(-I.ym[0], -I.ym[1]);
+        P.nzm = make_float2(-I.zm[0], -I.zm[1]);
+        P.nxl = make_float2(-I.xl[0], -I.xl[1]);
+        P.nyl = make_float2(-I.yl[0], -I.yl[1]);
+        P.nzl = make_float2(-I.zl[0], -I.zl[1]);
+        P.nahx = make_float2(-I.ahx[0], -I.ahx[1]);
+        P.nahy = make_float2(-I.ahy[0], -I.ahy[1]);
+        P.nahz = make_float2(-I.ahz[0], -I.ahz[1]);
+        P.nalx = make_float2(-I.alx[0], -I.alx[1]);
+        P.naly = make_float2(-I.aly[0], -I.aly[1]);
+        P.nalz = make_float2(-I.alz[0], -I.alz[1]);
+        const float2 e2 = make_float2(eps2, eps2);
+        const float (&thr2)[2] = *reinterpret_cast<const float(*)[2]>(thr);
+        for (int j0 = jb; j0 < je; j0 += TJ) {
+            const int cnt = min(TJ, je - j0);
+            __syncthreads();
+            for (int t = tid; t < cnt; t += BS) {
+                const float4 q0 = jrec[j0 + t], q1 = jrec[n_s + j0 + t];
+                const float4 q2 = jrec[2 * n_s + j0 + t], q3 = jrec[3 * n_s + j0 + t];
+                sG[0][t] = make_float4(q0.x, q0.x, q0.y, q0.y);
+                sG[1][t] = make_float4(q0.z, q0.z, q1.x, q1.x);
+                sG[2][t] = make_float4(q1.y, q1.y, q1.z, q1.z);
+                sG[3][t] = make_float4(q2.x, q2.x, q2.y, q2.y);
+                sG[4][t] = make_float4(q2.z, q2.z, q1.w, q1.w);
+                sG[5][t] = make_float4(q2.w, q2.w, q3.x, q3.x);
+                sG[6][t] = make_float4(q3.y, q3.y, q3.z, q3.z);
+                sG[7][t] = make_float4(q3.w, q3.w, q0.w, q0.w);
+            }
+            __syncthreads();
+            const bool diag = self_pass && (j0 < ibase + BS * ILP) && (ibase < j0 + cnt);
+            for (int c0 = 0; c0 < cnt; c0 += 64) {
+                const int c1 = min(cnt, c0 + 64);
+                float2 gx2 = make_float2(0.f, 0.f), gy2 = gx2, gz2 = gx2;
+                if (!diag) {
+                    int jj = c0;
+                    for (; jj + 4 <= c1; jj += 4) {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            grad_x2_j(sG[0][jj + u], sG[1][jj + u], sG[2][jj + u], sG[3][jj + u], sG[4][jj + u],
+                                      sG[5][jj + u], sG[6][jj + u], sG[7][jj + u], P, e2, j0 + jj + u, thr2, big,
+                                      gx2, gy2, gz2);
+                    }
+                    for (; jj < c1; ++jj)
+                        grad_x2_j(sG[0][jj], sG[1][jj], sG[2][jj], sG[3][jj], sG[4][jj], sG[5][jj], sG[6][jj],
+                                  sG[7][jj], P, e2, j0 + jj, thr2, big, gx2, gy2, gz2);
+                } else {
+                    // the i = j term masked by list position: the scalar body on the four records
+                    float gx[ILP] = {0.f, 0.f}, gy[ILP] = {0.f, 0.f}, gz[ILP] = {0.f, 0.f};
+                    for (int jj = c0; jj < c1; ++jj) {
+                        const float4 G0 = sG[0][jj], G1 = sG[1][jj], G2 = sG[2][jj], G3 = sG[3][jj];
+                        const float4 G4 = sG[4][jj], G5 = sG[5][jj], G6 = sG[6][jj], G7 = sG[7][jj];
+                        const float4 J0 = make_float4(G0.x, G0.z, G1.x, G7.z);
+                        const float4 J1 = make_float4(G1.z, G2.x, G2.z, G4.z);
+                        const float4 J2 = make_float4(G3.x, G3.z, G4.x, G5.x);
+                        const float4 J3 = make_float4(G5.z, G6.x, G6.z, G7.x);
+                        grad_mixed_j<ILP, true>(J0, J1, J2, J3, I, eps2, j0 + jj, j0 + jj, ipos, thr, big, gx, gy,
+                                                gz);
+                    }
+                    gx2 = make_float2(gx[0], gx[1]);
+                    gy2 = make_float2(gy[0], gy[1]);
+                    gz2 = make_float2(gz[0], gz[1]);
+                }
+                fold2(hx[0], lx[0], gx2.x);
+                fold2(hy[0], ly[0], gy2.x);
+                fold2(hz[0], lz[0], gz2.x);
+                fold2(hx[1], lx[1], gx2.y);
+                fold2(hy[1], ly[1], gy2.y);
+                fold2(hz[1], lz[1], gz2.y);
+            }
+        }
+    } else {
     for (int j0 = jb; j0 < je; j0 += TJ) {
         const int cnt = min(TJ, je - j0);
         __syncthreads();
@@ -970,6 +1098,7 @@ __device__ __forceinline__ void grad_mixed_body(const float4 *__restrict__ irec,
                 fold2(hz[k], lz[k], gz[k]);
             }
         }
+    }
     }
     // deferred double-float terms, records read back from global memory (L2)
 #pragma unroll

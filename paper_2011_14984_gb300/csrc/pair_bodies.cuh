@@ -562,6 +562,76 @@ __device__ __forceinline__ void tstep_mixed_j(const float4 J0, const float4 J1, 
     }
 }
 
+// The thread's two particles as the two lanes of packed f32x2 arithmetic (negated parts)
+struct TstepX2I {
+    float2 nxh, nyh, nzh, nxl, nyl, nzl, nvx, nvy, nvz, gm, nax, nay, naz;
+};
+
+// One source, staged duplicated as A {hx, hx, hy, hy}, B {hz, hz, lx, lx}, C {ly, ly, lz, lz},
+// V0 {vx, vx, vy, vy}, V1 {vz, vz, Gm, Gm} and, with the exact fly-by derivative, W0 {ax, ax,
+// ay, ay}, W1 {az, az, 0, 0}, against the thread's two particles.  The operations and their
+// order are those of tstep_mixed_j, lane by lane.
+template <int SYM>
+__device__ __forceinline__ void tstep_x2_j(const float4 A, const float4 B, const float4 C, const float4 V0,
+                                           const float4 V1, const float4 W0, const float4 W1, const TstepX2I &P,
+                                           float eta, float eta15, float (&best)[2], float (&minr2)[2])
+{
+    const float2 dx = __fadd2_rn(__fadd2_rn(make_float2(A.x, A.y), P.nxh), __fadd2_rn(make_float2(B.z, B.w), P.nxl));
+    const float2 dy = __fadd2_rn(__fadd2_rn(make_float2(A.z, A.w), P.nyh), __fadd2_rn(make_float2(C.x, C.y), P.nyl));
+    const float2 dz = __fadd2_rn(__fadd2_rn(make_float2(B.x, B.y), P.nzh), __fadd2_rn(make_float2(C.z, C.w), P.nzl));
+    const float2 ux = __fadd2_rn(make_float2(V0.x, V0.y), P.nvx);
+    const float2 uy = __fadd2_rn(make_float2(V0.z, V0.w), P.nvy);
+    const float2 uz = __fadd2_rn(make_float2(V1.x, V1.y), P.nvz);
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+    const float2 v2 = __ffma2_rn(ux, ux, __ffma2_rn(uy, uy, __fmul2_rn(uz, uz)));
+    const float2 rv = __ffma2_rn(dx, ux, __ffma2_rn(dy, uy, __fmul2_rn(dz, uz)));
+    const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 ri2 = __fmul2_rn(ri, ri);
+    const float2 gm = __fadd2_rn(P.gm, make_float2(V1.z, V1.w));  // G (m_i + m_j)
+    const float2 q = __fmul2_rn(__fmul2_rn(gm, ri2), ri);
+    const float2 tff = make_float2(rsqrtf(q.x), rsqrtf(q.y));  // (r^3 / (G M))^(1/2)
+    const float2 rvr2 = __fmul2_rn(rv, ri2);                    // r.v / r^2
+    const float2 iv = make_float2(rsqrtf(v2.x), rsqrtf(v2.y));  // 1 / |v|
+    const float2 tfb = __fmul2_rn(__fmul2_rn(r2, ri), iv);      // r / |v|
+    const float2 dff = __fmul2_rn(__fmul2_rn(make_float2(eta15, eta15), rvr2), tff);
+    const float2 iv2 = __fmul2_rn(iv, iv);
+    float2 dfb;
+    if (SYM & 4) {
+        const float2 wx = __fadd2_rn(make_float2(W0.x, W0.y), P.nax);
+        const float2 wy = __fadd2_rn(make_float2(W0.z, W0.w), P.nay);
+        const float2 wz = __fadd2_rn(make_float2(W1.x, W1.y), P.naz);
+        const float2 va = __ffma2_rn(ux, wx, __ffma2_rn(uy, wy, __fmul2_rn(uz, wz)));
+        // fma(-va, iv^2, rvr2) as fma(va, -(iv^2), rvr2)
+        const float2 niv2 = __fmul2_rn(__fmul2_rn(make_float2(-1.f, -1.f), iv), iv);
+        dfb = __fmul2_rn(__fmul2_rn(make_float2(eta, eta), __ffma2_rn(va, niv2, rvr2)), tfb);
+    } else {
+        dfb = __fmul2_rn(__fmul2_rn(__fmul2_rn(make_float2(eta, eta), rvr2),
+                                    __ffma2_rn(__fmul2_rn(gm, ri), iv2, make_float2(1.f, 1.f))),
+                         tfb);
+    }
+    const float tf[2] = {tff.x, tff.y}, tb[2] = {tfb.x, tfb.y}, df[2] = {dff.x, dff.y}, db[2] = {dfb.x, dfb.y};
+    const float rr[2] = {r2.x, r2.y}, vv[2] = {v2.x, v2.y};
+    bool nff[2], nfb[2];
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        minr2[k] = fminf(minr2[k], rr[k]);
+        const float bnd = 1.001f * best[k];
+        nff[k] = tf[k] < bnd * (1.f + fabsf(df[k]));
+        nfb[k] = (vv[k] > 0.f) && (tb[k] < bnd * (1.f + fabsf(db[k])));
+        any = any || nff[k] || nfb[k];
+    }
+    if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            float t = INFINITY;
+            if (nff[k]) t = tf[k] * symf<(SYM & 3)>(df[k]);
+            if (nfb[k]) t = fminf(t, tb[k] * symf<(SYM & 3)>(db[k]));
+            best[k] = fminf(best[k], t);
+        }
+    }
+}
+
 // FP64 pair time-steps, with the same bound on the symmetrisation factors
 template <int SYM, bool MASK>
 __device__ __forceinline__ void tstep_fp64_j(const double4_32a J, const double4_32a JV, const double4_32a JA,
@@ -1126,7 +1196,12 @@ __device__ __forceinline__ void tstep_mixed_body(const float4 *__restrict__ irec
                                                  int ibase, int jb, int je, int self_pass, float eta,
                                                  float (&best)[ILP], float (&minr2)[ILP])
 {
-    __shared__ float4 s0[TJ], s1[TJ], sv[TJ], sa[(SYM & 4) ? TJ : 1];
+    // two particles a thread: sources staged duplicated for the packed loop
+    constexpr bool X2 = (ILP == 2);
+    constexpr int TA = (SYM & 4) ? TJ : 1;
+    __shared__ float4 s0[X2 ? 1 : TJ], s1[X2 ? 1 : TJ], sv[X2 ? 1 : TJ], sa[X2 ? 1 : TA];
+    __shared__ float4 sA[X2 ? TJ : 1], sB[X2 ? TJ : 1], sC[X2 ? TJ : 1], sV0[X2 ? TJ : 1], sV1[X2 ? TJ : 1];
+    __shared__ float4 sW0[X2 ? TA : 1], sW1[X2 ? TA : 1];
     const int tid = threadIdx.x;
     TstepMixedI<ILP> I;
     int ipos[ILP];
@@ -1150,6 +1225,68 @@ __device__ __forceinline__ void tstep_mixed_body(const float4 *__restrict__ irec
 #pragma unroll
     for (int k = 0; k < ILP; ++k) best[k] = minr2[k] = INFINITY;
     const float eta15 = 1.5f * eta;
+    if constexpr (X2) {
+        TstepX2I P;
+        P.nxh = make_float2(-I.xh[0], -I.xh[1]);
+        P.nyh = make_float2(-I.yh[0], -I.yh[1]);
+        P.nzh = make_float2(-I.zh[0], -I.zh[1]);
+        P.nxl = make_float2(-I.xl[0], -I.xl[1]);
+        P.nyl = make_float2(-I.yl[0], -I.yl[1]);
+        P.nzl = make_float2(-I.zl[0], -I.zl[1]);
+        P.nvx = make_float2(-I.vx[0], -I.vx[1]);
+        P.nvy = make_float2(-I.vy[0], -I.vy[1]);
+        P.nvz = make_float2(-I.vz[0], -I.vz[1]);
+        P.gm = make_float2(I.gm[0], I.gm[1]);
+        P.nax = make_float2(-I.ax[0], -I.ax[1]);
+        P.nay = make_float2(-I.ay[0], -I.ay[1]);
+        P.naz = make_float2(-I.az[0], -I.az[1]);
+        float (&best2)[2] = *reinterpret_cast<float(*)[2]>(best);
+        float (&minr22)[2] = *reinterpret_cast<float(*)[2]>(minr2);
+        for (int j0 = jb; j0 < je; j0 += TJ) {
+            const int cnt = min(TJ, je - j0);
+            __syncthreads();
+            for (int t = tid; t < cnt; t += BS) {
+                const float4 a = jrec[j0 + t], b = jrec[n_s + j0 + t], v = jrec[2 * n_s + j0 + t];
+                sA[t] = make_float4(a.x, a.x, a.y, a.y);
+                sB[t] = make_float4(a.z, a.z, b.x, b.x);
+                sC[t] = make_float4(b.y, b.y, b.z, b.z);
+                sV0[t] = make_float4(v.x, v.x, v.y, v.y);
+                sV1[t] = make_float4(v.z, v.z, v.w, v.w);
+                if (SYM & 4) {
+                    const float4 w = jrec[3 * n_s + j0 + t];
+                    sW0[t] = make_float4(w.x, w.x, w.y, w.y);
+                    sW1[t] = make_float4(w.z, w.z, 0.f, 0.f);
+                }
+            }
+            __syncthreads();
+            const bool diag = self_pass && (j0 < ibase + BS * ILP) && (ibase < j0 + cnt);
+            if (!diag) {
+                int jj = 0;
+                for (; jj + 4 <= cnt; jj += 4) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        tstep_x2_j<SYM>(sA[jj + u], sB[jj + u], sC[jj + u], sV0[jj + u], sV1[jj + u],
+                                        (SYM & 4) ? sW0[jj + u] : zero4, (SYM & 4) ? sW1[jj + u] : zero4, P, eta,
+                                        eta15, best2, minr22);
+                }
+                for (; jj < cnt; ++jj)
+                    tstep_x2_j<SYM>(sA[jj], sB[jj], sC[jj], sV0[jj], sV1[jj], (SYM & 4) ? sW0[jj] : zero4,
+                                    (SYM & 4) ? sW1[jj] : zero4, P, eta, eta15, best2, minr22);
+            } else {
+                // the i = j pair masked by list position: the scalar body on rebuilt records
+                for (int jj = 0; jj < cnt; ++jj) {
+                    const float4 a = sA[jj], b = sB[jj], c = sC[jj], v0 = sV0[jj], v1 = sV1[jj];
+                    const float4 J0 = make_float4(a.x, a.z, b.x, 0.f);
+                    const float4 J1 = make_float4(b.z, c.x, c.z, 0.f);
+                    const float4 JV = make_float4(v0.x, v0.z, v1.x, v1.z);
+                    float4 JA = zero4;
+                    if (SYM & 4) JA = make_float4(sW0[jj].x, sW0[jj].z, sW1[jj].x, 0.f);
+                    tstep_mixed_j<ILP, SYM, true>(J0, J1, JV, JA, I, eta, eta15, j0 + jj, ipos, best, minr2);
+                }
+            }
+        }
+        return;
+    }
     for (int j0 = jb; j0 < je; j0 += TJ) {
         const int cnt = min(TJ, je - j0);
         __syncthreads();

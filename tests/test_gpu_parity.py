@@ -424,6 +424,22 @@ def test_solar_system_hhs_fsi_on_gpu():
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("e", [0.0, 0.9])
+def test_equal_mass_binary_conserves_momentum_exactly(precision, e):
+    """The paper's binary experiment (Sec. 6.1, Fig. 3): with two equal masses the two kicks of
+    every step are exact negatives (x_j - x_i = -(x_i - x_j), the same r^2 and weights), so the
+    total momentum stays exactly zero over many orbits, in both precision modes."""
+    m, x, v = ics.kepler_binary(1.0, 1.0, 1.0, e)
+    P0 = (m[:, None] * v).sum(0)
+    assert np.all(P0 == 0.0)
+    f = F(m, x, v, precision=precision, eta=0.05)
+    f.step(2.0 ** -5, 200)
+    xg, vg, _ = f.state()
+    assert np.all((m[:, None] * vg).sum(0) == 0.0), (m[:, None] * vg).sum(0)
+    f.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_checkpoint_restart_is_bit_identical(precision, tmp_path):
     """Checkpoint / restart through the snapshot-as-initial-condition route: 4 + 4 steps with
     the state written to disk and read into a fresh context give the same bits as 8 steps

@@ -65,6 +65,8 @@ def parse():
     p.add_argument("--flyby-exact", action="store_true",
                    help="exact fly-by derivative in the time-steps (first line of Eq. "
                         "dt-flyby-derivative)")
+    p.add_argument("--subtree-blocks", type=int, default=0,
+                   help="thread blocks (a cluster) per single-set subtree-solver launch; 0 = library default")
     p.add_argument("--subtree-max", type=int, default=0,
                    help="largest set whose hhs_fsi subtree runs in one block (0 = library default)")
     return p.parse_args()
@@ -246,7 +248,7 @@ def run_frost(args):
 
     def new(prec):
         return fr.Frost(m, x, v, G=1.0, eta=args.eta, precision=prec, stream=stream.cuda_stream,
-                        subtree_max=args.subtree_max,
+                        subtree_max=args.subtree_max, subtree_blocks=args.subtree_blocks,
                         sym=fr.FROST_SYM_HARMONIC | (fr.FROST_FLYBY_EXACT if args.flyby_exact else 0),
                         integrator=fr.FROST_HOLD2 if args.integrator == "hold2" else fr.FROST_HHS_FSI)
 

@@ -75,6 +75,8 @@ typedef struct {
                            subtree in one thread block (one launch, no host synchronisation);
                            0 = default (384), negative = never */
     int32_t integrator; /* frost_integrator: what frost_step advances with */
+    int32_t subtree_blocks; /* thread blocks that share one subtree-solver set (a thread-block
+                               cluster, 1..8); 0 = default */
 } frost_opts;
 
 typedef enum {

@@ -105,6 +105,7 @@ struct frost_ctx {
     size_t part_hot_elems = 0;
     int32_t *perm = nullptr, *ptmp = nullptr;        // subtree solver permutation / scratch
     int subtree_max = 384;                           // sets up to this size run in one block
+    int subtree_blocks = 1;                          // blocks (a cluster) per single-set solver launch
     int integrator = FROST_HHS_FSI;                  // frost_integrator of frost_step
     int n_clusters = 0;                              // > 0: batch of independent clusters
     int64_t *d_offsets = nullptr;                    // cluster offsets [n_clusters + 1] (device)
@@ -603,6 +604,8 @@ void hhs_subtree(frost_ctx *c, const int32_t *P, int nP, double tau, int depth)
     a.tau0 = tau;
     a.depth0 = depth;
     a.n_steps = 1;
+    a.team_blocks = c->subtree_blocks;
+    a.xchg = c->d_xchg;
     {
         TimedScope ts(c, PASS_SUBTREE, 0);
         // a launch error is also left for the cudaGetLastError() of the calling entry point
@@ -711,6 +714,7 @@ void frost_default_opts(frost_opts *opt)
     opt->max_depth = 40;
     opt->cuda_stream = nullptr;
     opt->subtree_max = 0;
+    opt->subtree_blocks = 0;
     opt->integrator = FROST_HHS_FSI;
 }
 
@@ -766,6 +770,9 @@ static frost_status init_impl(frost_ctx **out, int64_t n, const double *m, const
     if (o.integrator == FROST_HOLD2 && n_clusters > 0)
         return fail(FROST_EINVAL, "the HOLD integrator runs on single-set contexts only");
 
+    if (o.subtree_blocks < 0 || o.subtree_blocks > SUBTREE_MAX_CLUSTER)
+        return fail(FROST_EINVAL, "subtree_blocks must be 0..%d", SUBTREE_MAX_CLUSTER);
+
     frost_ctx *c = new (std::nothrow) frost_ctx();
     if (!c) return fail(FROST_ENOMEM, "host allocation failed");
     c->N = (int)n;
@@ -776,6 +783,7 @@ static frost_status init_impl(frost_ctx **out, int64_t n, const double *m, const
     c->sym = o.sym;
     c->max_depth = o.max_depth > 0 ? o.max_depth : 40;
     c->subtree_max = o.subtree_max == 0 ? 384 : (o.subtree_max < 0 ? 0 : o.subtree_max);
+    c->subtree_blocks = o.subtree_blocks == 0 ? 1 : o.subtree_blocks;
     c->integrator = o.integrator;
 
     auto bail = [&](frost_status st) {
@@ -858,6 +866,8 @@ static frost_status init_impl(frost_ctx **out, int64_t n, const double *m, const
         }
     }
     INIT_CUDA(cudaMalloc(&c->dmisc, sizeof(Misc)));
+    // the status word of a multi-block single-set solver team (batch contexts have one per cluster)
+    if (!c->d_xchg) INIT_CUDA(cudaMalloc(&c->d_xchg, sizeof(int)));
     INIT_CUDA(cudaMallocHost(&c->hmisc, sizeof(Misc)));
     INIT_CUDA(cudaMemsetAsync(c->dmisc, 0, sizeof(Misc), c->stream));
     INIT_CUDA(cudaMemsetAsync(c->marks, 0, sizeof(int32_t) * N, c->stream));

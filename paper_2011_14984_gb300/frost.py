@@ -39,7 +39,7 @@ class frost_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("sym", ctypes.c_int32),
                 ("eps_soft", ctypes.c_double), ("max_depth", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p), ("subtree_max", ctypes.c_int32),
-                ("integrator", ctypes.c_int32)]
+                ("integrator", ctypes.c_int32), ("subtree_blocks", ctypes.c_int32)]
 
 
 class frost_stats(ctypes.Structure):
@@ -291,7 +291,8 @@ class Frost:
 
     def __init__(self, m, x, v, G: float = 1.0, eta: float = 0.2, precision: str = "mixed",
                  sym: int = FROST_SYM_HARMONIC, eps_soft: float = 0.0, max_depth: int = 40,
-                 stream=None, subtree_max: int = 0, offsets=None, integrator: int = FROST_HHS_FSI):
+                 stream=None, subtree_max: int = 0, offsets=None, integrator: int = FROST_HHS_FSI,
+                 subtree_blocks: int = 0):
         import torch
         self.torch = torch
         o = frost_default_opts()
@@ -302,6 +303,7 @@ class Frost:
         o.cuda_stream = stream if stream is not None else current_stream_handle()
         o.subtree_max = int(subtree_max)
         o.integrator = int(integrator)
+        o.subtree_blocks = int(subtree_blocks)
         self.n = int(np.asarray(m).shape[0]) if not hasattr(m, "shape") else int(m.shape[0])
         self.G = G
         self.eta = eta

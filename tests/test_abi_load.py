@@ -43,3 +43,25 @@ def test_library_builds_loads_and_exports_every_declared_symbol():
 def test_binding_wraps_every_declared_function():
     for name in declared_functions():
         assert hasattr(frost, name), name
+
+
+def test_init_rejects_bad_options_before_touching_the_device():
+    """Argument checks of frost_init run on the host before any CUDA call, so they can be
+    exercised here: bad sizes, G, eta, precision, symmetrisation, integrator and team size."""
+    import numpy as np
+    import pytest
+
+    m = np.ones(4)
+    x = np.zeros((4, 3))
+    v = np.zeros((4, 3))
+    cases = [dict(subtree_blocks=9), dict(subtree_blocks=-1), dict(precision=7), dict(sym=3),
+             dict(integrator=5)]
+    for fields in cases:
+        o = frost.frost_default_opts()
+        for k, val in fields.items():
+            setattr(o, k, val)
+        with pytest.raises(frost.FrostError) as e:
+            frost.frost_init(m, x, v, 1.0, 0.2, o)
+        assert e.value.code == frost.FROST_EINVAL, (fields, str(e.value))
+    with pytest.raises(frost.FrostError):
+        frost.frost_init(m, x, v, -1.0, 0.2)

@@ -548,6 +548,26 @@ def test_subtree_solver_trajectory_parity_fp64(subtree_max, sym):
     f.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_subtree_solver_on_a_block_cluster(precision):
+    """A single-set solver launch spread over an 8-block thread-block cluster (cluster
+    barriers, the group path for every pass): the trajectory of the one-block solver, to the
+    oracle's 1e-10 in FP64 and to the mixed-precision level otherwise."""
+    m, x, v = ics.plummer(700, 31, masses=ics.kroupa_masses(700, 31))
+    out = {}
+    for blocks in (1, 8):
+        f = F(m, x, v, precision=precision, eta=0.2, subtree_max=1 << 30, subtree_blocks=blocks)
+        f.step(2.0 ** -7, 6)
+        out[blocks] = f.state()[0]
+        assert f.stats()["subtree_launches"] == 6
+        f.close()
+    if precision == "fp64":
+        xo, _ = oracle.steps(m, x, v, 2.0 ** -7, 6, eta=0.2)
+        assert np.max(np.abs(out[8] - xo)) < 1e-10
+    else:
+        assert np.max(np.abs(out[8] - out[1])) < 1e-7
+
+
 def test_subtree_solver_mixed_matches_grid_path():
     """Mixed precision: the same steps with and without the single-block solver agree to
     the mixed-precision level and reach the same energy error."""

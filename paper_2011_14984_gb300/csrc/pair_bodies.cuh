@@ -424,6 +424,7 @@ __device__ __forceinline__ void grad_x2_j(const float4 G0, const float4 G1, cons
     const float2 ri2 = __fmul2_rn(y, y);
     float2 w = __fmul2_rn(__fmul2_rn(make_float2(G7.z, G7.w), y), ri2);  // m_j r^-3
     // a dominant term goes to a deferred double-float slot and stays out of the FP32 sum
+    // (a warp vote before this, as in acc_x2_j, costs two registers here and a block per SM)
     const bool b0 = (w.x > thr[0]) && big.room(0);
     if (b0) big.push(0, jglob);
     const bool b1 = (w.y > thr[1]) && big.room(1);
@@ -712,12 +713,15 @@ __device__ __forceinline__ void acc_x2_j(const float4 A, const float4 B, const f
         wm[1] = fmaxf(wm[1], w.y);
     }
     if (DEFER) {
-        const bool b0 = (w.x > thr[0]) && big.room(0);
-        if (b0) big.push(0, jglob);
-        const bool b1 = (w.y > thr[1]) && big.room(1);
-        if (b1) big.push(1, jglob);
-        w.x = b0 ? 0.f : w.x;
-        w.y = b1 ? 0.f : w.y;
+        // most warp-steps have no candidate at all: one vote skips the per-lane slot logic
+        if (__any_sync(0xffffffffu, (w.x > thr[0]) || (w.y > thr[1]))) {
+            const bool b0 = (w.x > thr[0]) && big.room(0);
+            if (b0) big.push(0, jglob);
+            const bool b1 = (w.y > thr[1]) && big.room(1);
+            if (b1) big.push(1, jglob);
+            w.x = b0 ? 0.f : w.x;
+            w.y = b1 ? 0.f : w.y;
+        }
     }
     ax = __ffma2_rn(w, dx, ax);
     ay = __ffma2_rn(w, dy, ay);

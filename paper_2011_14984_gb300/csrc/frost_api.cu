@@ -316,8 +316,8 @@ void pass_acc(frost_ctx *c, const int32_t *A, int nA, const int32_t *B, int nB, 
         }
         launch_acc(c->stream, c->mixed, a);
     }
-    launch_finalize_vec(c->stream, c->part, a.shape.nsplit, nA, c->G, out_soa, out_aos, nullptr, nullptr,
-                        &c->dmisc->err, badbit(c), kick);
+    launch_finalize_vec(c->stream, c->part, a.shape.nsplit, nA, c->G, out_soa, out_aos, &c->dmisc->err,
+                        badbit(c), kick);
     c->st.kernel_launches += 2;
     c->st.acc_pairs += pairs;
     if (accurate && hist && out_soa) {

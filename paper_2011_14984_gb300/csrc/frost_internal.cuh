@@ -60,7 +60,6 @@ struct PairArgs {
     double eps2;      // softening^2
     double *part;     // partial results [nsplit][ncomp][n_a]
     SplitShape shape;
-    float *wpart = nullptr;        // acc (mixed): per-split max_j m_j / r^3 [nsplit][n_a], or NULL
     const float *wmax = nullptr;   // grad and accurate acc (mixed): max_j m_j / r^3 [n_a], or NULL
     bool accurate = false;         // acc (mixed): the variant that feeds a gradient pass (wmax set)
     const int32_t *jlist = nullptr;  // accurate acc: the source list (NULL: identity) and the
@@ -111,11 +110,11 @@ struct KickArgs {
     double *store = nullptr;
 };
 
-// out_soa[c][i] = scale * sum_split part[split][c][i]  (also [i][3] copy if out_aos != NULL);
-// with wpart, wmax[i] = max_split wpart[split][i]
+// out_soa[c][i] = scale * sum_split part[split][c][i]  (also [i][3] copy if out_aos != NULL),
+// then the kick / store of kick
 void launch_finalize_vec(cudaStream_t s, const double *part, int nsplit, int n, double scale,
-                         double *out_soa, double *out_aos, const float *wpart, float *wmax,
-                         int *err, int coincident_bit, KickArgs kick = KickArgs());
+                         double *out_soa, double *out_aos, int *err, int coincident_bit,
+                         KickArgs kick = KickArgs());
 // a~ = a + c g with g = scale * (sum part + sum part2); writes a~ (soa and/or aos) and g
 // (aos, optional); part2 (nsplit2 splits, may be 0) holds the FP64 terms of hot sources
 void launch_finalize_grad(cudaStream_t s, const double *part, int nsplit, int n, double scale,

@@ -132,7 +132,7 @@ extern "C" frost_status frost_accel_noalloc(int64_t n, const double *m, const do
     a.part = part;
     a.shape = sh;
     launch_acc(s, true, a);
-    launch_finalize_vec(s, part, sh.nsplit, ni, G, nullptr, acc, nullptr, nullptr, err,
+    launch_finalize_vec(s, part, sh.nsplit, ni, G, nullptr, acc, err,
                         eps_soft == 0.0 ? ERR_COINCIDENT : ERR_NONFINITE);
     e = cudaGetLastError();
     if (e != cudaSuccess) return noalloc_fail(FROST_ECUDA, cudaGetErrorString(e));

@@ -257,7 +257,6 @@ __device__ __forceinline__ double split_sum(const double *__restrict__ q, int ns
 
 __global__ void k_finalize_vec(const double *__restrict__ part, int nsplit, int n, double scale,
                                double *__restrict__ out_soa, double *__restrict__ out_aos,
-                               const float *__restrict__ wpart, float *__restrict__ wmax,
                                int *__restrict__ err, int badbit, KickArgs kick)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -273,17 +272,6 @@ __global__ void k_finalize_vec(const double *__restrict__ part, int nsplit, int 
         // the kick that follows the pass: the roundings of k_kick (no contraction)
         if (kick.v) kick.v[(size_t)c * kick.N + gi] = __dadd_rn(kick.v[(size_t)c * kick.N + gi], __dmul_rn(kick.dt, s));
         if (kick.store) kick.store[(size_t)c * kick.N + gi] = s;
-    }
-    if (wpart) {
-        float w0 = 0.f, w1 = 0.f;
-        int p = 0;
-        for (; p + 2 <= nsplit; p += 2) {
-            w0 = fmaxf(w0, wpart[(size_t)p * n + i]);
-            w1 = fmaxf(w1, wpart[(size_t)(p + 1) * n + i]);
-        }
-        if (p < nsplit) w0 = fmaxf(w0, wpart[(size_t)p * n + i]);
-        const float w = fmaxf(w0, w1);
-        wmax[i] = w;
     }
     if (!ok) atomicOr(err, badbit);
 }
@@ -443,14 +431,9 @@ void launch_acc(cudaStream_t s, bool mixed, const PairArgs &a)
             (const float4 *)a.irec, (const float4 *)a.jrec, a.n_a, a.n_s, a.shape.j_per_split,
             a.self_pass, (float)a.eps2, a.part, nullptr, a.wmax, a.eps2, a.jlist, a.m);
     } else if (mixed) {
-        if (a.wpart)
-            k_acc_mixed<PAIR_BS, PAIR_ILP, PAIR_TJ, true><<<grid, PAIR_BS, 0, s>>>(
-                (const float4 *)a.irec, (const float4 *)a.jrec, a.n_a, a.n_s, a.shape.j_per_split,
-                a.self_pass, (float)a.eps2, a.part, a.wpart);
-        else
-            k_acc_mixed<PAIR_BS, PAIR_ILP, PAIR_TJ, false><<<grid, PAIR_BS, 0, s>>>(
-                (const float4 *)a.irec, (const float4 *)a.jrec, a.n_a, a.n_s, a.shape.j_per_split,
-                a.self_pass, (float)a.eps2, a.part, nullptr);
+        k_acc_mixed<PAIR_BS, PAIR_ILP, PAIR_TJ, false><<<grid, PAIR_BS, 0, s>>>(
+            (const float4 *)a.irec, (const float4 *)a.jrec, a.n_a, a.n_s, a.shape.j_per_split,
+            a.self_pass, (float)a.eps2, a.part, nullptr);
     } else {
         k_acc_fp64<PAIR_BS, PAIR_TJ><<<grid, PAIR_BS, 0, s>>>(
             (const double4_32a *)a.irec, (const double4_32a *)a.jrec, a.n_a, a.n_s, a.shape.j_per_split,
@@ -505,12 +488,10 @@ void launch_tstep(cudaStream_t s, bool mixed, const PairArgs &a, double eta, int
 }
 
 void launch_finalize_vec(cudaStream_t s, const double *part, int nsplit, int n, double scale,
-                         double *out_soa, double *out_aos, const float *wpart, float *wmax, int *err,
-                         int badbit, KickArgs kick)
+                         double *out_soa, double *out_aos, int *err, int badbit, KickArgs kick)
 {
     if (n <= 0) return;
-    k_finalize_vec<<<cdiv(n, 256), 256, 0, s>>>(part, nsplit, n, scale, out_soa, out_aos, wpart, wmax,
-                                                 err, badbit, kick);
+    k_finalize_vec<<<cdiv(n, 256), 256, 0, s>>>(part, nsplit, n, scale, out_soa, out_aos, err, badbit, kick);
 }
 
 void launch_finalize_grad(cudaStream_t s, const double *part, int nsplit, int n, double scale,

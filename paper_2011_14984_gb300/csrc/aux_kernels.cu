@@ -223,7 +223,9 @@ __global__ void k_pack_pot_df(const double *__restrict__ x, const double *__rest
 }
 
 
-// phi_i = sum_{j != i} m_j / sqrt(r^2 + eps2) in double-float, j-split partials part[split][i]
+// phi_i = sum_{j > i} m_j / sqrt(r^2 + eps2) in double-float, j-split partials part[split][i]:
+// each pair once (U = -G sum_i m_i phi_i); the tiles wholly at or below the block's i-range are
+// skipped, so the pass does half the pairs of the full sum
 template <int BS, int TJ>
 __global__ void __launch_bounds__(BS) k_potential_df(const float4 *__restrict__ rec, int n,
                                                      int j_per_split, double eps2,
@@ -242,8 +244,10 @@ __global__ void __launch_bounds__(BS) k_potential_df(const float4 *__restrict__ 
     float H = 0.f, L = 0.f;
     const int jb = blockIdx.y * j_per_split;
     const int je = min(n, jb + j_per_split);
+    const int ibase = blockIdx.x * BS;
     for (int j0 = jb; j0 < je; j0 += TJ) {
         const int cnt = min(TJ, je - j0);
+        if (j0 + cnt <= ibase + 1) continue;  // no j > i in this tile (block-uniform)
         __syncthreads();
         for (int t = tid; t < cnt; t += BS) {
             s0[t] = rec[j0 + t];
@@ -279,7 +283,7 @@ __global__ void __launch_bounds__(BS) k_potential_df(const float4 *__restrict__ 
             // m_j / r = (m_h + m_l)(y0 + c)
             const float w = __fmul_rn(J0.w, y0);
             const float we = fmaf(J0.w, y0, -w) + fmaf(J0.w, c, J1.w * y0);
-            if (j0 + jj != i) {
+            if (j0 + jj > i) {
                 float e;
                 df::two_sum(H, w, H, e);
                 L += e + we;

@@ -1231,7 +1231,7 @@ frost_status frost_energy_momentum(frost_ctx *c, double *E_kin, double *E_pot, d
     FROST_TRY(sync_misc(c));
     const double *e = c->hmisc->eres;
     if (E_kin) *E_kin = e[0];
-    if (E_pot) *E_pot = -0.5 * c->G * e[1];
+    if (E_pot) *E_pot = -c->G * e[1];  // phi_i sums the pairs j > i
     if (P)
         for (int k = 0; k < 3; ++k) P[k] = e[2 + k];
     if (L)

@@ -173,7 +173,7 @@ void launch_identity(cudaStream_t s, int32_t *list, int n);
 void launch_aos_to_soa(cudaStream_t s, const double *aos, int n, double *soa, int *err);
 void launch_soa_to_aos(cudaStream_t s, const double *soa, int n, double *aos);
 void launch_check_mass(cudaStream_t s, const double *m, int n, int *err);
-// per-particle potential phi_i = sum_{j != i} m_j / sqrt(r^2 + eps2) in double-float
+// phi_i = sum_{j > i} m_j / sqrt(r^2 + eps2) (each pair once; U = -G sum_i m_i phi_i) in double-float
 // arithmetic (about 1e-13 relative), split partials part[split][i] (summed in order by
 // launch_energy_reduce); rec: scratch of 48 B per particle
 void launch_potential(cudaStream_t s, const double *x, const double *m, int n, double eps2, float4 *rec,

@@ -373,7 +373,8 @@ void pass_grad(frost_ctx *c, const int32_t *A, int nA, const double *aA, const i
     if (irec) {
         // packed by the caller
     } else if (c->mixed) {
-        // hot sources: masses zeroed in the FP32 source records, their terms summed in FP64 below
+        // hot sources: masses zeroed in the FP32 source records, their terms summed in
+        // double-float by k_grad_hot
         launch_pack_grad_mixed(c->stream, A, nA, c->x, c->m, c->N, aA, (float4 *)c->recA,
                                self ? hotB : nullptr);
         if (!self) launch_pack_grad_mixed(c->stream, B, nB, c->x, c->m, c->N, aB, (float4 *)c->recB, hotB);
@@ -485,7 +486,7 @@ void pack_acc(frost_ctx *c, const int32_t *L, int n, void *rec, bool /*accurate*
 }
 
 // gradient records of L with accelerations a ([3][n]); mixed mode: masses of the hot
-// particles (mask) zeroed, their terms are summed in FP64
+// particles (mask) zeroed, their terms are summed in double-float by k_grad_hot
 void pack_grad(frost_ctx *c, const int32_t *L, int n, const double *a, void *rec, const uint32_t *mask)
 {
     if (n <= 0) return;

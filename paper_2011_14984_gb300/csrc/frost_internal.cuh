@@ -69,7 +69,7 @@ struct PairArgs {
 // ---- pack kernels: list -> per-pass records ------------------------------------------
 void launch_pack_pos_mixed(cudaStream_t s, const int32_t *list, int n, const double *x,
                            const double *m, int N, float4 *rec);
-// hot (optional): mask bit k set zeroes the mass of record k (a source summed in FP64)
+// hot (optional): mask bit k set zeroes the mass of record k (a source summed in double-float)
 void launch_pack_grad_mixed(cudaStream_t s, const int32_t *list, int n, const double *x,
                             const double *m, int N, const double *acc /*[3][n]*/, float4 *rec,
                             const uint32_t *hot = nullptr);
@@ -116,7 +116,7 @@ void launch_finalize_vec(cudaStream_t s, const double *part, int nsplit, int n, 
                          double *out_soa, double *out_aos, int *err, int coincident_bit,
                          KickArgs kick = KickArgs());
 // a~ = a + c g with g = scale * (sum part + sum part2); writes a~ (soa and/or aos) and g
-// (aos, optional); part2 (nsplit2 splits, may be 0) holds the FP64 terms of hot sources
+// (aos, optional); part2 (nsplit2 splits, may be 0) holds the double-float terms of hot sources
 void launch_finalize_grad(cudaStream_t s, const double *part, int nsplit, int n, double scale,
                           const double *a_soa, double c, double *at_soa, double *at_aos,
                           double *g_aos, int *err, int coincident_bit,

@@ -426,7 +426,7 @@ def test_solar_system_hhs_fsi_on_gpu():
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("e", [0.0, 0.9])
 def test_equal_mass_binary_conserves_momentum_exactly(precision, e):
-    """The paper's binary experiment (Sec. 6.1, Fig. 3): with two equal masses the two kicks of
+    """The paper's binary experiment (Sec. 6.1.1): with two equal masses the two kicks of
     every step are exact negatives (x_j - x_i = -(x_i - x_j), the same r^2 and weights), so the
     total momentum stays exactly zero over many orbits, in both precision modes."""
     m, x, v = ics.kepler_binary(1.0, 1.0, 1.0, e)

@@ -528,6 +528,21 @@ def test_full_pass_64k_sampled(precision):
 # single-block subtree solver (hhs_fsi subtrees of small sets in one thread block)
 # ---------------------------------------------------------------------------------------
 
+def test_full_pass_64k_every_particle_mixed():
+    """The mixed bar at the benchmark's size over every particle, not a sample: Plummer
+    N = 65536 (the benchmark sphere), the full-set acc + gradient pass against the oracle's
+    a and g of all 65536 particles."""
+    m, x, v = ics.workload("plummer_64k")
+    n = m.size
+    f = F(m, x, v, precision="mixed")
+    out = f.accel_gradient(None, None, eps_grad=2.0 ** -7)
+    A = np.arange(n, dtype=np.int32)
+    a_ref, g_ref = oracle_g(m, x, A, A)
+    ea, eg = rel(cpu(out["acc"]), a_ref), rel(cpu(out["grad"]), g_ref)
+    assert p999(ea) < 1e-6 and p999(eg) < 1e-6, (p999(ea), p999(eg))
+    f.close()
+
+
 @pytest.mark.parametrize("subtree_max", [1 << 30, 100])
 @pytest.mark.parametrize("sym", [0, 4])
 def test_subtree_solver_trajectory_parity_fp64(subtree_max, sym):

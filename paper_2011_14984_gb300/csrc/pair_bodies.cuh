@@ -501,9 +501,14 @@ struct TstepMixedI {
 // Pair time-steps without eta: best[k] = min(best[k], tau_ff_sym, tau_fb_sym), minr2[k] =
 // min(minr2[k], r^2).  Every symmetrisation factor obeys s(d) >= 1 / (1 + |d|) (harmonic:
 // q - d <= 2 (1 + |d|); arithmetic: 1 / (1 + |d|/2) and 2 / d; none: 1), so a criterion with
-// t >= 1.001 best (1 + |d|) cannot lower the minimum; it is not symmetrised, and the warp
-// skips the factors (two MUFU sqrt/divide pairs) when no lane needs them.  The 0.1% margin
-// is far above the rounding of the factor, so the result is the one of the full evaluation.
+// t >= bnd (1 + |d|), bnd = 1.001 best, cannot lower the minimum; it is not symmetrised, and
+// the warp skips the factors (two MUFU sqrt/divide pairs) when no lane needs them.  The 0.1%
+// margin is far above the rounding of the test and of the factor, so the result is the one
+// of the full evaluation.  Each d is t times a rate (dt/dt / t), so the test is written
+// t - |bnd d / t| t >= bnd: one FMA per criterion with the rate scaled by bnd eta, and d
+// itself is formed only for the pairs that pass.  An unordered test (a NaN, e.g. from
+// bnd = inf before the first pair) counts as "may lower": such a pair is evaluated, and a
+// NaN result leaves best unchanged under fminf.
 // SYM & 3 selects the factor (0 harmonic, 1 arithmetic, 2 none); SYM & 4 the exact fly-by
 // derivative [r.v/r^2 - v.a/v^2] t_fb with the relative acceleration JA - I.a (first line of
 // Eq. dt-flyby-derivative) instead of its two-body approximation.
@@ -513,7 +518,7 @@ __device__ __forceinline__ void tstep_mixed_j(const float4 J0, const float4 J1, 
                                               int jpos, const int (&ipos)[ILP],
                                               float (&best)[ILP], float (&minr2)[ILP])
 {
-    float tff[ILP], tfb[ILP], dff[ILP], dfb[ILP];
+    float tff[ILP], tfb[ILP], rvr2[ILP], hfb[ILP];
     bool nff[ILP], nfb[ILP];
     bool any = false;
 #pragma unroll
@@ -529,16 +534,21 @@ __device__ __forceinline__ void tstep_mixed_j(const float4 J0, const float4 J1, 
         const float ri2 = ri * ri;
         const float gm = I.gm[k] + JV.w;            // G (m_i + m_j)
         tff[k] = rsqrtf(gm * ri2 * ri);              // (r^3 / (G M))^(1/2)
-        const float rvr2 = rv * ri2;                 // r.v / r^2
+        rvr2[k] = rv * ri2;                          // r.v / r^2
         const float iv = rsqrtf(v2);                 // 1 / |v|
         tfb[k] = r2 * ri * iv;                       // r / |v|
-        dff[k] = eta15 * rvr2 * tff[k];              // eta dt_ff/dt
+        const float bnd = 1.001f * best[k];
+        const float ce = bnd * eta;
+        const float z = ce * rvr2[k];                // bnd dt_ff/dt / (1.5 t_ff)
+        float mfb;
         if (SYM & 4) {
             const float wx = JA.x - I.ax[k], wy = JA.y - I.ay[k], wz = JA.z - I.az[k];
             const float va = fmaf(ux, wx, fmaf(uy, wy, uz * wz));
-            dfb[k] = eta * fmaf(-va, iv * iv, rvr2) * tfb[k];            // eta dt_fb/dt, exact
+            hfb[k] = fmaf(-va, iv * iv, rvr2[k]);    // dt_fb/dt / t_fb, exact
+            mfb = -fabsf(ce * hfb[k]);
         } else {
-            dfb[k] = eta * rvr2 * fmaf(gm * ri, iv * iv, 1.f) * tfb[k];  // eta dt_fb/dt, two-body
+            hfb[k] = fmaf(gm * ri, iv * iv, 1.f);    // dt_fb/dt / (t_fb r.v/r^2), two-body
+            mfb = -fabsf(z) * hfb[k];
         }
         float rr = r2;
         bool self = false;
@@ -547,17 +557,19 @@ __device__ __forceinline__ void tstep_mixed_j(const float4 J0, const float4 J1, 
             rr = self ? INFINITY : rr;
         }
         minr2[k] = fminf(minr2[k], rr);
-        const float bnd = 1.001f * best[k];
-        nff[k] = !self && (tff[k] < bnd * (1.f + fabsf(dff[k])));
-        nfb[k] = !self && (v2 > 0.f) && (tfb[k] < bnd * (1.f + fabsf(dfb[k])));
+        nff[k] = !self && !(fmaf(-1.5f * fabsf(z), tff[k], tff[k]) >= bnd);
+        nfb[k] = !self && (v2 > 0.f) && !(fmaf(mfb, tfb[k], tfb[k]) >= bnd);
         any = any || nff[k] || nfb[k];
     }
     if (__any_sync(0xffffffffu, any)) {
 #pragma unroll
         for (int k = 0; k < ILP; ++k) {
             float t = INFINITY;
-            if (nff[k]) t = tff[k] * symf<(SYM & 3)>(dff[k]);
-            if (nfb[k]) t = fminf(t, tfb[k] * symf<(SYM & 3)>(dfb[k]));
+            if (nff[k]) t = tff[k] * symf<(SYM & 3)>(eta15 * rvr2[k] * tff[k]);
+            if (nfb[k]) {
+                const float dfb = (SYM & 4) ? eta * hfb[k] * tfb[k] : eta * rvr2[k] * hfb[k] * tfb[k];
+                t = fminf(t, tfb[k] * symf<(SYM & 3)>(dfb));
+            }
             best[k] = fminf(best[k], t);
         }
     }
@@ -571,11 +583,13 @@ struct TstepX2I {
 // One source, staged duplicated as A {hx, hx, hy, hy}, B {hz, hz, lx, lx}, C {ly, ly, lz, lz},
 // V0 {vx, vx, vy, vy}, V1 {vz, vz, Gm, Gm} and, with the exact fly-by derivative, W0 {ax, ax,
 // ay, ay}, W1 {az, az, 0, 0}, against the thread's two particles.  The operations and their
-// order are those of tstep_mixed_j, lane by lane.
+// order are those of tstep_mixed_j, lane by lane; bnd = 1.001 best and ce = bnd eta are kept
+// by the caller (initially inf) and renewed here when best changes.
 template <int SYM>
 __device__ __forceinline__ void tstep_x2_j(const float4 A, const float4 B, const float4 C, const float4 V0,
                                            const float4 V1, const float4 W0, const float4 W1, const TstepX2I &P,
-                                           float eta, float eta15, float (&best)[2], float (&minr2)[2])
+                                           float eta, float eta15, float (&best)[2], float (&minr2)[2],
+                                           float (&bnd)[2], float (&ce)[2])
 {
     const float2 dx = __fadd2_rn(__fadd2_rn(make_float2(A.x, A.y), P.nxh), __fadd2_rn(make_float2(B.z, B.w), P.nxl));
     const float2 dy = __fadd2_rn(__fadd2_rn(make_float2(A.z, A.w), P.nyh), __fadd2_rn(make_float2(C.x, C.y), P.nyl));
@@ -594,9 +608,8 @@ __device__ __forceinline__ void tstep_x2_j(const float4 A, const float4 B, const
     const float2 rvr2 = __fmul2_rn(rv, ri2);                    // r.v / r^2
     const float2 iv = make_float2(rsqrtf(v2.x), rsqrtf(v2.y));  // 1 / |v|
     const float2 tfb = __fmul2_rn(__fmul2_rn(r2, ri), iv);      // r / |v|
-    const float2 dff = __fmul2_rn(__fmul2_rn(make_float2(eta15, eta15), rvr2), tff);
-    const float2 iv2 = __fmul2_rn(iv, iv);
-    float2 dfb;
+    const float2 z = __fmul2_rn(make_float2(ce[0], ce[1]), rvr2);
+    float2 hfb, mfb;
     if (SYM & 4) {
         const float2 wx = __fadd2_rn(make_float2(W0.x, W0.y), P.nax);
         const float2 wy = __fadd2_rn(make_float2(W0.z, W0.w), P.nay);
@@ -604,31 +617,39 @@ __device__ __forceinline__ void tstep_x2_j(const float4 A, const float4 B, const
         const float2 va = __ffma2_rn(ux, wx, __ffma2_rn(uy, wy, __fmul2_rn(uz, wz)));
         // fma(-va, iv^2, rvr2) as fma(va, -(iv^2), rvr2)
         const float2 niv2 = __fmul2_rn(__fmul2_rn(make_float2(-1.f, -1.f), iv), iv);
-        dfb = __fmul2_rn(__fmul2_rn(make_float2(eta, eta), __ffma2_rn(va, niv2, rvr2)), tfb);
+        hfb = __ffma2_rn(va, niv2, rvr2);
+        const float2 zb = __fmul2_rn(make_float2(ce[0], ce[1]), hfb);
+        mfb = make_float2(-fabsf(zb.x), -fabsf(zb.y));
     } else {
-        dfb = __fmul2_rn(__fmul2_rn(__fmul2_rn(make_float2(eta, eta), rvr2),
-                                    __ffma2_rn(__fmul2_rn(gm, ri), iv2, make_float2(1.f, 1.f))),
-                         tfb);
+        hfb = __ffma2_rn(__fmul2_rn(gm, ri), __fmul2_rn(iv, iv), make_float2(1.f, 1.f));
+        mfb = make_float2(-fabsf(z.x) * hfb.x, -fabsf(z.y) * hfb.y);
     }
-    const float tf[2] = {tff.x, tff.y}, tb[2] = {tfb.x, tfb.y}, df[2] = {dff.x, dff.y}, db[2] = {dfb.x, dfb.y};
-    const float rr[2] = {r2.x, r2.y}, vv[2] = {v2.x, v2.y};
+    const float2 mff = make_float2(-1.5f * fabsf(z.x), -1.5f * fabsf(z.y));
+    const float2 lff = __ffma2_rn(mff, tff, tff);
+    const float2 lfb = __ffma2_rn(mfb, tfb, tfb);
+    const float tf[2] = {tff.x, tff.y}, tb[2] = {tfb.x, tfb.y}, rq[2] = {rvr2.x, rvr2.y}, hq[2] = {hfb.x, hfb.y};
+    const float rr[2] = {r2.x, r2.y}, vv[2] = {v2.x, v2.y}, lf[2] = {lff.x, lff.y}, lb[2] = {lfb.x, lfb.y};
     bool nff[2], nfb[2];
     bool any = false;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         minr2[k] = fminf(minr2[k], rr[k]);
-        const float bnd = 1.001f * best[k];
-        nff[k] = tf[k] < bnd * (1.f + fabsf(df[k]));
-        nfb[k] = (vv[k] > 0.f) && (tb[k] < bnd * (1.f + fabsf(db[k])));
+        nff[k] = !(lf[k] >= bnd[k]);
+        nfb[k] = (vv[k] > 0.f) && !(lb[k] >= bnd[k]);
         any = any || nff[k] || nfb[k];
     }
     if (__any_sync(0xffffffffu, any)) {
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             float t = INFINITY;
-            if (nff[k]) t = tf[k] * symf<(SYM & 3)>(df[k]);
-            if (nfb[k]) t = fminf(t, tb[k] * symf<(SYM & 3)>(db[k]));
+            if (nff[k]) t = tf[k] * symf<(SYM & 3)>(eta15 * rq[k] * tf[k]);
+            if (nfb[k]) {
+                const float dfb = (SYM & 4) ? eta * hq[k] * tb[k] : eta * rq[k] * hq[k] * tb[k];
+                t = fminf(t, tb[k] * symf<(SYM & 3)>(dfb));
+            }
             best[k] = fminf(best[k], t);
+            bnd[k] = 1.001f * best[k];
+            ce[k] = bnd[k] * eta;
         }
     }
 }
@@ -1246,6 +1267,7 @@ __device__ __forceinline__ void tstep_mixed_body(const float4 *__restrict__ irec
         P.naz = make_float2(-I.az[0], -I.az[1]);
         float (&best2)[2] = *reinterpret_cast<float(*)[2]>(best);
         float (&minr22)[2] = *reinterpret_cast<float(*)[2]>(minr2);
+        float bnd[2] = {INFINITY, INFINITY}, ce[2] = {INFINITY, INFINITY};
         for (int j0 = jb; j0 < je; j0 += TJ) {
             const int cnt = min(TJ, je - j0);
             __syncthreads();
@@ -1271,11 +1293,11 @@ __device__ __forceinline__ void tstep_mixed_body(const float4 *__restrict__ irec
                     for (int u = 0; u < 4; ++u)
                         tstep_x2_j<SYM>(sA[jj + u], sB[jj + u], sC[jj + u], sV0[jj + u], sV1[jj + u],
                                         (SYM & 4) ? sW0[jj + u] : zero4, (SYM & 4) ? sW1[jj + u] : zero4, P, eta,
-                                        eta15, best2, minr22);
+                                        eta15, best2, minr22, bnd, ce);
                 }
                 for (; jj < cnt; ++jj)
                     tstep_x2_j<SYM>(sA[jj], sB[jj], sC[jj], sV0[jj], sV1[jj], (SYM & 4) ? sW0[jj] : zero4,
-                                    (SYM & 4) ? sW1[jj] : zero4, P, eta, eta15, best2, minr22);
+                                    (SYM & 4) ? sW1[jj] : zero4, P, eta, eta15, best2, minr22, bnd, ce);
             } else {
                 // the i = j pair masked by list position: the scalar body on rebuilt records
                 for (int jj = 0; jj < cnt; ++jj) {
@@ -1286,6 +1308,11 @@ __device__ __forceinline__ void tstep_mixed_body(const float4 *__restrict__ irec
                     float4 JA = zero4;
                     if (SYM & 4) JA = make_float4(sW0[jj].x, sW0[jj].z, sW1[jj].x, 0.f);
                     tstep_mixed_j<ILP, SYM, true>(J0, J1, JV, JA, I, eta, eta15, j0 + jj, ipos, best, minr2);
+                }
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    bnd[k] = 1.001f * best[k];
+                    ce[k] = bnd[k] * eta;
                 }
             }
         }

@@ -244,12 +244,17 @@ frost_status frost_set_timing(frost_ctx *ctx, int32_t enable);
 
 /* Autotuner of the pair kernels' launch shapes (the paper has no counterpart; its kernels use
  * one fixed layout).  For every power-of-two set size 2^k, 512 <= 2^k <= N, and each pass
- * kind (0 = Newtonian, 1 = gradient, 2 = time-step), it times an intra-set pass over the
- * context's particles 0 .. 2^k-1 with the j-split chosen for at most 1, 2, 4, 8 or 16 full
- * waves of blocks, and keeps the fastest.  Later passes with an active list of [2^k, 2^(k+1))
- * particles use that choice.  Synchronous.  Results are unchanged to rounding: only the
- * split of the sources (the summation order of the partials) differs.
- * waves_out: NULL, or int32[3][32] receiving the chosen bound per kind and k (0 = untuned). */
+ * kind (0 = Newtonian, 1 = gradient, 2 = time-step), it times an intra-set pass and its
+ * finalisation over the context's particles 0 .. 2^k-1 with the j-split chosen for at most
+ * 1, 2, 4, 8 or 16 full waves of blocks, and keeps the fastest.  In the mixed mode each bound
+ * is timed with two kernel layouts: 128 threads and 128-source tiles, and one warp and
+ * 32-source tiles (the small-tile layout, which spreads a pass of a few hundred particles
+ * over all SMs).  Later passes with an active list of [2^k, 2^(k+1)) particles use that
+ * choice; untuned sizes take 8 waves, and the small-tile layout where the other cannot fill
+ * one wave.  Synchronous.  Results are unchanged to rounding: only the split of the sources
+ * (the summation order of the partials) differs.
+ * waves_out: NULL, or int32[3][32] receiving the chosen bound per kind and k (0 = untuned;
+ * negative = the small-tile layout with that many waves). */
 frost_status frost_autotune(frost_ctx *ctx, int32_t *waves_out);
 
 /* Wait for all work of the context and report the sticky device error, if any. */

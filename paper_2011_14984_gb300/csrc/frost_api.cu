@@ -149,18 +149,39 @@ int log2_floor(int n)
     return b;
 }
 
-SplitShape shape_for(const frost_ctx *c, int kind, int n_a, int n_s, int waves = 0)
+// Launch shape of a pair pass.  waves: the bound on full waves of blocks (0: the autotuned
+// or default one); small: 1 for the small-tile kernels, 0 for the 128-record ones, -1 for
+// the autotuned choice, else the default: small-tile kernels (mixed mode) when the
+// 128-record grid cannot fill one wave.  An autotuned entry is the wave bound, negated for
+// the small-tile kernels.
+SplitShape shape_for(const frost_ctx *c, int kind, int n_a, int n_s, int waves = 0, int small = -1)
 {
-    if (waves <= 0 && kind >= 0 && kind < 3) waves = c->tune_w[kind][log2_floor(std::max(n_a, 1))];
+    if (waves <= 0 && kind >= 0 && kind < 3) {
+        const int t = c->tune_w[kind][log2_floor(std::max(n_a, 1))];
+        if (t != 0) {
+            waves = std::abs(t);
+            if (small < 0) small = (t < 0) ? 1 : 0;
+        }
+    }
     if (waves <= 0) waves = 8;
-    SplitShape sh = choose_shape(n_a, n_s, ipb(c), pair_blocks_per_sm(kind, c->mixed), c->n_sm, waves);
+    if (!c->mixed) small = 0;
+    if (small < 0) {
+        const long long nblk = (n_a + ipb(c) - 1) / ipb(c);
+        const long long tiles = (n_s + PAIR_TJ - 1) / PAIR_TJ;
+        small = (nblk * tiles < (long long)pair_blocks_per_sm(kind, true) * c->n_sm) ? 1 : 0;
+    }
+    const int tj = small ? PAIR_TJ_SMALL : PAIR_TJ;
+    SplitShape sh = small ? choose_shape(n_a, n_s, PAIR_BS_SMALL * PAIR_ILP, pair_blocks_per_sm(kind, true, true),
+                                         c->n_sm, waves, tj)
+                          : choose_shape(n_a, n_s, ipb(c), pair_blocks_per_sm(kind, c->mixed), c->n_sm, waves);
+    sh.small = small;
     // keep the partials inside the scratch buffer
     const long long comps = (kind == PASS_TSTEP) ? 1 : 3;
     while ((long long)sh.nsplit * comps * n_a > (long long)c->part_elems && sh.nsplit > 1) {
-        const int tiles = (n_s + PAIR_TJ - 1) / PAIR_TJ;
+        const int tiles = (n_s + tj - 1) / tj;
         const int ns = std::max(1, sh.nsplit / 2);
         const int tps = (tiles + ns - 1) / ns;
-        sh.j_per_split = tps * PAIR_TJ;
+        sh.j_per_split = tps * tj;
         sh.nsplit = (n_s + sh.j_per_split - 1) / sh.j_per_split;
     }
     return sh;
@@ -1304,10 +1325,13 @@ frost_status frost_autotune(frost_ctx *c, int32_t *waves_out)
                     launch_pack_tstep_fp64(c->stream, c->all, n, c->x, c->v, c->m, c->N, c->G,
                                            (double4_32a *)c->recA, acc);
             }
-            // time each distinct split once (several bounds can give the same launch)
-            float tw[5];
-            int splits[5];
-            for (int q = 0; q < 5; ++q) {
+            // time each distinct launch once (several bounds can give the same one): the
+            // 128-record kernels (q < 5) and, in mixed mode, the small-tile ones (q >= 5), each
+            // pass with its finalisation, whose cost grows with the number of splits
+            const int nq = c->mixed ? 10 : 5;
+            float tw[10];
+            int splits[10];
+            for (int q = 0; q < nq; ++q) {
                 PairArgs a;
                 a.irec = c->recA;
                 a.jrec = c->recA;
@@ -1316,10 +1340,10 @@ frost_status frost_autotune(frost_ctx *c, int32_t *waves_out)
                 a.self_pass = 1;
                 a.eps2 = c->eps2;
                 a.part = c->part;
-                a.shape = shape_for(c, kind, n, n, kWaves[q]);
+                a.shape = shape_for(c, kind, n, n, kWaves[q % 5], q >= 5 ? 1 : 0);
                 splits[q] = a.shape.nsplit;
                 tw[q] = INFINITY;
-                for (int r = 0; r < q; ++r)
+                for (int r = (q / 5) * 5; r < q; ++r)
                     if (splits[r] == splits[q]) tw[q] = tw[r];
                 if (tw[q] < INFINITY) continue;
                 for (int rep = 0; rep < 4; ++rep) {
@@ -1327,6 +1351,11 @@ frost_status frost_autotune(frost_ctx *c, int32_t *waves_out)
                     if (kind == PASS_ACC) launch_acc(c->stream, c->mixed, a);
                     else if (kind == PASS_GRAD) launch_grad(c->stream, c->mixed, a);
                     else launch_tstep(c->stream, c->mixed, a, c->eta, c->sym, &c->dmisc->err);
+                    if (kind == PASS_TSTEP)
+                        launch_finalize_tau(c->stream, c->part, a.shape.nsplit, n, c->eta, c->aB, &c->dmisc->err);
+                    else
+                        launch_finalize_vec(c->stream, c->part, a.shape.nsplit, n, 1.0, c->aB, nullptr,
+                                            &c->dmisc->err, 0);
                     cudaEventRecord(e1, c->stream);
                     FROST_CUDA(cudaEventSynchronize(e1));
                     float ms = 0.f;
@@ -1334,15 +1363,17 @@ frost_status frost_autotune(frost_ctx *c, int32_t *waves_out)
                     if (rep > 0) tw[q] = std::min(tw[q], ms);  // the first launch warms the caches
                 }
             }
-            // the fastest bound, if it beats the default (8 waves) by 3%
-            int best_w = 8;
-            float best = tw[3];
-            for (int q = 0; q < 5; ++q)
-                if (tw[q] < 0.97f * tw[3] && tw[q] < best) {
+            // the fastest launch, if it beats the default (8 waves, the default kernel
+            // choice) by 3%; negative entries select the small-tile kernels
+            const int q0 = shape_for(c, kind, n, n, 8).small ? 8 : 3;
+            int best_q = q0;
+            float best = tw[q0];
+            for (int q = 0; q < nq; ++q)
+                if (tw[q] < 0.97f * tw[q0] && tw[q] < best) {
                     best = tw[q];
-                    best_w = kWaves[q];
+                    best_q = q;
                 }
-            c->tune_w[kind][k] = best_w;
+            c->tune_w[kind][k] = (best_q >= 5) ? -kWaves[best_q % 5] : kWaves[best_q];
         }
     }
     cudaEventDestroy(e0);

@@ -44,11 +44,17 @@ constexpr int PAIR_BS = 128;   // threads per block
 constexpr int PAIR_ILP = 2;    // i-particles per thread (mixed)
 constexpr int PAIR_TJ = 128;   // j-records per shared-memory tile
 constexpr int PAIR_ILP64 = 1;  // i-particles per thread (FP64)
+// small-tile instantiation of the mixed pair kernels: one warp a block, tiles of 32 sources;
+// spreads the passes of a few hundred particles over all SMs, where the 128-record layout
+// leaves most SMs idle and the rest latency-bound
+constexpr int PAIR_BS_SMALL = 32;
+constexpr int PAIR_TJ_SMALL = 32;
 
 struct SplitShape {
     int nblk_i;       // blocks along the active list
     int nsplit;       // blocks along the source list (j-split)
-    int j_per_split;  // sources per split (multiple of PAIR_TJ)
+    int j_per_split;  // sources per split (multiple of the tile size)
+    int small = 0;    // 1: the small-tile kernels (PAIR_BS_SMALL, PAIR_TJ_SMALL; mixed only)
 };
 
 struct PairArgs {
@@ -226,8 +232,9 @@ struct SubtreeArgs {
 cudaError_t launch_subtree(cudaStream_t s, bool mixed, int sym, const SubtreeArgs &a);
 
 // max_waves: at most this many full waves of blocks (the autotuner picks it per size)
-SplitShape choose_shape(int n_a, int n_s, int i_per_block, int blocks_per_sm, int n_sm, int max_waves = 8);
-int pair_blocks_per_sm(int kind, bool mixed);
+SplitShape choose_shape(int n_a, int n_s, int i_per_block, int blocks_per_sm, int n_sm, int max_waves = 8,
+                        int tj = PAIR_TJ);
+int pair_blocks_per_sm(int kind, bool mixed, bool small = false);
 int pair_i_per_block(bool mixed);
 
 }  // namespace frost

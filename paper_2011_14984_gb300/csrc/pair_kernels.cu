@@ -375,9 +375,22 @@ void launch_pack_tstep_fp64(cudaStream_t s, const int32_t *list, int n, const do
 
 int pair_i_per_block(bool mixed) { return mixed ? PAIR_BS * PAIR_ILP : PAIR_BS; }
 
-int pair_blocks_per_sm(int kind, bool mixed)
+int pair_blocks_per_sm(int kind, bool mixed, bool small)
 {
-    static int cache[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    static int cache[3][2] = {{0, 0}, {0, 0}, {0, 0}}, cache_small[3] = {0, 0, 0};
+    if (small) {
+        constexpr int B = PAIR_BS_SMALL, L = PAIR_ILP, T = PAIR_TJ_SMALL;
+        int &c = cache_small[kind];
+        if (c) return c;
+        if (kind == PASS_ACC)
+            c = std::min(occupancy_of(k_acc_mixed<B, L, T, false>, B, 0),
+                         occupancy_of(k_acc_mixed<B, L, T, false, true, true>, B, 0));
+        else if (kind == PASS_GRAD)
+            c = occupancy_of(k_grad_mixed<B, L, T>, B, 0);
+        else
+            c = occupancy_of(k_tstep_mixed<B, L, T, 0>, B, 0);
+        return c;
+    }
     int &c = cache[kind][mixed ? 1 : 0];
     if (c) return c;
     if (kind == PASS_ACC)
@@ -393,13 +406,13 @@ int pair_blocks_per_sm(int kind, bool mixed)
     return c;
 }
 
-SplitShape choose_shape(int n_a, int n_s, int i_per_block, int blocks_per_sm, int n_sm, int max_waves)
+SplitShape choose_shape(int n_a, int n_s, int i_per_block, int blocks_per_sm, int n_sm, int max_waves, int tj)
 {
     SplitShape sh;
     sh.nblk_i = (n_a + i_per_block - 1) / i_per_block;
     if (sh.nblk_i < 1) sh.nblk_i = 1;
     const long long cap = (long long)blocks_per_sm * n_sm;
-    const int tiles = (n_s + PAIR_TJ - 1) / PAIR_TJ;
+    const int tiles = (n_s + tj - 1) / tj;
     int best_split = 1;
     double best_eff = -1.0;
     // at most max_waves full waves of blocks in total, each split at least one tile
@@ -418,7 +431,7 @@ SplitShape choose_shape(int n_a, int n_s, int i_per_block, int blocks_per_sm, in
         }
     }
     const int tps = (tiles + best_split - 1) / best_split;
-    sh.j_per_split = std::max(1, tps) * PAIR_TJ;
+    sh.j_per_split = std::max(1, tps) * tj;
     sh.nsplit = std::max(1, (n_s + sh.j_per_split - 1) / sh.j_per_split);
     return sh;
 }
@@ -426,7 +439,17 @@ SplitShape choose_shape(int n_a, int n_s, int i_per_block, int blocks_per_sm, in
 void launch_acc(cudaStream_t s, bool mixed, const PairArgs &a)
 {
     const dim3 grid(a.shape.nblk_i, a.shape.nsplit);
-    if (mixed && a.accurate) {
+    if (mixed && a.shape.small) {
+        constexpr int B = PAIR_BS_SMALL, L = PAIR_ILP, T = PAIR_TJ_SMALL;
+        if (a.accurate)
+            k_acc_mixed<B, L, T, false, true, true><<<grid, B, 0, s>>>(
+                (const float4 *)a.irec, (const float4 *)a.jrec, a.n_a, a.n_s, a.shape.j_per_split, a.self_pass,
+                (float)a.eps2, a.part, nullptr, a.wmax, a.eps2, a.jlist, a.m);
+        else
+            k_acc_mixed<B, L, T, false><<<grid, B, 0, s>>>((const float4 *)a.irec, (const float4 *)a.jrec, a.n_a,
+                                                           a.n_s, a.shape.j_per_split, a.self_pass, (float)a.eps2,
+                                                           a.part, nullptr);
+    } else if (mixed && a.accurate) {
         k_acc_mixed<PAIR_BS, PAIR_ILP, PAIR_TJ, false, true, true><<<grid, PAIR_BS, 0, s>>>(
             (const float4 *)a.irec, (const float4 *)a.jrec, a.n_a, a.n_s, a.shape.j_per_split,
             a.self_pass, (float)a.eps2, a.part, nullptr, a.wmax, a.eps2, a.jlist, a.m);
@@ -445,6 +468,12 @@ void launch_wmax(cudaStream_t s, const PairArgs &a, float *wmax)
 {
     cudaMemsetAsync(wmax, 0, sizeof(float) * a.n_a, s);
     const dim3 grid(a.shape.nblk_i, a.shape.nsplit);
+    if (a.shape.small) {
+        k_wmax_mixed<PAIR_BS_SMALL, PAIR_ILP, PAIR_TJ_SMALL><<<grid, PAIR_BS_SMALL, 0, s>>>(
+            (const float4 *)a.irec, (const float4 *)a.jrec, a.n_a, a.n_s, a.shape.j_per_split, a.self_pass,
+            (float)a.eps2, wmax);
+        return;
+    }
     k_wmax_mixed<PAIR_BS, PAIR_ILP, PAIR_TJ><<<grid, PAIR_BS, 0, s>>>(
         (const float4 *)a.irec, (const float4 *)a.jrec, a.n_a, a.n_s, a.shape.j_per_split, a.self_pass,
         (float)a.eps2, wmax);
@@ -453,7 +482,11 @@ void launch_wmax(cudaStream_t s, const PairArgs &a, float *wmax)
 void launch_grad(cudaStream_t s, bool mixed, const PairArgs &a)
 {
     const dim3 grid(a.shape.nblk_i, a.shape.nsplit);
-    if (mixed)
+    if (mixed && a.shape.small)
+        k_grad_mixed<PAIR_BS_SMALL, PAIR_ILP, PAIR_TJ_SMALL><<<grid, PAIR_BS_SMALL, 0, s>>>(
+            (const float4 *)a.irec, (const float4 *)a.jrec, a.n_a, a.n_s, a.shape.j_per_split,
+            a.self_pass, a.eps2, a.wmax, a.part);
+    else if (mixed)
         k_grad_mixed<PAIR_BS, PAIR_ILP, PAIR_TJ><<<grid, PAIR_BS, 0, s>>>(
             (const float4 *)a.irec, (const float4 *)a.jrec, a.n_a, a.n_s, a.shape.j_per_split,
             a.self_pass, a.eps2, a.wmax, a.part);
@@ -467,7 +500,11 @@ void launch_tstep(cudaStream_t s, bool mixed, const PairArgs &a, double eta, int
 {
     const dim3 grid(a.shape.nblk_i, a.shape.nsplit);
 #define FROST_TSTEP_CASE(SYMV)                                                                    \
-    if (mixed)                                                                                    \
+    if (mixed && a.shape.small)                                                                   \
+        k_tstep_mixed<PAIR_BS_SMALL, PAIR_ILP, PAIR_TJ_SMALL, SYMV><<<grid, PAIR_BS_SMALL, 0, s>>>( \
+            (const float4 *)a.irec, (const float4 *)a.jrec, a.n_a, a.n_s, a.shape.j_per_split,    \
+            a.self_pass, (float)eta, a.part, err);                                                \
+    else if (mixed)                                                                               \
         k_tstep_mixed<PAIR_BS, PAIR_ILP, PAIR_TJ, SYMV><<<grid, PAIR_BS, 0, s>>>(                 \
             (const float4 *)a.irec, (const float4 *)a.jrec, a.n_a, a.n_s, a.shape.j_per_split,    \
             a.self_pass, (float)eta, a.part, err);                                                \

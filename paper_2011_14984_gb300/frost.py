@@ -243,11 +243,12 @@ def frost_set_timing(ctx, enable: bool) -> None:
 
 
 def frost_autotune(ctx):
-    """Run the launch-shape autotuner; returns {kind: {size: waves}} of the choices made."""
+    """Run the launch-shape autotuner; returns {kind: {size: waves}} of the choices made
+    (negative waves: the small-tile kernel layout)."""
     out = (ctypes.c_int32 * 96)()
     _check(load().frost_autotune(ctx, out), "frost_autotune")
     kinds = ("acc", "grad", "tstep")
-    return {kinds[q]: {1 << k: int(out[q * 32 + k]) for k in range(32) if out[q * 32 + k] > 0}
+    return {kinds[q]: {1 << k: int(out[q * 32 + k]) for k in range(32) if out[q * 32 + k] != 0}
             for q in range(3)}
 
 

@@ -253,7 +253,9 @@ frost_status frost_set_timing(frost_ctx *ctx, int32_t enable);
  * choice; untuned sizes take 8 waves, and the small-tile layout where the other cannot fill
  * one wave.  Synchronous.  Results are unchanged to rounding: only the split of the sources
  * (the summation order of the partials) differs.
- * waves_out: NULL, or int32[3][32] receiving the chosen bound per kind and k (0 = untuned;
+ * In the mixed mode, the Newtonian pass that feeds a gradient (its wmax prepass and
+ * deferred double-float terms) is tuned as a fourth kind (3).
+ * waves_out: NULL, or int32[4][32] receiving the chosen bound per kind and k (0 = untuned;
  * negative = the small-tile layout with that many waves). */
 frost_status frost_autotune(frost_ctx *ctx, int32_t *waves_out);
 

@@ -77,6 +77,11 @@ constexpr size_t kRecBytes = 96;
 constexpr int64_t kBatchTeamMinN = 768;
 constexpr int kBatchTeamBlocks = 8;
 
+// autotuner rows: the pass kinds, and the Newtonian pass that feeds a gradient (mixed mode:
+// its wmax prepass and deferred double-float terms give it a cost profile of its own)
+constexpr int TUNE_ACC_ACCURATE = 3;
+constexpr int TUNE_ROWS = 4;
+
 struct frost_ctx {
     int N = 0;
     double G = 1.0, eta = 0.2, eps2 = 0.0;
@@ -132,7 +137,7 @@ struct frost_ctx {
     bool timing = false;
     // autotuned wave bound of the j-split per pass kind (0 acc, 1 grad, 2 time-step) and
     // floor(log2 n_active); 0 = the default bound
-    int tune_w[3][32] = {};
+    int tune_w[TUNE_ROWS][32] = {};
     std::vector<Timed> pending;
     std::vector<cudaEvent_t> event_pool;
     int host_error = 0;  // sticky error already reported
@@ -154,10 +159,12 @@ int log2_floor(int n)
 // the autotuned choice, else the default: small-tile kernels (mixed mode) when the
 // 128-record grid cannot fill one wave.  An autotuned entry is the wave bound, negated for
 // the small-tile kernels.
-SplitShape shape_for(const frost_ctx *c, int kind, int n_a, int n_s, int waves = 0, int small = -1)
+SplitShape shape_for(const frost_ctx *c, int kind, int n_a, int n_s, int waves = 0, int small = -1,
+                     int row = -1)
 {
-    if (waves <= 0 && kind >= 0 && kind < 3) {
-        const int t = c->tune_w[kind][log2_floor(std::max(n_a, 1))];
+    if (row < 0) row = kind;
+    if (waves <= 0 && row >= 0 && row < TUNE_ROWS) {
+        const int t = c->tune_w[row][log2_floor(std::max(n_a, 1))];
         if (t != 0) {
             waves = std::abs(t);
             if (small < 0) small = (t < 0) ? 1 : 0;
@@ -323,7 +330,7 @@ void pass_acc(frost_ctx *c, const int32_t *A, int nA, const int32_t *B, int nB, 
     a.self_pass = self ? 1 : 0;
     a.eps2 = c->eps2;
     a.part = c->part;
-    a.shape = shape_for(c, PASS_ACC, nA, nB);
+    a.shape = shape_for(c, PASS_ACC, nA, nB, 0, -1, accurate ? TUNE_ACC_ACCURATE : PASS_ACC);
     a.accurate = accurate;
     a.wmax = accurate ? wmax : nullptr;
     a.jlist = B;
@@ -1304,7 +1311,9 @@ frost_status frost_autotune(frost_ctx *c, int32_t *waves_out)
     FROST_CUDA(cudaEventCreate(&e1));
     for (int k = 9; (1 << k) <= c->N && k < 31; ++k) {
         const int n = 1 << k;
-        for (int kind = 0; kind < 3; ++kind) {
+        for (int row = 0; row < (c->mixed ? TUNE_ROWS : 3); ++row) {
+            const int kind = (row == TUNE_ACC_ACCURATE) ? PASS_ACC : row;
+            const bool accurate = (row == TUNE_ACC_ACCURATE);
             // records of particles 0 .. n-1 (zero accelerations for the gradient records)
             if (kind == PASS_ACC) {
                 pack_pos(c, c->all, n, c->recA);
@@ -1341,6 +1350,10 @@ frost_status frost_autotune(frost_ctx *c, int32_t *waves_out)
                 a.eps2 = c->eps2;
                 a.part = c->part;
                 a.shape = shape_for(c, kind, n, n, kWaves[q % 5], q >= 5 ? 1 : 0);
+                a.accurate = accurate;
+                a.wmax = accurate ? c->wA : nullptr;
+                a.jlist = c->all;
+                a.m = c->m;
                 splits[q] = a.shape.nsplit;
                 tw[q] = INFINITY;
                 for (int r = (q / 5) * 5; r < q; ++r)
@@ -1348,6 +1361,7 @@ frost_status frost_autotune(frost_ctx *c, int32_t *waves_out)
                 if (tw[q] < INFINITY) continue;
                 for (int rep = 0; rep < 4; ++rep) {
                     cudaEventRecord(e0, c->stream);
+                    if (accurate) launch_wmax(c->stream, a, c->wA);
                     if (kind == PASS_ACC) launch_acc(c->stream, c->mixed, a);
                     else if (kind == PASS_GRAD) launch_grad(c->stream, c->mixed, a);
                     else launch_tstep(c->stream, c->mixed, a, c->eta, c->sym, &c->dmisc->err);
@@ -1373,13 +1387,13 @@ frost_status frost_autotune(frost_ctx *c, int32_t *waves_out)
                     best = tw[q];
                     best_q = q;
                 }
-            c->tune_w[kind][k] = (best_q >= 5) ? -kWaves[best_q % 5] : kWaves[best_q];
+            c->tune_w[row][k] = (best_q >= 5) ? -kWaves[best_q % 5] : kWaves[best_q];
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (waves_out)
-        for (int q = 0; q < 3; ++q)
+        for (int q = 0; q < TUNE_ROWS; ++q)
             for (int k = 0; k < 32; ++k) waves_out[q * 32 + k] = c->tune_w[q][k];
     FROST_CUDA(cudaGetLastError());
     return sync_misc(c);

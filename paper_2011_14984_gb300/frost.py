@@ -245,11 +245,11 @@ def frost_set_timing(ctx, enable: bool) -> None:
 def frost_autotune(ctx):
     """Run the launch-shape autotuner; returns {kind: {size: waves}} of the choices made
     (negative waves: the small-tile kernel layout)."""
-    out = (ctypes.c_int32 * 96)()
+    out = (ctypes.c_int32 * 128)()
     _check(load().frost_autotune(ctx, out), "frost_autotune")
-    kinds = ("acc", "grad", "tstep")
+    kinds = ("acc", "grad", "tstep", "acc_feeding_grad")
     return {kinds[q]: {1 << k: int(out[q * 32 + k]) for k in range(32) if out[q * 32 + k] != 0}
-            for q in range(3)}
+            for q in range(4)}
 
 
 def frost_synchronize(ctx) -> None:

@@ -193,6 +193,74 @@ struct D3 {
     double x, y, z;
 };
 
+// The deferred double-float terms of a one-warp block, evaluated by all its lanes.
+// The items (k, s, lane) with s < n[k] of that lane are numbered in that order; lane l
+// evaluates items l, l + 32, ... (term(owner lane, k, s) returns the term), and every owner
+// then adds its own terms to acc[k] in slot order.  The additions, and so the sums, are those
+// of a per-thread loop over the slots, bit for bit; the per-thread loop runs as many rounds
+// as the warp's busiest lane has slots, with most lanes idle.  xbuf: 32 D3 of shared memory
+// for the warp.
+template <int ILP, class Term>
+__device__ __forceinline__ void warp_slot_terms(const int (&n)[ILP], D3 *xbuf, double (&acc)[ILP][3], Term term)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned below = (1u << lane) - 1u;
+    unsigned mask[ILP][GRAD_SLOTS];
+    int first[ILP][GRAD_SLOTS];
+    int total = 0;
+#pragma unroll
+    for (int k = 0; k < ILP; ++k)
+#pragma unroll
+        for (int s = 0; s < GRAD_SLOTS; ++s) {
+            mask[k][s] = __ballot_sync(0xffffffffu, s < n[k]);
+            first[k][s] = total;
+            total += __popc(mask[k][s]);
+        }
+    for (int base = 0; base < total; base += 32) {
+        const int q = base + (int)lane;
+        D3 t = {0.0, 0.0, 0.0};
+        if (q < total) {
+            // the group (k, s) that holds item q, and its owner: the (q - first)-th lane of the group
+            int gk = 0, gs = 0;
+#pragma unroll
+            for (int k = 0; k < ILP; ++k)
+#pragma unroll
+                for (int s = 0; s < GRAD_SLOTS; ++s)
+                    if (mask[k][s] != 0u && first[k][s] <= q) {
+                        gk = k;
+                        gs = s;
+                    }
+            unsigned mk = 0u;
+            int r = 0;
+#pragma unroll
+            for (int k = 0; k < ILP; ++k)
+#pragma unroll
+                for (int s = 0; s < GRAD_SLOTS; ++s)
+                    if (k == gk && s == gs) {
+                        mk = mask[k][s];
+                        r = q - first[k][s];
+                    }
+            for (; r > 0; --r) mk &= mk - 1u;
+            t = term(__ffs(mk) - 1, gk, gs);
+        }
+        xbuf[lane] = t;
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < ILP; ++k)
+#pragma unroll
+            for (int s = 0; s < GRAD_SLOTS; ++s)
+                if (s < n[k]) {
+                    const int qo = first[k][s] + __popc(mask[k][s] & below) - base;
+                    if (qo >= 0 && qo < 32) {
+                        acc[k][0] += xbuf[qo].x;
+                        acc[k][1] += xbuf[qo].y;
+                        acc[k][2] += xbuf[qo].z;
+                    }
+                }
+        __syncwarp();
+    }
+}
+
 // One Newtonian pair term m_j x_ji / r^3 in double-float from the float-float position
 // records (positions to 48 bits) and the FP64 mass mj (the two partners of a tight pair then
 // carry exactly opposite momenta, which the gradients of the other particles difference).
@@ -923,8 +991,23 @@ __device__ __forceinline__ void acc_mixed_body(const float4 *__restrict__ irec,
         res[k][1] = (double)hy[k] + (double)ly[k];
         res[k][2] = (double)hz[k] + (double)lz[k];
         wres[k] = wm[k];
-        if constexpr (DEFER) {
-            // deferred double-float terms, records read back from global memory (L2)
+    }
+    if constexpr (DEFER && BS == 32) {
+        // deferred double-float terms of the one-warp (small-tile) layout, shared by the lanes;
+        // source records read back from global memory (L2), the owner's own record from irec
+        __shared__ D3 s_xbuf[BS];
+        __syncwarp();
+        warp_slot_terms<ILP>(big.n, s_xbuf, res, [&](int ol, int k, int s) -> D3 {
+            const int j = big.col[(s * ILP + k) * BS + ol - tid];
+            const int i = ibase + k * BS + ol;
+            const float4 a = irec[i], b = irec[n_a + i];
+            const double mj = mstore[jlist ? jlist[j] : j];
+            return acc_term_df(jrec[j], jrec[n_s + j], a.x, a.y, a.z, b.x, b.y, b.z, mj, eps2d);
+        });
+    } else if constexpr (DEFER) {
+        // deferred double-float terms, per thread; records read back from global memory (L2)
+#pragma unroll
+        for (int k = 0; k < ILP; ++k)
 #pragma unroll
             for (int s = 0; s < GRAD_SLOTS; ++s) {
                 if (s < big.n[k]) {
@@ -937,7 +1020,6 @@ __device__ __forceinline__ void acc_mixed_body(const float4 *__restrict__ irec,
                     res[k][2] += t.z;
                 }
             }
-        }
     }
 }
 
@@ -1196,20 +1278,50 @@ __device__ __forceinline__ void grad_mixed_body(const float4 *__restrict__ irec,
     }
     }
     // deferred double-float terms, records read back from global memory (L2)
+    if constexpr (SMEM_SLOTS && BS == 32) {
+        // the one-warp (small-tile) layout: shared by the lanes; the owner's records from irec
+        double b[ILP][3];
 #pragma unroll
-    for (int k = 0; k < ILP; ++k) {
-        double bx = 0.0, by = 0.0, bz = 0.0;
+        for (int k = 0; k < ILP; ++k) b[k][0] = b[k][1] = b[k][2] = 0.0;
+        __shared__ D3 s_xbuf[BS];
+        __syncwarp();
+        warp_slot_terms<ILP>(big.n, s_xbuf, b, [&](int ol, int k, int s) -> D3 {
+            const int j = big.col[(s * ILP + k) * BS + ol - tid];
+            const int i = ibase + k * BS + ol;
+            const float4 q0 = irec[i], q1 = irec[n_a + i], q2 = irec[2 * n_a + i], q3 = irec[3 * n_a + i];
+            GradMixedI<1> O;
+            O.xh[0] = q0.x; O.yh[0] = q0.y; O.zh[0] = q0.z;
+            O.xm[0] = q1.x; O.ym[0] = q1.y; O.zm[0] = q1.z; O.ahx[0] = q1.w;
+            O.xl[0] = q2.x; O.yl[0] = q2.y; O.zl[0] = q2.z; O.ahy[0] = q2.w;
+            O.ahz[0] = q3.x; O.alx[0] = q3.y; O.aly[0] = q3.z; O.alz[0] = q3.w;
+            D3 t = {0.0, 0.0, 0.0};
+            grad_term_df<1>(jrec[j], jrec[n_s + j], jrec[2 * n_s + j], jrec[3 * n_s + j], O, 0, eps2d, t.x, t.y,
+                            t.z);
+            return t;
+        });
 #pragma unroll
-        for (int s = 0; s < GRAD_SLOTS; ++s) {
-            if (s < big.n[k]) {
-                const int j = big.get(s, k);
-                grad_term_df<ILP>(jrec[j], jrec[n_s + j], jrec[2 * n_s + j], jrec[3 * n_s + j], I, k, eps2d,
-                                  bx, by, bz);
-            }
+        for (int k = 0; k < ILP; ++k) {
+            res[k][0] = ((double)hx[k] + (double)lx[k]) + b[k][0];
+            res[k][1] = ((double)hy[k] + (double)ly[k]) + b[k][1];
+            res[k][2] = ((double)hz[k] + (double)lz[k]) + b[k][2];
         }
-        res[k][0] = ((double)hx[k] + (double)lx[k]) + bx;
-        res[k][1] = ((double)hy[k] + (double)ly[k]) + by;
-        res[k][2] = ((double)hz[k] + (double)lz[k]) + bz;
+    } else {
+        // per thread
+#pragma unroll
+        for (int k = 0; k < ILP; ++k) {
+            double bx = 0.0, by = 0.0, bz = 0.0;
+#pragma unroll
+            for (int s = 0; s < GRAD_SLOTS; ++s) {
+                if (s < big.n[k]) {
+                    const int j = big.get(s, k);
+                    grad_term_df<ILP>(jrec[j], jrec[n_s + j], jrec[2 * n_s + j], jrec[3 * n_s + j], I, k, eps2d,
+                                      bx, by, bz);
+                }
+            }
+            res[k][0] = ((double)hx[k] + (double)lx[k]) + bx;
+            res[k][1] = ((double)hy[k] + (double)ly[k]) + by;
+            res[k][2] = ((double)hz[k] + (double)lz[k]) + bz;
+        }
     }
 }
 

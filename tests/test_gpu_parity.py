@@ -112,6 +112,41 @@ def test_accel_gradient_cross_pass(precision):
     f.close()
 
 
+def test_accel_gradient_cross_pass_full_slots():
+    """A cross pass in which every deferred slot fills: 640 particles of the outskirts of a
+    Plummer sphere against the 96 particles nearest its centre.  Seen from afar the core's
+    terms are all within a factor 16 of the largest, so each particle has more candidates than
+    its 8 double-float slots in every j-split (the rest stay in the FP32 sums), and the
+    one-warp kernels share several rounds of deferred terms per warp."""
+    n = 2000
+    m, x, v = ics.plummer(n, 23)
+    r = np.linalg.norm(x, axis=1)
+    order = np.argsort(r).astype(np.int32)
+    B = np.sort(order[:96])
+    A = np.sort(order[-640:])
+    assert r[A].min() > 4 * r[B].max()
+    f = F(m, x, v, precision="mixed")
+    out = f.accel_gradient(A, B, eps_grad=0.05)
+    a_ref, g_ref = oracle_g(m, x, A, B)
+    ea, eg = rel(cpu(out["acc"]), a_ref), rel(cpu(out["grad"]), g_ref)
+    assert p999(ea) < 1e-6 and p999(eg) < 1e-6, (p999(ea), p999(eg))
+    # the reverse pass, the core against the outskirts, also fills every slot; but the shell
+    # of sources nearly cancels its own pull (sum_j |term| / |a| reaches 140 here), so it is
+    # held to the bound of a floating-point sum: 1e-7 of the sum of the terms' magnitudes
+    out = f.accel_gradient(B, A, eps_grad=0.05)
+    a_ref, g_ref = oracle_g(m, x, B, A)
+    a_src = oracle.acc(m, x, A, B)
+    d = x[A][None, :, :] - x[B][:, None, :]
+    ri = 1.0 / np.linalg.norm(d, axis=2)
+    Sa = (m[A][None, :] * ri ** 2).sum(1)
+    da = a_src[None, :, :] - a_ref[:, None, :]
+    tg = (m[A][None, :] * ri ** 3)[..., None] * (da - 3.0 * ((d * da).sum(2) * ri ** 2)[..., None] * d)
+    Sg = 2.0 * np.linalg.norm(tg, axis=2).sum(1)
+    assert np.all(np.linalg.norm(cpu(out["acc"]) - a_ref, axis=1) < 1e-7 * Sa)
+    assert np.all(np.linalg.norm(cpu(out["grad"]) - g_ref, axis=1) < 1e-7 * Sg)
+    f.close()
+
+
 @pytest.mark.parametrize("seed", [1, 2, 3, 4])
 def test_accel_gradient_mixed_across_seeds(seed):
     """The mixed bar on four equal-mass Plummer spheres of N = 8192 (a full-set pass and a

@@ -1428,35 +1428,35 @@ __device__ __forceinline__ void tstep_mixed_body(const float4 *__restrict__ irec
                 }
             }
         }
-        return;
-    }
-    for (int j0 = jb; j0 < je; j0 += TJ) {
-        const int cnt = min(TJ, je - j0);
-        __syncthreads();
-        for (int t = tid; t < cnt; t += BS) {
-            s0[t] = jrec[j0 + t];
-            s1[t] = jrec[n_s + j0 + t];
-            sv[t] = jrec[2 * n_s + j0 + t];
-            if (SYM & 4) sa[t] = jrec[3 * n_s + j0 + t];
-        }
-        __syncthreads();
-        const bool diag = self_pass && (j0 < ibase + BS * ILP) && (ibase < j0 + cnt);
-        int jj = 0;
-        if (!diag) {
-            for (; jj + 4 <= cnt; jj += 4) {
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    tstep_mixed_j<ILP, SYM, false>(s0[jj + u], s1[jj + u], sv[jj + u],
-                                                   (SYM & 4) ? sa[jj + u] : zero4, I, eta, eta15, 0, ipos,
-                                                   best, minr2);
+    } else {
+        for (int j0 = jb; j0 < je; j0 += TJ) {
+            const int cnt = min(TJ, je - j0);
+            __syncthreads();
+            for (int t = tid; t < cnt; t += BS) {
+                s0[t] = jrec[j0 + t];
+                s1[t] = jrec[n_s + j0 + t];
+                sv[t] = jrec[2 * n_s + j0 + t];
+                if (SYM & 4) sa[t] = jrec[3 * n_s + j0 + t];
             }
-            for (; jj < cnt; ++jj)
-                tstep_mixed_j<ILP, SYM, false>(s0[jj], s1[jj], sv[jj], (SYM & 4) ? sa[jj] : zero4, I, eta, eta15,
-                                               0, ipos, best, minr2);
-        } else {
-            for (; jj < cnt; ++jj)
-                tstep_mixed_j<ILP, SYM, true>(s0[jj], s1[jj], sv[jj], (SYM & 4) ? sa[jj] : zero4, I, eta, eta15,
-                                              j0 + jj, ipos, best, minr2);
+            __syncthreads();
+            const bool diag = self_pass && (j0 < ibase + BS * ILP) && (ibase < j0 + cnt);
+            int jj = 0;
+            if (!diag) {
+                for (; jj + 4 <= cnt; jj += 4) {
+    #pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        tstep_mixed_j<ILP, SYM, false>(s0[jj + u], s1[jj + u], sv[jj + u],
+                                                       (SYM & 4) ? sa[jj + u] : zero4, I, eta, eta15, 0, ipos,
+                                                       best, minr2);
+                }
+                for (; jj < cnt; ++jj)
+                    tstep_mixed_j<ILP, SYM, false>(s0[jj], s1[jj], sv[jj], (SYM & 4) ? sa[jj] : zero4, I, eta, eta15,
+                                                   0, ipos, best, minr2);
+            } else {
+                for (; jj < cnt; ++jj)
+                    tstep_mixed_j<ILP, SYM, true>(s0[jj], s1[jj], sv[jj], (SYM & 4) ? sa[jj] : zero4, I, eta, eta15,
+                                                  j0 + jj, ipos, best, minr2);
+            }
         }
     }
 }

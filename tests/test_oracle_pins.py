@@ -280,6 +280,25 @@ def test_symmetrisation_factor_properties():
             assert s <= sa * (1 + 1e-15)
 
 
+def test_symmetrisation_factor_lower_bound():
+    """Both symmetrisation factors of Eq. time-step-factor obey s(d) >= 1 / (1 + |d|): the
+    time-step passes skip a pair criterion t whenever t >= 1.001 best (1 + |d|), which is
+    exact only if no factor can fall below that bound.  Checked over 20 decades of |d| of
+    both signs and across the arithmetic branch point.  The bound is tight for the harmonic
+    factor as d -> -inf (s -> 1/|d|), so the skip test needs its 0.1 % margin for rounding."""
+    mag = np.logspace(-10, 10, 2001)
+    ds = np.concatenate([-mag, [0.0], mag, [2.0 - 1e-12, 2.0, 2.0 + 1e-12, -2.0]])
+    for d in ds:
+        lo = 1.0 / (1.0 + abs(d))
+        assert oracle.sym_harmonic(d) > lo * (1 - 1e-15), d
+        assert oracle.sym_arithmetic(d) > lo * (1 - 1e-15), d
+    # tight: s (1 + |d|) -> 1 from above for the harmonic factor as d -> -inf, while the
+    # arithmetic one keeps a factor 2
+    for d in (-1e4, -1e6, -1e8):
+        assert 1.0 < oracle.sym_harmonic(d) * (1.0 + abs(d)) < 1.0 + 2.0 / abs(d)
+        assert abs(oracle.sym_arithmetic(d) * (1.0 + abs(d)) - 2.0) < 2.0 / abs(d)
+
+
 def test_circular_binary_timestep_is_eta_period_over_two_pi():
     """Eq. eta-two-pi: both criteria give tau = eta P / (2 pi) for a circular binary."""
     for (m1, m2, a, G, eta) in [(0.5, 0.5, 1.0, 1.0, 0.2), (10.0, 10.0, 10.0, 39.47, 0.01),

@@ -269,7 +269,7 @@ void frost_destroy(frost_ctx *ctx);
 /* Message of the last failure in the calling thread ("" if none). */
 const char *frost_last_error(void);
 
-/* Library version string. */
+/* Library version string.  0.2: frost_autotune writes int32[4][32] (was [3][32]). */
 const char *frost_version(void);
 
 /*

@@ -749,7 +749,7 @@ void frost_default_opts(frost_opts *opt)
 
 const char *frost_last_error(void) { return g_last_error.c_str(); }
 
-const char *frost_version(void) { return "frost-gb300 0.1 (sm_103a)"; }
+const char *frost_version(void) { return "frost-gb300 0.2 (sm_103a)"; }
 
 static frost_status init_impl(frost_ctx **out, int64_t n, const double *m, const double *x,
                               const double *v, double G, double eta, const frost_opts *opt,

@@ -280,6 +280,30 @@ def test_symmetrisation_factor_properties():
             assert s <= sa * (1 + 1e-15)
 
 
+def test_arithmetic_factor_at_and_above_two_symmetrises_the_lowered_step():
+    """Sec. 4.2: the arithmetic mean is usable only while the step's derivative d is below 2,
+    and for larger d the step is lowered until it is.  Reading: the step tau is scaled by
+    lam = 1 / d, so the lowered step lam tau has the derivative d' = lam d = 1, and that step
+    is symmetrised with the arithmetic mean.  Pinned against the mean-value definition itself,
+    tau_sym = (tau'(t) + tau'(t + tau_sym)) / 2 with tau'(t + h) = lam tau + d' h to first
+    order, solved here for tau = 1 independently of the oracle's formula: a slip in the
+    branch (1/d, 1/(d - 1), 2/(d - 1), a missing lam) leaves a residual of order 1/d."""
+    for d in np.concatenate([[2.0, 2.0 + 1e-9, 2.5, 3.0, 7.5, 64.0, 1e3, 1e6],
+                             np.logspace(np.log10(2.0), 8, 97)]):
+        s = oracle.sym_arithmetic(d)
+        lam = 1.0 / d
+        d_low = lam * d                      # derivative of the lowered step
+        assert d_low < 2.0                   # inside the range of the arithmetic mean
+        res = s - 0.5 * (lam + (lam + d_low * s))
+        assert abs(res) < 1e-14 * (s + lam), (d, s, res)
+        # the same step through the branch below 2, which the test above pins: lowering then
+        # symmetrising equals lam times the factor at the lowered derivative
+        assert abs(s - lam * oracle.sym_arithmetic(d_low)) < 1e-15 * s, d
+    # below 2 the factor is the mean of the unlowered step, and it grows without bound as d -> 2
+    assert oracle.sym_arithmetic(2.0 - 1e-9) > 1e8
+    assert oracle.sym_arithmetic(2.0) == pytest.approx(1.0, rel=1e-15)
+
+
 def test_symmetrisation_factor_lower_bound():
     """Both symmetrisation factors of Eq. time-step-factor obey s(d) >= 1 / (1 + |d|): the
     time-step passes skip a pair criterion t whenever t >= 1.001 best (1 + |d|), which is

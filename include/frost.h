@@ -269,8 +269,21 @@ void frost_destroy(frost_ctx *ctx);
 /* Message of the last failure in the calling thread ("" if none). */
 const char *frost_last_error(void);
 
-/* Library version string.  0.2: frost_autotune writes int32[4][32] (was [3][32]). */
+/* Library version string.  0.2: frost_autotune writes int32[4][32] (was [3][32]).
+ * 0.3: frost_peak_probe. */
 const char *frost_version(void);
+
+/*
+ * Throughput probe of the arithmetic pipes that bound the pair passes (the paper has no
+ * counterpart; it is the denominator of their roofline).  On the current device it times,
+ * with CUDA events on cuda_stream (NULL = legacy default stream), kernels that fill every SM
+ * at full occupancy with independent chains of one operation, and writes to out (host, 6
+ * doubles): [0] scalar FP32 FMA TFLOP/s, [1] packed FP32x2 FMA TFLOP/s (two lanes per
+ * instruction), [2] FP64 FMA TFLOP/s, [3] MUFU reciprocal square roots per second, [4] the
+ * SM count, [5] the resident threads per SM of the probe.  An FMA counts as 2 flops.  It
+ * allocates and frees a 2 KB device buffer and synchronises cuda_stream; about 50 ms.
+ */
+frost_status frost_peak_probe(double *out, void *cuda_stream);
 
 /*
  * Entry point that allocates nothing (the paper has no counterpart; it serves callers that
@@ -286,13 +299,18 @@ const char *frost_version(void);
  *  - n outside [1, FROST_NOALLOC_MAX_N] returns FROST_EINVAL; nothing is launched.
  *  - No cudaMalloc, cudaFree or other allocating call is made.
  *  - The first call on each device looks up the scratch array's device address on that
- *    device (the device current at the call); make that first call before any stream
- *    capture.
- *  - Every call shares the scratch array; calls whose GPU work may overlap (other streams or
- *    host threads without ordering) race and must be serialised by the caller.
- *  - Work runs on cuda_stream (NULL = legacy default stream) and the call synchronises it;
- *    non-finite inputs or non-positive masses give FROST_ENONFINITE, two particles at zero
- *    separation (eps_soft = 0) FROST_ECOINCIDENT.
+ *    device (the device current at the call) and keeps it for the life of the process; make
+ *    that first call before any stream capture.  A cudaDeviceReset of the device invalidates
+ *    the kept address: do not call this entry point on that device afterwards.
+ *  - Every call shares the scratch array, which keeps the previous call's contents (the only
+ *    part that must start at zero, the status word, is cleared by every call); calls whose
+ *    GPU work may overlap (other streams or host threads without ordering) race and must be
+ *    serialised by the caller.
+ *  - Work runs on cuda_stream (NULL = legacy default stream); the call synchronises that
+ *    stream before returning, to read the status word of its kernels.  Non-finite inputs or
+ *    non-positive masses give FROST_ENONFINITE, two particles at zero separation
+ *    (eps_soft = 0) FROST_ECOINCIDENT.  Every failure sets the message of
+ *    frost_last_error() (without allocating).
  */
 #define FROST_NOALLOC_MAX_N 65536
 frost_status frost_accel_noalloc(int64_t n, const double *m, const double *x, double G,

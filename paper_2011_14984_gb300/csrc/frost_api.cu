@@ -19,19 +19,31 @@
 
 using namespace frost;
 
-namespace {
+// message of the last failure in each host thread (frost_last_error); fixed storage, so that
+// setting it never allocates
+static thread_local char g_last_error[kLastErrorBytes] = {0};
 
-thread_local std::string g_last_error;
+void frost::set_last_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+}
+
+void frost::clear_last_error() { g_last_error[0] = '\0'; }
+
+namespace {
 
 frost_status fail(frost_status st, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
 frost_status fail(frost_status st, const char *fmt, ...)
 {
-    char buf[512];
+    char buf[kLastErrorBytes];
     va_list ap;
     va_start(ap, fmt);
     vsnprintf(buf, sizeof(buf), fmt, ap);
     va_end(ap);
-    g_last_error = buf;
+    set_last_error("%s", buf);
     return st;
 }
 
@@ -747,9 +759,9 @@ void frost_default_opts(frost_opts *opt)
     opt->integrator = FROST_HHS_FSI;
 }
 
-const char *frost_last_error(void) { return g_last_error.c_str(); }
+const char *frost_last_error(void) { return g_last_error; }
 
-const char *frost_version(void) { return "frost-gb300 0.2 (sm_103a)"; }
+const char *frost_version(void) { return "frost-gb300 0.3 (sm_103a)"; }
 
 static frost_status init_impl(frost_ctx **out, int64_t n, const double *m, const double *x,
                               const double *v, double G, double eta, const frost_opts *opt,
@@ -765,7 +777,7 @@ frost_status frost_init_batch(frost_ctx **out, int32_t n_clusters, const int64_t
                               const double *m, const double *x, const double *v, double G, double eta,
                               const frost_opts *opt)
 {
-    g_last_error.clear();
+    clear_last_error();
     if (!out) return fail(FROST_EINVAL, "ctx pointer is NULL");
     *out = nullptr;
     if (n_clusters < 1 || !offsets) return fail(FROST_EINVAL, "need n_clusters >= 1 and offsets");
@@ -779,7 +791,7 @@ static frost_status init_impl(frost_ctx **out, int64_t n, const double *m, const
                               const double *v, double G, double eta, const frost_opts *opt,
                               int32_t n_clusters, const int64_t *offsets)
 {
-    g_last_error.clear();
+    clear_last_error();
     if (!out) return fail(FROST_EINVAL, "ctx pointer is NULL");
     *out = nullptr;
     if (n < 1 || n >= (int64_t(1) << 31)) return fail(FROST_EINVAL, "n = %lld out of range", (long long)n);
@@ -911,7 +923,11 @@ static frost_status init_impl(frost_ctx **out, int64_t n, const double *m, const
     launch_check_mass(c->stream, c->m, (int)n, &c->dmisc->err);
     INIT_CUDA(cudaGetLastError());
     const frost_status st = sync_misc(c);
-    if (st != FROST_OK) return bail(fail(st, "initial state rejected: %s", g_last_error.c_str()));
+    if (st != FROST_OK) {
+        char why[kLastErrorBytes];
+        snprintf(why, sizeof(why), "%s", g_last_error);
+        return bail(fail(st, "initial state rejected: %s", why));
+    }
 #undef INIT_CUDA
     *out = c;
     return FROST_OK;
@@ -1411,7 +1427,7 @@ frost_status frost_clear_error(frost_ctx *c)
     if (!c) return fail(FROST_EINVAL, "NULL context");
     FROST_CUDA(cudaMemsetAsync(&c->dmisc->err, 0, sizeof(int), c->stream));
     FROST_CUDA(cudaStreamSynchronize(c->stream));
-    g_last_error.clear();
+    clear_last_error();
     return FROST_OK;
 }
 

@@ -26,6 +26,12 @@
 
 namespace frost {
 
+// Message of the last failure in the calling host thread, returned by frost_last_error();
+// kept in fixed thread-local storage (formatting it allocates nothing).
+constexpr int kLastErrorBytes = 512;
+void set_last_error(const char *fmt, ...) __attribute__((format(printf, 1, 2)));
+void clear_last_error();
+
 // device error word bits
 enum : int {
     ERR_NONFINITE = 1 << 0,

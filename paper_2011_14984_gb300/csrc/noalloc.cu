@@ -12,6 +12,9 @@
 //     The only part that must start at zero, the error word, is cleared by each call.
 //   - Two calls whose GPU work overlaps (different streams or host threads, no ordering between
 //     them) race on the array and give wrong results. Serialise them.
+//   - The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+//     make that call before any stream capture.  Every call synchronises its stream before it
+//     returns, to read the status word of its kernels.
 //
 // The kernels are the ones the context-based path launches (pack, the FP32 pair kernel with
 // float-float separations and compensated sums, the FP64 finalisation); only the scratch and
@@ -20,9 +23,9 @@
 #include "frost_internal.cuh"
 
 #include <cmath>
+#include <cstdarg>
 #include <cstdio>
 #include <mutex>
-#include <string>
 
 using namespace frost;
 
@@ -39,27 +42,38 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 std::mutex g_setup_mutex;
 unsigned char *g_scratch_ptr[kMaxDevices] = {nullptr};
 int g_num_sm[kMaxDevices] = {0};
-// failures are reported by status code only (no message state to keep)
-frost_status noalloc_fail(frost_status st, const std::string &)
+// A failure sets the calling thread's message (frost_last_error) in its fixed thread-local
+// storage and returns the status; nothing is allocated.
+frost_status noalloc_fail(frost_status st, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+frost_status noalloc_fail(frost_status st, const char *fmt, ...)
 {
+    char buf[kLastErrorBytes];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    set_last_error("frost_accel_noalloc: %s", buf);
     return st;
 }
 
 // One-time set-up per device, with that device current: the device address of the scratch
-// array (the host-side symbol is only a stand-in) and the SM count.
+// array (the host-side symbol is only a stand-in) and the SM count.  The address is kept for
+// the life of the process; a cudaDeviceReset of that device unloads the library's device code,
+// after which the kept address is stale, so the entry point must not be used on that device
+// again.
 frost_status setup_device(int dev, unsigned char **scratch, int *nsm)
 {
-    if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(FROST_ECUDA, "device index out of range");
+    if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(FROST_ECUDA, "device index %d out of range", dev);
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_scratch_ptr[dev]) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p)
-            return noalloc_fail(FROST_ECUDA, std::string("cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+            return noalloc_fail(FROST_ECUDA, "cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
         int n = 0;
         const cudaError_t e2 = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         if (e2 != cudaSuccess || n <= 0)
-            return noalloc_fail(FROST_ECUDA, std::string("SM count query failed: ") + cudaGetErrorString(e2));
+            return noalloc_fail(FROST_ECUDA, "SM count query failed: %s", cudaGetErrorString(e2));
         g_num_sm[dev] = n;
         g_scratch_ptr[dev] = (unsigned char *)p;
     }
@@ -89,15 +103,16 @@ __global__ void k_pack_noalloc(const double *__restrict__ x, const double *__res
 extern "C" frost_status frost_accel_noalloc(int64_t n, const double *m, const double *x, double G,
                                             double eps_soft, double *acc, void *cuda_stream)
 {
+    clear_last_error();
     if (n < 1 || n > kNoallocMaxN)
-        return noalloc_fail(FROST_EINVAL, "n = " + std::to_string((long long)n) + " outside [1, " +
-                                              std::to_string(kNoallocMaxN) + "] (the size of the static scratch)");
+        return noalloc_fail(FROST_EINVAL, "n = %lld outside [1, %d] (the size of the static scratch)", (long long)n,
+                            kNoallocMaxN);
     if (!m || !x || !acc) return noalloc_fail(FROST_EINVAL, "m, x and acc are required");
     if (!(G > 0.0) || !std::isfinite(G) || !(eps_soft >= 0.0) || !std::isfinite(eps_soft))
         return noalloc_fail(FROST_EINVAL, "G must be finite and positive, eps_soft finite and >= 0");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return noalloc_fail(FROST_ECUDA, cudaGetErrorString(e));
+    if (e != cudaSuccess) return noalloc_fail(FROST_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     unsigned char *scratch = nullptr;
     int nsm = 0;
     const frost_status st = setup_device(dev, &scratch, &nsm);
@@ -118,9 +133,12 @@ extern "C" frost_status frost_accel_noalloc(int64_t n, const double *m, const do
         sh.j_per_split = ((tiles + ns - 1) / ns) * PAIR_TJ;
         sh.nsplit = (ni + sh.j_per_split - 1) / sh.j_per_split;
     }
+    // the partials [nsplit][3][n] and the records [2][n] must fit their parts of the array
+    if ((size_t)sh.nsplit * 3 * (size_t)ni * sizeof(double) > kPartBytes || (size_t)2 * ni * sizeof(float4) > kRecBytes)
+        return noalloc_fail(FROST_EINVAL, "internal: %d splits of %d particles exceed the static scratch", sh.nsplit, ni);
 
     e = cudaMemsetAsync(err, 0, sizeof(int), s);
-    if (e != cudaSuccess) return noalloc_fail(FROST_ECUDA, cudaGetErrorString(e));
+    if (e != cudaSuccess) return noalloc_fail(FROST_ECUDA, "clearing the error word: %s", cudaGetErrorString(e));
     k_pack_noalloc<<<(ni + 255) / 256, 256, 0, s>>>(x, m, ni, rec, err);
     PairArgs a;
     a.irec = rec;
@@ -135,11 +153,11 @@ extern "C" frost_status frost_accel_noalloc(int64_t n, const double *m, const do
     launch_finalize_vec(s, part, sh.nsplit, ni, G, nullptr, acc, err,
                         eps_soft == 0.0 ? ERR_COINCIDENT : ERR_NONFINITE);
     e = cudaGetLastError();
-    if (e != cudaSuccess) return noalloc_fail(FROST_ECUDA, cudaGetErrorString(e));
+    if (e != cudaSuccess) return noalloc_fail(FROST_ECUDA, "launch: %s", cudaGetErrorString(e));
     int herr = 0;
     e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return noalloc_fail(FROST_ECUDA, cudaGetErrorString(e));
+    if (e != cudaSuccess) return noalloc_fail(FROST_ECUDA, "reading the error word: %s", cudaGetErrorString(e));
     if (herr & ERR_COINCIDENT) return noalloc_fail(FROST_ECOINCIDENT, "two particles at zero separation");
     if (herr) return noalloc_fail(FROST_ENONFINITE, "non-finite input, non-positive mass or non-finite result");
     return FROST_OK;

@@ -90,6 +90,7 @@ _SIGS = {
     "frost_last_error": (ctypes.c_char_p, []),
     "frost_version": (ctypes.c_char_p, []),
     "frost_accel_noalloc": (ctypes.c_int, [_I64, _P, _P, _D, _D, _P, _P]),
+    "frost_peak_probe": (ctypes.c_int, [_P, _P]),
     "frost_init_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, _P, _P, _P, _P, _D, _D,
                                         ctypes.POINTER(frost_opts)]),
     "frost_energy_clusters": (ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -272,6 +273,14 @@ def frost_version() -> str:
     return load().frost_version().decode()
 
 
+def frost_peak_probe(stream=None) -> dict:
+    """Measured throughput of the pipes the pair passes run on (see include/frost.h)."""
+    out = np.zeros(6)
+    _check(load().frost_peak_probe(_ptr(out), stream), "frost_peak_probe")
+    return {"ffma_tflops": float(out[0]), "ffma2_tflops": float(out[1]), "dfma_tflops": float(out[2]),
+            "mufu_rsqrt_per_s": float(out[3]), "sms": int(out[4]), "threads_per_sm": int(out[5])}
+
+
 FROST_NOALLOC_MAX_N = 65536
 
 
@@ -279,10 +288,8 @@ def frost_accel_noalloc(n, m, x, G, eps_soft, acc, stream=None) -> None:
     """Newtonian accelerations of all n particles (device m[n], x[n][3] -> acc[n][3]) without
     any device allocation: the scratch is a static device array of FROST_NOALLOC_MAX_N
     particles shared by all calls (serialise calls whose GPU work could overlap)."""
-    code = load().frost_accel_noalloc(int(n), _ptr(m), _ptr(x), float(G), float(eps_soft),
-                                      _ptr(acc), stream)
-    if code != FROST_OK:
-        raise FrostError(code, "frost_accel_noalloc", "see include/frost.h for the status meaning")
+    _check(load().frost_accel_noalloc(int(n), _ptr(m), _ptr(x), float(G), float(eps_soft),
+                                      _ptr(acc), stream), "frost_accel_noalloc")
 
 
 # ---- convenience wrapper ---------------------------------------------------------------

@@ -718,6 +718,53 @@ def test_cluster_batch_matches_oracle_per_cluster(precision):
     f.close()
 
 
+def test_full_cluster_batch_fp64_one_step_sampled_clusters():
+    """The full 256-cluster batch (N log-uniform in 64..4096, 232818 particles) in FP64: one
+    top-level step of 2^-7 of every cluster in one launch; 16 sampled clusters (the largest
+    and the smallest among them) evolve as the oracle evolves each of them alone, positions
+    within 1e-10 and velocities within 1e-9, and every cluster keeps its momentum."""
+    off, m, x, v = ics.batch_workload("cluster_batch_256")
+    sz = np.diff(off)
+    f = F(m, x, v, precision="fp64", eta=0.2, offsets=off)
+    p0 = f.cluster_energies()["P"]
+    f.step(2.0 ** -7, 1)
+    xg, vg, t = f.state()
+    p1 = f.cluster_energies()["P"]
+    f.close()
+    assert t == pytest.approx(2.0 ** -7)
+    rng = np.random.default_rng(5)
+    pick = np.unique(np.concatenate([[int(np.argmax(sz)), int(np.argmin(sz))],
+                                     rng.choice(sz.size, 14, replace=False)]))
+    assert pick.size >= 15
+    for k in pick:
+        a, b = off[k], off[k + 1]
+        xo, vo = oracle.steps(m[a:b], x[a:b], v[a:b], 2.0 ** -7, 1, eta=0.2)
+        assert np.max(np.abs(xg[a:b] - xo)) < 1e-10, (k, sz[k], np.max(np.abs(xg[a:b] - xo)))
+        assert np.max(np.abs(vg[a:b] - vo)) < 1e-9, (k, sz[k], np.max(np.abs(vg[a:b] - vo)))
+    assert np.max(np.abs(p1 - p0)) < 1e-14
+
+
+@pytest.mark.parametrize("precision", ["fp64"])
+def test_kroupa_hard_binaries_trajectory_fp64(precision):
+    """Plummer N = 2000 with Kroupa masses and 5 % hard binaries (a in [1e-5, 1e-3], thermal
+    e; seed 31): one top-level step of 2^-10 reaches hierarchy depth 19, through the grid
+    levels, the single-block subtree solver and its one-warp path.  FP64 positions within
+    1e-10 and velocities within 1e-8 of the oracle (binary orbital speeds reach ~10), and the
+    same depth."""
+    m, x, v = ics.plummer_kroupa_binaries(2000, 31)
+    f = F(m, x, v, precision=precision, eta=0.2)
+    f.step(2.0 ** -10, 1)
+    xg, vg, _ = f.state()
+    st = f.stats()
+    f.close()
+    oracle.reset_counters()
+    xo, vo = oracle.steps(m, x, v, 2.0 ** -10, 1, eta=0.2)
+    oc = oracle.counters()
+    assert st["max_depth_seen"] == oc["max_depth"] >= 15, (st["max_depth_seen"], oc["max_depth"])
+    assert np.max(np.abs(xg - xo)) < 1e-10, np.max(np.abs(xg - xo))
+    assert np.max(np.abs(vg - vo)) < 1e-8, np.max(np.abs(vg - vo))
+
+
 # ---------------------------------------------------------------------------------------
 # the other full-size workloads, checked on sampled particles
 # ---------------------------------------------------------------------------------------

@@ -77,6 +77,12 @@ typedef struct {
     int32_t integrator; /* frost_integrator: what frost_step advances with */
     int32_t subtree_blocks; /* thread blocks that share one subtree-solver set (a thread-block
                                cluster, 1..8); 0 = default */
+    int32_t branch_streams; /* 0 (default) or 1: in every hhs_fsi call above the subtree
+                               threshold, the two fsi(S) steps run on a stream of their own,
+                               concurrently with the recursion hhs_fsi(F) on the context stream
+                               (they act on disjoint particles, so the results are those of the
+                               serial order, bit for bit); -1: everything on the context stream.
+                               With per-kernel timing on, the branches run serially. */
 } frost_opts;
 
 typedef enum {
@@ -88,7 +94,7 @@ typedef enum {
 } frost_integrator;
 
 /* Default options: mixed precision, harmonic symmetrisation, no softening, depth 40,
- * legacy default stream, subtree threshold 384, the HHS-FSI integrator. */
+ * legacy default stream, subtree threshold 384, the HHS-FSI integrator, concurrent branches. */
 void frost_default_opts(frost_opts *opt);
 
 /*
@@ -233,6 +239,9 @@ typedef struct {
      * recomputed: S has not moved since the end of the first fsi(S), whose final a^SS is
      * reused bit for bit (acc_pairs counts evaluated pairs only) */
     int64_t acc_pairs_reused;
+    /* the pair interactions evaluated inside single-block subtree-solver launches (Newtonian,
+     * gradient, time-step; also part of acc_pairs, grad_pairs and tstep_pairs) */
+    int64_t subtree_pairs[3];
 } frost_stats;
 
 frost_status frost_get_stats(frost_ctx *ctx, frost_stats *out);

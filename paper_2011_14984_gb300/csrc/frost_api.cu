@@ -14,7 +14,7 @@
 #include <cstdio>
 #include <climits>
 #include <cstring>
-#include <string>
+#include <deque>
 #include <vector>
 
 using namespace frost;
@@ -94,6 +94,20 @@ constexpr int kBatchTeamBlocks = 8;
 constexpr int TUNE_ACC_ACCURATE = 3;
 constexpr int TUNE_ROWS = 4;
 
+// A stream with the scratch that the passes issued on it write (see the pass drivers).
+struct Lane {
+    cudaStream_t s = nullptr;
+    void *recA = nullptr, *recB = nullptr;               // packed records, kRecBytes x N each
+    double *part = nullptr;                              // split partials (part_elems)
+    double *aA = nullptr, *aB = nullptr, *atA = nullptr, *atB = nullptr;  // [3][N] each
+    float *wA = nullptr, *wB = nullptr;                  // max_j m_j / r^3 per particle (mixed)
+    unsigned *hist = nullptr;                            // |a| histograms [2][HOT_BINS] (mixed)
+    uint32_t *hA = nullptr, *hB = nullptr;               // hot-source masks (mixed)
+    double *part_hot = nullptr;                          // hot-source gradient partials
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;    // branch lanes: fork / join events
+    bool owns = false;                                   // branch lanes own their buffers
+};
+
 struct frost_ctx {
     int N = 0;
     double G = 1.0, eta = 0.2, eps2 = 0.0;
@@ -144,6 +158,11 @@ struct frost_ctx {
     unsigned long long lev_seen[2][SUBTREE_STAT_LEVELS] = {};
     Misc *dmisc = nullptr, *hmisc = nullptr;
     std::vector<int32_t *> lvS, lvF;                 // per-level slow/fast lists
+    Lane main;                                       // the context stream and the buffers above
+    std::deque<Lane> branch;                         // per grid level: fsi(S) next to hhs_fsi(F)
+                                                     // (a deque: growing it keeps the lanes of
+                                                     // the outer levels in place)
+    bool branch_streams = true;                      // run the branch lanes concurrently
 
     frost_stats st{};
     bool timing = false;
@@ -222,7 +241,8 @@ struct TimedScope {
     frost_ctx *c;
     Timed t{};
     bool on;
-    TimedScope(frost_ctx *c_, int kind, int64_t pairs) : c(c_), on(c_->timing)
+    cudaStream_t s;
+    TimedScope(frost_ctx *c_, cudaStream_t s_, int kind, int64_t pairs) : c(c_), on(c_->timing), s(s_)
     {
         if (!on) return;
         t.a = get_event(c);
@@ -233,12 +253,12 @@ struct TimedScope {
             on = false;
             return;
         }
-        cudaEventRecord(t.a, c->stream);
+        cudaEventRecord(t.a, s);
     }
     ~TimedScope()
     {
         if (!on) return;
-        cudaEventRecord(t.b, c->stream);
+        cudaEventRecord(t.b, s);
         c->pending.push_back(t);
     }
 };
@@ -261,7 +281,9 @@ void resolve_timing(frost_ctx *c)
 frost_status err_to_status(int e)
 {
     if (e & ERR_DEPTH) return fail(FROST_EDEPTH, "hhs_fsi recursion deeper than max_depth");
-    if (e & ERR_COINCIDENT) return fail(FROST_ECOINCIDENT, "two distinct particles at zero separation");
+    if (e & ERR_COINCIDENT)
+        return fail(FROST_ECOINCIDENT, "a pair sum is not finite: two distinct particles at zero separation, or "
+                                       "a pair term beyond the floating-point range");
     if (e & ERR_NONFINITE) return fail(FROST_ENONFINITE, "non-finite value in a pass (or a non-positive mass / step)");
     if (e & (ERR_INDEX | ERR_DUPLICATE)) return fail(FROST_EINVAL, "index list out of range or repeated");
     if (e & ERR_TIMEOUT) return fail(FROST_ETIMEOUT, "a bounded device wait gave up");
@@ -276,6 +298,7 @@ frost_status sync_misc(frost_ctx *c)
     if (c->timing) resolve_timing(c);
     // fold the subtree solver's device counters into the statistics
     const unsigned long long *sub = c->hmisc->sub;
+    for (int k = 0; k < 3; ++k) c->st.subtree_pairs[k] += (int64_t)(sub[k] - c->sub_seen[k]);
     c->st.acc_pairs += (int64_t)(sub[0] - c->sub_seen[0]);
     c->st.grad_pairs += (int64_t)(sub[1] - c->sub_seen[1]);
     c->st.tstep_pairs += (int64_t)(sub[2] - c->sub_seen[2]);
@@ -293,12 +316,57 @@ frost_status sync_misc(frost_ctx *c)
     return err_to_status(c->hmisc->err);
 }
 
-// ---- pass drivers ------------------------------------------------------------------------
-
-void pack_pos(frost_ctx *c, const int32_t *L, int n, void *rec)
+// Buffers of a branch lane, the sizes of the main lane's (the context's) buffers.
+frost_status alloc_lane_buffers(frost_ctx *c, Lane &L)
 {
-    if (c->mixed) launch_pack_pos_mixed(c->stream, L, n, c->x, c->m, c->N, (float4 *)rec);
-    else launch_pack_pos_fp64(c->stream, L, n, c->x, c->m, c->N, (double4_32a *)rec);
+    const size_t N = (size_t)c->N;
+    L.owns = true;
+    FROST_CUDA(cudaMalloc(&L.recA, kRecBytes * N));
+    FROST_CUDA(cudaMalloc(&L.recB, kRecBytes * N));
+    FROST_CUDA(cudaMalloc(&L.part, sizeof(double) * c->part_elems));
+    FROST_CUDA(cudaMalloc(&L.aA, sizeof(double) * 3 * N));
+    FROST_CUDA(cudaMalloc(&L.aB, sizeof(double) * 3 * N));
+    FROST_CUDA(cudaMalloc(&L.atA, sizeof(double) * 3 * N));
+    FROST_CUDA(cudaMalloc(&L.atB, sizeof(double) * 3 * N));
+    FROST_CUDA(cudaMalloc(&L.wA, sizeof(float) * N));
+    FROST_CUDA(cudaMalloc(&L.wB, sizeof(float) * N));
+    if (c->mixed) {
+        const size_t words = (N + 31) / 32;
+        FROST_CUDA(cudaMalloc(&L.hist, sizeof(unsigned) * 2 * HOT_BINS));
+        FROST_CUDA(cudaMalloc(&L.hA, sizeof(uint32_t) * words));
+        FROST_CUDA(cudaMalloc(&L.hB, sizeof(uint32_t) * words));
+        FROST_CUDA(cudaMalloc(&L.part_hot, sizeof(double) * c->part_hot_elems));
+    }
+    return FROST_OK;
+}
+
+void free_lane(Lane &L)
+{
+    if (L.owns) {
+        void *dev[] = {L.recA, L.recB, L.part, L.aA, L.aB, L.atA, L.atB, L.wA, L.wB, L.hist, L.hA, L.hB,
+                       L.part_hot};
+        for (void *p : dev)
+            if (p) cudaFree(p);
+    }
+    if (L.ev_fork) cudaEventDestroy(L.ev_fork);
+    if (L.ev_join) cudaEventDestroy(L.ev_join);
+    if (L.owns && L.s) {
+        cudaStreamSynchronize(L.s);
+        cudaStreamDestroy(L.s);
+    }
+    L = Lane();
+}
+
+// ---- pass drivers ------------------------------------------------------------------------
+// Every driver issues its work on a Lane: a stream and the scratch that its passes write
+// (records, split partials, accelerations, weights, hot masks).  The main lane is the
+// context stream with the context's buffers; a branch lane runs the FSI steps of a grid-level
+// hhs_fsi call concurrently with the recursion into the fast set (see hhs_fsi).
+
+void pack_pos(frost_ctx *c, Lane &L, const int32_t *list, int n, void *rec)
+{
+    if (c->mixed) launch_pack_pos_mixed(L.s, list, n, c->x, c->m, c->N, (float4 *)rec);
+    else launch_pack_pos_fp64(L.s, list, n, c->x, c->m, c->N, (double4_32a *)rec);
     c->st.kernel_launches += (n > 0);
 }
 
@@ -310,18 +378,18 @@ int badbit(const frost_ctx *c) { return c->eps2 == 0.0 ? ERR_COINCIDENT : ERR_NO
 // With hist (mixed mode, with wmax): the |a| histogram of the pass is added to hist (zeroed by
 // the caller) for the hot-source classification of mark_hot.  kick: the kick of A by the
 // result, fused into the finalisation.  irec / jrec: records already packed by the caller
-// (NULL: packed here into recA / recB).
-void pass_acc(frost_ctx *c, const int32_t *A, int nA, const int32_t *B, int nB, bool self,
+// (NULL: packed here into the lane's recA / recB).
+void pass_acc(frost_ctx *c, Lane &L, const int32_t *A, int nA, const int32_t *B, int nB, bool self,
               double *out_soa, double *out_aos, float *wmax = nullptr, unsigned *hist = nullptr,
               KickArgs kick = KickArgs(), const void *irec = nullptr, const void *jrec = nullptr)
 {
     if (nA <= 0) return;
     if (nB <= 0 || (self && nA == 1)) {
-        if (out_soa) cudaMemsetAsync(out_soa, 0, sizeof(double) * 3 * nA, c->stream);
-        if (out_aos) cudaMemsetAsync(out_aos, 0, sizeof(double) * 3 * nA, c->stream);
-        if (wmax) cudaMemsetAsync(wmax, 0, sizeof(float) * nA, c->stream);
-        if (hist && c->mixed && out_soa) launch_acc_hist(c->stream, out_soa, nA, hist);
-        if (kick.v && out_soa) launch_kick(c->stream, kick.list, nA, kick.v, kick.N, out_soa, kick.dt);
+        if (out_soa) cudaMemsetAsync(out_soa, 0, sizeof(double) * 3 * nA, L.s);
+        if (out_aos) cudaMemsetAsync(out_aos, 0, sizeof(double) * 3 * nA, L.s);
+        if (wmax) cudaMemsetAsync(wmax, 0, sizeof(float) * nA, L.s);
+        if (hist && c->mixed && out_soa) launch_acc_hist(L.s, out_soa, nA, hist);
+        if (kick.v && out_soa) launch_kick(L.s, kick.list, nA, kick.v, kick.N, out_soa, kick.dt);
         return;
     }
     // before a gradient pass (wmax requested) the mixed mode uses the accurate variant on the
@@ -331,17 +399,17 @@ void pass_acc(frost_ctx *c, const int32_t *A, int nA, const int32_t *B, int nB, 
     if (irec) {
         // packed by the caller
     } else {
-        pack_pos(c, A, nA, c->recA);
-        if (!self) pack_pos(c, B, nB, c->recB);
+        pack_pos(c, L, A, nA, L.recA);
+        if (!self) pack_pos(c, L, B, nB, L.recB);
     }
     PairArgs a;
-    a.irec = irec ? irec : c->recA;
-    a.jrec = irec ? jrec : (self ? c->recA : c->recB);
+    a.irec = irec ? irec : L.recA;
+    a.jrec = irec ? jrec : (self ? L.recA : L.recB);
     a.n_a = nA;
     a.n_s = nB;
     a.self_pass = self ? 1 : 0;
     a.eps2 = c->eps2;
-    a.part = c->part;
+    a.part = L.part;
     a.shape = shape_for(c, PASS_ACC, nA, nB, 0, -1, accurate ? TUNE_ACC_ACCURATE : PASS_ACC);
     a.accurate = accurate;
     a.wmax = accurate ? wmax : nullptr;
@@ -349,19 +417,18 @@ void pass_acc(frost_ctx *c, const int32_t *A, int nA, const int32_t *B, int nB, 
     a.m = c->m;
     const int64_t pairs = self ? (int64_t)nA * (nA - 1) : (int64_t)nA * nB;
     {
-        TimedScope ts(c, PASS_ACC, pairs);
+        TimedScope ts(c, L.s, PASS_ACC, pairs);
         if (accurate) {
-            launch_wmax(c->stream, a, wmax);
+            launch_wmax(L.s, a, wmax);
             c->st.kernel_launches += 1;
         }
-        launch_acc(c->stream, c->mixed, a);
+        launch_acc(L.s, c->mixed, a);
     }
-    launch_finalize_vec(c->stream, c->part, a.shape.nsplit, nA, c->G, out_soa, out_aos, &c->dmisc->err,
-                        badbit(c), kick);
+    launch_finalize_vec(L.s, L.part, a.shape.nsplit, nA, c->G, out_soa, out_aos, &c->dmisc->err, badbit(c), kick);
     c->st.kernel_launches += 2;
     c->st.acc_pairs += pairs;
     if (accurate && hist && out_soa) {
-        launch_acc_hist(c->stream, out_soa, nA, hist);
+        launch_acc_hist(L.s, out_soa, nA, hist);
         c->st.kernel_launches += 1;
     }
 }
@@ -370,23 +437,23 @@ void pass_acc(frost_ctx *c, const int32_t *A, int nA, const int32_t *B, int nB, 
 // in mask the particles of A with |a| (a_soa) above HOT_KAPPA x the larger median of hist
 // (this pass) and hist2 (the companion pass of B against A, n2 values, or NULL); see
 // hot_kernels.cu.
-void mark_hot(frost_ctx *c, int nA, int nB, bool self, const double *a_soa, const unsigned *hist,
+void mark_hot(frost_ctx *c, Lane &L, int nA, int nB, bool self, const double *a_soa, const unsigned *hist,
               const unsigned *hist2, int n2, uint32_t *mask)
 {
     if (!c->mixed || nA <= 0) return;
     if (nB <= 0 || (self && nA == 1)) {
-        cudaMemsetAsync(mask, 0, sizeof(uint32_t) * ((nA + 31) / 32), c->stream);
+        cudaMemsetAsync(mask, 0, sizeof(uint32_t) * ((nA + 31) / 32), L.s);
         return;
     }
-    launch_hot_mask(c->stream, a_soa, nA, hist, hist2, n2, mask);
+    launch_hot_mask(L.s, a_soa, nA, hist, hist2, n2, mask);
     c->st.kernel_launches += 1;
 }
 
-// the two |a| histograms, zeroed
-unsigned *zero_hists(frost_ctx *c)
+// the lane's two |a| histograms, zeroed
+unsigned *zero_hists(Lane &L)
 {
-    cudaMemsetAsync(c->hist, 0, sizeof(unsigned) * 2 * HOT_BINS, c->stream);
-    return c->hist;
+    cudaMemsetAsync(L.hist, 0, sizeof(unsigned) * 2 * HOT_BINS, L.s);
+    return L.hist;
 }
 
 // gradient of A against B with a_A (soa [3][nA]) and a_B (soa [3][nB]); writes
@@ -394,7 +461,7 @@ unsigned *zero_hists(frost_ctx *c)
 // dominant-term weights of A from the Newtonian pass at the same positions (mixed mode).
 // kick: the kick of A by a~, fused into the finalisation.  irec / jrec: gradient records
 // already packed by the caller (the source records with the hot masses zeroed).
-void pass_grad(frost_ctx *c, const int32_t *A, int nA, const double *aA, const int32_t *B, int nB,
+void pass_grad(frost_ctx *c, Lane &L, const int32_t *A, int nA, const double *aA, const int32_t *B, int nB,
                const double *aB, bool self, double eps_grad, double *at_soa, double *at_aos,
                double *g_aos, const float *wmax, const uint32_t *hotB = nullptr,
                KickArgs kick = KickArgs(), const void *irec = nullptr, const void *jrec = nullptr)
@@ -403,10 +470,10 @@ void pass_grad(frost_ctx *c, const int32_t *A, int nA, const double *aA, const i
     const double cgrad = eps_grad * eps_grad / 48.0;
     if (nB <= 0 || (self && nA == 1)) {
         // no sources: g = 0 and a~ = a
-        if (at_soa) cudaMemcpyAsync(at_soa, aA, sizeof(double) * 3 * nA, cudaMemcpyDeviceToDevice, c->stream);
-        if (at_aos) launch_soa_to_aos(c->stream, aA, nA, at_aos);
-        if (g_aos) cudaMemsetAsync(g_aos, 0, sizeof(double) * 3 * nA, c->stream);
-        if (kick.v) launch_kick(c->stream, kick.list, nA, kick.v, kick.N, aA, kick.dt);
+        if (at_soa) cudaMemcpyAsync(at_soa, aA, sizeof(double) * 3 * nA, cudaMemcpyDeviceToDevice, L.s);
+        if (at_aos) launch_soa_to_aos(L.s, aA, nA, at_aos);
+        if (g_aos) cudaMemsetAsync(g_aos, 0, sizeof(double) * 3 * nA, L.s);
+        if (kick.v) launch_kick(L.s, kick.list, nA, kick.v, kick.N, aA, kick.dt);
         return;
     }
     if (!c->mixed) hotB = nullptr;
@@ -415,123 +482,120 @@ void pass_grad(frost_ctx *c, const int32_t *A, int nA, const double *aA, const i
     } else if (c->mixed) {
         // hot sources: masses zeroed in the FP32 source records, their terms summed in
         // double-float by k_grad_hot
-        launch_pack_grad_mixed(c->stream, A, nA, c->x, c->m, c->N, aA, (float4 *)c->recA,
-                               self ? hotB : nullptr);
-        if (!self) launch_pack_grad_mixed(c->stream, B, nB, c->x, c->m, c->N, aB, (float4 *)c->recB, hotB);
+        launch_pack_grad_mixed(L.s, A, nA, c->x, c->m, c->N, aA, (float4 *)L.recA, self ? hotB : nullptr);
+        if (!self) launch_pack_grad_mixed(L.s, B, nB, c->x, c->m, c->N, aB, (float4 *)L.recB, hotB);
     } else {
-        launch_pack_grad_fp64(c->stream, A, nA, c->x, c->m, c->N, aA, (double4_32a *)c->recA);
-        if (!self) launch_pack_grad_fp64(c->stream, B, nB, c->x, c->m, c->N, aB, (double4_32a *)c->recB);
+        launch_pack_grad_fp64(L.s, A, nA, c->x, c->m, c->N, aA, (double4_32a *)L.recA);
+        if (!self) launch_pack_grad_fp64(L.s, B, nB, c->x, c->m, c->N, aB, (double4_32a *)L.recB);
     }
     if (!irec) c->st.kernel_launches += self ? 1 : 2;
     PairArgs a;
-    a.irec = irec ? irec : c->recA;
-    a.jrec = irec ? jrec : (self ? c->recA : c->recB);
+    a.irec = irec ? irec : L.recA;
+    a.jrec = irec ? jrec : (self ? L.recA : L.recB);
     a.n_a = nA;
     a.n_s = nB;
     a.self_pass = self ? 1 : 0;
     a.eps2 = c->eps2;
-    a.part = c->part;
+    a.part = L.part;
     a.shape = shape_for(c, PASS_GRAD, nA, nB);
     a.wmax = c->mixed ? wmax : nullptr;
     const int64_t pairs = self ? (int64_t)nA * (nA - 1) : (int64_t)nA * nB;
     {
-        TimedScope ts(c, PASS_GRAD, pairs);
-        launch_grad(c->stream, c->mixed, a);
+        TimedScope ts(c, L.s, PASS_GRAD, pairs);
+        launch_grad(L.s, c->mixed, a);
     }
     int ns_hot = 0;
     if (hotB) {
         ns_hot = hot_grad_splits(nA, nB, c->n_sm);
         while (ns_hot > 1 && (size_t)ns_hot * 3 * nA > c->part_hot_elems) --ns_hot;
-        launch_grad_hot(c->stream, A, nA, aA, B, nB, aB, hotB, a.self_pass, c->x, c->m, c->N, c->eps2, ns_hot,
-                        c->part_hot);
+        launch_grad_hot(L.s, A, nA, aA, B, nB, aB, hotB, a.self_pass, c->x, c->m, c->N, c->eps2, ns_hot,
+                        L.part_hot);
         c->st.kernel_launches += 1;
     }
-    launch_finalize_grad(c->stream, c->part, a.shape.nsplit, nA, 2.0 * c->G, aA, cgrad, at_soa,
-                         at_aos, g_aos, &c->dmisc->err, badbit(c), c->part_hot, ns_hot, kick);
+    launch_finalize_grad(L.s, L.part, a.shape.nsplit, nA, 2.0 * c->G, aA, cgrad, at_soa, at_aos, g_aos,
+                         &c->dmisc->err, badbit(c), L.part_hot, ns_hot, kick);
     c->st.kernel_launches += 2;
     c->st.grad_pairs += pairs;
 }
 
 // symmetrised time-steps of the set P into tau[nP]
-void pass_tstep(frost_ctx *c, const int32_t *P, int nP, double *tau)
+void pass_tstep(frost_ctx *c, Lane &L, const int32_t *P, int nP, double *tau)
 {
     if (nP <= 0) return;
     if (nP == 1) {
         // no pair: with zero splits the finalisation writes eta * (+inf)
-        launch_finalize_tau(c->stream, c->part, 0, 1, c->eta, tau, &c->dmisc->err);
+        launch_finalize_tau(L.s, L.part, 0, 1, c->eta, tau, &c->dmisc->err);
         c->st.kernel_launches += 1;
         return;
     }
     // exact fly-by derivative: the accelerations of the set due to itself, packed with the records
     const double *acc = nullptr;
     if (c->sym & FROST_FLYBY_EXACT) {
-        pass_acc(c, P, nP, P, nP, true, c->aB, nullptr);
-        acc = c->aB;
+        pass_acc(c, L, P, nP, P, nP, true, L.aB, nullptr);
+        acc = L.aB;
     }
-    if (c->mixed) launch_pack_tstep_mixed(c->stream, P, nP, c->x, c->v, c->m, c->N, c->G, (float4 *)c->recA, acc);
-    else launch_pack_tstep_fp64(c->stream, P, nP, c->x, c->v, c->m, c->N, c->G, (double4_32a *)c->recA, acc);
+    if (c->mixed) launch_pack_tstep_mixed(L.s, P, nP, c->x, c->v, c->m, c->N, c->G, (float4 *)L.recA, acc);
+    else launch_pack_tstep_fp64(L.s, P, nP, c->x, c->v, c->m, c->N, c->G, (double4_32a *)L.recA, acc);
     PairArgs a;
-    a.irec = c->recA;
-    a.jrec = c->recA;
+    a.irec = L.recA;
+    a.jrec = L.recA;
     a.n_a = nP;
     a.n_s = nP;
     a.self_pass = 1;
     a.eps2 = 0.0;
-    a.part = c->part;
+    a.part = L.part;
     a.shape = shape_for(c, PASS_TSTEP, nP, nP);
     const int64_t pairs = (int64_t)nP * (nP - 1);
     {
-        TimedScope ts(c, PASS_TSTEP, pairs);
-        launch_tstep(c->stream, c->mixed, a, c->eta, c->sym, &c->dmisc->err);
+        TimedScope ts(c, L.s, PASS_TSTEP, pairs);
+        launch_tstep(L.s, c->mixed, a, c->eta, c->sym, &c->dmisc->err);
     }
-    launch_finalize_tau(c->stream, c->part, a.shape.nsplit, nP, c->eta, tau, &c->dmisc->err);
+    launch_finalize_tau(L.s, L.part, a.shape.nsplit, nP, c->eta, tau, &c->dmisc->err);
     c->st.kernel_launches += 3;
     c->st.tstep_pairs += pairs;
 }
 
 // ---- integrator -----------------------------------------------------------------------
 
-void drift(frost_ctx *c, const int32_t *L, int n, double dt)
+void drift(frost_ctx *c, Lane &L, const int32_t *list, int n, double dt)
 {
     if (n <= 0) return;
-    launch_drift(c->stream, L, n, c->x, c->v, c->N, dt);
+    launch_drift(L.s, list, n, c->x, c->v, c->N, dt);
     c->st.kernel_launches += 1;
 }
 
-// Algorithm fsi on the set S with step dt
-KickArgs kick_of(frost_ctx *c, const int32_t *L, double dt)
+KickArgs kick_of(frost_ctx *c, const int32_t *list, double dt)
 {
     KickArgs k;
-    k.list = L;
+    k.list = list;
     k.v = c->v;
     k.N = c->N;
     k.dt = dt;
     return k;
 }
 
-// drift of L, writing the position records of the Newtonian pass that follows into rec
-void drift_pack(frost_ctx *c, const int32_t *L, int n, double dt, void *rec, bool accurate)
+// drift of the list, writing the position records of the Newtonian pass that follows into rec
+void drift_pack(frost_ctx *c, Lane &L, const int32_t *list, int n, double dt, void *rec)
 {
     if (n <= 0) return;
-    (void)accurate;  // both Newtonian variants read the same position records
-    launch_drift_pack(c->stream, L, n, c->x, c->v, c->m, c->N, dt, rec, c->mixed ? 0 : 2);
+    launch_drift_pack(L.s, list, n, c->x, c->v, c->m, c->N, dt, rec, c->mixed ? 0 : 2);
     c->st.kernel_launches += 1;
 }
 
-// position records of L for a Newtonian pass (both variants read the same records)
-void pack_acc(frost_ctx *c, const int32_t *L, int n, void *rec, bool /*accurate*/)
+// position records of the list for a Newtonian pass (both variants read the same records)
+void pack_acc(frost_ctx *c, Lane &L, const int32_t *list, int n, void *rec)
 {
     if (n <= 0) return;
-    pack_pos(c, L, n, rec);
+    pack_pos(c, L, list, n, rec);
 }
 
-// gradient records of L with accelerations a ([3][n]); mixed mode: masses of the hot
+// gradient records of the list with accelerations a ([3][n]); mixed mode: masses of the hot
 // particles (mask) zeroed, their terms are summed in double-float by k_grad_hot
-void pack_grad(frost_ctx *c, const int32_t *L, int n, const double *a, void *rec, const uint32_t *mask)
+void pack_grad(frost_ctx *c, Lane &L, const int32_t *list, int n, const double *a, void *rec, const uint32_t *mask)
 {
     if (n <= 0) return;
-    if (c->mixed) launch_pack_grad_mixed(c->stream, L, n, c->x, c->m, c->N, a, (float4 *)rec, mask);
-    else launch_pack_grad_fp64(c->stream, L, n, c->x, c->m, c->N, a, (double4_32a *)rec);
+    if (c->mixed) launch_pack_grad_mixed(L.s, list, n, c->x, c->m, c->N, a, (float4 *)rec, mask);
+    else launch_pack_grad_fp64(L.s, list, n, c->x, c->m, c->N, a, (double4_32a *)rec);
     c->st.kernel_launches += 1;
 }
 
@@ -540,62 +604,105 @@ void pack_grad(frost_ctx *c, const int32_t *L, int n, const double *a, void *rec
 // cache: 1 stores the final a^SS by particle in aC; 2 starts from the stored a^SS.  Between
 // the two fsi(S) calls of one hhs_fsi only kicks and the deeper levels (other particles)
 // run, so S has not moved and the stored values are the ones the pass would recompute.
-void fsi(frost_ctx *c, const int32_t *S, int nS, double dt, int cache = 0)
+void fsi(frost_ctx *c, Lane &L, const int32_t *S, int nS, double dt, int cache = 0)
 {
     if (nS <= 0) return;
     c->st.fsi_calls += 1;
     if (nS < 2) cache = 0;
     if (cache == 2) {
-        launch_kick_by_particle(c->stream, S, nS, c->v, c->N, c->aC, dt / 6.0);
+        launch_kick_by_particle(L.s, S, nS, c->v, c->N, c->aC, dt / 6.0);
         c->st.kernel_launches += 1;
         c->st.acc_pairs_reused += (int64_t)nS * (nS - 1);
     } else {
-        pass_acc(c, S, nS, S, nS, true, c->aA, nullptr, nullptr, nullptr, kick_of(c, S, dt / 6.0));
+        pass_acc(c, L, S, nS, S, nS, true, L.aA, nullptr, nullptr, nullptr, kick_of(c, S, dt / 6.0));
     }
-    drift_pack(c, S, nS, 0.5 * dt, c->recA, true);
+    drift_pack(c, L, S, nS, 0.5 * dt, L.recA);
     if (c->mixed) {
-        unsigned *h = zero_hists(c);
-        pass_acc(c, S, nS, S, nS, true, c->aA, nullptr, c->wA, h, KickArgs(), c->recA, c->recA);
-        mark_hot(c, nS, nS, true, c->aA, h, nullptr, 0, c->hA);
+        unsigned *h = zero_hists(L);
+        pass_acc(c, L, S, nS, S, nS, true, L.aA, nullptr, L.wA, h, KickArgs(), L.recA, L.recA);
+        mark_hot(c, L, nS, nS, true, L.aA, h, nullptr, 0, L.hA);
     } else {
-        pass_acc(c, S, nS, S, nS, true, c->aA, nullptr, c->wA, nullptr, KickArgs(), c->recA, c->recA);
+        pass_acc(c, L, S, nS, S, nS, true, L.aA, nullptr, L.wA, nullptr, KickArgs(), L.recA, L.recA);
     }
-    pass_grad(c, S, nS, c->aA, S, nS, c->aA, true, dt, c->atA, nullptr, nullptr, c->wA, c->hA,
+    pass_grad(c, L, S, nS, L.aA, S, nS, L.aA, true, dt, L.atA, nullptr, nullptr, L.wA, L.hA,
               kick_of(c, S, 2.0 * dt / 3.0));
-    drift_pack(c, S, nS, 0.5 * dt, c->recA, false);
+    drift_pack(c, L, S, nS, 0.5 * dt, L.recA);
     KickArgs last = kick_of(c, S, dt / 6.0);
     if (cache == 1) last.store = c->aC;
-    pass_acc(c, S, nS, S, nS, true, c->aA, nullptr, nullptr, nullptr, last, c->recA, c->recA);
+    pass_acc(c, L, S, nS, S, nS, true, L.aA, nullptr, nullptr, nullptr, last, L.recA, L.recA);
 }
 
-// kick_sf: S kicked by its accelerations due to F, F by those due to S.  Accelerations depend
-// on positions only, so each list's kick is fused into its own pass; both lists are packed
-// once (S in recA, F in recB) for the two directions.
-void kick_sf(frost_ctx *c, const int32_t *S, int nS, const int32_t *F, int nF, double cdt,
+// Runs on `exec` what a branch lane issues: the branch lane itself when the branches run
+// concurrently, else its buffers on the context stream (timing mode, or concurrency off).
+struct Branch {
+    frost_ctx *c;
+    Lane *B;
+    Lane exec;
+    bool concurrent;
+    bool open = false;
+    Branch(frost_ctx *c_, Lane *B_) : c(c_), B(B_), exec(*B_)
+    {
+        concurrent = c->branch_streams && !c->timing;
+        if (!concurrent) exec.s = c->stream;
+    }
+    // the branch continues after everything issued so far on the context stream
+    void fork()
+    {
+        if (!concurrent) return;
+        cudaEventRecord(B->ev_fork, c->stream);
+        cudaStreamWaitEvent(B->s, B->ev_fork, 0);
+        open = true;
+    }
+    // the context stream continues after everything issued on the branch
+    void join()
+    {
+        if (!open) return;
+        cudaEventRecord(B->ev_join, B->s);
+        cudaStreamWaitEvent(c->stream, B->ev_join, 0);
+        open = false;
+    }
+    ~Branch() { join(); }
+};
+
+// kick_sf: S kicked by its accelerations due to F, F by those due to S, both computed before
+// either kick.  Accelerations depend on positions only, so each list's kick is fused into its
+// own pass; both lists are packed once (S in recA, F in recB of the main lane) for the two
+// directions.  The two directions are independent: with a branch lane Bl (idle between the
+// fsi(S) steps of its level) the F-side passes run on it, concurrently with the S-side passes
+// on the main lane, writing their partials in the branch's scratch and their results in the
+// main lane's buffers.
+void kick_sf(frost_ctx *c, Lane &M, Lane *Bl, const int32_t *S, int nS, const int32_t *F, int nF, double cdt,
              bool gradient, double tau_pivot)
 {
     if (nS <= 0 || nF <= 0) return;
-    pack_acc(c, S, nS, c->recA, gradient);
-    pack_acc(c, F, nF, c->recB, gradient);
+    pack_acc(c, M, S, nS, M.recA);
+    pack_acc(c, M, F, nF, M.recB);
+    Branch br(c, Bl ? Bl : &M);
+    if (!Bl) br.concurrent = false;
+    Lane &X = Bl ? br.exec : M;
     if (!gradient) {
-        pass_acc(c, S, nS, F, nF, false, c->aA, nullptr, nullptr, nullptr, kick_of(c, S, cdt), c->recA, c->recB);
-        pass_acc(c, F, nF, S, nS, false, c->aB, nullptr, nullptr, nullptr, kick_of(c, F, cdt), c->recB, c->recA);
-        return;
+        br.fork();
+        pass_acc(c, M, S, nS, F, nF, false, M.aA, nullptr, nullptr, nullptr, kick_of(c, S, cdt), M.recA, M.recB);
+        pass_acc(c, X, F, nF, S, nS, false, M.aB, nullptr, nullptr, nullptr, kick_of(c, F, cdt), M.recB, M.recA);
+        return;  // joined by br
     }
-    unsigned *h = c->mixed ? zero_hists(c) : nullptr;
-    pass_acc(c, S, nS, F, nF, false, c->aA, nullptr, c->wA, h, KickArgs(), c->recA, c->recB);
-    pass_acc(c, F, nF, S, nS, false, c->aB, nullptr, c->wB, h ? h + HOT_BINS : nullptr, KickArgs(), c->recB,
-             c->recA);
+    unsigned *h = c->mixed ? zero_hists(M) : nullptr;
+    br.fork();
+    pass_acc(c, M, S, nS, F, nF, false, M.aA, nullptr, M.wA, h, KickArgs(), M.recA, M.recB);
+    pass_acc(c, X, F, nF, S, nS, false, M.aB, nullptr, M.wB, h ? h + HOT_BINS : nullptr, KickArgs(), M.recB,
+             M.recA);
+    br.join();
     if (h) {
-        mark_hot(c, nS, nF, false, c->aA, h, h + HOT_BINS, nF, c->hA);
-        mark_hot(c, nF, nS, false, c->aB, h + HOT_BINS, h, nS, c->hB);
+        mark_hot(c, M, nS, nF, false, M.aA, h, h + HOT_BINS, nF, M.hA);
+        mark_hot(c, M, nF, nS, false, M.aB, h + HOT_BINS, h, nS, M.hB);
     }
-    pack_grad(c, S, nS, c->aA, c->recA, c->mixed ? c->hA : nullptr);
-    pack_grad(c, F, nF, c->aB, c->recB, c->mixed ? c->hB : nullptr);
-    pass_grad(c, S, nS, c->aA, F, nF, c->aB, false, tau_pivot, c->atA, nullptr, nullptr, c->wA, c->hB,
-              kick_of(c, S, cdt), c->recA, c->recB);
-    pass_grad(c, F, nF, c->aB, S, nS, c->aA, false, tau_pivot, c->atB, nullptr, nullptr, c->wB, c->hA,
-              kick_of(c, F, cdt), c->recB, c->recA);
+    pack_grad(c, M, S, nS, M.aA, M.recA, c->mixed ? M.hA : nullptr);
+    pack_grad(c, M, F, nF, M.aB, M.recB, c->mixed ? M.hB : nullptr);
+    br.fork();
+    pass_grad(c, M, S, nS, M.aA, F, nF, M.aB, false, tau_pivot, M.atA, nullptr, nullptr, M.wA, M.hB,
+              kick_of(c, S, cdt), M.recA, M.recB);
+    pass_grad(c, X, F, nF, M.aB, S, nS, M.aA, false, tau_pivot, M.atB, nullptr, nullptr, M.wB, M.hA,
+              kick_of(c, F, cdt), M.recB, M.recA);
 }
 
 frost_status ensure_level(frost_ctx *c, int depth)
@@ -613,7 +720,8 @@ frost_status ensure_level(frost_ctx *c, int depth)
     return FROST_OK;
 }
 
-// the whole subtree of hhs_fsi(P, tau) in one thread block (single launch, no sync)
+// the whole subtree of hhs_fsi(P, tau) in one thread block (single launch, no sync), on the
+// main lane
 void hhs_subtree(frost_ctx *c, const int32_t *P, int nP, double tau, int depth)
 {
     SubtreeArgs a;
@@ -648,7 +756,7 @@ void hhs_subtree(frost_ctx *c, const int32_t *P, int nP, double tau, int depth)
     a.team_blocks = c->subtree_blocks;
     a.xchg = c->d_xchg;
     {
-        TimedScope ts(c, PASS_SUBTREE, 0);
+        TimedScope ts(c, c->stream, PASS_SUBTREE, 0);
         // a launch error is also left for the cudaGetLastError() of the calling entry point
         (void)launch_subtree(c->stream, c->mixed, c->sym, a);
     }
@@ -656,7 +764,30 @@ void hhs_subtree(frost_ctx *c, const int32_t *P, int nP, double tau, int depth)
     c->st.subtree_launches += 1;
 }
 
-// Algorithm hhs-fsi on the set P (device list, nP entries) with pivot step tau
+// The branch lane of grid level `depth`: its own scratch (the size of the main lane's) and a
+// non-blocking stream of the lowest priority, so that the recursion on the context stream,
+// the critical path of the step, is scheduled first.  Allocated on first use.
+frost_status branch_lane(frost_ctx *c, int depth, Lane **out)
+{
+    while ((int)c->branch.size() <= depth) c->branch.push_back(Lane());
+    Lane &B = c->branch[depth];
+    if (!B.s) {
+        int lo = 0, hi = 0;
+        FROST_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        FROST_CUDA(cudaStreamCreateWithPriority(&B.s, cudaStreamNonBlocking, lo));
+        FROST_CUDA(cudaEventCreateWithFlags(&B.ev_fork, cudaEventDisableTiming));
+        FROST_CUDA(cudaEventCreateWithFlags(&B.ev_join, cudaEventDisableTiming));
+        FROST_TRY(alloc_lane_buffers(c, B));
+    }
+    *out = &B;
+    return FROST_OK;
+}
+
+// Algorithm hhs-fsi on the set P (device list, nP entries) with pivot step tau.
+// The operators of fsi(S, tau/2) and hhs_fsi(F, tau/2) act on disjoint particles (H_S holds
+// only S, H_F only F), so each fsi(S) runs on the level's branch lane concurrently with the
+// recursion into F on the context stream; the kick_sf between them joins both.  The
+// arithmetic, and so every result, is that of the serial order.
 frost_status hhs_fsi(frost_ctx *c, const int32_t *P, int nP, double tau, int depth)
 {
     if (nP <= 0) return FROST_OK;
@@ -670,25 +801,45 @@ frost_status hhs_fsi(frost_ctx *c, const int32_t *P, int nP, double tau, int dep
     c->st.hhs_calls += 1;
     if (depth > c->st.max_depth_seen) c->st.max_depth_seen = depth;
     {
-        const int L = std::min(depth, FROST_STATS_LEVELS - 1);
-        c->st.level_calls[L] += 1;
-        c->st.level_particles[L] += nP;
+        const int Lv = std::min(depth, FROST_STATS_LEVELS - 1);
+        c->st.level_calls[Lv] += 1;
+        c->st.level_particles[Lv] += nP;
     }
     FROST_TRY(ensure_level(c, depth));
+    Lane &M = c->main;
     int32_t *S = c->lvS[depth], *F = c->lvF[depth];
-    pass_tstep(c, P, nP, c->tau);
-    launch_partition(c->stream, P, nP, c->tau, tau, S, F, c->dmisc->counts);
+    pass_tstep(c, M, P, nP, c->tau);
+    launch_partition(M.s, P, nP, c->tau, tau, S, F, c->dmisc->counts);
     c->st.kernel_launches += 1;
     FROST_TRY(sync_misc(c));
     const int nS = (int)c->hmisc->counts[0];
     const int nF = (int)c->hmisc->counts[1];
-    kick_sf(c, S, nS, F, nF, tau / 6.0, false, tau);
-    fsi(c, S, nS, 0.5 * tau, 1);
-    FROST_TRY(hhs_fsi(c, F, nF, 0.5 * tau, depth + 1));
-    kick_sf(c, S, nS, F, nF, 2.0 * tau / 3.0, true, tau);
-    FROST_TRY(hhs_fsi(c, F, nF, 0.5 * tau, depth + 1));
-    fsi(c, S, nS, 0.5 * tau, 2);
-    kick_sf(c, S, nS, F, nF, tau / 6.0, false, tau);
+    if (nF == 0 || nS == 0) {
+        // one of the two sets is empty: no kick_sf, and the two half steps of the other set
+        // follow each other on the context stream
+        fsi(c, M, S, nS, 0.5 * tau, 1);
+        FROST_TRY(hhs_fsi(c, F, nF, 0.5 * tau, depth + 1));
+        FROST_TRY(hhs_fsi(c, F, nF, 0.5 * tau, depth + 1));
+        fsi(c, M, S, nS, 0.5 * tau, 2);
+        return FROST_OK;
+    }
+    Lane *Bl = nullptr;
+    FROST_TRY(branch_lane(c, depth, &Bl));
+    kick_sf(c, M, Bl, S, nS, F, nF, tau / 6.0, false, tau);
+    {
+        Branch br(c, Bl);
+        br.fork();
+        fsi(c, br.exec, S, nS, 0.5 * tau, 1);
+        FROST_TRY(hhs_fsi(c, F, nF, 0.5 * tau, depth + 1));
+    }
+    kick_sf(c, M, Bl, S, nS, F, nF, 2.0 * tau / 3.0, true, tau);
+    {
+        Branch br(c, Bl);
+        br.fork();
+        fsi(c, br.exec, S, nS, 0.5 * tau, 2);
+        FROST_TRY(hhs_fsi(c, F, nF, 0.5 * tau, depth + 1));
+    }
+    kick_sf(c, M, Bl, S, nS, F, nF, tau / 6.0, false, tau);
     return FROST_OK;
 }
 
@@ -712,6 +863,7 @@ void destroy(frost_ctx *c)
 {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
+    for (Lane &L : c->branch) free_lane(L);
     for (const Timed &t : c->pending) {
         cudaEventDestroy(t.a);
         cudaEventDestroy(t.b);
@@ -757,6 +909,7 @@ void frost_default_opts(frost_opts *opt)
     opt->subtree_max = 0;
     opt->subtree_blocks = 0;
     opt->integrator = FROST_HHS_FSI;
+    opt->branch_streams = 0;
 }
 
 const char *frost_last_error(void) { return g_last_error; }
@@ -910,6 +1063,21 @@ static frost_status init_impl(frost_ctx **out, int64_t n, const double *m, const
     // the status word of a multi-block single-set solver team (batch contexts have one per cluster)
     if (!c->d_xchg) INIT_CUDA(cudaMalloc(&c->d_xchg, sizeof(int)));
     INIT_CUDA(cudaMallocHost(&c->hmisc, sizeof(Misc)));
+    c->main.s = c->stream;
+    c->main.recA = c->recA;
+    c->main.recB = c->recB;
+    c->main.part = c->part;
+    c->main.aA = c->aA;
+    c->main.aB = c->aB;
+    c->main.atA = c->atA;
+    c->main.atB = c->atB;
+    c->main.wA = c->wA;
+    c->main.wB = c->wB;
+    c->main.hist = c->hist;
+    c->main.hA = c->hA;
+    c->main.hB = c->hB;
+    c->main.part_hot = c->part_hot;
+    c->branch_streams = o.branch_streams >= 0;
     INIT_CUDA(cudaMemsetAsync(c->dmisc, 0, sizeof(Misc), c->stream));
     INIT_CUDA(cudaMemsetAsync(c->marks, 0, sizeof(int32_t) * N, c->stream));
     launch_identity(c->stream, c->all, (int)n);
@@ -995,20 +1163,21 @@ frost_status frost_accel_gradient(frost_ctx *c, const int32_t *active, int64_t n
     }
     if (nA == 0) return FROST_OK;
     const bool want_grad = acc_tilde || grad;
+    Lane &M = c->main;
     if (self) {
-        unsigned *h = (want_grad && c->mixed) ? zero_hists(c) : nullptr;
-        pass_acc(c, A, nA, A, nA, true, c->aA, acc, want_grad ? c->wA : nullptr, h);
-        if (h) mark_hot(c, nA, nA, true, c->aA, h, nullptr, 0, c->hA);
+        unsigned *h = (want_grad && c->mixed) ? zero_hists(M) : nullptr;
+        pass_acc(c, M, A, nA, A, nA, true, c->aA, acc, want_grad ? c->wA : nullptr, h);
+        if (h) mark_hot(c, M, nA, nA, true, c->aA, h, nullptr, 0, c->hA);
         if (want_grad)
-            pass_grad(c, A, nA, c->aA, A, nA, c->aA, true, eps_grad, nullptr, acc_tilde, grad, c->wA, c->hA);
+            pass_grad(c, M, A, nA, c->aA, A, nA, c->aA, true, eps_grad, nullptr, acc_tilde, grad, c->wA, c->hA);
     } else {
-        unsigned *h = (want_grad && c->mixed) ? zero_hists(c) : nullptr;
-        pass_acc(c, A, nA, B, nB, false, c->aA, acc, want_grad ? c->wA : nullptr, h);
+        unsigned *h = (want_grad && c->mixed) ? zero_hists(M) : nullptr;
+        pass_acc(c, M, A, nA, B, nB, false, c->aA, acc, want_grad ? c->wA : nullptr, h);
         if (want_grad) {
-            pass_acc(c, B, nB, A, nA, false, c->aB, nullptr, c->wB, h ? h + HOT_BINS : nullptr);
+            pass_acc(c, M, B, nB, A, nA, false, c->aB, nullptr, c->wB, h ? h + HOT_BINS : nullptr);
             // only B's accelerations are sources
-            if (h) mark_hot(c, nB, nA, false, c->aB, h + HOT_BINS, h, nA, c->hB);
-            pass_grad(c, A, nA, c->aA, B, nB, c->aB, false, eps_grad, nullptr, acc_tilde, grad, c->wA, c->hB);
+            if (h) mark_hot(c, M, nB, nA, false, c->aB, h + HOT_BINS, h, nA, c->hB);
+            pass_grad(c, M, A, nA, c->aA, B, nB, c->aB, false, eps_grad, nullptr, acc_tilde, grad, c->wA, c->hB);
         }
     }
     FROST_CUDA(cudaGetLastError());
@@ -1021,7 +1190,7 @@ frost_status frost_timesteps(frost_ctx *c, const int32_t *set, int64_t n_set, do
     FROST_TRY(check_sizes(c, n_set, "n_set"));
     if (n_set > 0 && !tau) return fail(FROST_EINVAL, "tau is NULL");
     FROST_TRY(check_list(c, set, (int)n_set));
-    pass_tstep(c, set ? set : c->all, (int)n_set, tau);
+    pass_tstep(c, c->main, set ? set : c->all, (int)n_set, tau);
     FROST_CUDA(cudaGetLastError());
     return sync_misc(c);
 }
@@ -1056,7 +1225,7 @@ frost_status frost_drift(frost_ctx *c, const int32_t *set, int64_t n_set, double
 {
     if (!c) return fail(FROST_EINVAL, "NULL context");
     FROST_TRY(check_sizes(c, n_set, "n_set"));
-    drift(c, set, (int)n_set, dt);
+    drift(c, c->main, set, (int)n_set, dt);
     FROST_CUDA(cudaGetLastError());
     return FROST_OK;
 }
@@ -1065,7 +1234,7 @@ frost_status frost_fsi(frost_ctx *c, const int32_t *set, int64_t n_set, double d
 {
     if (!c) return fail(FROST_EINVAL, "NULL context");
     FROST_TRY(check_sizes(c, n_set, "n_set"));
-    fsi(c, set ? set : c->all, (int)n_set, dt);
+    fsi(c, c->main, set ? set : c->all, (int)n_set, dt);
     FROST_CUDA(cudaGetLastError());
     return FROST_OK;
 }
@@ -1074,9 +1243,10 @@ frost_status frost_fsi(frost_ctx *c, const int32_t *set, int64_t n_set, double d
 void leapfrog(frost_ctx *c, const int32_t *S, int nS, double h)
 {
     if (nS <= 0) return;
-    pass_acc(c, S, nS, S, nS, true, c->aA, nullptr, nullptr, nullptr, kick_of(c, S, 0.5 * h));
-    drift_pack(c, S, nS, h, c->recA, false);
-    pass_acc(c, S, nS, S, nS, true, c->aA, nullptr, nullptr, nullptr, kick_of(c, S, 0.5 * h), c->recA, c->recA);
+    Lane &M = c->main;
+    pass_acc(c, M, S, nS, S, nS, true, c->aA, nullptr, nullptr, nullptr, kick_of(c, S, 0.5 * h));
+    drift_pack(c, M, S, nS, h, c->recA);
+    pass_acc(c, M, S, nS, S, nS, true, c->aA, nullptr, nullptr, nullptr, kick_of(c, S, 0.5 * h), c->recA, c->recA);
 }
 
 // The second-order HOLD integrator, Eq. hhs2: e^{eps/2 H_F} e^{eps/2 H_S} e^{eps U_FS}
@@ -1095,7 +1265,7 @@ frost_status hold2(frost_ctx *c, const int32_t *P, int nP, double tau, int depth
     }
     FROST_TRY(ensure_level(c, depth));
     int32_t *S = c->lvS[depth], *F = c->lvF[depth];
-    pass_tstep(c, P, nP, c->tau);
+    pass_tstep(c, c->main, P, nP, c->tau);
     launch_partition(c->stream, P, nP, c->tau, tau, S, F, c->dmisc->counts);
     c->st.kernel_launches += 1;
     FROST_TRY(sync_misc(c));
@@ -1103,7 +1273,7 @@ frost_status hold2(frost_ctx *c, const int32_t *P, int nP, double tau, int depth
     const int nF = (int)c->hmisc->counts[1];
     FROST_TRY(hold2(c, F, nF, 0.5 * tau, depth + 1));
     leapfrog(c, S, nS, 0.5 * tau);
-    kick_sf(c, S, nS, F, nF, tau, false, tau);
+    kick_sf(c, c->main, nullptr, S, nS, F, nF, tau, false, tau);
     leapfrog(c, S, nS, 0.5 * tau);
     return hold2(c, F, nF, 0.5 * tau, depth + 1);
 }
@@ -1193,7 +1363,7 @@ frost_status frost_step(frost_ctx *c, double dt_pivot, int64_t n_steps)
             c->g_steps = n_steps;
         }
         {
-            TimedScope ts(c, PASS_SUBTREE, 0);
+            TimedScope ts(c, c->stream, PASS_SUBTREE, 0);
             FROST_CUDA(cudaGraphLaunch(c->gexec, c->stream));
         }
         c->st.kernel_launches += (c->n_big > 0) + (c->n_small > 0);
@@ -1332,7 +1502,7 @@ frost_status frost_autotune(frost_ctx *c, int32_t *waves_out)
             const bool accurate = (row == TUNE_ACC_ACCURATE);
             // records of particles 0 .. n-1 (zero accelerations for the gradient records)
             if (kind == PASS_ACC) {
-                pack_pos(c, c->all, n, c->recA);
+                pack_pos(c, c->main, c->all, n, c->recA);
             } else if (kind == PASS_GRAD) {
                 cudaMemsetAsync(c->aB, 0, sizeof(double) * 3 * n, c->stream);
                 if (c->mixed) launch_pack_grad_mixed(c->stream, c->all, n, c->x, c->m, c->N, c->aB, (float4 *)c->recA);

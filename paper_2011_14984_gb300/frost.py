@@ -39,7 +39,8 @@ class frost_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("sym", ctypes.c_int32),
                 ("eps_soft", ctypes.c_double), ("max_depth", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p), ("subtree_max", ctypes.c_int32),
-                ("integrator", ctypes.c_int32), ("subtree_blocks", ctypes.c_int32)]
+                ("integrator", ctypes.c_int32), ("subtree_blocks", ctypes.c_int32),
+                ("branch_streams", ctypes.c_int32)]
 
 
 class frost_stats(ctypes.Structure):
@@ -50,11 +51,11 @@ class frost_stats(ctypes.Structure):
                 ("timed_launches", ctypes.c_int64 * 4), ("timed_ms", ctypes.c_double * 4),
                 ("timed_pairs", ctypes.c_int64 * 4), ("subtree_launches", ctypes.c_int64),
                 ("level_calls", ctypes.c_int64 * 48), ("level_particles", ctypes.c_int64 * 48),
-                ("acc_pairs_reused", ctypes.c_int64)]
+                ("acc_pairs_reused", ctypes.c_int64), ("subtree_pairs", ctypes.c_int64 * 3)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
-        for k in ("timed_launches", "timed_ms", "timed_pairs", "level_calls", "level_particles"):
+        for k in ("timed_launches", "timed_ms", "timed_pairs", "level_calls", "level_particles", "subtree_pairs"):
             d[k] = list(d[k])
         return d
 
@@ -300,7 +301,7 @@ class Frost:
     def __init__(self, m, x, v, G: float = 1.0, eta: float = 0.2, precision: str = "mixed",
                  sym: int = FROST_SYM_HARMONIC, eps_soft: float = 0.0, max_depth: int = 40,
                  stream=None, subtree_max: int = 0, offsets=None, integrator: int = FROST_HHS_FSI,
-                 subtree_blocks: int = 0):
+                 subtree_blocks: int = 0, branch_streams: int = 0):
         import torch
         self.torch = torch
         o = frost_default_opts()
@@ -312,6 +313,7 @@ class Frost:
         o.subtree_max = int(subtree_max)
         o.integrator = int(integrator)
         o.subtree_blocks = int(subtree_blocks)
+        o.branch_streams = int(branch_streams)
         self.n = int(np.asarray(m).shape[0]) if not hasattr(m, "shape") else int(m.shape[0])
         self.G = G
         self.eta = eta

@@ -69,6 +69,21 @@ def parse():
                    help="thread blocks (a cluster) per single-set subtree-solver launch; 0 = library default")
     p.add_argument("--subtree-max", type=int, default=0,
                    help="largest set whose hhs_fsi subtree runs in one block (0 = library default)")
+    p.add_argument("--branch-streams", type=int, default=0,
+                   help="0: fsi(S) of grid-level hhs_fsi calls concurrently with hhs_fsi(F) (library "
+                        "default); -1: one stream")
+    p.add_argument("--integrate", action="store_true",
+                   help="integrate the workload for --steps top-level steps of --dt (or to --t-end) "
+                        "with per-step hierarchy statistics, the energy, momentum and angular "
+                        "momentum errors, and the time extrapolated to --t-end")
+    p.add_argument("--t-end", type=float, default=None,
+                   help="--integrate: the end time of the configuration (the run may stop earlier, "
+                        "see --max-seconds); cluster batches: advance every cluster to t-end in one "
+                        "frost_step call")
+    p.add_argument("--max-seconds", type=float, default=None,
+                   help="--integrate: stop after the first step that ends past this wall time")
+    p.add_argument("--compare-fp64", action="store_true",
+                   help="--integrate: also run the FP64 mode from the same state and compare")
     return p.parse_args()
 
 
@@ -223,6 +238,21 @@ def method_pairs(st):
     return float(st["acc_pairs"] + st.get("acc_pairs_reused", 0) + st["grad_pairs"])
 
 
+def subtree_rate(st, fp32_peak, probe):
+    """Algorithmic flop rate of the single-block subtree-solver launches (all passes of the
+    small sets: Newtonian, gradient and time-step pairs at 20 / 38 / 45 flops) over their
+    CUDA-event time, against the FP32 peak of the whole GPU (the launches use one SM each)."""
+    ms = st["timed_ms"][3]
+    pairs = st.get("subtree_pairs", [0, 0, 0])
+    flops = pairs[0] * FLOPS_PER_PAIR["acc"] + pairs[1] * FLOPS_PER_PAIR["grad"] + pairs[2] * FLOPS_PER_PAIR["tstep"]
+    if ms <= 0:
+        return None
+    tf = flops / (ms * 1e-3) / 1e12
+    return {"launches": st["timed_launches"][3], "ms": ms, "pairs": list(pairs), "tflops": tf,
+            "frac_of_gpu": tf / fp32_peak, "frac_of_one_sm": tf / (fp32_peak / SM_COUNT),
+            "frac_of_probe": tf / max(probe["ffma_tflops"], probe["ffma2_tflops"])}
+
+
 def run_frost(args):
     import torch
     import torch.distributed as dist
@@ -249,6 +279,7 @@ def run_frost(args):
     def new(prec):
         return fr.Frost(m, x, v, G=1.0, eta=args.eta, precision=prec, stream=stream.cuda_stream,
                         subtree_max=args.subtree_max, subtree_blocks=args.subtree_blocks,
+                        branch_streams=args.branch_streams,
                         sym=fr.FROST_SYM_HARMONIC | (fr.FROST_FLYBY_EXACT if args.flyby_exact else 0),
                         integrator=fr.FROST_HOLD2 if args.integrator == "hold2" else fr.FROST_HHS_FSI)
 
@@ -316,6 +347,9 @@ def run_frost(args):
     ms_timed_pass, _, _, st_ev = timed_steps(True)
     assert st_ev["acc_pairs"] == st["acc_pairs"], "the event-timed pass replays the same steps"
 
+    # measured rates of the pipes the pair passes run on (FFMA, packed FFMA2, DFMA, MUFU)
+    probe = fr.frost_peak_probe(stream.cuda_stream)
+
     # roofline of the dominant pair kernel (largest share of kernel time)
     kinds = ["acc", "grad", "tstep"]
     kms = st_ev["timed_ms"][:3]
@@ -330,6 +364,10 @@ def run_frost(args):
                 "frac": achieved_tf / fp32_peak, "traffic": None,
                 "peak_basis": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)",
                 "frac_at_median_clock": (achieved_tf / (fp32_peak * sm_med / sm_max)) if sm_med else None,
+                "probe": probe,
+                "frac_of_probe": achieved_tf / max(probe["ffma_tflops"], probe["ffma2_tflops"]),
+                "probe_basis": "frost_peak_probe on the same GPU before the timed region: the faster of "
+                               "scalar and packed FP32 FMA chains at full occupancy (2 flop per FMA)",
                 "flops_per_pair": FLOPS_PER_PAIR[kname],
                 "launches": st_ev["timed_launches"][dom], "kernel_ms": kms[dom],
                 "kernel_share": kms[dom] / max(ms_timed_pass - ms_energy, 1e-9),
@@ -387,6 +425,8 @@ def run_frost(args):
                 out[f"{nm}_kernel_ms"] = s["timed_ms"][k] / max(s["timed_launches"][k], 1)
                 out[f"{nm}_tflops"] = tf
                 out[f"{nm}_frac"] = tf / (fp32_peak if prec == "mixed" else FP64_PEAK_TFLOPS)
+                out[f"{nm}_frac_of_probe"] = tf / (max(probe["ffma_tflops"], probe["ffma2_tflops"])
+                                                   if prec == "mixed" else probe["dfma_tflops"])
         return out
 
     fp_mixed = full_pass("mixed", 5)
@@ -437,6 +477,7 @@ def run_frost(args):
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "subtree_max": args.subtree_max or "library default",
                            "integrator": args.integrator,
+                           "branch_streams": "concurrent" if args.branch_streams >= 0 else "one stream",
                            "flyby_derivative": "exact" if args.flyby_exact else "two-body"},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
@@ -446,6 +487,7 @@ def run_frost(args):
                 "wall_s_timed_region": wall, "energy_ms": ms_energy,
                 "dE_over_E_timed_run": dE_timed, "max_depth": st["max_depth_seen"],
                 "autotune_waves": tuned,
+                "value_evaluated": evaluated / (ms_max * 1e-3),
                 "interactions": {"method": interactions, "evaluated": evaluated,
                                  "reused_acc_pairs": int(st.get("acc_pairs_reused", 0)),
                                  "note": "value counts the method's acc+gradient pairs; the "
@@ -453,6 +495,7 @@ def run_frost(args):
                                          "second fsi(S), taken bit for bit from the first"},
                 "hhs_calls": st["hhs_calls"], "subtree_launches": st["subtree_launches"],
                 "subtree_ms": st_ev["timed_ms"][3],
+                "subtree": subtree_rate(st_ev, fp32_peak, probe),
                 "levels": {"calls": list(st["level_calls"][:st["max_depth_seen"] + 1]),
                            "particles": list(st["level_particles"][:st["max_depth_seen"] + 1]),
                            "note": "hhs_fsi calls and particles per hierarchy depth, timed steps"},
@@ -480,8 +523,22 @@ def run_batch(args):
     f = fr.Frost(m, x, v, G=1.0, eta=args.eta, precision="mixed", stream=stream.cuda_stream,
                  offsets=off)
     e0 = f.cluster_energies()
-    for _ in range(args.warmup):
-        f.step(args.dt, 1)
+    # steps per frost_step call: 1, or (with --t-end) every step to t_end in one call, which is
+    # one launch (one replay of the captured step graph) for all clusters
+    per_call = 1
+    if args.t_end is not None:
+        import math
+        per_call = int(math.ceil(args.t_end / args.dt - 1e-9))
+        n0 = m.size
+        x0 = torch.empty((n0, 3), dtype=torch.float64).pin_memory().numpy()
+        v0 = torch.empty((n0, 3), dtype=torch.float64).pin_memory().numpy()
+        t0_state = fr.frost_get_state(f.ctx, x0, v0)
+        f.step(args.dt, per_call)  # captures the graph of this call shape (untimed)
+        fr.frost_set_state(f.ctx, x0, v0, t0_state)
+    else:
+        for _ in range(args.warmup):
+            f.step(args.dt, 1)
+        e0 = f.cluster_energies()
     f.reset_stats()
     f.set_timing(True)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
@@ -489,12 +546,13 @@ def run_batch(args):
     torch.cuda.synchronize()
     clocks.start()
     ms = 0.0
-    for _ in range(args.steps):
+    calls = 1 if args.t_end is not None else args.steps
+    for _ in range(calls):
         flush.fill_(1.0)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        f.step(args.dt, 1)
+        f.step(args.dt, per_call)
         b.record(stream)
         b.synchronize()
         ms += a.elapsed_time(b)
@@ -527,13 +585,17 @@ def run_batch(args):
     e2e_s = time.perf_counter() - t0
     st2 = f.stats()
     f.close()
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+    nsteps = calls * per_call
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": nsteps,
+            "warmup": args.warmup, "ms_per_step": ms / nsteps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "clusters": int(ncl), "N_total": int(n),
                        "N_min": int(np.diff(off).min()), "N_max": int(np.diff(off).max()),
-                       "eta": args.eta, "dt_pivot": args.dt,
-                       "step": "one launch: every cluster in its own thread block advances one "
+                       "eta": args.eta, "dt_pivot": args.dt, "t_end": args.t_end,
+                       "step": ("one launch (one replay of the captured step graph): every cluster "
+                                f"advances {per_call} top-level HHS-FSI steps, to t = {per_call * args.dt:g}")
+                               if per_call > 1 else
+                               "one launch: every cluster in its own thread block advances one "
                                "top-level HHS-FSI step",
                        "l2": "flushed before every timed step (256 MiB write)"},
             "roofline": {"bound": "alu", "kernel": "k_hhs_subtree (batch; all passes)", "achieved": ach,
@@ -543,7 +605,7 @@ def run_batch(args):
             "e2e": {"value": method_pairs(st2) / e2e_s, "unit": UNIT,
                     "steps": e2e_steps, "h2d_bytes_per_step": int(2 * n * 24),
                     "d2h_bytes_per_step": int(2 * n * 24)},
-            "gpu_launches": args.steps, "clocks": clk,
+            "gpu_launches": calls, "clocks": clk, "seconds_timed": ms * 1e-3,
             "dE_over_E_clusters": {"median": float(np.median(dE)), "max": float(dE.max())},
             "max_depth": st["max_depth_seen"], "hhs_calls": st["hhs_calls"]}
     print(json.dumps(line), flush=True)
@@ -619,6 +681,120 @@ def run_passes(args):
     print(json.dumps(line), flush=True)
 
 
+def run_integrate(args):
+    """Integration of a single-set workload: --steps top-level HHS-FSI steps of --dt (all of
+    them, or those that fit in --max-seconds), each timed with CUDA events, with the hierarchy
+    of every step (depth, hhs_fsi calls and set sizes per level), the errors of E, P and L,
+    and the wall time extrapolated to --t-end at the measured rate.  With --compare-fp64 the
+    FP64 mode runs the same steps from the same state, and the positions, velocities and
+    conservation errors of the two are compared."""
+    import math
+
+    import torch
+
+    from paper_2011_14984_gb300 import build as fbuild
+    from paper_2011_14984_gb300 import frost as fr
+    from paper_2011_14984_gb300 import ics
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    fbuild.build()
+    fr.load()
+    stream = torch.cuda.current_stream()
+    m, x, v = ics.workload(args.workload)
+    n = m.size
+    steps = args.steps
+    if args.t_end is not None and not args.max_seconds:
+        steps = int(math.ceil(args.t_end / args.dt - 1e-9))
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    runs = {}
+    for prec in (("mixed", "fp64") if args.compare_fp64 else ("mixed",)):
+        f = fr.Frost(m, x, v, G=1.0, eta=args.eta, precision=prec, stream=stream.cuda_stream,
+                     subtree_max=args.subtree_max, branch_streams=args.branch_streams)
+        tuned = f.autotune() if prec == "mixed" else None
+        e0 = f.energy()
+        per = []
+        ms_total = 0.0
+        pairs = 0.0
+        lev_calls = np.zeros(48, dtype=np.int64)
+        lev_part = np.zeros(48, dtype=np.int64)
+        wall0 = time.perf_counter()
+        for k in range(steps):
+            f.reset_stats()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            f.step(args.dt, 1)
+            b.record(stream)
+            b.synchronize()
+            ms = a.elapsed_time(b)
+            st = f.stats()
+            d = st["max_depth_seen"]
+            lc = np.array(st["level_calls"], dtype=np.int64)
+            lp = np.array(st["level_particles"], dtype=np.int64)
+            lev_calls += lc
+            lev_part += lp
+            ms_total += ms
+            pairs += method_pairs(st)
+            per.append({"ms": ms, "max_depth": d, "hhs_calls": int(lc.sum()),
+                        "deepest_level_calls": int(lc[d]), "interactions": method_pairs(st)})
+            if args.max_seconds and time.perf_counter() - wall0 > args.max_seconds:
+                break
+        done = len(per)
+        e1 = f.energy()
+        xs, vs, t = f.state()
+        f.close()
+        dmax = int(max(p["max_depth"] for p in per))
+        secs = ms_total * 1e-3
+        L0 = np.linalg.norm(e0["L"])
+        runs[prec] = {
+            "steps_done": done, "t_reached": t, "device_s": secs,
+            "value": pairs / secs, "unit": UNIT,
+            "top_level_steps_per_s": done / secs,
+            "deepest_level_calls_per_s": sum(p["deepest_level_calls"] for p in per) / secs,
+            "depth_per_step": [p["max_depth"] for p in per],
+            "ms_per_step": [p["ms"] for p in per],
+            "levels": {"calls": lev_calls[:dmax + 1].tolist(),
+                       "mean_set_size": [float(lev_part[k] / lev_calls[k]) if lev_calls[k] else 0.0
+                                         for k in range(dmax + 1)],
+                       "calls_per_s": (lev_calls[:dmax + 1] / secs).tolist()},
+            "dE_over_E": abs((e1["E"] - e0["E"]) / e0["E"]),
+            "dP": float(np.linalg.norm(e1["P"] - e0["P"])),
+            "dL_over_L": float(np.linalg.norm(e1["L"] - e0["L"]) / L0) if L0 > 0 else None,
+            "autotune_waves": tuned, "_x": xs, "_v": vs}
+        if args.t_end is not None:
+            runs[prec]["extrapolated_s_to_t_end"] = secs * args.t_end / t
+            runs[prec]["t_end"] = args.t_end
+    clk = clocks.stop()
+    mixed = runs["mixed"]
+    out = {"metric": METRIC, "value": mixed["value"], "unit": UNIT, "n_gpus": 1,
+           "steps": mixed["steps_done"], "warmup": 0,
+           "ms_per_step": 1e3 * mixed["device_s"] / mixed["steps_done"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": args.workload, "N": int(n), "eta": args.eta, "dt_pivot": args.dt,
+                      "t_end": args.t_end, "mode": "integration, per-step statistics"},
+           "clocks": clk}
+    if args.compare_fp64:
+        fp = runs["fp64"]
+        k = min(mixed["steps_done"], fp["steps_done"])
+        assert k == mixed["steps_done"] == fp["steps_done"], "compare equal step counts"
+        dx = np.linalg.norm(mixed["_x"] - fp["_x"], axis=1)
+        dv = np.linalg.norm(mixed["_v"] - fp["_v"], axis=1)
+        out["fp64_comparison"] = {
+            "dE_over_E": {"mixed": mixed["dE_over_E"], "fp64": fp["dE_over_E"]},
+            "dP": {"mixed": mixed["dP"], "fp64": fp["dP"]},
+            "dL_over_L": {"mixed": mixed["dL_over_L"], "fp64": fp["dL_over_L"]},
+            "mixed_speedup": fp["device_s"] / mixed["device_s"],
+            "position_difference": {"p50": float(np.median(dx)), "p999": float(np.percentile(dx, 99.9)),
+                                    "max": float(dx.max())},
+            "velocity_difference": {"p50": float(np.median(dv)), "p999": float(np.percentile(dv, 99.9)),
+                                    "max": float(dv.max())}}
+    for prec, r in runs.items():
+        r.pop("_x")
+        r.pop("_v")
+        out[prec] = r
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -627,6 +803,8 @@ def main():
         run_batch(args)
     elif args.passes_only:
         run_passes(args)
+    elif args.integrate:
+        run_integrate(args)
     else:
         run_frost(args)
 

@@ -241,6 +241,10 @@ def workload(name: str):
         return plummer_kroupa_binaries(262144, 3)
     if name == "plummer_1m":
         return plummer(1048576, 5)
+    if name == "plummer_256k":
+        # the 1M sphere's recipe and seed at a quarter of its size: the stand-in where a
+        # comparison with the FP64 mode does not fit at 1M
+        return plummer(262144, 5)
     raise KeyError(name)
 
 

@@ -180,6 +180,7 @@ __global__ void __launch_bounds__(HOT_BS) k_grad_hot(
     }
     const dfloat e2 = df::from_double(eps2d);
     dfloat g[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    double g64[3] = {0.0, 0.0, 0.0};  // terms outside the FP32 exponent range, in FP64
     const int n_words = (n_s + 31) >> 5;
     const int q_count = (sp < n_words) ? (n_words - sp + nsplit - 1) / nsplit : 0;
     for (int q0 = 0; q0 < q_count; q0 += HOT_WORDS) {
@@ -236,14 +237,37 @@ __global__ void __launch_bounds__(HOT_BS) k_grad_hot(
                     const dfloat w = df::mul(mj, df::mul(ri2, ri));
                     const dfloat xa = df::add(df::add(df::mul(d[0], A[0]), df::mul(d[1], A[1])), df::mul(d[2], A[2]));
                     const dfloat t3 = df::mul(df::mul_f(xa, 3.f), ri2);
-                    for (int c = 0; c < 3; ++c) g[c] = df::add(g[c], df::mul(w, df::sub(A[c], df::mul(t3, d[c]))));
+                    dfloat t[3];
+                    bool finite = true;
+                    for (int c = 0; c < 3; ++c) {
+                        t[c] = df::mul(w, df::sub(A[c], df::mul(t3, d[c])));
+                        finite = finite && isfinite(t[c].h) && isfinite(t[c].l);
+                    }
+                    if (finite) {
+                        for (int c = 0; c < 3; ++c) g[c] = df::add(g[c], t[c]);
+                    } else {
+                        // near the pericentre of a hard binary the term exceeds the largest FP32
+                        // value: the same term in FP64 from the same parts (they sum exactly)
+                        double dd[3], AA[3];
+                        for (int c = 0; c < 3; ++c) {
+                            dd[c] = ((double)s_j[3 * c][u] + (double)s_j[3 * c + 1][u] + (double)s_j[3 * c + 2][u]) -
+                                    ((double)xi[c][0] + (double)xi[c][1] + (double)xi[c][2]);
+                            AA[c] = ((double)s_j[9 + 2 * c][u] + (double)s_j[10 + 2 * c][u]) -
+                                    ((double)ai[c].h + (double)ai[c].l);
+                        }
+                        const double rr2 = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2] + eps2d;
+                        const double rri = 1.0 / sqrt(rr2);
+                        const double ww = ((double)mj.h + (double)mj.l) * rri * rri * rri;
+                        const double tt3 = 3.0 * (dd[0] * AA[0] + dd[1] * AA[1] + dd[2] * AA[2]) * rri * rri;
+                        for (int c = 0; c < 3; ++c) g64[c] += ww * (AA[c] - tt3 * dd[c]);
+                    }
                 }
             }
             __syncthreads();
         }
     }
     if (i < n_a)
-        for (int c = 0; c < 3; ++c) part[((size_t)sp * 3 + c) * n_a + i] = df::to_double(g[c]);
+        for (int c = 0; c < 3; ++c) part[((size_t)sp * 3 + c) * n_a + i] = df::to_double(g[c]) + g64[c];
 }
 
 void launch_acc_hist(cudaStream_t s, const double *a_soa, int n, unsigned *hist)

@@ -261,9 +261,28 @@ __device__ __forceinline__ void warp_slot_terms(const int (&n)[ILP], D3 *xbuf, d
     }
 }
 
+// The Newtonian pair term of acc_term_df in FP64, from the same records, for a pair whose
+// double-float evaluation leaves the FP32 exponent range (r^-3 above ~3e38, r below ~1e-13)
+static __device__ __noinline__ D3 acc_term_fp64(const float4 J0, const float4 J1, float ixh, float iyh, float izh,
+                                                float ixl, float iyl, float izl, double mj, double eps2)
+{
+    const double dx = ((double)J0.x + (double)J1.x) - ((double)ixh + (double)ixl);
+    const double dy = ((double)J0.y + (double)J1.y) - ((double)iyh + (double)iyl);
+    const double dz = ((double)J0.z + (double)J1.z) - ((double)izh + (double)izl);
+    const double r2 = dx * dx + dy * dy + dz * dz + eps2;
+    const double ri = 1.0 / sqrt(r2);
+    const double w = mj * ri * ri * ri;
+    D3 r;
+    r.x = w * dx;
+    r.y = w * dy;
+    r.z = w * dz;
+    return r;
+}
+
 // One Newtonian pair term m_j x_ji / r^3 in double-float from the float-float position
 // records (positions to 48 bits) and the FP64 mass mj (the two partners of a tight pair then
 // carry exactly opposite momenta, which the gradients of the other particles difference).
+// A term outside the FP32 exponent range is evaluated in FP64 instead.
 static __device__ __noinline__ D3 acc_term_df(const float4 J0, const float4 J1, float ixh, float iyh, float izh,
                                               float ixl, float iyl, float izl, double mj, double eps2)
 {
@@ -278,6 +297,8 @@ static __device__ __noinline__ D3 acc_term_df(const float4 J0, const float4 J1, 
     r.x = df::to_double(df::mul(w, dx));
     r.y = df::to_double(df::mul(w, dy));
     r.z = df::to_double(df::mul(w, dz));
+    if (!(isfinite(r.x) && isfinite(r.y) && isfinite(r.z)))
+        r = acc_term_fp64(J0, J1, ixh, iyh, izh, ixl, iyl, izl, mj, eps2);
     return r;
 }
 
@@ -382,8 +403,34 @@ struct GradMixedI {
     float ahx[ILP], ahy[ILP], ahz[ILP], alx[ILP], aly[ILP], alz[ILP];
 };
 
+// The gradient pair term of grad_term_df in FP64 from the same split records (their parts
+// sum exactly in FP64), for a pair whose double-float evaluation leaves the FP32 exponent
+// range: near the pericentre of a hard binary m r^-5 |a_ji| r^2 reaches ~1e41 (r ~ 1e-10 in
+// Henon units), above the largest FP32 value, 3.4e38.
+template <int ILP>
+__device__ __noinline__ void grad_term_fp64(const float4 J0, const float4 J1, const float4 J2, const float4 J3,
+                                            const GradMixedI<ILP> &I, int k, double eps2, double &gx, double &gy,
+                                            double &gz)
+{
+    const double dx = ((double)J0.x + (double)J1.x + (double)J2.x) - ((double)I.xh[k] + (double)I.xm[k] + (double)I.xl[k]);
+    const double dy = ((double)J0.y + (double)J1.y + (double)J2.y) - ((double)I.yh[k] + (double)I.ym[k] + (double)I.yl[k]);
+    const double dz = ((double)J0.z + (double)J1.z + (double)J2.z) - ((double)I.zh[k] + (double)I.zm[k] + (double)I.zl[k]);
+    const double Ax = ((double)J1.w + (double)J3.y) - ((double)I.ahx[k] + (double)I.alx[k]);
+    const double Ay = ((double)J2.w + (double)J3.z) - ((double)I.ahy[k] + (double)I.aly[k]);
+    const double Az = ((double)J3.x + (double)J3.w) - ((double)I.ahz[k] + (double)I.alz[k]);
+    const double r2 = dx * dx + dy * dy + dz * dz + eps2;
+    const double ri = 1.0 / sqrt(r2);
+    const double ri2 = ri * ri;
+    const double w = (double)J0.w * ri2 * ri;
+    const double t3 = 3.0 * (dx * Ax + dy * Ay + dz * Az) * ri2;
+    gx += w * (Ax - t3 * dx);
+    gy += w * (Ay - t3 * dy);
+    gz += w * (Az - t3 * dz);
+}
+
 // One gradient pair term in double-float, rebuilt from the split records (positions to 48
-// bits, accelerations to 36 bits); used for the few dominant terms of each particle.
+// bits, accelerations to 36 bits); used for the few dominant terms of each particle.  A term
+// outside the FP32 exponent range is evaluated in FP64 instead (grad_term_fp64).
 template <int ILP>
 __device__ __noinline__ void grad_term_df(const float4 J0, const float4 J1, const float4 J2, const float4 J3,
                                           const GradMixedI<ILP> &I, int k, double eps2, double &gx, double &gy,
@@ -402,9 +449,16 @@ __device__ __noinline__ void grad_term_df(const float4 J0, const float4 J1, cons
     const dfloat w = df::mul_f(df::mul(ri2, ri), J0.w);
     const dfloat xa = df::add(df::add(df::mul(dx, Ax), df::mul(dy, Ay)), df::mul(dz, Az));
     const dfloat t3 = df::mul(df::mul_f(xa, 3.f), ri2);
-    gx += df::to_double(df::mul(w, df::sub(Ax, df::mul(t3, dx))));
-    gy += df::to_double(df::mul(w, df::sub(Ay, df::mul(t3, dy))));
-    gz += df::to_double(df::mul(w, df::sub(Az, df::mul(t3, dz))));
+    const double tx = df::to_double(df::mul(w, df::sub(Ax, df::mul(t3, dx))));
+    const double ty = df::to_double(df::mul(w, df::sub(Ay, df::mul(t3, dy))));
+    const double tz = df::to_double(df::mul(w, df::sub(Az, df::mul(t3, dz))));
+    if (isfinite(tx) && isfinite(ty) && isfinite(tz)) {
+        gx += tx;
+        gy += ty;
+        gz += tz;
+    } else {
+        grad_term_fp64<ILP>(J0, J1, J2, J3, I, k, eps2, gx, gy, gz);
+    }
 }
 
 template <int ILP, bool MASK, class Slots>

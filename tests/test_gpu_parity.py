@@ -449,6 +449,27 @@ def test_hhs_fsi_mixed_energy_parity():
     assert dE["mixed"] < 2 * dE["fp64"] + 1e-11, dE
 
 
+@pytest.mark.parametrize("precision,n,subtree_max", [("mixed", 16384, 0), ("mixed", 4096, 64),
+                                                      ("fp64", 4096, 100)])
+def test_concurrent_branches_are_bit_identical_to_the_serial_order(precision, n, subtree_max):
+    """fsi(S) of every grid-level hhs_fsi call runs on a stream of its own, concurrently with
+    hhs_fsi(F) (disjoint particles): the state after two steps is the serial order's bit for
+    bit, with the same pair counts and depth; small subtree thresholds put several grid
+    levels (several branch streams) in flight at once."""
+    m, x, v = ics.plummer(n, 40 + n % 7)
+    out = {}
+    for branch in (0, -1):
+        f = F(m, x, v, precision=precision, eta=0.2, subtree_max=subtree_max, branch_streams=branch)
+        f.step(2.0 ** -7, 2)
+        xg, vg, _ = f.state()
+        st = f.stats()
+        out[branch] = (xg, vg, st["acc_pairs"], st["grad_pairs"], st["max_depth_seen"], st["hhs_calls"])
+        f.close()
+    assert out[0][4] >= 3
+    assert np.array_equal(out[0][0], out[-1][0]) and np.array_equal(out[0][1], out[-1][1])
+    assert out[0][2:] == out[-1][2:]
+
+
 def test_solar_system_hhs_fsi_on_gpu():
     """The paper's five-body initial state (App. A1) through frost_step in FP64: the same
     trajectory as the oracle after 200 years at eta = 0.05."""
@@ -744,15 +765,44 @@ def test_full_cluster_batch_fp64_one_step_sampled_clusters():
     assert np.max(np.abs(p1 - p0)) < 1e-14
 
 
-@pytest.mark.parametrize("precision", ["fp64"])
-def test_kroupa_hard_binaries_trajectory_fp64(precision):
+def test_mixed_gradient_beyond_the_fp32_range_at_a_binary_pericentre():
+    """A Kroupa sphere (N = 2000) with two members 7e-11 apart, the pericentre of the tightest
+    binary of the 262k hard-binary workload (a = 1.6e-5, e = 0.999996): their mutual gradient
+    term, m r^-5 |r^2 a_ji - 3 (x.a) x| ~ 1e45, is beyond the largest FP32 value (3.4e38), so
+    the double-float evaluation of a dominant term overflows and the library evaluates that
+    term in FP64.  The mixed pass stays finite and meets the mixed-mode bars against the
+    oracle for every particle (a and g to 1e-6 at p99.9, 1e-5 at most)."""
+    m, x, v = ics.plummer(2000, 77, masses=ics.kroupa_masses(2000, 77))
+    d = np.random.default_rng(1).normal(size=3)
+    x[1] = x[0] + 7e-11 * d / np.linalg.norm(d)
+    A = np.arange(m.size, dtype=np.int32)
+    a_ref, g_ref = oracle_g(m, x, A, A)
+    f = F(m, x, v, precision="mixed")
+    out = f.accel_gradient(None, None, eps_grad=2.0 ** -20)
+    f.close()
+    a, g = cpu(out["acc"]), cpu(out["grad"])
+    assert np.isfinite(a).all() and np.isfinite(g).all()
+    assert np.linalg.norm(g_ref[:2], axis=1).min() > 1e40  # the case is out of the FP32 range
+    ea, eg = rel(a, a_ref), rel(g, g_ref)
+    assert p999(ea) < 1e-6 and ea.max() < 1e-5, (p999(ea), ea.max())
+    assert p999(eg) < 1e-6 and eg.max() < 1e-5, (p999(eg), eg.max(), eg[:2])
+
+
+def test_kroupa_hard_binaries_trajectory_fp64():
     """Plummer N = 2000 with Kroupa masses and 5 % hard binaries (a in [1e-5, 1e-3], thermal
     e; seed 31): one top-level step of 2^-10 reaches hierarchy depth 19, through the grid
-    levels, the single-block subtree solver and its one-warp path.  FP64 positions within
-    1e-10 and velocities within 1e-8 of the oracle (binary orbital speeds reach ~10), and the
-    same depth."""
+    levels, the single-block subtree solver and its one-warp path.
+
+    Tolerance.  Over the ~2^19 sub-steps of the hardest binaries, FP64 round-off is amplified
+    along the orbits: the oracle run on the same particles relabelled in reverse order (the
+    same arithmetic, every sum in another order) differs from the oracle by ~6e-6 in the
+    velocity of a binary member at ~6 (a relative error of 1e-6 in the binary's separation),
+    while positions agree to 1e-11.  So: the same depth; positions within 1e-10; velocities
+    within 4x the oracle's own spread under that relabelling (and within 1e-12 of it for the
+    particles outside binaries, whose orbits are regular)."""
     m, x, v = ics.plummer_kroupa_binaries(2000, 31)
-    f = F(m, x, v, precision=precision, eta=0.2)
+    n = m.size
+    f = F(m, x, v, precision="fp64", eta=0.2)
     f.step(2.0 ** -10, 1)
     xg, vg, _ = f.state()
     st = f.stats()
@@ -760,9 +810,50 @@ def test_kroupa_hard_binaries_trajectory_fp64(precision):
     oracle.reset_counters()
     xo, vo = oracle.steps(m, x, v, 2.0 ** -10, 1, eta=0.2)
     oc = oracle.counters()
+    rev = np.arange(n)[::-1]
+    xr, vr = oracle.steps(m[rev], x[rev], v[rev], 2.0 ** -10, 1, eta=0.2)
+    xr, vr = xr[rev], vr[rev]
+    spread_v = np.max(np.abs(vr - vo))
     assert st["max_depth_seen"] == oc["max_depth"] >= 15, (st["max_depth_seen"], oc["max_depth"])
     assert np.max(np.abs(xg - xo)) < 1e-10, np.max(np.abs(xg - xo))
-    assert np.max(np.abs(vg - vo)) < 1e-8, np.max(np.abs(vg - vo))
+    assert np.max(np.abs(vg - vo)) <= 4.0 * spread_v, (np.max(np.abs(vg - vo)), spread_v)
+    n_single = n - 2 * int(round(0.05 * n / 2.0))
+    assert np.max(np.abs(vg[:n_single] - vo[:n_single])) < 1e-12
+
+
+def test_plummer_64k_mixed_trajectory_matches_fp64():
+    """Plummer N = 65536 (seed 2), two top-level steps of 2^-7 (t = 2^-6) in the mixed mode and
+    in the FP64 mode on the GPU, compared particle by particle.
+
+    Tolerance, from the arithmetic: the mixed Newtonian pass carries a relative error of
+    0.7-1.4e-7 at the 99.9th percentile (at most 1e-5 per particle), and a kick or drift adds
+    no error of its own (FP64, the oracle's roundings), so an acceleration error eps |a|
+    held over the run moves v by eps |a| t and x by eps |a| t^2 / 2.  With eps = 2e-7 and
+    |a| = 2 (above the 99th percentile of |a| in the sphere, 1.3) the 99.9th percentiles are
+    bounded by 6.2e-9 (v) and 4.9e-11 (x); the 32 largest deviations are each bounded with
+    eps = 1e-5 and 4 max(|a_i|, 2), |a_i| from the oracle at t = 0.  The two runs reach the
+    same depth."""
+    m, x, v = ics.workload("plummer_64k")
+    n = m.size
+    t = 2.0 * 2.0 ** -7
+    out = {}
+    for prec in ("fp64", "mixed"):
+        f = F(m, x, v, precision=prec, eta=0.2)
+        f.step(2.0 ** -7, 2)
+        xg, vg, _ = f.state()
+        out[prec] = (xg, vg, f.stats()["max_depth_seen"])
+        f.close()
+    assert out["fp64"][2] == out["mixed"][2]
+    dx = np.linalg.norm(out["mixed"][0] - out["fp64"][0], axis=1)
+    dv = np.linalg.norm(out["mixed"][1] - out["fp64"][1], axis=1)
+    eps, A = 2e-7, 2.0
+    assert p999(dx) < 0.5 * eps * A * t * t, p999(dx)
+    assert p999(dv) < eps * A * t, p999(dv)
+    top = np.argsort(np.maximum(dx / (t * t), dv / t))[-32:].astype(np.int32)
+    a_top = np.linalg.norm(oracle.acc(m, x, top, np.arange(n, dtype=np.int32)), axis=1)
+    bound_a = 1e-5 * 4.0 * np.maximum(a_top, A)
+    assert np.all(dx[top] < 0.5 * bound_a * t * t), (dx[top].max(), a_top)
+    assert np.all(dv[top] < bound_a * t), (dv[top].max(), a_top)
 
 
 # ---------------------------------------------------------------------------------------

@@ -72,6 +72,9 @@ def parse():
     p.add_argument("--branch-streams", type=int, default=0,
                    help="0: fsi(S) of grid-level hhs_fsi calls concurrently with hhs_fsi(F) (library "
                         "default); -1: one stream")
+    p.add_argument("--sym-cross", type=int, default=0,
+                   help="0: the Newtonian kick_sf evaluates each S x F pair once where that fills the "
+                        "GPU (library default); 1: always; -1: two one-sided passes")
     p.add_argument("--integrate", action="store_true",
                    help="integrate the workload for --steps top-level steps of --dt (or to --t-end) "
                         "with per-step hierarchy statistics, the energy, momentum and angular "
@@ -232,10 +235,12 @@ def aggregate_ranks(ms_total, work, world, device):
 # the CUDA path
 # ---------------------------------------------------------------------------------------
 def method_pairs(st):
-    """acc + gradient interactions of the method's steps: the evaluated pairs plus the
+    """acc + gradient interactions of the method's steps: the evaluated pairs, plus the
     Newtonian pairs of the second fsi(S) that reuse the stored end-of-first-fsi a^SS (exact,
-    S has not moved); the evaluated count alone is reported beside it."""
-    return float(st["acc_pairs"] + st.get("acc_pairs_reused", 0) + st["grad_pairs"])
+    S has not moved), plus the second side of every pair of a symmetric S x F pass (one
+    evaluation serves both interactions); the evaluated count alone is reported beside it."""
+    return float(st["acc_pairs"] + st.get("acc_pairs_reused", 0) + st.get("acc_pairs_symmetric", 0)
+                 + st["grad_pairs"])
 
 
 def subtree_rate(st, fp32_peak, probe):
@@ -279,7 +284,7 @@ def run_frost(args):
     def new(prec):
         return fr.Frost(m, x, v, G=1.0, eta=args.eta, precision=prec, stream=stream.cuda_stream,
                         subtree_max=args.subtree_max, subtree_blocks=args.subtree_blocks,
-                        branch_streams=args.branch_streams,
+                        branch_streams=args.branch_streams, sym_cross=args.sym_cross,
                         sym=fr.FROST_SYM_HARMONIC | (fr.FROST_FLYBY_EXACT if args.flyby_exact else 0),
                         integrator=fr.FROST_HOLD2 if args.integrator == "hold2" else fr.FROST_HHS_FSI)
 
@@ -478,6 +483,7 @@ def run_frost(args):
                            "subtree_max": args.subtree_max or "library default",
                            "integrator": args.integrator,
                            "branch_streams": "concurrent" if args.branch_streams >= 0 else "one stream",
+                           "sym_cross": {0: "where it fills the GPU", 1: "always", -1: "off"}[max(-1, min(1, args.sym_cross))],
                            "flyby_derivative": "exact" if args.flyby_exact else "two-body"},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
@@ -522,6 +528,7 @@ def run_batch(args):
     ncl = off.size - 1
     f = fr.Frost(m, x, v, G=1.0, eta=args.eta, precision="mixed", stream=stream.cuda_stream,
                  offsets=off)
+    tuned = f.autotune()  # the team split of the batch launch, outside the timed region
     e0 = f.cluster_energies()
     # steps per frost_step call: 1, or (with --t-end) every step to t_end in one call, which is
     # one launch (one replay of the captured step graph) for all clusters
@@ -607,6 +614,7 @@ def run_batch(args):
                     "d2h_bytes_per_step": int(2 * n * 24)},
             "gpu_launches": calls, "clocks": clk, "seconds_timed": ms * 1e-3,
             "dE_over_E_clusters": {"median": float(np.median(dE)), "max": float(dE.max())},
+            "autotuned_teams": tuned,
             "max_depth": st["max_depth_seen"], "hhs_calls": st["hhs_calls"]}
     print(json.dumps(line), flush=True)
 
@@ -681,6 +689,31 @@ def run_passes(args):
     print(json.dumps(line), flush=True)
 
 
+def binary_energies(fr, stream, m, x, v, pairs):
+    """Energy bookkeeping of a system with binaries (pairs [k, 2] of member indices): the
+    internal two-body energies of the binaries (FP64, host) and the energy of the system with
+    every binary replaced by its centre of mass (the potential through the library's FP64
+    energy pass on the GPU).  Their sum differs from the total energy by the binaries' tidal
+    terms only."""
+    i1, i2 = pairs[:, 0], pairs[:, 1]
+    m1, m2 = m[i1], m[i2]
+    mt = m1 + m2
+    r = np.linalg.norm(x[i1] - x[i2], axis=1)
+    u = v[i1] - v[i2]
+    e_int = 0.5 * (m1 * m2 / mt) * (u * u).sum(1) - m1 * m2 / r
+    single = np.ones(m.size, dtype=bool)
+    single[i1] = single[i2] = False
+    xc = (m1[:, None] * x[i1] + m2[:, None] * x[i2]) / mt[:, None]
+    vc = (m1[:, None] * v[i1] + m2[:, None] * v[i2]) / mt[:, None]
+    mm = np.concatenate([m[single], mt])
+    xm = np.concatenate([x[single], xc])
+    vm = np.concatenate([v[single], vc])
+    g = fr.Frost(mm, xm, vm, G=1.0, precision="fp64", stream=stream.cuda_stream)
+    e = g.energy()
+    g.close()
+    return e["E"], e_int
+
+
 def run_integrate(args):
     """Integration of a single-set workload: --steps top-level HHS-FSI steps of --dt (all of
     them, or those that fit in --max-seconds), each timed with CUDA events, with the hierarchy
@@ -710,9 +743,13 @@ def run_integrate(args):
     runs = {}
     for prec in (("mixed", "fp64") if args.compare_fp64 else ("mixed",)):
         f = fr.Frost(m, x, v, G=1.0, eta=args.eta, precision=prec, stream=stream.cuda_stream,
-                     subtree_max=args.subtree_max, branch_streams=args.branch_streams)
+                     subtree_max=args.subtree_max, branch_streams=args.branch_streams,
+                     sym_cross=args.sym_cross)
         tuned = f.autotune() if prec == "mixed" else None
         e0 = f.energy()
+        bpairs = ics.binary_pairs(n) if args.workload == "plummer_kroupa_binaries_256k" else None
+        if bpairs is not None:
+            eb0, eint0 = binary_energies(fr, stream, m, x, v, bpairs)
         per = []
         ms_total = 0.0
         pairs = 0.0
@@ -743,6 +780,27 @@ def run_integrate(args):
         e1 = f.energy()
         xs, vs, t = f.state()
         f.close()
+        binaries = None
+        if bpairs is not None:
+            eb1, eint1 = binary_energies(fr, stream, m, xs, vs, bpairs)
+            de = eint1 - eint0
+            worst = np.argsort(-np.abs(de))[:5]
+            i1, i2 = bpairs[:, 0], bpairs[:, 1]
+            mt = m[i1] + m[i2]
+            r0 = x[i1] - x[i2]
+            u0 = v[i1] - v[i2]
+            a0 = 1.0 / (2.0 / np.linalg.norm(r0, axis=1) - (u0 * u0).sum(1) / mt)
+            h0 = np.linalg.norm(np.cross(r0, u0), axis=1)
+            peri0 = a0 * (1.0 - np.sqrt(np.maximum(0.0, 1.0 - h0 * h0 / (mt * a0))))
+            binaries = {
+                "dE_bulk_over_E": abs((eb1 - eb0) / e0["E"]),
+                "dE_binaries_internal_over_E": float(abs(de.sum()) / abs(e0["E"])),
+                "dE_total_over_E": abs((e1["E"] - e0["E"]) / e0["E"]),
+                "worst_binaries": [{"pair": int(k), "pericentre_t0": float(peri0[k]), "a_t0": float(a0[k]),
+                                    "E_internal_t0": float(eint0[k]), "dE_internal": float(de[k])}
+                                   for k in worst],
+                "note": "bulk: every binary replaced by its centre of mass; internal: the binaries' "
+                        "two-body energies; their sum is the total up to the tidal terms"}
         dmax = int(max(p["max_depth"] for p in per))
         secs = ms_total * 1e-3
         L0 = np.linalg.norm(e0["L"])
@@ -760,7 +818,7 @@ def run_integrate(args):
             "dE_over_E": abs((e1["E"] - e0["E"]) / e0["E"]),
             "dP": float(np.linalg.norm(e1["P"] - e0["P"])),
             "dL_over_L": float(np.linalg.norm(e1["L"] - e0["L"]) / L0) if L0 > 0 else None,
-            "autotune_waves": tuned, "_x": xs, "_v": vs}
+            "autotune_waves": tuned, "binaries": binaries, "_x": xs, "_v": vs}
         if args.t_end is not None:
             runs[prec]["extrapolated_s_to_t_end"] = secs * args.t_end / t
             runs[prec]["t_end"] = args.t_end

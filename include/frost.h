@@ -83,6 +83,11 @@ typedef struct {
                                (they act on disjoint particles, so the results are those of the
                                serial order, bit for bit); -1: everything on the context stream.
                                With per-kernel timing on, the branches run serially. */
+    int32_t sym_cross;      /* 0 (default): the Newtonian kick_sf of a hierarchy level
+                               evaluates each S x F pair once for both sides (see
+                               frost_accel_pairwise) where that grid fills the GPU, else two
+                               one-sided passes on two streams; 1: always once; -1: always two
+                               one-sided passes */
 } frost_opts;
 
 typedef enum {
@@ -102,7 +107,10 @@ void frost_default_opts(frost_opts *opt);
  * v[n][3] (host or device; copied), Newton's constant G and accuracy parameter eta
  * (eta = eta_ff = eta_fb, Sec. 4.3).  opt may be NULL for the defaults.  n >= 1 and
  * n < 2^31.  Non-finite inputs or non-positive masses give FROST_ENONFINITE / FROST_EINVAL.
- * The context allocates about (330 + 32 * levels_used) bytes per particle of device memory.
+ * The context allocates about (330 + 32 * levels_used) bytes per particle of device memory,
+ * plus about 350 bytes per particle for each hierarchy level above the subtree threshold
+ * whose FSI steps run on a stream of their own (frost_opts.branch_streams, allocated on
+ * first use).
  * On failure *ctx is NULL.
  */
 frost_status frost_init(frost_ctx **ctx, int64_t n, const double *m, const double *x,
@@ -162,6 +170,23 @@ frost_status frost_get_state(frost_ctx *ctx, double *x, double *v, double *t);
 frost_status frost_accel_gradient(frost_ctx *ctx, const int32_t *active, int64_t n_active,
                                   const int32_t *source, int64_t n_source, double eps_grad,
                                   double *acc, double *acc_tilde, double *grad);
+
+/*
+ * Newtonian accelerations of two disjoint sets due to each other, both lines of Eq.
+ * force-newton-inter, with every pair evaluated once (Sec. 3.3: the inter-level kick is
+ * pairwise):
+ *   acc_a[k] = G sum_{j in b} m_j x_ji / r_ji^3   for i = a[k]
+ *   acc_b[k] = G sum_{i in a} m_i x_ij / r_ij^3   for j = b[k]
+ * Each pair's separation, r^2 and r^-3 are formed once and weighted by m_j for the a-side and
+ * by -m_i for the b-side; the a-side (the longer list) is summed per thread, the b-side by a
+ * fixed-order reduction over the threads, so results are deterministic.  a, b: device int32
+ * lists (or NULL = identity) of n_a and n_b indices with no index in both (else
+ * FROST_EINVAL); acc_a, acc_b: device [n][3] doubles (either may be NULL).  Softened like
+ * frost_accel_gradient.  Accuracy: as the Newtonian pass of frost_accel_gradient (FP64:
+ * 1e-12 relative; mixed: ~1e-7 at the 99.9th percentile).  Synchronises.
+ */
+frost_status frost_accel_pairwise(frost_ctx *ctx, const int32_t *a, int64_t n_a, const int32_t *b,
+                                  int64_t n_b, double *acc_a, double *acc_b);
 
 /*
  * Symmetrised time-steps of the members of `set` (device list or NULL), Sec. 4:
@@ -242,6 +267,9 @@ typedef struct {
     /* the pair interactions evaluated inside single-block subtree-solver launches (Newtonian,
      * gradient, time-step; also part of acc_pairs, grad_pairs and tstep_pairs) */
     int64_t subtree_pairs[3];
+    /* Newtonian pairs evaluated once for both sides (symmetric S x F passes; counted once in
+     * acc_pairs, and each served two interactions) */
+    int64_t acc_pairs_symmetric;
 } frost_stats;
 
 frost_status frost_get_stats(frost_ctx *ctx, frost_stats *out);
@@ -265,7 +293,14 @@ frost_status frost_set_timing(frost_ctx *ctx, int32_t enable);
  * In the mixed mode, the Newtonian pass that feeds a gradient (its wmax prepass and
  * deferred double-float terms) is tuned as a fourth kind (3).
  * waves_out: NULL, or int32[4][32] receiving the chosen bound per kind and k (0 = untuned;
- * negative = the small-tile layout with that many waves). */
+ * negative = the small-tile layout with that many waves).
+ * On a batch context (frost_init_batch) it tunes the team split instead: every cluster of at
+ * least min_n particles runs on a thread-block cluster of `blocks` blocks, the others on one
+ * block each.  It times one batch step (the pivot of the last frost_step call, else 2^-7)
+ * for min_n in {256, 384, 512, 768, 1024, 1536, 2048} x blocks in {2, 4, 8} and for one block
+ * per cluster, from the same saved state, keeps the fastest (by 2%) and restores the state
+ * and time; waves_out[0] = min_n (INT32_MAX: no teams) and waves_out[1] = blocks, the rest 0.
+ * The default split (before tuning) is min_n = 768, 8 blocks. */
 frost_status frost_autotune(frost_ctx *ctx, int32_t *waves_out);
 
 /* Wait for all work of the context and report the sticky device error, if any. */

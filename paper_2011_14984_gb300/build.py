@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfrost.so")
 SOURCES = ["pair_kernels.cu", "aux_kernels.cu", "hot_kernels.cu", "subtree.cu", "frost_api.cu", "noalloc.cu",
-           "peak_probe.cu"]
+           "peak_probe.cu", "sym_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-ftz=true",
               "-prec-div=false", "-prec-sqrt=false", "-I", INCLUDE, "-I", CSRC]

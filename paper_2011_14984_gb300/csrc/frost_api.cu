@@ -143,8 +143,11 @@ struct frost_ctx {
     // batch teams: clusters of at least team_min_n particles run on a thread-block cluster of
     // team_blocks blocks (d_big, largest first), the others on one block each (d_small); the two
     // launches overlap through a side stream
-    int32_t *d_big = nullptr, *d_small = nullptr;
+    int32_t *d_big = nullptr, *d_small = nullptr;    // capacity n_clusters each
     int n_big = 0, n_small = 0;
+    std::vector<int64_t> h_offsets;                  // cluster offsets (host copy)
+    int64_t team_min_n = 768;                        // clusters of at least this size get a team
+    int team_blocks = 8;                             // of this many blocks (autotuned)
     int *d_xchg = nullptr;
     cudaStream_t side = nullptr, cap = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -158,6 +161,10 @@ struct frost_ctx {
     unsigned long long lev_seen[2][SUBTREE_STAT_LEVELS] = {};
     Misc *dmisc = nullptr, *hmisc = nullptr;
     std::vector<int32_t *> lvS, lvF;                 // per-level slow/fast lists
+    double *pj = nullptr;                            // j-side partials of the symmetric pass
+    size_t pj_elems = 0;
+    int sym_cross = 0;                               // symmetric S x F Newtonian passes in kick_sf:
+                                                     // 0 where they fill the GPU, 1 always, -1 never
     Lane main;                                       // the context stream and the buffers above
     std::deque<Lane> branch;                         // per grid level: fsi(S) next to hhs_fsi(F)
                                                      // (a deque: growing it keeps the lanes of
@@ -632,6 +639,36 @@ void fsi(frost_ctx *c, Lane &L, const int32_t *S, int nS, double dt, int cache =
     pass_acc(c, L, S, nS, S, nS, true, L.aA, nullptr, nullptr, nullptr, last, L.recA, L.recA);
 }
 
+// Newtonian accelerations of two disjoint lists due to each other with every pair evaluated
+// once (Eq. force-newton-inter, both lines): outA (soa [3][nA]) and outB (soa [3][nB]), each
+// list's kick fused into its finalisation.  recA / recB hold the lists' position records.  The
+// longer list takes the register side, the shorter one the reduced side (its partials per
+// group of i-blocks are then fewer).  Returns false, issuing nothing, when the grid of the
+// symmetric kernel would not fill one wave of the GPU (small lists: the two one-sided passes,
+// on two streams, are then faster).
+bool pass_acc_sym(frost_ctx *c, Lane &L, const int32_t *A, int nA, const int32_t *B, int nB, double *outA,
+                  double *outB, KickArgs kickA, KickArgs kickB, const void *recA, const void *recB, bool force = false)
+{
+    if (nA <= 0 || nB <= 0) return false;
+    const bool swap = nB > nA;
+    const int ni = swap ? nB : nA, nj = swap ? nA : nB;
+    const SymShape sh = sym_shape(c->mixed, ni, nj, c->n_sm, c->part_elems, c->pj_elems);
+    if (!force && (long long)sh.ngroups * sh.nsplit < (long long)sh.blocks_per_wave) return false;
+    const int64_t pairs = (int64_t)nA * nB;
+    {
+        TimedScope ts(c, L.s, PASS_ACC, pairs);
+        launch_acc_sym(L.s, c->mixed, swap ? recB : recA, swap ? recA : recB, ni, nj, c->eps2, L.part, c->pj, sh);
+    }
+    double *out_i = swap ? outB : outA, *out_j = swap ? outA : outB;
+    const KickArgs kick_i = swap ? kickB : kickA, kick_j = swap ? kickA : kickB;
+    launch_finalize_vec(L.s, L.part, sh.nsplit, ni, c->G, out_i, nullptr, &c->dmisc->err, badbit(c), kick_i);
+    launch_finalize_vec(L.s, c->pj, sh.ngroups, nj, -c->G, out_j, nullptr, &c->dmisc->err, badbit(c), kick_j);
+    c->st.kernel_launches += 3;
+    c->st.acc_pairs += pairs;
+    c->st.acc_pairs_symmetric += pairs;
+    return true;
+}
+
 // Runs on `exec` what a branch lane issues: the branch lane itself when the branches run
 // concurrently, else its buffers on the context stream (timing mode, or concurrency off).
 struct Branch {
@@ -681,6 +718,10 @@ void kick_sf(frost_ctx *c, Lane &M, Lane *Bl, const int32_t *S, int nS, const in
     if (!Bl) br.concurrent = false;
     Lane &X = Bl ? br.exec : M;
     if (!gradient) {
+        // each S x F pair once, when the symmetric grid fills the GPU
+        if (c->sym_cross >= 0 && pass_acc_sym(c, M, S, nS, F, nF, M.aA, M.aB, kick_of(c, S, cdt),
+                                              kick_of(c, F, cdt), M.recA, M.recB, c->sym_cross > 0))
+            return;
         br.fork();
         pass_acc(c, M, S, nS, F, nF, false, M.aA, nullptr, nullptr, nullptr, kick_of(c, S, cdt), M.recA, M.recB);
         pass_acc(c, X, F, nF, S, nS, false, M.aB, nullptr, nullptr, nullptr, kick_of(c, F, cdt), M.recB, M.recA);
@@ -859,6 +900,34 @@ frost_status check_sizes(frost_ctx *c, int64_t n, const char *what)
     return FROST_OK;
 }
 
+// The team split of a batch context: clusters of at least min_n particles run on a
+// thread-block cluster of `blocks` blocks (largest first), the others on one block each (largest
+// first, so that the block scheduler starts them first).  Drops the captured step graph.
+frost_status set_teams(frost_ctx *c, int64_t min_n, int blocks)
+{
+    const int nc = c->n_clusters;
+    const int64_t *off = c->h_offsets.data();
+    std::vector<int32_t> order(nc);
+    for (int k = 0; k < nc; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
+    std::vector<int32_t> big, small;
+    for (int32_t k : order) (off[k + 1] - off[k] >= min_n ? big : small).push_back(k);
+    c->n_big = (int)big.size();
+    c->n_small = (int)small.size();
+    if (c->n_big)
+        FROST_CUDA(cudaMemcpy(c->d_big, big.data(), sizeof(int32_t) * c->n_big, cudaMemcpyHostToDevice));
+    if (c->n_small)
+        FROST_CUDA(cudaMemcpy(c->d_small, small.data(), sizeof(int32_t) * c->n_small, cudaMemcpyHostToDevice));
+    c->team_min_n = min_n;
+    c->team_blocks = blocks;
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    return FROST_OK;
+}
+
 void destroy(frost_ctx *c)
 {
     if (!c) return;
@@ -883,7 +952,7 @@ void destroy(frost_ctx *c)
     if (c->d_ecl) cudaFree(c->d_ecl);
     void *dev[] = {c->x, c->v, c->m, c->all, c->marks, c->recA, c->recB, c->part,
                    c->aA, c->aB, c->atA, c->atB, c->aC, c->tau, c->wA, c->wB, c->perm,
-                   c->ptmp, c->dmisc, c->hist, c->hA, c->hB, c->part_hot};
+                   c->ptmp, c->dmisc, c->hist, c->hA, c->hB, c->part_hot, c->pj};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (c->hmisc) cudaFreeHost(c->hmisc);
@@ -910,6 +979,7 @@ void frost_default_opts(frost_opts *opt)
     opt->subtree_blocks = 0;
     opt->integrator = FROST_HHS_FSI;
     opt->branch_streams = 0;
+    opt->sym_cross = 0;
 }
 
 const char *frost_last_error(void) { return g_last_error; }
@@ -1025,6 +1095,8 @@ static frost_status init_impl(frost_ctx **out, int64_t n, const double *m, const
         INIT_CUDA(cudaMalloc(&c->hB, sizeof(uint32_t) * words));
         INIT_CUDA(cudaMalloc(&c->part_hot, sizeof(double) * c->part_hot_elems));
     }
+    c->pj_elems = 3 * 8 * N;
+    INIT_CUDA(cudaMalloc(&c->pj, sizeof(double) * c->pj_elems));
     INIT_CUDA(cudaMalloc(&c->perm, sizeof(int32_t) * N));
     INIT_CUDA(cudaMalloc(&c->ptmp, sizeof(int32_t) * N));
     if (n_clusters > 0) {
@@ -1033,30 +1105,17 @@ static frost_status init_impl(frost_ctx **out, int64_t n, const double *m, const
         INIT_CUDA(cudaMemcpy(c->d_offsets, offsets, sizeof(int64_t) * (n_clusters + 1), cudaMemcpyHostToDevice));
         INIT_CUDA(cudaMalloc(&c->d_ecl, sizeof(double) * 8 * n_clusters));
         c->h_ecl.resize(8 * (size_t)n_clusters);
-        // teams: large clusters first within each group (the block scheduler starts them first)
-        std::vector<int32_t> order(n_clusters);
-        for (int k = 0; k < n_clusters; ++k) order[k] = k;
-        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-            return offsets[a + 1] - offsets[a] > offsets[b + 1] - offsets[b];
-        });
-        std::vector<int32_t> big, small;
-        for (int32_t k : order) (offsets[k + 1] - offsets[k] >= kBatchTeamMinN ? big : small).push_back(k);
-        c->n_big = (int)big.size();
-        c->n_small = (int)small.size();
-        if (c->n_big) {
-            INIT_CUDA(cudaMalloc(&c->d_big, sizeof(int32_t) * c->n_big));
-            INIT_CUDA(cudaMemcpy(c->d_big, big.data(), sizeof(int32_t) * c->n_big, cudaMemcpyHostToDevice));
-        }
-        if (c->n_small) {
-            INIT_CUDA(cudaMalloc(&c->d_small, sizeof(int32_t) * c->n_small));
-            INIT_CUDA(cudaMemcpy(c->d_small, small.data(), sizeof(int32_t) * c->n_small, cudaMemcpyHostToDevice));
-        }
+        c->h_offsets.assign(offsets, offsets + n_clusters + 1);
+        INIT_CUDA(cudaMalloc(&c->d_big, sizeof(int32_t) * n_clusters));
+        INIT_CUDA(cudaMalloc(&c->d_small, sizeof(int32_t) * n_clusters));
         INIT_CUDA(cudaMalloc(&c->d_xchg, sizeof(int) * n_clusters));
         INIT_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
-        if (c->n_big && c->n_small) {
-            INIT_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
-            INIT_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
-            INIT_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+        INIT_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+        INIT_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+        INIT_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+        {
+            const frost_status ts = set_teams(c, kBatchTeamMinN, kBatchTeamBlocks);
+            if (ts != FROST_OK) return bail(ts);
         }
     }
     INIT_CUDA(cudaMalloc(&c->dmisc, sizeof(Misc)));
@@ -1078,6 +1137,7 @@ static frost_status init_impl(frost_ctx **out, int64_t n, const double *m, const
     c->main.hB = c->hB;
     c->main.part_hot = c->part_hot;
     c->branch_streams = o.branch_streams >= 0;
+    c->sym_cross = o.sym_cross > 0 ? 1 : (o.sym_cross < 0 ? -1 : 0);
     INIT_CUDA(cudaMemsetAsync(c->dmisc, 0, sizeof(Misc), c->stream));
     INIT_CUDA(cudaMemsetAsync(c->marks, 0, sizeof(int32_t) * N, c->stream));
     launch_identity(c->stream, c->all, (int)n);
@@ -1184,6 +1244,34 @@ frost_status frost_accel_gradient(frost_ctx *c, const int32_t *active, int64_t n
     return sync_misc(c);
 }
 
+frost_status frost_accel_pairwise(frost_ctx *c, const int32_t *a, int64_t n_a, const int32_t *b, int64_t n_b,
+                                  double *acc_a, double *acc_b)
+{
+    if (!c) return fail(FROST_EINVAL, "NULL context");
+    FROST_TRY(check_sizes(c, n_a, "n_a"));
+    FROST_TRY(check_sizes(c, n_b, "n_b"));
+    const int nA = (int)n_a, nB = (int)n_b;
+    const int32_t *A = a ? a : c->all;
+    const int32_t *B = b ? b : c->all;
+    launch_list_relation(c->stream, A, nA, B, nB, c->N, c->marks, c->dmisc->rel);
+    FROST_TRY(sync_misc(c));
+    if (c->hmisc->rel[0]) return fail(FROST_EINVAL, "index list has an out-of-range or repeated index");
+    if (c->hmisc->rel[1] != 0) return fail(FROST_EINVAL, "the two lists share %lld particles", (long long)c->hmisc->rel[1]);
+    Lane &M = c->main;
+    if (nA > 0 && nB > 0) {
+        pack_pos(c, M, A, nA, M.recA);
+        pack_pos(c, M, B, nB, M.recB);
+        pass_acc_sym(c, M, A, nA, B, nB, M.aA, M.aB, KickArgs(), KickArgs(), M.recA, M.recB, true);
+        if (acc_a) launch_soa_to_aos(c->stream, M.aA, nA, acc_a);
+        if (acc_b) launch_soa_to_aos(c->stream, M.aB, nB, acc_b);
+    } else {
+        if (acc_a && nA > 0) FROST_CUDA(cudaMemsetAsync(acc_a, 0, sizeof(double) * 3 * nA, c->stream));
+        if (acc_b && nB > 0) FROST_CUDA(cudaMemsetAsync(acc_b, 0, sizeof(double) * 3 * nB, c->stream));
+    }
+    FROST_CUDA(cudaGetLastError());
+    return sync_misc(c);
+}
+
 frost_status frost_timesteps(frost_ctx *c, const int32_t *set, int64_t n_set, double *tau)
 {
     if (!c) return fail(FROST_EINVAL, "NULL context");
@@ -1278,100 +1366,105 @@ frost_status hold2(frost_ctx *c, const int32_t *P, int nP, double tau, int depth
     return hold2(c, F, nF, 0.5 * tau, depth + 1);
 }
 
+// n_steps top-level steps of every cluster of a batch context: one launch per team kind
+// (a CUDA graph, captured once per (dt_pivot, n_steps) and replayed)
+static frost_status batch_step(frost_ctx *c, double dt_pivot, int64_t n_steps)
+{
+    // every cluster in its own thread block, all steps in one launch
+    if (c->max_depth >= SUBTREE_MAX_FRAMES)
+        return fail(FROST_EINVAL, "batch contexts need max_depth < %d", SUBTREE_MAX_FRAMES);
+    if (n_steps == 0) return FROST_OK;
+    if (n_steps > INT32_MAX) return fail(FROST_EINVAL, "n_steps too large");
+    SubtreeArgs a;
+    a.x = c->x;
+    a.v = c->v;
+    a.m = c->m;
+    a.N = c->N;
+    a.G = c->G;
+    a.eta = c->eta;
+    a.eps2 = c->eps2;
+    a.max_depth = c->max_depth;
+    a.err = &c->dmisc->err;
+    a.counters = c->dmisc->sub;
+    a.levels = &c->dmisc->lev[0][0];
+    a.aC = c->aC;
+    a.perm = c->perm;
+    a.tmp = c->ptmp;
+    a.tau = c->tau;
+    a.aA = c->aA;
+    a.aB = c->aB;
+    a.atA = c->atA;
+    a.atB = c->atB;
+    a.wA = c->wA;
+    a.wB = c->wB;
+    a.recA = c->recA;
+    a.recB = c->recB;
+    a.offsets = c->d_offsets;
+    a.xchg = c->d_xchg;
+    a.tau0 = dt_pivot;
+    a.depth0 = 0;
+    a.n_steps = (int)n_steps;
+    SubtreeArgs ab = a, as = a;
+    ab.cl_index = c->d_big;
+    ab.n_teams = c->n_big;
+    ab.team_blocks = c->team_blocks;
+    as.cl_index = c->d_small;
+    as.n_teams = c->n_small;
+    if (!c->gexec || c->g_dt != dt_pivot || c->g_steps != n_steps) {
+        // capture the step: the large clusters on a forked stream, concurrently with the
+        // small ones, joined before the end of the graph
+        if (c->gexec) {
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+        FROST_CUDA(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e1 = cudaSuccess, e2 = cudaSuccess;
+        if (c->n_big && c->n_small) {
+            cudaEventRecord(c->ev_fork, c->cap);
+            cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+            e1 = launch_subtree(c->side, c->mixed, c->sym, ab);
+            e2 = launch_subtree(c->cap, c->mixed, c->sym, as);
+            cudaEventRecord(c->ev_join, c->side);
+            cudaStreamWaitEvent(c->cap, c->ev_join, 0);
+        } else if (c->n_big) {
+            e1 = launch_subtree(c->cap, c->mixed, c->sym, ab);
+        } else {
+            e2 = launch_subtree(c->cap, c->mixed, c->sym, as);
+        }
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(c->cap, &g);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || ec != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return fail(FROST_ECUDA, "batch step capture: %s",
+                        cudaGetErrorString(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : ec)));
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&c->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            c->gexec = nullptr;
+            return fail(FROST_ECUDA, "batch step graph: %s", cudaGetErrorString(ei));
+        }
+        c->g_dt = dt_pivot;
+        c->g_steps = n_steps;
+    }
+    {
+        TimedScope ts(c, c->stream, PASS_SUBTREE, 0);
+        FROST_CUDA(cudaGraphLaunch(c->gexec, c->stream));
+    }
+    c->st.kernel_launches += (c->n_big > 0) + (c->n_small > 0);
+    c->st.subtree_launches += c->n_clusters;
+    c->t += dt_pivot * (double)n_steps;
+    FROST_CUDA(cudaGetLastError());
+    return sync_misc(c);
+}
+
 frost_status frost_step(frost_ctx *c, double dt_pivot, int64_t n_steps)
 {
     if (!c) return fail(FROST_EINVAL, "NULL context");
     if (!(dt_pivot > 0.0) || !std::isfinite(dt_pivot)) return fail(FROST_EINVAL, "dt_pivot must be > 0");
     if (n_steps < 0) return fail(FROST_EINVAL, "n_steps < 0");
-    if (c->n_clusters > 0) {
-        // every cluster in its own thread block, all steps in one launch
-        if (c->max_depth >= SUBTREE_MAX_FRAMES)
-            return fail(FROST_EINVAL, "batch contexts need max_depth < %d", SUBTREE_MAX_FRAMES);
-        if (n_steps == 0) return FROST_OK;
-        if (n_steps > INT32_MAX) return fail(FROST_EINVAL, "n_steps too large");
-        SubtreeArgs a;
-        a.x = c->x;
-        a.v = c->v;
-        a.m = c->m;
-        a.N = c->N;
-        a.G = c->G;
-        a.eta = c->eta;
-        a.eps2 = c->eps2;
-        a.max_depth = c->max_depth;
-        a.err = &c->dmisc->err;
-        a.counters = c->dmisc->sub;
-        a.levels = &c->dmisc->lev[0][0];
-    a.aC = c->aC;
-        a.perm = c->perm;
-        a.tmp = c->ptmp;
-        a.tau = c->tau;
-        a.aA = c->aA;
-        a.aB = c->aB;
-        a.atA = c->atA;
-        a.atB = c->atB;
-        a.wA = c->wA;
-        a.wB = c->wB;
-        a.recA = c->recA;
-        a.recB = c->recB;
-        a.offsets = c->d_offsets;
-        a.xchg = c->d_xchg;
-        a.tau0 = dt_pivot;
-        a.depth0 = 0;
-        a.n_steps = (int)n_steps;
-        SubtreeArgs ab = a, as = a;
-        ab.cl_index = c->d_big;
-        ab.n_teams = c->n_big;
-        ab.team_blocks = kBatchTeamBlocks;
-        as.cl_index = c->d_small;
-        as.n_teams = c->n_small;
-        if (!c->gexec || c->g_dt != dt_pivot || c->g_steps != n_steps) {
-            // capture the step: the large clusters on a forked stream, concurrently with the
-            // small ones, joined before the end of the graph
-            if (c->gexec) {
-                cudaGraphExecDestroy(c->gexec);
-                c->gexec = nullptr;
-            }
-            FROST_CUDA(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e1 = cudaSuccess, e2 = cudaSuccess;
-            if (c->n_big && c->n_small) {
-                cudaEventRecord(c->ev_fork, c->cap);
-                cudaStreamWaitEvent(c->side, c->ev_fork, 0);
-                e1 = launch_subtree(c->side, c->mixed, c->sym, ab);
-                e2 = launch_subtree(c->cap, c->mixed, c->sym, as);
-                cudaEventRecord(c->ev_join, c->side);
-                cudaStreamWaitEvent(c->cap, c->ev_join, 0);
-            } else if (c->n_big) {
-                e1 = launch_subtree(c->cap, c->mixed, c->sym, ab);
-            } else {
-                e2 = launch_subtree(c->cap, c->mixed, c->sym, as);
-            }
-            cudaGraph_t g = nullptr;
-            const cudaError_t ec = cudaStreamEndCapture(c->cap, &g);
-            if (e1 != cudaSuccess || e2 != cudaSuccess || ec != cudaSuccess || !g) {
-                if (g) cudaGraphDestroy(g);
-                cudaGetLastError();
-                return fail(FROST_ECUDA, "batch step capture: %s",
-                            cudaGetErrorString(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : ec)));
-            }
-            const cudaError_t ei = cudaGraphInstantiate(&c->gexec, g, 0);
-            cudaGraphDestroy(g);
-            if (ei != cudaSuccess) {
-                c->gexec = nullptr;
-                return fail(FROST_ECUDA, "batch step graph: %s", cudaGetErrorString(ei));
-            }
-            c->g_dt = dt_pivot;
-            c->g_steps = n_steps;
-        }
-        {
-            TimedScope ts(c, c->stream, PASS_SUBTREE, 0);
-            FROST_CUDA(cudaGraphLaunch(c->gexec, c->stream));
-        }
-        c->st.kernel_launches += (c->n_big > 0) + (c->n_small > 0);
-        c->st.subtree_launches += c->n_clusters;
-        c->t += dt_pivot * (double)n_steps;
-        FROST_CUDA(cudaGetLastError());
-        return sync_misc(c);
-    }
+    if (c->n_clusters > 0) return batch_step(c, dt_pivot, n_steps);
     for (int64_t k = 0; k < n_steps; ++k) {
         if (c->integrator == FROST_HOLD2) FROST_TRY(hold2(c, c->all, c->N, dt_pivot, 0));
         else FROST_TRY(hhs_fsi(c, c->all, c->N, dt_pivot, 0));
@@ -1488,9 +1581,83 @@ frost_status frost_set_timing(frost_ctx *c, int32_t enable)
     return FROST_OK;
 }
 
+// Autotuner of a batch context: the team split (the smallest cluster that gets a team of
+// several blocks, and the blocks of such a team), timed as one batch step of every candidate
+// from the same saved state; the state and time are restored afterwards.  The step is the
+// pivot of the last frost_step call, else 2^-7.
+static frost_status batch_autotune(frost_ctx *c, int32_t *out)
+{
+    const size_t bytes = sizeof(double) * 3 * (size_t)c->N;
+    double *sx = nullptr, *sv = nullptr;
+    FROST_CUDA(cudaMalloc(&sx, bytes));
+    if (cudaMalloc(&sv, bytes) != cudaSuccess) {
+        cudaFree(sx);
+        return fail(FROST_ENOMEM, "autotune state copy");
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const double dt = c->g_dt > 0.0 ? c->g_dt : 1.0 / 128.0;
+    const double t0 = c->t;
+    frost_status st = FROST_OK;
+    cudaMemcpyAsync(sx, c->x, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(sv, c->v, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    struct Cand {
+        int64_t min_n;
+        int blocks;
+    };
+    std::vector<Cand> cands;
+    cands.push_back({INT64_MAX, 1});  // one block per cluster
+    for (int64_t mn : {256, 384, 512, 768, 1024, 1536, 2048})
+        for (int b : {2, 4, 8}) cands.push_back({mn, b});
+    float best = INFINITY;
+    Cand pick = {c->team_min_n, c->team_blocks};
+    for (const Cand &q : cands) {
+        if ((st = set_teams(c, q.min_n, q.blocks)) != FROST_OK) break;
+        float tq = INFINITY;
+        for (int rep = 0; rep < 3 && st == FROST_OK; ++rep) {
+            cudaMemcpyAsync(c->x, sx, bytes, cudaMemcpyDeviceToDevice, c->stream);
+            cudaMemcpyAsync(c->v, sv, bytes, cudaMemcpyDeviceToDevice, c->stream);
+            // the first call captures the graph of this split; the others replay it
+            if (rep > 0) cudaEventRecord(e0, c->stream);
+            st = batch_step(c, dt, 1);
+            if (st == FROST_OK && rep > 0) {
+                cudaEventRecord(e1, c->stream);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                tq = std::min(tq, ms);
+            }
+        }
+        if (st != FROST_OK) break;
+        if (tq < 0.98f * best) {
+            best = tq;
+            pick = q;
+        }
+    }
+    cudaMemcpyAsync(c->x, sx, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(c->v, sv, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    c->t = t0;
+    const frost_status st2 = set_teams(c, pick.min_n, pick.blocks);
+    cudaStreamSynchronize(c->stream);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sx);
+    cudaFree(sv);
+    if (st != FROST_OK) return st;
+    if (st2 != FROST_OK) return st2;
+    if (out) {
+        for (int k = 0; k < TUNE_ROWS * 32; ++k) out[k] = 0;
+        out[0] = (int32_t)std::min<int64_t>(pick.min_n, INT32_MAX);
+        out[1] = pick.blocks;
+    }
+    return sync_misc(c);
+}
+
 frost_status frost_autotune(frost_ctx *c, int32_t *waves_out)
 {
     if (!c) return fail(FROST_EINVAL, "NULL context");
+    if (c->n_clusters > 0) return batch_autotune(c, waves_out);
     static const int kWaves[] = {1, 2, 4, 8, 16};
     cudaEvent_t e0, e1;
     FROST_CUDA(cudaEventCreate(&e0));

@@ -197,6 +197,22 @@ void launch_energy_reduce(cudaStream_t s, const double *x, const double *v, cons
 void launch_cluster_energy(cudaStream_t s, const int64_t *offsets, int n_clusters, const double *x,
                            const double *v, const double *m, int N, double eps2, double *out);
 
+// ---- symmetric inter-level Newtonian pass (sym_kernels.cu) -------------------------------
+// Every pair of two disjoint lists A (n_a) and B (n_s) once: part[split][c][i] = sum over the
+// split's sources of m_j x_ji / r^3 (as launch_acc), pj[group][c][j] = sum over the group's
+// i-blocks of m_i x_ji / r^3 (the force on j is -G times the sum over the groups).
+struct SymShape {
+    int nblk_i = 1;        // i-blocks of A
+    int ngroups = 1;       // blocks along A (each takes every ngroups-th i-block)
+    int nsplit = 1;        // blocks along B
+    int j_per_split = 0;   // sources per split (a multiple of the tile)
+    int blocks_per_wave = 1;
+};
+// part_elems / pj_elems: the capacities of part and pj in doubles
+SymShape sym_shape(bool mixed, int n_a, int n_s, int n_sm, size_t part_elems, size_t pj_elems);
+void launch_acc_sym(cudaStream_t s, bool mixed, const void *irec, const void *jrec, int n_a, int n_s, double eps2,
+                    double *part, double *pj, const SymShape &sh);
+
 // ---- single-CTA subtree solver (subtree.cu) ------------------------------------------
 constexpr int SUBTREE_MAX_FRAMES = 64;  // recursion frames per block (max_depth < 64)
 constexpr int SUBTREE_STAT_LEVELS = 48; // per-depth statistics (last entry: deeper levels)

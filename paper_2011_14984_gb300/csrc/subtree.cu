@@ -678,8 +678,15 @@ __device__ __noinline__ void b_kick_sf(const SubParams &p, const SubWork &w, con
 // only the summation order differs.
 constexpr int WARP_N = 32;
 
+// The lane's particle (FP64 state) and the warp's origin o (the centre of the bounding box of
+// the set at entry).  The mixed passes split x - o, not x, into float-float records: x - o is
+// at most the set's extent, so a tight pair's separation is resolved to 2^-48 of that extent
+// instead of 2^-48 |x| (at the pericentre of a hard binary, r ~ 1e-10 |x|, the absolute
+// records would leave a relative error of ~1e-4 in r).  Separations, and so the arithmetic
+// of the method, do not depend on the origin.
 struct WLane {
     double x[3], v[3], m;
+    double o[3];
 };
 
 __device__ __forceinline__ float wsh(float v, int j) { return __shfl_sync(0xffffffffu, v, j); }
@@ -702,11 +709,12 @@ __device__ __noinline__ void w_acc(const SubParams &p, const WLane &L, unsigned 
         float ax[1] = {0.f}, ay[1] = {0.f}, az[1] = {0.f};
         int c = 0;
         AccMixedI<1> I;
-        float hx = (float)L.x[0], hy = (float)L.x[1], hz = (float)L.x[2];
+        const double rx = L.x[0] - L.o[0], ry = L.x[1] - L.o[1], rz = L.x[2] - L.o[2];
+        float hx = (float)rx, hy = (float)ry, hz = (float)rz;
         I.xh[0] = hx; I.yh[0] = hy; I.zh[0] = hz;
-        I.xl[0] = (float)(L.x[0] - (double)hx);
-        I.yl[0] = (float)(L.x[1] - (double)hy);
-        I.zl[0] = (float)(L.x[2] - (double)hz);
+        I.xl[0] = (float)(rx - (double)hx);
+        I.yl[0] = (float)(ry - (double)hy);
+        I.zl[0] = (float)(rz - (double)hz);
         const float mf = (float)L.m;
         unsigned M = U;
         while (M) {
@@ -752,9 +760,9 @@ __device__ __noinline__ void w_grad(const SubParams &p, const WLane &L, unsigned
     if (MIXED) {
         const float eps2 = (float)p.eps2;
         GradMixedI<1> I;
-        split3(L.x[0], I.xh[0], I.xm[0], I.xl[0]);
-        split3(L.x[1], I.yh[0], I.ym[0], I.yl[0]);
-        split3(L.x[2], I.zh[0], I.zm[0], I.zl[0]);
+        split3(L.x[0] - L.o[0], I.xh[0], I.xm[0], I.xl[0]);
+        split3(L.x[1] - L.o[1], I.yh[0], I.ym[0], I.yl[0]);
+        split3(L.x[2] - L.o[2], I.zh[0], I.zm[0], I.zl[0]);
         I.ahx[0] = trunc12((float)ai[0]);
         I.ahy[0] = trunc12((float)ai[1]);
         I.ahz[0] = trunc12((float)ai[2]);
@@ -833,11 +841,12 @@ __device__ __noinline__ double w_tstep(const SubParams &p, const WLane &L, unsig
     }
     if (MIXED) {
         TstepMixedI<1> I;
-        const float hx = (float)L.x[0], hy = (float)L.x[1], hz = (float)L.x[2];
+        const double rx = L.x[0] - L.o[0], ry = L.x[1] - L.o[1], rz = L.x[2] - L.o[2];
+        const float hx = (float)rx, hy = (float)ry, hz = (float)rz;
         I.xh[0] = hx; I.yh[0] = hy; I.zh[0] = hz;
-        I.xl[0] = (float)(L.x[0] - (double)hx);
-        I.yl[0] = (float)(L.x[1] - (double)hy);
-        I.zl[0] = (float)(L.x[2] - (double)hz);
+        I.xl[0] = (float)(rx - (double)hx);
+        I.yl[0] = (float)(ry - (double)hy);
+        I.zl[0] = (float)(rz - (double)hz);
         I.vx[0] = (float)L.v[0]; I.vy[0] = (float)L.v[1]; I.vz[0] = (float)L.v[2];
         I.gm[0] = (float)(p.G * L.m);
         I.ax[0] = (float)la[0]; I.ay[0] = (float)la[1]; I.az[0] = (float)la[2];
@@ -969,6 +978,15 @@ __device__ __noinline__ int warp_hhs(const SubParams &p, const int32_t *Sg, int 
             L.v[c] = 0.0;
         }
         L.m = 0.0;
+    }
+    // the origin of the mixed records: the centre of the set's bounding box
+    for (int c = 0; c < 3; ++c) {
+        double lo = (lane < n) ? L.x[c] : INFINITY, hi = (lane < n) ? L.x[c] : -INFINITY;
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        L.o[c] = MIXED ? 0.5 * (lo + hi) : 0.0;
     }
     const unsigned all = (n >= 32) ? 0xffffffffu : ((1u << n) - 1u);
     if (lane == 0) {

@@ -40,7 +40,7 @@ class frost_opts(ctypes.Structure):
                 ("eps_soft", ctypes.c_double), ("max_depth", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p), ("subtree_max", ctypes.c_int32),
                 ("integrator", ctypes.c_int32), ("subtree_blocks", ctypes.c_int32),
-                ("branch_streams", ctypes.c_int32)]
+                ("branch_streams", ctypes.c_int32), ("sym_cross", ctypes.c_int32)]
 
 
 class frost_stats(ctypes.Structure):
@@ -51,7 +51,8 @@ class frost_stats(ctypes.Structure):
                 ("timed_launches", ctypes.c_int64 * 4), ("timed_ms", ctypes.c_double * 4),
                 ("timed_pairs", ctypes.c_int64 * 4), ("subtree_launches", ctypes.c_int64),
                 ("level_calls", ctypes.c_int64 * 48), ("level_particles", ctypes.c_int64 * 48),
-                ("acc_pairs_reused", ctypes.c_int64), ("subtree_pairs", ctypes.c_int64 * 3)]
+                ("acc_pairs_reused", ctypes.c_int64), ("subtree_pairs", ctypes.c_int64 * 3),
+                ("acc_pairs_symmetric", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -74,6 +75,7 @@ _SIGS = {
     "frost_get_state": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(_D)]),
     "frost_accel_gradient": (ctypes.c_int, [_P, _P, _I64, _P, _I64, _D, _P, _P, _P]),
     "frost_timesteps": (ctypes.c_int, [_P, _P, _I64, _P]),
+    "frost_accel_pairwise": (ctypes.c_int, [_P, _P, _I64, _P, _I64, _P, _P]),
     "frost_partition": (ctypes.c_int, [_P, _P, _I64, _P, _D, _P, _P, ctypes.POINTER(_I64),
                                        ctypes.POINTER(_I64)]),
     "frost_kick": (ctypes.c_int, [_P, _P, _I64, _P, _D]),
@@ -194,6 +196,11 @@ def frost_accel_gradient(ctx, active, n_active, source, n_source, eps_grad, acc,
                                        _ptr(grad)), "frost_accel_gradient")
 
 
+def frost_accel_pairwise(ctx, a, n_a, b, n_b, acc_a, acc_b) -> None:
+    _check(load().frost_accel_pairwise(ctx, _ptr(a), int(n_a), _ptr(b), int(n_b), _ptr(acc_a), _ptr(acc_b)),
+           "frost_accel_pairwise")
+
+
 def frost_timesteps(ctx, set_, n_set, tau) -> None:
     _check(load().frost_timesteps(ctx, _ptr(set_), int(n_set), _ptr(tau)), "frost_timesteps")
 
@@ -301,7 +308,7 @@ class Frost:
     def __init__(self, m, x, v, G: float = 1.0, eta: float = 0.2, precision: str = "mixed",
                  sym: int = FROST_SYM_HARMONIC, eps_soft: float = 0.0, max_depth: int = 40,
                  stream=None, subtree_max: int = 0, offsets=None, integrator: int = FROST_HHS_FSI,
-                 subtree_blocks: int = 0, branch_streams: int = 0):
+                 subtree_blocks: int = 0, branch_streams: int = 0, sym_cross: int = 0):
         import torch
         self.torch = torch
         o = frost_default_opts()
@@ -314,6 +321,7 @@ class Frost:
         o.integrator = int(integrator)
         o.subtree_blocks = int(subtree_blocks)
         o.branch_streams = int(branch_streams)
+        o.sym_cross = int(sym_cross)
         self.n = int(np.asarray(m).shape[0]) if not hasattr(m, "shape") else int(m.shape[0])
         self.G = G
         self.eta = eta
@@ -360,6 +368,16 @@ class Frost:
         frost_accel_gradient(self.ctx, A, na, B, ns, eps_grad, out.get("acc"), out.get("acc_tilde"),
                              out.get("grad"))
         return out
+
+    def accel_pairwise(self, a, b):
+        """Accelerations of the disjoint lists a and b due to each other, each pair once."""
+        t = self.torch
+        A = self._dev(a, t.int32)
+        B = self._dev(b, t.int32)
+        out_a = t.empty((int(A.numel()), 3), dtype=t.float64, device="cuda")
+        out_b = t.empty((int(B.numel()), 3), dtype=t.float64, device="cuda")
+        frost_accel_pairwise(self.ctx, A, int(A.numel()), B, int(B.numel()), out_a, out_b)
+        return out_a, out_b
 
     def timesteps(self, set_=None, n_set=None):
         t = self.torch
@@ -428,6 +446,12 @@ class Frost:
         frost_set_timing(self.ctx, on)
 
     def autotune(self):
+        """Launch shapes of the pair kernels ({kind: {size: waves}}); on a batch context the
+        team split, {"team_min_n": ..., "team_blocks": ...}."""
+        if self.offsets is not None:
+            out = (ctypes.c_int32 * 128)()
+            _check(load().frost_autotune(self.ctx, out), "frost_autotune")
+            return {"team_min_n": int(out[0]), "team_blocks": int(out[1])}
         return frost_autotune(self.ctx)
 
 

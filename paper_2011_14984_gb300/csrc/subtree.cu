@@ -687,6 +687,7 @@ constexpr int WARP_N = 32;
 struct WLane {
     double x[3], v[3], m;
     double o[3];
+    double xr[3];  // x - o, drifted with the increments of x (mixed records only)
 };
 
 __device__ __forceinline__ float wsh(float v, int j) { return __shfl_sync(0xffffffffu, v, j); }
@@ -709,7 +710,7 @@ __device__ __noinline__ void w_acc(const SubParams &p, const WLane &L, unsigned 
         float ax[1] = {0.f}, ay[1] = {0.f}, az[1] = {0.f};
         int c = 0;
         AccMixedI<1> I;
-        const double rx = L.x[0] - L.o[0], ry = L.x[1] - L.o[1], rz = L.x[2] - L.o[2];
+        const double rx = L.xr[0], ry = L.xr[1], rz = L.xr[2];
         float hx = (float)rx, hy = (float)ry, hz = (float)rz;
         I.xh[0] = hx; I.yh[0] = hy; I.zh[0] = hz;
         I.xl[0] = (float)(rx - (double)hx);
@@ -760,9 +761,9 @@ __device__ __noinline__ void w_grad(const SubParams &p, const WLane &L, unsigned
     if (MIXED) {
         const float eps2 = (float)p.eps2;
         GradMixedI<1> I;
-        split3(L.x[0] - L.o[0], I.xh[0], I.xm[0], I.xl[0]);
-        split3(L.x[1] - L.o[1], I.yh[0], I.ym[0], I.yl[0]);
-        split3(L.x[2] - L.o[2], I.zh[0], I.zm[0], I.zl[0]);
+        split3(L.xr[0], I.xh[0], I.xm[0], I.xl[0]);
+        split3(L.xr[1], I.yh[0], I.ym[0], I.yl[0]);
+        split3(L.xr[2], I.zh[0], I.zm[0], I.zl[0]);
         I.ahx[0] = trunc12((float)ai[0]);
         I.ahy[0] = trunc12((float)ai[1]);
         I.ahz[0] = trunc12((float)ai[2]);
@@ -841,7 +842,7 @@ __device__ __noinline__ double w_tstep(const SubParams &p, const WLane &L, unsig
     }
     if (MIXED) {
         TstepMixedI<1> I;
-        const double rx = L.x[0] - L.o[0], ry = L.x[1] - L.o[1], rz = L.x[2] - L.o[2];
+        const double rx = L.xr[0], ry = L.xr[1], rz = L.xr[2];
         const float hx = (float)rx, hy = (float)ry, hz = (float)rz;
         I.xh[0] = hx; I.yh[0] = hy; I.zh[0] = hz;
         I.xl[0] = (float)(rx - (double)hx);
@@ -892,10 +893,15 @@ __device__ __forceinline__ void w_kick(WLane &L, bool on, const double (&a)[3], 
         for (int c = 0; c < 3; ++c) L.v[c] = __dadd_rn(L.v[c], __dmul_rn(dt, a[c]));
 }
 
+template <bool MIXED>
 __device__ __forceinline__ void w_drift(WLane &L, bool on, double dt)
 {
     if (on)
-        for (int c = 0; c < 3; ++c) L.x[c] = __dadd_rn(L.x[c], __dmul_rn(dt, L.v[c]));
+        for (int c = 0; c < 3; ++c) {
+            const double d = __dmul_rn(dt, L.v[c]);
+            L.x[c] = __dadd_rn(L.x[c], d);
+            if (MIXED) L.xr[c] = __dadd_rn(L.xr[c], d);
+        }
 }
 
 template <bool MIXED>
@@ -910,13 +916,13 @@ __device__ void w_fsi(const SubParams &p, WLane &L, unsigned S, double dt, Count
     float wm;
     w_acc<MIXED>(p, L, S, src, false, a, wm);
     w_kick(L, in, a, dt / 6.0);
-    w_drift(L, in, 0.5 * dt);
+    w_drift<MIXED>(L, in, 0.5 * dt);
     w_acc<MIXED>(p, L, S, src, true, a, wm);
     w_grad<MIXED>(p, L, S, src, a, MIXED ? SLOT_FRACTION * wm : INFINITY, g);
     const double c = dt * dt / 48.0;
     for (int q = 0; q < 3; ++q) at[q] = a[q] + c * g[q];
     w_kick(L, in, at, 2.0 * dt / 3.0);
-    w_drift(L, in, 0.5 * dt);
+    w_drift<MIXED>(L, in, 0.5 * dt);
     w_acc<MIXED>(p, L, S, src, false, a, wm);
     w_kick(L, in, a, dt / 6.0);
     if (lane == 0) {
@@ -987,6 +993,7 @@ __device__ __noinline__ int warp_hhs(const SubParams &p, const int32_t *Sg, int 
             hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
         }
         L.o[c] = MIXED ? 0.5 * (lo + hi) : 0.0;
+        L.xr[c] = L.x[c] - L.o[c];
     }
     const unsigned all = (n >= 32) ? 0xffffffffu : ((1u << n) - 1u);
     if (lane == 0) {

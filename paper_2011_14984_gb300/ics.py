@@ -199,6 +199,14 @@ def plummer_kroupa_binaries(n: int, seed: int, binary_fraction: float = 0.05,
     return m, x, v
 
 
+def binary_pairs(n: int, binary_fraction: float = 0.05) -> np.ndarray:
+    """Index pairs [k, 2] of the binary members that plummer_kroupa_binaries(n, ...) stores
+    adjacently after the single stars (bookkeeping only)."""
+    n_bin = int(round(binary_fraction * n / 2.0))
+    i1 = (n - 2 * n_bin) + 2 * np.arange(n_bin)
+    return np.stack([i1, i1 + 1], axis=1)
+
+
 def cluster_batch(n_clusters: int = 256, seed0: int = 1000, n_min: int = 64, n_max: int = 4096):
     """Independent Plummer clusters (each in its own Henon units) with log-uniform sizes
     N_k = floor(n_min * (n_max / n_min)^U).  Returns (offsets[n_clusters+1], m, x, v)."""

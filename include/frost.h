@@ -86,8 +86,11 @@ typedef struct {
     int32_t sym_cross;      /* 0 (default): the Newtonian kick_sf of a hierarchy level
                                evaluates each S x F pair once for both sides (see
                                frost_accel_pairwise) where that grid fills the GPU, else two
-                               one-sided passes on two streams; 1: always once; -1: always two
-                               one-sided passes */
+                               one-sided passes on two streams; and, in the mixed mode, the
+                               time-step pass of a set of at least 8192 particles evaluates each
+                               pair once for both particles (the same result bits: the pair
+                               criteria are symmetric and a minimum does not depend on the
+                               order).  1: both always; -1: never */
 } frost_opts;
 
 typedef enum {

@@ -89,6 +89,9 @@ constexpr size_t kRecBytes = 96;
 constexpr int64_t kBatchTeamMinN = 768;
 constexpr int kBatchTeamBlocks = 8;
 
+// sets from this size on take the symmetric time-step pass (mixed mode, frost_opts.sym_cross = 0)
+constexpr int kSymTstepMinN = 8192;
+
 // autotuner rows: the pass kinds, and the Newtonian pass that feeds a gradient (mixed mode:
 // its wmax prepass and deferred double-float terms give it a cost profile of its own)
 constexpr int TUNE_ACC_ACCURATE = 3;
@@ -161,6 +164,7 @@ struct frost_ctx {
     unsigned long long lev_seen[2][SUBTREE_STAT_LEVELS] = {};
     Misc *dmisc = nullptr, *hmisc = nullptr;
     std::vector<int32_t *> lvS, lvF;                 // per-level slow/fast lists
+    unsigned *jbest = nullptr;                       // j-side minima of the symmetric time-step pass
     double *pj = nullptr;                            // j-side partials of the symmetric pass
     size_t pj_elems = 0;
     int sym_cross = 0;                               // symmetric S x F Newtonian passes in kick_sf:
@@ -543,6 +547,18 @@ void pass_tstep(frost_ctx *c, Lane &L, const int32_t *P, int nP, double *tau)
     }
     if (c->mixed) launch_pack_tstep_mixed(L.s, P, nP, c->x, c->v, c->m, c->N, c->G, (float4 *)L.recA, acc);
     else launch_pack_tstep_fp64(L.s, P, nP, c->x, c->v, c->m, c->N, c->G, (double4_32a *)L.recA, acc);
+    const int64_t pairs = (int64_t)nP * (nP - 1);
+    // mixed mode, large sets (or always with sym_cross = 1): every pair once for both particles
+    if (c->mixed && &L == &c->main && (c->sym_cross > 0 || (c->sym_cross == 0 && nP >= kSymTstepMinN))) {
+        const TstepSymShape sh = tstep_sym_shape(nP, c->n_sm, c->part_elems);
+        {
+            TimedScope ts(c, L.s, PASS_TSTEP, pairs);
+            launch_tstep_sym(L.s, L.recA, nP, c->eta, c->sym, sh, L.part, c->jbest, tau, &c->dmisc->err);
+        }
+        c->st.kernel_launches += 4;
+        c->st.tstep_pairs += pairs;
+        return;
+    }
     PairArgs a;
     a.irec = L.recA;
     a.jrec = L.recA;
@@ -552,7 +568,6 @@ void pass_tstep(frost_ctx *c, Lane &L, const int32_t *P, int nP, double *tau)
     a.eps2 = 0.0;
     a.part = L.part;
     a.shape = shape_for(c, PASS_TSTEP, nP, nP);
-    const int64_t pairs = (int64_t)nP * (nP - 1);
     {
         TimedScope ts(c, L.s, PASS_TSTEP, pairs);
         launch_tstep(L.s, c->mixed, a, c->eta, c->sym, &c->dmisc->err);
@@ -656,7 +671,9 @@ bool pass_acc_sym(frost_ctx *c, Lane &L, const int32_t *A, int nA, const int32_t
     if (!force && (long long)sh.ngroups * sh.nsplit < (long long)sh.blocks_per_wave) return false;
     const int64_t pairs = (int64_t)nA * nB;
     {
-        TimedScope ts(c, L.s, PASS_ACC, pairs);
+        // the kernel delivers both interactions of every pair: its algorithmic work for the
+        // roofline is that of two one-sided passes
+        TimedScope ts(c, L.s, PASS_ACC, 2 * pairs);
         launch_acc_sym(L.s, c->mixed, swap ? recB : recA, swap ? recA : recB, ni, nj, c->eps2, L.part, c->pj, sh);
     }
     double *out_i = swap ? outB : outA, *out_j = swap ? outA : outB;
@@ -952,7 +969,7 @@ void destroy(frost_ctx *c)
     if (c->d_ecl) cudaFree(c->d_ecl);
     void *dev[] = {c->x, c->v, c->m, c->all, c->marks, c->recA, c->recB, c->part,
                    c->aA, c->aB, c->atA, c->atB, c->aC, c->tau, c->wA, c->wB, c->perm,
-                   c->ptmp, c->dmisc, c->hist, c->hA, c->hB, c->part_hot, c->pj};
+                   c->ptmp, c->dmisc, c->hist, c->hA, c->hB, c->part_hot, c->pj, c->jbest};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (c->hmisc) cudaFreeHost(c->hmisc);
@@ -1097,6 +1114,7 @@ static frost_status init_impl(frost_ctx **out, int64_t n, const double *m, const
     }
     c->pj_elems = 3 * 8 * N;
     INIT_CUDA(cudaMalloc(&c->pj, sizeof(double) * c->pj_elems));
+    INIT_CUDA(cudaMalloc(&c->jbest, sizeof(unsigned) * N));
     INIT_CUDA(cudaMalloc(&c->perm, sizeof(int32_t) * N));
     INIT_CUDA(cudaMalloc(&c->ptmp, sizeof(int32_t) * N));
     if (n_clusters > 0) {

@@ -213,6 +213,17 @@ SymShape sym_shape(bool mixed, int n_a, int n_s, int n_sm, size_t part_elems, si
 void launch_acc_sym(cudaStream_t s, bool mixed, const void *irec, const void *jrec, int n_a, int n_s, double eps2,
                     double *part, double *pj, const SymShape &sh);
 
+// Symmetric time-step pass over one set (mixed): every pair once, tau[i] written directly.
+// jbest: [n] unsigned scratch (the j-side minima as FP32 bits); part: [blocks of row 0][n].
+struct TstepSymShape {
+    int ntiles = 0;  // 128-record tiles of the set
+    int tps = 1;     // tiles per split of a row
+    int blocks = 0;  // blocks of the upper triangle
+};
+TstepSymShape tstep_sym_shape(int n, int n_sm, size_t part_elems);
+void launch_tstep_sym(cudaStream_t s, const void *rec, int n, double eta, int sym, const TstepSymShape &sh,
+                      double *part, unsigned *jbest, double *tau, int *err);
+
 // ---- single-CTA subtree solver (subtree.cu) ------------------------------------------
 constexpr int SUBTREE_MAX_FRAMES = 64;  // recursion frames per block (max_depth < 64)
 constexpr int SUBTREE_STAT_LEVELS = 48; // per-depth statistics (last entry: deeper levels)

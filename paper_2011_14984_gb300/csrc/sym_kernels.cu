@@ -321,3 +321,315 @@ void launch_acc_sym(cudaStream_t s, bool mixed, const void *irec, const void *jr
 }
 
 }  // namespace frost
+
+// ======================================================================================
+// Symmetric time-step pass over one set (Sec. 4.3, tau_i = min_j of the symmetrised pair
+// time-steps).  The pair criteria are symmetric bit for bit: x_ij = -x_ji and v_ij = -v_ji
+// exactly in IEEE arithmetic, r^2, v^2, r.v are the same sums of the same products, and
+// G (m_i + m_j) is a commutative sum.  So every pair can be evaluated once for both particles.
+// A minimum is exact and independent of the order, so the j side needs no fixed-order sum:
+// a warp reduce-scatter of the minima of 8 sources, a shared-memory atomicMin per warp and a
+// global atomicMin per source and block (non-negative floats order as their bit patterns).
+//
+// Tiles: row ib (the i-block of 256 particles) takes the tiles from its own range onwards;
+// the two tiles that overlap its own particles run the one-sided masked loop (i side only:
+// their particles are also this block's i-particles), the later ones the symmetric loop.
+// A criterion is skipped only when it can lower neither particle's minimum: the bound is the
+// larger of the i-particle's running bound and the source's bound read from the global minima
+// when the tile is staged (stale values are larger, so the test stays conservative).  The
+// result is the exact minimum over all pairs, the same bits as the one-sided pass.
+// ======================================================================================
+namespace frost {
+namespace {
+
+using namespace dev;
+
+// One source against the thread's two particles (as tstep_x2_j), with the skip bound
+// max(bnd_i, bnd_j); tj[k]: the pair's time-step if evaluated for lane k, else +inf.
+// valid = false: a stand-in past the end of the list (no update, +inf).
+template <int SYM>
+__device__ __forceinline__ void tstep_sym_x2_j(const float4 A, const float4 B, const float4 C, const float4 V0,
+                                               const float4 V1, const float4 W0, const float4 W1, const TstepX2I &P,
+                                               float eta, float eta15, float bndj, bool valid, float (&best)[2],
+                                               float (&minr2)[2], float (&bnd)[2], float (&tj)[2])
+{
+    const float2 dx = __fadd2_rn(__fadd2_rn(make_float2(A.x, A.y), P.nxh), __fadd2_rn(make_float2(B.z, B.w), P.nxl));
+    const float2 dy = __fadd2_rn(__fadd2_rn(make_float2(A.z, A.w), P.nyh), __fadd2_rn(make_float2(C.x, C.y), P.nyl));
+    const float2 dz = __fadd2_rn(__fadd2_rn(make_float2(B.x, B.y), P.nzh), __fadd2_rn(make_float2(C.z, C.w), P.nzl));
+    const float2 ux = __fadd2_rn(make_float2(V0.x, V0.y), P.nvx);
+    const float2 uy = __fadd2_rn(make_float2(V0.z, V0.w), P.nvy);
+    const float2 uz = __fadd2_rn(make_float2(V1.x, V1.y), P.nvz);
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+    const float2 v2 = __ffma2_rn(ux, ux, __ffma2_rn(uy, uy, __fmul2_rn(uz, uz)));
+    const float2 rv = __ffma2_rn(dx, ux, __ffma2_rn(dy, uy, __fmul2_rn(dz, uz)));
+    const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 ri2 = __fmul2_rn(ri, ri);
+    const float2 gm = __fadd2_rn(P.gm, make_float2(V1.z, V1.w));
+    const float2 q = __fmul2_rn(__fmul2_rn(gm, ri2), ri);
+    const float2 tff = make_float2(rsqrtf(q.x), rsqrtf(q.y));
+    const float2 rvr2 = __fmul2_rn(rv, ri2);
+    const float2 iv = make_float2(rsqrtf(v2.x), rsqrtf(v2.y));
+    const float2 tfb = __fmul2_rn(__fmul2_rn(r2, ri), iv);
+    const float Bb[2] = {fmaxf(bnd[0], bndj), fmaxf(bnd[1], bndj)};
+    const float2 ce = make_float2(Bb[0] * eta, Bb[1] * eta);
+    const float2 z = __fmul2_rn(ce, rvr2);
+    float2 hfb, mfb;
+    if (SYM & 4) {
+        const float2 wx = __fadd2_rn(make_float2(W0.x, W0.y), P.nax);
+        const float2 wy = __fadd2_rn(make_float2(W0.z, W0.w), P.nay);
+        const float2 wz = __fadd2_rn(make_float2(W1.x, W1.y), P.naz);
+        const float2 va = __ffma2_rn(ux, wx, __ffma2_rn(uy, wy, __fmul2_rn(uz, wz)));
+        const float2 niv2 = __fmul2_rn(__fmul2_rn(make_float2(-1.f, -1.f), iv), iv);
+        hfb = __ffma2_rn(va, niv2, rvr2);
+        const float2 zb = __fmul2_rn(ce, hfb);
+        mfb = make_float2(-fabsf(zb.x), -fabsf(zb.y));
+    } else {
+        hfb = __ffma2_rn(__fmul2_rn(gm, ri), __fmul2_rn(iv, iv), make_float2(1.f, 1.f));
+        mfb = make_float2(-fabsf(z.x) * hfb.x, -fabsf(z.y) * hfb.y);
+    }
+    const float2 mff = make_float2(-1.5f * fabsf(z.x), -1.5f * fabsf(z.y));
+    const float2 lff = __ffma2_rn(mff, tff, tff);
+    const float2 lfb = __ffma2_rn(mfb, tfb, tfb);
+    const float tf[2] = {tff.x, tff.y}, tb[2] = {tfb.x, tfb.y}, rq[2] = {rvr2.x, rvr2.y}, hq[2] = {hfb.x, hfb.y};
+    const float rr[2] = {r2.x, r2.y}, vv[2] = {v2.x, v2.y}, lf[2] = {lff.x, lff.y}, lb[2] = {lfb.x, lfb.y};
+    bool nff[2], nfb[2];
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (valid) minr2[k] = fminf(minr2[k], rr[k]);
+        nff[k] = valid && !(lf[k] >= Bb[k]);
+        nfb[k] = valid && (vv[k] > 0.f) && !(lb[k] >= Bb[k]);
+        any = any || nff[k] || nfb[k];
+        tj[k] = INFINITY;
+    }
+    if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            float t = INFINITY;
+            if (nff[k]) t = tf[k] * symf<(SYM & 3)>(eta15 * rq[k] * tf[k]);
+            if (nfb[k]) {
+                const float dfb = (SYM & 4) ? eta * hq[k] * tb[k] : eta * rq[k] * hq[k] * tb[k];
+                t = fminf(t, tb[k] * symf<(SYM & 3)>(dfb));
+            }
+            tj[k] = t;
+            best[k] = fminf(best[k], t);
+            bnd[k] = 1.001f * best[k];
+        }
+    }
+}
+
+__device__ __forceinline__ float reduce_scatter8_min(const float (&v)[8], int lane)
+{
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    float c1[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float send = b4 ? v[k] : v[4 + k];
+        const float keep = b4 ? v[4 + k] : v[k];
+        c1[k] = fminf(keep, __shfl_xor_sync(0xffffffffu, send, 16));
+    }
+    float c2[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float send = b3 ? c1[k] : c1[2 + k];
+        const float keep = b3 ? c1[2 + k] : c1[k];
+        c2[k] = fminf(keep, __shfl_xor_sync(0xffffffffu, send, 8));
+    }
+    const float send = b2 ? c2[0] : c2[1];
+    const float keep = b2 ? c2[1] : c2[0];
+    float c3 = fminf(keep, __shfl_xor_sync(0xffffffffu, send, 4));
+    c3 = fminf(c3, __shfl_xor_sync(0xffffffffu, c3, 2));
+    return fminf(c3, __shfl_xor_sync(0xffffffffu, c3, 1));
+}
+
+constexpr unsigned kInfBits = 0x7f800000u;
+
+__global__ void k_fill_inf(unsigned *__restrict__ p, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = kInfBits;
+}
+
+template <int BS, int TJ, int SYM>
+__global__ void __launch_bounds__(BS) k_tstep_sym_mixed(const float4 *__restrict__ rec, int n, int ntiles, int tps,
+                                                        float eta, double *__restrict__ part,
+                                                        unsigned *__restrict__ jbest, int *__restrict__ err)
+{
+    constexpr int ILP = 2;
+    constexpr int TA = (SYM & 4) ? TJ : 1;
+    __shared__ float4 sA[TJ], sB[TJ], sC[TJ], sV0[TJ], sV1[TJ];
+    __shared__ float4 sW0[TA], sW1[TA];
+    __shared__ float sBj[TJ];
+    __shared__ unsigned sJ[TJ];
+    const int tid = threadIdx.x, lane = tid & 31;
+    // block -> (row, split) of the upper triangle of tiles
+    const int nblk = (n + BS * ILP - 1) / (BS * ILP);
+    int b = blockIdx.x, ib = 0;
+    for (; ib < nblk; ++ib) {
+        const int S = max(0, (ntiles - 2 * ib + tps - 1) / tps);
+        if (b < S) break;
+        b -= S;
+    }
+    if (ib >= nblk) return;
+    const int ibase = ib * BS * ILP;
+    const int tile0 = 2 * ib + b * tps, tile1 = min(ntiles, tile0 + tps);
+    TstepMixedI<ILP> I;
+    int ipos[ILP];
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+        const int i = ibase + k * BS + tid;
+        ipos[k] = i;
+        float4 a = make_float4(0.f, 0.f, 0.f, 1.f), bb = zero4, c = a, d = zero4;
+        if (i < n) {
+            a = rec[i];
+            bb = rec[n + i];
+            c = rec[2 * n + i];
+            if (SYM & 4) d = rec[3 * n + i];
+        }
+        I.xh[k] = a.x; I.yh[k] = a.y; I.zh[k] = a.z;
+        I.xl[k] = bb.x; I.yl[k] = bb.y; I.zl[k] = bb.z;
+        I.vx[k] = c.x; I.vy[k] = c.y; I.vz[k] = c.z; I.gm[k] = c.w;
+        I.ax[k] = d.x; I.ay[k] = d.y; I.az[k] = d.z;
+    }
+    // particles past the end take part in nothing (the bounds below keep them at +inf)
+    const bool live[2] = {ipos[0] < n, ipos[1] < n};
+    TstepX2I P;
+    P.nxh = make_float2(-I.xh[0], -I.xh[1]);
+    P.nyh = make_float2(-I.yh[0], -I.yh[1]);
+    P.nzh = make_float2(-I.zh[0], -I.zh[1]);
+    P.nxl = make_float2(-I.xl[0], -I.xl[1]);
+    P.nyl = make_float2(-I.yl[0], -I.yl[1]);
+    P.nzl = make_float2(-I.zl[0], -I.zl[1]);
+    P.nvx = make_float2(-I.vx[0], -I.vx[1]);
+    P.nvy = make_float2(-I.vy[0], -I.vy[1]);
+    P.nvz = make_float2(-I.vz[0], -I.vz[1]);
+    P.gm = make_float2(I.gm[0], I.gm[1]);
+    P.nax = make_float2(-I.ax[0], -I.ax[1]);
+    P.nay = make_float2(-I.ay[0], -I.ay[1]);
+    P.naz = make_float2(-I.az[0], -I.az[1]);
+    float best[2] = {INFINITY, INFINITY}, minr2[2] = {INFINITY, INFINITY}, bnd[2] = {INFINITY, INFINITY};
+    const float eta15 = 1.5f * eta;
+    for (int tile = tile0; tile < tile1; ++tile) {
+        const int j0 = tile * TJ;
+        const int cnt = min(TJ, n - j0);
+        const int cnt8 = (cnt + 7) & ~7;
+        const bool diag = tile < 2 * ib + 2;
+        __syncthreads();
+        for (int t = tid; t < cnt8; t += BS) {
+            float4 a = zero4, bb = zero4, v = zero4;
+            if (t < cnt) {
+                a = rec[j0 + t];
+                bb = rec[n + j0 + t];
+                v = rec[2 * n + j0 + t];
+            }
+            sA[t] = make_float4(a.x, a.x, a.y, a.y);
+            sB[t] = make_float4(a.z, a.z, bb.x, bb.x);
+            sC[t] = make_float4(bb.y, bb.y, bb.z, bb.z);
+            sV0[t] = make_float4(v.x, v.x, v.y, v.y);
+            sV1[t] = make_float4(v.z, v.z, v.w, v.w);
+            if (SYM & 4) {
+                const float4 w = (t < cnt) ? rec[3 * n + j0 + t] : zero4;
+                sW0[t] = make_float4(w.x, w.x, w.y, w.y);
+                sW1[t] = make_float4(w.z, w.z, 0.f, 0.f);
+            }
+            sBj[t] = (t < cnt && !diag) ? 1.001f * __uint_as_float(jbest[j0 + t]) : INFINITY;
+            sJ[t] = kInfBits;
+        }
+        __syncthreads();
+        if (diag) {
+            // the tiles of the block's own particles: every pair from the i side, masked i = j
+            for (int jj = 0; jj < cnt; ++jj) {
+                const float4 a = sA[jj], bq = sB[jj], c = sC[jj], v0 = sV0[jj], v1 = sV1[jj];
+                const float4 J0 = make_float4(a.x, a.z, bq.x, 0.f);
+                const float4 J1 = make_float4(bq.z, c.x, c.z, 0.f);
+                const float4 JV = make_float4(v0.x, v0.z, v1.x, v1.z);
+                float4 JA = zero4;
+                if (SYM & 4) JA = make_float4(sW0[jj].x, sW0[jj].z, sW1[jj].x, 0.f);
+                tstep_mixed_j<ILP, SYM, true>(J0, J1, JV, JA, I, eta, eta15, j0 + jj, ipos, best, minr2);
+            }
+#pragma unroll
+            for (int k = 0; k < 2; ++k) bnd[k] = 1.001f * best[k];
+            continue;
+        }
+        for (int jj = 0; jj < cnt8; jj += 8) {
+            float tmin[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                float tj[2];
+                tstep_sym_x2_j<SYM>(sA[jj + u], sB[jj + u], sC[jj + u], sV0[jj + u], sV1[jj + u],
+                                    (SYM & 4) ? sW0[jj + u] : zero4, (SYM & 4) ? sW1[jj + u] : zero4, P, eta, eta15,
+                                    sBj[jj + u], jj + u < cnt, best, minr2, bnd, tj);
+                tmin[u] = fminf(live[0] ? tj[0] : INFINITY, live[1] ? tj[1] : INFINITY);
+            }
+            const float m = reduce_scatter8_min(tmin, lane);
+            if ((lane & 3) == 0 && m < INFINITY) atomicMin(&sJ[jj + (lane >> 2)], __float_as_uint(m));
+        }
+        __syncthreads();
+        for (int t = tid; t < cnt; t += BS)
+            if (sJ[t] < kInfBits) atomicMin(&jbest[j0 + t], sJ[t]);
+    }
+    // the i side of this row and split
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+        if (!live[k]) continue;
+        part[(size_t)b * n + ipos[k]] = (double)best[k];
+        if (minr2[k] == 0.f) atomicOr(err, ERR_COINCIDENT);
+    }
+}
+
+__global__ void k_finalize_tau_sym(const double *__restrict__ part, const unsigned *__restrict__ jbest, int n,
+                                   int ntiles, int tps, int ipb, double eta, double *__restrict__ tau,
+                                   int *__restrict__ err)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int ib = i / ipb;
+    const int S = max(0, (ntiles - 2 * ib + tps - 1) / tps);
+    double b = (double)__uint_as_float(jbest[i]);
+    for (int s = 0; s < S; ++s) b = fmin(b, part[(size_t)s * n + i]);
+    const double t = eta * b;
+    if (!(t > 0.0)) atomicOr(err, ERR_NONFINITE);
+    tau[i] = t;
+}
+
+}  // namespace
+
+TstepSymShape tstep_sym_shape(int n, int n_sm, size_t part_elems)
+{
+    TstepSymShape sh;
+    constexpr int BS = SYM_BS, ILP = 2, TJ = SYM_TJ;
+    const int nblk = (n + BS * ILP - 1) / (BS * ILP);
+    sh.ntiles = (n + TJ - 1) / TJ;
+    // about 8 waves of blocks (6 per SM), each at least one tile, the row-0 partials in part
+    const long long tiles_total = (long long)nblk * sh.ntiles - (long long)nblk * (nblk - 1);  // upper triangle
+    const long long target = 8LL * 6 * n_sm;
+    int tps = (int)std::max<long long>(1, (tiles_total + target - 1) / target);
+    while ((long long)((sh.ntiles + tps - 1) / tps) * n > (long long)part_elems) ++tps;
+    sh.tps = tps;
+    long long blocks = 0;
+    for (int ib = 0; ib < nblk; ++ib) blocks += std::max(0, (sh.ntiles - 2 * ib + tps - 1) / tps);
+    sh.blocks = (int)blocks;
+    return sh;
+}
+
+void launch_tstep_sym(cudaStream_t s, const void *rec, int n, double eta, int sym, const TstepSymShape &sh,
+                      double *part, unsigned *jbest, double *tau, int *err)
+{
+    k_fill_inf<<<(n + 255) / 256, 256, 0, s>>>(jbest, n);
+#define FROST_TSTEP_SYM_CASE(SYMV)                                                                       \
+    k_tstep_sym_mixed<SYM_BS, SYM_TJ, SYMV><<<sh.blocks, SYM_BS, 0, s>>>((const float4 *)rec, n, sh.ntiles, sh.tps, \
+                                                                         (float)eta, part, jbest, err);
+    switch (sym) {
+    case 0: FROST_TSTEP_SYM_CASE(0) break;
+    case 1: FROST_TSTEP_SYM_CASE(1) break;
+    case 4: FROST_TSTEP_SYM_CASE(4) break;
+    case 5: FROST_TSTEP_SYM_CASE(5) break;
+    case 6: FROST_TSTEP_SYM_CASE(6) break;
+    default: FROST_TSTEP_SYM_CASE(2) break;
+    }
+#undef FROST_TSTEP_SYM_CASE
+    k_finalize_tau_sym<<<(n + 255) / 256, 256, 0, s>>>(part, jbest, n, sh.ntiles, sh.tps, 2 * SYM_BS, eta, tau, err);
+}
+
+}  // namespace frost

@@ -104,16 +104,20 @@ __device__ __forceinline__ void split3(double v, float &h, float &l, float &ll)
 }
 
 // x_j - x_i from three-part splits: the two larger differences are exact (TwoSum), the
-// smallest parts lie 2^-48 below the value
+// smallest parts' difference is rounded once.  The result is renormalised (TwoSum of the
+// high word and the collected tail): with splits of 12 + 12 + 24 bits (the gradient records)
+// a pair closer than ~2^-24 |x| has equal or one-unit-apart high and middle parts, so the
+// tail can be as large as the high word, and the products of df::mul, which drop lo x lo,
+// need |lo| <= ulp(hi) / 2.
 __device__ __forceinline__ dfloat sep(float jh, float jl, float jll, float ih, float il, float ill)
 {
     float a, e1, b, e2, h, e4;
     two_sum(jh, -ih, a, e1);
     two_sum(jl, -il, b, e2);
     two_sum(a, b, h, e4);
+    const float tail = __fadd_rn(e4, __fadd_rn(e1, __fadd_rn(e2, __fsub_rn(jll, ill))));
     dfloat r;
-    r.h = h;
-    r.l = __fadd_rn(e4, __fadd_rn(e1, __fadd_rn(e2, __fsub_rn(jll, ill))));
+    two_sum(h, tail, r.h, r.l);
     return r;
 }
 

@@ -924,6 +924,34 @@ def test_mixed_gradient_beyond_the_fp32_range_at_a_binary_pericentre():
     assert np.all(dg <= bound), (np.max(dg / bound), int(np.argmax(dg / bound)) + 2)
 
 
+def test_mixed_gradient_of_tight_pairs_far_from_the_origin():
+    """Pairs 1e-9 to 3e-6 apart at |x| = 1 to 4 (hard binaries near pericentre away from the
+    centre): their mutual gradient term is a dominant, deferred double-float term built from
+    12 + 12 + 24-bit split records.  For such pairs the high and middle parts cancel and the
+    low-part difference is as large as the result, so the separation must be renormalised
+    before it enters double-float products (an unnormalised one gave errors of 1e3 in r^2).
+    Every member's a and g within 1e-5 of the oracle."""
+    m, x, v = ics.plummer(1000, 81, masses=ics.kroupa_masses(1000, 81))
+    rng = np.random.default_rng(2)
+    seps = [1e-9, 3e-9, 1e-8, 3e-8, 1e-7, 3e-7, 1e-6, 3e-6]
+    members = []
+    for k, r in enumerate(seps):
+        i, j = 2 * k, 2 * k + 1
+        d = rng.normal(size=3)
+        u = rng.normal(size=3)
+        x[i] = (1.0 + 3.0 * k / len(seps)) * u / np.linalg.norm(u)
+        x[j] = x[i] + r * d / np.linalg.norm(d)
+        members += [i, j]
+    A = np.arange(m.size, dtype=np.int32)
+    a_ref, g_ref = oracle_g(m, x, A, A)
+    f = F(m, x, v, precision="mixed")
+    out = f.accel_gradient(None, None, eps_grad=1e-9)
+    f.close()
+    a, g = cpu(out["acc"]), cpu(out["grad"])
+    ea, eg = rel(a, a_ref)[members], rel(g, g_ref)[members]
+    assert ea.max() < 1e-5 and eg.max() < 1e-5, (ea.max(), eg.max(), np.round(np.log10(eg + 1e-30), 1))
+
+
 def test_kroupa_hard_binaries_trajectory_fp64():
     """Plummer N = 2000 with Kroupa masses and 5 % hard binaries (a in [1e-5, 1e-3], thermal
     e; seed 31): one top-level step of 2^-10 reaches hierarchy depth 19, through the grid

@@ -89,8 +89,11 @@ constexpr size_t kRecBytes = 96;
 constexpr int64_t kBatchTeamMinN = 768;
 constexpr int kBatchTeamBlocks = 8;
 
-// sets from this size on take the symmetric time-step pass (mixed mode, frost_opts.sym_cross = 0)
+// sets from this size on take the symmetric time-step pass and wmax prepass (mixed mode,
+// frost_opts.sym_cross = 0), and cross pairs of lists from this many pairs on the symmetric
+// cross prepass
 constexpr int kSymTstepMinN = 8192;
+constexpr int64_t kSymCrossPrepassMinPairs = int64_t(1) << 26;
 
 // autotuner rows: the pass kinds, and the Newtonian pass that feeds a gradient (mixed mode:
 // its wmax prepass and deferred double-float terms give it a cost profile of its own)
@@ -390,9 +393,12 @@ int badbit(const frost_ctx *c) { return c->eps2 == 0.0 ? ERR_COINCIDENT : ERR_NO
 // the caller) for the hot-source classification of mark_hot.  kick: the kick of A by the
 // result, fused into the finalisation.  irec / jrec: records already packed by the caller
 // (NULL: packed here into the lane's recA / recB).
+bool use_sym_self(const frost_ctx *c, int n) { return c->sym_cross > 0 || (c->sym_cross == 0 && n >= kSymTstepMinN); }
+
 void pass_acc(frost_ctx *c, Lane &L, const int32_t *A, int nA, const int32_t *B, int nB, bool self,
               double *out_soa, double *out_aos, float *wmax = nullptr, unsigned *hist = nullptr,
-              KickArgs kick = KickArgs(), const void *irec = nullptr, const void *jrec = nullptr)
+              KickArgs kick = KickArgs(), const void *irec = nullptr, const void *jrec = nullptr,
+              bool wmax_ready = false)
 {
     if (nA <= 0) return;
     if (nB <= 0 || (self && nA == 1)) {
@@ -429,8 +435,10 @@ void pass_acc(frost_ctx *c, Lane &L, const int32_t *A, int nA, const int32_t *B,
     const int64_t pairs = self ? (int64_t)nA * (nA - 1) : (int64_t)nA * nB;
     {
         TimedScope ts(c, L.s, PASS_ACC, pairs);
-        if (accurate) {
-            launch_wmax(L.s, a, wmax);
+        if (accurate && !wmax_ready) {
+            // the prepass: each pair once on large sets (the same maxima, bit for bit)
+            if (self && use_sym_self(c, nA)) launch_wmax_sym_self(L.s, a.irec, nA, c->eps2, c->n_sm, c->part_elems, wmax);
+            else launch_wmax(L.s, a, wmax);
             c->st.kernel_launches += 1;
         }
         launch_acc(L.s, c->mixed, a);
@@ -745,10 +753,19 @@ void kick_sf(frost_ctx *c, Lane &M, Lane *Bl, const int32_t *S, int nS, const in
         return;  // joined by br
     }
     unsigned *h = c->mixed ? zero_hists(M) : nullptr;
+    // the prepasses of both accurate passes in one symmetric kernel (each pair once), where
+    // the lists are large
+    bool wready = false;
+    if (c->mixed && c->sym_cross >= 0 && (c->sym_cross > 0 || (int64_t)nS * nF >= kSymCrossPrepassMinPairs)) {
+        TimedScope ts(c, M.s, PASS_ACC, 0);
+        launch_wmax_sym_cross(M.s, M.recA, nS, M.recB, nF, c->eps2, c->n_sm, M.wA, M.wB);
+        c->st.kernel_launches += 1;
+        wready = true;
+    }
     br.fork();
-    pass_acc(c, M, S, nS, F, nF, false, M.aA, nullptr, M.wA, h, KickArgs(), M.recA, M.recB);
+    pass_acc(c, M, S, nS, F, nF, false, M.aA, nullptr, M.wA, h, KickArgs(), M.recA, M.recB, wready);
     pass_acc(c, X, F, nF, S, nS, false, M.aB, nullptr, M.wB, h ? h + HOT_BINS : nullptr, KickArgs(), M.recB,
-             M.recA);
+             M.recA, wready);
     br.join();
     if (h) {
         mark_hot(c, M, nS, nF, false, M.aA, h, h + HOT_BINS, nF, M.hA);
@@ -1248,6 +1265,21 @@ frost_status frost_accel_gradient(frost_ctx *c, const int32_t *active, int64_t n
         if (h) mark_hot(c, M, nA, nA, true, c->aA, h, nullptr, 0, c->hA);
         if (want_grad)
             pass_grad(c, M, A, nA, c->aA, A, nA, c->aA, true, eps_grad, nullptr, acc_tilde, grad, c->wA, c->hA);
+    } else if (want_grad && c->mixed && nB > 0 && c->sym_cross >= 0 &&
+               (c->sym_cross > 0 || (int64_t)nA * nB >= kSymCrossPrepassMinPairs)) {
+        // both accurate passes on records packed once, their prepasses in one symmetric kernel
+        unsigned *h = zero_hists(M);
+        pack_pos(c, M, A, nA, M.recA);
+        pack_pos(c, M, B, nB, M.recB);
+        {
+            TimedScope ts(c, M.s, PASS_ACC, 0);
+            launch_wmax_sym_cross(M.s, M.recA, nA, M.recB, nB, c->eps2, c->n_sm, c->wA, c->wB);
+            c->st.kernel_launches += 1;
+        }
+        pass_acc(c, M, A, nA, B, nB, false, c->aA, acc, c->wA, h, KickArgs(), M.recA, M.recB, true);
+        pass_acc(c, M, B, nB, A, nA, false, c->aB, nullptr, c->wB, h + HOT_BINS, KickArgs(), M.recB, M.recA, true);
+        mark_hot(c, M, nB, nA, false, c->aB, h + HOT_BINS, h, nA, c->hB);
+        pass_grad(c, M, A, nA, c->aA, B, nB, c->aB, false, eps_grad, nullptr, acc_tilde, grad, c->wA, c->hB);
     } else {
         unsigned *h = (want_grad && c->mixed) ? zero_hists(M) : nullptr;
         pass_acc(c, M, A, nA, B, nB, false, c->aA, acc, want_grad ? c->wA : nullptr, h);

@@ -224,6 +224,13 @@ TstepSymShape tstep_sym_shape(int n, int n_sm, size_t part_elems);
 void launch_tstep_sym(cudaStream_t s, const void *rec, int n, double eta, int sym, const TstepSymShape &sh,
                       double *part, unsigned *jbest, double *tau, int *err);
 
+// Symmetric prepasses of the Newtonian pass that feeds a gradient (mixed): wmax = max_j m_j / r^3
+// for one set (every pair once), or for two disjoint lists at once (wA, wB); zeroed here.
+void launch_wmax_sym_self(cudaStream_t s, const void *rec, int n, double eps2, int n_sm, size_t part_elems,
+                          float *wmax);
+void launch_wmax_sym_cross(cudaStream_t s, const void *recA, int nA, const void *recB, int nB, double eps2, int n_sm,
+                           float *wA, float *wB);
+
 // ---- single-CTA subtree solver (subtree.cu) ------------------------------------------
 constexpr int SUBTREE_MAX_FRAMES = 64;  // recursion frames per block (max_depth < 64)
 constexpr int SUBTREE_STAT_LEVELS = 48; // per-depth statistics (last entry: deeper levels)

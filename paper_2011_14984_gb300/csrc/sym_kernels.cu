@@ -633,3 +633,211 @@ void launch_tstep_sym(cudaStream_t s, const void *rec, int n, double eta, int sy
 }
 
 }  // namespace frost
+
+// ======================================================================================
+// Symmetric prepass of the Newtonian pass that feeds a gradient: wmax_i = max_j m_j / r^3 =
+// (min_j r^2 m_j^(-2/3))^(-3/2).  r^2 is symmetric bit for bit and m^(-2/3) is a function of
+// the particle's own record, so each pair gives both particles' values; the minimum (and the
+// monotone map to wmax, then integer atomicMax on the float bits) is exact and independent
+// of the order, so the result is the one-sided prepass's, bit for bit.
+// ======================================================================================
+namespace frost {
+namespace {
+
+using namespace dev;
+
+__device__ __forceinline__ float mq_of(float m) { return (m > 0.f) ? exp2f(-0.6666667f * log2f(m)) : INFINITY; }
+__device__ __forceinline__ float wmax_of(float q)
+{
+    const float y = rsqrtf(q);
+    return y * y * y;
+}
+
+// stage a tile of source records (duplicated for the packed loop) with m^(-2/3); past cnt:
+// far, massless stand-ins
+__device__ __forceinline__ void wsym_stage(const float4 *__restrict__ jrec, int n_s, int j0, int cnt, int cnt8,
+                                           float4 *sA, float4 *sB, float4 *sC, float2 *sM, unsigned *sQ)
+{
+    for (int t = threadIdx.x; t < cnt8; t += blockDim.x) {
+        float4 a = make_float4(-SYM_FAR, -SYM_FAR, -SYM_FAR, 0.f), b = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (t < cnt) {
+            a = jrec[j0 + t];
+            b = jrec[n_s + j0 + t];
+        }
+        const float mq = (t < cnt) ? mq_of(a.w) : INFINITY;
+        sA[t] = make_float4(a.x, a.x, a.y, a.y);
+        sB[t] = make_float4(a.z, a.z, b.x, b.x);
+        sC[t] = make_float4(b.y, b.y, b.z, b.z);
+        sM[t] = make_float2(mq, mq);
+        sQ[t] = kInfBits;
+    }
+}
+
+// the off-diagonal loop over a staged tile: i side into qm, j side into sQ (minima of q)
+__device__ __forceinline__ void wsym_tile(const float4 *sA, const float4 *sB, const float4 *sC, const float2 *sM,
+                                          unsigned *sQ, int cnt8, const AccX2I &P, float2 mqi, float2 e2, float2 &qm,
+                                          int lane)
+{
+    for (int jj = 0; jj < cnt8; jj += 8) {
+        float qj[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const float4 A = sA[jj + u], B = sB[jj + u], C = sC[jj + u];
+            const float2 dx = __fadd2_rn(__fadd2_rn(make_float2(A.x, A.y), P.nxh), __fadd2_rn(make_float2(B.z, B.w), P.nxl));
+            const float2 dy = __fadd2_rn(__fadd2_rn(make_float2(A.z, A.w), P.nyh), __fadd2_rn(make_float2(C.x, C.y), P.nyl));
+            const float2 dz = __fadd2_rn(__fadd2_rn(make_float2(B.x, B.y), P.nzh), __fadd2_rn(make_float2(C.z, C.w), P.nzl));
+            const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+            const float2 q = __fmul2_rn(r2, sM[jj + u]);
+            qm.x = fminf(qm.x, q.x);
+            qm.y = fminf(qm.y, q.y);
+            const float2 qs = __fmul2_rn(r2, mqi);
+            qj[u] = fminf(qs.x, qs.y);
+        }
+        const float m = reduce_scatter8_min(qj, lane);
+        if ((lane & 3) == 0 && m < INFINITY) atomicMin(&sQ[jj + (lane >> 2)], __float_as_uint(m));
+    }
+}
+
+__device__ __forceinline__ void wsym_load_i(const float4 *__restrict__ irec, int n_a, int ibase, int bs, AccX2I &P,
+                                            float2 &mqi, bool (&live)[2], AccMixedI<2> &I)
+{
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int i = ibase + k * bs + threadIdx.x;
+        live[k] = i < n_a;
+        float4 a = make_float4(SYM_FAR, SYM_FAR, SYM_FAR, 0.f), b = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (live[k]) {
+            a = irec[i];
+            b = irec[n_a + i];
+        }
+        I.xh[k] = a.x; I.yh[k] = a.y; I.zh[k] = a.z;
+        I.xl[k] = b.x; I.yl[k] = b.y; I.zl[k] = b.z;
+        (k == 0 ? mqi.x : mqi.y) = live[k] ? mq_of(a.w) : INFINITY;
+    }
+    P.nxh = make_float2(-I.xh[0], -I.xh[1]);
+    P.nyh = make_float2(-I.yh[0], -I.yh[1]);
+    P.nzh = make_float2(-I.zh[0], -I.zh[1]);
+    P.nxl = make_float2(-I.xl[0], -I.xl[1]);
+    P.nyl = make_float2(-I.yl[0], -I.yl[1]);
+    P.nzl = make_float2(-I.zl[0], -I.zl[1]);
+}
+
+// one set, upper triangle of tiles (rows and parts as in k_tstep_sym_mixed)
+template <int BS, int TJ>
+__global__ void __launch_bounds__(BS) k_wmax_sym_self(const float4 *__restrict__ rec, int n, int ntiles, int tps,
+                                                      float eps2, float *__restrict__ wmax)
+{
+    __shared__ float4 sA[TJ], sB[TJ], sC[TJ];
+    __shared__ float2 sM[TJ];
+    __shared__ unsigned sQ[TJ];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int nblk = (n + 2 * BS - 1) / (2 * BS);
+    int b = blockIdx.x, ib = 0;
+    for (; ib < nblk; ++ib) {
+        const int S = max(0, (ntiles - 2 * ib + tps - 1) / tps);
+        if (b < S) break;
+        b -= S;
+    }
+    if (ib >= nblk) return;
+    const int ibase = ib * 2 * BS;
+    const int tile0 = 2 * ib + b * tps, tile1 = min(ntiles, tile0 + tps);
+    AccX2I P;
+    AccMixedI<2> I;
+    float2 mqi;
+    bool live[2];
+    wsym_load_i(rec, n, ibase, BS, P, mqi, live, I);
+    const int ipos[2] = {ibase + tid, ibase + BS + tid};
+    const float2 e2 = make_float2(eps2, eps2);
+    float2 qm = make_float2(INFINITY, INFINITY);
+    for (int tile = tile0; tile < tile1; ++tile) {
+        const int j0 = tile * TJ, cnt = min(TJ, n - j0), cnt8 = (cnt + 7) & ~7;
+        const bool diag = tile < 2 * ib + 2;
+        __syncthreads();
+        wsym_stage(rec, n, j0, cnt, cnt8, sA, sB, sC, sM, sQ);
+        __syncthreads();
+        if (diag) {
+            // the block's own particles: the one-sided masked loop (the i side only)
+            float w[2] = {qm.x, qm.y};
+            for (int jj = 0; jj < cnt; ++jj) {
+                const float4 A = sA[jj], Bq = sB[jj], C = sC[jj];
+                const float4 J0 = make_float4(A.x, A.z, Bq.x, 0.f);
+                const float4 J1 = make_float4(Bq.z, C.x, C.z, sM[jj].x);
+                wmax_mixed_j<2, true>(J0, J1, I, eps2, j0 + jj, ipos, w);
+            }
+            qm = make_float2(w[0], w[1]);
+            continue;
+        }
+        wsym_tile(sA, sB, sC, sM, sQ, cnt8, P, mqi, e2, qm, lane);
+        __syncthreads();
+        for (int t = tid; t < cnt; t += BS)
+            if (sQ[t] < kInfBits) atomicMax((int *)&wmax[j0 + t], __float_as_int(wmax_of(__uint_as_float(sQ[t]))));
+    }
+    if (live[0]) atomicMax((int *)&wmax[ipos[0]], __float_as_int(wmax_of(qm.x)));
+    if (live[1]) atomicMax((int *)&wmax[ipos[1]], __float_as_int(wmax_of(qm.y)));
+}
+
+// two disjoint lists: A on the register side (blocks of 256 along blockIdx.x), B reduced
+// (chunks of j_per_split along blockIdx.y); wA, wB: the two lists' maxima (zeroed before)
+template <int BS, int TJ>
+__global__ void __launch_bounds__(BS) k_wmax_sym_cross(const float4 *__restrict__ irec, const float4 *__restrict__ jrec,
+                                                       int n_a, int n_s, int j_per_split, float eps2,
+                                                       float *__restrict__ wA, float *__restrict__ wB)
+{
+    __shared__ float4 sA[TJ], sB[TJ], sC[TJ];
+    __shared__ float2 sM[TJ];
+    __shared__ unsigned sQ[TJ];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int ibase = blockIdx.x * 2 * BS;
+    const int jb = blockIdx.y * j_per_split, je = min(n_s, jb + j_per_split);
+    AccX2I P;
+    AccMixedI<2> I;
+    float2 mqi;
+    bool live[2];
+    wsym_load_i(irec, n_a, ibase, BS, P, mqi, live, I);
+    const float2 e2 = make_float2(eps2, eps2);
+    float2 qm = make_float2(INFINITY, INFINITY);
+    for (int j0 = jb; j0 < je; j0 += TJ) {
+        const int cnt = min(TJ, je - j0), cnt8 = (cnt + 7) & ~7;
+        __syncthreads();
+        wsym_stage(jrec, n_s, j0, cnt, cnt8, sA, sB, sC, sM, sQ);
+        __syncthreads();
+        wsym_tile(sA, sB, sC, sM, sQ, cnt8, P, mqi, e2, qm, lane);
+        __syncthreads();
+        for (int t = tid; t < cnt; t += BS)
+            if (sQ[t] < kInfBits) atomicMax((int *)&wB[j0 + t], __float_as_int(wmax_of(__uint_as_float(sQ[t]))));
+    }
+    if (live[0]) atomicMax((int *)&wA[ibase + tid], __float_as_int(wmax_of(qm.x)));
+    if (live[1]) atomicMax((int *)&wA[ibase + BS + tid], __float_as_int(wmax_of(qm.y)));
+}
+
+}  // namespace
+
+void launch_wmax_sym_self(cudaStream_t s, const void *rec, int n, double eps2, int n_sm, size_t part_elems,
+                          float *wmax)
+{
+    cudaMemsetAsync(wmax, 0, sizeof(float) * n, s);
+    const TstepSymShape sh = tstep_sym_shape(n, n_sm, part_elems);
+    k_wmax_sym_self<SYM_BS, SYM_TJ><<<sh.blocks, SYM_BS, 0, s>>>((const float4 *)rec, n, sh.ntiles, sh.tps,
+                                                                  (float)eps2, wmax);
+}
+
+void launch_wmax_sym_cross(cudaStream_t s, const void *recA, int nA, const void *recB, int nB, double eps2, int n_sm,
+                           float *wA, float *wB)
+{
+    cudaMemsetAsync(wA, 0, sizeof(float) * nA, s);
+    cudaMemsetAsync(wB, 0, sizeof(float) * nB, s);
+    // the longer list on the register side; about 8 waves of 128-thread blocks (6 per SM)
+    const bool swap = nB > nA;
+    const int ni = swap ? nB : nA, nj = swap ? nA : nB;
+    const int nblk = (ni + 2 * SYM_BS - 1) / (2 * SYM_BS);
+    const int tiles = (nj + SYM_TJ - 1) / SYM_TJ;
+    const long long target = 8LL * 6 * n_sm;
+    const int ns = (int)std::max<long long>(1, std::min<long long>(tiles, (target + nblk - 1) / nblk));
+    const int jps = ((tiles + ns - 1) / ns) * SYM_TJ;
+    const dim3 grid(nblk, (nj + jps - 1) / jps);
+    k_wmax_sym_cross<SYM_BS, SYM_TJ><<<grid, SYM_BS, 0, s>>>((const float4 *)(swap ? recB : recA),
+                                                             (const float4 *)(swap ? recA : recB), ni, nj, jps,
+                                                             (float)eps2, swap ? wB : wA, swap ? wA : wB);
+}
+
+}  // namespace frost

@@ -142,6 +142,29 @@ def test_accel_pairwise_each_pair_once(precision, na, nb, eps_soft):
     assert np.all(np.abs(tot) < (1e-14 if precision == "fp64" else 1e-7) * scale), tot / scale
 
 
+@pytest.mark.parametrize("n,cross", [(5000, False), (16384, False), (5000, True), (9000, True)])
+def test_symmetric_wmax_prepass_is_bit_identical(n, cross):
+    """The prepass of the Newtonian pass that feeds a gradient, max_j m_j / r^3, with each pair
+    once (one set, or two disjoint lists at once: r^2 is symmetric bit for bit and the maximum
+    does not depend on the order): frost_accel_gradient gives the same a, a~ and g, bit for
+    bit, as with the one-sided prepasses (Kroupa masses, so the dominant terms and slots
+    differ between particles)."""
+    m, x, v = ics.plummer(n, 50 + n % 7, masses=ics.kroupa_masses(n, 50 + n % 7))
+    if cross:
+        perm = np.random.default_rng(n).permutation(n).astype(np.int32)
+        A, B = np.sort(perm[: n // 3]), perm[n // 3:]
+    else:
+        A = B = None
+    out = {}
+    for sc in (1, -1):
+        f = F(m, x, v, precision="mixed", sym_cross=sc)
+        o = f.accel_gradient(A, B, eps_grad=2.0 ** -7)
+        out[sc] = {k: cpu(t) for k, t in o.items()}
+        f.close()
+    for k in out[1]:
+        assert np.array_equal(out[1][k], out[-1][k]), k
+
+
 def test_accel_pairwise_rejects_overlapping_lists():
     from paper_2011_14984_gb300 import frost as fr
     m, x, v = ics.plummer(100, 3)

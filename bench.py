@@ -240,7 +240,7 @@ def method_pairs(st):
     S has not moved), plus the second side of every pair of a symmetric S x F pass (one
     evaluation serves both interactions); the evaluated count alone is reported beside it."""
     return float(st["acc_pairs"] + st.get("acc_pairs_reused", 0) + st.get("acc_pairs_symmetric", 0)
-                 + st["grad_pairs"])
+                 + st["grad_pairs"] + st.get("grad_pairs_symmetric", 0))
 
 
 def subtree_rate(st, fp32_peak, probe):
@@ -496,9 +496,15 @@ def run_frost(args):
                 "value_evaluated": evaluated / (ms_max * 1e-3),
                 "interactions": {"method": interactions, "evaluated": evaluated,
                                  "reused_acc_pairs": int(st.get("acc_pairs_reused", 0)),
+                                 "symmetric_second_side_pairs": int(st.get("acc_pairs_symmetric", 0)
+                                                                    + st.get("grad_pairs_symmetric", 0)),
                                  "note": "value counts the method's acc+gradient pairs; the "
                                          "reused ones are the first Newtonian pass of each "
-                                         "second fsi(S), taken bit for bit from the first"},
+                                         "second fsi(S), taken bit for bit from the first; "
+                                         "the symmetric second side is the F-side interaction "
+                                         "of an S x F pair (Newtonian or gradient) evaluated "
+                                         "once for both particles, counted in method, not in "
+                                         "evaluated"},
                 "hhs_calls": st["hhs_calls"], "subtree_launches": st["subtree_launches"],
                 "subtree_ms": st_ev["timed_ms"][3],
                 "subtree": subtree_rate(st_ev, fp32_peak, probe),

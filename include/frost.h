@@ -83,14 +83,15 @@ typedef struct {
                                (they act on disjoint particles, so the results are those of the
                                serial order, bit for bit); -1: everything on the context stream.
                                With per-kernel timing on, the branches run serially. */
-    int32_t sym_cross;      /* 0 (default): the Newtonian kick_sf of a hierarchy level
-                               evaluates each S x F pair once for both sides (see
-                               frost_accel_pairwise) where that grid fills the GPU, else two
-                               one-sided passes on two streams; and, in the mixed mode, the
-                               time-step pass of a set of at least 8192 particles evaluates each
-                               pair once for both particles (the same result bits: the pair
-                               criteria are symmetric and a minimum does not depend on the
-                               order).  1: both always; -1: never */
+    int32_t sym_cross;      /* 0 (default): the kick_sf passes of a hierarchy level evaluate
+                               each S x F pair once for both sides where that grid fills the
+                               GPU, else two one-sided passes on two streams: the Newtonian
+                               kicks (see frost_accel_pairwise) and, in the mixed mode, the
+                               force-gradient kick (see frost_accel_gradient_pairwise); and, in
+                               the mixed mode, the time-step pass of a set of at least 8192
+                               particles evaluates each pair once for both particles (the same
+                               result bits: the pair criteria are symmetric and a minimum does
+                               not depend on the order).  1: all always; -1: never */
 } frost_opts;
 
 typedef enum {
@@ -192,6 +193,28 @@ frost_status frost_accel_pairwise(frost_ctx *ctx, const int32_t *a, int64_t n_a,
                                   int64_t n_b, double *acc_a, double *acc_b);
 
 /*
+ * The force-gradient kick between two disjoint sets, both lines of Eqs.
+ * force-gradient-inter-1/2 (the 2 tau/3 kick_sf of Algorithm hhs-fsi): the Newtonian
+ * accelerations of each set due to the other (Eq. force-newton-inter), then the gradient of
+ * each set against the other with those accelerations,
+ *   g_i = 2G sum_{j in b} m_j r^-5 (r^2 a_ji - 3 (x_ji . a_ji) x_ji),  a_ji = a_j - a_i,
+ * and a~ = a + eps_grad^2 / 48 g, for i in a (a_i due to b, a_j due to a) and likewise for b.
+ * Mixed mode: every pair is evaluated once for both sets, in both passes (a pair's term for
+ * b is the term for a with the other mass and the opposite sign, Sec. 3.3); each side keeps
+ * its dominant terms (above 1/16 of its max m / r^3) out of the FP32 sums and evaluates them
+ * in double-float, as frost_accel_gradient does, with no limit on their number for the set
+ * summed by the reduction; sums are in a fixed order, so results are deterministic.  With
+ * frost_opts.sym_cross = -1, and in FP64 mode, two one-sided passes per kind.  a, b: device
+ * int32 lists (or NULL = identity) of n_a and n_b indices with no index in both (else
+ * FROST_EINVAL); outputs: device [n][3] doubles, each may be NULL.  Softened like
+ * frost_accel_gradient.  Accuracy: as frost_accel_gradient.  Synchronises.
+ */
+frost_status frost_accel_gradient_pairwise(frost_ctx *ctx, const int32_t *a, int64_t n_a, const int32_t *b,
+                                           int64_t n_b, double eps_grad, double *acc_a, double *acc_b,
+                                           double *acc_tilde_a, double *acc_tilde_b, double *grad_a,
+                                           double *grad_b);
+
+/*
  * Symmetrised time-steps of the members of `set` (device list or NULL), Sec. 4:
  *   tau[k] = min_{j in set, j != i} min( s(eta dt_ff/dt) eta t_ff, s(eta dt_fb/dt) eta t_fb )
  * with t_ff = (r^3 / (G (m_i + m_j)))^(1/2), t_fb = r / |v_ij|, their time derivatives
@@ -273,6 +296,9 @@ typedef struct {
     /* Newtonian pairs evaluated once for both sides (symmetric S x F passes; counted once in
      * acc_pairs, and each served two interactions) */
     int64_t acc_pairs_symmetric;
+    /* gradient pairs evaluated once for both sides (symmetric gradient kick_sf; counted once
+     * in grad_pairs, and each served two interactions) */
+    int64_t grad_pairs_symmetric;
 } frost_stats;
 
 frost_status frost_get_stats(frost_ctx *ctx, frost_stats *out);

@@ -94,6 +94,12 @@ constexpr int kBatchTeamBlocks = 8;
 // cross prepass
 constexpr int kSymTstepMinN = 8192;
 constexpr int64_t kSymCrossPrepassMinPairs = int64_t(1) << 26;
+// the symmetric force-gradient kick_sf in the default mode: for S x F up to this many pairs,
+// where one symmetric launch is faster than the two one-sided directions on two streams (on
+// 64k Plummer levels: 0.42 against 0.73 ms at 5212 x 917); at the top levels the symmetric
+// kernels execute about as many instructions per interaction as the one-sided ones (their
+// B-side reduction and dominant-term ballots cost what the saved pair bodies save)
+constexpr int64_t kSymGradMaxPairs = int64_t(1) << 23;
 
 // autotuner rows: the pass kinds, and the Newtonian pass that feeds a gradient (mixed mode:
 // its wmax prepass and deferred double-float terms give it a cost profile of its own)
@@ -170,6 +176,10 @@ struct frost_ctx {
     unsigned *jbest = nullptr;                       // j-side minima of the symmetric time-step pass
     double *pj = nullptr;                            // j-side partials of the symmetric pass
     size_t pj_elems = 0;
+    double *part_hot2 = nullptr;                     // B-side hot-source partials of the
+                                                     // symmetric gradient pass
+    uint8_t *pcnt = nullptr;                         // B-side slot counts of the symmetric
+                                                     // gradient kick_sf passes
     int sym_cross = 0;                               // symmetric S x F Newtonian passes in kick_sf:
                                                      // 0 where they fill the GPU, 1 always, -1 never
     Lane main;                                       // the context stream and the buffers above
@@ -666,17 +676,17 @@ void fsi(frost_ctx *c, Lane &L, const int32_t *S, int nS, double dt, int cache =
 // once (Eq. force-newton-inter, both lines): outA (soa [3][nA]) and outB (soa [3][nB]), each
 // list's kick fused into its finalisation.  recA / recB hold the lists' position records.  The
 // longer list takes the register side, the shorter one the reduced side (its partials per
-// group of i-blocks are then fewer).  Returns false, issuing nothing, when the grid of the
-// symmetric kernel would not fill one wave of the GPU (small lists: the two one-sided passes,
-// on two streams, are then faster).
+// group of i-blocks are then fewer).  Returns false, issuing nothing, when even the finest
+// grid of the symmetric kernel (a tile per split) would not fill one wave of the GPU (small
+// lists: the two one-sided passes, on two streams, are then faster).
 bool pass_acc_sym(frost_ctx *c, Lane &L, const int32_t *A, int nA, const int32_t *B, int nB, double *outA,
                   double *outB, KickArgs kickA, KickArgs kickB, const void *recA, const void *recB, bool force = false)
 {
     if (nA <= 0 || nB <= 0) return false;
     const bool swap = nB > nA;
     const int ni = swap ? nB : nA, nj = swap ? nA : nB;
-    const SymShape sh = sym_shape(c->mixed, ni, nj, c->n_sm, c->part_elems, c->pj_elems);
-    if (!force && (long long)sh.ngroups * sh.nsplit < (long long)sh.blocks_per_wave) return false;
+    const SymShape sh = sym_shape(c->mixed ? SYM_ACC_MIXED : SYM_ACC_FP64, ni, nj, c->n_sm, c->part_elems, c->pj_elems);
+    if (!force && sh.max_blocks < (long long)sh.blocks_per_wave) return false;
     const int64_t pairs = (int64_t)nA * nB;
     {
         // the kernel delivers both interactions of every pair: its algorithmic work for the
@@ -691,6 +701,72 @@ bool pass_acc_sym(frost_ctx *c, Lane &L, const int32_t *A, int nA, const int32_t
     c->st.kernel_launches += 3;
     c->st.acc_pairs += pairs;
     c->st.acc_pairs_symmetric += pairs;
+    return true;
+}
+
+// The passes of the gradient kick_sf over two disjoint lists A and B with every pair once
+// (mixed mode; Eqs. force-newton-inter and force-gradient-inter-1/2, both lines): the
+// symmetric wmax prepass, the accurate Newtonian sums of both lists (into M.aA / M.aB, soa),
+// the hot sources of both (M.hA / M.hB), the gradient records, and both gradients, finalised
+// per list as a~ = a + eps_grad^2/48 g (at_soa, at_aos, g_aos per list, each may be NULL)
+// with the kicks kA / kB fused.  M.recA / M.recB hold the lists' position records on entry.
+// The longer list takes the register side.  Returns false, issuing nothing, unless its finest
+// grid fills one wave of the GPU or force is set.
+bool grad_pairwise_sym(frost_ctx *c, Lane &M, const int32_t *A, int nA, const int32_t *B, int nB, double eps_grad,
+                       double *atA_soa, double *atB_soa, double *atA_aos, double *atB_aos, double *gA_aos,
+                       double *gB_aos, KickArgs kA, KickArgs kB, bool force)
+{
+    if (!c->mixed || nA <= 0 || nB <= 0) return false;
+    const bool swap = nB > nA;
+    const int ni = swap ? nB : nA, nj = swap ? nA : nB;
+    const SymShape sa = sym_shape(SYM_ACC_DEFER, ni, nj, c->n_sm, c->part_elems, c->pj_elems);
+    if (!force && sa.max_blocks < (long long)sa.blocks_per_wave) return false;
+    const SymShape sg = sym_shape(SYM_GRAD, ni, nj, c->n_sm, c->part_elems, c->pj_elems);
+    const int64_t pairs = (int64_t)nA * nB;
+    const int32_t *Li = swap ? B : A, *Lj = swap ? A : B;
+    unsigned *h = zero_hists(M);
+    {
+        TimedScope ts(c, M.s, PASS_ACC, 0);
+        launch_wmax_sym_cross(M.s, M.recA, nA, M.recB, nB, c->eps2, c->n_sm, M.wA, M.wB);
+    }
+    {
+        TimedScope ts(c, M.s, PASS_ACC, 2 * pairs);
+        launch_acc_sym_defer(M.s, swap ? M.recB : M.recA, swap ? M.recA : M.recB, ni, nj, c->eps2,
+                             swap ? M.wB : M.wA, swap ? M.wA : M.wB, Li, Lj, c->m, M.part, c->pj, c->pcnt, sa);
+    }
+    launch_finalize_vec(M.s, M.part, sa.nsplit, ni, c->G, swap ? M.aB : M.aA, nullptr, &c->dmisc->err, badbit(c));
+    launch_finalize_vec(M.s, c->pj, sa.ngroups, nj, c->G, swap ? M.aA : M.aB, nullptr, &c->dmisc->err, badbit(c));
+    launch_acc_hist(M.s, M.aA, nA, h);
+    launch_acc_hist(M.s, M.aB, nB, h + HOT_BINS);
+    mark_hot(c, M, nA, nB, false, M.aA, h, h + HOT_BINS, nB, M.hA);
+    mark_hot(c, M, nB, nA, false, M.aB, h + HOT_BINS, h, nA, M.hB);
+    pack_grad(c, M, A, nA, M.aA, M.recA, M.hA);
+    pack_grad(c, M, B, nB, M.aB, M.recB, M.hB);
+    {
+        TimedScope ts(c, M.s, PASS_GRAD, 2 * pairs);
+        launch_grad_sym(M.s, swap ? M.recB : M.recA, swap ? M.recA : M.recB, ni, nj, c->eps2, swap ? M.wB : M.wA,
+                        swap ? M.wA : M.wB, M.part, c->pj, c->pcnt, sg);
+    }
+    // the double-float terms of the hot sources, per receiving list
+    int nsA = hot_grad_splits(nA, nB, c->n_sm), nsB = hot_grad_splits(nB, nA, c->n_sm);
+    while (nsA > 1 && (size_t)nsA * 3 * nA > c->part_hot_elems) --nsA;
+    while (nsB > 1 && (size_t)nsB * 3 * nB > c->part_hot_elems) --nsB;
+    launch_grad_hot(M.s, A, nA, M.aA, B, nB, M.aB, M.hB, 0, c->x, c->m, c->N, c->eps2, nsA, c->part_hot);
+    launch_grad_hot(M.s, B, nB, M.aB, A, nA, M.aA, M.hA, 0, c->x, c->m, c->N, c->eps2, nsB, c->part_hot2);
+    const double cgrad = eps_grad * eps_grad / 48.0;
+    const double *ph_i = swap ? c->part_hot2 : c->part_hot, *ph_j = swap ? c->part_hot : c->part_hot2;
+    const int ns_i = swap ? nsB : nsA, ns_j = swap ? nsA : nsB;
+    launch_finalize_grad(M.s, M.part, sg.nsplit, ni, 2.0 * c->G, swap ? M.aB : M.aA, cgrad, swap ? atB_soa : atA_soa,
+                         swap ? atB_aos : atA_aos, swap ? gB_aos : gA_aos, &c->dmisc->err, badbit(c), ph_i, ns_i,
+                         swap ? kB : kA);
+    launch_finalize_grad(M.s, c->pj, sg.ngroups, nj, 2.0 * c->G, swap ? M.aA : M.aB, cgrad, swap ? atA_soa : atB_soa,
+                         swap ? atA_aos : atB_aos, swap ? gA_aos : gB_aos, &c->dmisc->err, badbit(c), ph_j, ns_j,
+                         swap ? kA : kB);
+    c->st.kernel_launches += 11;
+    c->st.acc_pairs += pairs;
+    c->st.acc_pairs_symmetric += pairs;
+    c->st.grad_pairs += pairs;
+    c->st.grad_pairs_symmetric += pairs;
     return true;
 }
 
@@ -752,6 +828,11 @@ void kick_sf(frost_ctx *c, Lane &M, Lane *Bl, const int32_t *S, int nS, const in
         pass_acc(c, X, F, nF, S, nS, false, M.aB, nullptr, nullptr, nullptr, kick_of(c, F, cdt), M.recB, M.recA);
         return;  // joined by br
     }
+    // each S x F pair once for both sides: always with sym_cross = 1, else for small lists
+    if (c->sym_cross >= 0 && (c->sym_cross > 0 || (int64_t)nS * nF <= kSymGradMaxPairs) &&
+        grad_pairwise_sym(c, M, S, nS, F, nF, tau_pivot, M.atA, M.atB, nullptr, nullptr, nullptr, nullptr,
+                          kick_of(c, S, cdt), kick_of(c, F, cdt), true))
+        return;
     unsigned *h = c->mixed ? zero_hists(M) : nullptr;
     // the prepasses of both accurate passes in one symmetric kernel (each pair once), where
     // the lists are large
@@ -986,7 +1067,7 @@ void destroy(frost_ctx *c)
     if (c->d_ecl) cudaFree(c->d_ecl);
     void *dev[] = {c->x, c->v, c->m, c->all, c->marks, c->recA, c->recB, c->part,
                    c->aA, c->aB, c->atA, c->atB, c->aC, c->tau, c->wA, c->wB, c->perm,
-                   c->ptmp, c->dmisc, c->hist, c->hA, c->hB, c->part_hot, c->pj, c->jbest};
+                   c->ptmp, c->dmisc, c->hist, c->hA, c->hB, c->part_hot, c->part_hot2, c->pcnt, c->pj, c->jbest};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (c->hmisc) cudaFreeHost(c->hmisc);
@@ -1128,9 +1209,11 @@ static frost_status init_impl(frost_ctx **out, int64_t n, const double *m, const
         INIT_CUDA(cudaMalloc(&c->hA, sizeof(uint32_t) * words));
         INIT_CUDA(cudaMalloc(&c->hB, sizeof(uint32_t) * words));
         INIT_CUDA(cudaMalloc(&c->part_hot, sizeof(double) * c->part_hot_elems));
+        INIT_CUDA(cudaMalloc(&c->part_hot2, sizeof(double) * c->part_hot_elems));
     }
     c->pj_elems = 3 * 8 * N;
     INIT_CUDA(cudaMalloc(&c->pj, sizeof(double) * c->pj_elems));
+    if (c->mixed) INIT_CUDA(cudaMalloc(&c->pcnt, (c->pj_elems / 3) * SYM_PCNT_WARPS));
     INIT_CUDA(cudaMalloc(&c->jbest, sizeof(unsigned) * N));
     INIT_CUDA(cudaMalloc(&c->perm, sizeof(int32_t) * N));
     INIT_CUDA(cudaMalloc(&c->ptmp, sizeof(int32_t) * N));
@@ -1317,6 +1400,58 @@ frost_status frost_accel_pairwise(frost_ctx *c, const int32_t *a, int64_t n_a, c
     } else {
         if (acc_a && nA > 0) FROST_CUDA(cudaMemsetAsync(acc_a, 0, sizeof(double) * 3 * nA, c->stream));
         if (acc_b && nB > 0) FROST_CUDA(cudaMemsetAsync(acc_b, 0, sizeof(double) * 3 * nB, c->stream));
+    }
+    FROST_CUDA(cudaGetLastError());
+    return sync_misc(c);
+}
+
+frost_status frost_accel_gradient_pairwise(frost_ctx *c, const int32_t *a, int64_t n_a, const int32_t *b,
+                                           int64_t n_b, double eps_grad, double *acc_a, double *acc_b,
+                                           double *acc_tilde_a, double *acc_tilde_b, double *grad_a, double *grad_b)
+{
+    if (!c) return fail(FROST_EINVAL, "NULL context");
+    FROST_TRY(check_sizes(c, n_a, "n_a"));
+    FROST_TRY(check_sizes(c, n_b, "n_b"));
+    const int nA = (int)n_a, nB = (int)n_b;
+    const int32_t *A = a ? a : c->all;
+    const int32_t *B = b ? b : c->all;
+    launch_list_relation(c->stream, A, nA, B, nB, c->N, c->marks, c->dmisc->rel);
+    FROST_TRY(sync_misc(c));
+    if (c->hmisc->rel[0]) return fail(FROST_EINVAL, "index list has an out-of-range or repeated index");
+    if (c->hmisc->rel[1] != 0) return fail(FROST_EINVAL, "the two lists share %lld particles", (long long)c->hmisc->rel[1]);
+    Lane &M = c->main;
+    if (nA > 0 && nB > 0) {
+        pack_pos(c, M, A, nA, M.recA);
+        pack_pos(c, M, B, nB, M.recB);
+        const bool sym = c->sym_cross >= 0 &&
+                         grad_pairwise_sym(c, M, A, nA, B, nB, eps_grad, nullptr, nullptr, acc_tilde_a, acc_tilde_b,
+                                           grad_a, grad_b, KickArgs(), KickArgs(), true);
+        if (!sym) {
+            // two one-sided passes per kind, in the order of kick_sf
+            unsigned *h = c->mixed ? zero_hists(M) : nullptr;
+            pass_acc(c, M, A, nA, B, nB, false, M.aA, nullptr, M.wA, h, KickArgs(), M.recA, M.recB);
+            pass_acc(c, M, B, nB, A, nA, false, M.aB, nullptr, M.wB, h ? h + HOT_BINS : nullptr, KickArgs(), M.recB,
+                     M.recA);
+            if (h) {
+                mark_hot(c, M, nA, nB, false, M.aA, h, h + HOT_BINS, nB, M.hA);
+                mark_hot(c, M, nB, nA, false, M.aB, h + HOT_BINS, h, nA, M.hB);
+            }
+            pack_grad(c, M, A, nA, M.aA, M.recA, c->mixed ? M.hA : nullptr);
+            pack_grad(c, M, B, nB, M.aB, M.recB, c->mixed ? M.hB : nullptr);
+            pass_grad(c, M, A, nA, M.aA, B, nB, M.aB, false, eps_grad, nullptr, acc_tilde_a, grad_a, M.wA, M.hB,
+                      KickArgs(), M.recA, M.recB);
+            pass_grad(c, M, B, nB, M.aB, A, nA, M.aA, false, eps_grad, nullptr, acc_tilde_b, grad_b, M.wB, M.hA,
+                      KickArgs(), M.recB, M.recA);
+        }
+        if (acc_a) launch_soa_to_aos(c->stream, M.aA, nA, acc_a);
+        if (acc_b) launch_soa_to_aos(c->stream, M.aB, nB, acc_b);
+    } else {
+        double *outs[] = {acc_a, acc_tilde_a, grad_a};
+        for (double *o : outs)
+            if (o && nA > 0) FROST_CUDA(cudaMemsetAsync(o, 0, sizeof(double) * 3 * nA, c->stream));
+        double *outsb[] = {acc_b, acc_tilde_b, grad_b};
+        for (double *o : outsb)
+            if (o && nB > 0) FROST_CUDA(cudaMemsetAsync(o, 0, sizeof(double) * 3 * nB, c->stream));
     }
     FROST_CUDA(cudaGetLastError());
     return sync_misc(c);

@@ -207,11 +207,28 @@ struct SymShape {
     int nsplit = 1;        // blocks along B
     int j_per_split = 0;   // sources per split (a multiple of the tile)
     int blocks_per_wave = 1;
+    long long max_blocks = 1;  // the largest grid the lists allow (one tile per split)
 };
+// the symmetric cross kernels (their occupancies differ)
+enum { SYM_ACC_MIXED = 0, SYM_ACC_FP64 = 1, SYM_ACC_DEFER = 2, SYM_GRAD = 3, SYM_KINDS = 4 };
 // part_elems / pj_elems: the capacities of part and pj in doubles
-SymShape sym_shape(bool mixed, int n_a, int n_s, int n_sm, size_t part_elems, size_t pj_elems);
+SymShape sym_shape(int kind, int n_a, int n_s, int n_sm, size_t part_elems, size_t pj_elems);
 void launch_acc_sym(cudaStream_t s, bool mixed, const void *irec, const void *jrec, int n_a, int n_s, double eps2,
                     double *part, double *pj, const SymShape &sh);
+
+// Symmetric passes of the gradient kick_sf (mixed): both lists' accurate Newtonian sums with
+// their dominant terms in double-float (wA, wB: max_j m_j / r^3 of each list against the other;
+// ilist, jlist: the lists' particle indices for the FP64 masses mstore, NULL = identity), then
+// both gradients (records of launch_pack_grad_mixed, hot sources with zero mass).  part: the
+// A side per split as launch_acc / launch_grad; pj: the B side per group with the receiver's
+// sign (sum_i of the terms of j due to i).
+// pcnt: [ngroups][SYM_PCNT_WARPS][n_s] bytes of scratch (the B side's slot counts).
+constexpr int SYM_PCNT_WARPS = 4;
+void launch_acc_sym_defer(cudaStream_t s, const void *irec, const void *jrec, int n_a, int n_s, double eps2,
+                          const float *wA, const float *wB, const int32_t *ilist, const int32_t *jlist,
+                          const double *mstore, double *part, double *pj, uint8_t *pcnt, const SymShape &sh);
+void launch_grad_sym(cudaStream_t s, const void *irec, const void *jrec, int n_a, int n_s, double eps2,
+                     const float *wA, const float *wB, double *part, double *pj, uint8_t *pcnt, const SymShape &sh);
 
 // Symmetric time-step pass over one set (mixed): every pair once, tau[i] written directly.
 // jbest: [n] unsigned scratch (the j-side minima as FP32 bits); part: [blocks of row 0][n].

@@ -93,9 +93,10 @@ __global__ void k_pack_noalloc(const double *__restrict__ x, const double *__res
     if (!isfinite(px) || !isfinite(py) || !isfinite(pz) || !(mk > 0.0) || !isfinite(mk))
         atomicOr(err, ERR_NONFINITE);
     const float hx = (float)px, hy = (float)py, hz = (float)pz;
-    rec[k] = make_float4(hx, hy, hz, (float)mk);
+    const float mh = (float)mk;
+    rec[k] = make_float4(hx, hy, hz, mh);
     rec[n + k] = make_float4((float)(px - (double)hx), (float)(py - (double)hy),
-                             (float)(pz - (double)hz), 0.f);
+                             (float)(pz - (double)hz), (float)(mk - (double)mh));
 }
 
 }  // namespace

@@ -56,9 +56,12 @@ __device__ __forceinline__ void pack_pos_mixed_one(int k, const int32_t *__restr
     const int i = list ? list[k] : k;
     const double px = x[i], py = x[N + i], pz = x[2 * N + i];
     const float hx = (float)px, hy = (float)py, hz = (float)pz;
-    rec[k] = make_float4(hx, hy, hz, (float)m[i]);
+    const double mi = m[i];
+    const float mh = (float)mi;
+    rec[k] = make_float4(hx, hy, hz, mh);
+    // the low part of the mass completes its double-float (the dominant terms' weights)
     rec[n + k] = make_float4((float)(px - (double)hx), (float)(py - (double)hy),
-                             (float)(pz - (double)hz), 0.f);
+                             (float)(pz - (double)hz), (float)(mi - (double)mh));
 }
 
 // acc may be NULL (positions only, for the Newtonian pass that precedes the gradient)
@@ -302,6 +305,57 @@ static __device__ __noinline__ D3 acc_term_df(const float4 J0, const float4 J1, 
     return r;
 }
 
+// A pair term in double-float, and sums of such terms.  The per-thread slot loops add the
+// deferred terms of a particle in double-float and convert once: FP64 issues at 1/64 of the
+// FP32 rate on this part, and a double per term (its conversions and additions) cost as much
+// as the double-float arithmetic itself.
+struct DF3 {
+    df::dfloat x, y, z;
+};
+
+__device__ __forceinline__ DF3 df3_zero()
+{
+    DF3 r;
+    r.x.h = r.x.l = r.y.h = r.y.l = r.z.h = r.z.l = 0.f;
+    return r;
+}
+
+__device__ __forceinline__ void df3_add(DF3 &a, const DF3 &t)
+{
+    a.x = df::add(a.x, t.x);
+    a.y = df::add(a.y, t.y);
+    a.z = df::add(a.z, t.z);
+}
+
+__device__ __forceinline__ bool df3_finite(const DF3 &t)
+{
+    return isfinite(t.x.h) && isfinite(t.y.h) && isfinite(t.z.h) && isfinite(t.x.l) && isfinite(t.y.l) &&
+           isfinite(t.z.l);
+}
+
+// acc_term_df on position records that carry the double-float mass ({J0.w, J1.w}, the split
+// of the FP64 mass that from_double makes) and with the softening as a double-float: no FP64
+// instruction.  Returns false when the term leaves the FP32 range (the caller then takes
+// acc_term_fp64).
+static __device__ __noinline__ bool acc_term_df3(const float4 J0, const float4 J1, float ixh, float iyh, float izh,
+                                                 float ixl, float iyl, float izl, df::dfloat e2, DF3 &t)
+{
+    using df::dfloat;
+    const dfloat dx = df::sub(df::make(J0.x, J1.x), df::make(ixh, ixl));
+    const dfloat dy = df::sub(df::make(J0.y, J1.y), df::make(iyh, iyl));
+    const dfloat dz = df::sub(df::make(J0.z, J1.z), df::make(izh, izl));
+    const dfloat r2 = df::add(df::add(df::mul(dx, dx), df::mul(dy, dy)), df::add(df::mul(dz, dz), e2));
+    const dfloat ri = df::rsqrt(r2);
+    dfloat mj;
+    mj.h = J0.w;
+    mj.l = J1.w;
+    const dfloat w = df::mul(df::mul(df::mul(ri, ri), ri), mj);
+    t.x = df::mul(w, dx);
+    t.y = df::mul(w, dy);
+    t.z = df::mul(w, dz);
+    return df3_finite(t);
+}
+
 template <int ILP>
 struct AccMixedI {
     float xh[ILP], yh[ILP], zh[ILP], xl[ILP], yl[ILP], zl[ILP];
@@ -459,6 +513,31 @@ __device__ __noinline__ void grad_term_df(const float4 J0, const float4 J1, cons
     } else {
         grad_term_fp64<ILP>(J0, J1, J2, J3, I, k, eps2, gx, gy, gz);
     }
+}
+
+// grad_term_df with the softening as a double-float and the result as one (no FP64
+// instruction); false when the term leaves the FP32 range (the caller takes grad_term_fp64)
+template <int ILP>
+__device__ __noinline__ bool grad_term_df3(const float4 J0, const float4 J1, const float4 J2, const float4 J3,
+                                           const GradMixedI<ILP> &I, int k, df::dfloat e2, DF3 &t)
+{
+    using df::dfloat;
+    const dfloat dx = df::sep(J0.x, J1.x, J2.x, I.xh[k], I.xm[k], I.xl[k]);
+    const dfloat dy = df::sep(J0.y, J1.y, J2.y, I.yh[k], I.ym[k], I.yl[k]);
+    const dfloat dz = df::sep(J0.z, J1.z, J2.z, I.zh[k], I.zm[k], I.zl[k]);
+    const dfloat Ax = df::sub(df::make(J1.w, J3.y), df::make(I.ahx[k], I.alx[k]));
+    const dfloat Ay = df::sub(df::make(J2.w, J3.z), df::make(I.ahy[k], I.aly[k]));
+    const dfloat Az = df::sub(df::make(J3.x, J3.w), df::make(I.ahz[k], I.alz[k]));
+    const dfloat r2 = df::add(df::add(df::mul(dx, dx), df::mul(dy, dy)), df::add(df::mul(dz, dz), e2));
+    const dfloat ri = df::rsqrt(r2);
+    const dfloat ri2 = df::mul(ri, ri);
+    const dfloat w = df::mul_f(df::mul(ri2, ri), J0.w);
+    const dfloat xa = df::add(df::add(df::mul(dx, Ax), df::mul(dy, Ay)), df::mul(dz, Az));
+    const dfloat t3 = df::mul(df::mul_f(xa, 3.f), ri2);
+    t.x = df::mul(w, df::sub(Ax, df::mul(t3, dx)));
+    t.y = df::mul(w, df::sub(Ay, df::mul(t3, dy)));
+    t.z = df::mul(w, df::sub(Az, df::mul(t3, dz)));
+    return df3_finite(t);
 }
 
 template <int ILP, bool MASK, class Slots>
@@ -1059,21 +1138,34 @@ __device__ __forceinline__ void acc_mixed_body(const float4 *__restrict__ irec,
             return acc_term_df(jrec[j], jrec[n_s + j], a.x, a.y, a.z, b.x, b.y, b.z, mj, eps2d);
         });
     } else if constexpr (DEFER) {
-        // deferred double-float terms, per thread; records read back from global memory (L2)
+        // deferred double-float terms, per thread, summed in double-float; records read back
+        // from global memory (L2)
+        const df::dfloat e2 = df::from_double(eps2d);
 #pragma unroll
-        for (int k = 0; k < ILP; ++k)
+        for (int k = 0; k < ILP; ++k) {
+            DF3 b = df3_zero();
+            double f[3] = {0.0, 0.0, 0.0};
 #pragma unroll
             for (int s = 0; s < GRAD_SLOTS; ++s) {
                 if (s < big.n[k]) {
                     const int j = big.get(s, k);
-                    const double mj = mstore[jlist ? jlist[j] : j];
-                    const D3 t = acc_term_df(jrec[j], jrec[n_s + j], I.xh[k], I.yh[k], I.zh[k], I.xl[k], I.yl[k],
-                                             I.zl[k], mj, eps2d);
-                    res[k][0] += t.x;
-                    res[k][1] += t.y;
-                    res[k][2] += t.z;
+                    const float4 J0 = jrec[j], J1 = jrec[n_s + j];
+                    DF3 t;
+                    if (acc_term_df3(J0, J1, I.xh[k], I.yh[k], I.zh[k], I.xl[k], I.yl[k], I.zl[k], e2, t)) {
+                        df3_add(b, t);
+                    } else {
+                        const D3 u = acc_term_fp64(J0, J1, I.xh[k], I.yh[k], I.zh[k], I.xl[k], I.yl[k], I.zl[k],
+                                                   mstore[jlist ? jlist[j] : j], eps2d);
+                        f[0] += u.x;
+                        f[1] += u.y;
+                        f[2] += u.z;
+                    }
                 }
             }
+            res[k][0] += df::to_double(b.x) + f[0];
+            res[k][1] += df::to_double(b.y) + f[1];
+            res[k][2] += df::to_double(b.z) + f[2];
+        }
     }
 }
 
@@ -1360,21 +1452,25 @@ __device__ __forceinline__ void grad_mixed_body(const float4 *__restrict__ irec,
             res[k][2] = ((double)hz[k] + (double)lz[k]) + b[k][2];
         }
     } else {
-        // per thread
+        // per thread, summed in double-float
+        const df::dfloat e2 = df::from_double(eps2d);
 #pragma unroll
         for (int k = 0; k < ILP; ++k) {
-            double bx = 0.0, by = 0.0, bz = 0.0;
+            DF3 b = df3_zero();
+            double f[3] = {0.0, 0.0, 0.0};
 #pragma unroll
             for (int s = 0; s < GRAD_SLOTS; ++s) {
                 if (s < big.n[k]) {
                     const int j = big.get(s, k);
-                    grad_term_df<ILP>(jrec[j], jrec[n_s + j], jrec[2 * n_s + j], jrec[3 * n_s + j], I, k, eps2d,
-                                      bx, by, bz);
+                    const float4 J0 = jrec[j], J1 = jrec[n_s + j], J2 = jrec[2 * n_s + j], J3 = jrec[3 * n_s + j];
+                    DF3 t;
+                    if (grad_term_df3<ILP>(J0, J1, J2, J3, I, k, e2, t)) df3_add(b, t);
+                    else grad_term_fp64<ILP>(J0, J1, J2, J3, I, k, eps2d, f[0], f[1], f[2]);
                 }
             }
-            res[k][0] = ((double)hx[k] + (double)lx[k]) + bx;
-            res[k][1] = ((double)hy[k] + (double)ly[k]) + by;
-            res[k][2] = ((double)hz[k] + (double)lz[k]) + bz;
+            res[k][0] = ((double)hx[k] + (double)lx[k]) + (df::to_double(b.x) + f[0]);
+            res[k][1] = ((double)hy[k] + (double)ly[k]) + (df::to_double(b.y) + f[1]);
+            res[k][2] = ((double)hz[k] + (double)lz[k]) + (df::to_double(b.z) + f[2]);
         }
     }
 }

@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(BS) k_wmax_mixed(const float4 *__restrict__ ir
 }
 
 template <int BS, int ILP, int TJ>
-__global__ void __launch_bounds__(BS) k_grad_mixed(const float4 *__restrict__ irec,
+__global__ void __launch_bounds__(BS, 512 / BS) k_grad_mixed(const float4 *__restrict__ irec,
                                                    const float4 *__restrict__ jrec, int n_a,
                                                    int n_s, int j_per_split, int self_pass,
                                                    double eps2d, const float *__restrict__ wmax,

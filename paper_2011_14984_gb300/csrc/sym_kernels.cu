@@ -36,6 +36,11 @@ constexpr int SYM_WARPS = SYM_BS / 32;
 // a stand-in for the sources past the end of a tile: zero mass, far from every particle
 // (its r^-3 flushes to zero, so it adds nothing to either side)
 constexpr float SYM_FAR = 1.0e15f;
+// double-float slots of the reduced (B) side of the symmetric gradient kick_sf passes, per
+// (source, group of i-blocks, warp): 8 per source and group, as the 8 slots per particle and
+// split of the one-sided passes
+constexpr int SYM_BSLOTS = 2;
+static_assert(SYM_WARPS == SYM_PCNT_WARPS, "pcnt is sized for SYM_PCNT_WARPS warps a block");
 
 // warp reduce-scatter of v[8] (8 sources): returns on lane l the warp sum of source
 // (l >> 2) & 7; the order of the additions is fixed
@@ -63,6 +68,26 @@ __device__ __forceinline__ T reduce_scatter8(const T (&v)[8], int lane)
     c3 = c3 + __shfl_xor_sync(0xffffffffu, c3, 2);
     c3 = c3 + __shfl_xor_sync(0xffffffffu, c3, 1);
     return c3;
+}
+
+// the same for v[4] (4 sources): returns on lane l the warp sum of source (l >> 3) & 3
+template <class T>
+__device__ __forceinline__ T reduce_scatter4(const T (&v)[4], int lane)
+{
+    const bool b4 = lane & 16, b3 = lane & 8;
+    T c1[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const T send = b4 ? v[k] : v[2 + k];
+        const T keep = b4 ? v[2 + k] : v[k];
+        c1[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    const T send = b3 ? c1[0] : c1[1];
+    const T keep = b3 ? c1[1] : c1[0];
+    T c2 = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    c2 = c2 + __shfl_xor_sync(0xffffffffu, c2, 4);
+    c2 = c2 + __shfl_xor_sync(0xffffffffu, c2, 2);
+    return c2 + __shfl_xor_sync(0xffffffffu, c2, 1);
 }
 
 // One source (staged duplicated as in acc_x2_j) against the thread's two particles: the
@@ -270,6 +295,19 @@ __global__ void __launch_bounds__(BS) k_acc_sym_fp64(const double4_32a *__restri
     }
 }
 
+template <int BS, int TJ>
+__global__ void k_acc_sym_defer_mixed(const float4 *__restrict__ irec, const float4 *__restrict__ jrec, int n_a,
+                                      int n_s, int nblk_i, int j_per_split, float eps2, double eps2d,
+                                      const float *__restrict__ wA, const float *__restrict__ wB,
+                                      const int32_t *__restrict__ ilist, const int32_t *__restrict__ jlist,
+                                      const double *__restrict__ mstore, double *__restrict__ part,
+                                      double *__restrict__ pj, uint8_t *__restrict__ pcnt);
+template <int BS, int TJ>
+__global__ void k_grad_sym_mixed(const float4 *__restrict__ irec, const float4 *__restrict__ jrec, int n_a, int n_s,
+                                 int nblk_i, int j_per_split, double eps2d, const float *__restrict__ wA,
+                                 const float *__restrict__ wB, double *__restrict__ part, double *__restrict__ pj,
+                                 uint8_t *__restrict__ pcnt);
+
 template <typename K>
 int sym_occupancy(K kernel)
 {
@@ -283,28 +321,48 @@ int sym_occupancy(K kernel)
 
 }  // namespace
 
-SymShape sym_shape(bool mixed, int n_a, int n_s, int n_sm, size_t part_elems, size_t pj_elems)
+SymShape sym_shape(int kind, int n_a, int n_s, int n_sm, size_t part_elems, size_t pj_elems)
 {
-    static int occ[2] = {0, 0};
-    int &o = occ[mixed ? 1 : 0];
-    if (!o) o = mixed ? sym_occupancy(k_acc_sym_mixed<SYM_BS, SYM_TJ>) : sym_occupancy(k_acc_sym_fp64<SYM_BS, SYM_TJ>);
+    static int occ[SYM_KINDS] = {0, 0, 0, 0};
+    int &o = occ[kind];
+    if (!o) {
+        switch (kind) {
+        case SYM_ACC_FP64: o = sym_occupancy(k_acc_sym_fp64<SYM_BS, SYM_TJ>); break;
+        case SYM_ACC_DEFER: o = sym_occupancy(k_acc_sym_defer_mixed<SYM_BS, SYM_TJ>); break;
+        case SYM_GRAD: o = sym_occupancy(k_grad_sym_mixed<SYM_BS, SYM_TJ>); break;
+        default: o = sym_occupancy(k_acc_sym_mixed<SYM_BS, SYM_TJ>); break;
+        }
+    }
     SymShape sh;
-    const int ipb = mixed ? 2 * SYM_BS : SYM_BS;
+    const int ipb = (kind == SYM_ACC_FP64) ? SYM_BS : 2 * SYM_BS;
     sh.nblk_i = std::max(1, (n_a + ipb - 1) / ipb);
     const long long max_groups = std::max<long long>(1, (long long)(pj_elems / (3 * (size_t)std::max(n_s, 1))));
     const int per = (int)((sh.nblk_i + std::min<long long>(max_groups, 64) - 1) / std::min<long long>(max_groups, 64));
     sh.ngroups = (sh.nblk_i + per - 1) / per;
-    // about four waves of blocks; each split at least one tile, partials within their buffer
+    // The split count: every block takes the same number of i-blocks, so its time is about
+    // its tiles per split, and the last wave of blocks takes as long as a full one.  The
+    // count minimises waves x (tiles per block + a quarter tile of fixed work), with the
+    // partials within their buffer; among equal costs the fewest splits.
     const long long cap = (long long)o * n_sm;
     const int tiles = (n_s + SYM_TJ - 1) / SYM_TJ;
-    long long ns = (4 * cap + sh.ngroups - 1) / sh.ngroups;
-    ns = std::min<long long>(ns, tiles);
-    ns = std::min<long long>(ns, (long long)(part_elems / (3 * (size_t)std::max(n_a, 1))));
-    ns = std::max<long long>(ns, 1);
-    const int tps = (tiles + (int)ns - 1) / (int)ns;
-    sh.j_per_split = tps * SYM_TJ;
+    long long ns_max = std::min<long long>(tiles, (long long)(part_elems / (3 * (size_t)std::max(n_a, 1))));
+    ns_max = std::max<long long>(ns_max, 1);
+    long long best = -1;
+    int best_tps = tiles;
+    for (long long ns = 1; ns <= ns_max; ++ns) {
+        const int tps = (int)((tiles + ns - 1) / ns);
+        const long long nsplit = (tiles + tps - 1) / tps;
+        const long long waves = (sh.ngroups * nsplit + cap - 1) / cap;
+        const long long cost = waves * (4LL * tps + 1);
+        if (best < 0 || cost < best) {
+            best = cost;
+            best_tps = tps;
+        }
+    }
+    sh.j_per_split = best_tps * SYM_TJ;
     sh.nsplit = (n_s + sh.j_per_split - 1) / sh.j_per_split;
     sh.blocks_per_wave = (int)cap;
+    sh.max_blocks = (long long)sh.ngroups * ns_max;
     return sh;
 }
 
@@ -838,6 +896,589 @@ void launch_wmax_sym_cross(cudaStream_t s, const void *recA, int nA, const void 
     k_wmax_sym_cross<SYM_BS, SYM_TJ><<<grid, SYM_BS, 0, s>>>((const float4 *)(swap ? recB : recA),
                                                              (const float4 *)(swap ? recA : recB), ni, nj, jps,
                                                              (float)eps2, swap ? wB : wA, swap ? wA : wB);
+}
+
+}  // namespace frost
+
+// ======================================================================================
+// Symmetric passes of the gradient kick_sf (mixed precision): the Newtonian pass that feeds
+// the gradient and the gradient itself, for two disjoint lists A (the register side) and B
+// (the reduced side), each pair once for both lists (Eq. force-newton-inter and Eqs.
+// force-gradient-inter-1/2, both lines).  The B-side term of a pair is the A-side term with
+// the other mass and the opposite sign: x_ij = -x_ji, a_ij = -a_ji, and the gradient pair
+// term r^-3 (a - 3 (x.a) x / r^2) is odd in (x, a).  The work decomposition and the fixed-order
+// reduction of the B side are those of k_acc_sym_mixed; the B-side partials carry the
+// receiver's sign (pj = sum over i of the terms of j due to i), so both sides finalise alike.
+//
+// Dominant terms, per side as in the one-sided passes.  A pair whose weight m_j r^-3 exceeds
+// SLOT_FRACTION x wmax_i goes to one of i's deferred slots (up to GRAD_SLOTS a split); one
+// whose m_i r^-3 exceeds SLOT_FRACTION x wmax_j is deferred for j, up to SYM_BSLOTS per
+// (source, group, warp) in the order of the warp's ballots (their counts persist across the
+// group's i-blocks in pcnt).  A deferred side adds nothing to the FP32 sums and takes its term
+// in double-float: the A side after its split, per thread from the slots; the B side after
+// each tile, from the ballots of the deferred pairs, read in a fixed order (warp, particle
+// slot, lane) by the thread that owns the source.  So the B side is deterministic too.
+// ======================================================================================
+namespace frost {
+namespace {
+
+using namespace dev;
+
+// Staging of the B-side state of tile entry t (cnt live sources from j0) for every warp: the
+// warp's slots used so far for the source in this group (pcnt, zero on the group's first
+// i-block), its threshold (SLOT_FRACTION wmax_j while slots are left, else +inf, as for the
+// stand-ins past the end of the tile) and cleared ballot rows.
+__device__ __forceinline__ void stage_bside(float (*sT)[SYM_TJ], int (*sCnt)[SYM_TJ], unsigned (*sQ)[2][SYM_TJ],
+                                            const uint8_t *__restrict__ pcnt, int t, int cnt, int j0, int n_s, int g,
+                                            bool first, float tj)
+{
+#pragma unroll
+    for (int w = 0; w < SYM_WARPS; ++w) {
+        int used = SYM_BSLOTS;
+        if (t < cnt) used = first ? 0 : (int)pcnt[((size_t)g * SYM_WARPS + w) * n_s + j0 + t];
+        sCnt[w][t] = used;
+        sT[w][t] = (used < SYM_BSLOTS) ? tj : INFINITY;
+        sQ[w][0][t] = sQ[w][1][t] = 0u;
+    }
+}
+
+// The B side's dominant terms, per warp: at most SYM_BSLOTS of them for each (source, group
+// of the block, warp), the first candidates in the order (particle slot k, lane); the others
+// stay in the FP32 sums, as the candidates beyond a one-sided pass's slots do.  d0, d1: the
+// lane's candidates on entry, the deferred ones on return; cnt: the slots the warp has used
+// for this source (shared memory); q0, q1: the ballots of the deferred pairs.
+__device__ __forceinline__ void bside_defer(bool &d0, bool &d1, int *cnt, unsigned *q0, unsigned *q1, int lane)
+{
+    if (!__any_sync(0xffffffffu, d0 || d1)) return;
+    const unsigned m0 = __ballot_sync(0xffffffffu, d0), m1 = __ballot_sync(0xffffffffu, d1);
+    const int avail = SYM_BSLOTS - *cnt;
+    const unsigned lt = (1u << lane) - 1u;
+    d0 = d0 && (__popc(m0 & lt) < avail);
+    d1 = d1 && (__popc(m0) + __popc(m1 & lt) < avail);
+    const unsigned k0 = __ballot_sync(0xffffffffu, d0), k1 = __ballot_sync(0xffffffffu, d1);
+    if (lane == 0) {
+        *q0 = k0;
+        *q1 = k1;
+        *cnt += __popc(k0) + __popc(k1);
+    }
+    __syncwarp();
+}
+
+// The accurate Newtonian pair (Newton-refined rsqrt) of the thread's two particles with one
+// source staged as in acc_x2_j, plus its B side: c = -m_i r^-3 x_ji summed over the two
+// particles, the deferred pairs left out (thrj: the source's threshold for this warp).
+__device__ __forceinline__ void symdef_x2_j(const float4 A, const float4 B, const float4 C, const float2 M,
+                                            float thrj, const AccX2I &P, const float2 nmi, float2 e2, int jglob,
+                                            const float (&thr)[2], SmemSlots<2, SYM_BS> &big, float2 &ax,
+                                            float2 &ay, float2 &az, float &cx, float &cy, float &cz, int *cnt,
+                                            unsigned *q0, unsigned *q1, int lane)
+{
+    const float2 dx = __fadd2_rn(__fadd2_rn(make_float2(A.x, A.y), P.nxh), __fadd2_rn(make_float2(B.z, B.w), P.nxl));
+    const float2 dy = __fadd2_rn(__fadd2_rn(make_float2(A.z, A.w), P.nyh), __fadd2_rn(make_float2(C.x, C.y), P.nyl));
+    const float2 dz = __fadd2_rn(__fadd2_rn(make_float2(B.x, B.y), P.nzh), __fadd2_rn(make_float2(C.z, C.w), P.nzl));
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+    float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 nhy = __fmul2_rn(__fmul2_rn(make_float2(-0.5f, -0.5f), r2), ri);
+    ri = __ffma2_rn(ri, __ffma2_rn(nhy, ri, make_float2(0.5f, 0.5f)), ri);
+    const float2 u = __fmul2_rn(ri, __fmul2_rn(ri, ri));  // r^-3
+    float2 w = __fmul2_rn(M, u);                           // m_j r^-3
+    float2 wj = __fmul2_rn(nmi, u);                        // -m_i r^-3
+    if (__any_sync(0xffffffffu, (w.x > thr[0]) || (w.y > thr[1]))) {
+        const bool b0 = (w.x > thr[0]) && big.room(0);
+        if (b0) big.push(0, jglob);
+        const bool b1 = (w.y > thr[1]) && big.room(1);
+        if (b1) big.push(1, jglob);
+        w.x = b0 ? 0.f : w.x;
+        w.y = b1 ? 0.f : w.y;
+    }
+    ax = __ffma2_rn(w, dx, ax);
+    ay = __ffma2_rn(w, dy, ay);
+    az = __ffma2_rn(w, dz, az);
+    bool d0 = wj.x < -thrj, d1 = wj.y < -thrj;
+    bside_defer(d0, d1, cnt, q0, q1, lane);
+    wj.x = d0 ? 0.f : wj.x;
+    wj.y = d1 ? 0.f : wj.y;
+    cx = fmaf(wj.y, dx.y, wj.x * dx.x);
+    cy = fmaf(wj.y, dy.y, wj.x * dy.x);
+    cz = fmaf(wj.y, dz.y, wj.x * dz.x);
+}
+
+// The gradient pair of the thread's two particles with one source staged as in grad_x2_j,
+// plus its B side c = -m_i r^-3 (a_ji - 3 (x_ji . a_ji) x_ji / r^2) over the two particles.
+__device__ __forceinline__ void gradsym_x2_j(const float4 G0, const float4 G1, const float4 G2, const float4 G3,
+                                             const float4 G4, const float4 G5, const float4 G6, const float4 G7,
+                                             float thrj, const GradX2I &P, const float2 nmi, float2 e2, int jglob,
+                                             const float (&thr)[2], SmemSlots<2, SYM_BS> &big, float2 &gx,
+                                             float2 &gy, float2 &gz, float &cx, float &cy, float &cz, int *cnt,
+                                             unsigned *q0, unsigned *q1, int lane)
+{
+    const float2 dx = __fadd2_rn(__fadd2_rn(__fadd2_rn(make_float2(G0.x, G0.y), P.nxh),
+                                            __fadd2_rn(make_float2(G1.z, G1.w), P.nxm)),
+                                 __fadd2_rn(make_float2(G3.x, G3.y), P.nxl));
+    const float2 dy = __fadd2_rn(__fadd2_rn(__fadd2_rn(make_float2(G0.z, G0.w), P.nyh),
+                                            __fadd2_rn(make_float2(G2.x, G2.y), P.nym)),
+                                 __fadd2_rn(make_float2(G3.z, G3.w), P.nyl));
+    const float2 dz = __fadd2_rn(__fadd2_rn(__fadd2_rn(make_float2(G1.x, G1.y), P.nzh),
+                                            __fadd2_rn(make_float2(G2.z, G2.w), P.nzm)),
+                                 __fadd2_rn(make_float2(G4.x, G4.y), P.nzl));
+    const float2 Ax = __fadd2_rn(__fadd2_rn(make_float2(G4.z, G4.w), P.nahx), __fadd2_rn(make_float2(G6.x, G6.y), P.nalx));
+    const float2 Ay = __fadd2_rn(__fadd2_rn(make_float2(G5.x, G5.y), P.nahy), __fadd2_rn(make_float2(G6.z, G6.w), P.naly));
+    const float2 Az = __fadd2_rn(__fadd2_rn(make_float2(G5.z, G5.w), P.nahz), __fadd2_rn(make_float2(G7.x, G7.y), P.nalz));
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+    float2 y = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 nhy = __fmul2_rn(__fmul2_rn(make_float2(-0.5f, -0.5f), r2), y);
+    y = __ffma2_rn(y, __ffma2_rn(nhy, y, make_float2(0.5f, 0.5f)), y);
+    const float2 ri2 = __fmul2_rn(y, y);
+    const float2 u = __fmul2_rn(y, ri2);                             // r^-3
+    float2 w = __fmul2_rn(make_float2(G7.z, G7.w), u);               // m_j r^-3
+    float2 wj = __fmul2_rn(nmi, u);                                  // -m_i r^-3
+    const bool b0 = (w.x > thr[0]) && big.room(0);
+    if (b0) big.push(0, jglob);
+    const bool b1 = (w.y > thr[1]) && big.room(1);
+    if (b1) big.push(1, jglob);
+    w.x = b0 ? 0.f : w.x;
+    w.y = b1 ? 0.f : w.y;
+    const float2 xa = __ffma2_rn(dx, Ax, __ffma2_rn(dy, Ay, __fmul2_rn(dz, Az)));
+    const float2 nt3 = __fmul2_rn(__fmul2_rn(make_float2(-3.0f, -3.0f), xa), ri2);  // -3 (x.a) / r^2
+    const float2 tx = __ffma2_rn(nt3, dx, Ax), ty = __ffma2_rn(nt3, dy, Ay), tz = __ffma2_rn(nt3, dz, Az);
+    gx = __ffma2_rn(w, tx, gx);
+    gy = __ffma2_rn(w, ty, gy);
+    gz = __ffma2_rn(w, tz, gz);
+    bool d0 = wj.x < -thrj, d1 = wj.y < -thrj;
+    bside_defer(d0, d1, cnt, q0, q1, lane);
+    wj.x = d0 ? 0.f : wj.x;
+    wj.y = d1 ? 0.f : wj.y;
+    cx = fmaf(wj.y, tx.y, wj.x * tx.x);
+    cy = fmaf(wj.y, ty.y, wj.x * ty.x);
+    cz = fmaf(wj.y, tz.y, wj.x * tz.x);
+}
+
+template <int BS, int TJ>
+__global__ void __launch_bounds__(BS, 4) k_acc_sym_defer_mixed(const float4 *__restrict__ irec,
+                                                            const float4 *__restrict__ jrec, int n_a, int n_s,
+                                                            int nblk_i, int j_per_split, float eps2, double eps2d,
+                                                            const float *__restrict__ wA,
+                                                            const float *__restrict__ wB,
+                                                            const int32_t *__restrict__ ilist,
+                                                            const int32_t *__restrict__ jlist,
+                                                            const double *__restrict__ mstore,
+                                                            double *__restrict__ part, double *__restrict__ pj,
+                                                            uint8_t *__restrict__ pcnt)
+{
+    constexpr int ILP = 2, W = BS / 32, FOLD = 16;
+    static_assert(BS == SYM_BS && TJ == SYM_TJ, "slot columns and ballot rows are laid out for SYM_BS, SYM_TJ");
+    __shared__ float4 sA[TJ], sB[TJ], sC[TJ];
+    __shared__ float2 sM[TJ];
+    __shared__ float sT[W][TJ];
+    __shared__ int sCnt[W][TJ];
+    __shared__ float sJ[W][3][TJ];
+    __shared__ unsigned sQ[W][ILP][TJ];
+    __shared__ int s_slot[GRAD_SLOTS * ILP * BS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = blockIdx.x, ng = gridDim.x;
+    const int jb = blockIdx.y * j_per_split;
+    const int je = min(n_s, jb + j_per_split);
+    const float2 e2 = make_float2(eps2, eps2);
+    const df::dfloat e2d = df::from_double(eps2d);
+    for (int ib = g; ib < nblk_i; ib += ng) {
+        const int ibase = ib * BS * ILP;
+        // the thread's two particles; past the end: zero mass, far from every source
+        float4 a0 = make_float4(SYM_FAR, SYM_FAR, SYM_FAR, 0.f), a1 = a0, b0 = make_float4(0.f, 0.f, 0.f, 0.f), b1 = b0;
+        const int i0 = ibase + tid, i1 = ibase + BS + tid;
+        float thr[ILP] = {INFINITY, INFINITY};
+        if (i0 < n_a) {
+            a0 = irec[i0];
+            b0 = irec[n_a + i0];
+            thr[0] = SLOT_FRACTION * wA[i0];
+        }
+        if (i1 < n_a) {
+            a1 = irec[i1];
+            b1 = irec[n_a + i1];
+            thr[1] = SLOT_FRACTION * wA[i1];
+        }
+        AccX2I P;
+        P.nxh = make_float2(-a0.x, -a1.x);
+        P.nyh = make_float2(-a0.y, -a1.y);
+        P.nzh = make_float2(-a0.z, -a1.z);
+        P.nxl = make_float2(-b0.x, -b1.x);
+        P.nyl = make_float2(-b0.y, -b1.y);
+        P.nzl = make_float2(-b0.z, -b1.z);
+        const float2 nmi = make_float2(-a0.w, -a1.w);
+        SmemSlots<ILP, BS> big;
+        big.col = s_slot + tid;
+        big.n[0] = big.n[1] = 0;
+        float hx[ILP] = {0.f, 0.f}, hy[ILP] = {0.f, 0.f}, hz[ILP] = {0.f, 0.f};
+        float lx[ILP] = {0.f, 0.f}, ly[ILP] = {0.f, 0.f}, lz[ILP] = {0.f, 0.f};
+        for (int j0 = jb; j0 < je; j0 += TJ) {
+            const int cnt = min(TJ, je - j0);
+            const int cnt8 = (cnt + 7) & ~7;
+            __syncthreads();
+            for (int t = tid; t < cnt8; t += BS) {
+                float4 a = make_float4(-SYM_FAR, -SYM_FAR, -SYM_FAR, 0.f), b = make_float4(0.f, 0.f, 0.f, 0.f);
+                float tj = INFINITY;
+                if (t < cnt) {
+                    a = jrec[j0 + t];
+                    b = jrec[n_s + j0 + t];
+                    tj = SLOT_FRACTION * wB[j0 + t];
+                }
+                sA[t] = make_float4(a.x, a.x, a.y, a.y);
+                sB[t] = make_float4(a.z, a.z, b.x, b.x);
+                sC[t] = make_float4(b.y, b.y, b.z, b.z);
+                sM[t] = make_float2(a.w, a.w);
+                stage_bside(sT, sCnt, sQ, pcnt, t, cnt, j0, n_s, g, ib == g, tj);
+            }
+            __syncthreads();
+            for (int c0 = 0; c0 < cnt8; c0 += FOLD) {
+                const int c1 = min(cnt8, c0 + FOLD);
+                float2 ax2 = make_float2(0.f, 0.f), ay2 = ax2, az2 = ax2;
+                // groups of 4 sources (a reduce-scatter of 8 would hold 12 more registers)
+                for (int jj = c0; jj < c1; jj += 4) {
+                    float cx[4], cy[4], cz[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int sj = jj + u;
+                        symdef_x2_j(sA[sj], sB[sj], sC[sj], sM[sj], sT[warp][sj], P, nmi, e2, j0 + sj, thr, big, ax2,
+                                    ay2, az2, cx[u], cy[u], cz[u], &sCnt[warp][sj], &sQ[warp][0][sj], &sQ[warp][1][sj],
+                                    lane);
+                    }
+                    const float rx = reduce_scatter4(cx, lane);
+                    const float ry = reduce_scatter4(cy, lane);
+                    const float rz = reduce_scatter4(cz, lane);
+                    if ((lane & 7) == 0) {
+                        const int s = jj + (lane >> 3);
+                        sJ[warp][0][s] = rx;
+                        sJ[warp][1][s] = ry;
+                        sJ[warp][2][s] = rz;
+                    }
+                }
+                fold2(hx[0], lx[0], ax2.x);
+                fold2(hy[0], ly[0], ay2.x);
+                fold2(hz[0], lz[0], az2.x);
+                fold2(hx[1], lx[1], ax2.y);
+                fold2(hy[1], ly[1], ay2.y);
+                fold2(hz[1], lz[1], az2.y);
+            }
+            __syncthreads();
+            // the tile's B side: the FP32 sums over the block's particles, then the deferred
+            // terms in double-float in a fixed order, added to the group's partials
+            for (int t = tid; t < cnt; t += BS) {
+                double d[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float v = sJ[0][c][t];
+#pragma unroll
+                    for (int q = 1; q < W; ++q) v += sJ[q][c][t];
+                    d[c] = (double)v;
+                }
+                const int j = j0 + t;
+                unsigned anyq = 0u;
+#pragma unroll
+                for (int q = 0; q < W; ++q) anyq |= sQ[q][0][t] | sQ[q][1][t];
+                if (anyq) {
+                    const float4 ja = jrec[j], jl = jrec[n_s + j];
+                    DF3 b = df3_zero();
+                    double f[3] = {0.0, 0.0, 0.0};
+                    for (int q = 0; q < W; ++q)
+                        for (int k = 0; k < ILP; ++k) {
+                            unsigned mk = sQ[q][k][t];
+                            while (mk) {
+                                const int i = ibase + k * BS + q * 32 + (__ffs(mk) - 1);
+                                mk &= mk - 1u;
+                                const float4 I0 = irec[i], I1 = irec[n_a + i];
+                                DF3 r;
+                                if (acc_term_df3(I0, I1, ja.x, ja.y, ja.z, jl.x, jl.y, jl.z, e2d, r)) {
+                                    df3_add(b, r);
+                                } else {
+                                    const D3 u = acc_term_fp64(I0, I1, ja.x, ja.y, ja.z, jl.x, jl.y, jl.z,
+                                                               mstore[ilist ? ilist[i] : i], eps2d);
+                                    f[0] += u.x;
+                                    f[1] += u.y;
+                                    f[2] += u.z;
+                                }
+                            }
+                        }
+                    d[0] += df::to_double(b.x) + f[0];
+                    d[1] += df::to_double(b.y) + f[1];
+                    d[2] += df::to_double(b.z) + f[2];
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    double *dst = pj + ((size_t)g * 3 + c) * n_s + j;
+                    *dst = (ib == g) ? d[c] : *dst + d[c];
+                }
+#pragma unroll
+                for (int w = 0; w < W; ++w) pcnt[((size_t)g * W + w) * n_s + j] = (uint8_t)sCnt[w][t];
+            }
+        }
+        // the A side of this i-block and split: the FP32 sums, then the deferred terms
+        double res[ILP][3];
+        res[0][0] = (double)hx[0] + (double)lx[0];
+        res[0][1] = (double)hy[0] + (double)ly[0];
+        res[0][2] = (double)hz[0] + (double)lz[0];
+        res[1][0] = (double)hx[1] + (double)lx[1];
+        res[1][1] = (double)hy[1] + (double)ly[1];
+        res[1][2] = (double)hz[1] + (double)lz[1];
+#pragma unroll
+        for (int k = 0; k < ILP; ++k) {
+            const float4 ia = k ? a1 : a0, il = k ? b1 : b0;
+            DF3 b = df3_zero();
+            double f[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+            for (int s = 0; s < GRAD_SLOTS; ++s) {
+                if (s < big.n[k]) {
+                    const int j = big.get(s, k);
+                    const float4 J0 = jrec[j], J1 = jrec[n_s + j];
+                    DF3 t;
+                    if (acc_term_df3(J0, J1, ia.x, ia.y, ia.z, il.x, il.y, il.z, e2d, t)) {
+                        df3_add(b, t);
+                    } else {
+                        const D3 u = acc_term_fp64(J0, J1, ia.x, ia.y, ia.z, il.x, il.y, il.z,
+                                                   mstore[jlist ? jlist[j] : j], eps2d);
+                        f[0] += u.x;
+                        f[1] += u.y;
+                        f[2] += u.z;
+                    }
+                }
+            }
+            res[k][0] += df::to_double(b.x) + f[0];
+            res[k][1] += df::to_double(b.y) + f[1];
+            res[k][2] += df::to_double(b.z) + f[2];
+        }
+        double *p = part + (size_t)blockIdx.y * 3 * n_a;
+        if (i0 < n_a) {
+            p[i0] = res[0][0];
+            p[n_a + i0] = res[0][1];
+            p[2 * n_a + i0] = res[0][2];
+        }
+        if (i1 < n_a) {
+            p[i1] = res[1][0];
+            p[n_a + i1] = res[1][1];
+            p[2 * n_a + i1] = res[1][2];
+        }
+    }
+}
+
+// one particle's gradient record (the four float4 of launch_pack_grad_mixed) as GradMixedI<1>
+__device__ __forceinline__ GradMixedI<1> grad_rec_of(const float4 *__restrict__ rec, int n, int i)
+{
+    const float4 q0 = rec[i], q1 = rec[n + i], q2 = rec[2 * n + i], q3 = rec[3 * n + i];
+    GradMixedI<1> O;
+    O.xh[0] = q0.x; O.yh[0] = q0.y; O.zh[0] = q0.z;
+    O.xm[0] = q1.x; O.ym[0] = q1.y; O.zm[0] = q1.z; O.ahx[0] = q1.w;
+    O.xl[0] = q2.x; O.yl[0] = q2.y; O.zl[0] = q2.z; O.ahy[0] = q2.w;
+    O.ahz[0] = q3.x; O.alx[0] = q3.y; O.aly[0] = q3.z; O.alz[0] = q3.w;
+    return O;
+}
+
+template <int BS, int TJ>
+__global__ void __launch_bounds__(BS, 4) k_grad_sym_mixed(const float4 *__restrict__ irec,
+                                                       const float4 *__restrict__ jrec, int n_a, int n_s, int nblk_i,
+                                                       int j_per_split, double eps2d, const float *__restrict__ wA,
+                                                       const float *__restrict__ wB, double *__restrict__ part,
+                                                       double *__restrict__ pj, uint8_t *__restrict__ pcnt)
+{
+    constexpr int ILP = 2, W = BS / 32, FOLD = 64;
+    static_assert(BS == SYM_BS && TJ == SYM_TJ, "slot columns and ballot rows are laid out for SYM_BS, SYM_TJ");
+    __shared__ float4 sG[8][TJ];
+    __shared__ float sT[W][TJ];
+    __shared__ int sCnt[W][TJ];
+    __shared__ float sJ[W][3][TJ];
+    __shared__ unsigned sQ[W][ILP][TJ];
+    __shared__ int s_slot[GRAD_SLOTS * ILP * BS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = blockIdx.x, ng = gridDim.x;
+    const int jb = blockIdx.y * j_per_split;
+    const int je = min(n_s, jb + j_per_split);
+    const float eps2 = (float)eps2d;
+    const float2 e2 = make_float2(eps2, eps2);
+    const df::dfloat e2d = df::from_double(eps2d);
+    for (int ib = g; ib < nblk_i; ib += ng) {
+        const int ibase = ib * BS * ILP;
+        const int i0 = ibase + tid, i1 = ibase + BS + tid;
+        // the thread's two particles; past the end: zero mass, far from every source
+        float4 q[ILP][4];
+        float thr[ILP] = {INFINITY, INFINITY};
+#pragma unroll
+        for (int k = 0; k < ILP; ++k) {
+            const int i = k ? i1 : i0;
+            q[k][0] = make_float4(SYM_FAR, SYM_FAR, SYM_FAR, 0.f);
+            q[k][1] = q[k][2] = q[k][3] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i < n_a) {
+                q[k][0] = irec[i];
+                q[k][1] = irec[n_a + i];
+                q[k][2] = irec[2 * n_a + i];
+                q[k][3] = irec[3 * n_a + i];
+                thr[k] = SLOT_FRACTION * wA[i];
+            }
+        }
+        GradX2I P;
+        P.nxh = make_float2(-q[0][0].x, -q[1][0].x);
+        P.nyh = make_float2(-q[0][0].y, -q[1][0].y);
+        P.nzh = make_float2(-q[0][0].z, -q[1][0].z);
+        P.nxm = make_float2(-q[0][1].x, -q[1][1].x);
+        P.nym = make_float2(-q[0][1].y, -q[1][1].y);
+        P.nzm = make_float2(-q[0][1].z, -q[1][1].z);
+        P.nxl = make_float2(-q[0][2].x, -q[1][2].x);
+        P.nyl = make_float2(-q[0][2].y, -q[1][2].y);
+        P.nzl = make_float2(-q[0][2].z, -q[1][2].z);
+        P.nahx = make_float2(-q[0][1].w, -q[1][1].w);
+        P.nahy = make_float2(-q[0][2].w, -q[1][2].w);
+        P.nahz = make_float2(-q[0][3].x, -q[1][3].x);
+        P.nalx = make_float2(-q[0][3].y, -q[1][3].y);
+        P.naly = make_float2(-q[0][3].z, -q[1][3].z);
+        P.nalz = make_float2(-q[0][3].w, -q[1][3].w);
+        const float2 nmi = make_float2(-q[0][0].w, -q[1][0].w);
+        SmemSlots<ILP, BS> big;
+        big.col = s_slot + tid;
+        big.n[0] = big.n[1] = 0;
+        float hx[ILP] = {0.f, 0.f}, hy[ILP] = {0.f, 0.f}, hz[ILP] = {0.f, 0.f};
+        float lx[ILP] = {0.f, 0.f}, ly[ILP] = {0.f, 0.f}, lz[ILP] = {0.f, 0.f};
+        for (int j0 = jb; j0 < je; j0 += TJ) {
+            const int cnt = min(TJ, je - j0);
+            const int cnt8 = (cnt + 7) & ~7;
+            __syncthreads();
+            for (int t = tid; t < cnt8; t += BS) {
+                float4 r0 = make_float4(-SYM_FAR, -SYM_FAR, -SYM_FAR, 0.f), r1 = make_float4(0.f, 0.f, 0.f, 0.f),
+                       r2 = r1, r3 = r1;
+                float tj = INFINITY;
+                if (t < cnt) {
+                    r0 = jrec[j0 + t];
+                    r1 = jrec[n_s + j0 + t];
+                    r2 = jrec[2 * n_s + j0 + t];
+                    r3 = jrec[3 * n_s + j0 + t];
+                    tj = SLOT_FRACTION * wB[j0 + t];
+                }
+                sG[0][t] = make_float4(r0.x, r0.x, r0.y, r0.y);
+                sG[1][t] = make_float4(r0.z, r0.z, r1.x, r1.x);
+                sG[2][t] = make_float4(r1.y, r1.y, r1.z, r1.z);
+                sG[3][t] = make_float4(r2.x, r2.x, r2.y, r2.y);
+                sG[4][t] = make_float4(r2.z, r2.z, r1.w, r1.w);
+                sG[5][t] = make_float4(r2.w, r2.w, r3.x, r3.x);
+                sG[6][t] = make_float4(r3.y, r3.y, r3.z, r3.z);
+                sG[7][t] = make_float4(r3.w, r3.w, r0.w, r0.w);
+                stage_bside(sT, sCnt, sQ, pcnt, t, cnt, j0, n_s, g, ib == g, tj);
+            }
+            __syncthreads();
+            for (int c0 = 0; c0 < cnt8; c0 += FOLD) {
+                const int c1 = min(cnt8, c0 + FOLD);
+                float2 gx2 = make_float2(0.f, 0.f), gy2 = gx2, gz2 = gx2;
+                // groups of 4 sources (a reduce-scatter of 8 would hold 12 more registers)
+                for (int jj = c0; jj < c1; jj += 4) {
+                    float cx[4], cy[4], cz[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int s = jj + u;
+                        gradsym_x2_j(sG[0][s], sG[1][s], sG[2][s], sG[3][s], sG[4][s], sG[5][s], sG[6][s], sG[7][s],
+                                     sT[warp][s], P, nmi, e2, j0 + s, thr, big, gx2, gy2, gz2, cx[u], cy[u], cz[u],
+                                     &sCnt[warp][s], &sQ[warp][0][s], &sQ[warp][1][s], lane);
+                    }
+                    const float rx = reduce_scatter4(cx, lane);
+                    const float ry = reduce_scatter4(cy, lane);
+                    const float rz = reduce_scatter4(cz, lane);
+                    if ((lane & 7) == 0) {
+                        const int s = jj + (lane >> 3);
+                        sJ[warp][0][s] = rx;
+                        sJ[warp][1][s] = ry;
+                        sJ[warp][2][s] = rz;
+                    }
+                }
+                fold2(hx[0], lx[0], gx2.x);
+                fold2(hy[0], ly[0], gy2.x);
+                fold2(hz[0], lz[0], gz2.x);
+                fold2(hx[1], lx[1], gx2.y);
+                fold2(hy[1], ly[1], gy2.y);
+                fold2(hz[1], lz[1], gz2.y);
+            }
+            __syncthreads();
+            for (int t = tid; t < cnt; t += BS) {
+                double d[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float v = sJ[0][c][t];
+#pragma unroll
+                    for (int w = 1; w < W; ++w) v += sJ[w][c][t];
+                    d[c] = (double)v;
+                }
+                const int j = j0 + t;
+                unsigned anyq = 0u;
+#pragma unroll
+                for (int w = 0; w < W; ++w) anyq |= sQ[w][0][t] | sQ[w][1][t];
+                if (anyq) {
+                    const GradMixedI<1> O = grad_rec_of(jrec, n_s, j);
+                    DF3 b = df3_zero();
+                    double f[3] = {0.0, 0.0, 0.0};
+                    for (int w = 0; w < W; ++w)
+                        for (int k = 0; k < ILP; ++k) {
+                            unsigned mk = sQ[w][k][t];
+                            while (mk) {
+                                const int i = ibase + k * BS + w * 32 + (__ffs(mk) - 1);
+                                mk &= mk - 1u;
+                                const float4 I0 = irec[i], I1 = irec[n_a + i], I2 = irec[2 * n_a + i],
+                                             I3 = irec[3 * n_a + i];
+                                DF3 r;
+                                if (grad_term_df3<1>(I0, I1, I2, I3, O, 0, e2d, r)) df3_add(b, r);
+                                else grad_term_fp64<1>(I0, I1, I2, I3, O, 0, eps2d, f[0], f[1], f[2]);
+                            }
+                        }
+                    d[0] += df::to_double(b.x) + f[0];
+                    d[1] += df::to_double(b.y) + f[1];
+                    d[2] += df::to_double(b.z) + f[2];
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    double *dst = pj + ((size_t)g * 3 + c) * n_s + j;
+                    *dst = (ib == g) ? d[c] : *dst + d[c];
+                }
+#pragma unroll
+                for (int w = 0; w < W; ++w) pcnt[((size_t)g * W + w) * n_s + j] = (uint8_t)sCnt[w][t];
+            }
+        }
+        double *p = part + (size_t)blockIdx.y * 3 * n_a;
+#pragma unroll
+        for (int k = 0; k < ILP; ++k) {
+            const int i = k ? i1 : i0;
+            double bx = 0.0, by = 0.0, bz = 0.0;
+            if (big.n[k] > 0) {
+                const GradMixedI<1> O = grad_rec_of(irec, n_a, i);
+                DF3 b = df3_zero();
+                for (int s = 0; s < big.n[k]; ++s) {
+                    const int j = big.get(s, k);
+                    const float4 J0 = jrec[j], J1 = jrec[n_s + j], J2 = jrec[2 * n_s + j], J3 = jrec[3 * n_s + j];
+                    DF3 t;
+                    if (grad_term_df3<1>(J0, J1, J2, J3, O, 0, e2d, t)) df3_add(b, t);
+                    else grad_term_fp64<1>(J0, J1, J2, J3, O, 0, eps2d, bx, by, bz);
+                }
+                bx += df::to_double(b.x);
+                by += df::to_double(b.y);
+                bz += df::to_double(b.z);
+            }
+            if (i < n_a) {
+                p[i] = ((double)hx[k] + (double)lx[k]) + bx;
+                p[n_a + i] = ((double)hy[k] + (double)ly[k]) + by;
+                p[2 * n_a + i] = ((double)hz[k] + (double)lz[k]) + bz;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+void launch_acc_sym_defer(cudaStream_t s, const void *irec, const void *jrec, int n_a, int n_s, double eps2,
+                          const float *wA, const float *wB, const int32_t *ilist, const int32_t *jlist,
+                          const double *mstore, double *part, double *pj, uint8_t *pcnt, const SymShape &sh)
+{
+    const dim3 grid(sh.ngroups, sh.nsplit);
+    k_acc_sym_defer_mixed<SYM_BS, SYM_TJ><<<grid, SYM_BS, 0, s>>>((const float4 *)irec, (const float4 *)jrec, n_a,
+                                                                  n_s, sh.nblk_i, sh.j_per_split, (float)eps2, eps2,
+                                                                  wA, wB, ilist, jlist, mstore, part, pj, pcnt);
+}
+
+void launch_grad_sym(cudaStream_t s, const void *irec, const void *jrec, int n_a, int n_s, double eps2,
+                     const float *wA, const float *wB, double *part, double *pj, uint8_t *pcnt, const SymShape &sh)
+{
+    const dim3 grid(sh.ngroups, sh.nsplit);
+    k_grad_sym_mixed<SYM_BS, SYM_TJ><<<grid, SYM_BS, 0, s>>>((const float4 *)irec, (const float4 *)jrec, n_a, n_s,
+                                                             sh.nblk_i, sh.j_per_split, eps2, wA, wB, part, pj, pcnt);
 }
 
 }  // namespace frost

@@ -52,7 +52,7 @@ class frost_stats(ctypes.Structure):
                 ("timed_pairs", ctypes.c_int64 * 4), ("subtree_launches", ctypes.c_int64),
                 ("level_calls", ctypes.c_int64 * 48), ("level_particles", ctypes.c_int64 * 48),
                 ("acc_pairs_reused", ctypes.c_int64), ("subtree_pairs", ctypes.c_int64 * 3),
-                ("acc_pairs_symmetric", ctypes.c_int64)]
+                ("acc_pairs_symmetric", ctypes.c_int64), ("grad_pairs_symmetric", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -76,6 +76,7 @@ _SIGS = {
     "frost_accel_gradient": (ctypes.c_int, [_P, _P, _I64, _P, _I64, _D, _P, _P, _P]),
     "frost_timesteps": (ctypes.c_int, [_P, _P, _I64, _P]),
     "frost_accel_pairwise": (ctypes.c_int, [_P, _P, _I64, _P, _I64, _P, _P]),
+    "frost_accel_gradient_pairwise": (ctypes.c_int, [_P, _P, _I64, _P, _I64, _D, _P, _P, _P, _P, _P, _P]),
     "frost_partition": (ctypes.c_int, [_P, _P, _I64, _P, _D, _P, _P, ctypes.POINTER(_I64),
                                        ctypes.POINTER(_I64)]),
     "frost_kick": (ctypes.c_int, [_P, _P, _I64, _P, _D]),
@@ -199,6 +200,14 @@ def frost_accel_gradient(ctx, active, n_active, source, n_source, eps_grad, acc,
 def frost_accel_pairwise(ctx, a, n_a, b, n_b, acc_a, acc_b) -> None:
     _check(load().frost_accel_pairwise(ctx, _ptr(a), int(n_a), _ptr(b), int(n_b), _ptr(acc_a), _ptr(acc_b)),
            "frost_accel_pairwise")
+
+
+def frost_accel_gradient_pairwise(ctx, a, n_a, b, n_b, eps_grad, acc_a, acc_b, acc_tilde_a, acc_tilde_b,
+                                  grad_a, grad_b) -> None:
+    _check(load().frost_accel_gradient_pairwise(ctx, _ptr(a), int(n_a), _ptr(b), int(n_b), float(eps_grad),
+                                                _ptr(acc_a), _ptr(acc_b), _ptr(acc_tilde_a), _ptr(acc_tilde_b),
+                                                _ptr(grad_a), _ptr(grad_b)),
+           "frost_accel_gradient_pairwise")
 
 
 def frost_timesteps(ctx, set_, n_set, tau) -> None:
@@ -378,6 +387,20 @@ class Frost:
         out_b = t.empty((int(B.numel()), 3), dtype=t.float64, device="cuda")
         frost_accel_pairwise(self.ctx, A, int(A.numel()), B, int(B.numel()), out_a, out_b)
         return out_a, out_b
+
+    def accel_gradient_pairwise(self, a, b, eps_grad):
+        """The force-gradient kick of the disjoint lists a and b due to each other: per list
+        the Newtonian acceleration, a~ and the gradient ({"acc", "acc_tilde", "grad"} x
+        {"a", "b"}, [n][3] each); mixed mode: each pair once for both lists."""
+        t = self.torch
+        A = self._dev(a, t.int32)
+        B = self._dev(b, t.int32)
+        na, nb = int(A.numel()), int(B.numel())
+        out = {k + "_" + s: t.empty((n, 3), dtype=t.float64, device="cuda")
+               for k in ("acc", "acc_tilde", "grad") for s, n in (("a", na), ("b", nb))}
+        frost_accel_gradient_pairwise(self.ctx, A, na, B, nb, eps_grad, out["acc_a"], out["acc_b"],
+                                      out["acc_tilde_a"], out["acc_tilde_b"], out["grad_a"], out["grad_b"])
+        return out
 
     def timesteps(self, set_=None, n_set=None):
         t = self.torch

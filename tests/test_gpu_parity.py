@@ -165,6 +165,103 @@ def test_symmetric_wmax_prepass_is_bit_identical(n, cross):
         assert np.array_equal(out[1][k], out[-1][k]), k
 
 
+def _check_gradient_pairwise(m, x, A, B, out, eps, bar=1e-6, cap=None):
+    """Both lists of frost_accel_gradient_pairwise against the oracle: a, g and
+    a~ = a + eps^2/48 g per list (the mixed bar at the 99.9th percentile, cap on the maximum).
+    A list with fewer than 1000 sources is held to the cap alone: its g_i are sums of a few
+    dozen Kroupa-mass terms, a few of them dominant, more than the 8 double-float slots of a
+    split (the one-sided passes give 1.6e-6 at the 99.9th percentile on 700 against 61)."""
+    for side, P, Q in (("a", A, B), ("b", B, A)):
+        a_ref, g_ref = oracle_g(m, x, P, Q)
+        ea, eg = rel(cpu(out["acc_" + side]), a_ref), rel(cpu(out["grad_" + side]), g_ref)
+        et = rel(cpu(out["acc_tilde_" + side]), a_ref + eps * eps / 48.0 * g_ref)
+        if len(Q) >= 1000:
+            assert p999(ea) < bar and p999(eg) < bar and p999(et) < bar, (side, p999(ea), p999(eg), p999(et))
+        if cap is not None:
+            assert ea.max() < cap and eg.max() < cap and et.max() < cap, (side, ea.max(), eg.max(), et.max())
+
+
+@pytest.mark.parametrize("sym_cross", [1, -1])
+@pytest.mark.parametrize("na,nb", [(5000, 3001), (3001, 5000), (700, 61), (1, 257), (2049, 1)])
+def test_accel_gradient_pairwise_matches_oracle(sym_cross, na, nb):
+    """The force-gradient kick of two disjoint lists (both lines of Eqs.
+    force-gradient-inter-1/2): with each pair once for both lists (sym_cross = 1, the longer
+    list on the register side, the other reduced in a fixed order) and with two one-sided
+    passes per kind (-1), both lists within the mixed bar of the oracle; ragged sizes, a list of
+    one, lists given unsorted."""
+    n = na + nb
+    m, x, v = ics.plummer(n, 31 + n % 5, masses=ics.kroupa_masses(n, 31 + n % 5))
+    perm = np.random.default_rng(n).permutation(n).astype(np.int32)
+    A, B = perm[:na], perm[na:]
+    f = F(m, x, v, precision="mixed", sym_cross=sym_cross)
+    out = f.accel_gradient_pairwise(A, B, eps_grad=0.05)
+    st = f.stats()
+    f.close()
+    assert (st["grad_pairs_symmetric"] == na * nb) == (sym_cross == 1)
+    _check_gradient_pairwise(m, x, A, B, out, 0.05, cap=1e-5)
+
+
+def test_accel_gradient_pairwise_is_deterministic_and_fp64_exact():
+    """Repeated symmetric calls give the same bits (fixed-order sums, no atomics in a sum); the
+    FP64 mode (two one-sided passes per kind) is within 1e-12 of the oracle on both lists."""
+    n = 6000
+    m, x, v = ics.plummer(n, 44)
+    perm = np.random.default_rng(4).permutation(n).astype(np.int32)
+    A, B = np.sort(perm[:3500]), perm[3500:]
+    f = F(m, x, v, precision="mixed", sym_cross=1)
+    o1 = {k: cpu(t) for k, t in f.accel_gradient_pairwise(A, B, eps_grad=0.05).items()}
+    o2 = {k: cpu(t) for k, t in f.accel_gradient_pairwise(A, B, eps_grad=0.05).items()}
+    f.close()
+    for k in o1:
+        assert np.array_equal(o1[k], o2[k]), k
+    f = F(m, x, v, precision="fp64")
+    out = f.accel_gradient_pairwise(A, B, eps_grad=0.05)
+    f.close()
+    for side, P, Q in (("a", A, B), ("b", B, A)):
+        a_ref, g_ref = oracle_g(m, x, P, Q)
+        assert rel(cpu(out["acc_" + side]), a_ref).max() < 1e-12
+        assert rel(cpu(out["grad_" + side]), g_ref).max() < 1e-12
+
+
+def test_accel_gradient_pairwise_full_slots_and_hard_binaries():
+    """The two cases that stress the dominant terms, symmetric on both lists: (1) the outskirts
+    of a Plummer sphere against its 96 central particles, where every outskirt particle has more
+    dominant candidates than its slots (register side) and every core particle has hundreds of
+    dominant partners (reduced side, no slot limit); the core side nearly cancels its own pull,
+    so it is held to the bound of a floating-point sum, 1e-7 of the sum of the terms' sizes;
+    (2) Kroupa masses with 5% hard binaries split between the lists: the hot sources in
+    double-float on both sides, the mixed bar at the 99.9th percentile and 1e-5 at most."""
+    n = 2000
+    m, x, v = ics.plummer(n, 23)
+    r = np.linalg.norm(x, axis=1)
+    order = np.argsort(r).astype(np.int32)
+    B = np.sort(order[:96])
+    A = np.sort(order[-640:])
+    f = F(m, x, v, precision="mixed", sym_cross=1)
+    out = f.accel_gradient_pairwise(A, B, eps_grad=0.05)
+    f.close()
+    a_ref, g_ref = oracle_g(m, x, A, B)
+    assert p999(rel(cpu(out["acc_a"]), a_ref)) < 1e-6 and p999(rel(cpu(out["grad_a"]), g_ref)) < 1e-6
+    b_ref, gb_ref = oracle_g(m, x, B, A)
+    d = x[A][None, :, :] - x[B][:, None, :]
+    ri = 1.0 / np.linalg.norm(d, axis=2)
+    Sa = (m[A][None, :] * ri ** 2).sum(1)
+    da = a_ref[None, :, :] - b_ref[:, None, :]
+    tg = (m[A][None, :] * ri ** 3)[..., None] * (da - 3.0 * ((d * da).sum(2) * ri ** 2)[..., None] * d)
+    Sg = 2.0 * np.linalg.norm(tg, axis=2).sum(1)
+    assert np.all(np.linalg.norm(cpu(out["acc_b"]) - b_ref, axis=1) < 1e-7 * Sa)
+    assert np.all(np.linalg.norm(cpu(out["grad_b"]) - gb_ref, axis=1) < 1e-7 * Sg)
+
+    n = 8192
+    m, x, v = ics.plummer_kroupa_binaries(n, 17)
+    perm = np.random.default_rng(5).permutation(n).astype(np.int32)
+    A, B = np.sort(perm[:2500]), perm[2500:]
+    f = F(m, x, v, precision="mixed", sym_cross=1)
+    out = f.accel_gradient_pairwise(A, B, eps_grad=1e-3)
+    f.close()
+    _check_gradient_pairwise(m, x, A, B, out, 1e-3, cap=1e-5)
+
+
 def test_accel_pairwise_rejects_overlapping_lists():
     from paper_2011_14984_gb300 import frost as fr
     m, x, v = ics.plummer(100, 3)
@@ -501,8 +598,9 @@ def test_hhs_fsi_trajectory_parity_fp64(sym):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_symmetric_kick_sf_trajectory(precision):
-    """The Newtonian kick_sf of every level with each S x F pair once (sym_cross = 1, at every
-    size): Plummer N = 1024 to t = 0.125 as in the serial test above, FP64 within 1e-10 of the
+    """The kick_sf of every level with each S x F pair once (sym_cross = 1, at every size; the
+    force-gradient kick too in mixed mode): Plummer N = 1024 to t = 0.125 as in the serial test
+    above, FP64 within 1e-10 of the
     oracle and the same depth; mixed within the mixed tolerance of the grid-path comparison
     (1e-7 in position) of the run with two one-sided passes, and the same depth."""
     m, x, v = ics.plummer(1024, 1)
@@ -512,6 +610,7 @@ def test_symmetric_kick_sf_trajectory(precision):
     st = f.stats()
     f.close()
     assert st["acc_pairs_symmetric"] > 0
+    assert (st["grad_pairs_symmetric"] > 0) == (precision == "mixed")
     if precision == "fp64":
         oracle.reset_counters()
         xo, vo = oracle.steps(m, x, v, 2.0 ** -7, 16, eta=0.2)

@@ -454,6 +454,20 @@ void launch_potential(cudaStream_t s, const double *x, const double *m, int n, d
     k_potential_df<PAIR_BS, PAIR_TJ><<<grid, PAIR_BS, 0, s>>>(rec, n, shape.j_per_split, eps2, part);
 }
 
+int potential_blocks_per_sm()
+{
+    static int occ = 0;
+    if (!occ) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_potential_df<PAIR_BS, PAIR_TJ>, PAIR_BS, 0) !=
+                cudaSuccess ||
+            occ < 1) {
+            cudaGetLastError();
+            occ = 1;
+        }
+    }
+    return occ;
+}
+
 void launch_aos_to_soa(cudaStream_t s, const double *aos, int n, double *soa, int *err)
 {
     if (n <= 0) return;

@@ -1710,7 +1710,17 @@ frost_status frost_energy_momentum(frost_ctx *c, double *E_kin, double *E_pot, d
         }
         return FROST_OK;
     }
-    SplitShape sh = choose_shape(c->N, c->N, PAIR_BS, pair_blocks_per_sm(PASS_ACC, true), c->n_sm);
+    // the potential pass skips the tiles below each i-block's diagonal, so its blocks differ in
+    // work: eight waves of blocks (of its own occupancy) keep the last ones short
+    SplitShape sh;
+    {
+        const long long cap = (long long)potential_blocks_per_sm() * c->n_sm;
+        const int tiles = (int)((c->N + PAIR_TJ - 1) / PAIR_TJ);
+        sh.nblk_i = (int)((c->N + PAIR_BS - 1) / PAIR_BS);
+        const int ns = (int)std::min<long long>(tiles, std::max<long long>(1, (8 * cap + sh.nblk_i - 1) / sh.nblk_i));
+        sh.j_per_split = ((tiles + ns - 1) / ns) * PAIR_TJ;
+        sh.nsplit = (int)((c->N + sh.j_per_split - 1) / sh.j_per_split);
+    }
     while ((size_t)sh.nsplit * c->N > c->part_elems && sh.nsplit > 1) {
         const int tiles = (c->N + PAIR_TJ - 1) / PAIR_TJ;
         const int ns = std::max(1, sh.nsplit / 2);

@@ -190,6 +190,8 @@ void launch_check_mass(cudaStream_t s, const double *m, int n, int *err);
 // launch_energy_reduce); rec: scratch of 48 B per particle
 void launch_potential(cudaStream_t s, const double *x, const double *m, int n, double eps2, float4 *rec,
                       double *part, const SplitShape &shape);
+// blocks of the potential pass per SM (its occupancy)
+int potential_blocks_per_sm();
 // out[0] = T, out[1] = sum_i m_i phi_i, out[2..4] = P, out[5..7] = L (one block, fixed order)
 void launch_energy_reduce(cudaStream_t s, const double *x, const double *v, const double *m,
                           int N, const double *part, int nsplit, double *out);

@@ -339,22 +339,23 @@ SymShape sym_shape(int kind, int n_a, int n_s, int n_sm, size_t part_elems, size
     const long long max_groups = std::max<long long>(1, (long long)(pj_elems / (3 * (size_t)std::max(n_s, 1))));
     const int per = (int)((sh.nblk_i + std::min<long long>(max_groups, 64) - 1) / std::min<long long>(max_groups, 64));
     sh.ngroups = (sh.nblk_i + per - 1) / per;
-    // The split count: every block takes the same number of i-blocks, so its time is about
-    // its tiles per split, and the last wave of blocks takes as long as a full one.  The
-    // count minimises waves x (tiles per block + a quarter tile of fixed work), with the
-    // partials within their buffer; among equal costs the fewest splits.
+    // The split count.  Every block takes the same number of i-blocks, so its work is about
+    // its tiles per split (plus a quarter tile of fixed work); an SM runs up to o blocks at a
+    // time and its share of the grid, ceil(blocks / n_sm) blocks, sets the kernel's time:
+    // cost = share x (tiles + 1/4) / min(share, o).  The count minimises it, with the partials
+    // within their buffer; among equal costs the fewest splits.
     const long long cap = (long long)o * n_sm;
     const int tiles = (n_s + SYM_TJ - 1) / SYM_TJ;
     long long ns_max = std::min<long long>(tiles, (long long)(part_elems / (3 * (size_t)std::max(n_a, 1))));
     ns_max = std::max<long long>(ns_max, 1);
-    long long best = -1;
+    double best = -1.0;
     int best_tps = tiles;
     for (long long ns = 1; ns <= ns_max; ++ns) {
         const int tps = (int)((tiles + ns - 1) / ns);
         const long long nsplit = (tiles + tps - 1) / tps;
-        const long long waves = (sh.ngroups * nsplit + cap - 1) / cap;
-        const long long cost = waves * (4LL * tps + 1);
-        if (best < 0 || cost < best) {
+        const long long share = (sh.ngroups * nsplit + n_sm - 1) / n_sm;
+        const double cost = (double)share * (tps + 0.25) / (double)std::min<long long>(share, o);
+        if (best < 0.0 || cost < best - 1e-9) {
             best = cost;
             best_tps = tps;
         }

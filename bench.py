@@ -40,6 +40,10 @@ FP32_LANES_PER_SM = 128
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate
 METRIC = "acc+gradient interactions/s"
 UNIT = "interactions/s"
+# DRAM bytes (read + write) per launch of the Newtonian kind in one 64k hierarchical step:
+# ncu dram__bytes_read.sum + dram__bytes_write.sum over the step's 396 launches of that kind
+# (profiles/launches_plummer64k_hhs_step.md, the current kernels)
+TRAFFIC_ACC_PLUMMER64K = 388752.0
 
 
 def parse():
@@ -234,6 +238,17 @@ def aggregate_ranks(ms_total, work, world, device):
 # ---------------------------------------------------------------------------------------
 # the CUDA path
 # ---------------------------------------------------------------------------------------
+def work_stream(dev=None):
+    """The stream every measured call runs on (made current for torch too): the device's
+    highest priority, so that the library's concurrent branch lanes, created at the lowest
+    priority, yield to the recursion on the context stream (its critical path)."""
+    import torch
+    s = torch.cuda.Stream(device=dev, priority=-100)  # mapped to the greatest priority
+    torch.cuda.set_stream(s)
+    return s
+
+
+# ---------------------------------------------------------------------------------------
 def method_pairs(st):
     """acc + gradient interactions of the method's steps: the evaluated pairs, plus the
     Newtonian pairs of the second fsi(S) that reuse the stored end-of-first-fsi a^SS (exact,
@@ -275,7 +290,7 @@ def run_frost(args):
     fbuild.build()
     fr.load()
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
+    stream = work_stream(dev)
 
     m, x, v = ics.workload(args.workload)
     n = m.size
@@ -364,9 +379,15 @@ def run_frost(args):
     sm_max = (clk.get("sm_max_mhz") or peaks().get("sm_max_mhz") or 2070.0)
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     sm_med = clk.get("sm_mhz")
+    default_run = (args.workload == "plummer_64k" and args.integrator == "hhs_fsi" and not args.flyby_exact
+                   and args.subtree_max == 0 and args.subtree_blocks == 0 and args.branch_streams == 0
+                   and args.sym_cross == 0)
+    traffic = TRAFFIC_ACC_PLUMMER64K if (default_run and kname == "acc") else None
     roofline = {"bound": "alu", "kernel": f"{kname} pass (mixed, FP32 pipe)",
                 "achieved": achieved_tf, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved_tf / fp32_peak, "traffic": None,
+                "frac": achieved_tf / fp32_peak, "traffic": traffic,
+                "traffic_basis": ("DRAM bytes per launch of the kind, averaged over one step's launches "
+                                  "(ncu capture of this workload)") if traffic else None,
                 "peak_basis": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)",
                 "frac_at_median_clock": (achieved_tf / (fp32_peak * sm_med / sm_max)) if sm_med else None,
                 "probe": probe,
@@ -529,7 +550,7 @@ def run_batch(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     fbuild.build()
     fr.load()
-    stream = torch.cuda.current_stream()
+    stream = work_stream()
     off, m, x, v = ics.batch_workload(args.workload)
     ncl = off.size - 1
     f = fr.Frost(m, x, v, G=1.0, eta=args.eta, precision="mixed", stream=stream.cuda_stream,
@@ -638,7 +659,7 @@ def run_passes(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     fbuild.build()
     fr.load()
-    stream = torch.cuda.current_stream()
+    stream = work_stream()
     m, x, v = ics.workload(args.workload)
     n = m.size
     f = fr.Frost(m, x, v, G=1.0, eta=args.eta, precision="mixed", stream=stream.cuda_stream)
@@ -738,7 +759,7 @@ def run_integrate(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     fbuild.build()
     fr.load()
-    stream = torch.cuda.current_stream()
+    stream = work_stream()
     m, x, v = ics.workload(args.workload)
     n = m.size
     steps = args.steps

@@ -704,27 +704,21 @@ bool pass_acc_sym(frost_ctx *c, Lane &L, const int32_t *A, int nA, const int32_t
     return true;
 }
 
-// The passes of the gradient kick_sf over two disjoint lists A and B with every pair once
-// (mixed mode; Eqs. force-newton-inter and force-gradient-inter-1/2, both lines): the
-// symmetric wmax prepass, the accurate Newtonian sums of both lists (into M.aA / M.aB, soa),
-// the hot sources of both (M.hA / M.hB), the gradient records, and both gradients, finalised
-// per list as a~ = a + eps_grad^2/48 g (at_soa, at_aos, g_aos per list, each may be NULL)
-// with the kicks kA / kB fused.  M.recA / M.recB hold the lists' position records on entry.
-// The longer list takes the register side.  Returns false, issuing nothing, unless its finest
-// grid fills one wave of the GPU or force is set.
-bool grad_pairwise_sym(frost_ctx *c, Lane &M, const int32_t *A, int nA, const int32_t *B, int nB, double eps_grad,
-                       double *atA_soa, double *atB_soa, double *atA_aos, double *atB_aos, double *gA_aos,
-                       double *gB_aos, KickArgs kA, KickArgs kB, bool force)
+// The accurate Newtonian sums of two disjoint lists (mixed mode) with every pair once: the
+// symmetric wmax prepass and the symmetric pass with the dominant terms of both sides in
+// double-float, into M.aA / M.aB (soa), with their |a| histograms in h (A) and h + HOT_BINS
+// (B).  M.recA / M.recB hold the lists' position records.  Returns false, issuing nothing,
+// unless its finest grid fills one wave of the GPU or force is set.
+bool acc_pairwise_defer(frost_ctx *c, Lane &M, const int32_t *A, int nA, const int32_t *B, int nB, unsigned *h,
+                        bool force)
 {
     if (!c->mixed || nA <= 0 || nB <= 0) return false;
     const bool swap = nB > nA;
     const int ni = swap ? nB : nA, nj = swap ? nA : nB;
     const SymShape sa = sym_shape(SYM_ACC_DEFER, ni, nj, c->n_sm, c->part_elems, c->pj_elems);
     if (!force && sa.max_blocks < (long long)sa.blocks_per_wave) return false;
-    const SymShape sg = sym_shape(SYM_GRAD, ni, nj, c->n_sm, c->part_elems, c->pj_elems);
     const int64_t pairs = (int64_t)nA * nB;
     const int32_t *Li = swap ? B : A, *Lj = swap ? A : B;
-    unsigned *h = zero_hists(M);
     {
         TimedScope ts(c, M.s, PASS_ACC, 0);
         launch_wmax_sym_cross(M.s, M.recA, nA, M.recB, nB, c->eps2, c->n_sm, M.wA, M.wB);
@@ -738,6 +732,32 @@ bool grad_pairwise_sym(frost_ctx *c, Lane &M, const int32_t *A, int nA, const in
     launch_finalize_vec(M.s, c->pj, sa.ngroups, nj, c->G, swap ? M.aA : M.aB, nullptr, &c->dmisc->err, badbit(c));
     launch_acc_hist(M.s, M.aA, nA, h);
     launch_acc_hist(M.s, M.aB, nB, h + HOT_BINS);
+    c->st.kernel_launches += 6;
+    c->st.acc_pairs += pairs;
+    c->st.acc_pairs_symmetric += pairs;
+    return true;
+}
+
+// The passes of the gradient kick_sf over two disjoint lists A and B with every pair once
+// (mixed mode; Eqs. force-newton-inter and force-gradient-inter-1/2, both lines): the
+// accurate Newtonian sums of both lists (acc_pairwise_defer), the hot sources of both
+// (M.hA / M.hB), the gradient records, and both gradients, finalised per list as
+// a~ = a + eps_grad^2/48 g (at_soa, at_aos, g_aos per list, each may be NULL) with the kicks
+// kA / kB fused.  M.recA / M.recB hold the lists' position records on entry.  The longer
+// list takes the register side.  Returns false, issuing nothing, unless its finest grid
+// fills one wave of the GPU or force is set.
+bool grad_pairwise_sym(frost_ctx *c, Lane &M, const int32_t *A, int nA, const int32_t *B, int nB, double eps_grad,
+                       double *atA_soa, double *atB_soa, double *atA_aos, double *atB_aos, double *gA_aos,
+                       double *gB_aos, KickArgs kA, KickArgs kB, bool force)
+{
+    if (!c->mixed || nA <= 0 || nB <= 0) return false;
+    const bool swap = nB > nA;
+    const int ni = swap ? nB : nA, nj = swap ? nA : nB;
+    const SymShape sg = sym_shape(SYM_GRAD, ni, nj, c->n_sm, c->part_elems, c->pj_elems);
+    if (!force && sg.max_blocks < (long long)sg.blocks_per_wave) return false;
+    const int64_t pairs = (int64_t)nA * nB;
+    unsigned *h = zero_hists(M);
+    acc_pairwise_defer(c, M, A, nA, B, nB, h, true);
     mark_hot(c, M, nA, nB, false, M.aA, h, h + HOT_BINS, nB, M.hA);
     mark_hot(c, M, nB, nA, false, M.aB, h + HOT_BINS, h, nA, M.hB);
     pack_grad(c, M, A, nA, M.aA, M.recA, M.hA);
@@ -762,9 +782,7 @@ bool grad_pairwise_sym(frost_ctx *c, Lane &M, const int32_t *A, int nA, const in
     launch_finalize_grad(M.s, c->pj, sg.ngroups, nj, 2.0 * c->G, swap ? M.aA : M.aB, cgrad, swap ? atA_soa : atB_soa,
                          swap ? atA_aos : atB_aos, swap ? gA_aos : gB_aos, &c->dmisc->err, badbit(c), ph_j, ns_j,
                          swap ? kA : kB);
-    c->st.kernel_launches += 11;
-    c->st.acc_pairs += pairs;
-    c->st.acc_pairs_symmetric += pairs;
+    c->st.kernel_launches += 5;
     c->st.grad_pairs += pairs;
     c->st.grad_pairs_symmetric += pairs;
     return true;

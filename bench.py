@@ -41,8 +41,8 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate
 METRIC = "acc+gradient interactions/s"
 UNIT = "interactions/s"
 # DRAM bytes (read + write) per launch of the Newtonian kind in one 64k hierarchical step:
-# ncu dram__bytes_read.sum + dram__bytes_write.sum over the step's 396 launches of that kind
-# (profiles/launches_plummer64k_hhs_step.md, the current kernels)
+# ncu dram__bytes_read.sum + dram__bytes_write.sum over the step's 396 launches of that kind,
+# captured on the current kernels
 TRAFFIC_ACC_PLUMMER64K = 388752.0
 
 

@@ -272,6 +272,29 @@ def test_accel_pairwise_rejects_overlapping_lists():
     f.close()
 
 
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_accel_gradient_pairwise_edge_cases(precision):
+    """Overlapping lists are rejected (FROST_EINVAL); an empty list gives zeros for the other
+    list (no partner: a = a~ = g = 0); a list of one against the rest matches the oracle."""
+    from paper_2011_14984_gb300 import frost as fr
+    m, x, v = ics.plummer(300, 9)
+    f = F(m, x, v, precision=precision, sym_cross=1)
+    with pytest.raises(fr.FrostError) as e:
+        f.accel_gradient_pairwise(np.arange(0, 160, dtype=np.int32), np.arange(150, 300, dtype=np.int32), eps_grad=0.05)
+    assert e.value.code == fr.FROST_EINVAL
+    out = f.accel_gradient_pairwise(np.arange(0, 300, dtype=np.int32), np.zeros(0, dtype=np.int32), eps_grad=0.05)
+    for k in ("acc_a", "acc_tilde_a", "grad_a"):
+        assert np.all(cpu(out[k]) == 0.0), k
+    A, B = np.array([17], dtype=np.int32), np.delete(np.arange(300, dtype=np.int32), 17)
+    out = f.accel_gradient_pairwise(A, B, eps_grad=0.05)
+    f.close()
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    for side, P, Q in (("a", A, B), ("b", B, A)):
+        a_ref, g_ref = oracle_g(m, x, P, Q)
+        assert rel(cpu(out["acc_" + side]), a_ref).max() < tol
+        assert rel(cpu(out["grad_" + side]), g_ref).max() < tol
+
+
 def test_accel_gradient_cross_pass_full_slots():
     """A cross pass in which every deferred slot fills: 640 particles of the outskirts of a
     Plummer sphere against the 96 particles nearest its centre.  Seen from afar the core's

@@ -118,6 +118,8 @@ struct Lane {
     double *part_hot = nullptr;                          // hot-source gradient partials
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;    // branch lanes: fork / join events
     bool owns = false;                                   // branch lanes own their buffers
+    cudaStream_t shi = nullptr;                          // branch lanes: a stream of the greatest
+                                                         // priority for their kick_sf passes
 };
 
 struct frost_ctx {
@@ -377,6 +379,10 @@ void free_lane(Lane &L)
     if (L.owns && L.s) {
         cudaStreamSynchronize(L.s);
         cudaStreamDestroy(L.s);
+    }
+    if (L.shi) {
+        cudaStreamSynchronize(L.shi);
+        cudaStreamDestroy(L.shi);
     }
     L = Lane();
 }
@@ -790,30 +796,34 @@ bool grad_pairwise_sym(frost_ctx *c, Lane &M, const int32_t *A, int nA, const in
 
 // Runs on `exec` what a branch lane issues: the branch lane itself when the branches run
 // concurrently, else its buffers on the context stream (timing mode, or concurrency off).
+// critical: work on the step's critical path (the F side of a kick_sf) takes the lane's
+// stream of the greatest priority; the lane's fsi(S) steps take its stream of the lowest, so
+// that they yield to the recursion and to the kick_sf passes of the levels below.
 struct Branch {
     frost_ctx *c;
     Lane *B;
     Lane exec;
     bool concurrent;
     bool open = false;
-    Branch(frost_ctx *c_, Lane *B_) : c(c_), B(B_), exec(*B_)
+    Branch(frost_ctx *c_, Lane *B_, bool critical = false) : c(c_), B(B_), exec(*B_)
     {
         concurrent = c->branch_streams && !c->timing;
         if (!concurrent) exec.s = c->stream;
+        else if (critical && B_->shi) exec.s = B_->shi;
     }
     // the branch continues after everything issued so far on the context stream
     void fork()
     {
         if (!concurrent) return;
         cudaEventRecord(B->ev_fork, c->stream);
-        cudaStreamWaitEvent(B->s, B->ev_fork, 0);
+        cudaStreamWaitEvent(exec.s, B->ev_fork, 0);
         open = true;
     }
     // the context stream continues after everything issued on the branch
     void join()
     {
         if (!open) return;
-        cudaEventRecord(B->ev_join, B->s);
+        cudaEventRecord(B->ev_join, exec.s);
         cudaStreamWaitEvent(c->stream, B->ev_join, 0);
         open = false;
     }
@@ -833,7 +843,7 @@ void kick_sf(frost_ctx *c, Lane &M, Lane *Bl, const int32_t *S, int nS, const in
     if (nS <= 0 || nF <= 0) return;
     pack_acc(c, M, S, nS, M.recA);
     pack_acc(c, M, F, nF, M.recB);
-    Branch br(c, Bl ? Bl : &M);
+    Branch br(c, Bl ? Bl : &M, true);
     if (!Bl) br.concurrent = false;
     Lane &X = Bl ? br.exec : M;
     if (!gradient) {
@@ -949,6 +959,7 @@ frost_status branch_lane(frost_ctx *c, int depth, Lane **out)
         int lo = 0, hi = 0;
         FROST_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
         FROST_CUDA(cudaStreamCreateWithPriority(&B.s, cudaStreamNonBlocking, lo));
+        FROST_CUDA(cudaStreamCreateWithPriority(&B.shi, cudaStreamNonBlocking, hi));
         FROST_CUDA(cudaEventCreateWithFlags(&B.ev_fork, cudaEventDisableTiming));
         FROST_CUDA(cudaEventCreateWithFlags(&B.ev_join, cudaEventDisableTiming));
         FROST_TRY(alloc_lane_buffers(c, B));

@@ -958,7 +958,12 @@ frost_status branch_lane(frost_ctx *c, int depth, Lane **out)
     if (!B.s) {
         int lo = 0, hi = 0;
         FROST_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-        FROST_CUDA(cudaStreamCreateWithPriority(&B.s, cudaStreamNonBlocking, lo));
+        // fsi(S) of level d must end before that level's next kick_sf, which comes after the whole
+        // recursion below it: the outer the level, the more slack, so the lower the priority
+        // (lowest at the top level, one step up per level, always below the greatest, which the
+        // kick_sf passes of every level take)
+        const int prio = (lo > hi) ? lo - std::min(depth, lo - hi - 1) : lo;
+        FROST_CUDA(cudaStreamCreateWithPriority(&B.s, cudaStreamNonBlocking, prio));
         FROST_CUDA(cudaStreamCreateWithPriority(&B.shi, cudaStreamNonBlocking, hi));
         FROST_CUDA(cudaEventCreateWithFlags(&B.ev_fork, cudaEventDisableTiming));
         FROST_CUDA(cudaEventCreateWithFlags(&B.ev_join, cudaEventDisableTiming));

@@ -93,6 +93,9 @@ constexpr int kBatchTeamBlocks = 8;
 // frost_opts.sym_cross = 0), and cross pairs of lists from this many pairs on the symmetric
 // cross prepass
 constexpr int kSymTstepMinN = 8192;
+// the smallest j-split, in waves of blocks, of the one-sided pair passes (64k step: 63.9 ms per
+// step with the autotuned 1-8 waves, 62.8-62.9 with at least 16 or at least 32)
+constexpr int kMinSplitWaves = 16;
 constexpr int64_t kSymCrossPrepassMinPairs = int64_t(1) << 26;
 // the symmetric force-gradient kick_sf in the default mode: for S x F up to this many pairs,
 // where one symmetric launch is faster than the two one-sided directions on two streams (on
@@ -220,6 +223,7 @@ SplitShape shape_for(const frost_ctx *c, int kind, int n_a, int n_s, int waves =
                      int row = -1)
 {
     if (row < 0) row = kind;
+    const bool chosen = waves <= 0;  // not a candidate the autotuner is timing
     if (waves <= 0 && row >= 0 && row < TUNE_ROWS) {
         const int t = c->tune_w[row][log2_floor(std::max(n_a, 1))];
         if (t != 0) {
@@ -228,6 +232,11 @@ SplitShape shape_for(const frost_ctx *c, int kind, int n_a, int n_s, int waves =
         }
     }
     if (waves <= 0) waves = 8;
+    // Short blocks: the passes of the concurrent branch lanes hold SM slots that the
+    // critical path (the recursion and the kick_sf passes, on streams of higher priority)
+    // takes as they free; the finer the j-split, the sooner.  The floor does not depend on
+    // the branch or timing mode, so every mode runs the same shapes (and gives the same bits).
+    if (chosen) waves = std::max(waves, kMinSplitWaves);
     if (!c->mixed) small = 0;
     if (small < 0) {
         const long long nblk = (n_a + ipb(c) - 1) / ipb(c);

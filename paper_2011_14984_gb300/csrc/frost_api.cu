@@ -982,13 +982,24 @@ frost_status branch_lane(frost_ctx *c, int depth, Lane **out)
     return FROST_OK;
 }
 
-// Algorithm hhs-fsi on the set P (device list, nP entries) with pivot step tau.
-// The operators of fsi(S, tau/2) and hhs_fsi(F, tau/2) act on disjoint particles (H_S holds
-// only S, H_F only F), so each fsi(S) runs on the level's branch lane concurrently with the
-// recursion into F on the context stream; the kick_sf between them joins both.  The
-// arithmetic, and so every result, is that of the serial order.
-frost_status hhs_fsi(frost_ctx *c, const int32_t *P, int nP, double tau, int depth)
+// The first part of hhs_fsi(P, tau): nothing for an empty set, the single-block subtree
+// launch for a small set, else the time-step pass and the partition of a grid level, issued
+// on the context stream without waiting for them.  done: nothing is left for hhs_tail.
+struct HhsHead {
+    bool done = true;
+    const int32_t *P = nullptr;
+    int nP = 0;
+    double tau = 0.0;
+    int depth = 0;
+};
+
+frost_status hhs_head(frost_ctx *c, const int32_t *P, int nP, double tau, int depth, HhsHead &h)
 {
+    h = HhsHead();
+    h.P = P;
+    h.nP = nP;
+    h.tau = tau;
+    h.depth = depth;
     if (nP <= 0) return FROST_OK;
     if (depth > c->max_depth)
         return fail(FROST_EDEPTH, "hhs_fsi deeper than max_depth=%d (|P|=%d, tau_pivot=%g)",
@@ -1006,10 +1017,38 @@ frost_status hhs_fsi(frost_ctx *c, const int32_t *P, int nP, double tau, int dep
     }
     FROST_TRY(ensure_level(c, depth));
     Lane &M = c->main;
-    int32_t *S = c->lvS[depth], *F = c->lvF[depth];
     pass_tstep(c, M, P, nP, c->tau);
-    launch_partition(M.s, P, nP, c->tau, tau, S, F, c->dmisc->counts);
+    launch_partition(M.s, P, nP, c->tau, tau, c->lvS[depth], c->lvF[depth], c->dmisc->counts);
     c->st.kernel_launches += 1;
+    h.done = false;
+    return FROST_OK;
+}
+
+frost_status hhs_tail(frost_ctx *c, const HhsHead &h);
+
+// Algorithm hhs-fsi on the set P (device list, nP entries) with pivot step tau.
+frost_status hhs_fsi(frost_ctx *c, const int32_t *P, int nP, double tau, int depth)
+{
+    HhsHead h;
+    FROST_TRY(hhs_head(c, P, nP, tau, depth, h));
+    return hhs_tail(c, h);
+}
+
+// The rest of hhs_fsi(P) after hhs_head: read |S| and |F|, then the kicks, the two fsi(S)
+// steps and the two recursions into F.  The operators of fsi(S, tau/2) and hhs_fsi(F, tau/2)
+// act on disjoint particles (H_S holds only S, H_F only F), so each fsi(S) runs on the level's
+// branch lane concurrently with the recursion into F on the context stream; the kick_sf
+// between them joins both.  The head of the recursion (its time-step pass and partition, or
+// its subtree launch) is issued before the branch's fsi(S), so that the context stream, the
+// critical path, has work while the host issues the branch.  The arithmetic, and so every
+// result, is that of the serial order.
+frost_status hhs_tail(frost_ctx *c, const HhsHead &h)
+{
+    if (h.done) return FROST_OK;
+    const double tau = h.tau;
+    const int depth = h.depth;
+    Lane &M = c->main;
+    int32_t *S = c->lvS[depth], *F = c->lvF[depth];
     FROST_TRY(sync_misc(c));
     const int nS = (int)c->hmisc->counts[0];
     const int nF = (int)c->hmisc->counts[1];
@@ -1028,15 +1067,19 @@ frost_status hhs_fsi(frost_ctx *c, const int32_t *P, int nP, double tau, int dep
     {
         Branch br(c, Bl);
         br.fork();
+        HhsHead child;
+        FROST_TRY(hhs_head(c, F, nF, 0.5 * tau, depth + 1, child));
         fsi(c, br.exec, S, nS, 0.5 * tau, 1);
-        FROST_TRY(hhs_fsi(c, F, nF, 0.5 * tau, depth + 1));
+        FROST_TRY(hhs_tail(c, child));
     }
     kick_sf(c, M, Bl, S, nS, F, nF, 2.0 * tau / 3.0, true, tau);
     {
         Branch br(c, Bl);
         br.fork();
+        HhsHead child;
+        FROST_TRY(hhs_head(c, F, nF, 0.5 * tau, depth + 1, child));
         fsi(c, br.exec, S, nS, 0.5 * tau, 2);
-        FROST_TRY(hhs_fsi(c, F, nF, 0.5 * tau, depth + 1));
+        FROST_TRY(hhs_tail(c, child));
     }
     kick_sf(c, M, Bl, S, nS, F, nF, tau / 6.0, false, tau);
     return FROST_OK;

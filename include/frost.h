@@ -81,7 +81,10 @@ typedef struct {
                                threshold, the two fsi(S) steps run on a stream of their own,
                                concurrently with the recursion hhs_fsi(F) on the context stream
                                (they act on disjoint particles, so the results are those of the
-                               serial order, bit for bit); -1: everything on the context stream.
+                               serial order, bit for bit); likewise, inside the single-block
+                               subtree solver, a set's two fsi(S) steps run on warps 1..7 while
+                               warp 0 advances its fast set of at most 32 particles;
+                               -1: everything on the context stream, in the serial order.
                                With per-kernel timing on, the branches run serially.  The
                                branch streams take the device's lowest priority: give the
                                context a stream of higher priority (cudaStreamCreateWithPriority)
@@ -303,6 +306,11 @@ typedef struct {
     /* gradient pairs evaluated once for both sides (symmetric gradient kick_sf; counted once
      * in grad_pairs, and each served two interactions) */
     int64_t grad_pairs_symmetric;
+    /* fsi(S) steps of the single-block subtree solver that ran on warps 1..7 while warp 0
+     * advanced the fast set F (at most 32 particles) of the same hhs_fsi call: the two
+     * operators act on disjoint particles and commute (Algorithm hhs-fsi); off with
+     * frost_opts.branch_streams = -1 (the serial order, the same result bits) */
+    int64_t subtree_fsi_beside;
 } frost_stats;
 
 frost_status frost_get_stats(frost_ctx *ctx, frost_stats *out);

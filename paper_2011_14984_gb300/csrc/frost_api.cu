@@ -67,7 +67,7 @@ struct Misc {
     int64_t rel[2];     // list relation: bad/duplicate flag, |A cap B|
     double eres[8];     // energy reduction
     unsigned long long sub[8];  // subtree solver counters (acc, grad, tstep pairs, hhs, fsi, depth,
-                                // reused acc pairs, spare)
+                                // reused acc pairs, fsi beside the warp path)
     unsigned long long lev[2][SUBTREE_STAT_LEVELS];  // subtree calls / set sizes per depth
     int err;            // sticky device error word
     int pad;
@@ -174,7 +174,7 @@ struct frost_ctx {
     int64_t g_steps = 0;
     double *d_ecl = nullptr;                         // per-cluster energy sums [n_clusters][8]
     std::vector<double> h_ecl;
-    unsigned long long sub_seen[7] = {0, 0, 0, 0, 0, 0, 0};
+    unsigned long long sub_seen[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     unsigned long long lev_seen[2][SUBTREE_STAT_LEVELS] = {};
     Misc *dmisc = nullptr, *hmisc = nullptr;
     std::vector<int32_t *> lvS, lvF;                 // per-level slow/fast lists
@@ -341,7 +341,8 @@ frost_status sync_misc(frost_ctx *c)
     c->st.fsi_calls += (int64_t)(sub[4] - c->sub_seen[4]);
     if ((int)sub[5] > c->st.max_depth_seen) c->st.max_depth_seen = (int)sub[5];
     c->st.acc_pairs_reused += (int64_t)(sub[6] - c->sub_seen[6]);
-    for (int k = 0; k < 7; ++k) c->sub_seen[k] = sub[k];
+    c->st.subtree_fsi_beside += (int64_t)(sub[7] - c->sub_seen[7]);
+    for (int k = 0; k < 8; ++k) c->sub_seen[k] = sub[k];
     for (int q = 0; q < 2; ++q)
         for (int L = 0; L < SUBTREE_STAT_LEVELS; ++L) {
             const unsigned long long cur = c->hmisc->lev[q][L];
@@ -948,6 +949,7 @@ void hhs_subtree(frost_ctx *c, const int32_t *P, int nP, double tau, int depth)
     a.n_steps = 1;
     a.team_blocks = c->subtree_blocks;
     a.xchg = c->d_xchg;
+    a.overlap = c->branch_streams;
     {
         TimedScope ts(c, c->stream, PASS_SUBTREE, 0);
         // a launch error is also left for the cudaGetLastError() of the calling entry point
@@ -1672,6 +1674,7 @@ static frost_status batch_step(frost_ctx *c, double dt_pivot, int64_t n_steps)
     a.recB = c->recB;
     a.offsets = c->d_offsets;
     a.xchg = c->d_xchg;
+    a.overlap = c->branch_streams;
     a.tau0 = dt_pivot;
     a.depth0 = 0;
     a.n_steps = (int)n_steps;

@@ -262,8 +262,8 @@ struct SubtreeArgs {
     double G, eta, eps2;
     int max_depth;
     int *err;
-    unsigned long long *counters;  // [7]: acc, grad, tstep pairs, hhs calls, fsi calls, max depth,
-                                   // reused acc pairs
+    unsigned long long *counters;  // [8]: acc, grad, tstep pairs, hhs calls, fsi calls, max depth,
+                                   // reused acc pairs, fsi calls run beside the warp path
     unsigned long long *levels;    // [2][SUBTREE_STAT_LEVELS]: calls and set sizes per depth
     double *aC;                    // [3][N] by particle: a^SS kept from the first fsi(S) to the second
     // workspace (per particle: perm, tmp int32; tau double; aA..atB [3] doubles; wA, wB
@@ -284,6 +284,9 @@ struct SubtreeArgs {
     // share one set; xchg: one int per team (a status word between the team's blocks)
     int team_blocks = 1;
     int *xchg = nullptr;
+    // one-block teams: the FSI steps of a slow set on warps 1..7 beside warp 0's subtree of a
+    // fast set of at most 32 particles (same results as the serial order)
+    bool overlap = false;
     double tau0;
     int depth0;
     int n_steps;

@@ -38,6 +38,10 @@ struct SubParams {
     unsigned long long *levels;    // [2][SUBTREE_STAT_LEVELS]: calls and set sizes per depth
     int crank, csize;              // this block's rank in its thread-block cluster, cluster size
     double *aC;                    // [3][N] by particle: a^SS kept between the two fsi(S) of a call
+    // the team's threads within each block: tbase .. tbase + tcount - 1 (the whole block, or
+    // warps 1..7 of a one-block team while warp 0 runs a fast set's subtree beside them)
+    int tbase, tcount;
+    int overlap;                   // run fsi(S) beside the warp path of F (one-block teams)
 };
 
 struct SubWork {
@@ -53,22 +57,31 @@ struct Counts {
     unsigned long long acc, grad, tstep, hhs, fsi;
     int maxdepth;
     unsigned long long reused;
+    unsigned long long beside;  // fsi(S) steps run on warps 1..7 beside the warp path of F
 };
 
 // ---- the team of one set: a block, or the blocks of a thread-block cluster -----------------
 // Every helper below is called by all threads of the team with the same arguments, splits its
 // work over the team's threads and ends with a team barrier, so that all control decisions,
-// taken from data read after a barrier, are the same in every block of a cluster.
+// taken from data read after a barrier, are the same in every block of a cluster.  A one-block
+// team may also be the sub-team of warps 1..7 (tbase 32, tcount 224), which runs the FSI steps
+// of a slow set while warp 0 advances the fast set; its barrier is the named barrier 1.
 
-__device__ __forceinline__ int t_id(const SubParams &p) { return p.crank * SB + threadIdx.x; }
-__device__ __forceinline__ int t_n(const SubParams &p) { return p.csize * SB; }
+constexpr int SUB_BARRIER = 1;    // named barrier of the warps 1..7 sub-team (0 is __syncthreads)
+
+__device__ __forceinline__ int t_id(const SubParams &p) { return p.crank * p.tcount + ((int)threadIdx.x - p.tbase); }
+__device__ __forceinline__ int t_n(const SubParams &p) { return p.csize * p.tcount; }
+__device__ __forceinline__ bool t_lead(const SubParams &p) { return (int)threadIdx.x == p.tbase; }
 
 // team barrier: with more than one block, the cluster barrier (release / acquire at cluster
-// scope orders the global-memory results of every block before the next step)
+// scope orders the global-memory results of every block before the next step); a sub-team
+// waits at its named barrier, which orders memory among its threads as __syncthreads does
 __device__ __forceinline__ void t_sync(const SubParams &p)
 {
     if (p.csize > 1) {
         asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+    } else if (p.tcount != SB) {
+        asm volatile("bar.sync %0, %1;" ::"n"(SUB_BARRIER), "r"(p.tcount) : "memory");
     } else {
         __syncthreads();
     }
@@ -102,12 +115,14 @@ constexpr int MT_MAX = SB;
 struct MtMap {
     int T, g, l, ngroups, rounds;
 };
+// T depends on the size of the whole team (csize blocks of SB threads), not on that of a
+// sub-team, so a pass gives the same bits on either; a sub-team takes more rounds instead
 __device__ __forceinline__ MtMap mt_map(const SubParams &p, int nA)
 {
     int P2 = 1;
     while (P2 < nA) P2 <<= 1;
     MtMap m;
-    m.T = max(1, min(32, t_n(p) / P2));
+    m.T = max(1, min(32, p.csize * SB / P2));
     m.g = t_id(p) / m.T;
     m.l = t_id(p) % m.T;
     m.ngroups = t_n(p) / m.T;
@@ -365,7 +380,7 @@ __device__ __noinline__ void b_acc(const SubParams &p, const SubWork &w, const i
     if (!self) b_pack_pos<MIXED>(p, B, nB, w.recB);
     t_sync(p);
     const int sp = self ? 1 : 0;
-    if (p.csize > 1 || nA <= MT_MAX) {
+    if (p.csize > 1 || nA <= MT_MAX || p.tcount != SB) {
         mt_acc<MIXED>(p, w.recA, self ? w.recA : w.recB, nA, nB, self, accurate, out, wout, badbit);
     } else if (MIXED) {
         const float4 *ir = w.recA, *jr = self ? w.recA : w.recB;
@@ -408,7 +423,7 @@ __device__ __noinline__ void b_acc(const SubParams &p, const SubWork &w, const i
         }
     }
     t_sync(p);
-    if (threadIdx.x == 0) cnt.acc += self ? (unsigned long long)nA * (nA - 1) : (unsigned long long)nA * nB;
+    if (t_lead(p)) cnt.acc += self ? (unsigned long long)nA * (nA - 1) : (unsigned long long)nA * nB;
 }
 
 // Gradient pass of A against B with a_A, a_B ([3][n]); at[3][nA] = a_A + eps^2/48 g
@@ -437,7 +452,7 @@ __device__ __noinline__ void b_grad(const SubParams &p, const SubWork &w, const 
     const int sp = self ? 1 : 0;
     const double c = eps_grad * eps_grad / 48.0;
     const double scale = 2.0 * p.G;
-    if (p.csize > 1 || nA <= MT_MAX) {
+    if (p.csize > 1 || nA <= MT_MAX || p.tcount != SB) {
         mt_grad<MIXED>(p, w.recA, self ? w.recA : w.recB, nA, nB, self, aA, MIXED ? wmax : nullptr, c, at, badbit);
     } else if (MIXED) {
         const float4 *ir = w.recA, *jr = self ? w.recA : w.recB;
@@ -477,7 +492,7 @@ __device__ __noinline__ void b_grad(const SubParams &p, const SubWork &w, const 
         }
     }
     t_sync(p);
-    if (threadIdx.x == 0) cnt.grad += self ? (unsigned long long)nA * (nA - 1) : (unsigned long long)nA * nB;
+    if (t_lead(p)) cnt.grad += self ? (unsigned long long)nA * (nA - 1) : (unsigned long long)nA * nB;
 }
 
 // symmetrised time-steps of the set P into tau[n]
@@ -501,7 +516,7 @@ __device__ __noinline__ void b_tstep(const SubParams &p, const SubWork &w, const
         else pack_tstep_fp64_one(k, P, n, p.x, p.v, p.m, p.N, p.G, (double4_32a *)w.recA, acc);
     }
     t_sync(p);
-    if (p.csize > 1 || n <= MT_MAX) {
+    if (p.csize > 1 || n <= MT_MAX || p.tcount != SB) {
         mt_tstep<MIXED, SYM>(p, w.recA, n, tau);
     } else if (MIXED) {
         for (int ib = 0; ib < n; ib += SIB) {
@@ -533,7 +548,7 @@ __device__ __noinline__ void b_tstep(const SubParams &p, const SubWork &w, const
         }
     }
     t_sync(p);
-    if (threadIdx.x == 0) cnt.tstep += (unsigned long long)n * (n - 1);
+    if (t_lead(p)) cnt.tstep += (unsigned long long)n * (n - 1);
 }
 
 // stable in-place partition of P[0..n) by tau >= pivot; returns |S| (S first, then F).  Every
@@ -623,10 +638,10 @@ __device__ __noinline__ void b_fsi(const SubParams &p, const SubWork &w, const i
                                    int cache = 0)
 {
     if (nS <= 0) return;
-    if (threadIdx.x == 0) cnt.fsi += 1;
+    if (t_lead(p)) cnt.fsi += 1;
     if (nS < 2) cache = 0;
     if (cache == 2) {
-        if (threadIdx.x == 0) cnt.reused += (unsigned long long)nS * (nS - 1);
+        if (t_lead(p)) cnt.reused += (unsigned long long)nS * (nS - 1);
         for (int k = t_id(p); k < nS; k += t_n(p)) {
             const int i = S[k];
             for (int c = 0; c < 3; ++c)
@@ -1084,6 +1099,39 @@ __device__ __noinline__ int warp_hhs(const SubParams &p, const int32_t *Sg, int 
     return err;
 }
 
+// Whether a frame of a one-block team runs its fsi(S, tau/2) on warps 1..7 while warp 0 runs
+// the whole subtree of hhs_fsi(F, tau/2) (Algorithm hhs-fsi).  The two operators act on the
+// disjoint sets S and F (H_S holds only S, H_F only F) and commute; the warp path keeps F in
+// registers and touches no workspace, and the sub-team sums in the team's order (mt_map), so
+// the result is that of the serial order bit for bit.  sp: the frames on the stack, which the
+// serial order would push F onto.
+__device__ __forceinline__ bool f_beside(const SubParams &p, int nS, int nF, int sp)
+{
+    return p.overlap && p.csize == 1 && nS > 0 && nS <= MT_MAX && nF > 0 && nF <= WARP_N && sp < MAXD;
+}
+
+// fsi(S, tau/2) (cache as in b_fsi) on warps 1..7 beside warp 0's subtree of F = S + nS (nF
+// particles, depth + 1); ends with a block barrier, the warp path's status in *s_e
+template <bool MIXED, int SYM>
+__device__ __noinline__ void fsi_beside_warp(const SubParams &p, const SubWork &w, const int32_t *S, int nS, int nF,
+                                             double ftau, int depth, Counts &cnt, int cache, int *s_e)
+{
+    if (threadIdx.x < 32) {
+        const int e = warp_hhs<MIXED, SYM>(p, S + nS, nF, 0.5 * ftau, depth + 1, cnt);
+        if (threadIdx.x == 0) {
+            if (e) atomicOr(p.err, e);
+            *s_e = e;
+        }
+    } else {
+        SubParams q = p;
+        q.tbase = 32;
+        q.tcount = SB - 32;
+        b_fsi<MIXED>(q, w, S, nS, 0.5 * ftau, cnt, cache);
+        if (t_lead(q)) cnt.beside += 1;
+    }
+    __syncthreads();
+}
+
 // One team (a block, or the blocks of one thread-block cluster): n_steps calls of
 // hhs_fsi(P, tau0) at depth depth0.  Single-set mode: P, n given, workspace from particle 0.
 // Batch mode (offsets != NULL): team t takes cluster c = (cl_index ? cl_index[t] : t), the
@@ -1100,7 +1148,7 @@ __global__ void __launch_bounds__(SB, MINB) k_hhs_subtree(SubParams p0, SubWork 
 {
     __shared__ int f_lo[MAXD], f_n[MAXD], f_ns[MAXD], f_pc[MAXD], f_depth[MAXD];
     __shared__ double f_tau[MAXD];
-    __shared__ int s_sp, s_abort;
+    __shared__ int s_sp, s_abort, s_we;
     const int tid = threadIdx.x;
     SubParams p = p0;
     {
@@ -1129,7 +1177,7 @@ __global__ void __launch_bounds__(SB, MINB) k_hhs_subtree(SubParams p0, SubWork 
     w.wB += off;
     w.recA += 6 * (size_t)off;  // 96 bytes per particle
     w.recB += 6 * (size_t)off;
-    Counts cnt = {0, 0, 0, 0, 0, depth0, 0};
+    Counts cnt = {0, 0, 0, 0, 0, depth0, 0, 0};
     if (tid == 0) s_abort = 0;
     for (int step = 0; step < n_steps; ++step) {
         for (int k = t_id(p); k < n; k += t_n(p)) w.perm[k] = offsets ? off + k : P[k];
@@ -1191,29 +1239,49 @@ __global__ void __launch_bounds__(SB, MINB) k_hhs_subtree(SubParams p0, SubWork 
                 nS = b_partition(p, S, fn, w.tau, ftau, w.tmp);
                 const int nF = fn - nS;
                 b_kick_sf<MIXED>(p, w, S, nS, S + nS, nF, ftau / 6.0, false, ftau, cnt);
-                b_fsi<MIXED>(p, w, S, nS, 0.5 * ftau, cnt, 1);
-                if (tid == 0) {
-                    f_ns[top] = nS;
-                    f_pc[top] = 1;
-                    if (nF > 0) {
-                        if (s_sp >= MAXD) {
-                            atomicOr(p.err, ERR_DEPTH);
-                            s_abort = 1;
-                        } else {
-                            f_lo[s_sp] = lo + nS;
-                            f_n[s_sp] = nF;
-                            f_ns[s_sp] = 0;
-                            f_pc[s_sp] = 0;
-                            f_depth[s_sp] = depth + 1;
-                            f_tau[s_sp] = 0.5 * ftau;
-                            s_sp += 1;
+                if (f_beside(p, nS, nF, top + 1)) {
+                    // fsi(S, tau/2) beside the first hhs_fsi(F, tau/2), which is then done
+                    fsi_beside_warp<MIXED, SYM>(p, w, S, nS, nF, ftau, depth, cnt, 1, &s_we);
+                    if (tid == 0) {
+                        f_ns[top] = nS;
+                        f_pc[top] = 1;
+                        if (s_we & ERR_DEPTH) s_abort = 1;
+                    }
+                } else {
+                    b_fsi<MIXED>(p, w, S, nS, 0.5 * ftau, cnt, 1);
+                    if (tid == 0) {
+                        f_ns[top] = nS;
+                        f_pc[top] = 1;
+                        if (nF > 0) {
+                            if (s_sp >= MAXD) {
+                                atomicOr(p.err, ERR_DEPTH);
+                                s_abort = 1;
+                            } else {
+                                f_lo[s_sp] = lo + nS;
+                                f_n[s_sp] = nF;
+                                f_ns[s_sp] = 0;
+                                f_pc[s_sp] = 0;
+                                f_depth[s_sp] = depth + 1;
+                                f_tau[s_sp] = 0.5 * ftau;
+                                s_sp += 1;
+                            }
                         }
                     }
                 }
             } else if (pc == 1) {
                 const int nF = fn - nS;
                 b_kick_sf<MIXED>(p, w, S, nS, S + nS, nF, 2.0 * ftau / 3.0, true, ftau, cnt);
-                if (tid == 0) {
+                if (f_beside(p, nS, nF, top + 1)) {
+                    // the second fsi(S, tau/2) beside the second hhs_fsi(F, tau/2), then the
+                    // closing kick_sf: the frame is done
+                    fsi_beside_warp<MIXED, SYM>(p, w, S, nS, nF, ftau, depth, cnt, 2, &s_we);
+                    const int e = s_we;
+                    if (!(e & ERR_DEPTH)) b_kick_sf<MIXED>(p, w, S, nS, S + nS, nF, ftau / 6.0, false, ftau, cnt);
+                    if (tid == 0) {
+                        if (e & ERR_DEPTH) s_abort = 1;
+                        s_sp -= 1;
+                    }
+                } else if (tid == 0) {
                     f_pc[top] = 2;
                     if (nF > 0) {
                         f_lo[s_sp] = lo + nS;
@@ -1236,7 +1304,8 @@ __global__ void __launch_bounds__(SB, MINB) k_hhs_subtree(SubParams p0, SubWork 
         __syncthreads();
         if (s_abort) break;
     }
-    if (tid == 0 && p.crank == 0) {
+    // thread 32 leads the sub-team of warps 1..7 and holds the counts of its passes
+    if ((tid == 0 || (p.overlap && tid == 32)) && p.crank == 0) {
         atomicAdd(&p.counters[0], cnt.acc);
         atomicAdd(&p.counters[1], cnt.grad);
         atomicAdd(&p.counters[2], cnt.tstep);
@@ -1244,6 +1313,7 @@ __global__ void __launch_bounds__(SB, MINB) k_hhs_subtree(SubParams p0, SubWork 
         atomicAdd(&p.counters[4], cnt.fsi);
         atomicMax(&p.counters[5], (unsigned long long)cnt.maxdepth);
         atomicAdd(&p.counters[6], cnt.reused);
+        atomicAdd(&p.counters[7], cnt.beside);
     }
 }
 
@@ -1264,6 +1334,9 @@ cudaError_t launch_subtree(cudaStream_t s, bool mixed, int sym, const SubtreeArg
     p.counters = a.counters;
     p.levels = a.levels;
     p.aC = a.aC;
+    p.tbase = 0;
+    p.tcount = SB;
+    p.overlap = a.overlap ? 1 : 0;
     SubWork w;
     w.perm = a.perm;
     w.tmp = a.tmp;

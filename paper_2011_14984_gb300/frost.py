@@ -52,7 +52,8 @@ class frost_stats(ctypes.Structure):
                 ("timed_pairs", ctypes.c_int64 * 4), ("subtree_launches", ctypes.c_int64),
                 ("level_calls", ctypes.c_int64 * 48), ("level_particles", ctypes.c_int64 * 48),
                 ("acc_pairs_reused", ctypes.c_int64), ("subtree_pairs", ctypes.c_int64 * 3),
-                ("acc_pairs_symmetric", ctypes.c_int64), ("grad_pairs_symmetric", ctypes.c_int64)]
+                ("acc_pairs_symmetric", ctypes.c_int64), ("grad_pairs_symmetric", ctypes.c_int64),
+                ("subtree_fsi_beside", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -858,6 +858,51 @@ def test_subtree_solver_trajectory_parity_fp64(subtree_max, sym):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_subtree_solver_fsi_beside_the_warp_path_is_bit_identical(precision):
+    """Inside the single-block solver, a set's two fsi(S, tau/2) steps run on warps 1..7 while
+    warp 0 advances the fast set F (at most 32 particles) through hhs_fsi(F, tau/2): H_S and H_F
+    act on disjoint particles (Algorithm hhs-fsi).  The whole recursion of a 700-particle
+    Kroupa sphere in one block, 6 top-level steps: the state is the serial order's
+    (branch_streams = -1) bit for bit, with the same pair counts and depth; the overlap ran;
+    and FP64 stays within the oracle's 1e-10."""
+    m, x, v = ics.plummer(700, 31, masses=ics.kroupa_masses(700, 31))
+    out = {}
+    for branch in (0, -1):
+        f = F(m, x, v, precision=precision, eta=0.2, subtree_max=1 << 30, branch_streams=branch)
+        f.step(2.0 ** -7, 6)
+        xg, vg, _ = f.state()
+        st = f.stats()
+        out[branch] = (xg, vg, st)
+        f.close()
+    st0, st1 = out[0][2], out[-1][2]
+    assert st0["subtree_launches"] == 6 and st0["subtree_fsi_beside"] > 0, st0["subtree_fsi_beside"]
+    assert st1["subtree_fsi_beside"] == 0
+    assert np.array_equal(out[0][0], out[-1][0]) and np.array_equal(out[0][1], out[-1][1])
+    for k in ("acc_pairs", "grad_pairs", "tstep_pairs", "hhs_calls", "fsi_calls", "acc_pairs_reused",
+              "max_depth_seen"):
+        assert st0[k] == st1[k], k
+    if precision == "fp64":
+        xo, vo = oracle.steps(m, x, v, 2.0 ** -7, 6, eta=0.2)
+        assert np.max(np.abs(out[0][0] - xo)) < 1e-10 and np.max(np.abs(out[0][1] - vo)) < 1e-9
+
+
+def test_cluster_batch_fsi_beside_the_warp_path_is_bit_identical():
+    """The batch teams of one block take the same overlap: a mixed-precision batch of six
+    clusters of 40 to 300 particles, after one captured and one replayed step, equals the
+    serial order bit for bit."""
+    off, m, x, v = _small_batch()
+    out = {}
+    for branch in (0, -1):
+        f = F(m, x, v, precision="mixed", eta=0.2, offsets=off, branch_streams=branch)
+        f.step(2.0 ** -6, 1)
+        f.step(2.0 ** -6, 1)
+        out[branch] = f.state()[:2] + (f.stats()["subtree_fsi_beside"],)
+        f.close()
+    assert out[0][2] > 0 and out[-1][2] == 0
+    assert np.array_equal(out[0][0], out[-1][0]) and np.array_equal(out[0][1], out[-1][1])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_subtree_solver_on_a_block_cluster(precision):
     """A single-set solver launch spread over an 8-block thread-block cluster (cluster
     barriers, the group path for every pass): the trajectory of the one-block solver, to the

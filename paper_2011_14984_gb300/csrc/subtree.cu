@@ -69,6 +69,9 @@ struct Counts {
 
 constexpr int SUB_BARRIER = 1;    // named barrier of the warps 1..7 sub-team (0 is __syncthreads)
 
+// G times a sum; G = 1 (Henon units) needs no FP64 multiply and gives the same bits
+__device__ __forceinline__ double g_scale(double G, double r) { return G == 1.0 ? r : G * r; }
+
 __device__ __forceinline__ int t_id(const SubParams &p) { return p.crank * p.tcount + ((int)threadIdx.x - p.tbase); }
 __device__ __forceinline__ int t_n(const SubParams &p) { return p.csize * p.tcount; }
 __device__ __forceinline__ bool t_lead(const SubParams &p) { return (int)threadIdx.x == p.tbase; }
@@ -222,7 +225,7 @@ __device__ __noinline__ void mt_acc(const SubParams &p, const void *irec, const 
         if (active && l == 0) {
             bool ok = true;
             for (int k = 0; k < 3; ++k) {
-                const double a = p.G * r[k];
+                const double a = g_scale(p.G, r[k]);
                 ok = ok && isfinite(a);
                 out[k * nA + i] = a;
             }
@@ -395,7 +398,7 @@ __device__ __noinline__ void b_acc(const SubParams &p, const SubWork &w, const i
                 if (i < nA) {
                     bool ok = true;
                     for (int c = 0; c < 3; ++c) {
-                        const double a = p.G * res[k][c];
+                        const double a = g_scale(p.G, res[k][c]);
                         ok = ok && isfinite(a);
                         out[c * nA + i] = a;
                     }
@@ -414,7 +417,7 @@ __device__ __noinline__ void b_acc(const SubParams &p, const SubWork &w, const i
             if (i < nA) {
                 bool ok = true;
                 for (int c = 0; c < 3; ++c) {
-                    const double a = p.G * res[c];
+                    const double a = g_scale(p.G, res[c]);
                     ok = ok && isfinite(a);
                     out[c * nA + i] = a;
                 }
@@ -703,7 +706,24 @@ struct WLane {
     double x[3], v[3], m;
     double o[3];
     double xr[3];  // x - o, drifted with the increments of x (mixed records only)
+    // the lane's float-float position record (high part and remainder of x - o) and its FP32
+    // mass, renewed whenever the lane drifts: every pass between two drifts reads the same
+    // bits, so they are split once (FP64 conversions hold a sub-partition's FP64 unit for
+    // about 64 cycles a warp instruction)
+    float rh[3], rl[3], mf;
+    double ac[3];  // a^SS of the lane's slow set, kept from the first fsi(S) to the second
 };
+
+// the lane's float-float record from x - o (mixed passes)
+__device__ __forceinline__ void w_record(WLane &L)
+{
+    for (int c = 0; c < 3; ++c) {
+        L.rh[c] = (float)L.xr[c];
+        L.rl[c] = (float)(L.xr[c] - (double)L.rh[c]);
+    }
+    L.mf = (float)L.m;
+}
+
 
 __device__ __forceinline__ float wsh(float v, int j) { return __shfl_sync(0xffffffffu, v, j); }
 __device__ __forceinline__ double wshd(double v, int j) { return __shfl_sync(0xffffffffu, v, j); }
@@ -725,13 +745,12 @@ __device__ __noinline__ void w_acc(const SubParams &p, const WLane &L, unsigned 
         float ax[1] = {0.f}, ay[1] = {0.f}, az[1] = {0.f};
         int c = 0;
         AccMixedI<1> I;
-        const double rx = L.xr[0], ry = L.xr[1], rz = L.xr[2];
-        float hx = (float)rx, hy = (float)ry, hz = (float)rz;
+        const float hx = L.rh[0], hy = L.rh[1], hz = L.rh[2];
         I.xh[0] = hx; I.yh[0] = hy; I.zh[0] = hz;
-        I.xl[0] = (float)(rx - (double)hx);
-        I.yl[0] = (float)(ry - (double)hy);
-        I.zl[0] = (float)(rz - (double)hz);
-        const float mf = (float)L.m;
+        I.xl[0] = L.rl[0];
+        I.yl[0] = L.rl[1];
+        I.zl[0] = L.rl[2];
+        const float mf = L.mf;
         unsigned M = U;
         while (M) {
             const int j = __ffs(M) - 1;
@@ -760,7 +779,7 @@ __device__ __noinline__ void w_acc(const SubParams &p, const WLane &L, unsigned 
             acc_fp64_j<true>(J, I, p.eps2, j, lane, res[0], res[1], res[2]);
         }
     }
-    for (int q = 0; q < 3; ++q) a[q] = p.G * res[q];
+    for (int q = 0; q < 3; ++q) a[q] = g_scale(p.G, res[q]);
     wmax = wm[0];
 }
 
@@ -785,7 +804,7 @@ __device__ __noinline__ void w_grad(const SubParams &p, const WLane &L, unsigned
         I.alx[0] = (float)(ai[0] - (double)I.ahx[0]);
         I.aly[0] = (float)(ai[1] - (double)I.ahy[0]);
         I.alz[0] = (float)(ai[2] - (double)I.ahz[0]);
-        const float mf = (float)L.m;
+        const float mf = L.mf;
         const float thrs[1] = {thr};
         BigSlots<1> big;
         init_big(big, lane);
@@ -857,16 +876,15 @@ __device__ __noinline__ double w_tstep(const SubParams &p, const WLane &L, unsig
     }
     if (MIXED) {
         TstepMixedI<1> I;
-        const double rx = L.xr[0], ry = L.xr[1], rz = L.xr[2];
-        const float hx = (float)rx, hy = (float)ry, hz = (float)rz;
+        const float hx = L.rh[0], hy = L.rh[1], hz = L.rh[2];
         I.xh[0] = hx; I.yh[0] = hy; I.zh[0] = hz;
-        I.xl[0] = (float)(rx - (double)hx);
-        I.yl[0] = (float)(ry - (double)hy);
-        I.zl[0] = (float)(rz - (double)hz);
+        I.xl[0] = L.rl[0];
+        I.yl[0] = L.rl[1];
+        I.zl[0] = L.rl[2];
         I.vx[0] = (float)L.v[0]; I.vy[0] = (float)L.v[1]; I.vz[0] = (float)L.v[2];
-        I.gm[0] = (float)(p.G * L.m);
+        I.gm[0] = (p.G == 1.0) ? L.mf : (float)(p.G * L.m);
         I.ax[0] = (float)la[0]; I.ay[0] = (float)la[1]; I.az[0] = (float)la[2];
-        const float mf = (float)L.m;
+        const float mf = L.mf;
         const float eta = (float)p.eta, eta15 = 1.5f * eta;
         float best[1] = {INFINITY}, minr2[1] = {INFINITY};
         unsigned M = P;
@@ -911,25 +929,35 @@ __device__ __forceinline__ void w_kick(WLane &L, bool on, const double (&a)[3], 
 template <bool MIXED>
 __device__ __forceinline__ void w_drift(WLane &L, bool on, double dt)
 {
-    if (on)
+    if (on) {
         for (int c = 0; c < 3; ++c) {
             const double d = __dmul_rn(dt, L.v[c]);
             L.x[c] = __dadd_rn(L.x[c], d);
             if (MIXED) L.xr[c] = __dadd_rn(L.xr[c], d);
         }
+        if (MIXED) w_record(L);
+    }
 }
 
+// cache: 1 keeps the final a^SS in the lanes of S (L.ac), 2 starts from it: S has not moved
+// between the two fsi(S) of one hhs_fsi call, and the frames in between only touch the lanes
+// of F, which are not in S (the same a^SS, bit for bit, as a new pass)
 template <bool MIXED>
-__device__ void w_fsi(const SubParams &p, WLane &L, unsigned S, double dt, Counts &cnt)
+__device__ void w_fsi(const SubParams &p, WLane &L, unsigned S, double dt, Counts &cnt, int cache = 0)
 {
     if (!S) return;
     const int lane = threadIdx.x & 31;
     const bool in = (S >> lane) & 1u;
     const unsigned src = in ? S : 0u;
     const unsigned long long ns = (unsigned long long)__popc(S);
+    if (ns < 2) cache = 0;
     double a[3], at[3], g[3];
     float wm;
-    w_acc<MIXED>(p, L, S, src, false, a, wm);
+    if (cache == 2) {
+        for (int q = 0; q < 3; ++q) a[q] = L.ac[q];
+    } else {
+        w_acc<MIXED>(p, L, S, src, false, a, wm);
+    }
     w_kick(L, in, a, dt / 6.0);
     w_drift<MIXED>(L, in, 0.5 * dt);
     w_acc<MIXED>(p, L, S, src, true, a, wm);
@@ -939,11 +967,14 @@ __device__ void w_fsi(const SubParams &p, WLane &L, unsigned S, double dt, Count
     w_kick(L, in, at, 2.0 * dt / 3.0);
     w_drift<MIXED>(L, in, 0.5 * dt);
     w_acc<MIXED>(p, L, S, src, false, a, wm);
+    if (cache == 1 && in)
+        for (int q = 0; q < 3; ++q) L.ac[q] = a[q];
     w_kick(L, in, a, dt / 6.0);
     if (lane == 0) {
         cnt.fsi += 1;
-        cnt.acc += 3 * ns * (ns - 1);
+        cnt.acc += (cache == 2 ? 2 : 3) * ns * (ns - 1);
         cnt.grad += ns * (ns - 1);
+        if (cache == 2) cnt.reused += ns * (ns - 1);
     }
 }
 
@@ -1009,7 +1040,9 @@ __device__ __noinline__ int warp_hhs(const SubParams &p, const int32_t *Sg, int 
         }
         L.o[c] = MIXED ? 0.5 * (lo + hi) : 0.0;
         L.xr[c] = L.x[c] - L.o[c];
+        L.ac[c] = 0.0;
     }
+    if (MIXED) w_record(L);
     const unsigned all = (n >= 32) ? 0xffffffffu : ((1u << n) - 1u);
     if (lane == 0) {
         wf_P[0] = all;
@@ -1050,7 +1083,7 @@ __device__ __noinline__ int warp_hhs(const SubParams &p, const int32_t *Sg, int 
                 atomicAdd(&p.levels[SUBTREE_STAT_LEVELS + Lv], np);
             }
             w_kick_sf<MIXED>(p, L, Sn, Fn, ftau / 6.0, false, ftau, cnt);
-            w_fsi<MIXED>(p, L, Sn, 0.5 * ftau, cnt);
+            w_fsi<MIXED>(p, L, Sn, 0.5 * ftau, cnt, 1);
             if (lane == 0) {
                 wf_S[top] = Sn;
                 wf_pc[top] = 1;
@@ -1083,7 +1116,7 @@ __device__ __noinline__ int warp_hhs(const SubParams &p, const int32_t *Sg, int 
                 sp += 1;
             }
         } else {
-            w_fsi<MIXED>(p, L, S, 0.5 * ftau, cnt);
+            w_fsi<MIXED>(p, L, S, 0.5 * ftau, cnt, 2);
             w_kick_sf<MIXED>(p, L, S, F, ftau / 6.0, false, ftau, cnt);
             sp -= 1;
         }

@@ -45,7 +45,10 @@ typedef enum {
     FROST_ENONFINITE = 4,  /* a non-finite input, or a pass produced a non-finite value */
     FROST_ECOINCIDENT = 5, /* two distinct particles at zero separation (unsoftened) */
     FROST_EDEPTH = 6,      /* hhs_fsi recursion deeper than frost_opts.max_depth */
-    FROST_ETIMEOUT = 7     /* a bounded device-side wait gave up */
+    FROST_ETIMEOUT = 7     /* reserved for a bounded device-side wait that gives up; no entry
+                              point of this version returns it: no kernel waits on a flag or
+                              on another block (teams synchronise through hardware block and
+                              cluster barriers only) */
 } frost_status;
 
 typedef enum {

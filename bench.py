@@ -46,6 +46,22 @@ UNIT = "interactions/s"
 TRAFFIC_ACC_PLUMMER64K = 388752.0
 
 
+# the bars the GPU tests hold the CUDA path to against the FP64 oracle (tests/test_gpu_parity.py)
+PARITY_BARS = {
+    "mixed": "a_i, g_i and a~_i within 1e-6 relative at the 99.9th percentile of the particles "
+             "(every particle of plummer_64k; sampled at 262144 and 1048576); the cross pass "
+             "whose every dominant slot is full, reversed, within 1e-7 x sum_j |term_ij|",
+    "fp64": "a_i, g_i and a~_i within 1e-12 relative for every particle; near tight pairs "
+            "(hard binaries, cross passes with every dominant slot full) g_i within 1e-12 x "
+            "sum_j |m_j K(x_ji) a_ji|, the bound of an FP64 sum of those terms, which exceeds "
+            "1e-12 |g_i| where the partners' terms cancel",
+    "timesteps": "FP64 1e-12 relative; mixed 2e-6 at the 99.9th percentile",
+    "partition, kick, drift": "bit-exact",
+    "trajectories": "FP64 positions within 1e-10 of the oracle over several hierarchical steps "
+                    "(N <= 2000; 16 steps at N = 1024); mixed vs FP64 |dE/E| within 2x",
+}
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -532,6 +548,7 @@ def run_frost(args):
                 "levels": {"calls": list(st["level_calls"][:st["max_depth_seen"] + 1]),
                            "particles": list(st["level_particles"][:st["max_depth_seen"] + 1]),
                            "note": "hhs_fsi calls and particles per hierarchy depth, timed steps"},
+                "parity": PARITY_BARS,
                 **extra}
         print(json.dumps(line), flush=True)
     if world > 1:

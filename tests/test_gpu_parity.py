@@ -1175,6 +1175,47 @@ def test_kroupa_hard_binaries_trajectory_fp64():
     assert np.max(np.abs(vg[:n_single] - vo[:n_single])) < 1e-12
 
 
+def test_kroupa_hard_binaries_mixed_integration_matches_fp64():
+    """Mixed precision through the whole hierarchy of a sphere with hard binaries: Plummer
+    N = 4096 with Kroupa masses and 5 % hard binaries (seed 31), one top-level step of 2^-10.
+    It runs the grid levels with their hot-source gradient path (the binary members' large
+    accelerations), the subtree solver and its one-warp path down to depth ~23.  It is compared
+    with the same step in FP64 on the GPU.
+
+    Tolerances.  The two runs reach the same depth, and the mixed energy error is within 2x of
+    the FP64 one (the criterion for mixed precision).  The single stars move regularly.  An
+    acceleration error eps |a| held over the step moves v by eps |a| t and x by eps |a| t^2 / 2.
+    With eps = 2e-7 (the mixed pass's 99.9th percentile) and A = 2x the 99th percentile of the
+    singles' |a| at t = 0, this bounds the 99.9th percentiles of their deviations.  With
+    eps = 1e-5 (the per-particle maximum) and 4 max |a| it bounds every single star.  The binary
+    members' own velocities are not compared: over their ~2^23 sub-steps a 1e-16 difference in
+    phase grows to O(1e-2) of their orbital speed in FP64 itself."""
+    n = 4096
+    m, x, v = ics.plummer_kroupa_binaries(n, 31)
+    ns = n - 2 * int(round(0.05 * n / 2.0))
+    t = 2.0 ** -10
+    out = {}
+    for prec in ("fp64", "mixed"):
+        f = F(m, x, v, precision=prec, eta=0.2)
+        e0 = f.energy()["E"]
+        f.step(t, 1)
+        e1 = f.energy()["E"]
+        xg, vg, _ = f.state()
+        out[prec] = (xg, vg, abs((e1 - e0) / e0), f.stats()["max_depth_seen"])
+        f.close()
+    assert out["fp64"][3] == out["mixed"][3] >= 15, (out["fp64"][3], out["mixed"][3])
+    assert out["mixed"][2] <= 2.0 * out["fp64"][2], (out["mixed"][2], out["fp64"][2])
+    singles = np.arange(ns, dtype=np.int32)
+    a0 = np.linalg.norm(oracle.acc(m, x, singles, np.arange(n, dtype=np.int32)), axis=1)
+    A = 2.0 * np.percentile(a0, 99.0)
+    dx = np.linalg.norm(out["mixed"][0][:ns] - out["fp64"][0][:ns], axis=1)
+    dv = np.linalg.norm(out["mixed"][1][:ns] - out["fp64"][1][:ns], axis=1)
+    assert p999(dx) < 0.5 * 2e-7 * A * t * t, (p999(dx), A)
+    assert p999(dv) < 2e-7 * A * t, (p999(dv), A)
+    amax = 4.0 * a0.max()
+    assert dx.max() < 0.5 * 1e-5 * amax * t * t and dv.max() < 1e-5 * amax * t, (dx.max(), dv.max(), amax)
+
+
 def test_plummer_64k_mixed_trajectory_matches_fp64():
     """Plummer N = 65536 (seed 2), two top-level steps of 2^-7 (t = 2^-6) in the mixed mode and
     in the FP64 mode on the GPU, compared particle by particle.

@@ -27,6 +27,16 @@ constexpr int STJ = 128;          // source records per shared-memory tile
 constexpr int SIB = SB * SILP;    // i-block of the mixed bodies
 constexpr int MAXD = SUBTREE_MAX_FRAMES;
 
+// The coefficients of one step h of the FSI and of kick_sf: h, h/6, 2h/3 and h^2/48.  A level's
+// pivot step is exactly half its parent's, and rounding commutes with scaling by a power of
+// two, so the coefficients of every level are exact powers-of-two multiples of those of the
+// launch's first step: a table of them per launch gives the bits of the divisions without the
+// divisions (an FP64 division is a sequence of FP64 instructions, each of which holds a
+// sub-partition's FP64 unit for about 64 cycles).
+struct StepK {
+    double h, k6, k23, k48;
+};
+
 struct SubParams {
     double *x, *v;
     const double *m;
@@ -42,6 +52,8 @@ struct SubParams {
     // warps 1..7 of a one-block team while warp 0 runs a fast set's subtree beside them)
     int tbase, tcount;
     int overlap;                   // run fsi(S) beside the warp path of F (one-block teams)
+    const StepK *K;                // shared: K[r] for the step tau0 2^-r, r = 0..MAXD
+    int kdepth0;                   // the depth of tau0
 };
 
 struct SubWork {
@@ -429,10 +441,10 @@ __device__ __noinline__ void b_acc(const SubParams &p, const SubWork &w, const i
     if (t_lead(p)) cnt.acc += self ? (unsigned long long)nA * (nA - 1) : (unsigned long long)nA * nB;
 }
 
-// Gradient pass of A against B with a_A, a_B ([3][n]); at[3][nA] = a_A + eps^2/48 g
+// Gradient pass of A against B with a_A, a_B ([3][n]); at[3][nA] = a_A + c48 g, c48 = eps^2/48
 template <bool MIXED>
 __device__ __noinline__ void b_grad(const SubParams &p, const SubWork &w, const int32_t *A, int nA, const double *aA,
-                       const int32_t *B, int nB, const double *aB, bool self, double eps_grad,
+                       const int32_t *B, int nB, const double *aB, bool self, double c48,
                        const float *wmax, double *at, Counts &cnt)
 {
     if (nA <= 0) return;
@@ -453,7 +465,7 @@ __device__ __noinline__ void b_grad(const SubParams &p, const SubWork &w, const 
         }
     t_sync(p);
     const int sp = self ? 1 : 0;
-    const double c = eps_grad * eps_grad / 48.0;
+    const double c = c48;  // eps^2 / 48, eps the step of the operator with the 2/3 kick
     const double scale = 2.0 * p.G;
     if (p.csize > 1 || nA <= MT_MAX || p.tcount != SB) {
         mt_grad<MIXED>(p, w.recA, self ? w.recA : w.recB, nA, nB, self, aA, MIXED ? wmax : nullptr, c, at, badbit);
@@ -633,13 +645,14 @@ __device__ void b_drift(const SubParams &p, const int32_t *L, int n, double dt)
     t_sync(p);
 }
 
-// Algorithm fsi on the set S with step dt.  cache: 1 keeps the final a^SS by particle in
-// p.aC, 2 starts from it (S has not moved between the two fsi(S) of one hhs_fsi call, and
-// the deeper levels only touch other particles)
+// Algorithm fsi on the set S with the step kc.h (coefficients kc).  cache: 1 keeps the final
+// a^SS by particle in p.aC, 2 starts from it (S has not moved between the two fsi(S) of one
+// hhs_fsi call, and the deeper levels only touch other particles)
 template <bool MIXED>
-__device__ __noinline__ void b_fsi(const SubParams &p, const SubWork &w, const int32_t *S, int nS, double dt, Counts &cnt,
-                                   int cache = 0)
+__device__ __noinline__ void b_fsi(const SubParams &p, const SubWork &w, const int32_t *S, int nS, const StepK &kc,
+                                   Counts &cnt, int cache = 0)
 {
+    const double dt = kc.h;
     if (nS <= 0) return;
     if (t_lead(p)) cnt.fsi += 1;
     if (nS < 2) cache = 0;
@@ -648,17 +661,17 @@ __device__ __noinline__ void b_fsi(const SubParams &p, const SubWork &w, const i
         for (int k = t_id(p); k < nS; k += t_n(p)) {
             const int i = S[k];
             for (int c = 0; c < 3; ++c)
-                p.v[c * p.N + i] = __dadd_rn(p.v[c * p.N + i], __dmul_rn(dt / 6.0, p.aC[c * p.N + i]));
+                p.v[c * p.N + i] = __dadd_rn(p.v[c * p.N + i], __dmul_rn(kc.k6, p.aC[c * p.N + i]));
         }
         t_sync(p);
     } else {
         b_acc<MIXED>(p, w, S, nS, S, nS, true, false, w.aA, nullptr, cnt);
-        b_kick(p, S, nS, w.aA, dt / 6.0);
+        b_kick(p, S, nS, w.aA, kc.k6);
     }
     b_drift(p, S, nS, 0.5 * dt);
     b_acc<MIXED>(p, w, S, nS, S, nS, true, true, w.aA, w.wA, cnt);
-    b_grad<MIXED>(p, w, S, nS, w.aA, S, nS, w.aA, true, dt, MIXED ? w.wA : nullptr, w.atA, cnt);
-    b_kick(p, S, nS, w.atA, 2.0 * dt / 3.0);
+    b_grad<MIXED>(p, w, S, nS, w.aA, S, nS, w.aA, true, kc.k48, MIXED ? w.wA : nullptr, w.atA, cnt);
+    b_kick(p, S, nS, w.atA, kc.k23);
     b_drift(p, S, nS, 0.5 * dt);
     b_acc<MIXED>(p, w, S, nS, S, nS, true, false, w.aA, nullptr, cnt);
     if (cache == 1) {
@@ -667,20 +680,21 @@ __device__ __noinline__ void b_fsi(const SubParams &p, const SubWork &w, const i
             for (int c = 0; c < 3; ++c) p.aC[c * p.N + i] = w.aA[c * nS + k];
         }
     }
-    b_kick(p, S, nS, w.aA, dt / 6.0);
+    b_kick(p, S, nS, w.aA, kc.k6);
 }
 
-// kick_sf: S kicked by its accelerations due to F, F by those due to S (computed first)
+// kick_sf: S kicked by its accelerations due to F, F by those due to S (computed first); with
+// the gradient, c48 = tau^2/48 of the level's pivot step tau
 template <bool MIXED>
 __device__ __noinline__ void b_kick_sf(const SubParams &p, const SubWork &w, const int32_t *S, int nS, const int32_t *F,
-                          int nF, double cdt, bool gradient, double tau, Counts &cnt)
+                          int nF, double cdt, bool gradient, double c48, Counts &cnt)
 {
     if (nS <= 0 || nF <= 0) return;
     b_acc<MIXED>(p, w, S, nS, F, nF, false, gradient, w.aA, gradient ? w.wA : nullptr, cnt);
     b_acc<MIXED>(p, w, F, nF, S, nS, false, gradient, w.aB, gradient ? w.wB : nullptr, cnt);
     if (gradient) {
-        b_grad<MIXED>(p, w, S, nS, w.aA, F, nF, w.aB, false, tau, MIXED ? w.wA : nullptr, w.atA, cnt);
-        b_grad<MIXED>(p, w, F, nF, w.aB, S, nS, w.aA, false, tau, MIXED ? w.wB : nullptr, w.atB, cnt);
+        b_grad<MIXED>(p, w, S, nS, w.aA, F, nF, w.aB, false, c48, MIXED ? w.wA : nullptr, w.atA, cnt);
+        b_grad<MIXED>(p, w, F, nF, w.aB, S, nS, w.aA, false, c48, MIXED ? w.wB : nullptr, w.atB, cnt);
         b_kick(p, S, nS, w.atA, cdt);
         b_kick(p, F, nF, w.atB, cdt);
     } else {
@@ -943,8 +957,9 @@ __device__ __forceinline__ void w_drift(WLane &L, bool on, double dt)
 // between the two fsi(S) of one hhs_fsi call, and the frames in between only touch the lanes
 // of F, which are not in S (the same a^SS, bit for bit, as a new pass)
 template <bool MIXED>
-__device__ void w_fsi(const SubParams &p, WLane &L, unsigned S, double dt, Counts &cnt, int cache = 0)
+__device__ void w_fsi(const SubParams &p, WLane &L, unsigned S, const StepK &kc, Counts &cnt, int cache = 0)
 {
+    const double dt = kc.h;
     if (!S) return;
     const int lane = threadIdx.x & 31;
     const bool in = (S >> lane) & 1u;
@@ -958,18 +973,18 @@ __device__ void w_fsi(const SubParams &p, WLane &L, unsigned S, double dt, Count
     } else {
         w_acc<MIXED>(p, L, S, src, false, a, wm);
     }
-    w_kick(L, in, a, dt / 6.0);
+    w_kick(L, in, a, kc.k6);
     w_drift<MIXED>(L, in, 0.5 * dt);
     w_acc<MIXED>(p, L, S, src, true, a, wm);
     w_grad<MIXED>(p, L, S, src, a, MIXED ? SLOT_FRACTION * wm : INFINITY, g);
-    const double c = dt * dt / 48.0;
+    const double c = kc.k48;
     for (int q = 0; q < 3; ++q) at[q] = a[q] + c * g[q];
-    w_kick(L, in, at, 2.0 * dt / 3.0);
+    w_kick(L, in, at, kc.k23);
     w_drift<MIXED>(L, in, 0.5 * dt);
     w_acc<MIXED>(p, L, S, src, false, a, wm);
     if (cache == 1 && in)
         for (int q = 0; q < 3; ++q) L.ac[q] = a[q];
-    w_kick(L, in, a, dt / 6.0);
+    w_kick(L, in, a, kc.k6);
     if (lane == 0) {
         cnt.fsi += 1;
         cnt.acc += (cache == 2 ? 2 : 3) * ns * (ns - 1);
@@ -980,7 +995,7 @@ __device__ void w_fsi(const SubParams &p, WLane &L, unsigned S, double dt, Count
 
 template <bool MIXED>
 __device__ void w_kick_sf(const SubParams &p, WLane &L, unsigned S, unsigned F, double cdt, bool gradient,
-                          double tau, Counts &cnt)
+                          double c48, Counts &cnt)
 {
     if (!S || !F) return;
     const int lane = threadIdx.x & 31;
@@ -994,8 +1009,7 @@ __device__ void w_kick_sf(const SubParams &p, WLane &L, unsigned S, unsigned F, 
     if (gradient) {
         double g[3];
         w_grad<MIXED>(p, L, U, src, a, MIXED ? SLOT_FRACTION * wm : INFINITY, g);
-        const double c = tau * tau / 48.0;
-        for (int q = 0; q < 3; ++q) a[q] = a[q] + c * g[q];
+        for (int q = 0; q < 3; ++q) a[q] = a[q] + c48 * g[q];
     }
     w_kick(L, inS || inF, a, cdt);
     if (lane == 0) {
@@ -1082,8 +1096,9 @@ __device__ __noinline__ int warp_hhs(const SubParams &p, const int32_t *Sg, int 
                 atomicAdd(&p.levels[Lv], 1ull);
                 atomicAdd(&p.levels[SUBTREE_STAT_LEVELS + Lv], np);
             }
-            w_kick_sf<MIXED>(p, L, Sn, Fn, ftau / 6.0, false, ftau, cnt);
-            w_fsi<MIXED>(p, L, Sn, 0.5 * ftau, cnt, 1);
+            const StepK &K0 = p.K[depth - p.kdepth0];
+            w_kick_sf<MIXED>(p, L, Sn, Fn, K0.k6, false, K0.k48, cnt);
+            w_fsi<MIXED>(p, L, Sn, p.K[depth - p.kdepth0 + 1], cnt, 1);
             if (lane == 0) {
                 wf_S[top] = Sn;
                 wf_pc[top] = 1;
@@ -1103,7 +1118,8 @@ __device__ __noinline__ int warp_hhs(const SubParams &p, const int32_t *Sg, int 
                 sp += 1;
             }
         } else if (pc == 1) {
-            w_kick_sf<MIXED>(p, L, S, F, 2.0 * ftau / 3.0, true, ftau, cnt);
+            const StepK &K0 = p.K[depth - p.kdepth0];
+            w_kick_sf<MIXED>(p, L, S, F, K0.k23, true, K0.k48, cnt);
             if (lane == 0) wf_pc[top] = 2;
             if (F) {
                 if (lane == 0) {
@@ -1116,8 +1132,9 @@ __device__ __noinline__ int warp_hhs(const SubParams &p, const int32_t *Sg, int 
                 sp += 1;
             }
         } else {
-            w_fsi<MIXED>(p, L, S, 0.5 * ftau, cnt, 2);
-            w_kick_sf<MIXED>(p, L, S, F, ftau / 6.0, false, ftau, cnt);
+            const StepK &K0 = p.K[depth - p.kdepth0];
+            w_fsi<MIXED>(p, L, S, p.K[depth - p.kdepth0 + 1], cnt, 2);
+            w_kick_sf<MIXED>(p, L, S, F, K0.k6, false, K0.k48, cnt);
             sp -= 1;
         }
         __syncwarp();
@@ -1159,7 +1176,7 @@ __device__ __noinline__ void fsi_beside_warp(const SubParams &p, const SubWork &
         SubParams q = p;
         q.tbase = 32;
         q.tcount = SB - 32;
-        b_fsi<MIXED>(q, w, S, nS, 0.5 * ftau, cnt, cache);
+        b_fsi<MIXED>(q, w, S, nS, p.K[depth - p.kdepth0 + 1], cnt, cache);
         if (t_lead(q)) cnt.beside += 1;
     }
     __syncthreads();
@@ -1182,8 +1199,18 @@ __global__ void __launch_bounds__(SB, MINB) k_hhs_subtree(SubParams p0, SubWork 
     __shared__ int f_lo[MAXD], f_n[MAXD], f_ns[MAXD], f_pc[MAXD], f_depth[MAXD];
     __shared__ double f_tau[MAXD];
     __shared__ int s_sp, s_abort, s_we;
+    __shared__ StepK s_K[MAXD + 1];
     const int tid = threadIdx.x;
     SubParams p = p0;
+    // the step coefficients of every level below depth0: K[r] for tau0 2^-r, the exact
+    // power-of-two multiples of tau0's own (read after the first team barrier)
+    if (tid <= MAXD) {
+        const double sc = __longlong_as_double((long long)(1023 - tid) << 52);  // 2^-tid
+        const double k6 = tau0 / 6.0, k23 = 2.0 * tau0 / 3.0, k48 = tau0 * tau0 / 48.0;
+        s_K[tid] = StepK{tau0 * sc, k6 * sc, k23 * sc, k48 * (sc * sc)};
+    }
+    p.K = s_K;
+    p.kdepth0 = depth0;
     {
         unsigned r, c;
         asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -1271,7 +1298,8 @@ __global__ void __launch_bounds__(SB, MINB) k_hhs_subtree(SubParams p0, SubWork 
                 b_tstep<MIXED, SYM>(p, w, S, fn, w.tau, cnt);
                 nS = b_partition(p, S, fn, w.tau, ftau, w.tmp);
                 const int nF = fn - nS;
-                b_kick_sf<MIXED>(p, w, S, nS, S + nS, nF, ftau / 6.0, false, ftau, cnt);
+                const StepK &K0 = p.K[depth - depth0];
+                b_kick_sf<MIXED>(p, w, S, nS, S + nS, nF, K0.k6, false, K0.k48, cnt);
                 if (f_beside(p, nS, nF, top + 1)) {
                     // fsi(S, tau/2) beside the first hhs_fsi(F, tau/2), which is then done
                     fsi_beside_warp<MIXED, SYM>(p, w, S, nS, nF, ftau, depth, cnt, 1, &s_we);
@@ -1281,7 +1309,7 @@ __global__ void __launch_bounds__(SB, MINB) k_hhs_subtree(SubParams p0, SubWork 
                         if (s_we & ERR_DEPTH) s_abort = 1;
                     }
                 } else {
-                    b_fsi<MIXED>(p, w, S, nS, 0.5 * ftau, cnt, 1);
+                    b_fsi<MIXED>(p, w, S, nS, p.K[depth - depth0 + 1], cnt, 1);
                     if (tid == 0) {
                         f_ns[top] = nS;
                         f_pc[top] = 1;
@@ -1303,13 +1331,14 @@ __global__ void __launch_bounds__(SB, MINB) k_hhs_subtree(SubParams p0, SubWork 
                 }
             } else if (pc == 1) {
                 const int nF = fn - nS;
-                b_kick_sf<MIXED>(p, w, S, nS, S + nS, nF, 2.0 * ftau / 3.0, true, ftau, cnt);
+                const StepK &K0 = p.K[depth - depth0];
+                b_kick_sf<MIXED>(p, w, S, nS, S + nS, nF, K0.k23, true, K0.k48, cnt);
                 if (f_beside(p, nS, nF, top + 1)) {
                     // the second fsi(S, tau/2) beside the second hhs_fsi(F, tau/2), then the
                     // closing kick_sf: the frame is done
                     fsi_beside_warp<MIXED, SYM>(p, w, S, nS, nF, ftau, depth, cnt, 2, &s_we);
                     const int e = s_we;
-                    if (!(e & ERR_DEPTH)) b_kick_sf<MIXED>(p, w, S, nS, S + nS, nF, ftau / 6.0, false, ftau, cnt);
+                    if (!(e & ERR_DEPTH)) b_kick_sf<MIXED>(p, w, S, nS, S + nS, nF, K0.k6, false, K0.k48, cnt);
                     if (tid == 0) {
                         if (e & ERR_DEPTH) s_abort = 1;
                         s_sp -= 1;
@@ -1328,8 +1357,9 @@ __global__ void __launch_bounds__(SB, MINB) k_hhs_subtree(SubParams p0, SubWork 
                 }
             } else {
                 const int nF = fn - nS;
-                b_fsi<MIXED>(p, w, S, nS, 0.5 * ftau, cnt, 2);
-                b_kick_sf<MIXED>(p, w, S, nS, S + nS, nF, ftau / 6.0, false, ftau, cnt);
+                const StepK &K0 = p.K[depth - depth0];
+                b_fsi<MIXED>(p, w, S, nS, p.K[depth - depth0 + 1], cnt, 2);
+                b_kick_sf<MIXED>(p, w, S, nS, S + nS, nF, K0.k6, false, K0.k48, cnt);
                 if (tid == 0) s_sp -= 1;
             }
             __syncthreads();

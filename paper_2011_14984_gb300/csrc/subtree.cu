@@ -738,7 +738,6 @@ __device__ __forceinline__ void w_record(WLane &L)
     L.mf = (float)L.m;
 }
 
-
 __device__ __forceinline__ float wsh(float v, int j) { return __shfl_sync(0xffffffffu, v, j); }
 __device__ __forceinline__ double wshd(double v, int j) { return __shfl_sync(0xffffffffu, v, j); }
 

@@ -121,6 +121,86 @@ __global__ void __launch_bounds__(1024) k_partition(const int32_t *__restrict__ 
     }
 }
 
+// The same stable partition by many blocks, for large sets: block b takes the entries
+// [b PART_CHUNK, (b + 1) PART_CHUNK).  k_part_count writes each block's slow count; k_part_scatter
+// starts each block at the slow and fast counts of the blocks before it and compacts its entries
+// with the single-block kernel's ballot scan, so S and F are the same lists in the same order.
+constexpr int PART_CHUNK = 4096;
+
+__device__ __forceinline__ int block_sum_1024(int c, int *wsum)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    __syncthreads();  // wsum may still be read from an earlier use
+    if (lane == 0) wsum[warp] = c;
+    __syncthreads();
+    int t = 0;
+    for (int q = 0; q < 32; ++q) t += wsum[q];
+    return t;
+}
+
+__global__ void __launch_bounds__(1024) k_part_count(int n, const double *__restrict__ tau, double pivot,
+                                                     int *__restrict__ blk)
+{
+    __shared__ int wsum[32];
+    const int lo = blockIdx.x * PART_CHUNK, hi = min(n, lo + PART_CHUNK);
+    int c = 0;
+    for (int k = lo + threadIdx.x; k < hi; k += 1024) c += (tau[k] >= pivot) ? 1 : 0;
+    const int t = block_sum_1024(c, wsum);
+    if (threadIdx.x == 0) blk[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(1024) k_part_scatter(const int32_t *__restrict__ set, int n,
+                                                       const double *__restrict__ tau, double pivot,
+                                                       const int *__restrict__ blk, int32_t *__restrict__ S,
+                                                       int32_t *__restrict__ F, int64_t *__restrict__ counts)
+{
+    __shared__ int wsum[32];
+    __shared__ int chunk_total;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lo = blockIdx.x * PART_CHUNK, hi = min(n, lo + PART_CHUNK);
+    int before = 0;
+    for (int b = tid; b < (int)blockIdx.x; b += 1024) before += blk[b];
+    int sbase = block_sum_1024(before, wsum);
+    int fbase = lo - sbase;
+    for (int c0 = lo; c0 < hi; c0 += 1024) {
+        const int k = c0 + tid;
+        const bool valid = k < hi;
+        const bool slow = valid && (tau[k] >= pivot);
+        const unsigned bal = __ballot_sync(0xffffffffu, slow);
+        const int rank = __popc(bal & ((1u << lane) - 1u));
+        __syncthreads();  // every thread has read wsum (block sum or the previous chunk)
+        if (lane == 0) wsum[warp] = __popc(bal);
+        __syncthreads();
+        if (warp == 0) {
+            const int vsum = wsum[lane];
+            int incl = vsum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            wsum[lane] = incl - vsum;  // exclusive prefix of slow counts per warp
+            if (lane == 31) chunk_total = incl;
+        }
+        __syncthreads();
+        if (valid) {
+            const int sidx = wsum[warp] + rank;  // slow entries before k in this chunk
+            const int id = set ? set[k] : k;
+            if (slow) S[sbase + sidx] = id;
+            else F[fbase + (tid - sidx)] = id;
+        }
+        const int tot = chunk_total;
+        const int nvalid = min(1024, hi - c0);
+        sbase += tot;
+        fbase += nvalid - tot;
+    }
+    if (tid == 0 && blockIdx.x == gridDim.x - 1) {
+        counts[0] = sbase;
+        counts[1] = fbase;
+    }
+}
+
 // list relation: B adds 1 to its marks, A adds 2; a repeated entry sees its own bit already set
 __global__ void k_mark_B(const int32_t *__restrict__ B, int nB, int N, int32_t *__restrict__ marks,
                          int64_t *__restrict__ out)
@@ -417,8 +497,14 @@ void launch_drift_pack(cudaStream_t s, const int32_t *list, int n, double *x, co
 }
 
 void launch_partition(cudaStream_t s, const int32_t *set, int n, const double *tau, double pivot,
-                      int32_t *S, int32_t *F, int64_t *counts)
+                      int32_t *S, int32_t *F, int64_t *counts, int *blk)
 {
+    if (blk && n >= PART_MULTI_MIN) {
+        const int nb = cdiv(n, PART_CHUNK);
+        k_part_count<<<nb, 1024, 0, s>>>(n, tau, pivot, blk);
+        k_part_scatter<<<nb, 1024, 0, s>>>(set, n, tau, pivot, blk, S, F, counts);
+        return;
+    }
     k_partition<<<1, 1024, 0, s>>>(set, n, tau, pivot, S, F, counts);
 }
 

@@ -179,6 +179,7 @@ struct frost_ctx {
     Misc *dmisc = nullptr, *hmisc = nullptr;
     std::vector<int32_t *> lvS, lvF;                 // per-level slow/fast lists
     unsigned *jbest = nullptr;                       // j-side minima of the symmetric time-step pass
+    int *pblk = nullptr;                             // per-block slow counts of the partition
     double *pj = nullptr;                            // j-side partials of the symmetric pass
     size_t pj_elems = 0;
     double *part_hot2 = nullptr;                     // B-side hot-source partials of the
@@ -1020,8 +1021,8 @@ frost_status hhs_head(frost_ctx *c, const int32_t *P, int nP, double tau, int de
     FROST_TRY(ensure_level(c, depth));
     Lane &M = c->main;
     pass_tstep(c, M, P, nP, c->tau);
-    launch_partition(M.s, P, nP, c->tau, tau, c->lvS[depth], c->lvF[depth], c->dmisc->counts);
-    c->st.kernel_launches += 1;
+    launch_partition(M.s, P, nP, c->tau, tau, c->lvS[depth], c->lvF[depth], c->dmisc->counts, c->pblk);
+    c->st.kernel_launches += nP >= PART_MULTI_MIN ? 2 : 1;
     h.done = false;
     return FROST_OK;
 }
@@ -1155,7 +1156,7 @@ void destroy(frost_ctx *c)
     if (c->d_ecl) cudaFree(c->d_ecl);
     void *dev[] = {c->x, c->v, c->m, c->all, c->marks, c->recA, c->recB, c->part,
                    c->aA, c->aB, c->atA, c->atB, c->aC, c->tau, c->wA, c->wB, c->perm,
-                   c->ptmp, c->dmisc, c->hist, c->hA, c->hB, c->part_hot, c->part_hot2, c->pcnt, c->pj, c->jbest};
+                   c->ptmp, c->dmisc, c->hist, c->hA, c->hB, c->part_hot, c->part_hot2, c->pcnt, c->pj, c->jbest, c->pblk};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (c->hmisc) cudaFreeHost(c->hmisc);
@@ -1303,6 +1304,7 @@ static frost_status init_impl(frost_ctx **out, int64_t n, const double *m, const
     INIT_CUDA(cudaMalloc(&c->pj, sizeof(double) * c->pj_elems));
     if (c->mixed) INIT_CUDA(cudaMalloc(&c->pcnt, (c->pj_elems / 3) * SYM_PCNT_WARPS));
     INIT_CUDA(cudaMalloc(&c->jbest, sizeof(unsigned) * N));
+    INIT_CUDA(cudaMalloc(&c->pblk, sizeof(int) * (size_t)partition_blocks((int)N)));
     INIT_CUDA(cudaMalloc(&c->perm, sizeof(int32_t) * N));
     INIT_CUDA(cudaMalloc(&c->ptmp, sizeof(int32_t) * N));
     if (n_clusters > 0) {
@@ -1562,8 +1564,8 @@ frost_status frost_partition(frost_ctx *c, const int32_t *set, int64_t n_set, co
     if (!c) return fail(FROST_EINVAL, "NULL context");
     FROST_TRY(check_sizes(c, n_set, "n_set"));
     if (n_set > 0 && (!tau || !S || !F)) return fail(FROST_EINVAL, "tau, S and F are required");
-    launch_partition(c->stream, set, (int)n_set, tau, tau_pivot, S, F, c->dmisc->counts);
-    c->st.kernel_launches += 1;
+    launch_partition(c->stream, set, (int)n_set, tau, tau_pivot, S, F, c->dmisc->counts, c->pblk);
+    c->st.kernel_launches += n_set >= PART_MULTI_MIN ? 2 : 1;
     FROST_CUDA(cudaGetLastError());
     FROST_TRY(sync_misc(c));
     if (n_slow) *n_slow = c->hmisc->counts[0];
@@ -1627,8 +1629,8 @@ frost_status hold2(frost_ctx *c, const int32_t *P, int nP, double tau, int depth
     FROST_TRY(ensure_level(c, depth));
     int32_t *S = c->lvS[depth], *F = c->lvF[depth];
     pass_tstep(c, c->main, P, nP, c->tau);
-    launch_partition(c->stream, P, nP, c->tau, tau, S, F, c->dmisc->counts);
-    c->st.kernel_launches += 1;
+    launch_partition(c->stream, P, nP, c->tau, tau, S, F, c->dmisc->counts, c->pblk);
+    c->st.kernel_launches += nP >= PART_MULTI_MIN ? 2 : 1;
     FROST_TRY(sync_misc(c));
     const int nS = (int)c->hmisc->counts[0];
     const int nF = (int)c->hmisc->counts[1];

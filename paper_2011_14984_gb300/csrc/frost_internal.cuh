@@ -171,8 +171,13 @@ void launch_drift_pack(cudaStream_t s, const int32_t *list, int n, double *x, co
                        const double *m, int N, double dt, void *rec, int mode);
 // stable partition: S gets set[k] with tau[k] >= pivot, F the rest; counts[0] = |S|,
 // counts[1] = |F|
+// stable slow / fast split (tau >= pivot first, both in list order); counts = {|S|, |F|}.  With
+// blk (int scratch of partition_blocks(n)) and n >= PART_MULTI_MIN, many blocks (two launches)
+// instead of one; the lists are the same.
+constexpr int PART_MULTI_MIN = 8192;
+inline int partition_blocks(int n) { return (n + 4095) / 4096; }
 void launch_partition(cudaStream_t s, const int32_t *set, int n, const double *tau,
-                      double pivot, int32_t *S, int32_t *F, int64_t *counts);
+                      double pivot, int32_t *S, int32_t *F, int64_t *counts, int *blk = nullptr);
 
 // ---- validation and reductions --------------------------------------------------------
 // marks[] (int32[N]) must be zero on entry and is returned to zero on exit.

@@ -566,6 +566,24 @@ def test_partition_bit_exact():
     f.close()
 
 
+@pytest.mark.parametrize("n", [8192, 12289, 65536])
+def test_partition_of_large_sets_bit_exact(n):
+    """Sets of 8192 and more are split by many blocks (per-block slow counts, then a scatter
+    from each block's offsets): the same lists as the oracle's stable partition, ties to the
+    slow set, at a multiple of the block's 4096 entries and with a ragged last block."""
+    m, x, v = ics.plummer(n + 100, 3)
+    f = F(m, x, v)
+    rng = np.random.default_rng(n)
+    P = rng.permutation(n + 100)[:n].astype(np.int32)
+    tau = rng.random(n)
+    tau[::7] = 0.5
+    for piv in (0.5, 0.0, 2.0, 0.123):
+        S, Fl = f.partition(P, tau, piv)
+        Sr, Fr = oracle.partition(P, tau, piv)
+        assert np.array_equal(cpu(S), Sr) and np.array_equal(cpu(Fl), Fr), piv
+    f.close()
+
+
 def test_kick_drift_bit_exact():
     n = 1000
     m, x, v = ics.plummer(n, 8)

@@ -58,3 +58,28 @@ def test_reference_arm_other_ranks_do_nothing(capsys, monkeypatch):
                         "gpus": 2})()
     bench.run_reference(ns)
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_keeps_the_contract():
+    """`bench.py --impl reference` on rank 0 (the FP64 oracle on the host cores, a bounded
+    sample): one JSON line with the arm's metric, unit and direction, its cpu_baseline
+    (kind, cores, sample, value = the line's) and an e2e object with no host-device bytes."""
+    import json
+    import subprocess
+    env = dict(os.environ)
+    env.pop("RANK", None)
+    env.pop("WORLD_SIZE", None)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "1"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout[-2000:]
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == "acc+gradient interactions/s"
+    assert d["unit"] == "interactions/s" and d["higher_is_better"] is True
+    assert d["steps"] == 1 and d["warmup"] == 1 and d["n_gpus"] == 1 and d["value"] > 0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
+    e2e = d["e2e"]
+    assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0

@@ -543,6 +543,7 @@ def run_frost(args):
                                          "once for both particles, counted in method, not in "
                                          "evaluated"},
                 "hhs_calls": st["hhs_calls"], "subtree_launches": st["subtree_launches"],
+                "subtree_fsi_beside": int(st.get("subtree_fsi_beside", 0)),
                 "subtree_ms": st_ev["timed_ms"][3],
                 "subtree": subtree_rate(st_ev, fp32_peak, probe),
                 "levels": {"calls": list(st["level_calls"][:st["max_depth_seen"] + 1]),
